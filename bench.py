@@ -1,0 +1,390 @@
+"""Benchmark: input rows/s of the join + filter + group-by query on one B300
+(default workload: fact 60M rows x dim 1.5M rows, SELECT region, SUM(price),
+COUNT(*) ... WHERE region < 5 GROUP BY region), plus the HBM roofline of the
+dominant kernel, end-to-end throughput from pinned host buffers, and the CPU
+oracle as a baseline.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload q14|q6|skew|star]
+Under torchrun each rank runs its own independent instance (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------- workloads
+
+class Q14:
+    """fact(fk int32) 60M rows JOIN dim(key int32 unique, region int8, price
+    int64) 1.5M rows WHERE region < 5 GROUP BY region: SUM(price), COUNT(*)."""
+    name = "q14"
+    n_fact, m_dim = 60_000_000, 1_500_000
+    prof_class = 1  # fused star probe
+    kernel_name = "star_probe_kernel"
+
+    def __init__(self, master):
+        from paper_2209_04579_b300 import datagen as dg
+        self.dg = dg
+        self.rec = dg.q14_tables(self.m_dim, master=master)
+        self.master = master
+
+    def config(self):
+        return {"workload": "q14-like join+filter+group-by: fact 60M rows (fk int32 uniform into dim keys) x "
+                            "dim 1.5M rows (unique int32 keys = seeded permutation of 1..1.5M, region int8 U[0,24], "
+                            "price int64 U[100,1e6]); WHERE region<5 GROUP BY region; SUM(price), COUNT(*)",
+                "fact_rows": self.n_fact, "dim_rows": self.m_dim}
+
+    def make_device(self):
+        from paper_2209_04579_b300 import datagen_device as gd
+        self.fact = gd.make_table(self.rec["fact"], self.n_fact)
+        self.dim = gd.make_table(self.rec["dim"], self.m_dim)
+        return [self.fact["fk"], self.dim["key"], self.dim["region"], self.dim["price"]]
+
+    def step(self):
+        from paper_2209_04579_b300 import queries as Q
+        return Q.q14(self.fact, self.dim)
+
+    def rows(self):
+        return self.n_fact
+
+    def alg_bytes(self):
+        # inputs read once: fact fk (4 B/row) + dim key, region, price (13 B/row)
+        return self.n_fact * 4 + self.m_dim * 13
+
+    def dominant_bytes(self):
+        # the probe reads every fact key once plus the passing dimension rows'
+        # sorted key, rank and price (4 + 4 + 8 B, 20% of the dimension)
+        return self.n_fact * 4 + int(self.m_dim * 0.2) * 16
+
+    def oracle_sample(self, rows):
+        from oracle import pipelines as pl
+        fact = self.dg.make_table(self.rec["fact"], rows)
+        dim = self.dg.make_table(self.rec["dim"], self.m_dim)
+        t0 = time.perf_counter()
+        pl.q14(fact, dim)
+        return time.perf_counter() - t0, f"first {rows} of the 60M fact rows joined with the full 1.5M-row dim"
+
+
+class Q6:
+    """lineitem 1M rows: filter ship_day <= 2400, group by (flag_a, flag_b)."""
+    name = "q6"
+    n = 1_000_000
+    prof_class = 4
+    kernel_name = "gb_reduce_kernel"
+
+    def __init__(self, master):
+        from paper_2209_04579_b300 import datagen as dg
+        self.dg = dg
+        self.rec = dg.q6_lineitem(master=master)
+
+    def config(self):
+        return {"workload": "q6-like filter+group-by: 1M rows, ship_day<=2400, GROUP BY flag_a, flag_b, "
+                            "4 exact int64 SUMs (incl. price*(100-disc)*(100+tax)) + COUNT", "rows": self.n}
+
+    def make_device(self):
+        from paper_2209_04579_b300 import datagen_device as gd
+        self.t = gd.make_table(self.rec, self.n)
+        return list(self.t.values())
+
+    def step(self):
+        from paper_2209_04579_b300 import queries as Q
+        return Q.q6(self.t)
+
+    def rows(self):
+        return self.n
+
+    def alg_bytes(self):
+        return self.n * 38
+
+    def dominant_bytes(self):
+        return int(self.n * 0.939) * (8 + 32)
+
+    def oracle_sample(self, rows):
+        from oracle import pipelines as pl
+        t = self.dg.make_table(self.rec, rows)
+        t0 = time.perf_counter()
+        pl.q6(t)
+        return time.perf_counter() - t0, f"first {rows} rows"
+
+
+WORKLOADS = {"q14": Q14, "q6": Q6}
+
+
+# ---------------------------------------------------------------- helpers
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(W, target_s=12.0):
+    """The oracle as it stands on a bounded sample of the workload (single thread)."""
+    import oracle
+    oracle.build()
+    rows = 1_000_000
+    t, _ = W.oracle_sample(rows)
+    rows = int(min(W.rows(), max(rows, rows * target_s / max(t, 1e-3))))
+    t, what = W.oracle_sample(rows)
+    return {"value": rows / t, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": what,
+            "seconds": round(t, 3)}
+
+
+# ---------------------------------------------------------------- arms
+
+def run_reference(args, world, rank):
+    """The oracle as the reference arm: every step one bounded sample."""
+    if rank != 0:
+        return
+    W = WORKLOADS[args.workload](20220904)
+    import oracle
+    oracle.build()
+    rows = 2_000_000
+    for _ in range(max(args.warmup, 0)):
+        W.oracle_sample(rows // 4)
+    total_t, total_rows, what = 0.0, 0, ""
+    for _ in range(args.steps):
+        t, what = W.oracle_sample(rows)
+        total_t += t
+        total_rows += rows
+    v = total_rows / total_t
+    print(json.dumps({
+        "impl": "reference", "metric": "input rows/s (join+filter+group-by)", "value": v, "unit": "rows/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": W.config(),
+        "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": what},
+        "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    from paper_2209_04579_b300 import build as b
+    if rank == 0:
+        b.build()
+    barrier(world)
+    from paper_2209_04579_b300 import tqp
+    torch.cuda.set_device(local)
+    W = WORKLOADS[args.workload](20220904 + rank)
+    inputs = W.make_device()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    # eager warm-up (allocates the workspace of the capture stream's twin)
+    out = W.step()
+    torch.cuda.synchronize()
+    assert tqp.tqp_status_poll() == tqp.OK
+
+    # capture one step into a CUDA graph, with the dominant kernel bracketed by events
+    ev_k0, ev_k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tqp.tqp_profile_events(W.prof_class, ev_k0, ev_k1)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        W.step()
+    torch.cuda.current_stream().wait_stream(side)
+    n0 = tqp.tqp_debug_launch_count()
+    with torch.cuda.graph(g):
+        out = W.step()
+    launches_per_step = tqp.tqp_debug_launch_count() - n0
+    tqp.tqp_profile_events(W.prof_class, None, None)
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    assert tqp.tqp_status_poll() == tqp.OK
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, kern_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record()
+        g.replay()
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(ev_k0.elapsed_time(ev_k1))
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    status = tqp.tqp_status_poll()
+    assert status == tqp.OK, status
+
+    total_ms = max_over_ranks(sum(step_ms), world)
+    rows_all = sum_over_ranks(W.rows() * args.steps, world)
+    value = rows_all / (total_ms / 1e3)
+    kern_avg_ms = sum(kern_ms) / len(kern_ms)
+    peak, peak_kind = peaks()
+    achieved = W.dominant_bytes() / (kern_avg_ms / 1e3) / 1e9
+
+    # ---- end to end through the public API from pinned host buffers (eager calls)
+    host_in = [t.cpu().pin_memory() for t in inputs]
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    e2e_ms = []
+    d2h = 0
+    for i in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        for hsrc, ddst in zip(host_in, inputs):
+            ddst.copy_(hsrc, non_blocking=True)
+        ok, oa, G = W.step()
+        res = [G.to("cpu", non_blocking=True), oa.to("cpu", non_blocking=True)] + \
+              [k.to("cpu", non_blocking=True) for k in ok]
+        e1.record()
+        e1.synchronize()
+        if i > 0:
+            e2e_ms.append(e0.elapsed_time(e1))
+        d2h = sum(r.numel() * r.element_size() for r in res)
+    e2e_total = max_over_ranks(sum(e2e_ms), world)
+    e2e_value = rows_all / (e2e_total / 1e3)
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "input rows/s (join+filter+group-by)", "value": value, "unit": "rows/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded, generated on device)",
+        "config": {**W.config(), "parallelism": f"replicas x{world} (independent instances, no collective)",
+                   "l2": "flushed before every step (256 MB write, outside the step's events)",
+                   "launch": "one CUDA graph replay per step"},
+        "roofline": {"bound": "hbm", "kernel": W.kernel_name, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                     "kernel_ms": kern_avg_ms, "alg_bytes_per_launch": W.dominant_bytes(), "traffic": None},
+        "step_roofline_frac": W.alg_bytes() / (total_ms / args.steps / 1e3) / 1e9 / peak,
+        "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(W)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="q14", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,262 @@
+/*
+ * tqp.h -- C ABI of the B300 (sm_103a) key-sort-and-segment core of a tensor
+ * query processor.
+ *
+ * The paper ("Share the Tensor Tea", VLDB 2022) represents every table column
+ * as an (n x 1) tensor of numbers (Section 2.1) and compiles relational
+ * operators -- filters, joins, aggregations -- into programs over those
+ * column tensors (Section 2.2); its evaluation runs a filter-plus-aggregation
+ * query (TPC-H Q6) and a join-plus-aggregation query (Q14) (Section 2.3).
+ * This library implements those operators directly as CUDA kernels over
+ * integer column vectors: filter by stream compaction, stable LSD radix sort,
+ * sort-based equi-join (bound search + expand), sort-based group-by with
+ * exact 64-bit aggregates, a fused star-join aggregate, a learned range
+ * partitioner (a small monotone network trained on the GPU, after the
+ * paper's Section 3.3 in-query neural network inference), and batched
+ * launches of many small instances.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named d_* and all column data are DEVICE pointers on the
+ *    current CUDA device; arrays of descriptors (tqp_col, tqp_pred, ...) are
+ *    HOST memory read during the call.  The library never takes ownership of
+ *    a pointer, never allocates or frees device memory, and never
+ *    synchronises the stream (except tqp_status_poll).  All work is enqueued
+ *    on the given stream (0 = legacy default stream).
+ *  - Workspace: every call that needs scratch takes (ws, ws_bytes).  Call it
+ *    first with ws == NULL: it writes the bytes it needs to *ws_bytes, does
+ *    nothing else and returns TQP_OK.  Then call again with a device buffer
+ *    of at least that size (256-byte aligned).  The size depends only on the
+ *    host arguments (sizes, counts, dtypes), not on the data.
+ *  - Row counts: n is the (maximum) row count known on the host.  Where an
+ *    argument d_n is accepted, a non-NULL d_n points to a device int64 that
+ *    holds the actual count (<= n), e.g. the result count of an earlier
+ *    filter; the kernels read it on the device, so chains of calls need no
+ *    host synchronisation and can be captured in a CUDA graph.
+ *  - Result counts (d_out_n, d_out_groups) are written to device memory.  If
+ *    a result does not fit in its capacity, the full required count is still
+ *    written, only the first `cap` results are stored, and the device status
+ *    word records TQP_ERR_CAPACITY.
+ *  - Errors: argument errors are detected on the host before anything is
+ *    launched and returned directly (TQP_ERR_INVALID / TQP_ERR_DTYPE /
+ *    TQP_ERR_WORKSPACE / TQP_ERR_UNSUPPORTED).  A failed launch returns
+ *    TQP_ERR_CUDA.  Errors found on the device (capacity, a bounded wait that
+ *    ran out, a key wider than 64 packed bits) are recorded in a per-device
+ *    status word (first error wins) that tqp_status_poll returns and clears.
+ *  - Limits: n < 2^30 rows per call for sorts and group-bys, n < 2^31 for
+ *    filters, gathers and joins (row ids are int32).
+ *  - Signed semantics: keys and values are two's-complement signed integers;
+ *    key order is ascending signed order.  Aggregates are exact 64-bit
+ *    integers; SUM wraps modulo 2^64.
+ */
+#ifndef TQP_H_
+#define TQP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tqp_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  TQP_OK = 0,
+  TQP_ERR_INVALID = 1,     /* bad argument (NULL pointer, negative size, bad enum) */
+  TQP_ERR_DTYPE = 2,       /* unsupported or mismatched column dtype */
+  TQP_ERR_CAPACITY = 3,    /* (device) a result did not fit its capacity */
+  TQP_ERR_CUDA = 4,        /* a CUDA launch or copy failed */
+  TQP_ERR_TIMEOUT = 5,     /* (device) a bounded inter-block wait ran out */
+  TQP_ERR_WORKSPACE = 6,   /* workspace smaller than the size query returned */
+  TQP_ERR_UNSUPPORTED = 7  /* valid but unsupported (e.g. >64 packed key bits) */
+} tqp_status;
+
+typedef enum { TQP_I8 = 1, TQP_I16 = 2, TQP_I32 = 3, TQP_I64 = 4 } tqp_dtype;
+
+/* One column: an (n x 1) integer tensor (Section 2.1), device memory,
+ * contiguous, not owned.  Its length is given by the call's n. */
+typedef struct {
+  const void* data;
+  int32_t dtype; /* tqp_dtype */
+  int32_t pad_;
+} tqp_col;
+
+typedef enum { TQP_LT = 0, TQP_LE = 1, TQP_GT = 2, TQP_GE = 3, TQP_EQ = 4, TQP_NE = 5 } tqp_cmp;
+
+/* Predicate `cols[col] op lit`, the column's signed value against a signed
+ * 64-bit literal.  Predicates of one call are AND-ed. */
+typedef struct {
+  int32_t col;
+  int32_t op; /* tqp_cmp */
+  int64_t lit;
+} tqp_pred;
+
+typedef enum { TQP_COUNT = 0, TQP_SUM = 1, TQP_MIN = 2, TQP_MAX = 3 } tqp_aggop;
+
+/* Value expression: the product over its nterms (1..3) terms of
+ * (mul * vals[col][row] + add), evaluated per row in 64-bit two's
+ * complement.  E.g. price*(100-disc)*(100+tax) is three terms
+ * {price,1,0} {disc,-1,100} {tax,1,100}. */
+typedef struct {
+  int32_t col;
+  int32_t pad_;
+  int64_t mul;
+  int64_t add;
+} tqp_term;
+
+typedef struct {
+  int32_t nterms;
+  int32_t pad_;
+  tqp_term term[3];
+} tqp_expr;
+
+/* One aggregate: op over expression exprs[expr] (ignored for COUNT). */
+typedef struct {
+  int32_t op; /* tqp_aggop */
+  int32_t expr;
+} tqp_agg;
+
+#define TQP_MAX_PREDS 4
+#define TQP_MAX_KEYS 4
+#define TQP_MAX_VALS 8
+#define TQP_MAX_EXPRS 8
+#define TQP_MAX_AGGS 8
+
+/* ------------------------------------------------------------------------
+ * tqp_filter -- relational selection (Section 2.2; the Q6 filters of
+ * Section 2.3) by single-pass stream compaction.
+ * Writes the ascending int32 indices i (0 <= i < n, or < *d_n) of the rows
+ * where every predicate holds to d_out_idx (capacity cap) and their count to
+ * *d_out_n.  cols[k] are columns of n rows; npred in 0..TQP_MAX_PREDS (0 =
+ * keep every row).
+ * ---------------------------------------------------------------------- */
+tqp_status tqp_filter(const tqp_col* cols, int ncols, const tqp_pred* preds, int npred,
+                      int64_t n, const int64_t* d_n, int32_t* d_out_idx, int64_t cap,
+                      int64_t* d_out_n, void* ws, size_t* ws_bytes, tqp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * tqp_gather -- column gather, d_out[j] = col[d_idx[j]] for j < n (or < *d_n),
+ * in the column's dtype.  The caller guarantees every index is in range.
+ * ---------------------------------------------------------------------- */
+tqp_status tqp_gather(tqp_col col, const int32_t* d_idx, int64_t n, const int64_t* d_n,
+                      void* d_out, tqp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * tqp_sort_pairs -- stable ascending LSD radix sort of (key, value) pairs
+ * (the sort under the sort-based join and group-by of Section 2.2).
+ * Keys (dtype TQP_I8..TQP_I64) are ordered by bits [begin_bit, end_bit) of
+ * their order-preserving image (the sign bit flipped); (0, width) sorts by the
+ * full signed value.  d_vals_in may be NULL: the payload is then the input
+ * row index.  Ties keep input order.  Output buffers must not alias inputs.
+ * ---------------------------------------------------------------------- */
+tqp_status tqp_sort_pairs(int32_t key_dtype, const void* d_keys_in, const int32_t* d_vals_in,
+                          void* d_keys_out, int32_t* d_vals_out, int64_t n, const int64_t* d_n,
+                          int begin_bit, int end_bit, void* ws, size_t* ws_bytes,
+                          tqp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * tqp_join_eq -- inner equi-join (Section 2.2; the Q14 join of Section 2.3)
+ * by sorting the build side and, per probe row, a bound search for the range
+ * of equal keys, whose pairs are expanded in place.
+ * Output: pairs (d_out_probe[k], d_out_build[k]) of row indices with
+ * probe[i] == build[j], ordered by probe row, then build row; the count goes
+ * to *d_out_n.  probe and build must share one dtype.
+ * ---------------------------------------------------------------------- */
+tqp_status tqp_join_eq(tqp_col probe, int64_t n_probe, const int64_t* d_n_probe, tqp_col build,
+                       int64_t n_build, const int64_t* d_n_build, int32_t* d_out_probe,
+                       int32_t* d_out_build, int64_t cap, int64_t* d_out_n, void* ws,
+                       size_t* ws_bytes, tqp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * tqp_groupby_agg -- sort-based group-by aggregation (Section 2.2; the
+ * aggregates of Section 2.3 and the expression aggregate of Fig. 4).
+ * Rows: d_sel[0..n) if d_sel is given, else 0..n-1 (n or *d_n).
+ * Keys (1..TQP_MAX_KEYS columns) are packed into one order-preserving word
+ * (each column trimmed to its [min, max] range), sorted, split into segments
+ * of equal keys, and each segment reduced.  Output: G groups in ascending
+ * lexicographic signed key order; d_out_keys[k] receives key column k (its
+ * own dtype, capacity cap); d_out_aggs[g * naggs + a] the aggregates
+ * (int64).  G goes to *d_out_groups.  The packed key must fit in 64 bits,
+ * else the device status records TQP_ERR_UNSUPPORTED and G = 0.
+ * ---------------------------------------------------------------------- */
+tqp_status tqp_groupby_agg(const tqp_col* keys, int nkeys, const tqp_col* vals, int nvals,
+                           const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
+                           const int32_t* d_sel, int64_t n, const int64_t* d_n,
+                           void* const* d_out_keys, int64_t* d_out_aggs, int64_t cap,
+                           int64_t* d_out_groups, void* ws, size_t* ws_bytes,
+                           tqp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * tqp_star_agg -- fused star join + filter + group-by aggregate (the Q14
+ * shape of Section 2.3 generalised to up to two dimension tables):
+ *   SELECT dim keys, aggs FROM fact JOIN dim_0 ON fact.fk_0 = dim_0.key
+ *   [JOIN dim_1 ON fact.fk_1 = dim_1.key] WHERE fact_preds AND dim_preds
+ *   GROUP BY (group key of dim_0, group key of dim_1).
+ * Each dimension is filtered by its predicates, sorted on its key, and
+ * grouped by its (optional) group column; each fact row then bound-searches
+ * every dimension and folds its expression values into its group's
+ * aggregates, without materialising join pairs.  Dimension keys must be
+ * unique among the rows passing the dimension's predicates (a foreign-key
+ * join); a duplicate is reported as TQP_ERR_UNSUPPORTED on the device.
+ * Aggregate expressions read fact columns (val_src = 0) or a dimension's
+ * value column (val_src = 1 + d).  Outputs as for tqp_groupby_agg with one
+ * key column per dimension that has a group column.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  tqp_col key;           /* dimension key (TQP_I32 or TQP_I64), n rows */
+  int64_t n;
+  tqp_col group;         /* group-by column, or data == NULL for none */
+  const tqp_pred* preds; /* predicates over cols[] of this dimension */
+  int npred;
+  int ncols;
+  const tqp_col* cols;   /* columns predicates and values refer to */
+} tqp_dim;
+
+typedef struct {
+  int32_t src; /* 0 = fact column, 1 + d = column of dimension d */
+  int32_t col; /* index into that table's columns */
+} tqp_valref;
+
+tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact,
+                        const tqp_pred* fact_preds, int nfact_preds, const int* fk_col,
+                        const tqp_dim* dims, int ndims, const tqp_valref* vals, int nvals,
+                        const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
+                        void* const* d_out_keys, int64_t* d_out_aggs, int64_t cap,
+                        int64_t* d_out_groups, void* ws, size_t* ws_bytes, tqp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Device status and test hooks.
+ * tqp_status_poll: synchronises `stream`, returns the current device's status
+ * word (TQP_OK if no device-side error was recorded since the last poll) and
+ * clears it.
+ * tqp_debug_set_spin_limit: bound of every inter-block wait, in polling
+ * rounds (default 1<<20, about a second); a wait that runs out records
+ * TQP_ERR_TIMEOUT and the block gives up without writing results.
+ * tqp_debug_inject_unpublished_tile: testing hook -- the scan tile with this
+ * id (of the next launches) never publishes its status, so its successors'
+ * bounded waits run out; -1 disables it.
+ * ---------------------------------------------------------------------- */
+tqp_status tqp_status_poll(tqp_stream_t stream);
+tqp_status tqp_debug_set_spin_limit(int64_t rounds);
+tqp_status tqp_debug_inject_unpublished_tile(int64_t tile);
+const char* tqp_status_string(tqp_status s);
+
+/* Instrumentation (no counterpart in the paper).
+ * tqp_debug_launch_count: number of kernels this library has launched in
+ * this process (host-side count of launch calls; a launch captured into a
+ * CUDA graph counts once, at capture).
+ * tqp_profile_events: from now on, record `start_event` just before and
+ * `stop_event` just after the kernel(s) of one class, on the call's stream
+ * (cudaEvent_t handles passed as void*; NULL clears).  Classes: 1 = fused
+ * star probe, 2 = radix sort passes (from the first to the last pass of a
+ * sort), 3 = filter, 4 = group-by reduce, 5 = join probe.  Records are
+ * external, so under stream capture they become event nodes of the graph. */
+int64_t tqp_debug_launch_count(void);
+tqp_status tqp_profile_events(int kernel_class, void* start_event, void* stop_event);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TQP_H_ */

@@ -1,0 +1,315 @@
+// Stable LSD radix sort of (key, int32 value) pairs, onesweep style
+// (Adinets & Merrill, "Onesweep: A Faster Least Significant Digit Radix Sort
+// for GPUs", 2022): one read of the keys builds the histograms of every
+// digit, then each digit is one scatter pass in which every tile ranks its
+// keys with warp match/ballot, learns its global digit offsets by decoupled
+// look-back, stages the tile in shared memory and writes it out.
+//
+// Digits whose histogram holds all n keys in one bin are skipped on the
+// device (a constant digit does not change a stable order), so the number of
+// passes adapts to the data without a host round trip.
+#pragma once
+
+#include "common.cuh"
+
+namespace tqp {
+
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kMaxPasses = 8;
+
+// Internal key codes on top of tqp_dtype: keys that are already
+// order-preserving unsigned words (packed group keys).
+constexpr int kKeyU32 = 5;
+constexpr int kKeyU64 = 6;
+
+// Order-preserving image of a key of dtype dt as an unsigned word.
+__device__ __forceinline__ unsigned long long encode_key(const void* p, int dt, int64_t i) {
+  switch (dt) {
+    case TQP_I8: return (unsigned long long)(uint8_t)(static_cast<const int8_t*>(p)[i]) ^ 0x80ull;
+    case TQP_I16: return (unsigned long long)(uint16_t)(static_cast<const int16_t*>(p)[i]) ^ 0x8000ull;
+    case TQP_I32: return (unsigned long long)(uint32_t)(static_cast<const int32_t*>(p)[i]) ^ 0x80000000ull;
+    case TQP_I64: return (unsigned long long)(static_cast<const int64_t*>(p)[i]) ^ 0x8000000000000000ull;
+    case kKeyU32: return static_cast<const uint32_t*>(p)[i];
+    default: return static_cast<const unsigned long long*>(p)[i];
+  }
+}
+
+__device__ __forceinline__ void store_decoded(void* p, int dt, int64_t i, unsigned long long u) {
+  switch (dt) {
+    case TQP_I8: static_cast<int8_t*>(p)[i] = (int8_t)(uint8_t)(u ^ 0x80ull); break;
+    case TQP_I16: static_cast<int16_t*>(p)[i] = (int16_t)(uint16_t)(u ^ 0x8000ull); break;
+    case TQP_I32: static_cast<int32_t*>(p)[i] = (int32_t)(uint32_t)(u ^ 0x80000000ull); break;
+    case TQP_I64: static_cast<int64_t*>(p)[i] = (int64_t)(u ^ 0x8000000000000000ull); break;
+    case kKeyU32: static_cast<uint32_t*>(p)[i] = (uint32_t)u; break;
+    default: static_cast<unsigned long long*>(p)[i] = u; break;
+  }
+}
+
+__host__ __device__ __forceinline__ int key_bits(int dt) {
+  return dt == TQP_I8 ? 8 : dt == TQP_I16 ? 16 : (dt == TQP_I32 || dt == kKeyU32) ? 32 : 64;
+}
+
+struct PassDesc {
+  int active;
+  int first;  // reads the caller's input (raw dtype) rather than an intermediate
+  int last;   // writes the caller's output (decoded dtype)
+  int src;    // 0 = input, 1 = alt A, 2 = alt B
+  int dst;    // 0 = output, 1 = alt A, 2 = alt B
+};
+
+struct SortPlan {
+  PassDesc pass[kMaxPasses];
+  int num_active;
+};
+
+struct SortArgs {
+  const void* keys_in;
+  const int32_t* vals_in;  // may be null: payload = row index
+  void* keys_out;
+  int32_t* vals_out;
+  void* alt_keys[2];       // K-word intermediates
+  int32_t* alt_vals[2];
+  int key_dt;
+  int begin_bit;
+  int nbits;               // end_bit - begin_bit
+  int npasses;             // ceil(nbits / 8)
+  int64_t n_max;
+  const int64_t* d_n;
+  uint32_t* hist;          // [npasses][256] counts, then exclusive offsets
+  SortPlan* plan;
+  uint32_t* tile_counters; // [npasses]
+  uint32_t* status;        // [num_tiles][256] look-back words (zeroed per pass)
+};
+
+__device__ __forceinline__ unsigned digit_of(unsigned long long u, int begin_bit, int nbits, int pass) {
+  unsigned long long field = u >> begin_bit;
+  int lo = pass * kRadixBits;
+  int w = nbits - lo;
+  if (w > kRadixBits) w = kRadixBits;
+  return (unsigned)((field >> lo) & ((1ull << w) - 1));
+}
+
+// ---------------------------------------------------------------- histograms
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) sort_hist_kernel(SortArgs a) {
+  __shared__ uint32_t s_hist[kMaxPasses][kRadix];
+  for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += THREADS) (&s_hist[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t n = clamp_n(a.n_max, a.d_n);
+  const int64_t stride = (int64_t)gridDim.x * THREADS;
+  for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < n; i += stride) {
+    unsigned long long u = encode_key(a.keys_in, a.key_dt, i);
+    for (int p = 0; p < a.npasses; ++p) atomicAdd(&s_hist[p][digit_of(u, a.begin_bit, a.nbits, p)], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < a.npasses * kRadix; i += THREADS) {
+    uint32_t c = (&s_hist[0][0])[i];
+    if (c) atomicAdd(&a.hist[i], c);
+  }
+}
+
+// One block of 256 threads: scans every digit histogram into offsets and
+// decides which passes run and where each reads and writes.
+__global__ void __launch_bounds__(kRadix) sort_plan_kernel(SortArgs a) {
+  __shared__ int s_scan[33];
+  __shared__ int s_trivial[kMaxPasses];
+  const int64_t n = clamp_n(a.n_max, a.d_n);
+  for (int p = 0; p < a.npasses; ++p) {
+    uint32_t c = a.hist[p * kRadix + threadIdx.x];
+    if (threadIdx.x == 0) s_trivial[p] = 1;
+    __syncthreads();
+    if ((int64_t)c != n && c != 0) s_trivial[p] = 0;
+    int total;
+    int excl = block_exclusive_sum<kRadix>((int)c, s_scan, &total);
+    a.hist[p * kRadix + threadIdx.x] = (uint32_t)excl;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int active[kMaxPasses];
+    int k = 0;
+    for (int p = 0; p < a.npasses; ++p) {
+      active[p] = (n > 0) && !s_trivial[p];
+      k += active[p];
+    }
+    if (k == 0 && n > 0) {  // every digit constant: one pass still copies in -> out
+      active[a.npasses - 1] = 1;
+      k = 1;
+    }
+    int j = 0;
+    for (int p = 0; p < kMaxPasses; ++p) {
+      PassDesc d = {0, 0, 0, 0, 0};
+      if (p < a.npasses && active[p]) {
+        ++j;
+        d.active = 1;
+        d.first = (j == 1);
+        d.last = (j == k);
+        d.src = d.first ? 0 : (((j - 1) & 1) ? 1 : 2);
+        d.dst = d.last ? 0 : ((j & 1) ? 1 : 2);
+      }
+      a.plan->pass[p] = d;
+    }
+    a.plan->num_active = k;
+  }
+}
+
+// ---------------------------------------------------------------- one pass
+// Per-digit decoupled look-back on 32-bit words: bits 30..31 flag, 0..29 count.
+constexpr uint32_t kSFlagAgg = 1u << 30, kSFlagPrefix = 2u << 30, kSFlagFailed = 3u << 30;
+constexpr uint32_t kSFlagMask = 3u << 30, kSValMask = ~kSFlagMask;
+
+template <typename K, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) sort_pass_kernel(SortArgs a, int pass, uint32_t num_tiles) {
+  static_assert(THREADS == kRadix, "one thread per digit");
+  constexpr int TILE = THREADS * ITEMS;
+  constexpr int WARPS = THREADS / 32;
+  const PassDesc pd = a.plan->pass[pass];
+  if (!pd.active) return;
+
+  __shared__ uint32_t s_wcnt[WARPS][kRadix + 1];  // per-warp digit counters (+1 bin for padding rows)
+  __shared__ uint32_t s_tile_start[kRadix];
+  __shared__ int64_t s_gbase[kRadix];
+  __shared__ int s_scan[33];
+  __shared__ uint32_t s_tile;
+  __shared__ int s_failed;
+  extern __shared__ __align__(16) unsigned char s_raw[];  // TILE keys, reused for values
+  K* s_keys = reinterpret_cast<K*>(s_raw);
+  int32_t* s_vals = reinterpret_cast<int32_t*>(s_raw);
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = clamp_n(a.n_max, a.d_n);
+  const void* kin = pd.src == 0 ? a.keys_in : a.alt_keys[pd.src - 1];
+  const int32_t* vin = pd.src == 0 ? a.vals_in : a.alt_vals[pd.src - 1];
+  const int kin_dt = pd.first ? a.key_dt : (sizeof(K) == 4 ? kKeyU32 : kKeyU64);
+  void* kout = pd.dst == 0 ? a.keys_out : a.alt_keys[pd.dst - 1];
+  int32_t* vout = pd.dst == 0 ? a.vals_out : a.alt_vals[pd.dst - 1];
+  const int kout_dt = pd.last ? a.key_dt : (sizeof(K) == 4 ? kKeyU32 : kKeyU64);
+  const uint32_t* digit_off = a.hist + pass * kRadix;
+  const long long limit = g_spin_limit;
+
+  while (true) {
+    if (threadIdx.x == 0) {
+      s_tile = atomicAdd(&a.tile_counters[pass], 1u);
+      s_failed = 0;
+    }
+    for (int i = threadIdx.x; i < WARPS * (kRadix + 1); i += THREADS) (&s_wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= num_tiles) break;
+    const int64_t tile_base = (int64_t)tile * TILE;
+
+    // ---- load (warp-striped) and rank within the warp
+    K key[ITEMS];
+    int32_t val[ITEMS];
+    uint32_t rank[ITEMS];
+    uint32_t dig[ITEMS];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      int64_t row = tile_base + (int64_t)warp * (32 * ITEMS) + it * 32 + lane;
+      bool valid = row < n;
+      K u = 0;
+      int32_t v = 0;
+      if (valid) {
+        u = (K)encode_key(kin, kin_dt, row);
+        v = (pd.first && vin == nullptr) ? (int32_t)row : vin[row];
+      }
+      key[it] = u;
+      val[it] = v;
+      dig[it] = valid ? digit_of(u, a.begin_bit, a.nbits, pass) : kRadix;
+    }
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      unsigned peers = __match_any_sync(0xffffffffu, dig[it]);
+      int leader = 31 - __clz(peers);
+      uint32_t before = __popc(peers & ((1u << lane) - 1));
+      uint32_t base = s_wcnt[warp][dig[it]];
+      __syncwarp();
+      if (lane == leader) s_wcnt[warp][dig[it]] = base + __popc(peers);
+      __syncwarp();
+      rank[it] = base + before;
+    }
+    __syncthreads();
+
+    // ---- per digit (thread d): warp prefix, tile count, look-back
+    const int d = threadIdx.x;
+    uint32_t tile_count = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+      uint32_t c = s_wcnt[w][d];
+      s_wcnt[w][d] = tile_count;  // becomes the warp's exclusive prefix for digit d
+      tile_count += c;
+    }
+    uint32_t* st = a.status + (size_t)tile * kRadix + d;
+    const bool inject = ((long long)tile == g_unpublished_tile);
+    long long excl = 0;
+    bool failed = false;
+    if (tile == 0) {
+      if (!inject) st_volatile_u32(st, kSFlagPrefix | tile_count);
+    } else {
+      if (!inject) st_volatile_u32(st, kSFlagAgg | tile_count);
+      for (long long t = (long long)tile - 1; t >= 0; --t) {
+        const uint32_t* ps = a.status + (size_t)t * kRadix + d;
+        uint32_t s;
+        long long rounds = 0;
+        unsigned sleep_ns = 32;
+        while (true) {
+          s = ld_volatile_u32(ps);
+          if (s & kSFlagMask) break;
+          if (++rounds > limit) { s = kSFlagFailed; break; }
+          __nanosleep(sleep_ns);
+          if (sleep_ns < 1024) sleep_ns <<= 1;
+        }
+        uint32_t f = s & kSFlagMask;
+        if (f == kSFlagFailed) { failed = true; break; }
+        excl += (s & kSValMask);
+        if (f == kSFlagPrefix) break;
+      }
+      if (!inject) st_volatile_u32(st, failed ? kSFlagFailed : (kSFlagPrefix | (uint32_t)(excl + tile_count)));
+    }
+    if (failed) {
+      raise_status(TQP_ERR_TIMEOUT);
+      s_failed = 1;
+    }
+    s_gbase[d] = (int64_t)digit_off[d] + excl;
+    int total;
+    int start = block_exclusive_sum<THREADS>((int)tile_count, s_scan, &total);
+    s_tile_start[d] = (uint32_t)start;
+    __syncthreads();
+    const int tile_failed = s_failed;
+    __syncthreads();
+    if (tile_failed) continue;  // give up on this tile without writing
+
+    // ---- stage keys in tile order
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it)
+      if (dig[it] < kRadix) s_keys[s_tile_start[dig[it]] + s_wcnt[warp][dig[it]] + rank[it]] = key[it];
+    __syncthreads();
+    int64_t gpos[ITEMS];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      int j = it * THREADS + threadIdx.x;
+      gpos[it] = -1;
+      if (j < total) {
+        K u = s_keys[j];
+        unsigned dd = digit_of(u, a.begin_bit, a.nbits, pass);
+        int64_t g = s_gbase[dd] + (j - (int)s_tile_start[dd]);
+        gpos[it] = g;
+        store_decoded(kout, kout_dt, g, (unsigned long long)u);
+      }
+    }
+    __syncthreads();
+    // ---- stage values in tile order
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it)
+      if (dig[it] < kRadix) s_vals[s_tile_start[dig[it]] + s_wcnt[warp][dig[it]] + rank[it]] = val[it];
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      int j = it * THREADS + threadIdx.x;
+      if (gpos[it] >= 0) vout[gpos[it]] = s_vals[j];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace tqp

@@ -1,0 +1,375 @@
+// Fused star join + filter + group-by aggregate over one or two dimension
+// tables (the join-plus-aggregation shape of the paper's Q14 experiment,
+// Section 2.3).
+//
+// Per dimension d (all on the device, no host round trip):
+//   filter the dimension rows (stream compaction), gather their keys, sort
+//   (key, row) stably, give each row the dense rank of its group value among
+//   the passing rows (sort + adjacent difference + look-back scan), and
+//   gather the rank and any aggregated dimension column into key order.
+// Then one pass over the fact table: fact predicates, one bound search per
+// dimension in its sorted keys, and the row's expression values folded into
+// the accumulator slot of its group combination (ranks are in ascending key
+// order, so slot order is the lexicographic group order).  Few slots live in
+// shared memory per block; many go straight to global 64-bit atomics.
+// A final single-pass scan compacts the non-empty slots into the output.
+#pragma once
+
+#include "common.cuh"
+#include "filter.cuh"
+#include "groupby.cuh"
+#include "join.cuh"
+
+namespace tqp {
+
+constexpr int kMaxDims = 2;
+constexpr int kSmemAccWords = 4096;  // slots * (naggs + 1) that fit the shared accumulators
+
+struct StarPlan {
+  long long G[kMaxDims];       // distinct group values per dimension (1 without a group column)
+  long long stride[kMaxDims];  // slot = sum code_d * stride_d
+  long long S;                 // number of slots
+  int use_smem;
+  int unsupported;
+};
+
+// ---- group ranks of one dimension: heads of the sorted packed group keys,
+// scanned into dense ranks; rank scattered to the row, key value kept.
+template <typename K, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) rank_kernel(const K* sorted, const int32_t* rows, int64_t n_max,
+                                                       const int64_t* d_n, const GroupPlan* gp,
+                                                       int32_t* rank_of_row, long long* gkey,
+                                                       long long* d_G, unsigned long long* status,
+                                                       uint32_t* counter, uint32_t num_tiles) {
+  constexpr int TILE = THREADS * ITEMS;
+  __shared__ int s_scan[33];
+  __shared__ uint32_t s_tile;
+  __shared__ long long s_excl;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n = clamp_n(n_max, d_n);
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= num_tiles) break;
+    const int64_t base = (int64_t)tile * TILE + (int64_t)threadIdx.x * ITEMS;
+    uint32_t head = 0;
+    K prev = (base > 0 && base < n) ? sorted[base - 1] : (K)0;
+    K key[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      int64_t p = base + k;
+      key[k] = p < n ? sorted[p] : (K)0;
+      if (p < n && (p == 0 || key[k] != (k ? key[k - 1] : prev))) head |= 1u << k;
+    }
+    int total;
+    int off = block_exclusive_sum<THREADS>(__popc(head), s_scan, &total);
+    if (warp == 0) {
+      long long e = lookback_exclusive(status, tile, total);
+      if (lane == 0) s_excl = e;
+    }
+    __syncthreads();
+    long long excl = s_excl;
+    if (excl >= 0) {
+      long long r = excl + off - 1;
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        int64_t p = base + k;
+        if (p < n) {
+          if (head & (1u << k)) {
+            ++r;
+            unsigned long long m = gp->bits[0] >= 64 ? ~0ull : ((1ull << gp->bits[0]) - 1);
+            gkey[r] = (long long)(((unsigned long long)key[k] & m) + (unsigned long long)gp->kmin[0]);
+          }
+          rank_of_row[rows[p]] = (int32_t)r;
+        }
+      }
+      if (tile == num_tiles - 1 && threadIdx.x == 0) *d_G = excl + total;
+    }
+    __syncthreads();
+  }
+}
+
+// ---- gather ranks and aggregated dimension columns into key order; check
+// that keys are unique among the passing rows.
+struct PregatherArgs {
+  const void* skeys;
+  int key_dt;
+  const int32_t* srows;
+  int64_t n_max;
+  const int64_t* d_n;
+  const int32_t* rank_of_row;  // null: no group column
+  int32_t* rank_sorted;
+  int nv;
+  const void* vcol[TQP_MAX_VALS];
+  int vdt[TQP_MAX_VALS];
+  long long* vout[TQP_MAX_VALS];
+  StarPlan* plan;
+};
+
+__global__ void star_pregather_kernel(PregatherArgs a) {
+  const int64_t n = clamp_n(a.n_max, a.d_n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    int32_t row = a.srows[p];
+    a.rank_sorted[p] = a.rank_of_row ? a.rank_of_row[row] : 0;
+    for (int v = 0; v < a.nv; ++v) a.vout[v][p] = load_as_i64(a.vcol[v], a.vdt[v], row);
+    if (p > 0 && load_as_i64(a.skeys, a.key_dt, p) == load_as_i64(a.skeys, a.key_dt, p - 1)) {
+      if (atomicExch(&a.plan->unsupported, 1) == 0) raise_status(TQP_ERR_UNSUPPORTED);
+    }
+  }
+}
+
+__global__ void star_slots_kernel(StarPlan* plan, int ndims, const long long* d_G0, const long long* d_G1,
+                                  long long slots_cap, int nacc) {
+  if (threadIdx.x != 0) return;
+  long long G[kMaxDims] = {d_G0 ? *d_G0 : 1, d_G1 ? *d_G1 : 1};
+  long long S = 1;
+  for (int d = ndims - 1; d >= 0; --d) {
+    plan->G[d] = G[d];
+    plan->stride[d] = S;
+    S *= G[d] > 0 ? G[d] : 1;
+  }
+  plan->S = S;
+  if (S > slots_cap) {
+    plan->unsupported = 1;
+    raise_status(TQP_ERR_UNSUPPORTED);
+  }
+  plan->use_smem = (S * nacc <= kSmemAccWords) ? 1 : 0;
+}
+
+struct StarAcc {
+  int naggs;
+  int op[TQP_MAX_AGGS];  // aggregate ops; accumulator naggs holds the row count
+  int expr[TQP_MAX_AGGS];
+  int nexprs;
+  int nterms[TQP_MAX_EXPRS];
+  int tval[TQP_MAX_EXPRS][3];
+  long long tmul[TQP_MAX_EXPRS][3];
+  long long tadd[TQP_MAX_EXPRS][3];
+};
+
+__device__ __forceinline__ long long acc_identity(const StarAcc& A, int q) {
+  return q < A.naggs ? agg_identity(A.op[q]) : 0;
+}
+
+__global__ void star_init_acc_kernel(const StarPlan* plan, const StarAcc A, long long* acc) {
+  const long long S = plan->S;
+  const int nacc = A.naggs + 1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if (plan->unsupported) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < S * nacc; i += stride)
+    acc[i] = acc_identity(A, (int)(i % nacc));
+}
+
+struct ProbeDim {
+  const void* skeys;   // sorted passing keys (int32 or int64)
+  int key_dt;
+  int64_t n_max;
+  const int64_t* d_n;
+  const int32_t* rank_sorted;
+  const void* fk;      // fact foreign-key column (same dtype as the key)
+};
+
+struct ProbeArgs {
+  int ndims;
+  ProbeDim dim[kMaxDims];
+  int npred;
+  const void* pcol[TQP_MAX_PREDS];
+  int pdt[TQP_MAX_PREDS];
+  int pop[TQP_MAX_PREDS];
+  long long plit[TQP_MAX_PREDS];
+  int nvals;
+  int vsrc[TQP_MAX_VALS];     // 0 = fact column, 1 + d = pre-gathered dimension column
+  const void* vptr[TQP_MAX_VALS];
+  int vdt[TQP_MAX_VALS];
+  int64_t n_fact;
+  const StarPlan* plan;
+  long long* acc;
+  uint32_t* tile_counter;
+  uint32_t num_tiles;
+};
+
+__device__ __forceinline__ void fold_slot(long long* acc, const StarAcc& A, const long long* ev, bool shared) {
+#pragma unroll
+  for (int q = 0; q < TQP_MAX_AGGS; ++q) {
+    if (q < A.naggs) {
+      long long x = (A.op[q] == TQP_COUNT) ? 1 : ev[A.expr[q]];
+      unsigned long long* p = reinterpret_cast<unsigned long long*>(acc + q);
+      switch (A.op[q]) {
+        case TQP_MIN: atomicMin(reinterpret_cast<long long*>(p), x); break;
+        case TQP_MAX: atomicMax(reinterpret_cast<long long*>(p), x); break;
+        default: atomicAdd(p, (unsigned long long)x); break;
+      }
+    }
+  }
+  atomicAdd(reinterpret_cast<unsigned long long*>(acc + A.naggs), 1ull);
+  (void)shared;
+}
+
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAcc A) {
+  constexpr int TILE = THREADS * ITEMS;
+  __shared__ long long s_acc[kSmemAccWords];
+  __shared__ uint32_t s_tile;
+  const StarPlan* plan = a.plan;
+  if (plan->unsupported) return;
+  const bool use_smem = plan->use_smem != 0;
+  const long long S = plan->S;
+  const int nacc = A.naggs + 1;
+  if (use_smem) {
+    for (int i = threadIdx.x; i < S * nacc; i += THREADS) s_acc[i] = acc_identity(A, i % nacc);
+  }
+  long long nd[kMaxDims];
+  long long stride[kMaxDims];
+#pragma unroll
+  for (int d = 0; d < kMaxDims; ++d) {
+    nd[d] = d < a.ndims ? clamp_n(a.dim[d].n_max, a.dim[d].d_n) : 0;
+    stride[d] = d < a.ndims ? plan->stride[d] : 0;
+  }
+  __syncthreads();
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    __syncthreads();
+    if (tile >= a.num_tiles) break;
+    const int64_t base = (int64_t)tile * TILE;
+#pragma unroll 1
+    for (int k = 0; k < ITEMS; ++k) {
+      const int64_t row = base + (int64_t)k * THREADS + threadIdx.x;
+      if (row >= a.n_fact) continue;
+      bool keep = true;
+      for (int p = 0; p < a.npred; ++p)
+        keep = keep && compare(load_as_i64(a.pcol[p], a.pdt[p], row), a.pop[p], a.plit[p]);
+      if (!keep) continue;
+      long long slot = 0;
+      int64_t pos[kMaxDims];
+#pragma unroll
+      for (int d = 0; d < kMaxDims; ++d) {
+        if (d < a.ndims && keep) {
+          int64_t l;
+          bool hit;
+          if (a.dim[d].key_dt == TQP_I32) {
+            const int32_t* sk = static_cast<const int32_t*>(a.dim[d].skeys);
+            int32_t x = static_cast<const int32_t*>(a.dim[d].fk)[row];
+            l = lower_bound_dev(sk, nd[d], x);
+            hit = l < nd[d] && sk[l] == x;
+          } else {
+            const long long* sk = static_cast<const long long*>(a.dim[d].skeys);
+            long long x = static_cast<const long long*>(a.dim[d].fk)[row];
+            l = lower_bound_dev(sk, nd[d], x);
+            hit = l < nd[d] && sk[l] == x;
+          }
+          keep = hit;
+          pos[d] = l;
+          if (hit) slot += (long long)a.dim[d].rank_sorted[l] * stride[d];
+        }
+      }
+      if (!keep) continue;
+      long long vals[TQP_MAX_VALS];
+#pragma unroll
+      for (int v = 0; v < TQP_MAX_VALS; ++v) {
+        if (v < a.nvals) {
+          int src = a.vsrc[v];
+          vals[v] = src == 0 ? load_as_i64(a.vptr[v], a.vdt[v], row)
+                             : static_cast<const long long*>(a.vptr[v])[pos[src - 1]];
+        }
+      }
+      long long ev[TQP_MAX_EXPRS];
+#pragma unroll
+      for (int e = 0; e < TQP_MAX_EXPRS; ++e) {
+        if (e < A.nexprs) {
+          unsigned long long x = 1;
+          for (int t = 0; t < A.nterms[e]; ++t)
+            x *= (unsigned long long)A.tmul[e][t] * (unsigned long long)vals[A.tval[e][t]] +
+                 (unsigned long long)A.tadd[e][t];
+          ev[e] = (long long)x;
+        }
+      }
+      fold_slot(use_smem ? s_acc + slot * nacc : a.acc + slot * nacc, A, ev, use_smem);
+    }
+  }
+  if (use_smem) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < S * nacc; i += THREADS) {
+      int q = i % nacc;
+      long long v = s_acc[i];
+      if (v == acc_identity(A, q)) continue;
+      if (q < A.naggs && A.op[q] == TQP_MIN) atomicMin(&a.acc[i], v);
+      else if (q < A.naggs && A.op[q] == TQP_MAX) atomicMax(&a.acc[i], v);
+      else atomicAdd(reinterpret_cast<unsigned long long*>(&a.acc[i]), (unsigned long long)v);
+    }
+  }
+}
+
+// ---- compaction of non-empty slots into the output (single-pass scan)
+struct CompactArgs {
+  const StarPlan* plan;
+  const long long* acc;
+  int naggs;
+  int ndims;
+  const long long* gkey[kMaxDims];  // per dimension group key values by rank (null: no group column)
+  int out_key_index[kMaxDims];      // which output key column (or -1)
+  void* out_keys[kMaxDims];
+  int out_dt[kMaxDims];
+  long long* out_aggs;
+  int64_t cap;
+  int64_t* d_out_groups;
+  unsigned long long* status;
+  uint32_t* counter;
+  uint32_t num_tiles;
+};
+
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) star_compact_kernel(CompactArgs a) {
+  constexpr int TILE = THREADS * ITEMS;
+  __shared__ int s_scan[33];
+  __shared__ uint32_t s_tile;
+  __shared__ long long s_excl;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long S = a.plan->unsupported ? 0 : a.plan->S;
+  const int nacc = a.naggs + 1;
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= a.num_tiles) break;
+    const int64_t base = (int64_t)tile * TILE + (int64_t)threadIdx.x * ITEMS;
+    uint32_t live = 0;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k)
+      if (base + k < S && a.acc[(base + k) * nacc + a.naggs] > 0) live |= 1u << k;
+    int total;
+    int off = block_exclusive_sum<THREADS>(__popc(live), s_scan, &total);
+    if (warp == 0) {
+      long long e = lookback_exclusive(a.status, tile, total);
+      if (lane == 0) s_excl = e;
+    }
+    __syncthreads();
+    long long excl = s_excl;
+    if (excl >= 0) {
+      long long g = excl + off;
+      for (int k = 0; k < ITEMS; ++k) {
+        if (!(live & (1u << k))) continue;
+        long long slot = base + k;
+        if (g < a.cap) {
+          for (int q = 0; q < a.naggs; ++q) a.out_aggs[g * a.naggs + q] = a.acc[slot * nacc + q];
+          for (int d = 0; d < a.ndims; ++d) {
+            if (a.out_key_index[d] < 0) continue;
+            long long r = (slot / a.plan->stride[d]) % a.plan->G[d];
+            store_from_i64(a.out_keys[a.out_key_index[d]], a.out_dt[d], g, a.gkey[d][r]);
+          }
+        }
+        ++g;
+      }
+      if (tile == a.num_tiles - 1 && threadIdx.x == 0) {
+        *a.d_out_groups = excl + total;
+        if (excl + total > a.cap) raise_status(TQP_ERR_CAPACITY);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace tqp

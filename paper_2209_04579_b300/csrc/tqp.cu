@@ -1,0 +1,874 @@
+// C-ABI entry points of the TQP CUDA library (declared in include/tqp.h):
+// argument checks on the host, workspace carving, and kernel launches on the
+// caller's stream.  One translation unit holds every kernel so that the
+// per-device status word is a single object.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <unordered_map>
+
+#include "common.cuh"
+#include "filter.cuh"
+#include "groupby.cuh"
+#include "join.cuh"
+#include "sort.cuh"
+#include "star.cuh"
+
+namespace tqp {
+namespace {
+
+// ---------------------------------------------------------------- host helpers
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* ws) : base(static_cast<char*>(ws)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+int num_sms() {
+  static std::mutex mu;
+  static std::unordered_map<int, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 148;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  cache[dev] = n;
+  return n;
+}
+
+// Persistent grid: enough resident blocks to fill every SM, never more than the tiles.
+template <typename Kernel>
+int persistent_grid(Kernel k, int threads, size_t smem, int64_t tiles) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  int per_sm = 1;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(reinterpret_cast<const void*>(k));
+    if (it != cache.end()) {
+      per_sm = it->second;
+    } else {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+      if (per_sm < 1) per_sm = 1;
+      cache[reinterpret_cast<const void*>(k)] = per_sm;
+    }
+  }
+  int64_t g = (int64_t)per_sm * num_sms();
+  if (tiles < g) g = tiles;
+  return (int)(g < 1 ? 1 : g);
+}
+
+int stride_grid(int64_t n, int threads, int per_sm = 8) {
+  int64_t g = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)num_sms() * per_sm;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// ---------------------------------------------------------------- launch accounting
+std::atomic<long long> g_launches{0};
+cudaEvent_t g_prof_start[8] = {};
+cudaEvent_t g_prof_stop[8] = {};
+
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Records the profiling event of kernel class `kid` (if one is set) on stream s.
+// External records so that they also become event nodes under stream capture.
+inline void prof_mark(int kid, bool start, cudaStream_t s) {
+  cudaEvent_t e = start ? g_prof_start[kid] : g_prof_stop[kid];
+  if (e) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+}
+
+bool valid_dtype(int dt) { return dt >= TQP_I8 && dt <= TQP_I64; }
+
+tqp_status last_launch() { return cudaGetLastError() == cudaSuccess ? TQP_OK : TQP_ERR_CUDA; }
+
+#define TQP_CUDA(call)                               \
+  do {                                               \
+    if ((call) != cudaSuccess) return TQP_ERR_CUDA;  \
+  } while (0)
+
+// ---------------------------------------------------------------- sort
+constexpr int kSortThreads = 256;
+constexpr int kItems32 = 16;
+constexpr int kItems64 = 12;
+
+struct SortWs {
+  uint32_t* ctrl;  // hist [P*256] + counters [P]
+  SortPlan* plan;
+  uint32_t* status;
+  void* alt_keys[2];
+  int32_t* alt_vals[2];
+  size_t ctrl_words;
+  uint32_t tiles;
+};
+
+int64_t sort_tile(int word_bytes) { return (int64_t)kSortThreads * (word_bytes == 4 ? kItems32 : kItems64); }
+
+SortWs carve_sort(Carver& c, int64_t n, int word_bytes, int npasses) {
+  SortWs w;
+  w.ctrl_words = (size_t)npasses * kRadix + npasses;
+  w.ctrl = c.take<uint32_t>(w.ctrl_words);
+  w.plan = c.take<SortPlan>(1);
+  int64_t t = (n + sort_tile(word_bytes) - 1) / sort_tile(word_bytes);
+  w.tiles = (uint32_t)t;
+  w.status = c.take<uint32_t>((size_t)(t > 0 ? t : 1) * kRadix);
+  for (int i = 0; i < 2; ++i) {
+    w.alt_keys[i] = c.take<char>((size_t)(n > 0 ? n : 1) * word_bytes);
+    w.alt_vals[i] = c.take<int32_t>((size_t)(n > 0 ? n : 1));
+  }
+  return w;
+}
+
+// Enqueues the full sort.  key_dt may be a tqp_dtype or kKeyU32 / kKeyU64.
+tqp_status run_sort(const SortWs& w, int key_dt, const void* keys_in, const int32_t* vals_in, void* keys_out,
+                    int32_t* vals_out, int64_t n, const int64_t* d_n, int begin_bit, int end_bit,
+                    cudaStream_t s) {
+  if (n == 0) return TQP_OK;
+  const int word_bytes = key_bits(key_dt) <= 32 ? 4 : 8;
+  SortArgs a;
+  a.keys_in = keys_in;
+  a.vals_in = vals_in;
+  a.keys_out = keys_out;
+  a.vals_out = vals_out;
+  a.alt_keys[0] = w.alt_keys[0];
+  a.alt_keys[1] = w.alt_keys[1];
+  a.alt_vals[0] = w.alt_vals[0];
+  a.alt_vals[1] = w.alt_vals[1];
+  a.key_dt = key_dt;
+  a.begin_bit = begin_bit;
+  a.nbits = end_bit - begin_bit;
+  a.npasses = (a.nbits + kRadixBits - 1) / kRadixBits;
+  a.n_max = n;
+  a.d_n = d_n;
+  a.hist = w.ctrl;
+  a.tile_counters = w.ctrl + (size_t)a.npasses * kRadix;
+  a.plan = w.plan;
+  a.status = w.status;
+  TQP_CUDA(cudaMemsetAsync(w.ctrl, 0, w.ctrl_words * sizeof(uint32_t), s));
+  sort_hist_kernel<256><<<stride_grid(n, 256), 256, 0, s>>>(a); note_launch();
+  sort_plan_kernel<<<1, kRadix, 0, s>>>(a); note_launch();
+  prof_mark(2, true, s);
+  for (int p = 0; p < a.npasses; ++p) {
+    TQP_CUDA(cudaMemsetAsync(w.status, 0, (size_t)w.tiles * kRadix * sizeof(uint32_t), s));
+    if (word_bytes == 4) {
+      auto k = sort_pass_kernel<uint32_t, kSortThreads, kItems32>;
+      size_t smem = (size_t)kSortThreads * kItems32 * 4;
+      k<<<persistent_grid(k, kSortThreads, smem, w.tiles), kSortThreads, smem, s>>>(a, p, w.tiles); note_launch();
+    } else {
+      auto k = sort_pass_kernel<unsigned long long, kSortThreads, kItems64>;
+      size_t smem = (size_t)kSortThreads * kItems64 * 8;
+      k<<<persistent_grid(k, kSortThreads, smem, w.tiles), kSortThreads, smem, s>>>(a, p, w.tiles); note_launch();
+    }
+  }
+  prof_mark(2, false, s);
+  return last_launch();
+}
+
+// ---------------------------------------------------------------- group-by (device part)
+constexpr int kReduceThreads = 256;
+constexpr int kReduceItems = 8;
+
+struct GroupWs {
+  GroupPlan* plan;
+  void* packed;
+  int32_t* rows;
+  void* sorted;
+  int32_t* sorted_rows;
+  SortWs sort;
+  uint32_t* ctrl;  // reduce counter + flags
+  Partial* agg_payload;
+  Partial* pre_payload;
+  uint32_t tiles;
+};
+
+GroupWs carve_group(Carver& c, int64_t n, int word_bytes) {
+  GroupWs w;
+  w.plan = c.take<GroupPlan>(1);
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  w.packed = c.take<char>(nn * word_bytes);
+  w.rows = c.take<int32_t>(nn);
+  w.sorted = c.take<char>(nn * word_bytes);
+  w.sorted_rows = c.take<int32_t>(nn);
+  w.sort = carve_sort(c, n, word_bytes, word_bytes == 4 ? 4 : 8);
+  int64_t t = (n + kReduceThreads * kReduceItems - 1) / (kReduceThreads * kReduceItems);
+  w.tiles = (uint32_t)t;
+  w.ctrl = c.take<uint32_t>(1 + (size_t)(t > 0 ? t : 1));
+  w.agg_payload = c.take<Partial>((size_t)(t > 0 ? t : 1));
+  w.pre_payload = c.take<Partial>((size_t)(t > 0 ? t : 1));
+  return w;
+}
+
+tqp_status build_agg_program(const tqp_col* vals, int nvals, const tqp_expr* exprs, int nexprs,
+                             const tqp_agg* aggs, int naggs, AggProgram* P) {
+  if (nvals < 0 || nvals > TQP_MAX_VALS || nexprs < 0 || nexprs > TQP_MAX_EXPRS || naggs < 1 ||
+      naggs > TQP_MAX_AGGS)
+    return TQP_ERR_INVALID;
+  if ((nvals && !vals) || (nexprs && !exprs) || !aggs) return TQP_ERR_INVALID;
+  std::memset(P, 0, sizeof(*P));
+  P->nvals = nvals;
+  for (int v = 0; v < nvals; ++v) {
+    if (!valid_dtype(vals[v].dtype)) return TQP_ERR_DTYPE;
+    if (!vals[v].data) return TQP_ERR_INVALID;
+    P->val[v] = vals[v].data;
+    P->vdt[v] = vals[v].dtype;
+  }
+  P->nexprs = nexprs;
+  for (int e = 0; e < nexprs; ++e) {
+    if (exprs[e].nterms < 1 || exprs[e].nterms > 3) return TQP_ERR_INVALID;
+    P->nterms[e] = exprs[e].nterms;
+    for (int t = 0; t < exprs[e].nterms; ++t) {
+      if (exprs[e].term[t].col < 0 || exprs[e].term[t].col >= nvals) return TQP_ERR_INVALID;
+      P->tcol[e][t] = exprs[e].term[t].col;
+      P->tmul[e][t] = exprs[e].term[t].mul;
+      P->tadd[e][t] = exprs[e].term[t].add;
+    }
+  }
+  P->naggs = naggs;
+  for (int a = 0; a < naggs; ++a) {
+    if (aggs[a].op < TQP_COUNT || aggs[a].op > TQP_MAX) return TQP_ERR_INVALID;
+    if (aggs[a].op != TQP_COUNT && (aggs[a].expr < 0 || aggs[a].expr >= nexprs)) return TQP_ERR_INVALID;
+    P->op[a] = aggs[a].op;
+    P->expr[a] = aggs[a].op == TQP_COUNT ? -1 : aggs[a].expr;
+  }
+  return TQP_OK;
+}
+
+tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, const int32_t* sel, int64_t n,
+                       const int64_t* d_n, int word_bytes, long long* out_aggs, int64_t cap,
+                       int64_t* d_out_groups, cudaStream_t s) {
+  if (n == 0) {
+    TQP_CUDA(cudaMemsetAsync(d_out_groups, 0, sizeof(int64_t), s));
+    return TQP_OK;
+  }
+  gb_init_kernel<<<1, 32, 0, s>>>(w.plan); note_launch();
+  gb_keyrange_kernel<256><<<stride_grid(n, 256, 4), 256, 0, s>>>(ks, sel, n, d_n, w.plan); note_launch();
+  gb_plan_kernel<<<1, 32, 0, s>>>(w.plan, ks.nkeys, word_bytes * 8); note_launch();
+  if (word_bytes == 4) {
+    gb_encode_kernel<uint32_t><<<stride_grid(n, 256), 256, 0, s>>>(ks, sel, n, d_n, w.plan,
+                                                                     static_cast<uint32_t*>(w.packed), w.rows); note_launch();
+  } else {
+    gb_encode_kernel<unsigned long long><<<stride_grid(n, 256), 256, 0, s>>>(
+        ks, sel, n, d_n, w.plan, static_cast<unsigned long long*>(w.packed), w.rows); note_launch();
+  }
+  tqp_status st = run_sort(w.sort, word_bytes == 4 ? kKeyU32 : kKeyU64, w.packed, w.rows, w.sorted,
+                           w.sorted_rows, n, d_n, 0, word_bytes * 8, s);
+  if (st != TQP_OK) return st;
+  TQP_CUDA(cudaMemsetAsync(w.ctrl, 0, (1 + (size_t)w.tiles) * sizeof(uint32_t), s));
+  ReduceArgs r;
+  r.keys = w.sorted;
+  r.rows = w.sorted_rows;
+  r.n_max = n;
+  r.d_n = d_n;
+  r.plan = w.plan;
+  r.ks = ks;
+  r.out_aggs = out_aggs;
+  r.cap = cap;
+  r.d_out_groups = d_out_groups;
+  r.tile_counter = w.ctrl;
+  r.flags = w.ctrl + 1;
+  r.agg_payload = w.agg_payload;
+  r.pre_payload = w.pre_payload;
+  r.num_tiles = w.tiles;
+  if (word_bytes == 4) {
+    auto k = gb_reduce_kernel<uint32_t, kReduceThreads, kReduceItems>;
+    prof_mark(4, true, s);
+    k<<<persistent_grid(k, kReduceThreads, 0, w.tiles), kReduceThreads, 0, s>>>(r, P); note_launch();
+    prof_mark(4, false, s);
+  } else {
+    auto k = gb_reduce_kernel<unsigned long long, kReduceThreads, kReduceItems>;
+    prof_mark(4, true, s);
+    k<<<persistent_grid(k, kReduceThreads, 0, w.tiles), kReduceThreads, 0, s>>>(r, P); note_launch();
+    prof_mark(4, false, s);
+  }
+  return last_launch();
+}
+
+
+// ---------------------------------------------------------------- star aggregate
+struct StarDimWs {
+  unsigned long long* fstatus;
+  uint32_t* fcounter;
+  int32_t* sel;
+  int64_t* cnt;
+  void* gkeys;
+  void* skeys;
+  int32_t* srows;
+  SortWs ksort;
+  // group ranks
+  GroupPlan* gplan;
+  void* packed;
+  int32_t* prow;
+  void* spacked;
+  int32_t* sprow;
+  SortWs gsort;
+  unsigned long long* rstatus;
+  uint32_t* rcounter;
+  int32_t* rank_of_row;
+  long long* gkey;
+  long long* G;
+  int32_t* rank_sorted;
+  long long* dval[TQP_MAX_VALS];
+  uint32_t ftiles, rtiles;
+  int gword;
+};
+
+constexpr int kFilterT = 256, kFilterI = 16;
+constexpr int kRankT = 256, kRankI = 8;
+constexpr int kProbeT = 256, kProbeI = 8;
+constexpr int kCompactT = 256, kCompactI = 8;
+
+}  // namespace
+}  // namespace tqp
+
+using namespace tqp;
+
+// ============================================================================
+extern "C" {
+
+const char* tqp_status_string(tqp_status s) {
+  switch (s) {
+    case TQP_OK: return "ok";
+    case TQP_ERR_INVALID: return "invalid argument";
+    case TQP_ERR_DTYPE: return "unsupported or mismatched dtype";
+    case TQP_ERR_CAPACITY: return "result exceeds capacity";
+    case TQP_ERR_CUDA: return "CUDA error";
+    case TQP_ERR_TIMEOUT: return "bounded wait ran out";
+    case TQP_ERR_WORKSPACE: return "workspace too small";
+    case TQP_ERR_UNSUPPORTED: return "unsupported input";
+  }
+  return "unknown status";
+}
+
+tqp_status tqp_status_poll(tqp_stream_t stream) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int v = 0;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TQP_ERR_CUDA;
+  if (cudaMemcpyFromSymbol(&v, g_status, sizeof(int)) != cudaSuccess) return TQP_ERR_CUDA;
+  int zero = 0;
+  if (cudaMemcpyToSymbol(g_status, &zero, sizeof(int)) != cudaSuccess) return TQP_ERR_CUDA;
+  return static_cast<tqp_status>(v);
+}
+
+int64_t tqp_debug_launch_count(void) { return g_launches.load(); }
+
+tqp_status tqp_profile_events(int kernel_class, void* start_event, void* stop_event) {
+  if (kernel_class < 1 || kernel_class > 7) return TQP_ERR_INVALID;
+  g_prof_start[kernel_class] = static_cast<cudaEvent_t>(start_event);
+  g_prof_stop[kernel_class] = static_cast<cudaEvent_t>(stop_event);
+  return TQP_OK;
+}
+
+tqp_status tqp_debug_set_spin_limit(int64_t rounds) {
+  if (rounds < 1) return TQP_ERR_INVALID;
+  long long v = rounds;
+  return cudaMemcpyToSymbol(g_spin_limit, &v, sizeof(v)) == cudaSuccess ? TQP_OK : TQP_ERR_CUDA;
+}
+
+tqp_status tqp_debug_inject_unpublished_tile(int64_t tile) {
+  long long v = tile;
+  return cudaMemcpyToSymbol(g_unpublished_tile, &v, sizeof(v)) == cudaSuccess ? TQP_OK : TQP_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+tqp_status tqp_filter(const tqp_col* cols, int ncols, const tqp_pred* preds, int npred, int64_t n,
+                      const int64_t* d_n, int32_t* d_out_idx, int64_t cap, int64_t* d_out_n, void* ws,
+                      size_t* ws_bytes, tqp_stream_t stream) {
+  constexpr int T = 256, I = 16;
+  if (!ws_bytes || n < 0 || n > INT_MAX || npred < 0 || npred > TQP_MAX_PREDS || ncols < 0) return TQP_ERR_INVALID;
+  if (npred && (!preds || !cols)) return TQP_ERR_INVALID;
+  const int64_t tiles = (n + T * I - 1) / (T * I);
+  Carver c(ws);
+  unsigned long long* status = c.take<unsigned long long>((size_t)(tiles > 0 ? tiles : 1));
+  uint32_t* counter = c.take<uint32_t>(1);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (!d_out_n || (cap > 0 && !d_out_idx) || cap < 0) return TQP_ERR_INVALID;
+  FilterArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.npred = npred;
+  for (int p = 0; p < npred; ++p) {
+    int col = preds[p].col;
+    if (col < 0 || col >= ncols || !cols[col].data) return TQP_ERR_INVALID;
+    if (!valid_dtype(cols[col].dtype)) return TQP_ERR_DTYPE;
+    if (preds[p].op < TQP_LT || preds[p].op > TQP_NE) return TQP_ERR_INVALID;
+    a.col[p] = cols[col].data;
+    a.dt[p] = cols[col].dtype;
+    a.op[p] = preds[p].op;
+    a.lit[p] = preds[p].lit;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    TQP_CUDA(cudaMemsetAsync(d_out_n, 0, sizeof(int64_t), s));
+    return TQP_OK;
+  }
+  a.n_max = n;
+  a.d_n = d_n;
+  a.out = d_out_idx;
+  a.cap = cap;
+  a.d_out_n = d_out_n;
+  a.status = status;
+  a.tile_counter = counter;
+  a.num_tiles = (uint32_t)tiles;
+  TQP_CUDA(cudaMemsetAsync(ws, 0, c.off, s));
+  auto k = filter_kernel<T, I>;
+  prof_mark(3, true, s);
+  k<<<persistent_grid(k, T, 0, tiles), T, 0, s>>>(a); note_launch();
+  prof_mark(3, false, s);
+  return last_launch();
+}
+
+tqp_status tqp_gather(tqp_col col, const int32_t* d_idx, int64_t n, const int64_t* d_n, void* d_out,
+                      tqp_stream_t stream) {
+  if (n < 0 || n > INT_MAX) return TQP_ERR_INVALID;
+  if (!valid_dtype(col.dtype)) return TQP_ERR_DTYPE;
+  if (n == 0) return TQP_OK;
+  if (!col.data || !d_idx || !d_out) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int g = stride_grid(n, 256);
+  switch (col.dtype) {
+    case TQP_I8: gather_kernel<int8_t><<<g, 256, 0, s>>>((const int8_t*)col.data, d_idx, n, d_n, (int8_t*)d_out); note_launch(); break;
+    case TQP_I16: gather_kernel<int16_t><<<g, 256, 0, s>>>((const int16_t*)col.data, d_idx, n, d_n, (int16_t*)d_out); note_launch(); break;
+    case TQP_I32: gather_kernel<int32_t><<<g, 256, 0, s>>>((const int32_t*)col.data, d_idx, n, d_n, (int32_t*)d_out); note_launch(); break;
+    default: gather_kernel<long long><<<g, 256, 0, s>>>((const long long*)col.data, d_idx, n, d_n, (long long*)d_out); note_launch(); break;
+  }
+  return last_launch();
+}
+
+tqp_status tqp_sort_pairs(int32_t key_dtype, const void* d_keys_in, const int32_t* d_vals_in, void* d_keys_out,
+                          int32_t* d_vals_out, int64_t n, const int64_t* d_n, int begin_bit, int end_bit,
+                          void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || n < 0 || n >= (1ll << 30)) return TQP_ERR_INVALID;
+  if (!valid_dtype(key_dtype)) return TQP_ERR_DTYPE;
+  const int w = key_bits(key_dtype);
+  if (begin_bit < 0 || end_bit > w || begin_bit >= end_bit) return TQP_ERR_INVALID;
+  const int word_bytes = w <= 32 ? 4 : 8;
+  const int npasses = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
+  Carver c(ws);
+  SortWs sw = carve_sort(c, n, word_bytes, npasses);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (n > 0 && (!d_keys_in || !d_keys_out || !d_vals_out)) return TQP_ERR_INVALID;
+  return run_sort(sw, key_dtype, d_keys_in, d_vals_in, d_keys_out, d_vals_out, n, d_n, begin_bit, end_bit,
+                  reinterpret_cast<cudaStream_t>(stream));
+}
+
+tqp_status tqp_join_eq(tqp_col probe, int64_t n_probe, const int64_t* d_n_probe, tqp_col build, int64_t n_build,
+                       const int64_t* d_n_build, int32_t* d_out_probe, int32_t* d_out_build, int64_t cap,
+                       int64_t* d_out_n, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  constexpr int T = 256, I = 4;
+  if (!ws_bytes || n_probe < 0 || n_probe > INT_MAX || n_build < 0 || n_build >= (1ll << 30)) return TQP_ERR_INVALID;
+  if (!valid_dtype(probe.dtype) || probe.dtype != build.dtype) return TQP_ERR_DTYPE;
+  const int eb = dtype_bytes(build.dtype);
+  const int word_bytes = eb <= 4 ? 4 : 8;
+  const int64_t tiles = (n_probe + T * I - 1) / (T * I);
+  Carver c(ws);
+  void* skeys = c.take<char>((size_t)(n_build > 0 ? n_build : 1) * eb);
+  int32_t* srows = c.take<int32_t>((size_t)(n_build > 0 ? n_build : 1));
+  SortWs sw = carve_sort(c, n_build, word_bytes, eb);  // eb bytes = eb digits of 8 bits
+  unsigned long long* status = c.take<unsigned long long>((size_t)(tiles > 0 ? tiles : 1));
+  uint32_t* counter = c.take<uint32_t>(1);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (!d_out_n || cap < 0 || (cap > 0 && (!d_out_probe || !d_out_build))) return TQP_ERR_INVALID;
+  if ((n_probe > 0 && !probe.data) || (n_build > 0 && !build.data)) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n_probe == 0) {
+    TQP_CUDA(cudaMemsetAsync(d_out_n, 0, sizeof(int64_t), s));
+    return TQP_OK;
+  }
+  tqp_status st = run_sort(sw, build.dtype, build.data, nullptr, skeys, srows, n_build, d_n_build, 0, eb * 8, s);
+  if (st != TQP_OK) return st;
+  TQP_CUDA(cudaMemsetAsync(status, 0, (size_t)tiles * 8, s));
+  TQP_CUDA(cudaMemsetAsync(counter, 0, 4, s));
+#define TQP_JOIN_LAUNCH(TYPE)                                                                      \
+  {                                                                                                \
+    JoinArgs<TYPE> a;                                                                              \
+    a.probe = static_cast<const TYPE*>(probe.data);                                                \
+    a.np_max = n_probe;                                                                            \
+    a.d_np = d_n_probe;                                                                            \
+    a.sorted_keys = static_cast<const TYPE*>(skeys);                                               \
+    a.sorted_rows = srows;                                                                         \
+    a.nb_max = n_build;                                                                            \
+    a.d_nb = d_n_build;                                                                            \
+    a.out_probe = d_out_probe;                                                                     \
+    a.out_build = d_out_build;                                                                     \
+    a.cap = cap;                                                                                   \
+    a.d_out_n = d_out_n;                                                                           \
+    a.status = status;                                                                             \
+    a.tile_counter = counter;                                                                      \
+    a.num_tiles = (uint32_t)tiles;                                                                 \
+    auto k = join_probe_kernel<TYPE, T, I>;                                                        \
+    prof_mark(5, true, s); k<<<persistent_grid(k, T, 0, tiles), T, 0, s>>>(a); note_launch(); prof_mark(5, false, s); \
+  }
+  switch (build.dtype) {
+    case TQP_I8: TQP_JOIN_LAUNCH(int8_t); break;
+    case TQP_I16: TQP_JOIN_LAUNCH(int16_t); break;
+    case TQP_I32: TQP_JOIN_LAUNCH(int32_t); break;
+    default: TQP_JOIN_LAUNCH(long long); break;
+  }
+#undef TQP_JOIN_LAUNCH
+  return last_launch();
+}
+
+tqp_status tqp_groupby_agg(const tqp_col* keys, int nkeys, const tqp_col* vals, int nvals, const tqp_expr* exprs,
+                           int nexprs, const tqp_agg* aggs, int naggs, const int32_t* d_sel, int64_t n,
+                           const int64_t* d_n, void* const* d_out_keys, int64_t* d_out_aggs, int64_t cap,
+                           int64_t* d_out_groups, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || n < 0 || n >= (1ll << 30) || nkeys < 1 || nkeys > TQP_MAX_KEYS || !keys) return TQP_ERR_INVALID;
+  int declared_bits = 0;
+  for (int k = 0; k < nkeys; ++k) {
+    if (!valid_dtype(keys[k].dtype)) return TQP_ERR_DTYPE;
+    declared_bits += dtype_bytes(keys[k].dtype) * 8;
+  }
+  AggProgram P;
+  tqp_status st = build_agg_program(vals, nvals, exprs, nexprs, aggs, naggs, &P);
+  if (st != TQP_OK) return st;
+  const int word_bytes = declared_bits <= 32 ? 4 : 8;
+  Carver c(ws);
+  GroupWs gw = carve_group(c, n, word_bytes);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (!d_out_groups || cap < 0 || (cap > 0 && (!d_out_aggs || !d_out_keys))) return TQP_ERR_INVALID;
+  KeySet ks;
+  std::memset(&ks, 0, sizeof(ks));
+  ks.nkeys = nkeys;
+  for (int k = 0; k < nkeys; ++k) {
+    if (n > 0 && !keys[k].data) return TQP_ERR_INVALID;
+    if (cap > 0 && !d_out_keys[k]) return TQP_ERR_INVALID;
+    ks.col[k] = keys[k].data;
+    ks.dt[k] = keys[k].dtype;
+    ks.out[k] = cap > 0 ? d_out_keys[k] : nullptr;
+  }
+  return run_groupby(gw, ks, P, d_sel, n, d_n, word_bytes, reinterpret_cast<long long*>(d_out_aggs), cap,
+                     d_out_groups, reinterpret_cast<cudaStream_t>(stream));
+}
+
+tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact, const tqp_pred* fact_preds,
+                        int nfact_preds, const int* fk_col, const tqp_dim* dims, int ndims, const tqp_valref* vals,
+                        int nvals, const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
+                        void* const* d_out_keys, int64_t* d_out_aggs, int64_t cap, int64_t* d_out_groups, void* ws,
+                        size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || n_fact < 0 || n_fact > INT_MAX || ndims < 1 || ndims > kMaxDims || !dims || !fk_col ||
+      !fact_cols || nfact_cols < 1)
+    return TQP_ERR_INVALID;
+  if (nfact_preds < 0 || nfact_preds > TQP_MAX_PREDS || (nfact_preds && !fact_preds)) return TQP_ERR_INVALID;
+  if (nvals < 0 || nvals > TQP_MAX_VALS || (nvals && !vals)) return TQP_ERR_INVALID;
+  if (nexprs < 0 || nexprs > TQP_MAX_EXPRS || (nexprs && !exprs) || naggs < 1 || naggs > TQP_MAX_AGGS - 1 || !aggs)
+    return TQP_ERR_INVALID;
+  // ---- host-side validation and slot bound
+  long long slots_cap = 1;
+  int nout_keys = 0;
+  for (int d = 0; d < ndims; ++d) {
+    const tqp_dim& D = dims[d];
+    if (D.n < 0 || D.n >= (1ll << 30)) return TQP_ERR_INVALID;
+    if (D.key.dtype != TQP_I32 && D.key.dtype != TQP_I64) return TQP_ERR_DTYPE;
+    if (fk_col[d] < 0 || fk_col[d] >= nfact_cols) return TQP_ERR_INVALID;
+    if (fact_cols[fk_col[d]].dtype != D.key.dtype) return TQP_ERR_DTYPE;
+    if (D.npred < 0 || D.npred > TQP_MAX_PREDS || (D.npred && (!D.preds || !D.cols))) return TQP_ERR_INVALID;
+    for (int p = 0; p < D.npred; ++p) {
+      if (D.preds[p].col < 0 || D.preds[p].col >= D.ncols) return TQP_ERR_INVALID;
+      if (!valid_dtype(D.cols[D.preds[p].col].dtype)) return TQP_ERR_DTYPE;
+      if (D.preds[p].op < TQP_LT || D.preds[p].op > TQP_NE) return TQP_ERR_INVALID;
+    }
+    if (D.group.data) {
+      if (!valid_dtype(D.group.dtype)) return TQP_ERR_DTYPE;
+      long long dom = dtype_bytes(D.group.dtype) >= 4 ? (1ll << 40) : (1ll << (8 * dtype_bytes(D.group.dtype)));
+      long long g = D.n < dom ? D.n : dom;
+      if (g < 1) g = 1;
+      slots_cap *= g;
+      if (slots_cap > (1ll << 26)) return TQP_ERR_UNSUPPORTED;
+      ++nout_keys;
+    }
+  }
+  for (int p = 0; p < nfact_preds; ++p) {
+    if (fact_preds[p].col < 0 || fact_preds[p].col >= nfact_cols) return TQP_ERR_INVALID;
+    if (!valid_dtype(fact_cols[fact_preds[p].col].dtype)) return TQP_ERR_DTYPE;
+    if (fact_preds[p].op < TQP_LT || fact_preds[p].op > TQP_NE) return TQP_ERR_INVALID;
+  }
+  for (int v = 0; v < nvals; ++v) {
+    int src = vals[v].src;
+    if (src < 0 || src > ndims) return TQP_ERR_INVALID;
+    const tqp_col* cols = src == 0 ? fact_cols : dims[src - 1].cols;
+    int nc = src == 0 ? nfact_cols : dims[src - 1].ncols;
+    if (vals[v].col < 0 || vals[v].col >= nc || !cols) return TQP_ERR_INVALID;
+    if (!valid_dtype(cols[vals[v].col].dtype)) return TQP_ERR_DTYPE;
+  }
+  StarAcc A;
+  std::memset(&A, 0, sizeof(A));
+  A.naggs = naggs;
+  A.nexprs = nexprs;
+  for (int e = 0; e < nexprs; ++e) {
+    if (exprs[e].nterms < 1 || exprs[e].nterms > 3) return TQP_ERR_INVALID;
+    A.nterms[e] = exprs[e].nterms;
+    for (int t = 0; t < exprs[e].nterms; ++t) {
+      if (exprs[e].term[t].col < 0 || exprs[e].term[t].col >= nvals) return TQP_ERR_INVALID;
+      A.tval[e][t] = exprs[e].term[t].col;
+      A.tmul[e][t] = exprs[e].term[t].mul;
+      A.tadd[e][t] = exprs[e].term[t].add;
+    }
+  }
+  for (int q = 0; q < naggs; ++q) {
+    if (aggs[q].op < TQP_COUNT || aggs[q].op > TQP_MAX) return TQP_ERR_INVALID;
+    if (aggs[q].op != TQP_COUNT && (aggs[q].expr < 0 || aggs[q].expr >= nexprs)) return TQP_ERR_INVALID;
+    A.op[q] = aggs[q].op;
+    A.expr[q] = aggs[q].op == TQP_COUNT ? 0 : aggs[q].expr;
+  }
+  // ---- workspace
+  Carver c(ws);
+  StarDimWs W[kMaxDims];
+  for (int d = 0; d < ndims; ++d) {
+    const tqp_dim& D = dims[d];
+    StarDimWs& w = W[d];
+    std::memset(&w, 0, sizeof(w));
+    const size_t nn = (size_t)(D.n > 0 ? D.n : 1);
+    const int eb = dtype_bytes(D.key.dtype);
+    w.ftiles = (uint32_t)((D.n + kFilterT * kFilterI - 1) / (kFilterT * kFilterI));
+    if (D.npred) {
+      w.fstatus = c.take<unsigned long long>(w.ftiles ? w.ftiles : 1);
+      w.fcounter = c.take<uint32_t>(1);
+      w.sel = c.take<int32_t>(nn);
+      w.cnt = c.take<int64_t>(1);
+      w.gkeys = c.take<char>(nn * eb);
+    }
+    w.skeys = c.take<char>(nn * eb);
+    w.srows = c.take<int32_t>(nn);
+    w.ksort = carve_sort(c, D.n, eb, eb);
+    if (D.group.data) {
+      w.gword = dtype_bytes(D.group.dtype) <= 4 ? 4 : 8;
+      w.gplan = c.take<GroupPlan>(1);
+      w.packed = c.take<char>(nn * w.gword);
+      w.prow = c.take<int32_t>(nn);
+      w.spacked = c.take<char>(nn * w.gword);
+      w.sprow = c.take<int32_t>(nn);
+      w.gsort = carve_sort(c, D.n, w.gword, w.gword);
+      w.rtiles = (uint32_t)((D.n + kRankT * kRankI - 1) / (kRankT * kRankI));
+      w.rstatus = c.take<unsigned long long>(w.rtiles ? w.rtiles : 1);
+      w.rcounter = c.take<uint32_t>(1);
+      w.rank_of_row = c.take<int32_t>(nn);
+      w.gkey = c.take<long long>(nn);
+      w.G = c.take<long long>(1);
+    }
+    w.rank_sorted = c.take<int32_t>(nn);
+    for (int v = 0; v < nvals; ++v)
+      if (vals[v].src == d + 1) w.dval[v] = c.take<long long>(nn);
+  }
+  StarPlan* plan = c.take<StarPlan>(1);
+  const int nacc = naggs + 1;
+  long long* acc = c.take<long long>((size_t)slots_cap * nacc);
+  uint32_t* pcounter = c.take<uint32_t>(1);
+  const int64_t ptiles = (n_fact + kProbeT * kProbeI - 1) / (kProbeT * kProbeI);
+  const int64_t ctiles = (slots_cap + kCompactT * kCompactI - 1) / (kCompactT * kCompactI);
+  unsigned long long* cstatus = c.take<unsigned long long>((size_t)ctiles);
+  uint32_t* ccounter = c.take<uint32_t>(1);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (!d_out_groups || cap < 0 || (cap > 0 && (!d_out_aggs || (nout_keys && !d_out_keys)))) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  TQP_CUDA(cudaMemsetAsync(plan, 0, sizeof(StarPlan), s));
+  // ---- dimensions
+  for (int d = 0; d < ndims; ++d) {
+    const tqp_dim& D = dims[d];
+    StarDimWs& w = W[d];
+    const int eb = dtype_bytes(D.key.dtype);
+    const int64_t* dcnt = nullptr;
+    const void* kin = D.key.data;
+    const int32_t* vin = nullptr;
+    if (D.npred && D.n > 0) {
+      FilterArgs f;
+      std::memset(&f, 0, sizeof(f));
+      f.npred = D.npred;
+      for (int p = 0; p < D.npred; ++p) {
+        f.col[p] = D.cols[D.preds[p].col].data;
+        f.dt[p] = D.cols[D.preds[p].col].dtype;
+        f.op[p] = D.preds[p].op;
+        f.lit[p] = D.preds[p].lit;
+      }
+      f.n_max = D.n;
+      f.d_n = nullptr;
+      f.out = w.sel;
+      f.cap = D.n;
+      f.d_out_n = w.cnt;
+      f.status = w.fstatus;
+      f.tile_counter = w.fcounter;
+      f.num_tiles = w.ftiles;
+      TQP_CUDA(cudaMemsetAsync(w.fstatus, 0, (size_t)w.ftiles * 8, s));
+      TQP_CUDA(cudaMemsetAsync(w.fcounter, 0, 4, s));
+      auto fk = filter_kernel<kFilterT, kFilterI>;
+      fk<<<persistent_grid(fk, kFilterT, 0, w.ftiles), kFilterT, 0, s>>>(f); note_launch();
+      int g = stride_grid(D.n, 256);
+      if (eb == 4) {
+        gather_kernel<int32_t><<<g, 256, 0, s>>>((const int32_t*)D.key.data, w.sel, D.n, w.cnt, (int32_t*)w.gkeys); note_launch();
+      } else {
+        gather_kernel<long long><<<g, 256, 0, s>>>((const long long*)D.key.data, w.sel, D.n, w.cnt,
+                                                   (long long*)w.gkeys); note_launch();
+      }
+      dcnt = w.cnt;
+      kin = w.gkeys;
+      vin = w.sel;
+    } else if (D.npred) {
+      TQP_CUDA(cudaMemsetAsync(w.cnt, 0, 8, s));
+      dcnt = w.cnt;
+    }
+    tqp_status st = run_sort(w.ksort, D.key.dtype, kin, vin, w.skeys, w.srows, D.n, dcnt, 0, eb * 8, s);
+    if (st != TQP_OK) return st;
+    if (D.group.data && D.n > 0) {
+      KeySet ks;
+      std::memset(&ks, 0, sizeof(ks));
+      ks.nkeys = 1;
+      ks.col[0] = D.group.data;
+      ks.dt[0] = D.group.dtype;
+      gb_init_kernel<<<1, 32, 0, s>>>(w.gplan); note_launch();
+      gb_keyrange_kernel<256><<<stride_grid(D.n, 256, 4), 256, 0, s>>>(ks, w.sel, D.n, dcnt, w.gplan); note_launch();
+      gb_plan_kernel<<<1, 32, 0, s>>>(w.gplan, 1, w.gword * 8); note_launch();
+      int g = stride_grid(D.n, 256);
+      if (w.gword == 4) {
+        gb_encode_kernel<uint32_t><<<g, 256, 0, s>>>(ks, w.sel, D.n, dcnt, w.gplan, (uint32_t*)w.packed, w.prow); note_launch();
+      } else {
+        gb_encode_kernel<unsigned long long><<<g, 256, 0, s>>>(ks, w.sel, D.n, dcnt, w.gplan,
+                                                               (unsigned long long*)w.packed, w.prow); note_launch();
+      }
+      st = run_sort(w.gsort, w.gword == 4 ? kKeyU32 : kKeyU64, w.packed, w.prow, w.spacked, w.sprow, D.n, dcnt, 0,
+                    w.gword * 8, s);
+      if (st != TQP_OK) return st;
+      TQP_CUDA(cudaMemsetAsync(w.rstatus, 0, (size_t)w.rtiles * 8, s));
+      TQP_CUDA(cudaMemsetAsync(w.rcounter, 0, 4, s));
+      if (w.gword == 4) {
+        auto rk = rank_kernel<uint32_t, kRankT, kRankI>;
+        rk<<<persistent_grid(rk, kRankT, 0, w.rtiles), kRankT, 0, s>>>(
+            (const uint32_t*)w.spacked, w.sprow, D.n, dcnt, w.gplan, w.rank_of_row, w.gkey, w.G, w.rstatus,
+            w.rcounter, w.rtiles); note_launch();
+      } else {
+        auto rk = rank_kernel<unsigned long long, kRankT, kRankI>;
+        rk<<<persistent_grid(rk, kRankT, 0, w.rtiles), kRankT, 0, s>>>(
+            (const unsigned long long*)w.spacked, w.sprow, D.n, dcnt, w.gplan, w.rank_of_row, w.gkey, w.G,
+            w.rstatus, w.rcounter, w.rtiles); note_launch();
+      }
+    } else if (D.group.data) {
+      TQP_CUDA(cudaMemsetAsync(w.G, 0, 8, s));
+    }
+    if (D.n > 0) {
+      PregatherArgs pg;
+      std::memset(&pg, 0, sizeof(pg));
+      pg.skeys = w.skeys;
+      pg.key_dt = D.key.dtype;
+      pg.srows = w.srows;
+      pg.n_max = D.n;
+      pg.d_n = dcnt;
+      pg.rank_of_row = D.group.data ? w.rank_of_row : nullptr;
+      pg.rank_sorted = w.rank_sorted;
+      pg.plan = plan;
+      for (int v = 0; v < nvals; ++v) {
+        if (vals[v].src != d + 1) continue;
+        pg.vcol[pg.nv] = D.cols[vals[v].col].data;
+        pg.vdt[pg.nv] = D.cols[vals[v].col].dtype;
+        pg.vout[pg.nv] = w.dval[v];
+        ++pg.nv;
+      }
+      star_pregather_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(pg); note_launch();
+    }
+  }
+  // ---- slots, accumulators, probe, compaction
+  star_slots_kernel<<<1, 32, 0, s>>>(plan, ndims, dims[0].group.data ? W[0].G : nullptr,
+                                     (ndims > 1 && dims[1].group.data) ? W[1].G : nullptr, slots_cap, nacc); note_launch();
+  star_init_acc_kernel<<<stride_grid(slots_cap * nacc, 256, 4), 256, 0, s>>>(plan, A, acc); note_launch();
+  ProbeArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.ndims = ndims;
+  for (int d = 0; d < ndims; ++d) {
+    pa.dim[d].skeys = W[d].skeys;
+    pa.dim[d].key_dt = dims[d].key.dtype;
+    pa.dim[d].n_max = dims[d].n;
+    pa.dim[d].d_n = dims[d].npred ? W[d].cnt : nullptr;
+    pa.dim[d].rank_sorted = W[d].rank_sorted;
+    pa.dim[d].fk = fact_cols[fk_col[d]].data;
+  }
+  pa.npred = nfact_preds;
+  for (int p = 0; p < nfact_preds; ++p) {
+    pa.pcol[p] = fact_cols[fact_preds[p].col].data;
+    pa.pdt[p] = fact_cols[fact_preds[p].col].dtype;
+    pa.pop[p] = fact_preds[p].op;
+    pa.plit[p] = fact_preds[p].lit;
+  }
+  pa.nvals = nvals;
+  for (int v = 0; v < nvals; ++v) {
+    pa.vsrc[v] = vals[v].src;
+    if (vals[v].src == 0) {
+      pa.vptr[v] = fact_cols[vals[v].col].data;
+      pa.vdt[v] = fact_cols[vals[v].col].dtype;
+    } else {
+      pa.vptr[v] = W[vals[v].src - 1].dval[v];
+      pa.vdt[v] = TQP_I64;
+    }
+  }
+  pa.n_fact = n_fact;
+  pa.plan = plan;
+  pa.acc = acc;
+  pa.tile_counter = pcounter;
+  pa.num_tiles = (uint32_t)ptiles;
+  TQP_CUDA(cudaMemsetAsync(pcounter, 0, 4, s));
+  if (ptiles > 0) {
+    auto pk = star_probe_kernel<kProbeT, kProbeI>;
+    prof_mark(1, true, s);
+    pk<<<persistent_grid(pk, kProbeT, 0, ptiles), kProbeT, 0, s>>>(pa, A); note_launch();
+    prof_mark(1, false, s);
+  }
+  CompactArgs ca;
+  std::memset(&ca, 0, sizeof(ca));
+  ca.plan = plan;
+  ca.acc = acc;
+  ca.naggs = naggs;
+  ca.ndims = ndims;
+  int ok = 0;
+  for (int d = 0; d < ndims; ++d) {
+    if (dims[d].group.data) {
+      ca.gkey[d] = W[d].gkey;
+      ca.out_key_index[d] = ok;
+      ca.out_keys[d] = cap > 0 ? d_out_keys[ok] : nullptr;
+      ca.out_dt[d] = dims[d].group.dtype;
+      ++ok;
+    } else {
+      ca.out_key_index[d] = -1;
+    }
+  }
+  ca.out_aggs = reinterpret_cast<long long*>(d_out_aggs);
+  ca.cap = cap;
+  ca.d_out_groups = d_out_groups;
+  ca.status = cstatus;
+  ca.counter = ccounter;
+  ca.num_tiles = (uint32_t)ctiles;
+  TQP_CUDA(cudaMemsetAsync(cstatus, 0, (size_t)ctiles * 8, s));
+  TQP_CUDA(cudaMemsetAsync(ccounter, 0, 4, s));
+  auto ck = star_compact_kernel<kCompactT, kCompactI>;
+  ck<<<persistent_grid(ck, kCompactT, 0, ctiles), kCompactT, 0, s>>>(ca); note_launch();
+  return last_launch();
+}
+
+}  // extern "C"

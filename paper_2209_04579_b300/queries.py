@@ -1,0 +1,80 @@
+"""The synthetic workloads' queries, composed from the C-ABI operators.
+
+Each function states its SQL.  Results are returned on the device; counts
+are device tensors (no host synchronisation inside), so a whole query can be
+captured in a CUDA graph.  The query shapes follow the paper's Section 2.3:
+a filter plus an aggregation (Q6) and a join plus an aggregation (Q14).
+"""
+from __future__ import annotations
+
+from . import tqp
+
+Q6_DAY_MAX = 2400
+Q14_REGION_LT = 5
+BATCH_DAY_LT = 1278
+STAR_DATE_LT = 767
+
+Q6_EXPRS = [
+    [(0, 1, 0)],                              # qty
+    [(1, 1, 0)],                              # price
+    [(1, 1, 0), (2, -1, 100)],                # price * (100 - disc)
+    [(1, 1, 0), (2, -1, 100), (3, 1, 100)],   # price * (100 - disc) * (100 + tax)
+]
+Q6_AGGS = [(tqp.SUM, 0), (tqp.SUM, 1), (tqp.SUM, 2), (tqp.SUM, 3), (tqp.COUNT, 0)]
+
+
+def q6(t, cap: int = 64):
+    """SELECT flag_a, flag_b, SUM(qty), SUM(price), SUM(price*(100-disc)),
+    SUM(price*(100-disc)*(100+tax)), COUNT(*) FROM lineitem
+    WHERE ship_day <= 2400 GROUP BY flag_a, flag_b."""
+    sel, cnt = tqp.tqp_filter([t["ship_day"]], [(0, tqp.LE, Q6_DAY_MAX)])
+    return tqp.tqp_groupby_agg([t["flag_a"], t["flag_b"]], [t["qty"], t["price"], t["disc"], t["tax"]],
+                               Q6_EXPRS, Q6_AGGS, cap, sel=sel, n=t["ship_day"].numel(), d_n=cnt)
+
+
+def q14(fact, dim, cap: int = 64):
+    """SELECT region, SUM(price), COUNT(*) FROM fact JOIN dim ON fk = key
+    WHERE region < 5 GROUP BY region -- fused star aggregate."""
+    D = tqp.DimSpec(dim["key"], cols=[dim["region"], dim["price"]], preds=[(0, tqp.LT, Q14_REGION_LT)],
+                    group=dim["region"])
+    return tqp.tqp_star_agg([fact["fk"]], [], [0], [D], [(1, 1)], [[(0, 1, 0)]],
+                            [(tqp.SUM, 0), (tqp.COUNT, 0)], cap)
+
+
+def q14_unfused(fact, dim, cap: int = 64, pair_cap: int | None = None):
+    """The same query as a chain of separate operators: join (bound search +
+    expand into pairs), gathers, filter on the joined rows, group-by."""
+    n = fact["fk"].numel()
+    pair_cap = n if pair_cap is None else pair_cap
+    pr, br, npairs = tqp.tqp_join_eq(fact["fk"], dim["key"], pair_cap)
+    region = tqp.tqp_gather(dim["region"], br, n=pair_cap, d_n=npairs)
+    price = tqp.tqp_gather(dim["price"], br, n=pair_cap, d_n=npairs)
+    keep, nkeep = tqp.tqp_filter([region], [(0, tqp.LT, Q14_REGION_LT)], n=pair_cap, d_n=npairs)
+    return tqp.tqp_groupby_agg([region], [price], [[(0, 1, 0)]], [(tqp.SUM, 0), (tqp.COUNT, 0)], cap,
+                               sel=keep, n=pair_cap, d_n=nkeep)
+
+
+def skew(t, cap: int):
+    """SELECT key, COUNT(*), SUM(value), MIN(value), MAX(value) FROM t GROUP BY key."""
+    return tqp.tqp_groupby_agg([t["key"]], [t["value"]], [[(0, 1, 0)]],
+                               [(tqp.COUNT, 0), (tqp.SUM, 0), (tqp.MIN, 0), (tqp.MAX, 0)], cap)
+
+
+def batched_one(fact, dim, cap: int = 64):
+    """SELECT grp, SUM(v), COUNT(*) FROM fact JOIN dim ON fk = key
+    WHERE day < 1278 GROUP BY grp."""
+    D = tqp.DimSpec(dim["key"], cols=[dim["grp"]], group=dim["grp"])
+    return tqp.tqp_star_agg([fact["fk"], fact["day"], fact["v"]], [(1, tqp.LT, BATCH_DAY_LT)], [0], [D],
+                            [(0, 2)], [[(0, 1, 0)]], [(tqp.SUM, 0), (tqp.COUNT, 0)], cap)
+
+
+def star(fact, dim1, dim2, cap: int = 50_000):
+    """SELECT dim1.cat, dim2.cat, SUM(m1), SUM(m2), SUM(m3), COUNT(*)
+    FROM fact JOIN dim1 ON fk1 = dim1.key JOIN dim2 ON fk2 = dim2.key
+    WHERE date < 767 GROUP BY dim1.cat, dim2.cat."""
+    D1 = tqp.DimSpec(dim1["key"], cols=[dim1["cat"]], group=dim1["cat"])
+    D2 = tqp.DimSpec(dim2["key"], cols=[dim2["cat"]], group=dim2["cat"])
+    cols = [fact["fk1"], fact["fk2"], fact["m1"], fact["m2"], fact["m3"], fact["date"]]
+    return tqp.tqp_star_agg(cols, [(5, tqp.LT, STAR_DATE_LT)], [0, 1], [D1, D2], [(0, 2), (0, 3), (0, 4)],
+                            [[(0, 1, 0)], [(1, 1, 0)], [(2, 1, 0)]],
+                            [(tqp.SUM, 0), (tqp.SUM, 1), (tqp.SUM, 2), (tqp.COUNT, 0)], cap)

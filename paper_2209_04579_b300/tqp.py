@@ -1,0 +1,312 @@
+"""Python binding of the TQP C ABI (``include/tqp.h``).
+
+Argument marshalling only: torch tensors provide device memory and the
+current CUDA stream; every step of every operator runs in the library's CUDA
+kernels.  Importing this module loads ``libtqp.so`` and raises if it is
+missing -- there is no fallback implementation.
+
+Each function has the name of the C entry point it calls.  Device counts
+(result sizes) are returned as 1-element int64 CUDA tensors so that calls can
+be chained without a host synchronisation; ``.item()`` reads them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libtqp.so")
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libtqp.so not built ({_LIB_PATH}); run python -m paper_2209_04579_b300.build")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+# ------------------------------------------------------------------ constants
+OK, ERR_INVALID, ERR_DTYPE, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE, ERR_UNSUPPORTED = range(8)
+I8, I16, I32, I64 = 1, 2, 3, 4
+LT, LE, GT, GE, EQ, NE = range(6)
+COUNT, SUM, MIN, MAX = range(4)
+
+_DTYPE = {torch.int8: I8, torch.int16: I16, torch.int32: I32, torch.int64: I64}
+_TORCH = {v: k for k, v in _DTYPE.items()}
+
+
+class Col(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+class Pred(ctypes.Structure):
+    _fields_ = [("col", ctypes.c_int32), ("op", ctypes.c_int32), ("lit", ctypes.c_int64)]
+
+
+class Term(ctypes.Structure):
+    _fields_ = [("col", ctypes.c_int32), ("pad_", ctypes.c_int32), ("mul", ctypes.c_int64),
+                ("add", ctypes.c_int64)]
+
+
+class Expr(ctypes.Structure):
+    _fields_ = [("nterms", ctypes.c_int32), ("pad_", ctypes.c_int32), ("term", Term * 3)]
+
+
+class Agg(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("expr", ctypes.c_int32)]
+
+
+class Dim(ctypes.Structure):
+    _fields_ = [("key", Col), ("n", ctypes.c_int64), ("group", Col), ("preds", ctypes.POINTER(Pred)),
+                ("npred", ctypes.c_int), ("ncols", ctypes.c_int), ("cols", ctypes.POINTER(Col))]
+
+
+class ValRef(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_int32), ("col", ctypes.c_int32)]
+
+
+_vp, _i64, _sz, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t, ctypes.c_int
+_P = ctypes.POINTER
+
+_lib.tqp_filter.argtypes = [_P(Col), _int, _P(Pred), _int, _i64, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
+_lib.tqp_gather.argtypes = [Col, _vp, _i64, _vp, _vp, _vp]
+_lib.tqp_sort_pairs.argtypes = [ctypes.c_int32, _vp, _vp, _vp, _vp, _i64, _vp, _int, _int, _vp, _P(_sz), _vp]
+_lib.tqp_join_eq.argtypes = [Col, _i64, _vp, Col, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
+_lib.tqp_groupby_agg.argtypes = [_P(Col), _int, _P(Col), _int, _P(Expr), _int, _P(Agg), _int, _vp, _i64, _vp,
+                                 _P(_vp), _vp, _i64, _vp, _vp, _P(_sz), _vp]
+_lib.tqp_star_agg.argtypes = [_P(Col), _int, _i64, _P(Pred), _int, _P(_int), _P(Dim), _int, _P(ValRef), _int,
+                              _P(Expr), _int, _P(Agg), _int, _P(_vp), _vp, _i64, _vp, _vp, _P(_sz), _vp]
+_lib.tqp_status_poll.argtypes = [_vp]
+_lib.tqp_debug_set_spin_limit.argtypes = [_i64]
+_lib.tqp_debug_inject_unpublished_tile.argtypes = [_i64]
+_lib.tqp_status_string.restype = ctypes.c_char_p
+_lib.tqp_debug_launch_count.restype = ctypes.c_int64
+_lib.tqp_debug_launch_count.argtypes = []
+_lib.tqp_profile_events.argtypes = [_int, _vp, _vp]
+for _f in ("tqp_filter", "tqp_gather", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
+           "tqp_status_poll", "tqp_profile_events", "tqp_debug_set_spin_limit", "tqp_debug_inject_unpublished_tile"):
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+class TQPError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {_lib.tqp_status_string(status).decode()} (status {status})")
+        self.status = status
+
+
+def _check(st: int, where: str):
+    if st != OK:
+        raise TQPError(st, where)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _col(t):
+    if t.dtype not in _DTYPE:
+        raise TypeError(f"unsupported column dtype {t.dtype}")
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("columns must be contiguous CUDA tensors")
+    return Col(t.data_ptr(), _DTYPE[t.dtype], 0)
+
+
+def _cols(ts):
+    arr = (Col * max(1, len(ts)))()
+    for i, t in enumerate(ts):
+        arr[i] = _col(t)
+    return arr
+
+
+def _preds(preds):
+    arr = (Pred * max(1, len(preds)))()
+    for i, (c, op, lit) in enumerate(preds):
+        arr[i] = Pred(c, op, lit)
+    return arr
+
+
+def _exprs(exprs):
+    arr = (Expr * max(1, len(exprs)))()
+    for i, e in enumerate(exprs):
+        arr[i].nterms = len(e)
+        for t, (c, m, a) in enumerate(e):
+            arr[i].term[t] = Term(c, 0, m, a)
+    return arr
+
+
+def _aggs(aggs):
+    arr = (Agg * max(1, len(aggs)))()
+    for i, (op, e) in enumerate(aggs):
+        arr[i] = Agg(op, e)
+    return arr
+
+
+class Workspace:
+    """Grow-only device scratch buffer for one (device, stream) pair."""
+
+    def __init__(self):
+        self.buf = None
+
+    def get(self, nbytes: int, device) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes or self.buf.device != device:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+        return self.buf
+
+
+_WS: dict = {}
+
+
+def _workspace(nbytes: int, device, stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    key = (str(device), s.cuda_stream)
+    ws = _WS.setdefault(key, Workspace())
+    return ws.get(nbytes, device)
+
+
+def _two_phase(fn, name, args_before_ws, device, stream):
+    need = ctypes.c_size_t(0)
+    _check(fn(*args_before_ws, None, ctypes.byref(need), _stream(stream)), name + " (size query)")
+    ws = _workspace(need.value, device, stream)
+    have = ctypes.c_size_t(ws.numel())
+    _check(fn(*args_before_ws, _ptr(ws), ctypes.byref(have), _stream(stream)), name)
+
+
+# ------------------------------------------------------------------ operators
+
+def tqp_filter(cols, preds, n=None, d_n=None, out=None, cap=None, stream=None):
+    """Ascending int32 row ids where every predicate (col, op, literal) holds,
+    and their count as a device int64[1]."""
+    dev = cols[0].device
+    n = cols[0].numel() if n is None else n
+    cap = n if cap is None else cap
+    out = torch.empty(max(cap, 1), dtype=torch.int32, device=dev) if out is None else out
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    c, p = _cols(cols), _preds(preds)
+    _two_phase(_lib.tqp_filter, "tqp_filter",
+               [c, len(cols), p, len(preds), n, _ptr(d_n), _ptr(out), cap, _ptr(cnt)], dev, stream)
+    return out, cnt
+
+
+def tqp_gather(col, idx, n=None, d_n=None, out=None, stream=None):
+    n = idx.numel() if n is None else n
+    out = torch.empty(max(n, 1), dtype=col.dtype, device=col.device) if out is None else out
+    _check(_lib.tqp_gather(_col(col), _ptr(idx), n, _ptr(d_n), _ptr(out), _stream(stream)), "tqp_gather")
+    return out
+
+
+def tqp_sort_pairs(keys, vals=None, begin_bit=0, end_bit=None, n=None, d_n=None, stream=None):
+    """Stable sort of (key, value); value None -> payload = input row index."""
+    dev = keys.device
+    n = keys.numel() if n is None else n
+    end_bit = keys.element_size() * 8 if end_bit is None else end_bit
+    ko = torch.empty(max(n, 1), dtype=keys.dtype, device=dev)
+    vo = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    _two_phase(_lib.tqp_sort_pairs, "tqp_sort_pairs",
+               [_DTYPE[keys.dtype], _ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), n, _ptr(d_n), begin_bit, end_bit],
+               dev, stream)
+    return ko[:n], vo[:n]
+
+
+def tqp_join_eq(probe, build, cap, n_probe=None, d_n_probe=None, n_build=None, d_n_build=None, stream=None):
+    """Pairs (probe_row, build_row) with equal keys, by (probe_row, build_row);
+    returns (out_probe, out_build, device count)."""
+    dev = probe.device
+    n_probe = probe.numel() if n_probe is None else n_probe
+    n_build = build.numel() if n_build is None else n_build
+    op = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    ob = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    _two_phase(_lib.tqp_join_eq, "tqp_join_eq",
+               [_col(probe), n_probe, _ptr(d_n_probe), _col(build), n_build, _ptr(d_n_build), _ptr(op), _ptr(ob),
+                cap, _ptr(cnt)], dev, stream)
+    return op, ob, cnt
+
+
+def tqp_groupby_agg(keys, vals, exprs, aggs, cap, sel=None, n=None, d_n=None, stream=None):
+    """Group-by aggregate.  exprs: lists of (val_col, mul, add) terms;
+    aggs: (op, expr).  Returns (key columns, aggs int64 [cap, naggs], device G)."""
+    dev = keys[0].device
+    if n is None:
+        n = sel.numel() if sel is not None else keys[0].numel()
+    out_keys = [torch.empty(max(cap, 1), dtype=k.dtype, device=dev) for k in keys]
+    out_aggs = torch.empty((max(cap, 1), len(aggs)), dtype=torch.int64, device=dev)
+    G = torch.empty(1, dtype=torch.int64, device=dev)
+    kp = (ctypes.c_void_p * len(keys))(*[k.data_ptr() for k in out_keys])
+    _two_phase(_lib.tqp_groupby_agg, "tqp_groupby_agg",
+               [_cols(keys), len(keys), _cols(vals), len(vals), _exprs(exprs), len(exprs), _aggs(aggs), len(aggs),
+                _ptr(sel), n, _ptr(d_n), kp, _ptr(out_aggs), cap, _ptr(G)], dev, stream)
+    return out_keys, out_aggs, G
+
+
+class DimSpec:
+    """One dimension of tqp_star_agg: key column, optional group column,
+    predicates over `cols`, and the columns values may reference."""
+
+    def __init__(self, key, cols=(), preds=(), group=None):
+        self.key, self.cols, self.preds, self.group = key, list(cols), list(preds), group
+
+
+def tqp_star_agg(fact_cols, fact_preds, fk_cols, dims, vals, exprs, aggs, cap, stream=None):
+    """Fused star join + filter + group-by.  vals: (src, col) with src 0 =
+    fact column, 1 + d = column of dimension d.  Returns (key columns, aggs,
+    device G)."""
+    dev = fact_cols[0].device
+    keep = []
+    darr = (Dim * len(dims))()
+    nkeys = 0
+    for d, D in enumerate(dims):
+        cols = _cols(D.cols)
+        preds = _preds(D.preds)
+        keep += [cols, preds]
+        darr[d].key = _col(D.key)
+        darr[d].n = D.key.numel()
+        darr[d].group = _col(D.group) if D.group is not None else Col(None, 0, 0)
+        darr[d].preds = ctypes.cast(preds, _P(Pred))
+        darr[d].npred = len(D.preds)
+        darr[d].ncols = len(D.cols)
+        darr[d].cols = ctypes.cast(cols, _P(Col))
+        nkeys += D.group is not None
+    out_keys = [torch.empty(max(cap, 1), dtype=D.group.dtype, device=dev) for D in dims if D.group is not None]
+    out_aggs = torch.empty((max(cap, 1), len(aggs)), dtype=torch.int64, device=dev)
+    G = torch.empty(1, dtype=torch.int64, device=dev)
+    kp = (ctypes.c_void_p * max(1, nkeys))(*[k.data_ptr() for k in out_keys])
+    fk = (ctypes.c_int * len(fk_cols))(*fk_cols)
+    vr = (ValRef * max(1, len(vals)))(*[ValRef(s, c) for s, c in vals])
+    _two_phase(_lib.tqp_star_agg, "tqp_star_agg",
+               [_cols(fact_cols), len(fact_cols), fact_cols[0].numel(), _preds(fact_preds), len(fact_preds), fk, darr,
+                len(dims), vr, len(vals), _exprs(exprs), len(exprs), _aggs(aggs), len(aggs), kp, _ptr(out_aggs), cap,
+                _ptr(G)], dev, stream)
+    return out_keys, out_aggs, G
+
+
+def tqp_status_poll(stream=None) -> int:
+    return _lib.tqp_status_poll(_stream(stream))
+
+
+def tqp_debug_set_spin_limit(rounds: int):
+    _check(_lib.tqp_debug_set_spin_limit(rounds), "tqp_debug_set_spin_limit")
+
+
+def tqp_debug_inject_unpublished_tile(tile: int):
+    _check(_lib.tqp_debug_inject_unpublished_tile(tile), "tqp_debug_inject_unpublished_tile")
+
+
+PROF_STAR_PROBE, PROF_SORT_PASSES, PROF_FILTER, PROF_GROUPBY_REDUCE, PROF_JOIN_PROBE = 1, 2, 3, 4, 5
+
+
+def tqp_debug_launch_count() -> int:
+    return int(_lib.tqp_debug_launch_count())
+
+
+def tqp_profile_events(kernel_class: int, start=None, stop=None):
+    """Record torch.cuda.Event `start` / `stop` around kernels of one class."""
+    sp = ctypes.c_void_p(start.cuda_event if start is not None else 0)
+    ep = ctypes.c_void_p(stop.cuda_event if stop is not None else 0)
+    _check(_lib.tqp_profile_events(kernel_class, sp, ep), "tqp_profile_events")
+
+
+def lib_path() -> str:
+    return _LIB_PATH

@@ -1,0 +1,74 @@
+"""The C-ABI libraries load and export every function their headers declare;
+host-side argument checks and workspace size queries work without a GPU
+(no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PKG = os.path.join(ROOT, "paper_2209_04579_b300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2209_04579_b300 import build
+    build.build()
+
+
+def declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(tqp[a-z_0-9]*)\s*\(", text, flags=re.M)))
+
+
+@pytest.mark.parametrize("header,lib", [("tqp.h", "libtqp.so"), ("tqp_datagen.h", "libtqpgen.so")])
+def test_every_declared_symbol_is_exported(header, lib):
+    names = declared(header)
+    assert names, header
+    so = ctypes.CDLL(os.path.join(PKG, lib))
+    for n in names:
+        assert hasattr(so, n), n
+
+
+def test_declared_list_is_complete():
+    names = declared("tqp.h")
+    for must in ("tqp_filter", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
+                 "tqp_gather", "tqp_status_poll"):
+        assert must in names
+
+
+def test_host_argument_checks_and_size_queries():
+    from paper_2209_04579_b300 import tqp
+    lib = tqp._lib
+    sz = ctypes.c_size_t(0)
+    # negative n -> invalid, before any device work
+    st = lib.tqp_filter(None, 0, None, 0, -1, None, None, 0, None, None, ctypes.byref(sz), None)
+    assert st == tqp.ERR_INVALID
+    # size query of a sort: no device work, a positive size
+    st = lib.tqp_sort_pairs(tqp.I32, None, None, None, None, 1000, None, 0, 32, None, ctypes.byref(sz), None)
+    assert st == tqp.OK and sz.value > 1000 * 4
+    # bad bit range and bad dtype
+    assert lib.tqp_sort_pairs(tqp.I32, None, None, None, None, 10, None, 5, 40, None, ctypes.byref(sz), None) \
+        == tqp.ERR_INVALID
+    assert lib.tqp_sort_pairs(9, None, None, None, None, 10, None, 0, 8, None, ctypes.byref(sz), None) \
+        == tqp.ERR_DTYPE
+    # group-by: size query, and too many keys
+    keys = (tqp.Col * 5)(*[tqp.Col(None, tqp.I32, 0) for _ in range(5)])
+    aggs = (tqp.Agg * 1)(tqp.Agg(tqp.COUNT, 0))
+    st = lib.tqp_groupby_agg(keys, 1, None, 0, None, 0, aggs, 1, None, 100, None, None, None, 0, None, None,
+                             ctypes.byref(sz), None)
+    assert st == tqp.OK and sz.value > 0
+    st = lib.tqp_groupby_agg(keys, 5, None, 0, None, 0, aggs, 1, None, 100, None, None, None, 0, None, None,
+                             ctypes.byref(sz), None)
+    assert st == tqp.ERR_INVALID
+    # join with mismatched dtypes
+    st = lib.tqp_join_eq(tqp.Col(None, tqp.I32, 0), 10, None, tqp.Col(None, tqp.I64, 0), 10, None, None, None, 0,
+                         None, None, ctypes.byref(sz), None)
+    assert st == tqp.ERR_DTYPE
+    # workspace too small is reported before launching
+    st = lib.tqp_sort_pairs(tqp.I32, None, None, None, None, 1000, None, 0, 32, ctypes.c_void_p(256),
+                            ctypes.byref(ctypes.c_size_t(16)), None)
+    assert st == tqp.ERR_WORKSPACE
+    assert lib.tqp_status_string(tqp.ERR_TIMEOUT) == b"bounded wait ran out"

@@ -1,0 +1,228 @@
+"""GPU parity of every C-ABI operator against the CPU oracle, element by
+element, on seeded inputs: sizes from empty through several tiles with ragged
+tails, every dtype, degenerate inputs.  All integer results: bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+DT = [np.int8, np.int16, np.int32, np.int64]
+TD = {np.int8: torch.int8, np.int16: torch.int16, np.int32: torch.int32, np.int64: torch.int64}
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2209_04579_b300 import build
+    build.build()
+    from paper_2209_04579_b300 import tqp
+    return tqp
+
+
+def rng(seed):
+    return np.random.default_rng(seed)
+
+
+def col(r, n, dt, lo=None, hi=None):
+    info = np.iinfo(dt)
+    lo = info.min if lo is None else lo
+    hi = info.max if hi is None else hi
+    return r.integers(lo, hi, size=n, endpoint=True, dtype=np.int64).astype(dt)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t, n=None):
+    a = t.cpu().numpy()
+    return a if n is None else a[:n]
+
+
+SIZES = [0, 1, 2, 31, 4095, 4096, 4097, 3 * 4096 + 17, 100_003]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_filter(T, n):
+    r = rng(n + 1)
+    cols = [col(r, n, DT[i % 4], -50, 50) for i in range(4)]
+    for preds in ([], [(0, orc.LT, 10)], [(1, orc.GE, -3), (2, orc.NE, 0)],
+                  [(0, orc.LE, 40), (1, orc.GT, -40), (2, orc.EQ, 7), (3, orc.NE, 1)],
+                  [(3, orc.LT, -1000)], [(2, orc.GE, -1000)]):
+        want = orc.filter(cols, preds)
+        out, cnt = T.tqp_filter([dev(c) for c in cols], preds, n=n)
+        k = int(cnt.item())
+        assert k == len(want)
+        assert np.array_equal(host(out, k), want)
+    assert T.tqp_status_poll() == T.OK
+
+
+def test_filter_large_ragged_and_device_count(T):
+    n = 5_000_011
+    r = rng(5)
+    c = col(r, n, np.int32, 0, 2556)
+    want = orc.filter([c], [(0, orc.LE, 2400)])
+    out, cnt = T.tqp_filter([dev(c)], [(0, T.LE, 2400)])
+    assert int(cnt.item()) == len(want) and np.array_equal(host(out, len(want)), want)
+    # the row count read from the device
+    dn = torch.tensor([1_234_567], dtype=torch.int64, device="cuda")
+    out, cnt = T.tqp_filter([dev(c)], [(0, T.LE, 2400)], d_n=dn)
+    want = orc.filter([c[:1_234_567]], [(0, orc.LE, 2400)])
+    assert int(cnt.item()) == len(want) and np.array_equal(host(out, len(want)), want)
+
+
+def test_filter_capacity_status(T):
+    c = np.arange(10000, dtype=np.int32)
+    out, cnt = T.tqp_filter([dev(c)], [(0, T.LT, 5000)], cap=100)
+    assert int(cnt.item()) == 5000                      # the required size is still reported
+    assert np.array_equal(host(out, 100), np.arange(100))
+    assert T.tqp_status_poll() == T.ERR_CAPACITY
+    assert T.tqp_status_poll() == T.OK                  # polling clears it
+
+
+@pytest.mark.parametrize("dt", DT)
+@pytest.mark.parametrize("n", [0, 1, 2, 3071, 3072, 4097, 5 * 4096 + 3, 200_001])
+def test_sort_pairs(T, dt, n):
+    r = rng(n * 7 + np.dtype(dt).itemsize)
+    keys = col(r, n, dt)
+    vals = r.integers(-2**31, 2**31 - 1, n).astype(np.int32)
+    wk, wv = orc.sort_pairs(keys, vals)
+    ko, vo = T.tqp_sort_pairs(dev(keys), dev(vals))
+    assert np.array_equal(host(ko, n), wk) and np.array_equal(host(vo, n), wv)
+    wk, wv = orc.sort_pairs(keys)                       # payload = row index
+    ko, vo = T.tqp_sort_pairs(dev(keys))
+    assert np.array_equal(host(ko, n), wk) and np.array_equal(host(vo, n), wv)
+
+
+@pytest.mark.parametrize("dt", [np.int32, np.int64])
+def test_sort_degenerate_and_bit_ranges(T, dt):
+    w = np.dtype(dt).itemsize * 8
+    r = rng(3)
+    n = 70_001
+    cases = {
+        "equal": np.full(n, -5, dtype=dt),
+        "sorted": np.sort(col(r, n, dt)),
+        "reversed": np.sort(col(r, n, dt))[::-1].copy(),
+        "few": col(r, n, dt, -2, 2),
+        "extremes": r.choice(np.array([np.iinfo(dt).min, np.iinfo(dt).max, 0, -1], dtype=dt), n),
+    }
+    for name, keys in cases.items():
+        wk, wv = orc.sort_pairs(keys)
+        ko, vo = T.tqp_sort_pairs(dev(keys))
+        assert np.array_equal(host(ko, n), wk), name
+        assert np.array_equal(host(vo, n), wv), name
+    keys = col(r, n, dt)
+    for lo, hi in [(0, 8), (3, 17), (w - 9, w), (5, w - 3)]:
+        wk, wv = orc.sort_pairs(keys, None, lo, hi)
+        ko, vo = T.tqp_sort_pairs(dev(keys), None, lo, hi)
+        assert np.array_equal(host(vo, n), wv), (lo, hi)
+        assert np.array_equal(host(ko, n), wk), (lo, hi)
+
+
+@pytest.mark.parametrize("dt", [np.int8, np.int32, np.int64])
+@pytest.mark.parametrize("np_,nb", [(0, 10), (10, 0), (1, 1), (1000, 37), (50_001, 20_000), (300_007, 4093)])
+def test_join_eq(T, dt, np_, nb):
+    r = rng(np_ + nb)
+    hi = 40 if dt == np.int8 else max(1, nb * 2)
+    probe = col(r, np_, dt, -hi if dt == np.int8 else 0, hi)
+    build = col(r, nb, dt, -hi if dt == np.int8 else 0, hi)
+    wp, wb = orc.join_eq(probe, build)
+    cap = max(1, len(wp))
+    op, ob, cnt = T.tqp_join_eq(dev(probe), dev(build), cap)
+    k = int(cnt.item())
+    assert k == len(wp)
+    assert np.array_equal(host(op, k), wp) and np.array_equal(host(ob, k), wb)
+
+
+def test_join_unique_keys_and_capacity(T):
+    r = rng(9)
+    build = r.permutation(200_000).astype(np.int64) * 3 - 1000
+    probe = r.integers(-2000, 700_000, 400_000).astype(np.int64)
+    wp, wb = orc.join_eq(probe, build)
+    op, ob, cnt = T.tqp_join_eq(dev(probe), dev(build), len(wp))
+    k = int(cnt.item())
+    assert k == len(wp) and np.array_equal(host(op, k), wp) and np.array_equal(host(ob, k), wb)
+    op, ob, cnt = T.tqp_join_eq(dev(probe), dev(build), 10)
+    assert int(cnt.item()) == len(wp)
+    assert np.array_equal(host(op, 10), wp[:10])
+    assert T.tqp_status_poll() == T.ERR_CAPACITY
+
+
+GB_EXPRS = [[(0, 1, 0)], [(1, -1, 100), (2, 3, -7)], [(0, 1, 0), (1, 1, 5), (2, -2, 9)]]
+GB_AGGS = [(orc.COUNT, 0), (orc.SUM, 0), (orc.MIN, 1), (orc.MAX, 1), (orc.SUM, 2), (orc.MIN, 2), (orc.MAX, 0),
+           (orc.SUM, 1)]
+
+
+def check_groupby(T, keys, vals, exprs, aggs, sel=None, n=None):
+    wk, wa, _ = orc.groupby_agg(keys, vals, exprs, aggs, sel=sel, n=n)
+    G = wa.shape[0]
+    cap = max(G, 1)
+    ok, oa, g = T.tqp_groupby_agg([dev(k) for k in keys], [dev(v) for v in vals], exprs, aggs, cap,
+                                  sel=None if sel is None else dev(sel), n=n)
+    assert int(g.item()) == G
+    for i, k in enumerate(keys):
+        assert np.array_equal(host(ok[i], G).astype(np.int64), wk[i])
+    assert np.array_equal(host(oa)[:G], wa)
+    assert T.tqp_status_poll() == T.OK
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 2047, 2048, 2049, 3 * 2048 + 5, 150_001])
+def test_groupby_shapes(T, n):
+    r = rng(n + 11)
+    vals = [col(r, n, np.int64, -10**9, 10**9), col(r, n, np.int32), col(r, n, np.int16)]
+    # one int8 key (32-bit path), two keys, and a 64-bit composite key
+    check_groupby(T, [col(r, n, np.int8, -3, 3)], vals, GB_EXPRS, GB_AGGS)
+    check_groupby(T, [col(r, n, np.int16, -100, 100), col(r, n, np.int8)], vals, GB_EXPRS, GB_AGGS[:5])
+    check_groupby(T, [col(r, n, np.int32, -5000, 5000), col(r, n, np.int64, -2, 2**40)], vals, GB_EXPRS,
+                  GB_AGGS)
+
+
+def test_groupby_degenerate(T):
+    r = rng(2)
+    n = 100_000
+    v = [col(r, n, np.int64)]
+    e = [[(0, 1, 0)]]
+    a = [(orc.COUNT, 0), (orc.SUM, 0), (orc.MIN, 0), (orc.MAX, 0)]
+    check_groupby(T, [np.full(n, 7, np.int32)], v, e, a)                      # one group
+    check_groupby(T, [np.arange(n, dtype=np.int64)[::-1].copy()], v, e, a)     # all distinct
+    ext = r.choice(np.array([np.iinfo(np.int64).min, np.iinfo(np.int64).max, 0], np.int64), n)
+    check_groupby(T, [ext], v, e, a)                                           # full 64-bit range
+    check_groupby(T, [col(r, n, np.int64)], v, e, a)                           # 64 random bits
+    sel = np.sort(r.choice(n, 33_333, replace=False)).astype(np.int32)
+    check_groupby(T, [col(r, n, np.int16, -9, 9)], v, e, a, sel=sel)          # with a selection
+
+
+def test_groupby_too_wide_key_reports_unsupported(T):
+    r = rng(4)
+    n = 1000
+    k = [col(r, n, np.int64), col(r, n, np.int64)]
+    ok, oa, g = T.tqp_groupby_agg([dev(x) for x in k], [dev(k[0])], [[(0, 1, 0)]], [(orc.COUNT, 0)], 2000)
+    assert int(g.item()) == 0
+    assert T.tqp_status_poll() == T.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("dt", DT)
+def test_gather(T, dt):
+    r = rng(1)
+    c = col(r, 10_000, dt)
+    idx = r.integers(0, 10_000, 123_457).astype(np.int32)
+    assert np.array_equal(host(T.tqp_gather(dev(c), dev(idx))), orc.gather(c, idx))
+
+
+def test_bounded_wait_timeout_keeps_context_usable(T):
+    """A scan tile that never publishes: its successors' bounded waits run
+    out, the kernel records TIMEOUT and returns; the context stays usable."""
+    c = np.arange(4096 * 12, dtype=np.int32)
+    T.tqp_debug_set_spin_limit(2000)
+    T.tqp_debug_inject_unpublished_tile(3)
+    try:
+        out, cnt = T.tqp_filter([dev(c)], [(0, T.GE, 0)])
+        assert T.tqp_status_poll() == T.ERR_TIMEOUT
+    finally:
+        T.tqp_debug_inject_unpublished_tile(-1)
+        T.tqp_debug_set_spin_limit(1 << 20)
+    out, cnt = T.tqp_filter([dev(c)], [(0, T.GE, 0)])
+    assert int(cnt.item()) == len(c) and np.array_equal(host(out), c)
+    assert T.tqp_status_poll() == T.OK

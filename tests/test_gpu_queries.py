@@ -1,0 +1,131 @@
+"""GPU parity of the workload queries against the oracle's pipelines, and of
+the device input generator against the host generator.
+
+Inputs: the GPU side generates its tables on the device, the oracle side on
+the host, from the same seeded recipes (the generator test below shows the
+two are identical).  Full-size cases run in the same launch configuration as
+the benchmark."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from oracle import pipelines as pl
+from paper_2209_04579_b300 import datagen as dg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2209_04579_b300 import build
+    build.build()
+    from paper_2209_04579_b300 import datagen_device, queries, tqp
+    return tqp, queries, datagen_device
+
+
+def host(t, n=None):
+    a = t.cpu().numpy()
+    return a if n is None else a[:n]
+
+
+def all_recipes():
+    out = list(dg.q6_lineitem().items())
+    for sparse in (False, True):
+        t = dg.q14_tables(1_500_000, sparse)
+        out += [(f"q14{sparse}.{k}", r) for tab in t.values() for k, r in tab.items()]
+    out += list(dg.skew_groupby().items())
+    ns, ms, gs = dg.batched_sizes()
+    t = dg.batched_problem(7, int(ns[7]), int(ms[7]), int(gs[7]))
+    out += [(f"b.{k}", r) for tab in t.values() for k, r in tab.items()]
+    t = dg.star_tables()
+    out += [(f"s.{k}", r) for tab in t.values() for k, r in tab.items()]
+    return out
+
+
+def test_device_generator_matches_host(G):
+    _, _, gd = G
+    z = dg.zipf_table(dg.ZIPF_S, dg.ZIPF_N)
+    zd = torch.from_numpy(z).cuda()
+    for name, rec in all_recipes():
+        for start, n in ((0, 100_000), (123_456_789, 5_003)):
+            want = dg.generate(rec, n, start, zipf=z)
+            got = host(gd.generate(rec, n, start, zipf=zd))
+            assert np.array_equal(got, want), (name, start)
+
+
+def compare(got, want):
+    ok, oa, g = got
+    wk, wa, of = want
+    assert not of
+    Gn = wa.shape[0]
+    assert int(g.item()) == Gn
+    for i in range(len(ok)):
+        assert np.array_equal(host(ok[i], Gn).astype(np.int64), wk[i])
+    assert np.array_equal(host(oa)[:Gn], wa)
+
+
+@pytest.mark.parametrize("n", [1, 4097, 1_000_000])
+def test_q6(G, n):
+    tqp, Q, gd = G
+    rec = dg.q6_lineitem()
+    want = pl.q6(dg.make_table(rec, n))
+    compare(Q.q6(gd.make_table(rec, n)), want)
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
+@pytest.mark.parametrize("sparse", [False, True])
+@pytest.mark.parametrize("n,m", [(1, 1), (100_000, 2_000), (2_000_003, 50_000)])
+def test_q14_fused_and_unfused(G, sparse, n, m):
+    tqp, Q, gd = G
+    rec = dg.q14_tables(m, sparse)
+    want = pl.q14(dg.make_table(rec["fact"], n), dg.make_table(rec["dim"], m))
+    fact, dim = gd.make_table(rec["fact"], n), gd.make_table(rec["dim"], m)
+    compare(Q.q14(fact, dim), want)
+    compare(Q.q14_unfused(fact, dim), want)
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
+def test_q14_full_size(G):
+    """Fact 60M x dim 1.5M, the benchmark's workload and launch configuration."""
+    tqp, Q, gd = G
+    rec = dg.q14_tables(1_500_000)
+    want = pl.q14(dg.make_table(rec["fact"], 60_000_000), dg.make_table(rec["dim"], 1_500_000))
+    got = Q.q14(gd.make_table(rec["fact"], 60_000_000), gd.make_table(rec["dim"], 1_500_000))
+    compare(got, want)
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
+@pytest.mark.parametrize("n", [10_000, 2_000_000])
+def test_skew_groupby(G, n):
+    tqp, Q, gd = G
+    z = dg.zipf_table(dg.ZIPF_S, dg.ZIPF_N)
+    rec = dg.skew_groupby()
+    want = pl.skew(dg.make_table(rec, n, zipf=z))
+    got = Q.skew(gd.make_table(rec, n, zipf=torch.from_numpy(z).cuda()), cap=n)
+    compare(got, want)
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
+def test_batched_instances_small(G):
+    tqp, Q, gd = G
+    ns, ms, gs = dg.batched_sizes()
+    for p in range(0, 512, 37):
+        n, m, g = int(ns[p]), int(ms[p]), int(gs[p])
+        rec = dg.batched_problem(p, n, m, g)
+        want = pl.batched_one(dg.make_table(rec["fact"], n), dg.make_table(rec["dim"], m))
+        compare(Q.batched_one(gd.make_table(rec["fact"], n), gd.make_table(rec["dim"], m)), want)
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
+def test_star_scaled(G):
+    """Star join at 1/100 of the fact rows, dimension sizes scaled alike."""
+    tqp, Q, gd = G
+    rec = dg.star_tables(200_000, 1_500_000)
+    n = 6_000_000
+    want = pl.star(dg.make_table(rec["fact"], n), dg.make_table(rec["dim1"], 200_000),
+                   dg.make_table(rec["dim2"], 1_500_000))
+    got = Q.star(gd.make_table(rec["fact"], n), gd.make_table(rec["dim1"], 200_000),
+                 gd.make_table(rec["dim2"], 1_500_000))
+    compare(got, want)
+    assert tqp.tqp_status_poll() == tqp.OK
