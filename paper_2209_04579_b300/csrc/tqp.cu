@@ -212,7 +212,7 @@ GroupWs carve_group(Carver& c, int64_t n, int word_bytes) {
 }
 
 tqp_status build_agg_program(const tqp_col* vals, int nvals, const tqp_expr* exprs, int nexprs,
-                             const tqp_agg* aggs, int naggs, AggProgram* P) {
+                             const tqp_agg* aggs, int naggs, AggProgram* P, bool have_rows) {
   if (nvals < 0 || nvals > TQP_MAX_VALS || nexprs < 0 || nexprs > TQP_MAX_EXPRS || naggs < 1 ||
       naggs > TQP_MAX_AGGS)
     return TQP_ERR_INVALID;
@@ -221,7 +221,7 @@ tqp_status build_agg_program(const tqp_col* vals, int nvals, const tqp_expr* exp
   P->nvals = nvals;
   for (int v = 0; v < nvals; ++v) {
     if (!valid_dtype(vals[v].dtype)) return TQP_ERR_DTYPE;
-    if (!vals[v].data) return TQP_ERR_INVALID;
+    if (have_rows && !vals[v].data) return TQP_ERR_INVALID;
     P->val[v] = vals[v].data;
     P->vdt[v] = vals[v].dtype;
   }
@@ -404,7 +404,7 @@ tqp_status tqp_filter(const tqp_col* cols, int ncols, const tqp_pred* preds, int
   a.npred = npred;
   for (int p = 0; p < npred; ++p) {
     int col = preds[p].col;
-    if (col < 0 || col >= ncols || !cols[col].data) return TQP_ERR_INVALID;
+    if (col < 0 || col >= ncols || (n > 0 && !cols[col].data)) return TQP_ERR_INVALID;
     if (!valid_dtype(cols[col].dtype)) return TQP_ERR_DTYPE;
     if (preds[p].op < TQP_LT || preds[p].op > TQP_NE) return TQP_ERR_INVALID;
     a.col[p] = cols[col].data;
@@ -543,7 +543,7 @@ tqp_status tqp_groupby_agg(const tqp_col* keys, int nkeys, const tqp_col* vals, 
     declared_bits += dtype_bytes(keys[k].dtype) * 8;
   }
   AggProgram P;
-  tqp_status st = build_agg_program(vals, nvals, exprs, nexprs, aggs, naggs, &P);
+  tqp_status st = build_agg_program(vals, nvals, exprs, nexprs, aggs, naggs, &P, n > 0);
   if (st != TQP_OK) return st;
   const int word_bytes = declared_bits <= 32 ? 4 : 8;
   Carver c(ws);

@@ -6,6 +6,7 @@ import os
 import re
 
 import pytest
+import torch
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PKG = os.path.join(ROOT, "paper_2209_04579_b300")
@@ -72,3 +73,28 @@ def test_host_argument_checks_and_size_queries():
                             ctypes.byref(ctypes.c_size_t(16)), None)
     assert st == tqp.ERR_WORKSPACE
     assert lib.tqp_status_string(tqp.ERR_TIMEOUT) == b"bounded wait ran out"
+
+
+def test_empty_inputs_accept_null_data():
+    """Empty columns have no storage (NULL data); n = 0 must not be an argument error."""
+    from paper_2209_04579_b300 import tqp
+    lib = tqp._lib
+    sz = ctypes.c_size_t(0)
+    cols = (tqp.Col * 1)(tqp.Col(None, tqp.I32, 0))
+    preds = (tqp.Pred * 1)(tqp.Pred(0, tqp.LT, 5))
+    assert lib.tqp_filter(cols, 1, preds, 1, 0, None, None, 0, None, None, ctypes.byref(sz), None) == tqp.OK
+    if not torch.cuda.is_available():
+        # no device here: the call gets past the argument checks and its first
+        # CUDA call (a memset of the count) reports ERR_CUDA; placeholder
+        # pointers are never handed to a real device
+        ws = ctypes.c_void_p(256)
+        st = lib.tqp_filter(cols, 1, preds, 1, 0, None, None, 0, ctypes.c_void_p(512), ws, ctypes.byref(sz), None)
+        assert st == tqp.ERR_CUDA
+    vals = (tqp.Col * 1)(tqp.Col(None, tqp.I64, 0))
+    ex = (tqp.Expr * 1)()
+    ex[0].nterms = 1
+    ex[0].term[0] = tqp.Term(0, 0, 1, 0)
+    aggs = (tqp.Agg * 1)(tqp.Agg(tqp.SUM, 0))
+    st = lib.tqp_groupby_agg(cols, 1, vals, 1, ex, 1, aggs, 1, None, 0, None, None, None, 0, None, None,
+                             ctypes.byref(sz), None)
+    assert st == tqp.OK
