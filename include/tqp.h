@@ -225,6 +225,110 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
                         void* const* d_out_keys, int64_t* d_out_aggs, int64_t cap,
                         int64_t* d_out_groups, void* ws, size_t* ws_bytes, tqp_stream_t stream);
 
+/* ========================================================================
+ * Learned range partitioner.
+ *
+ * The paper's third scenario (Section 3.3) runs a neural network inside the
+ * same tensor program as the relational operators.  Here a small network is
+ * trained, on the GPU, on the key distribution that the method's own sort
+ * produces, and used to route rows into ordered key-range buckets before the
+ * final sort, so that each bucket can be sorted on-chip.  Results never
+ * depend on the model: any non-decreasing bucket function gives the same,
+ * exact group-by.
+ *
+ * Model (TQP_CDF_HIDDEN = H hidden units, float32):
+ *   key normalisation  q = (p - umin) >> shift   (p: order-preserving packed
+ *                      key, q < 2^24 so the conversion is exact),
+ *                      x = (float)q * inv;
+ *   unit j             z_j = fmaf(w[j], x, b[j]), h_j = min(max(z_j, 0), 1);
+ *   output             F = c, then F = fmaf(a[j], h_j, F) for j = 0..H-1;
+ *   bucket of B        min(B - 1, (int)(min(max(F, 0), 1) * B)).
+ * With w >= 0 and a >= 0 (kept by projection after every training step)
+ * F and the bucket are non-decreasing in the key.
+ * ====================================================================== */
+#define TQP_CDF_HIDDEN 64
+
+typedef struct {
+  float w[TQP_CDF_HIDDEN];
+  float b[TQP_CDF_HIDDEN];
+  float a[TQP_CDF_HIDDEN];
+  float c;
+  int32_t shift;
+  float inv;
+  int32_t pad_;
+  uint64_t umin;
+} tqp_cdf_model; /* 792 bytes; lives in device memory */
+
+typedef struct {
+  int32_t epochs; /* full-sample Adam steps */
+  float lr;       /* Adam (Kingma & Ba 2015) step size and moments */
+  float beta1;
+  float beta2;
+  float eps;
+  int32_t pad_;
+} tqp_train_cfg;
+
+/* tqp_cdf_forward: F[i] = model(x[i]) (float32, the fixed evaluation order
+ * above) for i < n; if d_bucket is not NULL also its bucket of B. */
+tqp_status tqp_cdf_forward(const tqp_cdf_model* d_model, const float* d_x, int64_t n, float* d_F,
+                           int32_t* d_bucket, int B, tqp_stream_t stream);
+
+/* tqp_cdf_backward: gradient of the mean-squared error
+ * L = (1/n) sum_i (F(x_i) - y_i)^2 (F without the output clamp) with respect
+ * to w, b, a, c: d_grad[0..H) = dL/dw, [H..2H) = dL/db, [2H..3H) = dL/da,
+ * [3H] = dL/dc, [3H+1] = L.  Where a unit is clamped (z <= 0 or z >= 1) its
+ * w and b receive no gradient.  Deterministic: fixed reduction order.
+ * n <= 2^20. */
+tqp_status tqp_cdf_backward(const tqp_cdf_model* d_model, const float* d_x, const float* d_y, int64_t n,
+                            float* d_grad, void* ws, size_t* ws_bytes, tqp_stream_t stream);
+
+/* tqp_cdf_train: cfg->epochs Adam steps on (x, y) starting from *d_model
+ * (updated in place), each followed by the projection w, a >= 0.  The loss
+ * before each step goes to d_loss[epoch] when d_loss is not NULL. n <= 2^20. */
+tqp_status tqp_cdf_train(const float* d_x, const float* d_y, int64_t n, tqp_cdf_model* d_model,
+                         const tqp_train_cfg* cfg, float* d_loss, void* ws, size_t* ws_bytes,
+                         tqp_stream_t stream);
+
+typedef struct {
+  int32_t sample;  /* keys sampled (strided) to train on; power of two in [1024, 2^20] */
+  int32_t buckets; /* learned buckets B (power of two <= 65536); 0 = from n */
+  int32_t train;   /* 1 = train the network; 0 = keep the identity CDF F(x) = x */
+  int32_t heavy;   /* 1 = aggregate the sample's frequent keys directly */
+  tqp_train_cfg train_cfg;
+} tqp_learned_cfg;
+
+typedef struct {          /* written to device memory by the learned group-by */
+  int64_t buckets;        /* B */
+  int64_t heavy_keys;     /* keys aggregated directly */
+  int64_t light_rows;     /* rows routed through the buckets */
+  int64_t max_bucket;     /* largest bucket (rows) */
+  int64_t over_capacity;  /* buckets sorted by the global-memory fallback */
+  int64_t nonempty;       /* non-empty buckets */
+  float loss_first;       /* training loss before the first / the last step */
+  float loss_last;
+} tqp_learned_stats;
+
+/* ------------------------------------------------------------------------
+ * tqp_groupby_agg_learned -- the group-by of tqp_groupby_agg (same inputs,
+ * outputs and guarantees: bit-identical results) computed through the
+ * learned range partitioner: key range and packing; a strided sample of the
+ * packed keys sorted by the radix sort; empirical-CDF targets
+ * (first rank + count / 2) / S per distinct sample key; GPU training; keys
+ * that are frequent in the sample aggregated directly; the other rows
+ * scattered into the network's buckets and each bucket sorted on-chip (a
+ * bucket beyond the on-chip capacity is radix-sorted by one block in global
+ * memory); one reduce-by-key over the sorted rows that merges the directly
+ * aggregated keys in key order.  d_model_out (nullable) receives the trained
+ * model, d_stats (nullable) the statistics above.
+ * ---------------------------------------------------------------------- */
+tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col* vals, int nvals,
+                                   const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
+                                   const int32_t* d_sel, int64_t n, const int64_t* d_n,
+                                   void* const* d_out_keys, int64_t* d_out_aggs, int64_t cap,
+                                   int64_t* d_out_groups, const tqp_learned_cfg* cfg,
+                                   tqp_cdf_model* d_model_out, tqp_learned_stats* d_stats, void* ws,
+                                   size_t* ws_bytes, tqp_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Device status and test hooks.
  * tqp_status_poll: synchronises `stream`, returns the current device's status

@@ -235,7 +235,43 @@ struct ReduceArgs {
   Partial* pre_payload;    // [num_tiles]
   uint32_t* tile_counter;
   uint32_t num_tiles;
+  // keys aggregated outside the sorted rows (learned path), merged in key
+  // order: sorted packed keys, their count (device) and aggregates [nh][naggs]
+  const unsigned long long* heavy;
+  const int* d_nheavy;
+  const long long* heavy_acc;
 };
+
+__device__ __forceinline__ int64_t heavy_lower(const unsigned long long* h, int nh, unsigned long long x) {
+  int lo = 0, len = nh;
+  while (len > 0) {
+    int half = len >> 1;
+    if (h[lo + half] < x) { lo += half + 1; len -= half + 1; } else { len = half; }
+  }
+  return lo;
+}
+
+// Writes group g: key columns decoded from the packed word, aggregates.
+__device__ __forceinline__ void write_group(const ReduceArgs& a, int naggs, long long g, unsigned long long u,
+                                            const long long* v) {
+  if (g < 0 || g >= a.cap) return;
+  for (int j = 0; j < a.ks.nkeys; ++j) {
+    int b = a.plan->bits[j];
+    unsigned long long m = b >= 64 ? ~0ull : ((1ull << b) - 1);
+    long long kv = (long long)(((u >> a.plan->shift[j]) & m) + (unsigned long long)a.plan->kmin[j]);
+    store_from_i64(a.ks.out[j], a.ks.dt[j], g, kv);
+  }
+  for (int q = 0; q < naggs; ++q) a.out_aggs[g * naggs + q] = v[q];
+}
+
+// Heavy groups when no row went through the sort: group i at position i
+// (the reduce kernel then writes the group count, nh).
+__global__ void gb_heavy_only_kernel(ReduceArgs a, int naggs) {
+  if (a.plan->unsupported || clamp_n(a.n_max, a.d_n) > 0) return;
+  const int nh = a.d_nheavy ? *a.d_nheavy : 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nh; i += gridDim.x * blockDim.x)
+    write_group(a, naggs, i, a.heavy[i], a.heavy_acc + (size_t)i * naggs);
+}
 
 __device__ __forceinline__ void store_partial_relaxed(Partial* dst, const Partial& p, int naggs) {
   unsigned long long* d = reinterpret_cast<unsigned long long*>(dst->v);
@@ -274,6 +310,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
   const K* keys = static_cast<const K*>(a.keys);
   const bool unsupported = a.plan->unsupported != 0;
   const long long limit = g_spin_limit;
+  const int nh = (a.heavy && a.d_nheavy) ? *a.d_nheavy : 0;
 
   while (true) {
     if (threadIdx.x == 0) {
@@ -373,7 +410,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
       }
       s_tile_excl = acc;
       if (!failed && tile == a.num_tiles - 1) {
-        long long g = (long long)acc.c + tile_agg.c;
+        long long g = (long long)acc.c + tile_agg.c + nh;
         *a.d_out_groups = g;
         if (g > a.cap) raise_status(TQP_ERR_CAPACITY);
       }
@@ -397,23 +434,25 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
           ++seg;
 #pragma unroll
           for (int q = 0; q < TQP_MAX_AGGS; ++q) run.v[q] = (q < P.naggs) ? agg_identity(P.op[q]) : 0;
-          if (seg < a.cap) {
-            unsigned long long u = (unsigned long long)key[k];
-            for (int j = 0; j < a.ks.nkeys; ++j) {
-              int b = a.plan->bits[j];
-              unsigned long long m = b >= 64 ? ~0ull : ((1ull << b) - 1);
-              long long v = (long long)(((u >> a.plan->shift[j]) & m) + (unsigned long long)a.plan->kmin[j]);
-              store_from_i64(a.ks.out[j], a.ks.dt[j], seg, v);
-            }
+          if (nh) {
+            // heavy keys between the previous group's key and this one go just before it
+            int64_t hi_i = heavy_lower(a.heavy, nh, (unsigned long long)key[k]);
+            int64_t lo_i = p == 0 ? 0 : heavy_lower(a.heavy, nh, (unsigned long long)(k ? key[k - 1] : prev));
+            for (int64_t i = lo_i; i < hi_i; ++i)
+              write_group(a, P.naggs, seg + i, a.heavy[i], a.heavy_acc + (size_t)i * P.naggs);
           }
         }
         fold_row(run, P, a.rows[p]);
         K nk = (k + 1 < ITEMS) ? key[k + 1] : next_after;
         bool last = (p == nn - 1) || (nk != key[k]);
-        if (last && seg >= 0 && seg < a.cap) {
-#pragma unroll
-          for (int q = 0; q < TQP_MAX_AGGS; ++q)
-            if (q < P.naggs) a.out_aggs[seg * P.naggs + q] = run.v[q];
+        if (last && seg >= 0) {
+          long long hr = nh ? heavy_lower(a.heavy, nh, (unsigned long long)key[k]) : 0;
+          write_group(a, P.naggs, seg + hr, (unsigned long long)key[k], run.v);
+          if (nh && p == nn - 1) {
+            // heavy keys above the last group's key
+            for (int64_t i = hr; i < nh; ++i)
+              write_group(a, P.naggs, seg + 1 + i, a.heavy[i], a.heavy_acc + (size_t)i * P.naggs);
+          }
         }
       }
     }

@@ -1,0 +1,768 @@
+// Learned range partitioner: a monotone 1 -> H -> 1 network (clamp units,
+// non-negative weights) trained on the GPU on the empirical CDF of a sorted
+// key sample, then used to route the rows of a group-by into ordered
+// key-range buckets that are sorted on-chip.
+//
+// Forward, gradient and Adam kernels are hand-written and deterministic
+// (fixed reduction orders, no floating-point atomics).  The partition uses
+// the network's bucket function exactly: because the bucket is a
+// non-decreasing step function of the 24-bit normalised key q, it is fully
+// described by its B-1 step positions t_b = min{q : bucket(q) >= b}, found
+// by binary search with the same forward evaluation; a row's bucket is then
+// the number of steps at or below its q.  Keys that are frequent in the
+// sample are not scattered at all: their aggregates are folded in shared
+// memory during the partition pass and merged into the output in key order.
+#pragma once
+
+#include "common.cuh"
+#include "groupby.cuh"
+#include "sort.cuh"
+
+namespace tqp {
+
+constexpr int kH = TQP_CDF_HIDDEN;
+constexpr int kNP = 3 * kH + 1;   // parameters: w, b, a, c
+constexpr int kGradLen = kNP + 1; // + loss
+constexpr int kGradChunk = 1024;  // samples per gradient block
+constexpr int kMaxHeavy = 1024;
+constexpr int kDirBits = 12;      // directory over the top bits of q
+constexpr int kLocalCap = 8192;   // rows a block sorts on-chip
+constexpr int kLocalThreads = 512;
+constexpr int kLocalWarps = kLocalThreads / 32;
+constexpr int kLocalItems = kLocalCap / kLocalThreads;  // 16
+
+__device__ __forceinline__ float cdf_eval(const tqp_cdf_model& m, float x) {
+  float f = m.c;
+#pragma unroll 16
+  for (int j = 0; j < kH; ++j) {
+    float z = fmaf(m.w[j], x, m.b[j]);
+    float h = fminf(fmaxf(z, 0.0f), 1.0f);
+    f = fmaf(m.a[j], h, f);
+  }
+  return f;
+}
+
+__device__ __forceinline__ int cdf_bucket_of(float F, int B) {
+  float t = fminf(fmaxf(F, 0.0f), 1.0f) * (float)B;
+  int b = (int)t;
+  return b < B - 1 ? b : B - 1;
+}
+
+__device__ __forceinline__ void load_model_shared(tqp_cdf_model& dst, const tqp_cdf_model* src) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(tqp_cdf_model) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+// ---------------------------------------------------------------- forward
+__global__ void cdf_forward_kernel(const tqp_cdf_model* gm, const float* x, int64_t n, float* F, int32_t* bucket,
+                                   int B) {
+  __shared__ tqp_cdf_model m;
+  load_model_shared(m, gm);
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    float f = cdf_eval(m, x[i]);
+    F[i] = f;
+    if (bucket) bucket[i] = cdf_bucket_of(f, B);
+  }
+}
+
+// ---------------------------------------------------------------- gradient
+// One block per chunk of kGradChunk samples writes its partial sums
+// [gw(H), gb(H), ga(H), gc, sum of squared residuals] to partial[block].
+__global__ void __launch_bounds__(256) cdf_grad_kernel(const tqp_cdf_model* gm, const float* x, const float* y,
+                                                       const int64_t* d_n, int64_t n_max, float* partial) {
+  __shared__ tqp_cdf_model m;
+  __shared__ float sx[kGradChunk], sd[kGradChunk];
+  __shared__ float red[4][3 * kH];
+  __shared__ float s_loss[8], s_gc[8];
+  load_model_shared(m, gm);
+  __syncthreads();
+  const int64_t n = clamp_n(n_max, d_n);
+  const float scale = n > 0 ? 2.0f / (float)n : 0.0f;
+  const int64_t base = (int64_t)blockIdx.x * kGradChunk;
+  float loss = 0.0f, gc = 0.0f;
+  for (int k = threadIdx.x; k < kGradChunk; k += 256) {
+    int64_t i = base + k;
+    float xi = 0.0f, d = 0.0f;
+    if (i < n) {
+      xi = x[i];
+      float r = cdf_eval(m, xi) - y[i];
+      loss = fmaf(r, r, loss);
+      d = r * scale;
+      gc += d;
+    }
+    sx[k] = xi;
+    sd[k] = d;
+  }
+  // block sums of loss and gc in a fixed order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    gc += __shfl_xor_sync(0xffffffffu, gc, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_loss[threadIdx.x >> 5] = loss;
+    s_gc[threadIdx.x >> 5] = gc;
+  }
+  __syncthreads();
+  const int j = threadIdx.x & (kH - 1), q = threadIdx.x / kH;  // 4 quarters of the chunk
+  const float wj = m.w[j], bj = m.b[j], aj = m.a[j];
+  float gw = 0.0f, gb = 0.0f, ga = 0.0f;
+  for (int k = q * (kGradChunk / 4); k < (q + 1) * (kGradChunk / 4); ++k) {
+    float z = fmaf(wj, sx[k], bj);
+    float h = fminf(fmaxf(z, 0.0f), 1.0f);
+    float d = sd[k];
+    ga = fmaf(d, h, ga);
+    if (z > 0.0f && z < 1.0f) {
+      float da = d * aj;
+      gb += da;
+      gw = fmaf(da, sx[k], gw);
+    }
+  }
+  red[q][j] = gw;
+  red[q][kH + j] = gb;
+  red[q][2 * kH + j] = ga;
+  __syncthreads();
+  float* out = partial + (size_t)blockIdx.x * kGradLen;
+  if (threadIdx.x < 3 * kH) {
+    int t = threadIdx.x;
+    out[t] = ((red[0][t] + red[1][t]) + red[2][t]) + red[3][t];
+  } else if (threadIdx.x == 3 * kH) {
+    float s = 0.0f;
+    for (int w = 0; w < 8; ++w) s += s_gc[w];
+    out[kNP - 1] = s;
+  } else if (threadIdx.x == 3 * kH + 1) {
+    float s = 0.0f;
+    for (int w = 0; w < 8; ++w) s += s_loss[w];
+    out[kNP] = s;
+  }
+}
+
+// Sums the block partials in block order: grad[k] (k < kNP), grad[kNP] = loss.
+__global__ void cdf_grad_finish_kernel(const float* partial, int nblocks, const int64_t* d_n, int64_t n_max,
+                                       float* grad) {
+  int k = threadIdx.x;
+  if (k >= kGradLen) return;
+  float s = 0.0f;
+  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * kGradLen + k];
+  const int64_t n = clamp_n(n_max, d_n);
+  grad[k] = (k == kNP) ? (n > 0 ? s / (float)n : 0.0f) : s;
+}
+
+struct AdamState {
+  float m[kNP];
+  float v[kNP];
+};
+
+__device__ __forceinline__ float* param_ptr(tqp_cdf_model* md, int k) {
+  return k < kH ? &md->w[k] : k < 2 * kH ? &md->b[k - kH] : k < 3 * kH ? &md->a[k - 2 * kH] : &md->c;
+}
+
+// One Adam step from the block partials, then the projection w, a >= 0.
+__global__ void cdf_adam_kernel(tqp_cdf_model* md, const float* partial, int nblocks, const int64_t* d_n,
+                                int64_t n_max, AdamState* st, tqp_train_cfg cfg, int step, float* loss_out) {
+  int k = threadIdx.x;
+  if (k >= kGradLen) return;
+  float s = 0.0f;
+  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * kGradLen + k];
+  if (k == kNP) {
+    const int64_t n = clamp_n(n_max, d_n);
+    if (loss_out) loss_out[step] = n > 0 ? s / (float)n : 0.0f;
+    return;
+  }
+  const float t = (float)(step + 1);
+  float mk = cfg.beta1 * st->m[k] + (1.0f - cfg.beta1) * s;
+  float vk = cfg.beta2 * st->v[k] + (1.0f - cfg.beta2) * s * s;
+  st->m[k] = mk;
+  st->v[k] = vk;
+  float mh = mk / (1.0f - powf(cfg.beta1, t));
+  float vh = vk / (1.0f - powf(cfg.beta2, t));
+  float* p = param_ptr(md, k);
+  float np = *p - cfg.lr * mh / (sqrtf(vh) + cfg.eps);
+  bool nonneg = (k < kH) || (k >= 2 * kH && k < 3 * kH);
+  if (nonneg && np < 0.0f) np = 0.0f;
+  *p = np;
+}
+
+// ---------------------------------------------------------------- learned group-by plan
+struct LearnedPlan {
+  int shift;            // q = p >> shift
+  float inv;            // x = q * inv
+  unsigned long long qmax;
+  int dshift;           // directory index = q >> dshift
+  int B;
+  int nheavy;
+  int min_count;
+};
+
+// Identity CDF F(x) = x on [0, 1]: unit j ramps over [j/H, (j+1)/H].
+__device__ __forceinline__ void model_identity(tqp_cdf_model* md) {
+  for (int j = 0; j < kH; ++j) {
+    md->w[j] = (float)kH;
+    md->b[j] = -(float)j;
+    md->a[j] = 1.0f / (float)kH;
+  }
+  md->c = 0.0f;
+}
+
+// Normalisation of the packed keys from the group plan: p <= pmax, where
+// pmax packs every key column's (max - min).
+__global__ void lp_init_kernel(const GroupPlan* gp, int nkeys, tqp_cdf_model* md, LearnedPlan* lp, AdamState* st,
+                               int B, int min_count) {
+  if (threadIdx.x != 0) return;
+  unsigned long long pmax = 0;
+  for (int k = 0; k < nkeys; ++k)
+    if (gp->kmax[k] >= gp->kmin[k])
+      pmax |= ((unsigned long long)gp->kmax[k] - (unsigned long long)gp->kmin[k]) << gp->shift[k];
+  int bits = pmax ? 64 - __clzll((long long)pmax) : 0;
+  int shift = bits > 24 ? bits - 24 : 0;
+  unsigned long long qmax = pmax >> shift;
+  model_identity(md);
+  md->shift = shift;
+  md->umin = 0;
+  md->inv = qmax ? 1.0f / (float)qmax : 0.0f;
+  lp->shift = shift;
+  lp->inv = md->inv;
+  lp->qmax = qmax;
+  int qbits = qmax ? 64 - __clzll((long long)qmax) : 0;
+  lp->dshift = qbits > kDirBits ? qbits - kDirBits : 0;
+  lp->B = B;
+  lp->nheavy = 0;
+  lp->min_count = min_count;
+  for (int k = 0; k < kNP; ++k) st->m[k] = st->v[k] = 0.0f;
+}
+
+__device__ __forceinline__ unsigned long long pack_row(const KeySet& ks, const GroupPlan* gp, int64_t row) {
+  unsigned long long u = 0;
+  for (int k = 0; k < ks.nkeys; ++k)
+    u |= ((unsigned long long)load_as_i64(ks.col[k], ks.dt[k], row) - (unsigned long long)gp->kmin[k]) << gp->shift[k];
+  return u;
+}
+
+// Strided sample: sample[j] = packed key of selected row floor(j * n / S).
+__global__ void lp_sample_kernel(KeySet ks, const int32_t* sel, int64_t n_max, const int64_t* d_n,
+                                 const GroupPlan* gp, int S, unsigned long long* sample) {
+  const int64_t n = clamp_n(n_max, d_n);
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= S) return;
+  int64_t i = n > 0 ? (int64_t)j * n / S : 0;
+  int64_t row = sel ? sel[i] : i;
+  sample[j] = n > 0 ? pack_row(ks, gp, row) : 0ull;
+}
+
+__device__ __forceinline__ int64_t lb_u64(const unsigned long long* a, int64_t n, unsigned long long x) {
+  int64_t lo = 0, len = n;
+  while (len > 0) {
+    int64_t h = len >> 1;
+    if (a[lo + h] < x) { lo += h + 1; len -= h + 1; } else { len = h; }
+  }
+  return lo;
+}
+__device__ __forceinline__ int64_t ub_u64(const unsigned long long* a, int64_t lo, int64_t n, unsigned long long x) {
+  int64_t len = n - lo;
+  while (len > 0) {
+    int64_t h = len >> 1;
+    if (!(x < a[lo + h])) { lo += h + 1; len -= h + 1; } else { len = h; }
+  }
+  return lo;
+}
+
+// Training pairs from the sorted sample: x = normalised key, y = empirical
+// CDF midpoint (first rank + count / 2) / S of its key.
+__global__ void lp_targets_kernel(const unsigned long long* sorted, int S, const LearnedPlan* lp, float* x, float* y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S) return;
+  unsigned long long k = sorted[i];
+  int64_t lo = lb_u64(sorted, S, k);
+  int64_t hi = ub_u64(sorted, lo, S, k);
+  y[i] = (float)(((double)lo + 0.5 * (double)(hi - lo)) / (double)S);
+  x[i] = (float)(k >> lp->shift) * lp->inv;
+}
+
+// Heavy keys: distinct sample keys whose count reaches min_count; if more
+// than kMaxHeavy qualify, the count cut is raised until they fit.  Written
+// in ascending key order.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) lp_heavy_kernel(const unsigned long long* sorted, int S, LearnedPlan* lp,
+                                                         unsigned long long* heavy) {
+  __shared__ int hist[4096];
+  __shared__ int s_scan[33];
+  __shared__ int s_cut, s_base;
+  for (int i = threadIdx.x; i < 4096; i += 1024) hist[i] = 0;
+  __syncthreads();
+  const int minc = lp->min_count;
+  for (int i = threadIdx.x; i < S; i += 1024) {
+    if (i > 0 && sorted[i] == sorted[i - 1]) continue;
+    int c = (int)(ub_u64(sorted, i, S, sorted[i]) - i);
+    if (c >= minc) atomicAdd(&hist[c < 4095 ? c : 4095], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0, cut = 4096;
+    for (int c = 4095; c >= minc && c >= 1; --c) {
+      if (acc + hist[c] > kMaxHeavy) break;
+      acc += hist[c];
+      cut = c;
+    }
+    s_cut = cut;
+    s_base = 0;
+  }
+  __syncthreads();
+  const int cut = s_cut;
+  for (int base = 0; base < S; base += 1024) {
+    int i = base + threadIdx.x;
+    int flag = 0;
+    if (i < S && (i == 0 || sorted[i] != sorted[i - 1])) {
+      int c = (int)(ub_u64(sorted, i, S, sorted[i]) - i);
+      flag = (c >= cut);
+    }
+    int total;
+    int off = block_exclusive_sum<1024>(flag, s_scan, &total);
+    if (flag) heavy[s_base + off] = sorted[i];
+    __syncthreads();
+    if (threadIdx.x == 0) s_base += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) lp->nheavy = s_base;
+}
+
+__global__ void lp_no_heavy_kernel(LearnedPlan* lp) {
+  if (threadIdx.x == 0) lp->nheavy = 0;
+}
+
+// Step positions of the bucket function: thr[b-1] = min{q : bucket(q) >= b}
+// (qmax + 1 if none), b = 1..B-1.
+__global__ void lp_thresholds_kernel(const tqp_cdf_model* gm, const LearnedPlan* lp, unsigned* thr) {
+  __shared__ tqp_cdf_model m;
+  load_model_shared(m, gm);
+  __syncthreads();
+  const int B = lp->B;
+  int b = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  if (b >= B) return;
+  const unsigned long long qmax = lp->qmax;
+  unsigned long long lo = 0, hi = qmax + 1;
+  while (lo < hi) {
+    unsigned long long mid = (lo + hi) >> 1;
+    float x = (float)mid * m.inv;
+    if (cdf_bucket_of(cdf_eval(m, x), B) >= b) hi = mid; else lo = mid + 1;
+  }
+  thr[b - 1] = (unsigned)lo;
+}
+
+// dir[h] = number of steps below h << dshift, h = 0..2^kDirBits.
+__global__ void lp_directory_kernel(const LearnedPlan* lp, const unsigned* thr, int* dir) {
+  int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h > (1 << kDirBits)) return;
+  const int nt = lp->B - 1;
+  unsigned long long v = (unsigned long long)h << lp->dshift;
+  int lo = 0, len = nt;
+  while (len > 0) {
+    int half = len >> 1;
+    if ((unsigned long long)thr[lo + half] < v) { lo += half + 1; len -= half + 1; } else { len = half; }
+  }
+  dir[h] = lo;
+}
+
+__device__ __forceinline__ int lp_bucket(unsigned long long p, const LearnedPlan& lp, const int* s_dir,
+                                         const unsigned* thr) {
+  unsigned long long q = p >> lp.shift;
+  int h = (int)(q >> lp.dshift);
+  int lo = s_dir[h], hi = s_dir[h + 1];
+  while (lo < hi) {  // first step above q
+    int mid = (lo + hi) >> 1;
+    if ((unsigned long long)thr[mid] <= q) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int heavy_index(const unsigned long long* s_heavy, int nh, unsigned long long p) {
+  int lo = 0, len = nh;
+  while (len > 0) {
+    int half = len >> 1;
+    if (s_heavy[lo + half] < p) { lo += half + 1; len -= half + 1; } else { len = half; }
+  }
+  return (lo < nh && s_heavy[lo] == p) ? lo : -1;
+}
+
+struct PartArgs {
+  KeySet ks;
+  const int32_t* sel;
+  int64_t n_max;
+  const int64_t* d_n;
+  const GroupPlan* gp;
+  const LearnedPlan* lp;
+  const unsigned* thr;
+  const int* dir;
+  const unsigned long long* heavy;
+  unsigned* count;          // [B]
+  unsigned* cursor;         // [B]
+  unsigned long long* out_p;
+  int32_t* out_row;
+  long long* heavy_acc;     // [nheavy][naggs]
+};
+
+// Light rows per bucket.
+__global__ void __launch_bounds__(256) lp_hist_kernel(PartArgs a) {
+  __shared__ int s_dir[(1 << kDirBits) + 1];
+  __shared__ unsigned long long s_heavy[kMaxHeavy];
+  const LearnedPlan lp = *a.lp;
+  for (int i = threadIdx.x; i <= (1 << kDirBits); i += blockDim.x) s_dir[i] = a.dir[i];
+  for (int i = threadIdx.x; i < lp.nheavy; i += blockDim.x) s_heavy[i] = a.heavy[i];
+  __syncthreads();
+  const int64_t n = clamp_n(a.n_max, a.d_n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    int64_t row = a.sel ? a.sel[i] : i;
+    unsigned long long p = pack_row(a.ks, a.gp, row);
+    if (lp.nheavy && heavy_index(s_heavy, lp.nheavy, p) >= 0) continue;
+    atomicAdd(&a.count[lp_bucket(p, lp, s_dir, a.thr)], 1u);
+  }
+}
+
+// Exclusive scan of the bucket counts into offsets (and cursors), the
+// light-row total, and statistics.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) lp_offsets_kernel(const LearnedPlan* lp, const unsigned* count, unsigned* off,
+                                                          unsigned* cursor, tqp_learned_stats* stats,
+                                                          const float* loss, int epochs, int64_t* light_n) {
+  __shared__ int s_scan[33];
+  __shared__ unsigned s_max[32];
+  __shared__ int s_over[32], s_ne[32];
+  const int B = lp->B;
+  const int per = (B + 1023) / 1024;
+  const int b0 = threadIdx.x * per;
+  unsigned sum = 0, mx = 0;
+  int over = 0, ne = 0;
+  for (int b = b0; b < b0 + per && b < B; ++b) {
+    unsigned c = count[b];
+    sum += c;
+    mx = c > mx ? c : mx;
+    over += c > (unsigned)kLocalCap;
+    ne += c > 0;
+  }
+  int total;
+  int excl = block_exclusive_sum<1024>((int)sum, s_scan, &total);
+  unsigned run = (unsigned)excl;
+  for (int b = b0; b < b0 + per && b < B; ++b) {
+    off[b] = run;
+    cursor[b] = run;
+    run += count[b];
+  }
+  if (threadIdx.x == 1023) {
+    off[B] = (unsigned)total;
+    *light_n = total;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = m2 > mx ? m2 : mx;
+    over += __shfl_xor_sync(0xffffffffu, over, o);
+    ne += __shfl_xor_sync(0xffffffffu, ne, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_max[threadIdx.x >> 5] = mx;
+    s_over[threadIdx.x >> 5] = over;
+    s_ne[threadIdx.x >> 5] = ne;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && stats) {
+    unsigned m3 = 0;
+    long long o3 = 0, n3 = 0;
+    for (int w = 0; w < 32; ++w) {
+      m3 = s_max[w] > m3 ? s_max[w] : m3;
+      o3 += s_over[w];
+      n3 += s_ne[w];
+    }
+    stats->buckets = B;
+    stats->heavy_keys = lp->nheavy;
+    stats->light_rows = total;
+    stats->max_bucket = m3;
+    stats->over_capacity = o3;
+    stats->nonempty = n3;
+    stats->loss_first = (loss && epochs > 0) ? loss[0] : 0.0f;
+    stats->loss_last = (loss && epochs > 0) ? loss[epochs - 1] : 0.0f;
+  }
+}
+
+__global__ void lp_heavy_init_kernel(const LearnedPlan* lp, AggProgram P, long long* acc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < lp->nheavy * P.naggs) acc[i] = agg_identity(P.op[i % P.naggs]);
+}
+
+__device__ __forceinline__ void fold_atomic(long long* slot, int op, long long x) {
+  switch (op) {
+    case TQP_MIN: atomicMin(slot, x); break;
+    case TQP_MAX: atomicMax(slot, x); break;
+    default: atomicAdd(reinterpret_cast<unsigned long long*>(slot), (unsigned long long)x); break;
+  }
+}
+
+// Scatter of the light rows into their buckets; heavy rows folded into
+// per-block shared accumulators, flushed with atomics at the end.
+__global__ void __launch_bounds__(256) lp_scatter_kernel(PartArgs a, AggProgram P) {
+  __shared__ int s_dir[(1 << kDirBits) + 1];
+  __shared__ unsigned long long s_heavy[kMaxHeavy];
+  extern __shared__ long long s_acc[];  // [nheavy][naggs]
+  const LearnedPlan lp = *a.lp;
+  const int nh = lp.nheavy;
+  for (int i = threadIdx.x; i <= (1 << kDirBits); i += blockDim.x) s_dir[i] = a.dir[i];
+  for (int i = threadIdx.x; i < nh; i += blockDim.x) s_heavy[i] = a.heavy[i];
+  for (int i = threadIdx.x; i < nh * P.naggs; i += blockDim.x) s_acc[i] = agg_identity(P.op[i % P.naggs]);
+  __syncthreads();
+  const int64_t n = clamp_n(a.n_max, a.d_n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    int64_t row = a.sel ? a.sel[i] : i;
+    unsigned long long p = pack_row(a.ks, a.gp, row);
+    int h = nh ? heavy_index(s_heavy, nh, p) : -1;
+    if (h >= 0) {
+      for (int q = 0; q < P.naggs; ++q) {
+        long long x = P.op[q] == TQP_COUNT ? 1 : eval_expr(P, P.expr[q], row);
+        fold_atomic(&s_acc[h * P.naggs + q], P.op[q], x);
+      }
+      continue;
+    }
+    int b = lp_bucket(p, lp, s_dir, a.thr);
+    unsigned pos = atomicAdd(&a.cursor[b], 1u);
+    a.out_p[pos] = p;
+    a.out_row[pos] = (int32_t)row;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nh * P.naggs; i += blockDim.x) {
+    long long v = s_acc[i];
+    int op = P.op[i % P.naggs];
+    if (v != agg_identity(op)) fold_atomic(&a.heavy_acc[i], op, v);
+  }
+}
+
+// ---------------------------------------------------------------- bucket sort
+// Stable rank within a block whose warp w owns items [w * per, (w + 1) * per)
+// in rounds of 32: returns in pos[] the block-local destination of each item
+// for digit values dig[] (kRadix = invalid).  s_cnt: [WARPS][kRadix + 1],
+// s_start: [kRadix] (exclusive digit starts), s_scan: 33 ints.
+template <int WARPS, int ITEMS>
+__device__ __forceinline__ void block_rank(const unsigned (&dig)[ITEMS], int (&pos)[ITEMS], unsigned* s_cnt,
+                                           unsigned* s_start, int* s_scan, int* total_out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < WARPS * (kRadix + 1); i += WARPS * 32) s_cnt[i] = 0;
+  __syncthreads();
+  unsigned rank[ITEMS];
+#pragma unroll
+  for (int it = 0; it < ITEMS; ++it) {
+    unsigned peers = __match_any_sync(0xffffffffu, dig[it]);
+    int leader = 31 - __clz(peers);
+    unsigned before = __popc(peers & ((1u << lane) - 1));
+    unsigned* c = s_cnt + warp * (kRadix + 1) + dig[it];
+    unsigned base = *c;
+    __syncwarp();
+    if (lane == leader) *c = base + __popc(peers);
+    __syncwarp();
+    rank[it] = base + before;
+  }
+  __syncthreads();
+  int tc = 0;
+  if (threadIdx.x < kRadix) {
+    unsigned run = 0;
+    for (int w = 0; w < WARPS; ++w) {
+      unsigned c = s_cnt[w * (kRadix + 1) + threadIdx.x];
+      s_cnt[w * (kRadix + 1) + threadIdx.x] = run;
+      run += c;
+    }
+    tc = (int)run;
+  }
+  int total;
+  int st = block_exclusive_sum<WARPS * 32>(tc, s_scan, &total);
+  if (threadIdx.x < kRadix) s_start[threadIdx.x] = (unsigned)st;
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < ITEMS; ++it)
+    pos[it] = dig[it] < kRadix ? (int)(s_start[dig[it]] + s_cnt[warp * (kRadix + 1) + dig[it]] + rank[it]) : -1;
+  *total_out = total;
+  __syncthreads();
+}
+
+struct BucketSortArgs {
+  const LearnedPlan* lp;
+  const unsigned* off;          // [B + 1]
+  unsigned long long* p;        // light rows, bucketed (sorted in place)
+  int32_t* row;
+  unsigned long long* alt_p;    // scratch of the same size (global fallback)
+  int32_t* alt_row;
+  uint32_t* queue;
+};
+
+__device__ __forceinline__ unsigned long long block_minmax_span(unsigned long long lo_in, unsigned long long hi_in,
+                                                                unsigned long long* s_red, unsigned long long* mn) {
+  unsigned long long lo = lo_in, hi = hi_in;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long a = __shfl_xor_sync(0xffffffffu, lo, o), b = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    s_red[2 * w] = lo;
+    s_red[2 * w + 1] = hi;
+  }
+  __syncthreads();
+  lo = ~0ull;
+  hi = 0;
+  for (int i = 0; i < kLocalWarps; ++i) {
+    lo = s_red[2 * i] < lo ? s_red[2 * i] : lo;
+    hi = s_red[2 * i + 1] > hi ? s_red[2 * i + 1] : hi;
+  }
+  __syncthreads();
+  *mn = lo;
+  return hi >= lo ? hi - lo : 0;
+}
+
+__global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSortArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* const kA0 = reinterpret_cast<unsigned long long*>(smem);
+  unsigned long long* const kB0 = kA0 + kLocalCap;
+  int32_t* const rA0 = reinterpret_cast<int32_t*>(kB0 + kLocalCap);
+  int32_t* const rB0 = rA0 + kLocalCap;
+  unsigned* s_cnt = reinterpret_cast<unsigned*>(rB0 + kLocalCap);
+  unsigned* s_start = s_cnt + kLocalWarps * (kRadix + 1);
+  __shared__ int s_scan[33];
+  __shared__ unsigned long long s_red[2 * kLocalWarps];
+  __shared__ uint32_t s_b;
+  const int B = a.lp->B;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  while (true) {
+    if (threadIdx.x == 0) s_b = atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const uint32_t b = s_b;
+    __syncthreads();
+    if (b >= (uint32_t)B) break;
+    const int64_t o0 = a.off[b], o1 = a.off[b + 1];
+    const int64_t m = o1 - o0;
+    if (m <= 1) continue;
+    if (m <= kLocalCap) {
+      // ---- on-chip: load, find the key span, LSD over its bits, store
+      unsigned long long* kA = kA0;
+      unsigned long long* kB = kB0;
+      int32_t* rA = rA0;
+      int32_t* rB = rB0;
+      unsigned long long lo = ~0ull, hi = 0;
+      for (int i = threadIdx.x; i < m; i += kLocalThreads) {
+        unsigned long long k = a.p[o0 + i];
+        kA[i] = k;
+        rA[i] = a.row[o0 + i];
+        lo = k < lo ? k : lo;
+        hi = k > hi ? k : hi;
+      }
+      unsigned long long pmin;
+      unsigned long long span = block_minmax_span(lo, hi, s_red, &pmin);
+      if (span == 0) continue;  // one key: already in order
+      const int bits = 64 - __clzll((long long)span);
+      const int per = (int)((m + kLocalWarps - 1) / kLocalWarps);
+      const int wbeg = warp * per;
+      for (int sh = 0; sh < bits; sh += kRadixBits) {
+        unsigned dig[kLocalItems];
+        int pos[kLocalItems];
+#pragma unroll
+        for (int it = 0; it < kLocalItems; ++it) {
+          int i = wbeg + it * 32 + lane;
+          bool v = (it * 32 + lane < per) && i < m;
+          dig[it] = v ? (unsigned)(((kA[i] - pmin) >> sh) & (kRadix - 1)) : kRadix;
+        }
+        int total;
+        block_rank<kLocalWarps, kLocalItems>(dig, pos, s_cnt, s_start, s_scan, &total);
+#pragma unroll
+        for (int it = 0; it < kLocalItems; ++it) {
+          if (pos[it] >= 0) {
+            int i = wbeg + it * 32 + lane;
+            kB[pos[it]] = kA[i];
+            rB[pos[it]] = rA[i];
+          }
+        }
+        __syncthreads();
+        unsigned long long* tk = kA; kA = kB; kB = tk;
+        int32_t* tr = rA; rA = rB; rB = tr;
+      }
+      for (int i = threadIdx.x; i < m; i += kLocalThreads) {
+        a.p[o0 + i] = kA[i];
+        a.row[o0 + i] = rA[i];
+      }
+      __syncthreads();
+    } else {
+      // ---- fallback: LSD radix sort of this bucket in global memory by one
+      // block, tile by tile (tiles in order keep it stable)
+      unsigned long long lo = ~0ull, hi = 0;
+      for (int64_t i = threadIdx.x; i < m; i += kLocalThreads) {
+        unsigned long long k = a.p[o0 + i];
+        lo = k < lo ? k : lo;
+        hi = k > hi ? k : hi;
+      }
+      unsigned long long pmin;
+      unsigned long long span = block_minmax_span(lo, hi, s_red, &pmin);
+      if (span == 0) continue;
+      const int bits = 64 - __clzll((long long)span);
+      unsigned long long* src_p = a.p + o0;
+      int32_t* src_r = a.row + o0;
+      unsigned long long* dst_p = a.alt_p + o0;
+      int32_t* dst_r = a.alt_row + o0;
+      unsigned* s_base = reinterpret_cast<unsigned*>(kA0);  // running digit offsets
+      for (int sh = 0; sh < bits; sh += kRadixBits) {
+        unsigned* s_hist = s_start;
+        for (int d = threadIdx.x; d < kRadix; d += kLocalThreads) s_hist[d] = 0;
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < m; i += kLocalThreads)
+          atomicAdd(&s_hist[((src_p[i] - pmin) >> sh) & (kRadix - 1)], 1u);
+        __syncthreads();
+        int c = threadIdx.x < kRadix ? (int)s_hist[threadIdx.x] : 0;
+        int tot;
+        int ex = block_exclusive_sum<kLocalThreads>(c, s_scan, &tot);
+        if (threadIdx.x < kRadix) s_base[threadIdx.x] = (unsigned)ex;
+        __syncthreads();
+        for (int64_t t0 = 0; t0 < m; t0 += kLocalCap) {
+          const int tm = (int)(m - t0 < kLocalCap ? m - t0 : kLocalCap);
+          const int per = (tm + kLocalWarps - 1) / kLocalWarps;
+          const int wbeg = warp * per;
+          unsigned dig[kLocalItems];
+          int pos[kLocalItems];
+          unsigned long long kk[kLocalItems];
+#pragma unroll
+          for (int it = 0; it < kLocalItems; ++it) {
+            int i = wbeg + it * 32 + lane;
+            bool v = (it * 32 + lane < per) && i < tm;
+            kk[it] = v ? src_p[t0 + i] : 0ull;
+            dig[it] = v ? (unsigned)(((kk[it] - pmin) >> sh) & (kRadix - 1)) : kRadix;
+          }
+          int total;
+          block_rank<kLocalWarps, kLocalItems>(dig, pos, s_cnt, s_start, s_scan, &total);
+#pragma unroll
+          for (int it = 0; it < kLocalItems; ++it) {
+            if (pos[it] >= 0) {
+              int i = wbeg + it * 32 + lane;
+              unsigned d = dig[it];
+              int64_t g = (int64_t)s_base[d] + (pos[it] - (int)s_start[d]);
+              dst_p[g] = kk[it];
+              dst_r[g] = src_r[t0 + i];
+            }
+          }
+          __syncthreads();
+          if (threadIdx.x < kRadix) {  // advance by this tile's digit counts
+            unsigned d = threadIdx.x;
+            unsigned next = (d + 1 < kRadix) ? s_start[d + 1] : (unsigned)total;
+            s_base[d] += next - s_start[d];
+          }
+          __syncthreads();
+        }
+        unsigned long long* tp = src_p; src_p = dst_p; dst_p = tp;
+        int32_t* tr = src_r; src_r = dst_r; dst_r = tr;
+      }
+      if (src_p != a.p + o0) {  // odd number of passes: copy back
+        for (int64_t i = threadIdx.x; i < m; i += kLocalThreads) {
+          a.p[o0 + i] = src_p[i];
+          a.row[o0 + i] = src_r[i];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace tqp

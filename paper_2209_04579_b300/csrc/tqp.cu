@@ -14,6 +14,7 @@
 #include "filter.cuh"
 #include "groupby.cuh"
 #include "join.cuh"
+#include "learned.cuh"
 #include "sort.cuh"
 #include "star.cuh"
 
@@ -282,6 +283,9 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
   r.agg_payload = w.agg_payload;
   r.pre_payload = w.pre_payload;
   r.num_tiles = w.tiles;
+  r.heavy = nullptr;
+  r.d_nheavy = nullptr;
+  r.heavy_acc = nullptr;
   if (word_bytes == 4) {
     auto k = gb_reduce_kernel<uint32_t, kReduceThreads, kReduceItems>;
     prof_mark(4, true, s);
@@ -868,6 +872,258 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
   TQP_CUDA(cudaMemsetAsync(ccounter, 0, 4, s));
   auto ck = star_compact_kernel<kCompactT, kCompactI>;
   ck<<<persistent_grid(ck, kCompactT, 0, ctiles), kCompactT, 0, s>>>(ca); note_launch();
+  return last_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Learned CDF model and the learned group-by.
+tqp_status tqp_cdf_forward(const tqp_cdf_model* d_model, const float* d_x, int64_t n, float* d_F, int32_t* d_bucket,
+                           int B, tqp_stream_t stream) {
+  if (n < 0 || n > INT_MAX || (d_bucket && (B < 1 || B > (1 << 24)))) return TQP_ERR_INVALID;
+  if (n == 0) return TQP_OK;
+  if (!d_model || !d_x || !d_F) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cdf_forward_kernel<<<stride_grid(n, 256), 256, 0, s>>>(d_model, d_x, n, d_F, d_bucket, B); note_launch();
+  return last_launch();
+}
+
+tqp_status tqp_cdf_backward(const tqp_cdf_model* d_model, const float* d_x, const float* d_y, int64_t n,
+                            float* d_grad, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || n < 0 || n > (1 << 20)) return TQP_ERR_INVALID;
+  const int nb = (int)((n + kGradChunk - 1) / kGradChunk);
+  Carver c(ws);
+  float* partial = c.take<float>((size_t)(nb > 0 ? nb : 1) * kGradLen);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (!d_model || !d_grad || (n > 0 && (!d_x || !d_y))) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (nb > 0) {
+    cdf_grad_kernel<<<nb, 256, 0, s>>>(d_model, d_x, d_y, nullptr, n, partial); note_launch();
+  }
+  cdf_grad_finish_kernel<<<1, 256, 0, s>>>(partial, nb, nullptr, n, d_grad); note_launch();
+  return last_launch();
+}
+
+namespace {
+bool valid_train_cfg(const tqp_train_cfg* cfg) {
+  return cfg && cfg->epochs >= 0 && cfg->epochs <= 100000 && cfg->lr > 0 && cfg->beta1 >= 0 && cfg->beta1 < 1 &&
+         cfg->beta2 >= 0 && cfg->beta2 < 1 && cfg->eps > 0;
+}
+
+void launch_training(tqp_cdf_model* model, const float* x, const float* y, int64_t n, const int64_t* d_n,
+                     const tqp_train_cfg& cfg, float* partial, AdamState* st, float* loss, cudaStream_t s) {
+  const int nb = (int)((n + kGradChunk - 1) / kGradChunk);
+  for (int e = 0; e < cfg.epochs; ++e) {
+    cdf_grad_kernel<<<nb, 256, 0, s>>>(model, x, y, d_n, n, partial); note_launch();
+    cdf_adam_kernel<<<1, 256, 0, s>>>(model, partial, nb, d_n, n, st, cfg, e, loss); note_launch();
+  }
+}
+}  // namespace
+
+tqp_status tqp_cdf_train(const float* d_x, const float* d_y, int64_t n, tqp_cdf_model* d_model,
+                         const tqp_train_cfg* cfg, float* d_loss, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || n < 1 || n > (1 << 20) || !valid_train_cfg(cfg)) return TQP_ERR_INVALID;
+  const int nb = (int)((n + kGradChunk - 1) / kGradChunk);
+  Carver c(ws);
+  float* partial = c.take<float>((size_t)nb * kGradLen);
+  AdamState* st = c.take<AdamState>(1);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (!d_x || !d_y || !d_model) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  TQP_CUDA(cudaMemsetAsync(st, 0, sizeof(AdamState), s));
+  launch_training(d_model, d_x, d_y, n, nullptr, *cfg, partial, st, d_loss, s);
+  return last_launch();
+}
+
+tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col* vals, int nvals,
+                                   const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
+                                   const int32_t* d_sel, int64_t n, const int64_t* d_n, void* const* d_out_keys,
+                                   int64_t* d_out_aggs, int64_t cap, int64_t* d_out_groups,
+                                   const tqp_learned_cfg* cfg, tqp_cdf_model* d_model_out,
+                                   tqp_learned_stats* d_stats, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || !cfg || n < 0 || n >= (1ll << 30) || nkeys < 1 || nkeys > TQP_MAX_KEYS || !keys)
+    return TQP_ERR_INVALID;
+  const int S = cfg->sample;
+  if (S < 1024 || S > (1 << 20) || (S & (S - 1))) return TQP_ERR_INVALID;
+  if (cfg->buckets < 0 || cfg->buckets == 1 || cfg->buckets > 65536 || (cfg->buckets & (cfg->buckets - 1)))
+    return TQP_ERR_INVALID;
+  if (cfg->train && !valid_train_cfg(&cfg->train_cfg)) return TQP_ERR_INVALID;
+  for (int k = 0; k < nkeys; ++k)
+    if (!valid_dtype(keys[k].dtype)) return TQP_ERR_DTYPE;
+  AggProgram P;
+  tqp_status st = build_agg_program(vals, nvals, exprs, nexprs, aggs, naggs, &P, n > 0);
+  if (st != TQP_OK) return st;
+  int B = cfg->buckets;
+  if (B == 0) {
+    B = 256;
+    while (B < 65536 && (int64_t)B * 2048 < n) B <<= 1;
+  }
+  const int epochs = cfg->train ? cfg->train_cfg.epochs : 0;
+  long long minc = (long long)((double)S * kLocalCap / (2.0 * (double)(n > 0 ? n : 1))) + 1;
+  if (minc < 2) minc = 2;
+  if (minc > 4095) minc = 4095;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const int nb = S / kGradChunk;
+  const int64_t rtiles = (n + kReduceThreads * kReduceItems - 1) / (kReduceThreads * kReduceItems);
+  Carver c(ws);
+  GroupPlan* gp = c.take<GroupPlan>(1);
+  unsigned long long* sample = c.take<unsigned long long>(S);
+  unsigned long long* ssorted = c.take<unsigned long long>(S);
+  int32_t* srows = c.take<int32_t>(S);
+  SortWs ssort = carve_sort(c, S, 8, 8);
+  float* tx = c.take<float>(S);
+  float* ty = c.take<float>(S);
+  tqp_cdf_model* model = c.take<tqp_cdf_model>(1);
+  LearnedPlan* lp = c.take<LearnedPlan>(1);
+  AdamState* adam = c.take<AdamState>(1);
+  float* partial = c.take<float>((size_t)nb * kGradLen);
+  float* loss = c.take<float>((size_t)(epochs > 0 ? epochs : 1));
+  unsigned long long* heavy = c.take<unsigned long long>(kMaxHeavy);
+  long long* heavy_acc = c.take<long long>((size_t)kMaxHeavy * naggs);
+  unsigned* thr = c.take<unsigned>((size_t)B);
+  int* dir = c.take<int>((1 << kDirBits) + 1);
+  unsigned* count = c.take<unsigned>((size_t)B);
+  unsigned* cursor = c.take<unsigned>((size_t)B);
+  unsigned* off = c.take<unsigned>((size_t)B + 1);
+  int64_t* light_n = c.take<int64_t>(1);
+  unsigned long long* lpk = c.take<unsigned long long>(nn);
+  int32_t* lrow = c.take<int32_t>(nn);
+  unsigned long long* apk = c.take<unsigned long long>(nn);
+  int32_t* arow = c.take<int32_t>(nn);
+  uint32_t* queue = c.take<uint32_t>(1);
+  uint32_t* rctrl = c.take<uint32_t>(1 + (size_t)(rtiles > 0 ? rtiles : 1));
+  Partial* ragg = c.take<Partial>((size_t)(rtiles > 0 ? rtiles : 1));
+  Partial* rpre = c.take<Partial>((size_t)(rtiles > 0 ? rtiles : 1));
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (!d_out_groups || cap < 0 || (cap > 0 && (!d_out_aggs || !d_out_keys))) return TQP_ERR_INVALID;
+  KeySet ks;
+  std::memset(&ks, 0, sizeof(ks));
+  ks.nkeys = nkeys;
+  for (int k = 0; k < nkeys; ++k) {
+    if (n > 0 && !keys[k].data) return TQP_ERR_INVALID;
+    if (cap > 0 && !d_out_keys[k]) return TQP_ERR_INVALID;
+    ks.col[k] = keys[k].data;
+    ks.dt[k] = keys[k].dtype;
+    ks.out[k] = cap > 0 ? d_out_keys[k] : nullptr;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    TQP_CUDA(cudaMemsetAsync(d_out_groups, 0, sizeof(int64_t), s));
+    if (d_stats) TQP_CUDA(cudaMemsetAsync(d_stats, 0, sizeof(tqp_learned_stats), s));
+    return TQP_OK;
+  }
+  // 1. key range and packing (always a 64-bit packed word on this path)
+  gb_init_kernel<<<1, 32, 0, s>>>(gp); note_launch();
+  gb_keyrange_kernel<256><<<stride_grid(n, 256, 4), 256, 0, s>>>(ks, d_sel, n, d_n, gp); note_launch();
+  gb_plan_kernel<<<1, 32, 0, s>>>(gp, nkeys, 64); note_launch();
+  lp_init_kernel<<<1, 32, 0, s>>>(gp, nkeys, model, lp, adam, B, (int)minc); note_launch();
+  // 2. sample, sorted by the radix sort; training pairs
+  lp_sample_kernel<<<(S + 255) / 256, 256, 0, s>>>(ks, d_sel, n, d_n, gp, S, sample); note_launch();
+  st = run_sort(ssort, kKeyU64, sample, nullptr, ssorted, srows, S, nullptr, 0, 64, s);
+  if (st != TQP_OK) return st;
+  lp_targets_kernel<<<(S + 255) / 256, 256, 0, s>>>(ssorted, S, lp, tx, ty); note_launch();
+  // 3. training
+  if (epochs > 0) launch_training(model, tx, ty, S, nullptr, cfg->train_cfg, partial, adam, loss, s);
+  // 4. heavy keys, step positions and their directory
+  if (cfg->heavy) {
+    lp_heavy_kernel<<<1, 1024, 0, s>>>(ssorted, S, lp, heavy); note_launch();
+  } else {
+    lp_no_heavy_kernel<<<1, 32, 0, s>>>(lp); note_launch();
+  }
+  if (B > 1) {
+    lp_thresholds_kernel<<<(B - 1 + 255) / 256, 256, 0, s>>>(model, lp, thr); note_launch();
+  }
+  lp_directory_kernel<<<((1 << kDirBits) + 1 + 255) / 256, 256, 0, s>>>(lp, thr, dir); note_launch();
+  // 5. partition: bucket counts, offsets, scatter (heavy rows folded on the fly)
+  PartArgs pa;
+  pa.ks = ks;
+  pa.sel = d_sel;
+  pa.n_max = n;
+  pa.d_n = d_n;
+  pa.gp = gp;
+  pa.lp = lp;
+  pa.thr = thr;
+  pa.dir = dir;
+  pa.heavy = heavy;
+  pa.count = count;
+  pa.cursor = cursor;
+  pa.out_p = lpk;
+  pa.out_row = lrow;
+  pa.heavy_acc = heavy_acc;
+  TQP_CUDA(cudaMemsetAsync(count, 0, (size_t)B * sizeof(unsigned), s));
+  lp_hist_kernel<<<stride_grid(n, 256, 8), 256, 0, s>>>(pa); note_launch();
+  lp_offsets_kernel<<<1, 1024, 0, s>>>(lp, count, off, cursor, d_stats, loss, epochs, light_n); note_launch();
+  lp_heavy_init_kernel<<<(kMaxHeavy * naggs + 255) / 256, 256, 0, s>>>(lp, P, heavy_acc); note_launch();
+  {
+    size_t smem = (size_t)kMaxHeavy * naggs * sizeof(long long);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(lp_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kMaxHeavy * TQP_MAX_AGGS * sizeof(long long)));
+      attr = true;
+    }
+    lp_scatter_kernel<<<stride_grid(n, 256, 2), 256, smem, s>>>(pa, P); note_launch();
+  }
+  // 6. every bucket sorted: on-chip up to the capacity, else by one block in global memory
+  {
+    BucketSortArgs ba;
+    ba.lp = lp;
+    ba.off = off;
+    ba.p = lpk;
+    ba.row = lrow;
+    ba.alt_p = apk;
+    ba.alt_row = arow;
+    ba.queue = queue;
+    size_t smem = (size_t)kLocalCap * (8 + 8 + 4 + 4) + (size_t)kLocalWarps * (kRadix + 1) * 4 + kRadix * 4;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(lp_bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    TQP_CUDA(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
+    int g = num_sms();
+    if (g > B) g = B;
+    lp_bucket_sort_kernel<<<g, kLocalThreads, smem, s>>>(ba); note_launch();
+  }
+  // 7. reduce-by-key over the sorted light rows, merging the heavy keys
+  TQP_CUDA(cudaMemsetAsync(rctrl, 0, (1 + (size_t)rtiles) * sizeof(uint32_t), s));
+  ReduceArgs r;
+  r.keys = lpk;
+  r.rows = lrow;
+  r.n_max = n;
+  r.d_n = light_n;
+  r.plan = gp;
+  r.ks = ks;
+  r.out_aggs = reinterpret_cast<long long*>(d_out_aggs);
+  r.cap = cap;
+  r.d_out_groups = d_out_groups;
+  r.tile_counter = rctrl;
+  r.flags = rctrl + 1;
+  r.agg_payload = ragg;
+  r.pre_payload = rpre;
+  r.num_tiles = (uint32_t)rtiles;
+  r.heavy = heavy;
+  r.d_nheavy = &lp->nheavy;
+  r.heavy_acc = heavy_acc;
+  {
+    auto k = gb_reduce_kernel<unsigned long long, kReduceThreads, kReduceItems>;
+    prof_mark(4, true, s);
+    k<<<persistent_grid(k, kReduceThreads, 0, rtiles), kReduceThreads, 0, s>>>(r, P); note_launch();
+    prof_mark(4, false, s);
+  }
+  gb_heavy_only_kernel<<<(kMaxHeavy + 255) / 256, 256, 0, s>>>(r, naggs); note_launch();
+  if (d_model_out) TQP_CUDA(cudaMemcpyAsync(d_model_out, model, sizeof(tqp_cdf_model), cudaMemcpyDeviceToDevice, s));
   return last_launch();
 }
 
