@@ -60,6 +60,13 @@ def skew(t, cap: int):
                                [(tqp.COUNT, 0), (tqp.SUM, 0), (tqp.MIN, 0), (tqp.MAX, 0)], cap)
 
 
+def skew_learned(t, cap: int, cfg=None):
+    """The skewed group-by through the learned range partitioner (same
+    results as skew())."""
+    return tqp.tqp_groupby_agg_learned([t["key"]], [t["value"]], [[(0, 1, 0)]],
+                                       [(tqp.COUNT, 0), (tqp.SUM, 0), (tqp.MIN, 0), (tqp.MAX, 0)], cap, cfg=cfg)
+
+
 def batched_one(fact, dim, cap: int = 64):
     """SELECT grp, SUM(v), COUNT(*) FROM fact JOIN dim ON fk = key
     WHERE day < 1278 GROUP BY grp."""

@@ -63,6 +63,31 @@ class ValRef(ctypes.Structure):
     _fields_ = [("src", ctypes.c_int32), ("col", ctypes.c_int32)]
 
 
+H = 64  # TQP_CDF_HIDDEN
+
+
+class CdfModel(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_float * H), ("b", ctypes.c_float * H), ("a", ctypes.c_float * H),
+                ("c", ctypes.c_float), ("shift", ctypes.c_int32), ("inv", ctypes.c_float), ("pad_", ctypes.c_int32),
+                ("umin", ctypes.c_uint64)]
+
+
+class TrainCfg(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("pad_", ctypes.c_int32)]
+
+
+class LearnedCfg(ctypes.Structure):
+    _fields_ = [("sample", ctypes.c_int32), ("buckets", ctypes.c_int32), ("train", ctypes.c_int32),
+                ("heavy", ctypes.c_int32), ("train_cfg", TrainCfg)]
+
+
+class LearnedStats(ctypes.Structure):
+    _fields_ = [("buckets", ctypes.c_int64), ("heavy_keys", ctypes.c_int64), ("light_rows", ctypes.c_int64),
+                ("max_bucket", ctypes.c_int64), ("over_capacity", ctypes.c_int64), ("nonempty", ctypes.c_int64),
+                ("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float)]
+
+
 _vp, _i64, _sz, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t, ctypes.c_int
 _P = ctypes.POINTER
 
@@ -74,6 +99,11 @@ _lib.tqp_groupby_agg.argtypes = [_P(Col), _int, _P(Col), _int, _P(Expr), _int, _
                                  _P(_vp), _vp, _i64, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_star_agg.argtypes = [_P(Col), _int, _i64, _P(Pred), _int, _P(_int), _P(Dim), _int, _P(ValRef), _int,
                               _P(Expr), _int, _P(Agg), _int, _P(_vp), _vp, _i64, _vp, _vp, _P(_sz), _vp]
+_lib.tqp_cdf_forward.argtypes = [_vp, _vp, _i64, _vp, _vp, _int, _vp]
+_lib.tqp_cdf_backward.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
+_lib.tqp_cdf_train.argtypes = [_vp, _vp, _i64, _vp, _P(TrainCfg), _vp, _vp, _P(_sz), _vp]
+_lib.tqp_groupby_agg_learned.argtypes = [_P(Col), _int, _P(Col), _int, _P(Expr), _int, _P(Agg), _int, _vp, _i64,
+                                         _vp, _P(_vp), _vp, _i64, _vp, _P(LearnedCfg), _vp, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_status_poll.argtypes = [_vp]
 _lib.tqp_debug_set_spin_limit.argtypes = [_i64]
 _lib.tqp_debug_inject_unpublished_tile.argtypes = [_i64]
@@ -82,7 +112,8 @@ _lib.tqp_debug_launch_count.restype = ctypes.c_int64
 _lib.tqp_debug_launch_count.argtypes = []
 _lib.tqp_profile_events.argtypes = [_int, _vp, _vp]
 for _f in ("tqp_filter", "tqp_gather", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
-           "tqp_status_poll", "tqp_profile_events", "tqp_debug_set_spin_limit", "tqp_debug_inject_unpublished_tile"):
+           "tqp_status_poll", "tqp_profile_events", "tqp_cdf_forward", "tqp_cdf_backward", "tqp_cdf_train",
+           "tqp_groupby_agg_learned", "tqp_debug_set_spin_limit", "tqp_debug_inject_unpublished_tile"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -280,6 +311,83 @@ def tqp_star_agg(fact_cols, fact_preds, fk_cols, dims, vals, exprs, aggs, cap, s
                 len(dims), vr, len(vals), _exprs(exprs), len(exprs), _aggs(aggs), len(aggs), kp, _ptr(out_aggs), cap,
                 _ptr(G)], dev, stream)
     return out_keys, out_aggs, G
+
+
+# ------------------------------------------------------------------ learned partitioner
+
+def model_to_device(w, b, a, c, shift=0, inv=1.0, umin=0, device="cuda"):
+    m = CdfModel()
+    for i in range(H):
+        m.w[i], m.b[i], m.a[i] = float(w[i]), float(b[i]), float(a[i])
+    m.c, m.shift, m.inv, m.umin = float(c), int(shift), float(inv), int(umin)
+    return torch.frombuffer(bytearray(bytes(m)), dtype=torch.uint8).to(device)
+
+
+def model_from_device(t):
+    m = CdfModel.from_buffer_copy(t.cpu().numpy().tobytes())
+    return {"w": list(m.w), "b": list(m.b), "a": list(m.a), "c": m.c, "shift": m.shift, "inv": m.inv, "umin": m.umin}
+
+
+def empty_model(device="cuda"):
+    return torch.zeros(ctypes.sizeof(CdfModel), dtype=torch.uint8, device=device)
+
+
+def tqp_cdf_forward(model, x, B=0, stream=None):
+    n = x.numel()
+    F = torch.empty(max(n, 1), dtype=torch.float32, device=x.device)
+    bk = torch.empty(max(n, 1), dtype=torch.int32, device=x.device) if B else None
+    _check(_lib.tqp_cdf_forward(_ptr(model), _ptr(x), n, _ptr(F), _ptr(bk), B, _stream(stream)), "tqp_cdf_forward")
+    return F[:n], (bk[:n] if B else None)
+
+
+def tqp_cdf_backward(model, x, y, stream=None):
+    """[dL/dw (H), dL/db (H), dL/da (H), dL/dc, L] as a float32 device tensor."""
+    g = torch.empty(3 * H + 2, dtype=torch.float32, device=x.device)
+    _two_phase(_lib.tqp_cdf_backward, "tqp_cdf_backward", [_ptr(model), _ptr(x), _ptr(y), x.numel(), _ptr(g)],
+               x.device, stream)
+    return g
+
+
+def train_cfg(epochs=200, lr=5e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    return TrainCfg(epochs, lr, beta1, beta2, eps, 0)
+
+
+def tqp_cdf_train(x, y, model, cfg=None, stream=None):
+    """Trains `model` (device bytes) in place; returns the per-step loss."""
+    cfg = cfg or train_cfg()
+    loss = torch.empty(max(cfg.epochs, 1), dtype=torch.float32, device=x.device)
+    _two_phase(_lib.tqp_cdf_train, "tqp_cdf_train",
+               [_ptr(x), _ptr(y), x.numel(), _ptr(model), ctypes.byref(cfg), _ptr(loss)], x.device, stream)
+    return loss[:cfg.epochs]
+
+
+def learned_cfg(sample=65536, buckets=0, train=True, heavy=True, tcfg=None):
+    return LearnedCfg(sample, buckets, int(train), int(heavy), tcfg or train_cfg())
+
+
+def tqp_groupby_agg_learned(keys, vals, exprs, aggs, cap, cfg=None, sel=None, n=None, d_n=None, stream=None):
+    """The group-by of tqp_groupby_agg through the learned range partitioner.
+    Returns (key columns, aggs [cap, naggs], device G, trained model bytes, stats bytes)."""
+    dev = keys[0].device
+    cfg = cfg or learned_cfg()
+    if n is None:
+        n = sel.numel() if sel is not None else keys[0].numel()
+    out_keys = [torch.empty(max(cap, 1), dtype=k.dtype, device=dev) for k in keys]
+    out_aggs = torch.empty((max(cap, 1), len(aggs)), dtype=torch.int64, device=dev)
+    G = torch.empty(1, dtype=torch.int64, device=dev)
+    model = empty_model(dev)
+    stats = torch.zeros(ctypes.sizeof(LearnedStats), dtype=torch.uint8, device=dev)
+    kp = (ctypes.c_void_p * len(keys))(*[k.data_ptr() for k in out_keys])
+    _two_phase(_lib.tqp_groupby_agg_learned, "tqp_groupby_agg_learned",
+               [_cols(keys), len(keys), _cols(vals), len(vals), _exprs(exprs), len(exprs), _aggs(aggs), len(aggs),
+                _ptr(sel), n, _ptr(d_n), kp, _ptr(out_aggs), cap, _ptr(G), ctypes.byref(cfg), _ptr(model),
+                _ptr(stats)], dev, stream)
+    return out_keys, out_aggs, G, model, stats
+
+
+def stats_from_device(t):
+    st = LearnedStats.from_buffer_copy(t.cpu().numpy().tobytes())
+    return {f: getattr(st, f) for f, _ in LearnedStats._fields_}
 
 
 def tqp_status_poll(stream=None) -> int:
