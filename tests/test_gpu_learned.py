@@ -1,0 +1,171 @@
+"""GPU parity of the learned range partitioner: the network's forward pass
+(bit-exact against the oracle's float32 evaluation in the same order), its
+gradients (against the oracle's float64 analytic gradients), the Adam step,
+and the learned group-by (bit-identical to the oracle and to the plain radix
+path for every configuration, including the global-memory fallback)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from oracle import pipelines as pl
+from paper_2209_04579_b300 import datagen as dg
+
+pytestmark = pytest.mark.gpu
+H = 64
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2209_04579_b300 import build
+    build.build()
+    from paper_2209_04579_b300 import tqp
+    return tqp
+
+
+def rand_model(rng, H=H):
+    w = rng.uniform(0.5, 80, H).astype(np.float32)
+    b = rng.uniform(-60, 1, H).astype(np.float32)
+    a = rng.uniform(0, 2.0 / H, H).astype(np.float32)
+    c = np.float32(rng.uniform(-0.05, 0.05))
+    return w, b, a, c
+
+
+def test_forward_bit_exact_and_buckets(T):
+    rng = np.random.default_rng(1)
+    w, b, a, c = rand_model(rng)
+    x = rng.uniform(-0.1, 1.1, 300_001).astype(np.float32)
+    m = T.model_to_device(w, b, a, c)
+    F, bk = T.tqp_cdf_forward(m, torch.from_numpy(x).cuda(), B=4096)
+    want = orc.cdf_forward_f32(w, b, a, float(c), x)
+    assert np.array_equal(F.cpu().numpy().view(np.uint32), want.view(np.uint32))
+    assert np.array_equal(bk.cpu().numpy(), orc.cdf_bucket(want, 4096))
+
+
+def test_backward_vs_float64(T):
+    rng = np.random.default_rng(2)
+    for n in (1000, 65536, 200_003):
+        w, b, a, c = rand_model(rng)
+        x = rng.uniform(0, 1, n).astype(np.float32)
+        y = np.sort(rng.uniform(0, 1, n)).astype(np.float32)
+        g = T.tqp_cdf_backward(T.model_to_device(w, b, a, c), torch.from_numpy(x).cuda(),
+                               torch.from_numpy(y).cuda()).cpu().numpy().astype(np.float64)
+        loss, gw, gb, ga, gc = orc.cdf_grad_f64(w.astype(np.float64), b.astype(np.float64), a.astype(np.float64),
+                                                float(c), x.astype(np.float64), y.astype(np.float64))
+        want = np.concatenate([gw, gb, ga, [gc]])
+        scale = np.max(np.abs(want))
+        # float32 sums over n samples: relative error well under 1e-4 of the largest component
+        assert np.all(np.abs(g[:3 * H + 1] - want) <= 1e-4 * scale + 1e-4 * np.abs(want)), n
+        assert abs(g[3 * H + 1] - loss) <= 1e-4 * loss
+
+
+def test_adam_step_vs_float64(T):
+    rng = np.random.default_rng(3)
+    w, b, a, c = rand_model(rng)
+    x = rng.uniform(0, 1, 8192).astype(np.float32)
+    y = np.sort(rng.uniform(0, 1, 8192)).astype(np.float32)
+    m = T.model_to_device(w, b, a, c)
+    loss = T.tqp_cdf_train(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), m, T.train_cfg(epochs=1, lr=1e-2))
+    got = T.model_from_device(m)
+    p = np.concatenate([w, b, a, [c]]).astype(np.float64)
+    l0, gw, gb, ga, gc = orc.cdf_grad_f64(w.astype(np.float64), b.astype(np.float64), a.astype(np.float64), float(c),
+                                          x.astype(np.float64), y.astype(np.float64))
+    nonneg = np.r_[np.ones(H), np.zeros(H), np.ones(H), [0]].astype(np.int32)
+    orc.adam_step_f64(p, np.concatenate([gw, gb, ga, [gc]]), np.zeros(3 * H + 1), np.zeros(3 * H + 1), nonneg, 1,
+                      lr=1e-2)
+    gp = np.concatenate([got["w"], got["b"], got["a"], [got["c"]]])
+    # first Adam step moves each parameter by about lr * sign(g); float32 vs float64 agree to ~1e-6
+    assert np.max(np.abs(gp - p)) < 2e-5 * max(1.0, np.max(np.abs(p)))
+    assert abs(loss.cpu().numpy()[0] - l0) <= 1e-4 * l0
+    assert min(got["w"]) >= 0 and min(got["a"]) >= 0
+
+
+def test_training_reduces_loss_and_stays_monotone(T):
+    z = dg.zipf_table(dg.ZIPF_S, dg.ZIPF_N)
+    keys = np.sort(dg.make_table(dg.skew_groupby(), 65536, zipf=z)["key"])
+    u = keys.view(np.uint64) ^ np.uint64(1 << 63)
+    umin, span = int(u[0]), int(u[-1] - u[0])
+    shift = max(0, span.bit_length() - 24)
+    inv = float(np.float32(1.0) / np.float32(span >> shift))
+    x = orc.cdf_normalize(keys, umin, shift, inv)
+    y = orc.cdf_targets(keys).astype(np.float32)
+    j = np.arange(H)
+    m = T.model_to_device(np.full(H, float(H)), -j.astype(np.float64), np.full(H, 1.0 / H), 0.0)
+    loss = T.tqp_cdf_train(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), m, T.train_cfg(epochs=200))
+    loss = loss.cpu().numpy()
+    assert loss[-1] < 0.2 * loss[0]
+    F, _ = T.tqp_cdf_forward(m, torch.from_numpy(np.linspace(0, 1, 100_001, dtype=np.float32)).cuda())
+    assert np.all(np.diff(F.cpu().numpy()) >= 0)
+
+
+def skew_case(n, master=20220904):
+    z = dg.zipf_table(dg.ZIPF_S, dg.ZIPF_N)
+    rec = dg.skew_groupby(master=master)
+    return dg.make_table(rec, n, zipf=z), rec, z
+
+
+def compare(got, want):
+    ok, oa, g = got[:3]
+    wk, wa, _ = want
+    G = wa.shape[0]
+    assert int(g.item()) == G
+    for i in range(len(ok)):
+        assert np.array_equal(ok[i].cpu().numpy()[:G].astype(np.int64), wk[i])
+    assert np.array_equal(oa.cpu().numpy()[:G], wa)
+
+
+@pytest.mark.parametrize("n", [1, 1000, 70_001, 3_000_000])
+@pytest.mark.parametrize("train,heavy,buckets", [(1, 1, 0), (0, 1, 0), (1, 0, 0), (1, 1, 2), (0, 0, 16)])
+def test_learned_groupby_parity(T, n, train, heavy, buckets):
+    from paper_2209_04579_b300 import datagen_device as gd
+    from paper_2209_04579_b300 import queries as Q
+    host, rec, z = skew_case(n)
+    want = pl.skew(host)
+    dev = gd.make_table(rec, n, zipf=torch.from_numpy(z).cuda())
+    cfg = T.learned_cfg(sample=4096 if n < 100_000 else 65536, buckets=buckets, train=bool(train),
+                        heavy=bool(heavy), tcfg=T.train_cfg(epochs=50))
+    got = Q.skew_learned(dev, cap=max(n, 1), cfg=cfg)
+    compare(got, want)
+    assert T.tqp_status_poll() == T.OK
+    compare(Q.skew(dev, cap=max(n, 1)), want)     # the plain radix path agrees
+
+
+def test_learned_groupby_general_keys(T):
+    """Two key columns of mixed widths, a selection, several aggregates."""
+    rng = np.random.default_rng(5)
+    n = 500_000
+    k1 = rng.integers(-30_000, 30_000, n).astype(np.int16)
+    k2 = (rng.zipf(1.3, n) % 1000).astype(np.int32) - 500
+    v = rng.integers(-10**9, 10**9, n).astype(np.int64)
+    sel = np.sort(rng.choice(n, n // 3, replace=False)).astype(np.int32)
+    ex = [[(0, 1, 0)], [(0, 3, -7), (0, 1, 1)]]
+    ag = [(orc.COUNT, 0), (orc.SUM, 0), (orc.MIN, 1), (orc.MAX, 0), (orc.SUM, 1)]
+    want = orc.groupby_agg([k1, k2], [v], ex, ag, sel=sel)
+    cu = lambda a: torch.from_numpy(a).cuda()
+    got = T.tqp_groupby_agg_learned([cu(k1), cu(k2)], [cu(v)], ex, ag, n, cfg=T.learned_cfg(sample=16384),
+                                    sel=cu(sel))
+    compare(got, want)
+    assert T.tqp_status_poll() == T.OK
+
+
+def test_trained_network_gains_over_identity(T):
+    """On keys whose distribution is far from uniform in key space (a
+    log-normal spread), the trained network balances the buckets; the
+    identity CDF (the method without a trained network) leaves a few buckets
+    holding most rows, which the global-memory fallback must sort."""
+    rng = np.random.default_rng(7)
+    n = 4_000_000
+    keys = np.exp(rng.normal(12, 1.5, n)).astype(np.int64)
+    vals = rng.integers(0, 2**31, n).astype(np.int64)
+    want = orc.groupby_agg([keys], [vals], [[(0, 1, 0)]], [(orc.COUNT, 0), (orc.SUM, 0)])
+    cu = lambda a: torch.from_numpy(a).cuda()
+    res = {}
+    for train in (True, False):
+        cfg = T.learned_cfg(sample=65536, buckets=4096, train=train, heavy=True, tcfg=T.train_cfg(epochs=200))
+        got = T.tqp_groupby_agg_learned([cu(keys)], [cu(vals)], [[(0, 1, 0)]], [(orc.COUNT, 0), (orc.SUM, 0)], n,
+                                        cfg=cfg)
+        compare(got, want)
+        res[train] = T.stats_from_device(got[4])
+    assert res[True]["max_bucket"] * 4 < res[False]["max_bucket"]
+    assert res[True]["over_capacity"] <= res[False]["over_capacity"]
+    assert res[True]["loss_last"] < res[True]["loss_first"]
