@@ -276,6 +276,9 @@ def run_ours(args, world, rank, local):
 
     # capture one step into a CUDA graph, with the dominant kernel bracketed by events
     ev_k0, ev_k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev_k0.record()  # torch creates the CUDA event at its first record
+    ev_k1.record()
+    torch.cuda.synchronize()
     tqp.tqp_profile_events(W.prof_class, ev_k0, ev_k1)
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()

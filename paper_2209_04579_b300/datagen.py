@@ -117,8 +117,11 @@ def _feistel(x, seed: int, half: int, mask: int):
 
 def perm(i, n: int, seed: int):
     """Seeded bijection of [0, n): Feistel network plus cycle walking."""
+    i = np.asarray(i, dtype=np.uint64)
+    if i.size and int(i.max()) >= n:
+        raise ValueError("perm is defined on [0, n) only")
     half, mask = _feistel_params(n)
-    y = _feistel(np.asarray(i, dtype=np.uint64), seed, half, mask)
+    y = _feistel(i, seed, half, mask)
     todo = y >= _U64(n)
     while np.any(todo):
         y[todo] = _feistel(y[todo], seed, half, mask)

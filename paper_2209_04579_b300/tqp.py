@@ -410,7 +410,11 @@ def tqp_debug_launch_count() -> int:
 
 
 def tqp_profile_events(kernel_class: int, start=None, stop=None):
-    """Record torch.cuda.Event `start` / `stop` around kernels of one class."""
+    """Record torch.cuda.Event `start` / `stop` around kernels of one class
+    (each event must have been recorded once, which creates it)."""
+    for e in (start, stop):
+        if e is not None and not e.cuda_event:
+            raise ValueError("record the event once before handing it to the library")
     sp = ctypes.c_void_p(start.cuda_event if start is not None else 0)
     ep = ctypes.c_void_p(stop.cuda_event if stop is not None else 0)
     _check(_lib.tqp_profile_events(kernel_class, sp, ep), "tqp_profile_events")
