@@ -329,6 +329,63 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
                                    tqp_cdf_model* d_model_out, tqp_learned_stats* d_stats, void* ws,
                                    size_t* ws_bytes, tqp_stream_t stream);
 
+/* ========================================================================
+ * Batched instances: many independent join + filter + group-by problems of
+ * uneven size (the Q14 shape of Section 2.3, one query per problem) in one
+ * sequence of persistent launches instead of one call per problem.
+ *
+ * Every problem has the same query shape (tqp_batch_shape):
+ *   SELECT dim.group, aggs FROM fact JOIN dim ON fact.fk = dim.key
+ *   WHERE fact predicates GROUP BY dim.group
+ * with its own columns and sizes (tqp_problem).  All dimensions are sorted
+ * by (problem, key) in one radix sort and grouped by (problem, group) in a
+ * second; one persistent probe kernel pulls fact tiles of all problems from
+ * one work queue (a tile never spans two problems) and folds each row into
+ * its problem's group slots in shared memory; a final kernel writes each
+ * problem's groups in ascending group order.  Dimension keys must be unique
+ * within a problem (TQP_ERR_UNSUPPORTED on the device otherwise).
+ * ====================================================================== */
+#define TQP_BATCH_MAX_COLS 4
+
+typedef struct {
+  int32_t nfact_cols;
+  int32_t fact_dtype[TQP_BATCH_MAX_COLS]; /* dtypes of the fact columns */
+  int32_t fk_col;                         /* fact column holding the foreign key */
+  int32_t key_dtype;                      /* TQP_I32 (dimension key and fact fk) */
+  int32_t group_dtype;                    /* TQP_I8 / TQP_I16 / TQP_I32 */
+  int32_t npred;
+  tqp_pred preds[TQP_MAX_PREDS];          /* over fact columns; literals shared */
+  int32_t nexprs;
+  tqp_expr exprs[TQP_MAX_EXPRS];          /* terms index fact columns */
+  int32_t naggs;
+  tqp_agg aggs[TQP_MAX_AGGS];
+} tqp_batch_shape;
+
+typedef struct {
+  int64_t n_fact;
+  const void* fact_cols[TQP_BATCH_MAX_COLS]; /* device */
+  int64_t n_dim;
+  const void* dim_key;                       /* device, unique keys */
+  const void* dim_group;                     /* device */
+  void* out_keys;                            /* device, group_dtype, capacity cap */
+  int64_t* out_aggs;                         /* device, [cap][naggs] */
+  int64_t cap;
+  int64_t* d_out_groups;                     /* device */
+} tqp_problem;
+
+typedef struct {
+  int32_t probe_items; /* fact rows per thread per probe tile: 4, 8 or 16 (0 = 8) */
+  int32_t pad_;
+} tqp_batch_cfg;
+
+/* tqp_star_agg_batched: runs all nprob problems (host array of
+ * descriptors; device pointers inside).  Results per problem as for
+ * tqp_star_agg.  Limits: nprob <= 65536, sum of n_dim < 2^30, each
+ * problem's distinct group values <= 4096. */
+tqp_status tqp_star_agg_batched(const tqp_batch_shape* shape, const tqp_problem* probs, int nprob,
+                                const tqp_batch_cfg* cfg, void* ws, size_t* ws_bytes,
+                                tqp_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Device status and test hooks.
  * tqp_status_poll: synchronises `stream`, returns the current device's status
