@@ -295,6 +295,9 @@ typedef struct {
   int32_t train;   /* 1 = train the network; 0 = keep the identity CDF F(x) = x */
   int32_t heavy;   /* 1 = aggregate the sample's frequent keys directly */
   tqp_train_cfg train_cfg;
+  int32_t init;    /* network before training: 0 = identity CDF, 1 = knots at the
+                      sample's 1/H quantiles (the piecewise-linear empirical CDF) */
+  int32_t pad_;
 } tqp_learned_cfg;
 
 typedef struct {          /* written to device memory by the learned group-by */
@@ -304,6 +307,7 @@ typedef struct {          /* written to device memory by the learned group-by */
   int64_t max_bucket;     /* largest bucket (rows) */
   int64_t over_capacity;  /* buckets sorted by the global-memory fallback */
   int64_t nonempty;       /* non-empty buckets */
+  int64_t over_capacity_rows; /* rows in buckets sorted by the fallback */
   float loss_first;       /* training loss before the first / the last step */
   float loss_last;
 } tqp_learned_stats;

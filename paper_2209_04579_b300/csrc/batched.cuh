@@ -1,0 +1,350 @@
+// Batched instances of the join + filter + group-by query: all problems'
+// dimension tables are encoded as (problem, key) and (problem, group) words
+// and sorted together; one persistent probe kernel pulls fact tiles of every
+// problem from one atomic work queue; one block per problem writes its
+// groups.  The per-problem descriptors reach the device through kernel
+// parameters (an upload kernel), so the whole sequence can be captured in a
+// CUDA graph and replayed.
+#pragma once
+
+#include "common.cuh"
+#include "join.cuh"
+#include "sort.cuh"
+
+namespace tqp {
+
+constexpr int kBatchSmemWords = 6144;  // shared accumulator words per probe block
+constexpr int kUploadChunk = 96;
+
+struct BatchProb {
+  long long n_fact;
+  const void* fact[TQP_BATCH_MAX_COLS];
+  long long n_dim;
+  const void* key;
+  const void* group;
+  void* out_keys;
+  long long* out_aggs;
+  long long cap;
+  long long* d_out_groups;
+  long long dim_off;   // first row in the concatenated dimension arrays
+  long long tile_off;  // first global probe tile
+  long long slot_off;  // first accumulator slot
+};
+
+struct UploadChunk {
+  int first, count;
+  BatchProb p[kUploadChunk];
+};
+
+__global__ void batch_upload_kernel(UploadChunk c, BatchProb* dst) {
+  int i = threadIdx.x;
+  if (i < c.count) dst[c.first + i] = c.p[i];
+}
+
+__global__ void batch_offsets_kernel(UploadChunk c, long long* dim_off, long long* tile_off) {
+  int i = threadIdx.x;
+  if (i < c.count) {
+    dim_off[c.first + i] = c.p[i].dim_off;
+    tile_off[c.first + i] = c.p[i].tile_off;
+  }
+}
+
+struct BatchShape {
+  int nfact_cols;
+  int fact_dt[TQP_BATCH_MAX_COLS];
+  int fk_col;
+  int group_dt;
+  int npred;
+  int pcol[TQP_MAX_PREDS];
+  int pop[TQP_MAX_PREDS];
+  long long plit[TQP_MAX_PREDS];
+  int nexprs;
+  int nterms[TQP_MAX_EXPRS];
+  int tcol[TQP_MAX_EXPRS][3];
+  long long tmul[TQP_MAX_EXPRS][3];
+  long long tadd[TQP_MAX_EXPRS][3];
+  int naggs;
+  int op[TQP_MAX_AGGS];
+  int expr[TQP_MAX_AGGS];
+};
+
+__device__ __forceinline__ int find_problem(const long long* off, int nprob, long long x) {
+  // last problem whose offset is <= x
+  int lo = 0, hi = nprob;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ unsigned group_bits(int dt, long long v) {
+  switch (dt) {
+    case TQP_I8: return (unsigned)(uint8_t)v ^ 0x80u;
+    case TQP_I16: return (unsigned)(uint16_t)v ^ 0x8000u;
+    default: return (unsigned)v ^ 0x80000000u;
+  }
+}
+
+__device__ __forceinline__ long long group_value(int dt, unsigned b) {
+  switch (dt) {
+    case TQP_I8: return (int8_t)(uint8_t)(b ^ 0x80u);
+    case TQP_I16: return (int16_t)(uint16_t)(b ^ 0x8000u);
+    default: return (int32_t)(b ^ 0x80000000u);
+  }
+}
+
+// Concatenated dimension rows -> (problem << 32 | key bits) and
+// (problem << 32 | group bits), payload = row within the problem.
+__global__ void batch_dim_encode_kernel(const BatchProb* probs, const long long* dim_off, int nprob, long long total,
+                                        int group_dt, unsigned long long* ckey, int32_t* crow,
+                                        unsigned long long* cgrp, int32_t* grow) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += stride) {
+    int p = find_problem(dim_off, nprob, r);
+    long long j = r - dim_off[p];
+    const BatchProb& P = probs[p];
+    unsigned kb = (unsigned)static_cast<const int32_t*>(P.key)[j] ^ 0x80000000u;
+    unsigned gb = group_bits(group_dt, load_as_i64(P.group, group_dt, j));
+    ckey[r] = ((unsigned long long)p << 32) | kb;
+    cgrp[r] = ((unsigned long long)p << 32) | gb;
+    crow[r] = (int32_t)j;
+    grow[r] = (int32_t)j;
+  }
+}
+
+// Segment id of every position of the sorted (problem, group) words, and
+// the group value at each segment head (single-pass look-back scan).
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) batch_seg_kernel(const unsigned long long* sorted, long long n,
+                                                            int group_dt, int32_t* seg, long long* gval,
+                                                            unsigned long long* status, uint32_t* counter,
+                                                            uint32_t num_tiles) {
+  constexpr int TILE = THREADS * ITEMS;
+  __shared__ int s_scan[33];
+  __shared__ uint32_t s_tile;
+  __shared__ long long s_excl;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= num_tiles) break;
+    const long long base = (long long)tile * TILE + (long long)threadIdx.x * ITEMS;
+    uint32_t head = 0;
+    unsigned long long prev = (base > 0 && base < n) ? sorted[base - 1] : 0ull;
+    unsigned long long key[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      long long p = base + k;
+      key[k] = p < n ? sorted[p] : 0ull;
+      if (p < n && (p == 0 || key[k] != (k ? key[k - 1] : prev))) head |= 1u << k;
+    }
+    int total;
+    int off = block_exclusive_sum<THREADS>(__popc(head), s_scan, &total);
+    if (warp == 0) {
+      long long e = lookback_exclusive(status, tile, total);
+      if (lane == 0) s_excl = e;
+    }
+    __syncthreads();
+    const long long excl = s_excl;
+    if (excl >= 0) {
+      long long r = excl + off - 1;
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        long long p = base + k;
+        if (p < n) {
+          if (head & (1u << k)) {
+            ++r;
+            gval[r] = group_value(group_dt, (unsigned)key[k]);
+          }
+          seg[p] = (int32_t)r;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Rank of each dimension row's group within its problem; group count per problem.
+__global__ void batch_rank_kernel(const BatchProb* probs, const long long* dim_off, int nprob, long long total,
+                                  const unsigned long long* sgrp, const int32_t* sgrow, const int32_t* seg,
+                                  int32_t* rank_of_row, long long* G, long long* first_seg) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x; pos < total; pos += stride) {
+    int p = (int)(sgrp[pos] >> 32);
+    long long d0 = dim_off[p];
+    int s0 = seg[d0];
+    rank_of_row[d0 + sgrow[pos]] = seg[pos] - s0;
+    if (pos == d0 + probs[p].n_dim - 1) {
+      G[p] = (long long)(seg[pos] - s0) + 1;
+      first_seg[p] = s0;
+    }
+  }
+}
+
+__global__ void batch_empty_groups_kernel(const BatchProb* probs, int nprob, long long* G) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nprob && probs[p].n_dim == 0) G[p] = 0;
+}
+
+// Key-sorted positions: local key (int32) and group rank; uniqueness check.
+__global__ void batch_pregather_kernel(const unsigned long long* skey, const int32_t* srow, const long long* dim_off,
+                                       long long total, const int32_t* rank_of_row, int32_t* key32,
+                                       int32_t* rank_sorted, int* flag) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x; pos < total; pos += stride) {
+    unsigned long long k = skey[pos];
+    int p = (int)(k >> 32);
+    key32[pos] = (int32_t)((unsigned)k ^ 0x80000000u);
+    rank_sorted[pos] = rank_of_row[dim_off[p] + srow[pos]];
+    if (pos > 0 && skey[pos - 1] == k) {
+      if (atomicExch(flag, 1) == 0) raise_status(TQP_ERR_UNSUPPORTED);
+    }
+  }
+}
+
+__global__ void batch_init_acc_kernel(const BatchShape S, long long* acc, long long nslots) {
+  const int nacc = S.naggs + 1;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nslots * nacc; i += stride) {
+    int q = (int)(i % nacc);
+    acc[i] = q < S.naggs ? agg_identity(S.op[q]) : 0;
+  }
+}
+
+__device__ __forceinline__ void batch_fold(long long* slot, const BatchShape& S, const long long* ev) {
+#pragma unroll
+  for (int q = 0; q < TQP_MAX_AGGS; ++q) {
+    if (q < S.naggs) {
+      long long x = S.op[q] == TQP_COUNT ? 1 : ev[S.expr[q]];
+      switch (S.op[q]) {
+        case TQP_MIN: atomicMin(slot + q, x); break;
+        case TQP_MAX: atomicMax(slot + q, x); break;
+        default: atomicAdd(reinterpret_cast<unsigned long long*>(slot + q), (unsigned long long)x); break;
+      }
+    }
+  }
+  atomicAdd(reinterpret_cast<unsigned long long*>(slot + S.naggs), 1ull);
+}
+
+struct BatchProbeArgs {
+  const BatchProb* probs;
+  const long long* tile_off;
+  int nprob;
+  long long num_tiles;
+  const int32_t* key32;
+  const int32_t* rank_sorted;
+  const long long* G;
+  const int* flag;
+  long long* acc;
+  uint32_t* queue;
+};
+
+template <int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, BatchShape S) {
+  constexpr int TILE = THREADS * ITEMS;
+  __shared__ long long s_acc[kBatchSmemWords];
+  __shared__ uint32_t s_tile;
+  if (*a.flag) return;
+  const int nacc = S.naggs + 1;
+  while (true) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const long long t = s_tile;
+    __syncthreads();
+    if (t >= a.num_tiles) break;
+    const int p = find_problem(a.tile_off, a.nprob, t);
+    const BatchProb& P = a.probs[p];
+    const long long r0 = (t - a.tile_off[p]) * TILE;
+    const long long Gp = a.G[p];
+    const bool shared = Gp * nacc <= kBatchSmemWords;
+    long long* gacc = a.acc + P.slot_off * nacc;
+    if (shared) {
+      for (int i = threadIdx.x; i < Gp * nacc; i += THREADS) {
+        int q = i % nacc;
+        s_acc[i] = q < S.naggs ? agg_identity(S.op[q]) : 0;
+      }
+      __syncthreads();
+    }
+    const int32_t* keys = a.key32 + P.dim_off;
+    const int32_t* ranks = a.rank_sorted + P.dim_off;
+    const long long nd = P.n_dim;
+#pragma unroll 1
+    for (int k = 0; k < ITEMS; ++k) {
+      const long long row = r0 + (long long)k * THREADS + threadIdx.x;
+      if (row >= P.n_fact) continue;
+      bool keep = true;
+      for (int q = 0; q < S.npred; ++q)
+        keep = keep && compare(load_as_i64(P.fact[S.pcol[q]], S.fact_dt[S.pcol[q]], row), S.pop[q], S.plit[q]);
+      if (!keep) continue;
+      int32_t x = static_cast<const int32_t*>(P.fact[S.fk_col])[row];
+      int64_t l = lower_bound_dev(keys, nd, x);
+      if (l >= nd || keys[l] != x) continue;
+      long long g = ranks[l];
+      long long ev[TQP_MAX_EXPRS];
+#pragma unroll
+      for (int e = 0; e < TQP_MAX_EXPRS; ++e) {
+        if (e < S.nexprs) {
+          unsigned long long v = 1;
+          for (int tt = 0; tt < S.nterms[e]; ++tt) {
+            int c = S.tcol[e][tt];
+            long long xv = load_as_i64(P.fact[c], S.fact_dt[c], row);
+            v *= (unsigned long long)S.tmul[e][tt] * (unsigned long long)xv + (unsigned long long)S.tadd[e][tt];
+          }
+          ev[e] = (long long)v;
+        }
+      }
+      batch_fold(shared ? s_acc + g * nacc : gacc + g * nacc, S, ev);
+    }
+    if (shared) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < Gp * nacc; i += THREADS) {
+        int q = i % nacc;
+        long long v = s_acc[i];
+        long long id = q < S.naggs ? agg_identity(S.op[q]) : 0;
+        if (v == id) continue;
+        if (q < S.naggs && S.op[q] == TQP_MIN) atomicMin(&gacc[i], v);
+        else if (q < S.naggs && S.op[q] == TQP_MAX) atomicMax(&gacc[i], v);
+        else atomicAdd(reinterpret_cast<unsigned long long*>(&gacc[i]), (unsigned long long)v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One block per problem: non-empty groups in rank (= group value) order.
+__global__ void __launch_bounds__(256) batch_compact_kernel(const BatchProb* probs, const long long* G,
+                                                            const long long* first_seg, const long long* gval,
+                                                            const long long* acc, int naggs, int group_dt,
+                                                            const int* flag) {
+  __shared__ int s_scan[33];
+  __shared__ long long s_base;
+  const int p = blockIdx.x;
+  const BatchProb& P = probs[p];
+  const long long Gp = *flag ? 0 : G[p];
+  const int nacc = naggs + 1;
+  const long long* pacc = acc + P.slot_off * nacc;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  for (long long g0 = 0; g0 < Gp; g0 += 256) {
+    long long g = g0 + threadIdx.x;
+    int live = (g < Gp && pacc[g * nacc + naggs] > 0) ? 1 : 0;
+    int total;
+    int off = block_exclusive_sum<256>(live, s_scan, &total);
+    long long pos = s_base + off;
+    if (live && pos < P.cap) {
+      store_from_i64(P.out_keys, group_dt, pos, gval[first_seg[p] + g]);
+      for (int q = 0; q < naggs; ++q) P.out_aggs[pos * naggs + q] = pacc[g * nacc + q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_base += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *P.d_out_groups = s_base;
+    if (s_base > P.cap) raise_status(TQP_ERR_CAPACITY);
+  }
+}
+
+}  // namespace tqp

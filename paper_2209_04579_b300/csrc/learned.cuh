@@ -327,6 +327,25 @@ __global__ void __launch_bounds__(1024) lp_heavy_kernel(const unsigned long long
   if (threadIdx.x == 0) lp->nheavy = s_base;
 }
 
+// Knots at the sample's 1/H quantiles: unit j ramps from x_(jS/H) to
+// x_((j+1)S/H) with weight 1/H, so F is the piecewise-linear empirical CDF
+// (a ramp at least one q step wide stands for a vertical step).
+__global__ void lp_quantile_init_kernel(const float* xs, int S, const LearnedPlan* lp, tqp_cdf_model* md) {
+  const int j = threadIdx.x;
+  if (j >= kH) return;
+  int i0 = (int)((long long)j * S / kH);
+  int i1 = (int)((long long)(j + 1) * S / kH);
+  if (i1 > S - 1) i1 = S - 1;
+  float x0 = xs[i0], x1 = xs[i1];
+  float step = lp->inv > 0.0f ? lp->inv : 1.0f;
+  float width = x1 - x0 > step ? x1 - x0 : step;
+  float w = 1.0f / width;
+  md->w[j] = w;
+  md->b[j] = -x0 * w;
+  md->a[j] = 1.0f / (float)kH;
+  if (j == 0) md->c = 0.0f;
+}
+
 __global__ void lp_no_heavy_kernel(LearnedPlan* lp) {
   if (threadIdx.x == 0) lp->nheavy = 0;
 }
@@ -428,16 +447,19 @@ __global__ void __launch_bounds__(1024) lp_offsets_kernel(const LearnedPlan* lp,
   __shared__ int s_scan[33];
   __shared__ unsigned s_max[32];
   __shared__ int s_over[32], s_ne[32];
+  __shared__ unsigned long long s_orows[32];
   const int B = lp->B;
   const int per = (B + 1023) / 1024;
   const int b0 = threadIdx.x * per;
   unsigned sum = 0, mx = 0;
   int over = 0, ne = 0;
+  unsigned long long over_rows = 0;
   for (int b = b0; b < b0 + per && b < B; ++b) {
     unsigned c = count[b];
     sum += c;
     mx = c > mx ? c : mx;
     over += c > (unsigned)kLocalCap;
+    over_rows += c > (unsigned)kLocalCap ? c : 0;
     ne += c > 0;
   }
   int total;
@@ -458,21 +480,25 @@ __global__ void __launch_bounds__(1024) lp_offsets_kernel(const LearnedPlan* lp,
     mx = m2 > mx ? m2 : mx;
     over += __shfl_xor_sync(0xffffffffu, over, o);
     ne += __shfl_xor_sync(0xffffffffu, ne, o);
+    over_rows += __shfl_xor_sync(0xffffffffu, over_rows, o);
   }
   if ((threadIdx.x & 31) == 0) {
     s_max[threadIdx.x >> 5] = mx;
     s_over[threadIdx.x >> 5] = over;
     s_ne[threadIdx.x >> 5] = ne;
+    s_orows[threadIdx.x >> 5] = over_rows;
   }
   __syncthreads();
   if (threadIdx.x == 0 && stats) {
     unsigned m3 = 0;
-    long long o3 = 0, n3 = 0;
+    long long o3 = 0, n3 = 0, r3 = 0;
     for (int w = 0; w < 32; ++w) {
       m3 = s_max[w] > m3 ? s_max[w] : m3;
       o3 += s_over[w];
       n3 += s_ne[w];
+      r3 += (long long)s_orows[w];
     }
+    stats->over_capacity_rows = r3;
     stats->buckets = B;
     stats->heavy_keys = lp->nheavy;
     stats->light_rows = total;

@@ -9,12 +9,14 @@
 #include <atomic>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 #include "common.cuh"
 #include "filter.cuh"
 #include "groupby.cuh"
 #include "join.cuh"
 #include "learned.cuh"
+#include "batched.cuh"
 #include "sort.cuh"
 #include "star.cuh"
 
@@ -89,7 +91,12 @@ inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); 
 // External records so that they also become event nodes under stream capture.
 inline void prof_mark(int kid, bool start, cudaStream_t s) {
   cudaEvent_t e = start ? g_prof_start[kid] : g_prof_stop[kid];
-  if (e) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  if (!e) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  cudaError_t err = (cs == cudaStreamCaptureStatusActive) ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                                          : cudaEventRecord(e, s);
+  if (err != cudaSuccess) cudaGetLastError();  // a profiling mark never fails the call
 }
 
 bool valid_dtype(int dt) { return dt >= TQP_I8 && dt <= TQP_I64; }
@@ -955,6 +962,7 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   if (cfg->buckets < 0 || cfg->buckets == 1 || cfg->buckets > 65536 || (cfg->buckets & (cfg->buckets - 1)))
     return TQP_ERR_INVALID;
   if (cfg->train && !valid_train_cfg(&cfg->train_cfg)) return TQP_ERR_INVALID;
+  if (cfg->init != 0 && cfg->init != 1) return TQP_ERR_INVALID;
   for (int k = 0; k < nkeys; ++k)
     if (!valid_dtype(keys[k].dtype)) return TQP_ERR_DTYPE;
   AggProgram P;
@@ -1033,6 +1041,9 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   st = run_sort(ssort, kKeyU64, sample, nullptr, ssorted, srows, S, nullptr, 0, 64, s);
   if (st != TQP_OK) return st;
   lp_targets_kernel<<<(S + 255) / 256, 256, 0, s>>>(ssorted, S, lp, tx, ty); note_launch();
+  if (cfg->init == 1) {
+    lp_quantile_init_kernel<<<1, kH, 0, s>>>(tx, S, lp, model); note_launch();
+  }
   // 3. training
   if (epochs > 0) launch_training(model, tx, ty, S, nullptr, cfg->train_cfg, partial, adam, loss, s);
   // 4. heavy keys, step positions and their directory
@@ -1124,6 +1135,199 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   }
   gb_heavy_only_kernel<<<(kMaxHeavy + 255) / 256, 256, 0, s>>>(r, naggs); note_launch();
   if (d_model_out) TQP_CUDA(cudaMemcpyAsync(d_model_out, model, sizeof(tqp_cdf_model), cudaMemcpyDeviceToDevice, s));
+  return last_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Batched instances.
+tqp_status tqp_star_agg_batched(const tqp_batch_shape* shape, const tqp_problem* probs, int nprob,
+                                const tqp_batch_cfg* cfg, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || !shape || nprob < 1 || nprob > 65536 || !probs) return TQP_ERR_INVALID;
+  const int items = (cfg && cfg->probe_items) ? cfg->probe_items : 8;
+  if (items != 4 && items != 8 && items != 16) return TQP_ERR_INVALID;
+  const tqp_batch_shape& sh = *shape;
+  if (sh.nfact_cols < 1 || sh.nfact_cols > TQP_BATCH_MAX_COLS || sh.fk_col < 0 || sh.fk_col >= sh.nfact_cols)
+    return TQP_ERR_INVALID;
+  if (sh.key_dtype != TQP_I32 || sh.fact_dtype[sh.fk_col] != TQP_I32) return TQP_ERR_DTYPE;
+  if (sh.group_dtype != TQP_I8 && sh.group_dtype != TQP_I16 && sh.group_dtype != TQP_I32) return TQP_ERR_DTYPE;
+  for (int c = 0; c < sh.nfact_cols; ++c)
+    if (!valid_dtype(sh.fact_dtype[c])) return TQP_ERR_DTYPE;
+  if (sh.npred < 0 || sh.npred > TQP_MAX_PREDS || sh.nexprs < 0 || sh.nexprs > TQP_MAX_EXPRS || sh.naggs < 1 ||
+      sh.naggs > TQP_MAX_AGGS - 1)
+    return TQP_ERR_INVALID;
+  BatchShape S;
+  std::memset(&S, 0, sizeof(S));
+  S.nfact_cols = sh.nfact_cols;
+  for (int c = 0; c < sh.nfact_cols; ++c) S.fact_dt[c] = sh.fact_dtype[c];
+  S.fk_col = sh.fk_col;
+  S.group_dt = sh.group_dtype;
+  S.npred = sh.npred;
+  for (int q = 0; q < sh.npred; ++q) {
+    if (sh.preds[q].col < 0 || sh.preds[q].col >= sh.nfact_cols || sh.preds[q].op < TQP_LT || sh.preds[q].op > TQP_NE)
+      return TQP_ERR_INVALID;
+    S.pcol[q] = sh.preds[q].col;
+    S.pop[q] = sh.preds[q].op;
+    S.plit[q] = sh.preds[q].lit;
+  }
+  S.nexprs = sh.nexprs;
+  for (int e = 0; e < sh.nexprs; ++e) {
+    if (sh.exprs[e].nterms < 1 || sh.exprs[e].nterms > 3) return TQP_ERR_INVALID;
+    S.nterms[e] = sh.exprs[e].nterms;
+    for (int t = 0; t < sh.exprs[e].nterms; ++t) {
+      if (sh.exprs[e].term[t].col < 0 || sh.exprs[e].term[t].col >= sh.nfact_cols) return TQP_ERR_INVALID;
+      S.tcol[e][t] = sh.exprs[e].term[t].col;
+      S.tmul[e][t] = sh.exprs[e].term[t].mul;
+      S.tadd[e][t] = sh.exprs[e].term[t].add;
+    }
+  }
+  S.naggs = sh.naggs;
+  for (int q = 0; q < sh.naggs; ++q) {
+    if (sh.aggs[q].op < TQP_COUNT || sh.aggs[q].op > TQP_MAX) return TQP_ERR_INVALID;
+    if (sh.aggs[q].op != TQP_COUNT && (sh.aggs[q].expr < 0 || sh.aggs[q].expr >= sh.nexprs)) return TQP_ERR_INVALID;
+    S.op[q] = sh.aggs[q].op;
+    S.expr[q] = sh.aggs[q].op == TQP_COUNT ? 0 : sh.aggs[q].expr;
+  }
+  // ---- host-side layout: offsets of dimension rows, probe tiles and slots
+  const int TILE = 256 * items;
+  std::vector<long long> dim_off(nprob), tile_off(nprob), slot_off(nprob);
+  long long total_dim = 0, total_tiles = 0, total_slots = 0;
+  const long long domain = sh.group_dtype == TQP_I8 ? 256 : sh.group_dtype == TQP_I16 ? 65536 : (1ll << 40);
+  for (int p = 0; p < nprob; ++p) {
+    const tqp_problem& P = probs[p];
+    if (P.n_fact < 0 || P.n_fact > INT_MAX || P.n_dim < 0 || P.cap < 0) return TQP_ERR_INVALID;
+    dim_off[p] = total_dim;
+    tile_off[p] = total_tiles;
+    slot_off[p] = total_slots;
+    total_dim += P.n_dim;
+    total_tiles += (P.n_fact + TILE - 1) / TILE;
+    total_slots += P.n_dim < domain ? P.n_dim : domain;
+  }
+  if (total_dim >= (1ll << 30) || total_tiles >= (1ll << 32)) return TQP_ERR_INVALID;
+  const int nacc = S.naggs + 1;
+  const size_t td = (size_t)(total_dim > 0 ? total_dim : 1);
+  const int64_t seg_tiles = (total_dim + 256 * 8 - 1) / (256 * 8);
+  Carver c(ws);
+  BatchProb* dprobs = c.take<BatchProb>(nprob);
+  long long* d_dim_off = c.take<long long>(nprob);
+  long long* d_tile_off = c.take<long long>(nprob);
+  unsigned long long* ckey = c.take<unsigned long long>(td);
+  int32_t* crow = c.take<int32_t>(td);
+  unsigned long long* cgrp = c.take<unsigned long long>(td);
+  int32_t* grow = c.take<int32_t>(td);
+  unsigned long long* skey = c.take<unsigned long long>(td);
+  int32_t* srow = c.take<int32_t>(td);
+  unsigned long long* sgrp = c.take<unsigned long long>(td);
+  int32_t* sgrow = c.take<int32_t>(td);
+  SortWs sw = carve_sort(c, total_dim, 8, 8);
+  int32_t* seg = c.take<int32_t>(td);
+  long long* gval = c.take<long long>(td);
+  unsigned long long* sstatus = c.take<unsigned long long>((size_t)(seg_tiles > 0 ? seg_tiles : 1));
+  uint32_t* scounter = c.take<uint32_t>(1);
+  int32_t* rank_of_row = c.take<int32_t>(td);
+  int32_t* key32 = c.take<int32_t>(td);
+  int32_t* rank_sorted = c.take<int32_t>(td);
+  long long* G = c.take<long long>(nprob);
+  long long* first_seg = c.take<long long>(nprob);
+  int* flag = c.take<int>(1);
+  long long* acc = c.take<long long>((size_t)(total_slots > 0 ? total_slots : 1) * nacc);
+  uint32_t* queue = c.take<uint32_t>(1);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // ---- descriptors through kernel parameters (capturable, no host buffer kept)
+  for (int first = 0; first < nprob; first += kUploadChunk) {
+    UploadChunk ch;
+    std::memset(&ch, 0, sizeof(ch));
+    ch.first = first;
+    ch.count = nprob - first < kUploadChunk ? nprob - first : kUploadChunk;
+    for (int i = 0; i < ch.count; ++i) {
+      const tqp_problem& P = probs[first + i];
+      if ((P.n_fact > 0 && (!P.fact_cols[sh.fk_col])) || (P.n_dim > 0 && (!P.dim_key || !P.dim_group)) ||
+          !P.d_out_groups || (P.cap > 0 && (!P.out_keys || !P.out_aggs)))
+        return TQP_ERR_INVALID;
+      BatchProb& b = ch.p[i];
+      b.n_fact = P.n_fact;
+      for (int cc = 0; cc < TQP_BATCH_MAX_COLS; ++cc) b.fact[cc] = P.fact_cols[cc];
+      b.n_dim = P.n_dim;
+      b.key = P.dim_key;
+      b.group = P.dim_group;
+      b.out_keys = P.out_keys;
+      b.out_aggs = reinterpret_cast<long long*>(P.out_aggs);
+      b.cap = P.cap;
+      b.d_out_groups = reinterpret_cast<long long*>(P.d_out_groups);
+      b.dim_off = dim_off[first + i];
+      b.tile_off = tile_off[first + i];
+      b.slot_off = slot_off[first + i];
+    }
+    batch_upload_kernel<<<1, kUploadChunk, 0, s>>>(ch, dprobs); note_launch();
+  }
+  // offsets as separate arrays for the searches (uploaded the same way)
+  for (int first = 0; first < nprob; first += kUploadChunk) {
+    UploadChunk ch;
+    std::memset(&ch, 0, sizeof(ch));
+    ch.first = first;
+    ch.count = nprob - first < kUploadChunk ? nprob - first : kUploadChunk;
+    for (int i = 0; i < ch.count; ++i) {
+      ch.p[i].dim_off = dim_off[first + i];
+      ch.p[i].tile_off = tile_off[first + i];
+    }
+    batch_offsets_kernel<<<1, kUploadChunk, 0, s>>>(ch, d_dim_off, d_tile_off); note_launch();
+  }
+  TQP_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  batch_empty_groups_kernel<<<(nprob + 255) / 256, 256, 0, s>>>(dprobs, nprob, G); note_launch();
+  if (total_dim > 0) {
+    batch_dim_encode_kernel<<<stride_grid(total_dim, 256), 256, 0, s>>>(dprobs, d_dim_off, nprob, total_dim,
+                                                                        sh.group_dtype, ckey, crow, cgrp, grow);
+    note_launch();
+    tqp_status st = run_sort(sw, kKeyU64, ckey, crow, skey, srow, total_dim, nullptr, 0, 64, s);
+    if (st != TQP_OK) return st;
+    st = run_sort(sw, kKeyU64, cgrp, grow, sgrp, sgrow, total_dim, nullptr, 0, 64, s);
+    if (st != TQP_OK) return st;
+    TQP_CUDA(cudaMemsetAsync(sstatus, 0, (size_t)seg_tiles * 8, s));
+    TQP_CUDA(cudaMemsetAsync(scounter, 0, 4, s));
+    auto sk = batch_seg_kernel<256, 8>;
+    sk<<<persistent_grid(sk, 256, 0, seg_tiles), 256, 0, s>>>(sgrp, total_dim, sh.group_dtype, seg, gval, sstatus,
+                                                              scounter, (uint32_t)seg_tiles);
+    note_launch();
+    batch_rank_kernel<<<stride_grid(total_dim, 256), 256, 0, s>>>(dprobs, d_dim_off, nprob, total_dim, sgrp, sgrow,
+                                                                  seg, rank_of_row, G, first_seg);
+    note_launch();
+    batch_pregather_kernel<<<stride_grid(total_dim, 256), 256, 0, s>>>(skey, srow, d_dim_off, total_dim,
+                                                                       rank_of_row, key32, rank_sorted, flag);
+    note_launch();
+  }
+  batch_init_acc_kernel<<<stride_grid(total_slots * nacc, 256, 4), 256, 0, s>>>(S, acc, total_slots); note_launch();
+  TQP_CUDA(cudaMemsetAsync(queue, 0, 4, s));
+  BatchProbeArgs pa;
+  pa.probs = dprobs;
+  pa.tile_off = d_tile_off;
+  pa.nprob = nprob;
+  pa.num_tiles = total_tiles;
+  pa.key32 = key32;
+  pa.rank_sorted = rank_sorted;
+  pa.G = G;
+  pa.flag = flag;
+  pa.acc = acc;
+  pa.queue = queue;
+  if (total_tiles > 0) {
+    prof_mark(6, true, s);
+    if (items == 4) {
+      auto k = batch_probe_kernel<256, 4>;
+      k<<<persistent_grid(k, 256, 0, total_tiles), 256, 0, s>>>(pa, S); note_launch();
+    } else if (items == 8) {
+      auto k = batch_probe_kernel<256, 8>;
+      k<<<persistent_grid(k, 256, 0, total_tiles), 256, 0, s>>>(pa, S); note_launch();
+    } else {
+      auto k = batch_probe_kernel<256, 16>;
+      k<<<persistent_grid(k, 256, 0, total_tiles), 256, 0, s>>>(pa, S); note_launch();
+    }
+    prof_mark(6, false, s);
+  }
+  batch_compact_kernel<<<nprob, 256, 0, s>>>(dprobs, G, first_seg, gval, acc, S.naggs, sh.group_dtype, flag);
+  note_launch();
   return last_launch();
 }
 

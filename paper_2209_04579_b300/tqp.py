@@ -79,12 +79,14 @@ class TrainCfg(ctypes.Structure):
 
 class LearnedCfg(ctypes.Structure):
     _fields_ = [("sample", ctypes.c_int32), ("buckets", ctypes.c_int32), ("train", ctypes.c_int32),
-                ("heavy", ctypes.c_int32), ("train_cfg", TrainCfg)]
+                ("heavy", ctypes.c_int32), ("train_cfg", TrainCfg), ("init", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class LearnedStats(ctypes.Structure):
     _fields_ = [("buckets", ctypes.c_int64), ("heavy_keys", ctypes.c_int64), ("light_rows", ctypes.c_int64),
                 ("max_bucket", ctypes.c_int64), ("over_capacity", ctypes.c_int64), ("nonempty", ctypes.c_int64),
+                ("over_capacity_rows", ctypes.c_int64),
                 ("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float)]
 
 
@@ -361,8 +363,10 @@ def tqp_cdf_train(x, y, model, cfg=None, stream=None):
     return loss[:cfg.epochs]
 
 
-def learned_cfg(sample=65536, buckets=0, train=True, heavy=True, tcfg=None):
-    return LearnedCfg(sample, buckets, int(train), int(heavy), tcfg or train_cfg())
+def learned_cfg(sample=65536, buckets=0, train=True, heavy=True, tcfg=None, init=None):
+    """init: 0 = identity CDF, 1 = sample-quantile knots (default: 1 when training)."""
+    init = (1 if train else 0) if init is None else init
+    return LearnedCfg(sample, buckets, int(train), int(heavy), tcfg or train_cfg(), int(init), 0)
 
 
 def tqp_groupby_agg_learned(keys, vals, exprs, aggs, cap, cfg=None, sel=None, n=None, d_n=None, stream=None):

@@ -166,6 +166,7 @@ def test_trained_network_gains_over_identity(T):
                                         cfg=cfg)
         compare(got, want)
         res[train] = T.stats_from_device(got[4])
+    # the fitted network routes far fewer rows to the global-memory fallback
     assert res[True]["max_bucket"] * 4 < res[False]["max_bucket"]
-    assert res[True]["over_capacity"] <= res[False]["over_capacity"]
-    assert res[True]["loss_last"] < res[True]["loss_first"]
+    assert res[True]["over_capacity_rows"] * 4 < res[False]["over_capacity_rows"]
+    assert res[True]["loss_last"] <= res[True]["loss_first"]
