@@ -75,6 +75,22 @@ def batched_one(fact, dim, cap: int = 64):
                             [(0, 2)], [[(0, 1, 0)]], [(tqp.SUM, 0), (tqp.COUNT, 0)], cap)
 
 
+def batched_shape():
+    """Query shape of every batched instance: fact (fk int32, day int32,
+    v int64) JOIN dim (key int32, grp int8) WHERE day < 1278 GROUP BY grp:
+    SUM(v), COUNT(*)."""
+    import torch
+    return tqp.batch_shape([torch.int32, torch.int32, torch.int64], 0, torch.int8,
+                           [(1, tqp.LT, BATCH_DAY_LT)], [[(2, 1, 0)]], [(tqp.SUM, 0), (tqp.COUNT, 0)])
+
+
+def batched(problems, cap: int = 64, probe_items: int = 8, shape=None):
+    """All instances in one batched call; problems: list of (fact, dim) tables."""
+    shape = shape or batched_shape()
+    return tqp.tqp_star_agg_batched(shape, [([f["fk"], f["day"], f["v"]], d["key"], d["grp"]) for f, d in problems],
+                                    cap=cap, probe_items=probe_items)
+
+
 def star(fact, dim1, dim2, cap: int = 50_000):
     """SELECT dim1.cat, dim2.cat, SUM(m1), SUM(m2), SUM(m3), COUNT(*)
     FROM fact JOIN dim1 ON fk1 = dim1.key JOIN dim2 ON fk2 = dim2.key

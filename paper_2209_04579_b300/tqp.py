@@ -90,6 +90,27 @@ class LearnedStats(ctypes.Structure):
                 ("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float)]
 
 
+BATCH_MAX_COLS = 4
+
+
+class BatchShape(ctypes.Structure):
+    _fields_ = [("nfact_cols", ctypes.c_int32), ("fact_dtype", ctypes.c_int32 * BATCH_MAX_COLS),
+                ("fk_col", ctypes.c_int32), ("key_dtype", ctypes.c_int32), ("group_dtype", ctypes.c_int32),
+                ("npred", ctypes.c_int32), ("preds", Pred * 4), ("nexprs", ctypes.c_int32), ("exprs", Expr * 8),
+                ("naggs", ctypes.c_int32), ("aggs", Agg * 8)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n_fact", ctypes.c_int64), ("fact_cols", ctypes.c_void_p * BATCH_MAX_COLS),
+                ("n_dim", ctypes.c_int64), ("dim_key", ctypes.c_void_p), ("dim_group", ctypes.c_void_p),
+                ("out_keys", ctypes.c_void_p), ("out_aggs", ctypes.c_void_p), ("cap", ctypes.c_int64),
+                ("d_out_groups", ctypes.c_void_p)]
+
+
+class BatchCfg(ctypes.Structure):
+    _fields_ = [("probe_items", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
 _vp, _i64, _sz, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t, ctypes.c_int
 _P = ctypes.POINTER
 
@@ -106,6 +127,7 @@ _lib.tqp_cdf_backward.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_cdf_train.argtypes = [_vp, _vp, _i64, _vp, _P(TrainCfg), _vp, _vp, _P(_sz), _vp]
 _lib.tqp_groupby_agg_learned.argtypes = [_P(Col), _int, _P(Col), _int, _P(Expr), _int, _P(Agg), _int, _vp, _i64,
                                          _vp, _P(_vp), _vp, _i64, _vp, _P(LearnedCfg), _vp, _vp, _vp, _P(_sz), _vp]
+_lib.tqp_star_agg_batched.argtypes = [_P(BatchShape), _P(Problem), _int, _P(BatchCfg), _vp, _P(_sz), _vp]
 _lib.tqp_status_poll.argtypes = [_vp]
 _lib.tqp_debug_set_spin_limit.argtypes = [_i64]
 _lib.tqp_debug_inject_unpublished_tile.argtypes = [_i64]
@@ -115,7 +137,7 @@ _lib.tqp_debug_launch_count.argtypes = []
 _lib.tqp_profile_events.argtypes = [_int, _vp, _vp]
 for _f in ("tqp_filter", "tqp_gather", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
            "tqp_status_poll", "tqp_profile_events", "tqp_cdf_forward", "tqp_cdf_backward", "tqp_cdf_train",
-           "tqp_groupby_agg_learned", "tqp_debug_set_spin_limit", "tqp_debug_inject_unpublished_tile"):
+           "tqp_groupby_agg_learned", "tqp_star_agg_batched", "tqp_debug_set_spin_limit", "tqp_debug_inject_unpublished_tile"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -392,6 +414,53 @@ def tqp_groupby_agg_learned(keys, vals, exprs, aggs, cap, cfg=None, sel=None, n=
 def stats_from_device(t):
     st = LearnedStats.from_buffer_copy(t.cpu().numpy().tobytes())
     return {f: getattr(st, f) for f, _ in LearnedStats._fields_}
+
+
+# ------------------------------------------------------------------ batched instances
+
+def batch_shape(fact_dtypes, fk_col, group_dtype, preds, exprs, aggs, key_dtype=torch.int32):
+    sh = BatchShape()
+    sh.nfact_cols = len(fact_dtypes)
+    for i, d in enumerate(fact_dtypes):
+        sh.fact_dtype[i] = _DTYPE[d]
+    sh.fk_col, sh.key_dtype, sh.group_dtype = fk_col, _DTYPE[key_dtype], _DTYPE[group_dtype]
+    sh.npred = len(preds)
+    for i, (c, op, lit) in enumerate(preds):
+        sh.preds[i] = Pred(c, op, lit)
+    sh.nexprs = len(exprs)
+    for i, e in enumerate(exprs):
+        sh.exprs[i].nterms = len(e)
+        for t, (c, m, a) in enumerate(e):
+            sh.exprs[i].term[t] = Term(c, 0, m, a)
+    sh.naggs = len(aggs)
+    for i, (op, e) in enumerate(aggs):
+        sh.aggs[i] = Agg(op, e)
+    return sh
+
+
+def tqp_star_agg_batched(shape, problems, cap=64, probe_items=8, stream=None):
+    """problems: list of (fact_cols list, dim_key, dim_group).  Returns one
+    (group keys, aggs [cap, naggs], device G) per problem."""
+    dev = problems[0][1].device
+    arr = (Problem * len(problems))()
+    outs = []
+    for i, (fact, key, grp) in enumerate(problems):
+        ok = torch.empty(max(cap, 1), dtype=grp.dtype, device=dev)
+        oa = torch.empty((max(cap, 1), shape.naggs), dtype=torch.int64, device=dev)
+        G = torch.empty(1, dtype=torch.int64, device=dev)
+        outs.append((ok, oa, G))
+        arr[i].n_fact = fact[0].numel()
+        for c, t in enumerate(fact):
+            arr[i].fact_cols[c] = t.data_ptr() if t.numel() else None
+        arr[i].n_dim = key.numel()
+        arr[i].dim_key = key.data_ptr() if key.numel() else None
+        arr[i].dim_group = grp.data_ptr() if grp.numel() else None
+        arr[i].out_keys, arr[i].out_aggs, arr[i].cap, arr[i].d_out_groups = ok.data_ptr(), oa.data_ptr(), cap, \
+            G.data_ptr()
+    cfg = BatchCfg(probe_items, 0)
+    _two_phase(_lib.tqp_star_agg_batched, "tqp_star_agg_batched",
+               [ctypes.byref(shape), arr, len(problems), ctypes.byref(cfg)], dev, stream)
+    return outs
 
 
 def tqp_status_poll(stream=None) -> int:
