@@ -98,3 +98,34 @@ def test_empty_inputs_accept_null_data():
     st = lib.tqp_groupby_agg(cols, 1, vals, 1, ex, 1, aggs, 1, None, 0, None, None, None, 0, None, None,
                              ctypes.byref(sz), None)
     assert st == tqp.OK
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes mirror of a header struct has the C size and field offsets."""
+    import subprocess
+    from paper_2209_04579_b300 import tqp
+    mirrors = {"tqp_col": tqp.Col, "tqp_pred": tqp.Pred, "tqp_term": tqp.Term, "tqp_expr": tqp.Expr,
+               "tqp_agg": tqp.Agg, "tqp_dim": tqp.Dim, "tqp_valref": tqp.ValRef, "tqp_cdf_model": tqp.CdfModel,
+               "tqp_train_cfg": tqp.TrainCfg, "tqp_learned_cfg": tqp.LearnedCfg,
+               "tqp_learned_stats": tqp.LearnedStats, "tqp_batch_shape": tqp.BatchShape,
+               "tqp_problem": tqp.Problem, "tqp_batch_cfg": tqp.BatchCfg}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tqp.h"', "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    out = subprocess.check_output([str(exe)]).decode().split("\n")
+    want = {}
+    for ln in out:
+        if ln:
+            a, b, v = ln.split()
+            want[(a, b)] = int(v)
+    for cname, cls in mirrors.items():
+        assert want[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert want[(cname, f)] == getattr(cls, f).offset, (cname, f)
