@@ -129,7 +129,133 @@ class Q6:
         return time.perf_counter() - t0, f"first {rows} rows"
 
 
-WORKLOADS = {"q14": Q14, "q6": Q6}
+class Skew:
+    """100M-row group-by on skewed int64 keys (90% Zipf(1) over 10M values,
+    10% uniform noise) through the learned range partitioner (training
+    included in every step); the plain radix path is timed beside it."""
+    name = "skew"
+    n = 100_000_000
+    prof_class = 7
+    kernel_name = "lp_bucket_sort_kernel"
+
+    def __init__(self, master):
+        from paper_2209_04579_b300 import datagen as dg
+        self.dg = dg
+        self.rec = dg.skew_groupby(master=master)
+        self.cap = self.n
+
+    def config(self):
+        return {"workload": "skewed group-by: 100M rows, int64 key 90% Zipf(1.0) over 10M values (hashed) + 10% "
+                            "uniform 64-bit noise, value int64 U[0,2^31]; COUNT, SUM, MIN, MAX per key; learned range "
+                            "partitioner trained on the GPU inside every step", "rows": self.n}
+
+    def make_device(self):
+        from paper_2209_04579_b300 import datagen_device as gd
+        z = torch.from_numpy(self.dg.zipf_table(self.dg.ZIPF_S, self.dg.ZIPF_N)).cuda()
+        self.t = gd.make_table(self.rec, self.n, zipf=z)
+        return [self.t["key"], self.t["value"]]
+
+    def step(self):
+        from paper_2209_04579_b300 import queries as Q
+        from paper_2209_04579_b300 import tqp
+        r = Q.skew_learned(self.t, cap=self.cap, cfg=tqp.learned_cfg(sample=65536, tcfg=tqp.train_cfg(epochs=100)))
+        self.stats = r[4]
+        return r[:3]
+
+    def plain_step(self):
+        from paper_2209_04579_b300 import queries as Q
+        return Q.skew(self.t, cap=self.cap)
+
+    def rows(self):
+        return self.n
+
+    def alg_bytes(self):
+        return self.n * 16 + 17_000_000 * 40
+
+    def dominant_bytes(self):
+        # the bucket sort reads and writes every light row's packed key and row id
+        return int(getattr(self, "light_rows", self.n) * 12 * 2)
+
+    def oracle_sample(self, rows):
+        from oracle import pipelines as pl
+        z = self.dg.zipf_table(self.dg.ZIPF_S, self.dg.ZIPF_N)
+        t = self.dg.make_table(self.rec, rows, zipf=z)
+        t0 = time.perf_counter()
+        pl.skew(t)
+        return time.perf_counter() - t0, f"first {rows} of the 100M rows"
+
+
+class Batched:
+    """512 independent join+filter+group-by problems (fact sizes log-uniform
+    1K..4M, sum ~247M rows) in one batched call; the same problems as 512
+    separate calls are timed beside it."""
+    name = "batched"
+    prof_class = 6
+    kernel_name = "batch_probe_kernel"
+
+    def __init__(self, master):
+        from paper_2209_04579_b300 import datagen as dg
+        self.dg = dg
+        self.master = master
+        ns, ms, gs = dg.batched_sizes(master=master)
+        self.spec = [(p, int(ns[p]), int(ms[p]), int(gs[p])) for p in range(len(ns))]
+        self.items = 8
+
+    def config(self):
+        return {"workload": "batched: 512 problems fact JOIN dim WHERE day<1278 GROUP BY dim.grp, SUM(v), COUNT; fact "
+                            "rows log-uniform 1e3..4e6 (sum %d), dim = fact/40, 1..64 groups; one batched call"
+                            % sum(s[1] for s in self.spec), "problems": len(self.spec), "probe_items": self.items}
+
+    def make_device(self):
+        from paper_2209_04579_b300 import autotune
+        from paper_2209_04579_b300 import datagen_device as gd
+        from paper_2209_04579_b300 import queries as Q
+        self.probs = []
+        ins = []
+        for p, n, m, g in self.spec:
+            rec = self.dg.batched_problem(p, n, m, g, master=self.master)
+            f, d = gd.make_table(rec["fact"], n), gd.make_table(rec["dim"], m)
+            self.probs.append((f, d))
+            ins += [f["fk"], f["day"], f["v"], d["key"], d["grp"]]
+        shape = Q.batched_shape()
+        self.items, self.tune = autotune.tune_batched(
+            [([f["fk"], f["day"], f["v"]], d["key"], d["grp"]) for f, d in self.probs], shape)
+        return ins
+
+    def step(self):
+        from paper_2209_04579_b300 import queries as Q
+        return Q.batched(self.probs, probe_items=self.items)
+
+    def plain_step(self):
+        from paper_2209_04579_b300 import queries as Q
+        return [Q.batched_one(f, d) for f, d in self.probs]
+
+    def rows(self):
+        return sum(s[1] for s in self.spec)
+
+    def alg_bytes(self):
+        return sum(n * 16 + m * 5 for _, n, m, _ in self.spec)
+
+    def dominant_bytes(self):
+        return sum(n * 16 for _, n, _, _ in self.spec)
+
+    def oracle_sample(self, rows):
+        from oracle import pipelines as pl
+        done, t = 0, 0.0
+        for p, n, m, g in sorted(self.spec, key=lambda s: s[1]):
+            if done + n > rows:
+                break
+            rec = self.dg.batched_problem(p, n, m, g, master=self.master)
+            f, d = self.dg.make_table(rec["fact"], n), self.dg.make_table(rec["dim"], m)
+            t0 = time.perf_counter()
+            pl.batched_one(f, d)
+            t += time.perf_counter() - t0
+            done += n
+        self._sample_rows = done
+        return t, f"the smallest problems up to {done} fact rows"
+
+
+WORKLOADS = {"q14": Q14, "q6": Q6, "skew": Skew, "batched": Batched}
 
 
 # ---------------------------------------------------------------- helpers
@@ -226,6 +352,7 @@ def cpu_baseline(W, target_s=12.0):
     t, _ = W.oracle_sample(rows)
     rows = int(min(W.rows(), max(rows, rows * target_s / max(t, 1e-3))))
     t, what = W.oracle_sample(rows)
+    rows = getattr(W, "_sample_rows", rows)
     return {"value": rows / t, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": what,
             "seconds": round(t, 3)}
 
@@ -337,9 +464,12 @@ def run_ours(args, world, rank, local):
         e0.record()
         for hsrc, ddst in zip(host_in, inputs):
             ddst.copy_(hsrc, non_blocking=True)
-        ok, oa, G = W.step()
-        res = [G.to("cpu", non_blocking=True), oa.to("cpu", non_blocking=True)] + \
-              [k.to("cpu", non_blocking=True) for k in ok]
+        outs = W.step()
+        outs = outs if isinstance(outs, list) else [outs]
+        res = []
+        for ok, oa, G in outs:
+            res += [G.to("cpu", non_blocking=True), oa.to("cpu", non_blocking=True)] + \
+                   [k.to("cpu", non_blocking=True) for k in ok]
         e1.record()
         e1.synchronize()
         if i > 0:
@@ -365,6 +495,26 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
+    if hasattr(W, "plain_step"):
+        # the same workload through the plain path (no learned partition /
+        # one call per problem), timed the same way, eagerly
+        W.plain_step()
+        torch.cuda.synchronize()
+        pm = []
+        for _ in range(max(1, min(args.steps, 5))):
+            flush.zero_()
+            e0.record()
+            W.plain_step()
+            e1.record()
+            e1.synchronize()
+            pm.append(e0.elapsed_time(e1))
+        line["plain_path"] = {"value": W.rows() / (sum(pm) / len(pm) / 1e3), "unit": "rows/s",
+                              "ms_per_step": sum(pm) / len(pm), "launch": "eager calls"}
+        if hasattr(W, "stats"):
+            from paper_2209_04579_b300 import tqp as _t
+            line["learned_stats"] = _t.stats_from_device(W.stats)
+        if hasattr(W, "tune"):
+            line["autotune"] = W.tune
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
     print(json.dumps(line), flush=True)

@@ -415,7 +415,8 @@ const char* tqp_status_string(tqp_status s);
  * `stop_event` just after the kernel(s) of one class, on the call's stream
  * (cudaEvent_t handles passed as void*; NULL clears).  Classes: 1 = fused
  * star probe, 2 = radix sort passes (from the first to the last pass of a
- * sort), 3 = filter, 4 = group-by reduce, 5 = join probe.  Records are
+ * sort), 3 = filter, 4 = group-by reduce, 5 = join probe, 6 = batched probe,
+ * 7 = learned bucket sort, 8 = learned partition scatter.  Records are
  * external, so under stream capture they become event nodes of the graph. */
 int64_t tqp_debug_launch_count(void);
 tqp_status tqp_profile_events(int kernel_class, void* start_event, void* stop_event);

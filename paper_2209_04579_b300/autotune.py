@@ -1,0 +1,110 @@
+"""Autotuner for the tunable launch parameters.
+
+It times each candidate with CUDA events on the current stream (after a
+warm-up call) and checks that every candidate produces identical bytes. The
+fastest candidate is cached in a JSON file keyed by GPU name, operator and
+size class (log2 of the row count). The cache lives at
+$TQP_AUTOTUNE_CACHE, else ~/.cache/tqp/autotune.json.
+
+Tuned parameters:
+  batched  -- fact rows per thread of the batched probe tile (4, 8, 16);
+  learned  -- number of learned buckets B (n/1024 .. n/4096, powers of two).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import torch
+
+from . import tqp
+
+_CACHE_PATH = os.environ.get("TQP_AUTOTUNE_CACHE",
+                             os.path.join(os.path.expanduser("~"), ".cache", "tqp", "autotune.json"))
+
+
+def _load():
+    try:
+        with open(_CACHE_PATH) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d):
+    try:
+        os.makedirs(os.path.dirname(_CACHE_PATH), exist_ok=True)
+        with open(_CACHE_PATH, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+    except OSError:
+        pass
+
+
+def _key(op: str, rows: int) -> str:
+    return f"{torch.cuda.get_device_name()}|{op}|{int(math.log2(max(rows, 1)))}"
+
+
+def _time(fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(reps):
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def _fingerprint(outs):
+    return [tuple(t.cpu().numpy().tobytes() for t in o) for o in outs]
+
+
+def tune_batched(problems, shape, cap=64, candidates=(4, 8, 16), force=False):
+    """Best probe_items for one batched call; results of all candidates must agree."""
+    rows = sum(int(p[0][0].numel()) for p in problems)
+    cache = _load()
+    k = _key("batched", rows)
+    if not force and k in cache:
+        return int(cache[k]["best"]), cache[k]
+    times, ref = {}, None
+    for c in candidates:
+        times[c] = _time(lambda c=c: tqp.tqp_star_agg_batched(shape, problems, cap=cap, probe_items=c))
+        fp = _fingerprint(tqp.tqp_star_agg_batched(shape, problems, cap=cap, probe_items=c))
+        if ref is None:
+            ref = fp
+        elif fp != ref:
+            raise RuntimeError(f"batched results differ between tile choices ({c})")
+    best = min(times, key=times.get)
+    cache[k] = {"best": best, "ms": {str(c): t for c, t in times.items()}}
+    _store(cache)
+    return best, cache[k]
+
+
+def tune_learned(run, rows, candidates=None, force=False):
+    """Best bucket count for the learned group-by.  run(B) performs one call
+    and returns its outputs (for the identity check)."""
+    cache = _load()
+    k = _key("learned", rows)
+    if not force and k in cache:
+        return int(cache[k]["best"]), cache[k]
+    if candidates is None:
+        base = 256
+        while base < 65536 and base * 2048 < rows:
+            base <<= 1
+        candidates = sorted({max(256, base // 2), base, min(65536, base * 2)})
+    times, ref = {}, None
+    for b in candidates:
+        times[b] = _time(lambda b=b: run(b))
+        fp = _fingerprint([run(b)[:3]])
+        if ref is None:
+            ref = fp
+        elif fp != ref:
+            raise RuntimeError(f"learned results differ between bucket counts ({b})")
+    best = min(times, key=times.get)
+    cache[k] = {"best": best, "ms": {str(b): t for b, t in times.items()}}
+    _store(cache)
+    return best, cache[k]

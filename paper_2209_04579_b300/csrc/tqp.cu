@@ -82,8 +82,8 @@ int stride_grid(int64_t n, int threads, int per_sm = 8) {
 
 // ---------------------------------------------------------------- launch accounting
 std::atomic<long long> g_launches{0};
-cudaEvent_t g_prof_start[8] = {};
-cudaEvent_t g_prof_stop[8] = {};
+cudaEvent_t g_prof_start[16] = {};
+cudaEvent_t g_prof_stop[16] = {};
 
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -376,7 +376,7 @@ tqp_status tqp_status_poll(tqp_stream_t stream) {
 int64_t tqp_debug_launch_count(void) { return g_launches.load(); }
 
 tqp_status tqp_profile_events(int kernel_class, void* start_event, void* stop_event) {
-  if (kernel_class < 1 || kernel_class > 7) return TQP_ERR_INVALID;
+  if (kernel_class < 1 || kernel_class > 15) return TQP_ERR_INVALID;
   g_prof_start[kernel_class] = static_cast<cudaEvent_t>(start_event);
   g_prof_stop[kernel_class] = static_cast<cudaEvent_t>(stop_event);
   return TQP_OK;
@@ -1084,7 +1084,9 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
                            (int)(kMaxHeavy * TQP_MAX_AGGS * sizeof(long long)));
       attr = true;
     }
+    prof_mark(8, true, s);
     lp_scatter_kernel<<<stride_grid(n, 256, 2), 256, smem, s>>>(pa, P); note_launch();
+    prof_mark(8, false, s);
   }
   // 6. every bucket sorted: on-chip up to the capacity, else by one block in global memory
   {
@@ -1105,7 +1107,9 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
     TQP_CUDA(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
     int g = num_sms();
     if (g > B) g = B;
+    prof_mark(7, true, s);
     lp_bucket_sort_kernel<<<g, kLocalThreads, smem, s>>>(ba); note_launch();
+    prof_mark(7, false, s);
   }
   // 7. reduce-by-key over the sorted light rows, merging the heavy keys
   TQP_CUDA(cudaMemsetAsync(rctrl, 0, (1 + (size_t)rtiles) * sizeof(uint32_t), s));

@@ -476,6 +476,7 @@ def tqp_debug_inject_unpublished_tile(tile: int):
 
 
 PROF_STAR_PROBE, PROF_SORT_PASSES, PROF_FILTER, PROF_GROUPBY_REDUCE, PROF_JOIN_PROBE = 1, 2, 3, 4, 5
+PROF_BATCH_PROBE, PROF_BUCKET_SORT, PROF_PARTITION_SCATTER = 6, 7, 8
 
 
 def tqp_debug_launch_count() -> int:
