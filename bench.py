@@ -160,6 +160,9 @@ class Skew:
         from paper_2209_04579_b300 import tqp
         r = Q.skew_learned(self.t, cap=self.cap, cfg=tqp.learned_cfg(sample=65536, tcfg=tqp.train_cfg(epochs=100)))
         self.stats = r[4]
+        if self.cap == self.n:  # first (eager) call: size the outputs to the group count
+            self.cap = int(r[2].item())
+            self.light_rows = tqp.stats_from_device(self.stats)["light_rows"]
         return r[:3]
 
     def plain_step(self):
