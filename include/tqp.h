@@ -69,7 +69,8 @@ typedef enum {
   TQP_ERR_CUDA = 4,        /* a CUDA launch or copy failed */
   TQP_ERR_TIMEOUT = 5,     /* (device) a bounded inter-block wait ran out */
   TQP_ERR_WORKSPACE = 6,   /* workspace smaller than the size query returned */
-  TQP_ERR_UNSUPPORTED = 7  /* valid but unsupported (e.g. >64 packed key bits) */
+  TQP_ERR_UNSUPPORTED = 7, /* valid but unsupported (e.g. >64 packed key bits) */
+  TQP_ERR_TOO_LARGE = 8    /* input larger than a fixed-size entry point accepts */
 } tqp_status;
 
 typedef enum { TQP_I8 = 1, TQP_I16 = 2, TQP_I32 = 3, TQP_I64 = 4 } tqp_dtype;
@@ -134,6 +135,33 @@ typedef struct {
 tqp_status tqp_filter(const tqp_col* cols, int ncols, const tqp_pred* preds, int npred,
                       int64_t n, const int64_t* d_n, int32_t* d_out_idx, int64_t cap,
                       int64_t* d_out_n, void* ws, size_t* ws_bytes, tqp_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * tqp_filter_noalloc -- the filter of tqp_filter for callers that cannot
+ * provide a workspace.  The paper has no counterpart; this is a packaging
+ * variant of the same kernel.
+ *
+ * Some callers cannot allocate device memory at all: a host program whose
+ * own memory manager owns every device allocation and forbids others, or
+ * code running where an allocation is not allowed or could stall (inside a
+ * driver callback or a latency-critical loop).  They still own and pass the
+ * inputs and the outputs (d_out_idx, d_out_n); only the scratch moves: the
+ * kernel's look-back status words and tile counter live in a fixed array of
+ * the library's device data (about 512 KiB, held by every GPU that loads the
+ * library until the process exits).  Hence the size limit: n may not exceed
+ * TQP_NOALLOC_MAX_ROWS, else TQP_ERR_TOO_LARGE is returned before any work.
+ * The call allocates nothing and zeroes the scratch it uses on `stream`.
+ * The first call on each device looks up the array's device address (done
+ * once per device, with that device current); make that first call before
+ * any stream capture.  Every call shares the one array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Arguments, results and errors otherwise as for
+ * tqp_filter.
+ * ---------------------------------------------------------------------- */
+#define TQP_NOALLOC_MAX_ROWS (1LL << 28)
+tqp_status tqp_filter_noalloc(const tqp_col* cols, int ncols, const tqp_pred* preds, int npred,
+                              int64_t n, const int64_t* d_n, int32_t* d_out_idx, int64_t cap,
+                              int64_t* d_out_n, tqp_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * tqp_gather -- column gather, d_out[j] = col[d_idx[j]] for j < n (or < *d_n),

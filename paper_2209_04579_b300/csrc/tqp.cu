@@ -359,6 +359,7 @@ const char* tqp_status_string(tqp_status s) {
     case TQP_ERR_TIMEOUT: return "bounded wait ran out";
     case TQP_ERR_WORKSPACE: return "workspace too small";
     case TQP_ERR_UNSUPPORTED: return "unsupported input";
+    case TQP_ERR_TOO_LARGE: return "input larger than the entry point's fixed scratch allows";
   }
   return "unknown status";
 }
@@ -1332,6 +1333,88 @@ tqp_status tqp_star_agg_batched(const tqp_batch_shape* shape, const tqp_problem*
   }
   batch_compact_kernel<<<nprob, 256, 0, s>>>(dprobs, G, first_seg, gval, acc, S.naggs, sh.group_dtype, flag);
   note_launch();
+  return last_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Filter with a fixed, library-owned scratch array (for callers that cannot
+// allocate a workspace).  One look-back status word per tile of
+// 256 x 16 rows, then the tile counter.
+}  // extern "C"
+
+namespace {
+constexpr int kNoAllocThreads = 256, kNoAllocItems = 16;
+constexpr long long kNoAllocTiles = TQP_NOALLOC_MAX_ROWS / (kNoAllocThreads * kNoAllocItems);
+}  // namespace
+
+static __device__ __align__(256) unsigned long long g_filter_noalloc_scratch[kNoAllocTiles + 32];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[128] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code only sees a stand-in for the symbol).
+tqp_status noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return TQP_ERR_CUDA;
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_filter_noalloc_scratch) != cudaSuccess || !p) return TQP_ERR_CUDA;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return TQP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+tqp_status tqp_filter_noalloc(const tqp_col* cols, int ncols, const tqp_pred* preds, int npred, int64_t n,
+                              const int64_t* d_n, int32_t* d_out_idx, int64_t cap, int64_t* d_out_n,
+                              tqp_stream_t stream) {
+  if (n > TQP_NOALLOC_MAX_ROWS) return TQP_ERR_TOO_LARGE;
+  if (n < 0 || npred < 0 || npred > TQP_MAX_PREDS || ncols < 0) return TQP_ERR_INVALID;
+  if (npred && (!preds || !cols)) return TQP_ERR_INVALID;
+  if (!d_out_n || cap < 0 || (cap > 0 && !d_out_idx)) return TQP_ERR_INVALID;
+  FilterArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.npred = npred;
+  for (int p = 0; p < npred; ++p) {
+    int col = preds[p].col;
+    if (col < 0 || col >= ncols || (n > 0 && !cols[col].data)) return TQP_ERR_INVALID;
+    if (!valid_dtype(cols[col].dtype)) return TQP_ERR_DTYPE;
+    if (preds[p].op < TQP_LT || preds[p].op > TQP_NE) return TQP_ERR_INVALID;
+    a.col[p] = cols[col].data;
+    a.dt[p] = cols[col].dtype;
+    a.op[p] = preds[p].op;
+    a.lit[p] = preds[p].lit;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    TQP_CUDA(cudaMemsetAsync(d_out_n, 0, sizeof(int64_t), s));
+    return TQP_OK;
+  }
+  void* scratch = nullptr;
+  tqp_status st = noalloc_scratch(&scratch);
+  if (st != TQP_OK) return st;
+  const int64_t tiles = (n + kNoAllocThreads * kNoAllocItems - 1) / (kNoAllocThreads * kNoAllocItems);
+  unsigned long long* status = static_cast<unsigned long long*>(scratch);
+  uint32_t* counter = reinterpret_cast<uint32_t*>(status + kNoAllocTiles);
+  // the array keeps the previous call's words: clear what this call uses
+  TQP_CUDA(cudaMemsetAsync(status, 0, (size_t)tiles * sizeof(unsigned long long), s));
+  TQP_CUDA(cudaMemsetAsync(counter, 0, sizeof(uint32_t), s));
+  a.n_max = n;
+  a.d_n = d_n;
+  a.out = d_out_idx;
+  a.cap = cap;
+  a.d_out_n = d_out_n;
+  a.status = status;
+  a.tile_counter = counter;
+  a.num_tiles = (uint32_t)tiles;
+  auto k = filter_kernel<kNoAllocThreads, kNoAllocItems>;
+  k<<<persistent_grid(k, kNoAllocThreads, 0, tiles), kNoAllocThreads, 0, s>>>(a); note_launch();
   return last_launch();
 }
 

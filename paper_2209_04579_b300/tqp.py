@@ -24,7 +24,8 @@ if not os.path.exists(_LIB_PATH):
 _lib = ctypes.CDLL(_LIB_PATH)
 
 # ------------------------------------------------------------------ constants
-OK, ERR_INVALID, ERR_DTYPE, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE, ERR_UNSUPPORTED = range(8)
+OK, ERR_INVALID, ERR_DTYPE, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_WORKSPACE, ERR_UNSUPPORTED, ERR_TOO_LARGE = range(9)
+NOALLOC_MAX_ROWS = 1 << 28
 I8, I16, I32, I64 = 1, 2, 3, 4
 LT, LE, GT, GE, EQ, NE = range(6)
 COUNT, SUM, MIN, MAX = range(4)
@@ -128,6 +129,8 @@ _lib.tqp_cdf_train.argtypes = [_vp, _vp, _i64, _vp, _P(TrainCfg), _vp, _vp, _P(_
 _lib.tqp_groupby_agg_learned.argtypes = [_P(Col), _int, _P(Col), _int, _P(Expr), _int, _P(Agg), _int, _vp, _i64,
                                          _vp, _P(_vp), _vp, _i64, _vp, _P(LearnedCfg), _vp, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_star_agg_batched.argtypes = [_P(BatchShape), _P(Problem), _int, _P(BatchCfg), _vp, _P(_sz), _vp]
+_lib.tqp_filter_noalloc.argtypes = [_P(Col), _int, _P(Pred), _int, _i64, _vp, _vp, _i64, _vp, _vp]
+_lib.tqp_filter_noalloc.restype = ctypes.c_int
 _lib.tqp_status_poll.argtypes = [_vp]
 _lib.tqp_debug_set_spin_limit.argtypes = [_i64]
 _lib.tqp_debug_inject_unpublished_tile.argtypes = [_i64]
@@ -242,6 +245,21 @@ def tqp_filter(cols, preds, n=None, d_n=None, out=None, cap=None, stream=None):
     c, p = _cols(cols), _preds(preds)
     _two_phase(_lib.tqp_filter, "tqp_filter",
                [c, len(cols), p, len(preds), n, _ptr(d_n), _ptr(out), cap, _ptr(cnt)], dev, stream)
+    return out, cnt
+
+
+def tqp_filter_noalloc(cols, preds, n=None, d_n=None, out=None, cap=None, stream=None):
+    """tqp_filter for callers that cannot provide a workspace: the library's
+    fixed scratch array is used instead (n <= NOALLOC_MAX_ROWS; calls must
+    not overlap on the GPU).  The caller passes the outputs (allocated here
+    when not given)."""
+    dev = cols[0].device
+    n = cols[0].numel() if n is None else n
+    cap = n if cap is None else cap
+    out = torch.empty(max(cap, 1), dtype=torch.int32, device=dev) if out is None else out
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    _check(_lib.tqp_filter_noalloc(_cols(cols), len(cols), _preds(preds), len(preds), n, _ptr(d_n), _ptr(out), cap,
+                                   _ptr(cnt), _stream(stream)), "tqp_filter_noalloc")
     return out, cnt
 
 
