@@ -162,6 +162,65 @@ __global__ void star_init_acc_kernel(const StarPlan* plan, const StarAcc A, long
     acc[i] = acc_identity(A, (int)(i % nacc));
 }
 
+// ---- key directory of one dimension: the range of its sorted passing keys
+// is cut into at most 2^log2_cells cells of 2^bshift key values; dir[c] is
+// the first sorted position whose key falls in cell c or later, and a bitmap
+// marks the non-empty cells.  A probe tests the cell's bit (an L1-resident
+// word) and then compares the few keys of dir[c] .. dir[c+1]: a bound search
+// whose first levels are the directory.  Exact for any key distribution.
+struct DimDir {
+  unsigned long long umin, umax;  // order-preserving images of the first and last key
+  int bshift;
+  int pad_;
+  long long ncells;               // 0: no passing rows (every probe misses)
+};
+
+__device__ __forceinline__ unsigned long long key_image(const void* p, int dt, int64_t i) {
+  return dt == TQP_I32 ? (unsigned long long)((uint32_t) static_cast<const int32_t*>(p)[i] ^ 0x80000000u)
+                       : ((unsigned long long) static_cast<const long long*>(p)[i] ^ 0x8000000000000000ull);
+}
+
+__global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, const int64_t* d_n, int log2_cells_max,
+                                DimDir* dd) {
+  if (threadIdx.x != 0) return;
+  const int64_t nd = clamp_n(n_max, d_n);
+  DimDir r;
+  r.pad_ = 0;
+  if (nd == 0) {
+    r.umin = 1;
+    r.umax = 0;
+    r.bshift = 0;
+    r.ncells = 0;
+    *dd = r;
+    return;
+  }
+  r.umin = key_image(skeys, key_dt, 0);
+  r.umax = key_image(skeys, key_dt, nd - 1);
+  unsigned long long span = r.umax - r.umin;
+  int tb = 1;
+  while (tb < log2_cells_max && (1ll << tb) < 2 * nd) ++tb;
+  int bits = span ? 64 - __clzll((long long)span) : 0;
+  r.bshift = bits > tb ? bits - tb : 0;
+  r.ncells = (long long)(span >> r.bshift) + 1;
+  *dd = r;
+}
+
+__global__ void dir_fill_kernel(const void* skeys, int key_dt, int64_t n_max, const int64_t* d_n, const DimDir* dd,
+                                int* dir, uint32_t* bitmap) {
+  const int64_t nd = clamp_n(n_max, d_n);
+  const DimDir r = *dd;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nd; p += stride) {
+    long long c = (long long)((key_image(skeys, key_dt, p) - r.umin) >> r.bshift);
+    long long prev = p ? (long long)((key_image(skeys, key_dt, p - 1) - r.umin) >> r.bshift) : -1;
+    if (c != prev) {
+      for (long long h = prev + 1; h <= c; ++h) dir[h] = (int)p;
+      atomicOr(&bitmap[c >> 5], 1u << (c & 31));
+    }
+    if (p == nd - 1) dir[c + 1] = (int)nd;
+  }
+}
+
 struct ProbeDim {
   const void* skeys;   // sorted passing keys (int32 or int64)
   int key_dt;
@@ -169,6 +228,9 @@ struct ProbeDim {
   const int64_t* d_n;
   const int32_t* rank_sorted;
   const void* fk;      // fact foreign-key column (same dtype as the key)
+  const DimDir* dir_plan;
+  const int* dir;
+  const uint32_t* bitmap;
 };
 
 struct ProbeArgs {
@@ -190,7 +252,7 @@ struct ProbeArgs {
   uint32_t num_tiles;
 };
 
-__device__ __forceinline__ void fold_slot(long long* acc, const StarAcc& A, const long long* ev, bool shared) {
+__device__ __forceinline__ void fold_slot(long long* acc, const StarAcc& A, const long long* ev) {
 #pragma unroll
   for (int q = 0; q < TQP_MAX_AGGS; ++q) {
     if (q < A.naggs) {
@@ -204,9 +266,11 @@ __device__ __forceinline__ void fold_slot(long long* acc, const StarAcc& A, cons
     }
   }
   atomicAdd(reinterpret_cast<unsigned long long*>(acc + A.naggs), 1ull);
-  (void)shared;
 }
 
+// Each thread carries ITEMS independent fact rows through the stages
+// (predicates, then per dimension: cell bit, directory bounds, key compare;
+// then values and the fold), so that ITEMS memory chains are in flight.
 template <int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAcc A) {
   constexpr int TILE = THREADS * ITEMS;
@@ -220,12 +284,17 @@ __global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAc
   if (use_smem) {
     for (int i = threadIdx.x; i < S * nacc; i += THREADS) s_acc[i] = acc_identity(A, i % nacc);
   }
-  long long nd[kMaxDims];
+  DimDir dd[kMaxDims];
   long long stride[kMaxDims];
 #pragma unroll
   for (int d = 0; d < kMaxDims; ++d) {
-    nd[d] = d < a.ndims ? clamp_n(a.dim[d].n_max, a.dim[d].d_n) : 0;
-    stride[d] = d < a.ndims ? plan->stride[d] : 0;
+    if (d < a.ndims) {
+      dd[d] = *a.dim[d].dir_plan;
+      stride[d] = plan->stride[d];
+    } else {
+      dd[d].ncells = 0;
+      stride[d] = 0;
+    }
   }
   __syncthreads();
   while (true) {
@@ -234,46 +303,80 @@ __global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAc
     const uint32_t tile = s_tile;
     __syncthreads();
     if (tile >= a.num_tiles) break;
-    const int64_t base = (int64_t)tile * TILE;
-#pragma unroll 1
-    for (int k = 0; k < ITEMS; ++k) {
-      const int64_t row = base + (int64_t)k * THREADS + threadIdx.x;
-      if (row >= a.n_fact) continue;
-      bool keep = true;
-      for (int p = 0; p < a.npred; ++p)
-        keep = keep && compare(load_as_i64(a.pcol[p], a.pdt[p], row), a.pop[p], a.plit[p]);
-      if (!keep) continue;
-      long long slot = 0;
-      int64_t pos[kMaxDims];
+    const int64_t base = (int64_t)tile * TILE + threadIdx.x;
+    bool live[ITEMS];
+    long long slot[ITEMS];
+    int pos[kMaxDims][ITEMS];
 #pragma unroll
-      for (int d = 0; d < kMaxDims; ++d) {
-        if (d < a.ndims && keep) {
-          int64_t l;
-          bool hit;
-          if (a.dim[d].key_dt == TQP_I32) {
-            const int32_t* sk = static_cast<const int32_t*>(a.dim[d].skeys);
-            int32_t x = static_cast<const int32_t*>(a.dim[d].fk)[row];
-            l = lower_bound_dev(sk, nd[d], x);
-            hit = l < nd[d] && sk[l] == x;
-          } else {
-            const long long* sk = static_cast<const long long*>(a.dim[d].skeys);
-            long long x = static_cast<const long long*>(a.dim[d].fk)[row];
-            l = lower_bound_dev(sk, nd[d], x);
-            hit = l < nd[d] && sk[l] == x;
-          }
-          keep = hit;
-          pos[d] = l;
-          if (hit) slot += (long long)a.dim[d].rank_sorted[l] * stride[d];
+    for (int k = 0; k < ITEMS; ++k) {
+      live[k] = base + (int64_t)k * THREADS < a.n_fact;
+      slot[k] = 0;
+    }
+    for (int p = 0; p < a.npred; ++p) {
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k)
+        if (live[k]) live[k] = compare(load_as_i64(a.pcol[p], a.pdt[p], base + (int64_t)k * THREADS), a.pop[p], a.plit[p]);
+    }
+#pragma unroll
+    for (int d = 0; d < kMaxDims; ++d) {
+      if (d >= a.ndims) break;
+      const ProbeDim& D = a.dim[d];
+      unsigned long long u[ITEMS];
+      long long c[ITEMS];
+      // A: key image and cell, cell bit
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        c[k] = 0;
+        if (live[k]) {
+          u[k] = key_image(D.fk, D.key_dt, base + (int64_t)k * THREADS);
+          if (u[k] < dd[d].umin || u[k] > dd[d].umax) live[k] = false;
+          else c[k] = (long long)((u[k] - dd[d].umin) >> dd[d].bshift);
         }
       }
-      if (!keep) continue;
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k)
+        if (live[k]) live[k] = (__ldg(&D.bitmap[c[k] >> 5]) >> (c[k] & 31)) & 1u;
+      // B: directory bounds
+      int lo[ITEMS], hi[ITEMS];
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        lo[k] = hi[k] = 0;
+        if (live[k]) {
+          lo[k] = __ldg(&D.dir[c[k]]);
+          hi[k] = __ldg(&D.dir[c[k] + 1]);
+        }
+      }
+      // C: the keys of the cell (a bound search when the cell is crowded)
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        if (!live[k]) continue;
+        int l = lo[k], h = hi[k];
+        while (h - l > 4) {
+          int mid = (l + h) >> 1;
+          if (key_image(D.skeys, D.key_dt, mid) < u[k]) l = mid + 1; else h = mid;
+        }
+        int found = -1;
+        for (int i = l; i < h; ++i)
+          if (key_image(D.skeys, D.key_dt, i) == u[k]) { found = i; break; }
+        live[k] = found >= 0;
+        pos[d][k] = found;
+      }
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k)
+        if (live[k]) slot[k] += (long long)__ldg(&D.rank_sorted[pos[d][k]]) * stride[d];
+    }
+    // D: values, expressions, fold
+#pragma unroll 1
+    for (int k = 0; k < ITEMS; ++k) {
+      if (!live[k]) continue;
+      const int64_t row = base + (int64_t)k * THREADS;
       long long vals[TQP_MAX_VALS];
 #pragma unroll
       for (int v = 0; v < TQP_MAX_VALS; ++v) {
         if (v < a.nvals) {
           int src = a.vsrc[v];
           vals[v] = src == 0 ? load_as_i64(a.vptr[v], a.vdt[v], row)
-                             : static_cast<const long long*>(a.vptr[v])[pos[src - 1]];
+                             : static_cast<const long long*>(a.vptr[v])[pos[src - 1][k]];
         }
       }
       long long ev[TQP_MAX_EXPRS];
@@ -287,7 +390,7 @@ __global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAc
           ev[e] = (long long)x;
         }
       }
-      fold_slot(use_smem ? s_acc + slot * nacc : a.acc + slot * nacc, A, ev, use_smem);
+      fold_slot(use_smem ? s_acc + slot[k] * nacc : a.acc + slot[k] * nacc, A, ev);
     }
   }
   if (use_smem) {

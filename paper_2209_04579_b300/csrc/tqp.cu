@@ -334,6 +334,11 @@ struct StarDimWs {
   long long* dval[TQP_MAX_VALS];
   uint32_t ftiles, rtiles;
   int gword;
+  // key directory
+  DimDir* dplan;
+  int* dir;
+  uint32_t* bitmap;
+  int log2cells;
 };
 
 constexpr int kFilterT = 256, kFilterI = 16;
@@ -688,6 +693,11 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
     w.rank_sorted = c.take<int32_t>(nn);
     for (int v = 0; v < nvals; ++v)
       if (vals[v].src == d + 1) w.dval[v] = c.take<long long>(nn);
+    w.log2cells = 1;
+    while (w.log2cells < 27 && (1ll << w.log2cells) < 2 * D.n) ++w.log2cells;
+    w.dplan = c.take<DimDir>(1);
+    w.dir = c.take<int>((size_t)(1ll << w.log2cells) + 2);
+    w.bitmap = c.take<uint32_t>((size_t)(1ll << w.log2cells) / 32 + 1);
   }
   StarPlan* plan = c.take<StarPlan>(1);
   const int nacc = naggs + 1;
@@ -806,6 +816,13 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
       }
       star_pregather_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(pg); note_launch();
     }
+    dir_plan_kernel<<<1, 32, 0, s>>>(w.skeys, D.key.dtype, D.n, dcnt, w.log2cells, w.dplan); note_launch();
+    if (D.n > 0) {
+      TQP_CUDA(cudaMemsetAsync(w.bitmap, 0, ((size_t)(1ll << w.log2cells) / 32 + 1) * sizeof(uint32_t), s));
+      dir_fill_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(w.skeys, D.key.dtype, D.n, dcnt, w.dplan, w.dir,
+                                                             w.bitmap);
+      note_launch();
+    }
   }
   // ---- slots, accumulators, probe, compaction
   star_slots_kernel<<<1, 32, 0, s>>>(plan, ndims, dims[0].group.data ? W[0].G : nullptr,
@@ -821,6 +838,9 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
     pa.dim[d].d_n = dims[d].npred ? W[d].cnt : nullptr;
     pa.dim[d].rank_sorted = W[d].rank_sorted;
     pa.dim[d].fk = fact_cols[fk_col[d]].data;
+    pa.dim[d].dir_plan = W[d].dplan;
+    pa.dim[d].dir = W[d].dir;
+    pa.dim[d].bitmap = W[d].bitmap;
   }
   pa.npred = nfact_preds;
   for (int p = 0; p < nfact_preds; ++p) {
