@@ -350,14 +350,21 @@ __global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAc
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
         if (!live[k]) continue;
+        // first key >= u lies in [l, h]; narrow while the interval is long,
+        // then scan forward from l up to the cell's end
         int l = lo[k], h = hi[k];
         while (h - l > 4) {
           int mid = (l + h) >> 1;
           if (key_image(D.skeys, D.key_dt, mid) < u[k]) l = mid + 1; else h = mid;
         }
         int found = -1;
-        for (int i = l; i < h; ++i)
-          if (key_image(D.skeys, D.key_dt, i) == u[k]) { found = i; break; }
+        for (int i = l; i < hi[k]; ++i) {
+          unsigned long long ki = key_image(D.skeys, D.key_dt, i);
+          if (ki >= u[k]) {
+            if (ki == u[k]) found = i;
+            break;
+          }
+        }
         live[k] = found >= 0;
         pos[d][k] = found;
       }
