@@ -50,10 +50,12 @@ struct AggProgram {
 };
 
 // ---------------------------------------------------------------- aggregates
-struct Partial {
-  long long v[TQP_MAX_AGGS];
+template <int N>
+struct PartialT {
+  long long v[N];
   int c;  // segment heads inside the span
 };
+using Partial = PartialT<TQP_MAX_AGGS>;  // storage layout of the look-back payloads
 
 __device__ __forceinline__ long long agg_identity(int op) {
   return op == TQP_MIN ? LLONG_MAX : (op == TQP_MAX ? LLONG_MIN : 0ll);
@@ -67,17 +69,20 @@ __device__ __forceinline__ long long agg_fold(int op, long long acc, long long x
   }
 }
 
-__device__ __forceinline__ void partial_identity(Partial& p, const AggProgram& P) {
+template <int N>
+__device__ __forceinline__ void partial_identity(PartialT<N>& p, const AggProgram& P) {
 #pragma unroll
-  for (int a = 0; a < TQP_MAX_AGGS; ++a) p.v[a] = (a < P.naggs) ? agg_identity(P.op[a]) : 0;
+  for (int a = 0; a < N; ++a) p.v[a] = (a < P.naggs) ? agg_identity(P.op[a]) : 0;
   p.c = 0;
 }
 
 // left (+) right of the segmented reduction: a head inside `right` cuts off `left`.
-__device__ __forceinline__ Partial partial_combine(const Partial& l, const Partial& r, const AggProgram& P) {
-  Partial o;
+template <int N>
+__device__ __forceinline__ PartialT<N> partial_combine(const PartialT<N>& l, const PartialT<N>& r,
+                                                      const AggProgram& P) {
+  PartialT<N> o;
 #pragma unroll
-  for (int a = 0; a < TQP_MAX_AGGS; ++a)
+  for (int a = 0; a < N; ++a)
     o.v[a] = (r.c > 0 || a >= P.naggs) ? r.v[a] : agg_fold(P.op[a], l.v[a], r.v[a]);
   o.c = l.c + r.c;
   return o;
@@ -86,20 +91,24 @@ __device__ __forceinline__ Partial partial_combine(const Partial& l, const Parti
 // Expression e at row: product of (mul * val + add) over its terms, mod 2^64.
 __device__ __forceinline__ long long eval_expr(const AggProgram& P, int e, int64_t row) {
   unsigned long long v = 1;
-  for (int t = 0; t < P.nterms[e]; ++t) {
-    int c = P.tcol[e][t];
-    long long x = load_as_i64(P.val[c], P.vdt[c], row);
-    v *= (unsigned long long)P.tmul[e][t] * (unsigned long long)x + (unsigned long long)P.tadd[e][t];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    if (t < P.nterms[e]) {
+      int c = P.tcol[e][t];
+      long long x = load_as_i64(P.val[c], P.vdt[c], row);
+      v *= (unsigned long long)P.tmul[e][t] * (unsigned long long)x + (unsigned long long)P.tadd[e][t];
+    }
   }
   return (long long)v;
 }
 
-__device__ __forceinline__ void fold_row(Partial& p, const AggProgram& P, int64_t row) {
+template <int N>
+__device__ __forceinline__ void fold_row(PartialT<N>& p, const AggProgram& P, int64_t row) {
   long long ev[TQP_MAX_EXPRS];
 #pragma unroll
   for (int e = 0; e < TQP_MAX_EXPRS; ++e) ev[e] = (e < P.nexprs) ? eval_expr(P, e, row) : 0;
 #pragma unroll
-  for (int a = 0; a < TQP_MAX_AGGS; ++a) {
+  for (int a = 0; a < N; ++a) {
     if (a < P.naggs) {
       long long x = 1;
 #pragma unroll
@@ -110,10 +119,11 @@ __device__ __forceinline__ void fold_row(Partial& p, const AggProgram& P, int64_
   }
 }
 
-__device__ __forceinline__ Partial shfl_up_partial(const Partial& p, int d) {
-  Partial o;
+template <int N>
+__device__ __forceinline__ PartialT<N> shfl_up_partial(const PartialT<N>& p, int d) {
+  PartialT<N> o;
 #pragma unroll
-  for (int a = 0; a < TQP_MAX_AGGS; ++a) o.v[a] = __shfl_up_sync(0xffffffffu, p.v[a], d);
+  for (int a = 0; a < N; ++a) o.v[a] = __shfl_up_sync(0xffffffffu, p.v[a], d);
   o.c = __shfl_up_sync(0xffffffffu, p.c, d);
   return o;
 }
@@ -273,17 +283,19 @@ __global__ void gb_heavy_only_kernel(ReduceArgs a, int naggs) {
     write_group(a, naggs, i, a.heavy[i], a.heavy_acc + (size_t)i * naggs);
 }
 
-__device__ __forceinline__ void store_partial_relaxed(Partial* dst, const Partial& p, int naggs) {
+template <int N>
+__device__ __forceinline__ void store_partial_relaxed(Partial* dst, const PartialT<N>& p, int naggs) {
   unsigned long long* d = reinterpret_cast<unsigned long long*>(dst->v);
   for (int a = 0; a < naggs; ++a) st_volatile_u64(d + a, (unsigned long long)p.v[a]);
   st_volatile_u32(reinterpret_cast<uint32_t*>(&dst->c), (uint32_t)p.c);
 }
 
-__device__ __forceinline__ Partial load_partial_relaxed(const Partial* src, const AggProgram& P) {
-  Partial p;
+template <int N>
+__device__ __forceinline__ PartialT<N> load_partial_relaxed(const Partial* src, const AggProgram& P) {
+  PartialT<N> p;
   const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src->v);
 #pragma unroll
-  for (int a = 0; a < TQP_MAX_AGGS; ++a) p.v[a] = (a < P.naggs) ? (long long)ld_volatile_u64(s + a) : 0;
+  for (int a = 0; a < N; ++a) p.v[a] = (a < P.naggs) ? (long long)ld_volatile_u64(s + a) : 0;
   p.c = (int)ld_volatile_u32(reinterpret_cast<const uint32_t*>(&src->c));
   return p;
 }
@@ -297,12 +309,16 @@ __device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <typename K, int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggProgram P) {
+template <typename K, int THREADS, int ITEMS, int NAGG>
+__global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggProgram Pg) {
   constexpr int TILE = THREADS * ITEMS;
   constexpr int WARPS = THREADS / 32;
-  __shared__ Partial s_warp[WARPS];
-  __shared__ Partial s_tile_excl;
+  using PT = PartialT<NAGG>;
+  __shared__ PT s_warp[WARPS];
+  __shared__ PT s_tile_excl;
+  __shared__ AggProgram P;  // the program in shared memory: indexed by runtime values below
+  if (threadIdx.x == 0) P = Pg;
+  __syncthreads();
   __shared__ uint32_t s_tile;
   __shared__ int s_failed;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -334,7 +350,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
       key[k] = (p < nn) ? keys[p] : (K)0;
       if (p < nn && (p == 0 || key[k] != (k ? key[k - 1] : prev))) head |= 1u << k;
     }
-    Partial mine;
+    PT mine;
     partial_identity(mine, P);
     mine.c = __popc(head);
     {
@@ -345,28 +361,28 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
     }
 
     // ---- block exclusive segmented scan of the thread partials
-    Partial incl = mine;
+    PT incl = mine;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      Partial up = shfl_up_partial(incl, d);
+      PT up = shfl_up_partial(incl, d);
       if (lane >= d) incl = partial_combine(up, incl, P);
     }
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    Partial wexcl;
+    PT wexcl;
     partial_identity(wexcl, P);
     for (int w = 0; w < warp; ++w) wexcl = partial_combine(wexcl, s_warp[w], P);
-    Partial texcl = shfl_up_partial(incl, 1);
+    PT texcl = shfl_up_partial(incl, 1);
     if (lane == 0) partial_identity(texcl, P);
-    Partial thread_excl = partial_combine(wexcl, texcl, P);
+    PT thread_excl = partial_combine(wexcl, texcl, P);
 
     // ---- tile look-back (thread 0)
     if (threadIdx.x == 0) {
-      Partial tile_agg;
+      PT tile_agg;
       partial_identity(tile_agg, P);
       for (int w = 0; w < WARPS; ++w) tile_agg = partial_combine(tile_agg, s_warp[w], P);
       const bool inject = ((long long)tile == g_unpublished_tile);
-      Partial acc;
+      PT acc;
       partial_identity(acc, P);
       bool failed = false;
       if (tile == 0) {
@@ -391,7 +407,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
             if (sleep_ns < 1024) sleep_ns <<= 1;
           }
           if (f == 3u) { failed = true; break; }
-          Partial pt = load_partial_relaxed(f == 2u ? &a.pre_payload[t] : &a.agg_payload[t], P);
+          PT pt = load_partial_relaxed<NAGG>(f == 2u ? &a.pre_payload[t] : &a.agg_payload[t], P);
           acc = partial_combine(pt, acc, P);
           if (f == 2u) break;
         }
@@ -417,12 +433,12 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
     }
     __syncthreads();
     const int tile_failed = s_failed;
-    Partial in = partial_combine(s_tile_excl, thread_excl, P);
+    PT in = partial_combine(s_tile_excl, thread_excl, P);
     __syncthreads();
     if (tile_failed) continue;
 
     // ---- pass 2: finish every segment whose last row this thread holds
-    Partial run = in;
+    PT run = in;
     long long seg = (long long)in.c - 1;
     K next_after = 0;
     if (base + ITEMS < nn) next_after = keys[base + ITEMS];
@@ -433,7 +449,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
         if (head & (1u << k)) {
           ++seg;
 #pragma unroll
-          for (int q = 0; q < TQP_MAX_AGGS; ++q) run.v[q] = (q < P.naggs) ? agg_identity(P.op[q]) : 0;
+          for (int q = 0; q < NAGG; ++q) run.v[q] = (q < P.naggs) ? agg_identity(P.op[q]) : 0;
           if (nh) {
             // heavy keys between the previous group's key and this one go just before it
             int64_t hi_i = heavy_lower(a.heavy, nh, (unsigned long long)key[k]);

@@ -219,6 +219,23 @@ GroupWs carve_group(Carver& c, int64_t n, int word_bytes) {
   return w;
 }
 
+// Reduce-by-key launch, specialised on the number of aggregates carried.
+template <typename K, int NAGG>
+void launch_reduce_n(const ReduceArgs& r, const AggProgram& P, uint32_t tiles, cudaStream_t s) {
+  auto k = gb_reduce_kernel<K, kReduceThreads, kReduceItems, NAGG>;
+  k<<<persistent_grid(k, kReduceThreads, 0, tiles), kReduceThreads, 0, s>>>(r, P);
+  note_launch();
+}
+
+template <typename K>
+void launch_reduce(const ReduceArgs& r, const AggProgram& P, uint32_t tiles, cudaStream_t s) {
+  prof_mark(4, true, s);
+  if (P.naggs <= 2) launch_reduce_n<K, 2>(r, P, tiles, s);
+  else if (P.naggs <= 4) launch_reduce_n<K, 4>(r, P, tiles, s);
+  else launch_reduce_n<K, TQP_MAX_AGGS>(r, P, tiles, s);
+  prof_mark(4, false, s);
+}
+
 tqp_status build_agg_program(const tqp_col* vals, int nvals, const tqp_expr* exprs, int nexprs,
                              const tqp_agg* aggs, int naggs, AggProgram* P, bool have_rows) {
   if (nvals < 0 || nvals > TQP_MAX_VALS || nexprs < 0 || nexprs > TQP_MAX_EXPRS || naggs < 1 ||
@@ -294,15 +311,9 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
   r.d_nheavy = nullptr;
   r.heavy_acc = nullptr;
   if (word_bytes == 4) {
-    auto k = gb_reduce_kernel<uint32_t, kReduceThreads, kReduceItems>;
-    prof_mark(4, true, s);
-    k<<<persistent_grid(k, kReduceThreads, 0, w.tiles), kReduceThreads, 0, s>>>(r, P); note_launch();
-    prof_mark(4, false, s);
+    launch_reduce<uint32_t>(r, P, w.tiles, s);
   } else {
-    auto k = gb_reduce_kernel<unsigned long long, kReduceThreads, kReduceItems>;
-    prof_mark(4, true, s);
-    k<<<persistent_grid(k, kReduceThreads, 0, w.tiles), kReduceThreads, 0, s>>>(r, P); note_launch();
-    prof_mark(4, false, s);
+    launch_reduce<unsigned long long>(r, P, w.tiles, s);
   }
   return last_launch();
 }
@@ -1152,12 +1163,7 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   r.heavy = heavy;
   r.d_nheavy = &lp->nheavy;
   r.heavy_acc = heavy_acc;
-  {
-    auto k = gb_reduce_kernel<unsigned long long, kReduceThreads, kReduceItems>;
-    prof_mark(4, true, s);
-    k<<<persistent_grid(k, kReduceThreads, 0, rtiles), kReduceThreads, 0, s>>>(r, P); note_launch();
-    prof_mark(4, false, s);
-  }
+  launch_reduce<unsigned long long>(r, P, (uint32_t)rtiles, s);
   gb_heavy_only_kernel<<<(kMaxHeavy + 255) / 256, 256, 0, s>>>(r, naggs); note_launch();
   if (d_model_out) TQP_CUDA(cudaMemcpyAsync(d_model_out, model, sizeof(tqp_cdf_model), cudaMemcpyDeviceToDevice, s));
   return last_launch();

@@ -130,3 +130,22 @@ def test_star_scaled(G):
                  gd.make_table(rec["dim2"], 1_500_000))
     compare(got, want)
     assert tqp.tqp_status_poll() == tqp.OK
+
+
+def test_star_crowded_directory_cells(G):
+    """Dimension keys clustered in a tiny part of their range (plus far
+    outliers), so one directory cell holds hundreds of keys: the in-cell
+    bound search must find every one."""
+    tqp, Q, gd = G
+    r = np.random.default_rng(12)
+    key = np.concatenate([np.arange(-500, 500), [2**30, -2**30, 2**31 - 1]]).astype(np.int32)
+    key = key[r.permutation(len(key))]
+    m = len(key)
+    dim = {"key": key, "region": r.integers(0, 25, m).astype(np.int8),
+           "price": r.integers(100, 10**6, m).astype(np.int64)}
+    fk = r.choice(np.concatenate([key, np.arange(600, 700, dtype=np.int32)]), 500_000).astype(np.int32)
+    fact = {"fk": fk}
+    want = pl.q14(fact, dim)
+    cu = lambda t: {k: torch.from_numpy(v).cuda() for k, v in t.items()}
+    compare(Q.q14(cu(fact), cu(dim)), want)
+    assert tqp.tqp_status_poll() == tqp.OK
