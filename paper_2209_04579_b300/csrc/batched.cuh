@@ -29,7 +29,62 @@ struct BatchProb {
   long long dim_off;   // first row in the concatenated dimension arrays
   long long tile_off;  // first global probe tile
   long long slot_off;  // first accumulator slot
+  long long cell_off;  // first directory entry of this problem
+  long long word_off;  // first bitmap word of this problem
+  int log2cells;       // directory size bound (2^log2cells cells)
+  int pad_;
 };
+
+// Per-problem key directory (as for a star dimension): cells of 2^bshift key
+// values over [umin, umax]; dir[c] = first position of the problem's sorted
+// keys in cell c or later; bit c marks a non-empty cell.
+struct ProbDir {
+  unsigned umin, umax;
+  int bshift;
+  int ncells;  // 0: no dimension rows
+};
+
+__global__ void batch_dir_plan_kernel(const BatchProb* probs, int nprob, const int32_t* key32, ProbDir* pd) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  const BatchProb& P = probs[p];
+  ProbDir r;
+  if (P.n_dim == 0) {
+    r.umin = 1;
+    r.umax = 0;
+    r.bshift = 0;
+    r.ncells = 0;
+  } else {
+    r.umin = (unsigned)key32[P.dim_off] ^ 0x80000000u;
+    r.umax = (unsigned)key32[P.dim_off + P.n_dim - 1] ^ 0x80000000u;
+    unsigned span = r.umax - r.umin;
+    int bits = span ? 32 - __clz((int)span) : 0;
+    r.bshift = bits > P.log2cells ? bits - P.log2cells : 0;
+    r.ncells = (int)(span >> r.bshift) + 1;
+  }
+  pd[p] = r;
+}
+
+__global__ void batch_dir_fill_kernel(const BatchProb* probs, const long long* dim_off, int nprob, long long total,
+                                      const unsigned long long* skey, const int32_t* key32, const ProbDir* pd,
+                                      int* dir, uint32_t* bitmap) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x; pos < total; pos += stride) {
+    const int p = (int)(skey[pos] >> 32);
+    const BatchProb& P = probs[p];
+    const ProbDir r = pd[p];
+    const long long j = pos - P.dim_off;
+    int* d = dir + P.cell_off;
+    uint32_t* bm = bitmap + P.word_off;
+    int c = (int)((((unsigned)key32[pos] ^ 0x80000000u) - r.umin) >> r.bshift);
+    int prev = j ? (int)((((unsigned)key32[pos - 1] ^ 0x80000000u) - r.umin) >> r.bshift) : -1;
+    if (c != prev) {
+      for (int h = prev + 1; h <= c; ++h) d[h] = (int)j;
+      atomicOr(&bm[c >> 5], 1u << (c & 31));
+    }
+    if (j == P.n_dim - 1) d[c + 1] = (int)P.n_dim;
+  }
+}
 
 struct UploadChunk {
   int first, count;
@@ -229,6 +284,9 @@ __device__ __forceinline__ void batch_fold(long long* slot, const BatchShape& S,
 }
 
 struct BatchProbeArgs {
+  const ProbDir* pdir;
+  const int* dir;
+  const uint32_t* bitmap;
   const BatchProb* probs;
   const long long* tile_off;
   int nprob;
@@ -269,7 +327,9 @@ __global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, 
     }
     const int32_t* keys = a.key32 + P.dim_off;
     const int32_t* ranks = a.rank_sorted + P.dim_off;
-    const long long nd = P.n_dim;
+    const ProbDir pd = a.pdir[p];
+    const int* dir = a.dir + P.cell_off;
+    const uint32_t* bm = a.bitmap + P.word_off;
 #pragma unroll 1
     for (int k = 0; k < ITEMS; ++k) {
       const long long row = r0 + (long long)k * THREADS + threadIdx.x;
@@ -279,8 +339,19 @@ __global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, 
         keep = keep && compare(load_as_i64(P.fact[S.pcol[q]], S.fact_dt[S.pcol[q]], row), S.pop[q], S.plit[q]);
       if (!keep) continue;
       int32_t x = static_cast<const int32_t*>(P.fact[S.fk_col])[row];
-      int64_t l = lower_bound_dev(keys, nd, x);
-      if (l >= nd || keys[l] != x) continue;
+      const unsigned u = (unsigned)x ^ 0x80000000u;
+      if (u < pd.umin || u > pd.umax) continue;
+      const int c = (int)((u - pd.umin) >> pd.bshift);
+      if (!((__ldg(&bm[c >> 5]) >> (c & 31)) & 1u)) continue;
+      int l = __ldg(&dir[c]);
+      const int hi = __ldg(&dir[c + 1]);
+      int h = hi;
+      while (h - l > 4) {  // first key >= x lies in [l, h]
+        int mid = (l + h) >> 1;
+        if (keys[mid] < x) l = mid + 1; else h = mid;
+      }
+      while (l < hi && keys[l] < x) ++l;
+      if (l >= hi || keys[l] != x) continue;
       long long g = ranks[l];
       long long ev[TQP_MAX_EXPRS];
 #pragma unroll

@@ -104,16 +104,12 @@ __device__ __forceinline__ long long eval_expr(const AggProgram& P, int e, int64
 
 template <int N>
 __device__ __forceinline__ void fold_row(PartialT<N>& p, const AggProgram& P, int64_t row) {
-  long long ev[TQP_MAX_EXPRS];
-#pragma unroll
-  for (int e = 0; e < TQP_MAX_EXPRS; ++e) ev[e] = (e < P.nexprs) ? eval_expr(P, e, row) : 0;
+  // each aggregate evaluates its own expression (a value shared by several
+  // aggregates is re-read from L1)
 #pragma unroll
   for (int a = 0; a < N; ++a) {
     if (a < P.naggs) {
-      long long x = 1;
-#pragma unroll
-      for (int e = 0; e < TQP_MAX_EXPRS; ++e)
-        if (P.op[a] != TQP_COUNT && P.expr[a] == e) x = ev[e];
+      long long x = P.op[a] == TQP_COUNT ? 1 : eval_expr(P, P.expr[a], row);
       p.v[a] = agg_fold(P.op[a], p.v[a], x);
     }
   }
@@ -261,17 +257,34 @@ __device__ __forceinline__ int64_t heavy_lower(const unsigned long long* h, int 
   return lo;
 }
 
-// Writes group g: key columns decoded from the packed word, aggregates.
-__device__ __forceinline__ void write_group(const ReduceArgs& a, int naggs, long long g, unsigned long long u,
-                                            const long long* v) {
-  if (g < 0 || g >= a.cap) return;
-  for (int j = 0; j < a.ks.nkeys; ++j) {
-    int b = a.plan->bits[j];
+// Writes the key columns of group g, decoded from the packed word.
+__device__ __forceinline__ void write_group_keys(const KeySet& ks, const GroupPlan* plan, long long g,
+                                                 unsigned long long u) {
+  for (int j = 0; j < ks.nkeys; ++j) {
+    int b = plan->bits[j];
     unsigned long long m = b >= 64 ? ~0ull : ((1ull << b) - 1);
-    long long kv = (long long)(((u >> a.plan->shift[j]) & m) + (unsigned long long)a.plan->kmin[j]);
-    store_from_i64(a.ks.out[j], a.ks.dt[j], g, kv);
+    long long kv = (long long)(((u >> plan->shift[j]) & m) + (unsigned long long)plan->kmin[j]);
+    store_from_i64(ks.out[j], ks.dt[j], g, kv);
   }
+}
+
+// Writes group g: key columns and aggregates (from memory).
+__device__ __forceinline__ void write_group(const ReduceArgs& a, const KeySet& ks, int naggs, long long g,
+                                            unsigned long long u, const long long* v) {
+  if (g < 0 || g >= a.cap) return;
+  write_group_keys(ks, a.plan, g, u);
   for (int q = 0; q < naggs; ++q) a.out_aggs[g * naggs + q] = v[q];
+}
+
+// Writes group g: key columns and aggregates (from registers).
+template <int N>
+__device__ __forceinline__ void write_group_regs(const ReduceArgs& a, const KeySet& ks, int naggs, long long g,
+                                                 unsigned long long u, const PartialT<N>& r) {
+  if (g < 0 || g >= a.cap) return;
+  write_group_keys(ks, a.plan, g, u);
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+    if (q < naggs) a.out_aggs[g * naggs + q] = r.v[q];
 }
 
 // Heavy groups when no row went through the sort: group i at position i
@@ -280,13 +293,15 @@ __global__ void gb_heavy_only_kernel(ReduceArgs a, int naggs) {
   if (a.plan->unsupported || clamp_n(a.n_max, a.d_n) > 0) return;
   const int nh = a.d_nheavy ? *a.d_nheavy : 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nh; i += gridDim.x * blockDim.x)
-    write_group(a, naggs, i, a.heavy[i], a.heavy_acc + (size_t)i * naggs);
+    write_group(a, a.ks, naggs, i, a.heavy[i], a.heavy_acc + (size_t)i * naggs);
 }
 
 template <int N>
 __device__ __forceinline__ void store_partial_relaxed(Partial* dst, const PartialT<N>& p, int naggs) {
   unsigned long long* d = reinterpret_cast<unsigned long long*>(dst->v);
-  for (int a = 0; a < naggs; ++a) st_volatile_u64(d + a, (unsigned long long)p.v[a]);
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+    if (a < naggs) st_volatile_u64(d + a, (unsigned long long)p.v[a]);
   st_volatile_u32(reinterpret_cast<uint32_t*>(&dst->c), (uint32_t)p.c);
 }
 
@@ -316,8 +331,12 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
   using PT = PartialT<NAGG>;
   __shared__ PT s_warp[WARPS];
   __shared__ PT s_tile_excl;
-  __shared__ AggProgram P;  // the program in shared memory: indexed by runtime values below
-  if (threadIdx.x == 0) P = Pg;
+  __shared__ AggProgram P;  // the program and the key set in shared memory: indexed by runtime values below
+  __shared__ KeySet s_ks;
+  if (threadIdx.x == 0) {
+    P = Pg;
+    s_ks = a.ks;
+  }
   __syncthreads();
   __shared__ uint32_t s_tile;
   __shared__ int s_failed;
@@ -442,7 +461,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
     long long seg = (long long)in.c - 1;
     K next_after = 0;
     if (base + ITEMS < nn) next_after = keys[base + ITEMS];
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < ITEMS; ++k) {
       int64_t p = base + k;
       if (p < nn) {
@@ -455,7 +474,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
             int64_t hi_i = heavy_lower(a.heavy, nh, (unsigned long long)key[k]);
             int64_t lo_i = p == 0 ? 0 : heavy_lower(a.heavy, nh, (unsigned long long)(k ? key[k - 1] : prev));
             for (int64_t i = lo_i; i < hi_i; ++i)
-              write_group(a, P.naggs, seg + i, a.heavy[i], a.heavy_acc + (size_t)i * P.naggs);
+              write_group(a, s_ks, P.naggs, seg + i, a.heavy[i], a.heavy_acc + (size_t)i * P.naggs);
           }
         }
         fold_row(run, P, a.rows[p]);
@@ -463,11 +482,11 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
         bool last = (p == nn - 1) || (nk != key[k]);
         if (last && seg >= 0) {
           long long hr = nh ? heavy_lower(a.heavy, nh, (unsigned long long)key[k]) : 0;
-          write_group(a, P.naggs, seg + hr, (unsigned long long)key[k], run.v);
+          write_group_regs(a, s_ks, P.naggs, seg + hr, (unsigned long long)key[k], run);
           if (nh && p == nn - 1) {
             // heavy keys above the last group's key
             for (int64_t i = hr; i < nh; ++i)
-              write_group(a, P.naggs, seg + 1 + i, a.heavy[i], a.heavy_acc + (size_t)i * P.naggs);
+              write_group(a, s_ks, P.naggs, seg + 1 + i, a.heavy[i], a.heavy_acc + (size_t)i * P.naggs);
           }
         }
       }

@@ -1220,8 +1220,9 @@ tqp_status tqp_star_agg_batched(const tqp_batch_shape* shape, const tqp_problem*
   }
   // ---- host-side layout: offsets of dimension rows, probe tiles and slots
   const int TILE = 256 * items;
-  std::vector<long long> dim_off(nprob), tile_off(nprob), slot_off(nprob);
-  long long total_dim = 0, total_tiles = 0, total_slots = 0;
+  std::vector<long long> dim_off(nprob), tile_off(nprob), slot_off(nprob), cell_off(nprob), word_off(nprob);
+  std::vector<int> log2cells(nprob);
+  long long total_dim = 0, total_tiles = 0, total_slots = 0, total_cells = 0, total_words = 0;
   const long long domain = sh.group_dtype == TQP_I8 ? 256 : sh.group_dtype == TQP_I16 ? 65536 : (1ll << 40);
   for (int p = 0; p < nprob; ++p) {
     const tqp_problem& P = probs[p];
@@ -1232,6 +1233,13 @@ tqp_status tqp_star_agg_batched(const tqp_batch_shape* shape, const tqp_problem*
     total_dim += P.n_dim;
     total_tiles += (P.n_fact + TILE - 1) / TILE;
     total_slots += P.n_dim < domain ? P.n_dim : domain;
+    int l2 = 1;
+    while (l2 < 30 && (1ll << l2) < 2 * P.n_dim) ++l2;
+    log2cells[p] = l2;
+    cell_off[p] = total_cells;
+    word_off[p] = total_words;
+    total_cells += (1ll << l2) + 2;
+    total_words += (1ll << l2) / 32 + 1;
   }
   if (total_dim >= (1ll << 30) || total_tiles >= (1ll << 32)) return TQP_ERR_INVALID;
   const int nacc = S.naggs + 1;
@@ -1262,6 +1270,9 @@ tqp_status tqp_star_agg_batched(const tqp_batch_shape* shape, const tqp_problem*
   int* flag = c.take<int>(1);
   long long* acc = c.take<long long>((size_t)(total_slots > 0 ? total_slots : 1) * nacc);
   uint32_t* queue = c.take<uint32_t>(1);
+  ProbDir* pdir = c.take<ProbDir>(nprob);
+  int* dir = c.take<int>((size_t)total_cells);
+  uint32_t* bitmap = c.take<uint32_t>((size_t)total_words);
   if (!ws) {
     *ws_bytes = c.off;
     return TQP_OK;
@@ -1292,6 +1303,9 @@ tqp_status tqp_star_agg_batched(const tqp_batch_shape* shape, const tqp_problem*
       b.dim_off = dim_off[first + i];
       b.tile_off = tile_off[first + i];
       b.slot_off = slot_off[first + i];
+      b.cell_off = cell_off[first + i];
+      b.word_off = word_off[first + i];
+      b.log2cells = log2cells[first + i];
     }
     batch_upload_kernel<<<1, kUploadChunk, 0, s>>>(ch, dprobs); note_launch();
   }
@@ -1330,9 +1344,19 @@ tqp_status tqp_star_agg_batched(const tqp_batch_shape* shape, const tqp_problem*
                                                                        rank_of_row, key32, rank_sorted, flag);
     note_launch();
   }
+  batch_dir_plan_kernel<<<(nprob + 255) / 256, 256, 0, s>>>(dprobs, nprob, key32, pdir); note_launch();
+  TQP_CUDA(cudaMemsetAsync(bitmap, 0, (size_t)total_words * sizeof(uint32_t), s));
+  if (total_dim > 0) {
+    batch_dir_fill_kernel<<<stride_grid(total_dim, 256), 256, 0, s>>>(dprobs, d_dim_off, nprob, total_dim, skey,
+                                                                      key32, pdir, dir, bitmap);
+    note_launch();
+  }
   batch_init_acc_kernel<<<stride_grid(total_slots * nacc, 256, 4), 256, 0, s>>>(S, acc, total_slots); note_launch();
   TQP_CUDA(cudaMemsetAsync(queue, 0, 4, s));
   BatchProbeArgs pa;
+  pa.pdir = pdir;
+  pa.dir = dir;
+  pa.bitmap = bitmap;
   pa.probs = dprobs;
   pa.tile_off = d_tile_off;
   pa.nprob = nprob;
