@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = clamp_n(a.n_max, a.d_n);
   const K* keys = static_cast<const K*>(a.keys);
+  const int32_t* rows = a.rows;  // null: the value columns are already in sorted order
   const bool unsupported = a.plan->unsupported != 0;
   const long long limit = g_spin_limit;
   const int nh = (a.heavy && a.d_nheavy) ? *a.d_nheavy : 0;
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
       int last_head = head ? (31 - __clz(head)) : 0;
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k)
-        if (k >= last_head && base + k < nn) fold_row(mine, P, a.rows[base + k]);
+        if (k >= last_head && base + k < nn) fold_row(mine, P, rows ? rows[base + k] : base + k);
     }
 
     // ---- block exclusive segmented scan of the thread partials
@@ -477,7 +478,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
               write_group(a, s_ks, P.naggs, seg + i, a.heavy[i], a.heavy_acc + (size_t)i * P.naggs);
           }
         }
-        fold_row(run, P, a.rows[p]);
+        fold_row(run, P, rows ? rows[p] : p);
         K nk = (k + 1 < ITEMS) ? key[k + 1] : next_after;
         bool last = (p == nn - 1) || (nk != key[k]);
         if (last && seg >= 0) {

@@ -190,6 +190,7 @@ constexpr int kReduceThreads = 256;
 constexpr int kReduceItems = 8;
 
 struct GroupWs {
+  void* gathered[TQP_MAX_VALS];  // value columns in sorted order (large inputs)
   GroupPlan* plan;
   void* packed;
   int32_t* rows;
@@ -202,10 +203,18 @@ struct GroupWs {
   uint32_t tiles;
 };
 
-GroupWs carve_group(Carver& c, int64_t n, int word_bytes) {
+// From this many rows on, the value columns are gathered into sorted order
+// (one streaming gather kernel with many loads in flight) before the reduce,
+// which then reads them sequentially instead of chasing row ids.
+constexpr int64_t kPregatherRows = 1 << 22;
+
+GroupWs carve_group(Carver& c, int64_t n, int word_bytes, const AggProgram* P = nullptr) {
   GroupWs w;
+  std::memset(w.gathered, 0, sizeof(w.gathered));
   w.plan = c.take<GroupPlan>(1);
   size_t nn = (size_t)(n > 0 ? n : 1);
+  if (P && n >= kPregatherRows)
+    for (int v = 0; v < P->nvals; ++v) w.gathered[v] = c.take<char>(nn * dtype_bytes(P->vdt[v]));
   w.packed = c.take<char>(nn * word_bytes);
   w.rows = c.take<int32_t>(nn);
   w.sorted = c.take<char>(nn * word_bytes);
@@ -234,6 +243,33 @@ void launch_reduce(const ReduceArgs& r, const AggProgram& P, uint32_t tiles, cud
   else if (P.naggs <= 4) launch_reduce_n<K, 4>(r, P, tiles, s);
   else launch_reduce_n<K, TQP_MAX_AGGS>(r, P, tiles, s);
   prof_mark(4, false, s);
+}
+
+// Gathers every value column into the order of `rows` (n or *d_n rows);
+// returns the program reading the gathered columns.
+AggProgram pregather_values(const AggProgram& P, void* const* dst, const int32_t* rows, int64_t n,
+                            const int64_t* d_n, cudaStream_t s) {
+  AggProgram Q = P;
+  const int g = stride_grid(n, 256);
+  for (int v = 0; v < P.nvals; ++v) {
+    switch (P.vdt[v]) {
+      case TQP_I8:
+        gather_kernel<int8_t><<<g, 256, 0, s>>>((const int8_t*)P.val[v], rows, n, d_n, (int8_t*)dst[v]);
+        break;
+      case TQP_I16:
+        gather_kernel<int16_t><<<g, 256, 0, s>>>((const int16_t*)P.val[v], rows, n, d_n, (int16_t*)dst[v]);
+        break;
+      case TQP_I32:
+        gather_kernel<int32_t><<<g, 256, 0, s>>>((const int32_t*)P.val[v], rows, n, d_n, (int32_t*)dst[v]);
+        break;
+      default:
+        gather_kernel<long long><<<g, 256, 0, s>>>((const long long*)P.val[v], rows, n, d_n, (long long*)dst[v]);
+        break;
+    }
+    note_launch();
+    Q.val[v] = dst[v];
+  }
+  return Q;
 }
 
 tqp_status build_agg_program(const tqp_col* vals, int nvals, const tqp_expr* exprs, int nexprs,
@@ -310,10 +346,15 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
   r.heavy = nullptr;
   r.d_nheavy = nullptr;
   r.heavy_acc = nullptr;
+  AggProgram Pr = P;
+  if (w.gathered[0] || P.nvals == 0) {
+    if (P.nvals) Pr = pregather_values(P, w.gathered, w.sorted_rows, n, d_n, s);
+    r.rows = nullptr;
+  }
   if (word_bytes == 4) {
-    launch_reduce<uint32_t>(r, P, w.tiles, s);
+    launch_reduce<uint32_t>(r, Pr, w.tiles, s);
   } else {
-    launch_reduce<unsigned long long>(r, P, w.tiles, s);
+    launch_reduce<unsigned long long>(r, Pr, w.tiles, s);
   }
   return last_launch();
 }
@@ -575,7 +616,7 @@ tqp_status tqp_groupby_agg(const tqp_col* keys, int nkeys, const tqp_col* vals, 
   if (st != TQP_OK) return st;
   const int word_bytes = declared_bits <= 32 ? 4 : 8;
   Carver c(ws);
-  GroupWs gw = carve_group(c, n, word_bytes);
+  GroupWs gw = carve_group(c, n, word_bytes, &P);
   if (!ws) {
     *ws_bytes = c.off;
     return TQP_OK;
@@ -1041,6 +1082,9 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   uint32_t* rctrl = c.take<uint32_t>(1 + (size_t)(rtiles > 0 ? rtiles : 1));
   Partial* ragg = c.take<Partial>((size_t)(rtiles > 0 ? rtiles : 1));
   Partial* rpre = c.take<Partial>((size_t)(rtiles > 0 ? rtiles : 1));
+  void* lgath[TQP_MAX_VALS] = {};
+  if (n >= kPregatherRows)
+    for (int v = 0; v < P.nvals; ++v) lgath[v] = c.take<char>(nn * dtype_bytes(P.vdt[v]));
   if (!ws) {
     *ws_bytes = c.off;
     return TQP_OK;
@@ -1163,7 +1207,12 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   r.heavy = heavy;
   r.d_nheavy = &lp->nheavy;
   r.heavy_acc = heavy_acc;
-  launch_reduce<unsigned long long>(r, P, (uint32_t)rtiles, s);
+  AggProgram Pr = P;
+  if (lgath[0] || P.nvals == 0) {
+    if (P.nvals) Pr = pregather_values(P, lgath, lrow, n, light_n, s);
+    r.rows = nullptr;
+  }
+  launch_reduce<unsigned long long>(r, Pr, (uint32_t)rtiles, s);
   gb_heavy_only_kernel<<<(kMaxHeavy + 255) / 256, 256, 0, s>>>(r, naggs); note_launch();
   if (d_model_out) TQP_CUDA(cudaMemcpyAsync(d_model_out, model, sizeof(tqp_cdf_model), cudaMemcpyDeviceToDevice, s));
   return last_launch();
