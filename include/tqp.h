@@ -319,7 +319,7 @@ tqp_status tqp_cdf_train(const float* d_x, const float* d_y, int64_t n, tqp_cdf_
 
 typedef struct {
   int32_t sample;  /* keys sampled (strided) to train on; power of two in [1024, 2^20] */
-  int32_t buckets; /* learned buckets B (power of two <= 65536); 0 = from n */
+  int32_t buckets; /* learned buckets B (power of two <= 2^17); 0 = from n */
   int32_t train;   /* 1 = train the network; 0 = keep the identity CDF F(x) = x */
   int32_t heavy;   /* 1 = aggregate the sample's frequent keys directly */
   tqp_train_cfg train_cfg;
@@ -444,7 +444,8 @@ const char* tqp_status_string(tqp_status s);
  * (cudaEvent_t handles passed as void*; NULL clears).  Classes: 1 = fused
  * star probe, 2 = radix sort passes (from the first to the last pass of a
  * sort), 3 = filter, 4 = group-by reduce, 5 = join probe, 6 = batched probe,
- * 7 = learned bucket sort, 8 = learned partition scatter.  Records are
+ * 7 = learned bucket sort (block kernel), 8 = learned partition scatter,
+ * 9 = learned bucket sort (warp kernel).  Records are
  * external, so under stream capture they become event nodes of the graph. */
 int64_t tqp_debug_launch_count(void);
 tqp_status tqp_profile_events(int kernel_class, void* start_event, void* stop_event);

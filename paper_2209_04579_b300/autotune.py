@@ -93,9 +93,9 @@ def tune_learned(run, rows, candidates=None, force=False):
         return int(cache[k]["best"]), cache[k]
     if candidates is None:
         base = 256
-        while base < 65536 and base * 2048 < rows:
+        while base < (1 << 17) and base * 512 < rows:
             base <<= 1
-        candidates = sorted({max(256, base // 2), base, min(65536, base * 2)})
+        candidates = sorted({max(256, base // 2), base, min(1 << 17, base * 2)})
     times, ref = {}, None
     for b in candidates:
         times[b] = _time(lambda b=b: run(b))

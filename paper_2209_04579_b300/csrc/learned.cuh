@@ -615,7 +615,10 @@ struct BucketSortArgs {
   unsigned long long* alt_p;    // scratch of the same size (global fallback)
   int32_t* alt_row;
   uint32_t* queue;
+  const uint32_t* big_flags;  // null, or: small buckets handled by the warp kernel unless flagged
 };
+
+__device__ __forceinline__ bool warp_bucket_size(long long m) { return m > 1 && m <= 1024; }
 
 __device__ __forceinline__ unsigned long long block_minmax_span(unsigned long long lo_in, unsigned long long hi_in,
                                                                 unsigned long long* s_red, unsigned long long* mn) {
@@ -665,6 +668,7 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
     const int64_t o0 = a.off[b], o1 = a.off[b + 1];
     const int64_t m = o1 - o0;
     if (m <= 1) continue;
+    if (a.big_flags && m <= kLocalCap && warp_bucket_size(m) && !a.big_flags[b]) continue;  // sorted by a warp
     if (m <= kLocalCap) {
       // ---- on-chip: load, find the key span, LSD over its bits, store
       unsigned long long* kA = kA0;
@@ -788,6 +792,117 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
       }
       __syncthreads();
     }
+  }
+}
+
+
+// ---------------------------------------------------------------- warp bucket sort
+// Small buckets (at most kWarpCap rows, key span below 2^48) are sorted by
+// one warp each: item i becomes the word ((key - bucket min) << 16 | i), the
+// words are LSD-sorted on their key bits in the warp's shared memory (the low
+// 16 bits only carry the original index back), and the rows are permuted by
+// the recovered indices.  No block barrier is involved.
+constexpr int kWarpCap = 1024;
+constexpr int kWarpItems = kWarpCap / 32;
+constexpr int kWarpSortWarps = 4;
+
+
+__global__ void __launch_bounds__(kWarpSortWarps * 32) lp_bucket_sort_warp_kernel(BucketSortArgs a, uint32_t* queue,
+                                                                                 uint32_t* big_flags) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long* wA = reinterpret_cast<unsigned long long*>(smem) + (size_t)warp * 2 * kWarpCap;
+  unsigned long long* wB = wA + kWarpCap;
+  unsigned* cnt = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned long long*>(smem) +
+                                              (size_t)kWarpSortWarps * 2 * kWarpCap) + warp * (kRadix + 1);
+  const int B = a.lp->B;
+  while (true) {
+    uint32_t b = 0;
+    if (lane == 0) b = atomicAdd(queue, 1u);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (b >= (uint32_t)B) break;
+    const long long o0 = a.off[b], m = (long long)a.off[b + 1] - o0;
+    if (m <= 1 || m > kWarpCap) continue;
+    unsigned long long lo = ~0ull, hi = 0;
+    for (int i = lane; i < m; i += 32) {
+      unsigned long long k = a.p[o0 + i];
+      lo = k < lo ? k : lo;
+      hi = k > hi ? k : hi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long x = __shfl_xor_sync(0xffffffffu, lo, o), y = __shfl_xor_sync(0xffffffffu, hi, o);
+      lo = x < lo ? x : lo;
+      hi = y > hi ? y : hi;
+    }
+    const unsigned long long span = hi - lo;
+    if (span == 0) continue;
+    if (span >> 48) {  // too wide for the packed words: leave it to the block kernel
+      if (lane == 0) big_flags[b] = 1;
+      continue;
+    }
+    for (int i = lane; i < m; i += 32) wA[i] = ((a.p[o0 + i] - lo) << 16) | (unsigned long long)i;
+    __syncwarp();
+    const int bits = 64 - __clzll((long long)span);
+    for (int sh = 16; sh < 16 + bits; sh += kRadixBits) {
+      for (int d = lane; d <= kRadix; d += 32) cnt[d] = 0;
+      __syncwarp();
+      unsigned dig[kWarpItems], rank[kWarpItems];
+#pragma unroll
+      for (int it = 0; it < kWarpItems; ++it) {
+        int i = it * 32 + lane;
+        dig[it] = i < m ? (unsigned)((wA[i] >> sh) & (kRadix - 1)) : kRadix;
+        unsigned peers = __match_any_sync(0xffffffffu, dig[it]);
+        int leader = 31 - __clz(peers);
+        unsigned before = __popc(peers & ((1u << lane) - 1));
+        unsigned base = cnt[dig[it]];
+        __syncwarp();
+        if (lane == leader) cnt[dig[it]] = base + __popc(peers);
+        __syncwarp();
+        rank[it] = base + before;
+      }
+      // exclusive scan of the 256 digit counts: 8 consecutive digits per lane
+      unsigned c8[8], run = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        c8[q] = cnt[lane * 8 + q];
+        run += c8[q];
+      }
+      unsigned incl = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      unsigned start = incl - run;
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        cnt[lane * 8 + q] = start;
+        start += c8[q];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int it = 0; it < kWarpItems; ++it) {
+        int i = it * 32 + lane;
+        if (i < m) wB[cnt[dig[it]] + rank[it]] = wA[i];
+      }
+      __syncwarp();
+      unsigned long long* t = wA; wA = wB; wB = t;
+    }
+    // permute: sorted key = lo + (word >> 16), row = rows[word & 0xffff];
+    // the buffer not holding the sorted words is free for the rows
+    int32_t* rtmp = reinterpret_cast<int32_t*>(wB);
+    for (int i = lane; i < m; i += 32) rtmp[i] = a.row[o0 + (int)(wA[i] & 0xffffull)];
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) {
+      a.p[o0 + i] = lo + (wA[i] >> 16);
+      a.row[o0 + i] = rtmp[i];
+    }
+    __syncwarp();
+    // restore this warp's buffer roles for the next bucket
+    wA = reinterpret_cast<unsigned long long*>(smem) + (size_t)warp * 2 * kWarpCap;
+    wB = wA + kWarpCap;
   }
 }
 

@@ -1032,7 +1032,7 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
     return TQP_ERR_INVALID;
   const int S = cfg->sample;
   if (S < 1024 || S > (1 << 20) || (S & (S - 1))) return TQP_ERR_INVALID;
-  if (cfg->buckets < 0 || cfg->buckets == 1 || cfg->buckets > 65536 || (cfg->buckets & (cfg->buckets - 1)))
+  if (cfg->buckets < 0 || cfg->buckets == 1 || cfg->buckets > (1 << 17) || (cfg->buckets & (cfg->buckets - 1)))
     return TQP_ERR_INVALID;
   if (cfg->train && !valid_train_cfg(&cfg->train_cfg)) return TQP_ERR_INVALID;
   if (cfg->init != 0 && cfg->init != 1) return TQP_ERR_INVALID;
@@ -1042,9 +1042,9 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   tqp_status st = build_agg_program(vals, nvals, exprs, nexprs, aggs, naggs, &P, n > 0);
   if (st != TQP_OK) return st;
   int B = cfg->buckets;
-  if (B == 0) {
+  if (B == 0) {  // about 512 rows per bucket: most buckets fit one warp's sort
     B = 256;
-    while (B < 65536 && (int64_t)B * 2048 < n) B <<= 1;
+    while (B < (1 << 17) && (int64_t)B * 512 < n) B <<= 1;
   }
   const int epochs = cfg->train ? cfg->train_cfg.epochs : 0;
   long long minc = (long long)((double)S * kLocalCap / (2.0 * (double)(n > 0 ? n : 1))) + 1;
@@ -1078,7 +1078,8 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   int32_t* lrow = c.take<int32_t>(nn);
   unsigned long long* apk = c.take<unsigned long long>(nn);
   int32_t* arow = c.take<int32_t>(nn);
-  uint32_t* queue = c.take<uint32_t>(1);
+  uint32_t* queue = c.take<uint32_t>(2);
+  uint32_t* big_flags = c.take<uint32_t>((size_t)B);
   uint32_t* rctrl = c.take<uint32_t>(1 + (size_t)(rtiles > 0 ? rtiles : 1));
   Partial* ragg = c.take<Partial>((size_t)(rtiles > 0 ? rtiles : 1));
   Partial* rpre = c.take<Partial>((size_t)(rtiles > 0 ? rtiles : 1));
@@ -1174,13 +1175,23 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
     ba.alt_p = apk;
     ba.alt_row = arow;
     ba.queue = queue;
+    ba.big_flags = big_flags;
     size_t smem = (size_t)kLocalCap * (8 + 8 + 4 + 4) + (size_t)kLocalWarps * (kRadix + 1) * 4 + kRadix * 4;
+    size_t wsmem = (size_t)kWarpSortWarps * (2 * kWarpCap * 8 + (kRadix + 1) * 4);
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(lp_bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(lp_bucket_sort_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
       attr = true;
     }
-    TQP_CUDA(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
+    TQP_CUDA(cudaMemsetAsync(queue, 0, 2 * sizeof(uint32_t), s));
+    TQP_CUDA(cudaMemsetAsync(big_flags, 0, (size_t)B * sizeof(uint32_t), s));
+    {
+      int gw = persistent_grid(lp_bucket_sort_warp_kernel, kWarpSortWarps * 32, wsmem, (B + kWarpSortWarps - 1) / kWarpSortWarps);
+      prof_mark(9, true, s);
+      lp_bucket_sort_warp_kernel<<<gw, kWarpSortWarps * 32, wsmem, s>>>(ba, queue + 1, big_flags); note_launch();
+      prof_mark(9, false, s);
+    }
     int g = num_sms();
     if (g > B) g = B;
     prof_mark(7, true, s);
