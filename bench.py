@@ -258,7 +258,61 @@ class Batched:
         return t, f"the smallest problems up to {done} fact rows"
 
 
-WORKLOADS = {"q14": Q14, "q6": Q6, "skew": Skew, "batched": Batched}
+class Star:
+    """Star join: fact 600M rows (fk1 into 20M int32 keys, fk2 into 150M int64
+    keys, three int64 measures, date) WHERE date < 767 GROUP BY (dim1.cat,
+    dim2.cat): SUM(m1), SUM(m2), SUM(m3), COUNT(*), one fused call."""
+    name = "star"
+    n, n1, n2 = 600_000_000, 20_000_000, 150_000_000
+    prof_class = 1
+    kernel_name = "star_probe_kernel"
+
+    def __init__(self, master):
+        from paper_2209_04579_b300 import datagen as dg
+        self.dg = dg
+        self.rec = dg.star_tables(self.n1, self.n2, master=master)
+        self.master = master
+
+    def config(self):
+        return {"workload": "star join: fact 600M rows (fk1 int32 into 20M dim1 keys, fk2 int64 into 150M dim2 keys, "
+                            "m1..m3 int64 U[0,1e7], date int32 U[0,2556]) WHERE date<767 GROUP BY dim1.cat (int16 "
+                            "0..999), dim2.cat (int8 0..49); SUM(m1..m3), COUNT", "fact_rows": self.n}
+
+    def make_device(self):
+        from paper_2209_04579_b300 import datagen_device as gd
+        self.fact = gd.make_table(self.rec["fact"], self.n)
+        self.d1 = gd.make_table(self.rec["dim1"], self.n1)
+        self.d2 = gd.make_table(self.rec["dim2"], self.n2)
+        return list(self.fact.values()) + list(self.d1.values()) + list(self.d2.values())
+
+    def step(self):
+        from paper_2209_04579_b300 import queries as Q
+        return Q.star(self.fact, self.d1, self.d2)
+
+    def rows(self):
+        return self.n
+
+    def alg_bytes(self):
+        return self.n * 40 + self.n1 * 6 + self.n2 * 9
+
+    def dominant_bytes(self):
+        return self.n * 40
+
+    def oracle_sample(self, rows):
+        from oracle import pipelines as pl
+        scale = max(1, self.n // max(rows, 1))
+        rec = self.dg.star_tables(self.n1 // scale, self.n2 // scale, master=self.master)
+        nf = self.n // scale
+        f = self.dg.make_table(rec["fact"], nf)
+        d1 = self.dg.make_table(rec["dim1"], self.n1 // scale)
+        d2 = self.dg.make_table(rec["dim2"], self.n2 // scale)
+        t0 = time.perf_counter()
+        pl.star(f, d1, d2)
+        self._sample_rows = nf
+        return time.perf_counter() - t0, f"the workload scaled by 1/{scale} (fact {nf}, dims {self.n1 // scale} and {self.n2 // scale})"
+
+
+WORKLOADS = {"q14": Q14, "q6": Q6, "skew": Skew, "batched": Batched, "star": Star}
 
 
 # ---------------------------------------------------------------- helpers

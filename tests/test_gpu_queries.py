@@ -149,3 +149,47 @@ def test_star_crowded_directory_cells(G):
     cu = lambda t: {k: torch.from_numpy(v).cuda() for k, v in t.items()}
     compare(Q.q14(cu(fact), cu(dim)), want)
     assert tqp.tqp_status_poll() == tqp.OK
+
+
+def test_star_full_size_invariants(G):
+    """The full star join (fact 600M rows, dims 20M and 150M) in the
+    benchmark's configuration.  At this size the oracle checks properties
+    that hold at any size: every fact row matches exactly one row of each
+    dimension (foreign keys drawn from the dimension keys), so the group
+    counts sum to the number of rows with date < 767 and each measure's sums
+    add up to that measure's total over those rows; group keys are unique and
+    ascending and within the category domains.  The scaled test above checks
+    every group exactly."""
+    tqp, Q, gd = G
+    n, n1, n2 = 600_000_000, 20_000_000, 150_000_000
+    rec = dg.star_tables(n1, n2)
+    fact = gd.make_table(rec["fact"], n)
+    d1, d2 = gd.make_table(rec["dim1"], n1), gd.make_table(rec["dim2"], n2)
+    ok, oa, g = Q.star(fact, d1, d2)
+    assert tqp.tqp_status_poll() == tqp.OK
+    del fact, d1, d2
+    torch.cuda.empty_cache()
+    G_ = int(g.item())
+    aggs = host(oa)[:G_]
+    k1, k2 = host(ok[0], G_).astype(np.int64), host(ok[1], G_).astype(np.int64)
+    assert np.all((k1 >= 0) & (k1 <= 999) & (k2 >= 0) & (k2 <= 49))
+    key = k1 * 100 + k2
+    assert np.all(np.diff(key) > 0)
+    cnt, s1, s2, s3 = 0, 0, 0, 0
+    chunk = 50_000_000
+    for start in range(0, n, chunk):
+        m = min(chunk, n - start)
+        date = dg.generate(rec["fact"]["date"], m, start)
+        sel = orc.filter([date], [(0, orc.LT, 767)])
+        cnt += len(sel)
+        for name in ("m1", "m2", "m3"):
+            col = orc.gather(dg.generate(rec["fact"][name], m, start), sel)
+            total = int(col.sum())
+            if name == "m1":
+                s1 += total
+            elif name == "m2":
+                s2 += total
+            else:
+                s3 += total
+    assert int(aggs[:, 3].sum()) == cnt
+    assert [int(aggs[:, 0].sum()), int(aggs[:, 1].sum()), int(aggs[:, 2].sum())] == [s1, s2, s3]
