@@ -317,10 +317,13 @@ __global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, 
     const long long r0 = (t - a.tile_off[p]) * TILE;
     const long long Gp = a.G[p];
     const bool shared = Gp * nacc <= kBatchSmemWords;
+    // one accumulator copy per warp when they fit (no cross-warp contention)
+    const int copies = (Gp * nacc * (THREADS / 32) <= kBatchSmemWords) ? THREADS / 32 : 1;
+    long long* my_acc = s_acc + (copies > 1 ? (threadIdx.x >> 5) * Gp * nacc : 0);
     long long* gacc = a.acc + P.slot_off * nacc;
     if (shared) {
-      for (int i = threadIdx.x; i < Gp * nacc; i += THREADS) {
-        int q = i % nacc;
+      for (int i = threadIdx.x; i < Gp * nacc * copies; i += THREADS) {
+        int q = (int)((i % (Gp * nacc)) % nacc);
         s_acc[i] = q < S.naggs ? agg_identity(S.op[q]) : 0;
       }
       __syncthreads();
@@ -366,13 +369,17 @@ __global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, 
           ev[e] = (long long)v;
         }
       }
-      batch_fold(shared ? s_acc + g * nacc : gacc + g * nacc, S, ev);
+      batch_fold(shared ? my_acc + g * nacc : gacc + g * nacc, S, ev);
     }
     if (shared) {
       __syncthreads();
       for (int i = threadIdx.x; i < Gp * nacc; i += THREADS) {
         int q = i % nacc;
         long long v = s_acc[i];
+        for (int w = 1; w < copies; ++w) {  // merge the warps' copies
+          long long x = s_acc[(long long)w * Gp * nacc + i];
+          v = (q < S.naggs) ? agg_fold(S.op[q], v, x) : v + x;
+        }
         long long id = q < S.naggs ? agg_identity(S.op[q]) : 0;
         if (v == id) continue;
         if (q < S.naggs && S.op[q] == TQP_MIN) atomicMin(&gacc[i], v);

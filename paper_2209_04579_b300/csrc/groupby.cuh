@@ -116,6 +116,15 @@ __device__ __forceinline__ void fold_row(PartialT<N>& p, const AggProgram& P, in
 }
 
 template <int N>
+__device__ __forceinline__ PartialT<N> shfl_down_partial(const PartialT<N>& p, int d) {
+  PartialT<N> o;
+#pragma unroll
+  for (int a = 0; a < N; ++a) o.v[a] = __shfl_down_sync(0xffffffffu, p.v[a], d);
+  o.c = __shfl_down_sync(0xffffffffu, p.c, d);
+  return o;
+}
+
+template <int N>
 __device__ __forceinline__ PartialT<N> shfl_up_partial(const PartialT<N>& p, int d) {
   PartialT<N> o;
 #pragma unroll
@@ -396,8 +405,8 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
     if (lane == 0) partial_identity(texcl, P);
     PT thread_excl = partial_combine(wexcl, texcl, P);
 
-    // ---- tile look-back (thread 0)
-    if (threadIdx.x == 0) {
+    // ---- tile look-back (warp 0: 32 predecessors per step, folded in order)
+    if (warp == 0) {
       PT tile_agg;
       partial_identity(tile_agg, P);
       for (int w = 0; w < WARPS; ++w) tile_agg = partial_combine(tile_agg, s_warp[w], P);
@@ -406,32 +415,48 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
       partial_identity(acc, P);
       bool failed = false;
       if (tile == 0) {
-        if (!inject) {
+        if (lane == 0 && !inject) {
           store_partial_relaxed(&a.pre_payload[0], tile_agg, P.naggs);
           st_release_u32(&a.flags[0], 2u);
         }
       } else {
-        if (!inject) {
+        if (lane == 0 && !inject) {
           store_partial_relaxed(&a.agg_payload[tile], tile_agg, P.naggs);
           st_release_u32(&a.flags[tile], 1u);
         }
-        for (long long t = (long long)tile - 1; t >= 0; --t) {
-          uint32_t f;
-          long long rounds = 0;
-          unsigned sleep_ns = 32;
-          while (true) {
-            f = ld_acquire_u32(&a.flags[t]);
-            if (f) break;
-            if (++rounds > limit) { f = 3u; break; }
-            __nanosleep(sleep_ns);
-            if (sleep_ns < 1024) sleep_ns <<= 1;
+        long long window_end = tile;
+        while (true) {
+          const long long t = window_end - 1 - lane;
+          uint32_t f = 2u;  // before tile 0: an empty inclusive prefix
+          PT v;
+          partial_identity(v, P);
+          if (t >= 0) {
+            long long rounds = 0;
+            unsigned sleep_ns = 32;
+            while (true) {
+              f = ld_acquire_u32(&a.flags[t]);
+              if (f) break;
+              if (++rounds > limit) { f = 3u; break; }
+              __nanosleep(sleep_ns);
+              if (sleep_ns < 1024) sleep_ns <<= 1;
+            }
+            if (f == 1u || f == 2u) v = load_partial_relaxed<NAGG>(f == 2u ? &a.pre_payload[t] : &a.agg_payload[t], P);
           }
-          if (f == 3u) { failed = true; break; }
-          PT pt = load_partial_relaxed<NAGG>(f == 2u ? &a.pre_payload[t] : &a.agg_payload[t], P);
-          acc = partial_combine(pt, acc, P);
-          if (f == 2u) break;
+          if (__ballot_sync(0xffffffffu, f == 3u)) { failed = true; break; }
+          const unsigned pm = __ballot_sync(0xffffffffu, f == 2u);
+          const int first = pm ? __ffs(pm) - 1 : 31;
+          if (lane > first) partial_identity(v, P);
+          // fold lanes first .. 0 (higher lanes are further left)
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            PT other = shfl_down_partial(v, o);
+            if (lane + o < 32) v = partial_combine(other, v, P);
+          }
+          acc = partial_combine(v, acc, P);  // lane 0 holds the window's fold
+          if (pm) break;
+          window_end -= 32;
         }
-        if (!inject) {
+        if (lane == 0 && !inject) {
           if (failed) {
             st_release_u32(&a.flags[tile], 3u);
           } else {
@@ -440,15 +465,17 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
           }
         }
       }
-      if (failed) {
-        raise_status(TQP_ERR_TIMEOUT);
-        s_failed = 1;
-      }
-      s_tile_excl = acc;
-      if (!failed && tile == a.num_tiles - 1) {
-        long long g = (long long)acc.c + tile_agg.c + nh;
-        *a.d_out_groups = g;
-        if (g > a.cap) raise_status(TQP_ERR_CAPACITY);
+      if (lane == 0) {
+        if (failed) {
+          raise_status(TQP_ERR_TIMEOUT);
+          s_failed = 1;
+        }
+        s_tile_excl = acc;
+        if (!failed && tile == a.num_tiles - 1) {
+          long long g = (long long)acc.c + tile_agg.c + nh;
+          *a.d_out_groups = g;
+          if (g > a.cap) raise_status(TQP_ERR_CAPACITY);
+        }
       }
     }
     __syncthreads();

@@ -135,7 +135,9 @@ __global__ void star_slots_kernel(StarPlan* plan, int ndims, const long long* d_
     plan->unsupported = 1;
     raise_status(TQP_ERR_UNSUPPORTED);
   }
-  plan->use_smem = (S * nacc <= kSmemAccWords) ? 1 : 0;
+  // 2: one accumulator copy per warp of the probe block (no cross-warp
+  // contention on few groups); 1: one copy per block; 0: global atomics
+  plan->use_smem = (S * nacc * 8 <= kSmemAccWords) ? 2 : (S * nacc <= kSmemAccWords) ? 1 : 0;
 }
 
 struct StarAcc {
@@ -281,8 +283,10 @@ __global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAc
   const bool use_smem = plan->use_smem != 0;
   const long long S = plan->S;
   const int nacc = A.naggs + 1;
+  const int copies = plan->use_smem == 2 ? THREADS / 32 : 1;
+  long long* my_acc = s_acc + (plan->use_smem == 2 ? (threadIdx.x >> 5) * S * nacc : 0);
   if (use_smem) {
-    for (int i = threadIdx.x; i < S * nacc; i += THREADS) s_acc[i] = acc_identity(A, i % nacc);
+    for (int i = threadIdx.x; i < S * nacc * copies; i += THREADS) s_acc[i] = acc_identity(A, (i % (S * nacc)) % nacc);
   }
   DimDir dd[kMaxDims];
   long long stride[kMaxDims];
@@ -346,7 +350,12 @@ __global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAc
           hi[k] = __ldg(&D.dir[c[k] + 1]);
         }
       }
-      // C: the keys of the cell (a bound search when the cell is crowded)
+      // C: the keys of the cell (a bound search when the cell is crowded);
+      // cells one key value wide hold exactly the key whose bit is set
+      if (dd[d].bshift == 0) {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) pos[d][k] = lo[k];
+      } else {
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
         if (!live[k]) continue;
@@ -367,6 +376,7 @@ __global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAc
         }
         live[k] = found >= 0;
         pos[d][k] = found;
+      }
       }
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k)
@@ -397,7 +407,7 @@ __global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAc
           ev[e] = (long long)x;
         }
       }
-      fold_slot(use_smem ? s_acc + slot[k] * nacc : a.acc + slot[k] * nacc, A, ev);
+      fold_slot(use_smem ? my_acc + slot[k] * nacc : a.acc + slot[k] * nacc, A, ev);
     }
   }
   if (use_smem) {
@@ -405,6 +415,10 @@ __global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAc
     for (int i = threadIdx.x; i < S * nacc; i += THREADS) {
       int q = i % nacc;
       long long v = s_acc[i];
+      for (int w = 1; w < copies; ++w) {  // merge the warps' copies
+        long long x = s_acc[(long long)w * S * nacc + i];
+        v = (q < A.naggs) ? agg_fold(A.op[q], v, x) : v + x;
+      }
       if (v == acc_identity(A, q)) continue;
       if (q < A.naggs && A.op[q] == TQP_MIN) atomicMin(&a.acc[i], v);
       else if (q < A.naggs && A.op[q] == TQP_MAX) atomicMax(&a.acc[i], v);
