@@ -247,22 +247,32 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(SortArgs a, int pass
       if (!inject) st_volatile_u32(st, kSFlagPrefix | tile_count);
     } else {
       if (!inject) st_volatile_u32(st, kSFlagAgg | tile_count);
-      for (long long t = (long long)tile - 1; t >= 0; --t) {
-        const uint32_t* ps = a.status + (size_t)t * kRadix + d;
-        uint32_t s;
-        long long rounds = 0;
-        unsigned sleep_ns = 32;
-        while (true) {
-          s = ld_volatile_u32(ps);
-          if (s & kSFlagMask) break;
-          if (++rounds > limit) { s = kSFlagFailed; break; }
-          __nanosleep(sleep_ns);
-          if (sleep_ns < 1024) sleep_ns <<= 1;
+      // walk back four predecessors at a time: their words are loaded
+      // together, then consumed in order (waiting only on a word not yet set)
+      bool done = false;
+      for (long long t = (long long)tile - 1; t >= 0 && !done && !failed; t -= 4) {
+        const int cnt = t >= 3 ? 4 : (int)t + 1;
+        uint32_t w4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          w4[q] = q < cnt ? ld_volatile_u32(a.status + (size_t)(t - q) * kRadix + d) : 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (q >= cnt || done || failed) break;
+          uint32_t sv = w4[q];
+          long long rounds = 0;
+          unsigned sleep_ns = 32;
+          while (!(sv & kSFlagMask)) {
+            if (++rounds > limit) { sv = kSFlagFailed; break; }
+            __nanosleep(sleep_ns);
+            if (sleep_ns < 1024) sleep_ns <<= 1;
+            sv = ld_volatile_u32(a.status + (size_t)(t - q) * kRadix + d);
+          }
+          const uint32_t f = sv & kSFlagMask;
+          if (f == kSFlagFailed) { failed = true; break; }
+          excl += (sv & kSValMask);
+          if (f == kSFlagPrefix) done = true;
         }
-        uint32_t f = s & kSFlagMask;
-        if (f == kSFlagFailed) { failed = true; break; }
-        excl += (s & kSValMask);
-        if (f == kSFlagPrefix) break;
       }
       if (!inject) st_volatile_u32(st, failed ? kSFlagFailed : (kSFlagPrefix | (uint32_t)(excl + tile_count)));
     }
