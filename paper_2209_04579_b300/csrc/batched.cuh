@@ -13,7 +13,7 @@
 
 namespace tqp {
 
-constexpr int kBatchSmemWords = 6144;  // shared accumulator words per probe block
+constexpr int kBatchSmemWords = 5760;  // shared accumulator words per probe block (static smem < 48 KB)
 constexpr int kUploadChunk = 96;
 
 struct BatchProb {
@@ -300,10 +300,13 @@ struct BatchProbeArgs {
 };
 
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, BatchShape S) {
+__global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, BatchShape Sg) {
   constexpr int TILE = THREADS * ITEMS;
   __shared__ long long s_acc[kBatchSmemWords];
   __shared__ uint32_t s_tile;
+  __shared__ BatchShape S;  // indexed by runtime values: kept in shared memory
+  if (threadIdx.x == 0) S = Sg;
+  __syncthreads();
   if (*a.flag) return;
   const int nacc = S.naggs + 1;
   while (true) {
@@ -356,20 +359,27 @@ __global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, 
       while (l < hi && keys[l] < x) ++l;
       if (l >= hi || keys[l] != x) continue;
       long long g = ranks[l];
-      long long ev[TQP_MAX_EXPRS];
-#pragma unroll
-      for (int e = 0; e < TQP_MAX_EXPRS; ++e) {
-        if (e < S.nexprs) {
+      long long* dst = shared ? my_acc + g * nacc : gacc + g * nacc;
+      for (int q = 0; q < S.naggs; ++q) {
+        long long xq = 1;
+        const int op = S.op[q];
+        if (op != TQP_COUNT) {
+          const int e = S.expr[q];
           unsigned long long v = 1;
           for (int tt = 0; tt < S.nterms[e]; ++tt) {
             int c = S.tcol[e][tt];
             long long xv = load_as_i64(P.fact[c], S.fact_dt[c], row);
             v *= (unsigned long long)S.tmul[e][tt] * (unsigned long long)xv + (unsigned long long)S.tadd[e][tt];
           }
-          ev[e] = (long long)v;
+          xq = (long long)v;
+        }
+        switch (op) {
+          case TQP_MIN: atomicMin(dst + q, xq); break;
+          case TQP_MAX: atomicMax(dst + q, xq); break;
+          default: atomicAdd(reinterpret_cast<unsigned long long*>(dst + q), (unsigned long long)xq); break;
         }
       }
-      batch_fold(shared ? my_acc + g * nacc : gacc + g * nacc, S, ev);
+      atomicAdd(reinterpret_cast<unsigned long long*>(dst + S.naggs), 1ull);
     }
     if (shared) {
       __syncthreads();

@@ -537,21 +537,38 @@ __global__ void __launch_bounds__(256) lp_scatter_kernel(PartArgs a, AggProgram 
   __syncthreads();
   const int64_t n = clamp_n(a.n_max, a.d_n);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    int64_t row = a.sel ? a.sel[i] : i;
-    unsigned long long p = pack_row(a.ks, a.gp, row);
-    int h = nh ? heavy_index(s_heavy, nh, p) : -1;
-    if (h >= 0) {
-      for (int q = 0; q < P.naggs; ++q) {
-        long long x = P.op[q] == TQP_COUNT ? 1 : eval_expr(P, P.expr[q], row);
-        fold_atomic(&s_acc[h * P.naggs + q], P.op[q], x);
-      }
-      continue;
+  const int lane = threadIdx.x & 31;
+  // warp-uniform trip count (lanes past n carry h = -2), so that rows of the
+  // same heavy key within a warp are combined before one shared atomic
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    int64_t row = 0;
+    unsigned long long p = 0;
+    int h = -2;
+    if (i < n) {
+      row = a.sel ? a.sel[i] : i;
+      p = pack_row(a.ks, a.gp, row);
+      h = nh ? heavy_index(s_heavy, nh, p) : -1;
     }
-    int b = lp_bucket(p, lp, s_dir, a.thr);
-    unsigned pos = atomicAdd(&a.cursor[b], 1u);
-    a.out_p[pos] = p;
-    a.out_row[pos] = (int32_t)row;
+    const unsigned peers = __match_any_sync(0xffffffffu, h);
+    if (h >= 0) {
+      const int leader = __ffs(peers) - 1;
+      for (int q = 0; q < P.naggs; ++q) {
+        const int op = P.op[q];
+        long long x = op == TQP_COUNT ? 1 : eval_expr(P, P.expr[q], row);
+        long long acc = x;
+        for (unsigned others = peers & ~(1u << leader); others; others &= others - 1) {
+          long long y = __shfl_sync(peers, x, __ffs(others) - 1);
+          acc = agg_fold(op, acc, y);
+        }
+        if (lane == leader) fold_atomic(&s_acc[h * P.naggs + q], op, acc);
+      }
+    } else if (h == -1) {
+      int b = lp_bucket(p, lp, s_dir, a.thr);
+      unsigned pos = atomicAdd(&a.cursor[b], 1u);
+      a.out_p[pos] = p;
+      a.out_row[pos] = (int32_t)row;
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nh * P.naggs; i += blockDim.x) {

@@ -274,10 +274,25 @@ __device__ __forceinline__ void fold_slot(long long* acc, const StarAcc& A, cons
 // (predicates, then per dimension: cell bit, directory bounds, key compare;
 // then values and the fold), so that ITEMS memory chains are in flight.
 template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAcc A) {
+__global__ void __launch_bounds__(THREADS, 3) star_probe_kernel(ProbeArgs a, StarAcc Ag) {
   constexpr int TILE = THREADS * ITEMS;
   __shared__ long long s_acc[kSmemAccWords];
   __shared__ uint32_t s_tile;
+  // the aggregate program and value references in shared memory: they are
+  // indexed by runtime values below (kernel parameters indexed that way are
+  // copied to local memory)
+  __shared__ StarAcc A;
+  __shared__ int s_vsrc[TQP_MAX_VALS], s_vdt[TQP_MAX_VALS];
+  __shared__ const void* s_vptr[TQP_MAX_VALS];
+  if (threadIdx.x == 0) {
+    A = Ag;
+    for (int v = 0; v < TQP_MAX_VALS; ++v) {
+      s_vsrc[v] = a.vsrc[v];
+      s_vdt[v] = a.vdt[v];
+      s_vptr[v] = a.vptr[v];
+    }
+  }
+  __syncthreads();
   const StarPlan* plan = a.plan;
   if (plan->unsupported) return;
   const bool use_smem = plan->use_smem != 0;
@@ -383,31 +398,34 @@ __global__ void __launch_bounds__(THREADS) star_probe_kernel(ProbeArgs a, StarAc
         if (live[k]) slot[k] += (long long)__ldg(&D.rank_sorted[pos[d][k]]) * stride[d];
     }
     // D: values, expressions, fold
-#pragma unroll 1
+#pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       if (!live[k]) continue;
       const int64_t row = base + (int64_t)k * THREADS;
-      long long vals[TQP_MAX_VALS];
-#pragma unroll
-      for (int v = 0; v < TQP_MAX_VALS; ++v) {
-        if (v < a.nvals) {
-          int src = a.vsrc[v];
-          vals[v] = src == 0 ? load_as_i64(a.vptr[v], a.vdt[v], row)
-                             : static_cast<const long long*>(a.vptr[v])[pos[src - 1][k]];
+      const int p0 = pos[0][k], p1 = kMaxDims > 1 ? pos[1][k] : 0;
+      long long* dst = use_smem ? my_acc + slot[k] * nacc : a.acc + slot[k] * nacc;
+      for (int q = 0; q < A.naggs; ++q) {
+        long long x = 1;
+        const int op = A.op[q];
+        if (op != TQP_COUNT) {
+          const int e = A.expr[q];
+          unsigned long long ev = 1;
+          for (int t = 0; t < A.nterms[e]; ++t) {
+            const int v = A.tval[e][t];
+            const int src = s_vsrc[v];
+            long long val = src == 0 ? load_as_i64(s_vptr[v], s_vdt[v], row)
+                                     : static_cast<const long long*>(s_vptr[v])[src == 1 ? p0 : p1];
+            ev *= (unsigned long long)A.tmul[e][t] * (unsigned long long)val + (unsigned long long)A.tadd[e][t];
+          }
+          x = (long long)ev;
+        }
+        switch (op) {
+          case TQP_MIN: atomicMin(dst + q, x); break;
+          case TQP_MAX: atomicMax(dst + q, x); break;
+          default: atomicAdd(reinterpret_cast<unsigned long long*>(dst + q), (unsigned long long)x); break;
         }
       }
-      long long ev[TQP_MAX_EXPRS];
-#pragma unroll
-      for (int e = 0; e < TQP_MAX_EXPRS; ++e) {
-        if (e < A.nexprs) {
-          unsigned long long x = 1;
-          for (int t = 0; t < A.nterms[e]; ++t)
-            x *= (unsigned long long)A.tmul[e][t] * (unsigned long long)vals[A.tval[e][t]] +
-                 (unsigned long long)A.tadd[e][t];
-          ev[e] = (long long)x;
-        }
-      }
-      fold_slot(use_smem ? my_acc + slot[k] * nacc : a.acc + slot[k] * nacc, A, ev);
+      atomicAdd(reinterpret_cast<unsigned long long*>(dst + A.naggs), 1ull);
     }
   }
   if (use_smem) {
