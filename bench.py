@@ -155,9 +155,13 @@ class Skew:
         self.t = gd.make_table(self.rec, self.n, zipf=z)
         return [self.t["key"], self.t["value"]]
 
+    variant = "learned"
+
     def step(self):
         from paper_2209_04579_b300 import queries as Q
         from paper_2209_04579_b300 import tqp
+        if self.variant == "plain":
+            return Q.skew(self.t, cap=self.cap)
         r = Q.skew_learned(self.t, cap=self.cap, cfg=tqp.learned_cfg(sample=65536, tcfg=tqp.train_cfg(epochs=100)))
         self.stats = r[4]
         if self.cap == self.n:  # first (eager) call: size the outputs to the group count
@@ -449,6 +453,8 @@ def run_ours(args, world, rank, local):
     from paper_2209_04579_b300 import tqp
     torch.cuda.set_device(local)
     W = WORKLOADS[args.workload](20220904 + rank)
+    if args.variant:
+        W.variant = args.variant
     inputs = W.make_device()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
@@ -596,6 +602,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="q14", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default="", help="skew: 'plain' times the plain radix path as the step")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
