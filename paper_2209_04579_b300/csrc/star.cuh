@@ -202,6 +202,9 @@ __global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, co
   int tb = 1;
   while (tb < log2_cells_max && (1ll << tb) < 2 * nd) ++tb;
   int bits = span ? 64 - __clzll((long long)span) : 0;
+  // keys dense in their range (span within 8x their count): one cell per key
+  // value, so the bit alone decides membership
+  if (span < 8ull * (unsigned long long)nd && bits <= log2_cells_max) tb = bits > tb ? bits : tb;
   r.bshift = bits > tb ? bits - tb : 0;
   r.ncells = (long long)(span >> r.bshift) + 1;
   *dd = r;
@@ -223,12 +226,41 @@ __global__ void dir_fill_kernel(const void* skeys, int key_dt, int64_t n_max, co
   }
 }
 
+// Unit-width cells (bshift == 0) also get per-cell copies of the group rank
+// and of the aggregated dimension values, so that a probe hit reads them
+// directly by cell instead of through the position table.
+struct CellArgs {
+  const void* skeys;
+  int key_dt;
+  int64_t n_max;
+  const int64_t* d_n;
+  const DimDir* dd;
+  const int32_t* rank_sorted;
+  int32_t* rank_cell;
+  int nv;
+  const long long* dval[TQP_MAX_VALS];
+  long long* dval_cell[TQP_MAX_VALS];
+};
+
+__global__ void dir_cells_kernel(CellArgs a) {
+  const DimDir r = *a.dd;
+  if (r.bshift != 0 || r.ncells == 0) return;
+  const int64_t nd = clamp_n(a.n_max, a.d_n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nd; p += stride) {
+    const long long c = (long long)(key_image(a.skeys, a.key_dt, p) - r.umin);
+    a.rank_cell[c] = a.rank_sorted[p];
+    for (int v = 0; v < a.nv; ++v) a.dval_cell[v][c] = a.dval[v][p];
+  }
+}
+
 struct ProbeDim {
   const void* skeys;   // sorted passing keys (int32 or int64)
   int key_dt;
   int64_t n_max;
   const int64_t* d_n;
   const int32_t* rank_sorted;
+  const int32_t* rank_cell;
   const void* fk;      // fact foreign-key column (same dtype as the key)
   const DimDir* dir_plan;
   const int* dir;
@@ -246,6 +278,7 @@ struct ProbeArgs {
   int nvals;
   int vsrc[TQP_MAX_VALS];     // 0 = fact column, 1 + d = pre-gathered dimension column
   const void* vptr[TQP_MAX_VALS];
+  const void* vptr_cell[TQP_MAX_VALS];  // the same dimension column by cell (unit-width cells)
   int vdt[TQP_MAX_VALS];
   int64_t n_fact;
   const StarPlan* plan;
@@ -284,12 +317,14 @@ __global__ void __launch_bounds__(THREADS, 3) star_probe_kernel(ProbeArgs a, Sta
   __shared__ StarAcc A;
   __shared__ int s_vsrc[TQP_MAX_VALS], s_vdt[TQP_MAX_VALS];
   __shared__ const void* s_vptr[TQP_MAX_VALS];
+  __shared__ const void* s_vptr_cell[TQP_MAX_VALS];
   if (threadIdx.x == 0) {
     A = Ag;
     for (int v = 0; v < TQP_MAX_VALS; ++v) {
       s_vsrc[v] = a.vsrc[v];
       s_vdt[v] = a.vdt[v];
       s_vptr[v] = a.vptr[v];
+      s_vptr_cell[v] = a.vptr_cell[v];
     }
   }
   __syncthreads();
@@ -326,6 +361,7 @@ __global__ void __launch_bounds__(THREADS, 3) star_probe_kernel(ProbeArgs a, Sta
     bool live[ITEMS];
     long long slot[ITEMS];
     int pos[kMaxDims][ITEMS];
+    bool unit[kMaxDims] = {false, false};
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       live[k] = base + (int64_t)k * THREADS < a.n_fact;
@@ -347,7 +383,10 @@ __global__ void __launch_bounds__(THREADS, 3) star_probe_kernel(ProbeArgs a, Sta
       for (int k = 0; k < ITEMS; ++k) {
         c[k] = 0;
         if (live[k]) {
-          u[k] = key_image(D.fk, D.key_dt, base + (int64_t)k * THREADS);
+          const int64_t r = base + (int64_t)k * THREADS;
+          u[k] = D.key_dt == TQP_I32
+                     ? (unsigned long long)((uint32_t)__ldcs(static_cast<const int32_t*>(D.fk) + r) ^ 0x80000000u)
+                     : ((unsigned long long)__ldcs(static_cast<const long long*>(D.fk) + r) ^ 0x8000000000000000ull);
           if (u[k] < dd[d].umin || u[k] > dd[d].umax) live[k] = false;
           else c[k] = (long long)((u[k] - dd[d].umin) >> dd[d].bshift);
         }
@@ -355,6 +394,17 @@ __global__ void __launch_bounds__(THREADS, 3) star_probe_kernel(ProbeArgs a, Sta
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k)
         if (live[k]) live[k] = (__ldg(&D.bitmap[c[k] >> 5]) >> (c[k] & 31)) & 1u;
+      if (dd[d].bshift == 0) {
+        // unit-width cells: the bit proves the key; rank and values by cell
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+          pos[d][k] = (int)c[k];
+          if (live[k]) slot[k] += (long long)__ldg(&D.rank_cell[c[k]]) * stride[d];
+        }
+        unit[d] = true;
+        continue;
+      }
+      unit[d] = false;
       // B: directory bounds
       int lo[ITEMS], hi[ITEMS];
 #pragma unroll
@@ -365,12 +415,8 @@ __global__ void __launch_bounds__(THREADS, 3) star_probe_kernel(ProbeArgs a, Sta
           hi[k] = __ldg(&D.dir[c[k] + 1]);
         }
       }
-      // C: the keys of the cell (a bound search when the cell is crowded);
-      // cells one key value wide hold exactly the key whose bit is set
-      if (dd[d].bshift == 0) {
-#pragma unroll
-        for (int k = 0; k < ITEMS; ++k) pos[d][k] = lo[k];
-      } else {
+      // C: the keys of the cell (a bound search when the cell is crowded)
+      {
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
         if (!live[k]) continue;
@@ -413,8 +459,13 @@ __global__ void __launch_bounds__(THREADS, 3) star_probe_kernel(ProbeArgs a, Sta
           for (int t = 0; t < A.nterms[e]; ++t) {
             const int v = A.tval[e][t];
             const int src = s_vsrc[v];
-            long long val = src == 0 ? load_as_i64(s_vptr[v], s_vdt[v], row)
-                                     : static_cast<const long long*>(s_vptr[v])[src == 1 ? p0 : p1];
+            long long val;
+            if (src == 0) {
+              val = load_as_i64(s_vptr[v], s_vdt[v], row);
+            } else {
+              const bool cell = src == 1 ? unit[0] : unit[1];
+              val = static_cast<const long long*>(cell ? s_vptr_cell[v] : s_vptr[v])[src == 1 ? p0 : p1];
+            }
             ev *= (unsigned long long)A.tmul[e][t] * (unsigned long long)val + (unsigned long long)A.tadd[e][t];
           }
           x = (long long)ev;

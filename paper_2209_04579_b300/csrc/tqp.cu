@@ -391,6 +391,8 @@ struct StarDimWs {
   int* dir;
   uint32_t* bitmap;
   int log2cells;
+  int32_t* rank_cell;
+  long long* dval_cell[TQP_MAX_VALS];
 };
 
 constexpr int kFilterT = 256, kFilterI = 16;
@@ -746,10 +748,13 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
     for (int v = 0; v < nvals; ++v)
       if (vals[v].src == d + 1) w.dval[v] = c.take<long long>(nn);
     w.log2cells = 1;
-    while (w.log2cells < 27 && (1ll << w.log2cells) < 2 * D.n) ++w.log2cells;
+    while (w.log2cells < 27 && (1ll << w.log2cells) < 8 * D.n) ++w.log2cells;
     w.dplan = c.take<DimDir>(1);
     w.dir = c.take<int>((size_t)(1ll << w.log2cells) + 2);
     w.bitmap = c.take<uint32_t>((size_t)(1ll << w.log2cells) / 32 + 1);
+    w.rank_cell = c.take<int32_t>((size_t)(1ll << w.log2cells) + 1);
+    for (int v = 0; v < nvals; ++v)
+      if (vals[v].src == d + 1) w.dval_cell[v] = c.take<long long>((size_t)(1ll << w.log2cells) + 1);
   }
   StarPlan* plan = c.take<StarPlan>(1);
   const int nacc = naggs + 1;
@@ -874,6 +879,22 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
       dir_fill_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(w.skeys, D.key.dtype, D.n, dcnt, w.dplan, w.dir,
                                                              w.bitmap);
       note_launch();
+      CellArgs ca;
+      std::memset(&ca, 0, sizeof(ca));
+      ca.skeys = w.skeys;
+      ca.key_dt = D.key.dtype;
+      ca.n_max = D.n;
+      ca.d_n = dcnt;
+      ca.dd = w.dplan;
+      ca.rank_sorted = w.rank_sorted;
+      ca.rank_cell = w.rank_cell;
+      for (int v = 0; v < nvals; ++v) {
+        if (vals[v].src != d + 1) continue;
+        ca.dval[ca.nv] = w.dval[v];
+        ca.dval_cell[ca.nv] = w.dval_cell[v];
+        ++ca.nv;
+      }
+      dir_cells_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(ca); note_launch();
     }
   }
   // ---- slots, accumulators, probe, compaction
@@ -889,6 +910,7 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
     pa.dim[d].n_max = dims[d].n;
     pa.dim[d].d_n = dims[d].npred ? W[d].cnt : nullptr;
     pa.dim[d].rank_sorted = W[d].rank_sorted;
+    pa.dim[d].rank_cell = W[d].rank_cell;
     pa.dim[d].fk = fact_cols[fk_col[d]].data;
     pa.dim[d].dir_plan = W[d].dplan;
     pa.dim[d].dir = W[d].dir;
@@ -909,6 +931,7 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
       pa.vdt[v] = fact_cols[vals[v].col].dtype;
     } else {
       pa.vptr[v] = W[vals[v].src - 1].dval[v];
+      pa.vptr_cell[v] = W[vals[v].src - 1].dval_cell[v];
       pa.vdt[v] = TQP_I64;
     }
   }
