@@ -159,7 +159,7 @@ constexpr uint32_t kSFlagAgg = 1u << 30, kSFlagPrefix = 2u << 30, kSFlagFailed =
 constexpr uint32_t kSFlagMask = 3u << 30, kSValMask = ~kSFlagMask;
 
 template <typename K, int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS) sort_pass_kernel(SortArgs a, int pass, uint32_t num_tiles) {
+__global__ void __launch_bounds__(THREADS, 3) sort_pass_kernel(SortArgs a, int pass, uint32_t num_tiles) {
   static_assert(THREADS == kRadix, "one thread per digit");
   constexpr int TILE = THREADS * ITEMS;
   constexpr int WARPS = THREADS / 32;
@@ -172,17 +172,19 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(SortArgs a, int pass
   __shared__ int s_scan[33];
   __shared__ uint32_t s_tile;
   __shared__ int s_failed;
+  __shared__ uint8_t s_dig[TILE];  // digit of every staged slot
   extern __shared__ __align__(16) unsigned char s_raw[];  // TILE keys, reused for values
   K* s_keys = reinterpret_cast<K*>(s_raw);
   int32_t* s_vals = reinterpret_cast<int32_t*>(s_raw);
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = clamp_n(a.n_max, a.d_n);
-  const void* kin = pd.src == 0 ? a.keys_in : a.alt_keys[pd.src - 1];
-  const int32_t* vin = pd.src == 0 ? a.vals_in : a.alt_vals[pd.src - 1];
+  // (no runtime index into the parameter arrays: that would copy them to local memory)
+  const void* kin = pd.src == 0 ? a.keys_in : (pd.src == 1 ? a.alt_keys[0] : a.alt_keys[1]);
+  const int32_t* vin = pd.src == 0 ? a.vals_in : (pd.src == 1 ? a.alt_vals[0] : a.alt_vals[1]);
   const int kin_dt = pd.first ? a.key_dt : (sizeof(K) == 4 ? kKeyU32 : kKeyU64);
-  void* kout = pd.dst == 0 ? a.keys_out : a.alt_keys[pd.dst - 1];
-  int32_t* vout = pd.dst == 0 ? a.vals_out : a.alt_vals[pd.dst - 1];
+  void* kout = pd.dst == 0 ? a.keys_out : (pd.dst == 1 ? a.alt_keys[0] : a.alt_keys[1]);
+  int32_t* vout = pd.dst == 0 ? a.vals_out : (pd.dst == 1 ? a.alt_vals[0] : a.alt_vals[1]);
   const int kout_dt = pd.last ? a.key_dt : (sizeof(K) == 4 ? kKeyU32 : kKeyU64);
   const uint32_t* digit_off = a.hist + pass * kRadix;
   const long long limit = g_spin_limit;
@@ -201,8 +203,7 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(SortArgs a, int pass
     // ---- load (warp-striped) and rank within the warp
     K key[ITEMS];
     int32_t val[ITEMS];
-    uint32_t rank[ITEMS];
-    uint32_t dig[ITEMS];
+    uint32_t dr[ITEMS];  // (rank within the warp's digit << 9) | digit (kRadix = padding row)
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
       int64_t row = tile_base + (int64_t)warp * (32 * ITEMS) + it * 32 + lane;
@@ -215,18 +216,19 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(SortArgs a, int pass
       }
       key[it] = u;
       val[it] = v;
-      dig[it] = valid ? digit_of(u, a.begin_bit, a.nbits, pass) : kRadix;
+      dr[it] = valid ? digit_of(u, a.begin_bit, a.nbits, pass) : kRadix;
     }
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
-      unsigned peers = __match_any_sync(0xffffffffu, dig[it]);
+      const unsigned dg = dr[it];
+      unsigned peers = __match_any_sync(0xffffffffu, dg);
       int leader = 31 - __clz(peers);
       uint32_t before = __popc(peers & ((1u << lane) - 1));
-      uint32_t base = s_wcnt[warp][dig[it]];
+      uint32_t base = s_wcnt[warp][dg];
       __syncwarp();
-      if (lane == leader) s_wcnt[warp][dig[it]] = base + __popc(peers);
+      if (lane == leader) s_wcnt[warp][dg] = base + __popc(peers);
       __syncwarp();
-      rank[it] = base + before;
+      dr[it] = ((base + before) << 9) | dg;
     }
     __syncthreads();
 
@@ -289,34 +291,40 @@ __global__ void __launch_bounds__(THREADS) sort_pass_kernel(SortArgs a, int pass
     __syncthreads();
     if (tile_failed) continue;  // give up on this tile without writing
 
-    // ---- stage keys in tile order
+    // ---- stage keys in tile order (with each slot's digit)
 #pragma unroll
-    for (int it = 0; it < ITEMS; ++it)
-      if (dig[it] < kRadix) s_keys[s_tile_start[dig[it]] + s_wcnt[warp][dig[it]] + rank[it]] = key[it];
+    for (int it = 0; it < ITEMS; ++it) {
+      const unsigned dg = dr[it] & 511u;
+      if (dg < kRadix) {
+        const unsigned slot = s_tile_start[dg] + s_wcnt[warp][dg] + (dr[it] >> 9);
+        s_keys[slot] = key[it];
+        s_dig[slot] = (uint8_t)dg;
+      }
+    }
     __syncthreads();
-    int64_t gpos[ITEMS];
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
       int j = it * THREADS + threadIdx.x;
-      gpos[it] = -1;
       if (j < total) {
-        K u = s_keys[j];
-        unsigned dd = digit_of(u, a.begin_bit, a.nbits, pass);
-        int64_t g = s_gbase[dd] + (j - (int)s_tile_start[dd]);
-        gpos[it] = g;
-        store_decoded(kout, kout_dt, g, (unsigned long long)u);
+        const unsigned dd = s_dig[j];
+        store_decoded(kout, kout_dt, s_gbase[dd] + (j - (int)s_tile_start[dd]), (unsigned long long)s_keys[j]);
       }
     }
     __syncthreads();
     // ---- stage values in tile order
 #pragma unroll
-    for (int it = 0; it < ITEMS; ++it)
-      if (dig[it] < kRadix) s_vals[s_tile_start[dig[it]] + s_wcnt[warp][dig[it]] + rank[it]] = val[it];
+    for (int it = 0; it < ITEMS; ++it) {
+      const unsigned dg = dr[it] & 511u;
+      if (dg < kRadix) s_vals[s_tile_start[dg] + s_wcnt[warp][dg] + (dr[it] >> 9)] = val[it];
+    }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
       int j = it * THREADS + threadIdx.x;
-      if (gpos[it] >= 0) vout[gpos[it]] = s_vals[j];
+      if (j < total) {
+        const unsigned dd = s_dig[j];
+        vout[s_gbase[dd] + (j - (int)s_tile_start[dd])] = s_vals[j];
+      }
     }
     __syncthreads();
   }
