@@ -306,8 +306,11 @@ __device__ __forceinline__ void fold_slot(long long* acc, const StarAcc& A, cons
 // Each thread carries ITEMS independent fact rows through the stages
 // (predicates, then per dimension: cell bit, directory bounds, key compare;
 // then values and the fold), so that ITEMS memory chains are in flight.
-template <int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS, 3) star_probe_kernel(ProbeArgs a, StarAcc Ag) {
+// SMEM_BM: the first dimension's cell bitmap is copied into dynamic shared
+// memory (when it fits in smem_bm_words) so that a miss costs one shared
+// read; used for small first dimensions, one large block per SM.
+template <int THREADS, int ITEMS, bool SMEM_BM>
+__global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(ProbeArgs a, StarAcc Ag, int smem_bm_words) {
   constexpr int TILE = THREADS * ITEMS;
   __shared__ long long s_acc[kSmemAccWords];
   __shared__ uint32_t s_tile;
@@ -333,8 +336,14 @@ __global__ void __launch_bounds__(THREADS, 3) star_probe_kernel(ProbeArgs a, Sta
   const bool use_smem = plan->use_smem != 0;
   const long long S = plan->S;
   const int nacc = A.naggs + 1;
-  const int copies = plan->use_smem == 2 ? THREADS / 32 : 1;
-  long long* my_acc = s_acc + (plan->use_smem == 2 ? (threadIdx.x >> 5) * S * nacc : 0);
+  // accumulator copies: as many as fit (up to one per warp); warp w uses copy w % copies
+  int copies = 1;
+  if (plan->use_smem == 2) {
+    long long fit = kSmemAccWords / (S * nacc);
+    copies = (int)(fit < THREADS / 32 ? fit : THREADS / 32);
+    if (copies < 1) copies = 1;
+  }
+  long long* my_acc = s_acc + ((threadIdx.x >> 5) % copies) * S * nacc;
   if (use_smem) {
     for (int i = threadIdx.x; i < S * nacc * copies; i += THREADS) s_acc[i] = acc_identity(A, (i % (S * nacc)) % nacc);
   }
@@ -349,6 +358,14 @@ __global__ void __launch_bounds__(THREADS, 3) star_probe_kernel(ProbeArgs a, Sta
       dd[d].ncells = 0;
       stride[d] = 0;
     }
+  }
+  extern __shared__ uint32_t s_bm[];
+  bool sbm = false;
+  if (SMEM_BM) {
+    const long long words = (dd[0].ncells + 31) / 32;
+    sbm = words <= smem_bm_words;
+    if (sbm)
+      for (long long i = threadIdx.x; i < words; i += THREADS) s_bm[i] = __ldg(&a.dim[0].bitmap[i]);
   }
   __syncthreads();
   while (true) {
@@ -393,7 +410,10 @@ __global__ void __launch_bounds__(THREADS, 3) star_probe_kernel(ProbeArgs a, Sta
       }
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k)
-        if (live[k]) live[k] = (__ldg(&D.bitmap[c[k] >> 5]) >> (c[k] & 31)) & 1u;
+        if (live[k]) {
+          const uint32_t w = (SMEM_BM && d == 0 && sbm) ? s_bm[c[k] >> 5] : __ldg(&D.bitmap[c[k] >> 5]);
+          live[k] = (w >> (c[k] & 31)) & 1u;
+        }
       if (dd[d].bshift == 0) {
         // unit-width cells: the bit proves the key; rank and values by cell
 #pragma unroll

@@ -398,6 +398,8 @@ struct StarDimWs {
 constexpr int kFilterT = 256, kFilterI = 16;
 constexpr int kRankT = 256, kRankI = 8;
 constexpr int kProbeT = 256, kProbeI = 8;
+constexpr int kSmemBitmapBytes = 190 * 1024;       // shared bitmap of the first dimension
+constexpr int64_t kSmemBitmapDimRows = 4'000'000;  // first dimensions up to this size try it
 constexpr int kCompactT = 256, kCompactI = 8;
 
 }  // namespace
@@ -942,9 +944,24 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
   pa.num_tiles = (uint32_t)ptiles;
   TQP_CUDA(cudaMemsetAsync(pcounter, 0, 4, s));
   if (ptiles > 0) {
-    auto pk = star_probe_kernel<kProbeT, kProbeI>;
     prof_mark(1, true, s);
-    pk<<<persistent_grid(pk, kProbeT, 0, ptiles), kProbeT, 0, s>>>(pa, A); note_launch();
+    if (dims[0].n <= kSmemBitmapDimRows) {
+      // small first dimension: its bitmap can live in shared memory
+      auto pk = star_probe_kernel<1024, 4, true>;
+      const int words = kSmemBitmapBytes / 4;
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBitmapBytes);
+        attr = true;
+      }
+      const int64_t t1024 = (n_fact + 1024 * 4 - 1) / (1024 * 4);
+      pa.num_tiles = (uint32_t)t1024;
+      pk<<<persistent_grid(pk, 1024, kSmemBitmapBytes, t1024), 1024, kSmemBitmapBytes, s>>>(pa, A, words);
+      note_launch();
+    } else {
+      auto pk = star_probe_kernel<kProbeT, kProbeI, false>;
+      pk<<<persistent_grid(pk, kProbeT, 0, ptiles), kProbeT, 0, s>>>(pa, A, 0); note_launch();
+    }
     prof_mark(1, false, s);
   }
   CompactArgs ca;
