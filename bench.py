@@ -41,8 +41,6 @@ class Q14:
     int64) 1.5M rows WHERE region < 5 GROUP BY region: SUM(price), COUNT(*)."""
     name = "q14"
     n_fact, m_dim = 60_000_000, 1_500_000
-    prof_class = 1  # fused star probe
-    kernel_name = "star_probe_kernel"
 
     def __init__(self, master):
         from paper_2209_04579_b300 import datagen as dg
@@ -73,10 +71,10 @@ class Q14:
         # inputs read once: fact fk (4 B/row) + dim key, region, price (13 B/row)
         return self.n_fact * 4 + self.m_dim * 13
 
-    def dominant_bytes(self):
+    def prof(self):
         # the probe reads every fact key once plus the passing dimension rows'
-        # sorted key, rank and price (4 + 4 + 8 B, 20% of the dimension)
-        return self.n_fact * 4 + int(self.m_dim * 0.2) * 16
+        # rank and price by cell (4 + 8 B, 20% of the dimension) and their bits
+        return [(1, "star_probe_kernel", self.n_fact * 4 + int(self.m_dim * 0.2) * 12 + self.m_dim // 8)]
 
     def oracle_sample(self, rows):
         from oracle import pipelines as pl
@@ -91,8 +89,6 @@ class Q6:
     """lineitem 1M rows: filter ship_day <= 2400, group by (flag_a, flag_b)."""
     name = "q6"
     n = 1_000_000
-    prof_class = 4
-    kernel_name = "gb_reduce_kernel"
 
     def __init__(self, master):
         from paper_2209_04579_b300 import datagen as dg
@@ -118,8 +114,11 @@ class Q6:
     def alg_bytes(self):
         return self.n * 38
 
-    def dominant_bytes(self):
-        return int(self.n * 0.939) * (8 + 32)
+    def prof(self):
+        sel = int(self.n * 0.939)
+        return [(4, "gb_reduce_kernel", sel * (4 + 32)),          # row ids + the 4 value columns per selected row
+                (3, "filter_kernel", self.n * 4 + sel * 4),        # ship_day in, selected row ids out
+                (2, "sort_pass_kernel (whole sort)", sel * 8 * 2)]  # one pass of (u32 key, row id) in and out
 
     def oracle_sample(self, rows):
         from oracle import pipelines as pl
@@ -135,8 +134,6 @@ class Skew:
     included in every step); the plain radix path is timed beside it."""
     name = "skew"
     n = 100_000_000
-    prof_class = 7
-    kernel_name = "lp_bucket_sort_kernel"
 
     def __init__(self, master):
         from paper_2209_04579_b300 import datagen as dg
@@ -161,12 +158,15 @@ class Skew:
         from paper_2209_04579_b300 import queries as Q
         from paper_2209_04579_b300 import tqp
         if self.variant == "plain":
-            return Q.skew(self.t, cap=self.cap)
+            r = Q.skew(self.t, cap=self.cap)
+            if self.cap == self.n:
+                self.cap = int(r[2].item())
+            return r
         r = Q.skew_learned(self.t, cap=self.cap, cfg=tqp.learned_cfg(sample=65536, tcfg=tqp.train_cfg(epochs=100)))
         self.stats = r[4]
         if self.cap == self.n:  # first (eager) call: size the outputs to the group count
             self.cap = int(r[2].item())
-            self.light_rows = tqp.stats_from_device(self.stats)["light_rows"]
+            self.stats_h = tqp.stats_from_device(self.stats)
         return r[:3]
 
     def plain_step(self):
@@ -179,9 +179,19 @@ class Skew:
     def alg_bytes(self):
         return self.n * 16 + 17_000_000 * 40
 
-    def dominant_bytes(self):
-        # the bucket sort reads and writes every light row's packed key and row id
-        return int(getattr(self, "light_rows", self.n) * 12 * 2)
+    def prof(self):
+        n, G = self.n, self.cap
+        if self.variant == "plain":
+            return [(2, "sort_pass_kernel (8 passes, with the histogram)", n * 8 + 8 * n * 12 * 2),
+                    (4, "gb_reduce_kernel", n * 16 + G * 40)]
+        st = self.stats_h
+        light, small = st["light_rows"], st["small_rows"]
+        # scatter: every key read, the heavy rows' values read for the fold,
+        # each light row's packed key and row id written
+        return [(8, "lp_scatter_kernel", n * 8 + (n - light) * 8 + light * 12),
+                (9, "lp_bucket_sort_warp_kernel", small * 12 * 2),
+                (7, "lp_bucket_sort_kernel", (light - small) * 12 * 2),
+                (4, "gb_reduce_kernel", light * 16 + G * 40)]
 
     def oracle_sample(self, rows):
         from oracle import pipelines as pl
@@ -197,8 +207,6 @@ class Batched:
     1K..4M, sum ~247M rows) in one batched call; the same problems as 512
     separate calls are timed beside it."""
     name = "batched"
-    prof_class = 6
-    kernel_name = "batch_probe_kernel"
 
     def __init__(self, master):
         from paper_2209_04579_b300 import datagen as dg
@@ -243,8 +251,9 @@ class Batched:
     def alg_bytes(self):
         return sum(n * 16 + m * 5 for _, n, m, _ in self.spec)
 
-    def dominant_bytes(self):
-        return sum(n * 16 for _, n, _, _ in self.spec)
+    def prof(self):
+        # fk (4), day (4) and v (8) of every fact row
+        return [(6, "batch_probe_kernel", sum(n * 16 for _, n, _, _ in self.spec))]
 
     def oracle_sample(self, rows):
         from oracle import pipelines as pl
@@ -268,8 +277,6 @@ class Star:
     dim2.cat): SUM(m1), SUM(m2), SUM(m3), COUNT(*), one fused call."""
     name = "star"
     n, n1, n2 = 600_000_000, 20_000_000, 150_000_000
-    prof_class = 1
-    kernel_name = "star_probe_kernel"
 
     def __init__(self, master):
         from paper_2209_04579_b300 import datagen as dg
@@ -299,8 +306,9 @@ class Star:
     def alg_bytes(self):
         return self.n * 40 + self.n1 * 6 + self.n2 * 9
 
-    def dominant_bytes(self):
-        return self.n * 40
+    def prof(self):
+        # fk1 (4), fk2 (8), date (4) and m1..m3 (24) of every fact row
+        return [(1, "star_probe_kernel", self.n * 40)]
 
     def oracle_sample(self, rows):
         from oracle import pipelines as pl
@@ -322,33 +330,89 @@ WORKLOADS = {"q14": Q14, "q6": Q6, "skew": Skew, "batched": Batched, "star": Sta
 # ---------------------------------------------------------------- helpers
 
 class ClockSampler:
+    """SM clock, its maximum and the clock-event (throttle) reasons, sampled
+    through NVML every 5 ms by a thread while the timed region runs, plus one
+    sample as it starts and one as it ends (nvidia-smi as a fallback)."""
+    REASONS = (("hw_slowdown", 0x8), ("sw_thermal_slowdown", 0x20), ("hw_thermal_slowdown", 0x40),
+               ("hw_power_brake_slowdown", 0x80), ("sw_power_cap", 0x4))
+
+    def __init__(self, device):
+        import threading
+        self.dev = device
+        self.samples = []
+        self.stop_evt = threading.Event()
+        self.thread = None
+        self.nv = self.h = None
+        self.smi = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            p = torch.cuda.get_device_properties(device)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+            self.h = pynvml.nvmlDeviceGetHandleByPciBusId(bus)
+            self.nv = pynvml
+        except Exception:
+            self.h = None
+
+    def _sample(self):
+        nv, h = self.nv, self.h
+        try:
+            sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
+            mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
+            get = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.samples.append((sm, mx, int(get(h))))
+        except Exception:
+            pass
+
+    def _loop(self):
+        while not self.stop_evt.wait(0.005):
+            self._sample()
+
+    def start(self):
+        import threading
+        if self.h is None:
+            self._start_smi()
+            return
+        self._sample()
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.h is None:
+            return self._stop_smi()
+        self.stop_evt.set()
+        self.thread.join()
+        self._sample()
+        if not self.samples:
+            return None
+        reasons = sorted({nm for _, _, r in self.samples for nm, bit in self.REASONS if r & bit})
+        return {"sm_mhz": statistics.median(x[0] for x in self.samples),
+                "sm_max_mhz": max(x[1] for x in self.samples), "reasons": reasons,
+                "samples": len(self.samples), "source": "nvml, 5 ms"}
+
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.idx = gpu_index
-        self.proc = None
-        self.path = None
-
-    def start(self):
+    def _start_smi(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            self.smi = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                         "--format=csv,noheader,nounits", "-lms", "200"],
+                                        stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
-            self.proc = None
+            self.smi = None
 
-    def stop(self):
-        if self.proc is None:
+    def _stop_smi(self):
+        if self.smi is None:
             return None
-        self.proc.terminate()
+        self.smi.terminate()
         try:
-            self.proc.wait(5)
+            self.smi.wait(5)
         except subprocess.TimeoutExpired:
-            self.proc.kill()
+            self.smi.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
@@ -367,7 +431,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 def dist_setup(args):
@@ -464,12 +528,17 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     assert tqp.tqp_status_poll() == tqp.OK
 
-    # capture one step into a CUDA graph, with the dominant kernel bracketed by events
-    ev_k0, ev_k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev_k0.record()  # torch creates the CUDA event at its first record
-    ev_k1.record()
+    # capture one step into a CUDA graph, with each profiled kernel class
+    # bracketed by its own pair of events
+    classes = [c for c, _, _ in W.prof()]
+    kev = {}
+    for c in classes:
+        kev[c] = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        kev[c][0].record()  # torch creates the CUDA event at its first record
+        kev[c][1].record()
     torch.cuda.synchronize()
-    tqp.tqp_profile_events(W.prof_class, ev_k0, ev_k1)
+    for c in classes:
+        tqp.tqp_profile_events(c, *kev[c])
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
@@ -480,7 +549,8 @@ def run_ours(args, world, rank, local):
     with torch.cuda.graph(g):
         out = W.step()
     launches_per_step = tqp.tqp_debug_launch_count() - n0
-    tqp.tqp_profile_events(W.prof_class, None, None)
+    for c in classes:
+        tqp.tqp_profile_events(c, None, None)
     torch.cuda.synchronize()
 
     for _ in range(args.warmup):
@@ -494,7 +564,7 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    step_ms, kern_ms = [], []
+    step_ms, kern_ms = [], {c: [] for c in classes}
     for _ in range(args.steps):
         flush.zero_()
         e0.record()
@@ -502,7 +572,8 @@ def run_ours(args, world, rank, local):
         e1.record()
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        kern_ms.append(ev_k0.elapsed_time(ev_k1))
+        for c in classes:
+            kern_ms[c].append(kev[c][0].elapsed_time(kev[c][1]))
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
@@ -512,9 +583,13 @@ def run_ours(args, world, rank, local):
     total_ms = max_over_ranks(sum(step_ms), world)
     rows_all = sum_over_ranks(W.rows() * args.steps, world)
     value = rows_all / (total_ms / 1e3)
-    kern_avg_ms = sum(kern_ms) / len(kern_ms)
     peak, peak_kind = peaks()
-    achieved = W.dominant_bytes() / (kern_avg_ms / 1e3) / 1e9
+    kern = []
+    for c, name, nbytes in W.prof():
+        ms = sum(kern_ms[c]) / len(kern_ms[c])
+        kern.append({"kernel": name, "ms": ms, "alg_bytes": nbytes, "gbs": nbytes / (ms / 1e3) / 1e9})
+    dom = max(kern, key=lambda k: k["ms"])
+    achieved = dom["gbs"]
 
     # ---- end to end through the public API from pinned host buffers (eager calls)
     host_in = [t.cpu().pin_memory() for t in inputs]
@@ -550,9 +625,10 @@ def run_ours(args, world, rank, local):
         "config": {**W.config(), "parallelism": f"replicas x{world} (independent instances, no collective)",
                    "l2": "flushed before every step (256 MB write, outside the step's events)",
                    "launch": "one CUDA graph replay per step"},
-        "roofline": {"bound": "hbm", "kernel": W.kernel_name, "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": dom["kernel"], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                     "kernel_ms": kern_avg_ms, "alg_bytes_per_launch": W.dominant_bytes(), "traffic": None},
+                     "kernel_ms": dom["ms"], "alg_bytes_per_launch": dom["alg_bytes"], "traffic": None},
+        "kernels": [{**k, "frac": k["gbs"] / peak} for k in kern],
         "step_roofline_frac": W.alg_bytes() / (total_ms / args.steps / 1e3) / 1e9 / peak,
         "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,

@@ -336,6 +336,8 @@ typedef struct {          /* written to device memory by the learned group-by */
   int64_t over_capacity;  /* buckets sorted by the global-memory fallback */
   int64_t nonempty;       /* non-empty buckets */
   int64_t over_capacity_rows; /* rows in buckets sorted by the fallback */
+  int64_t small_rows;     /* rows in buckets of 2..1024 rows (sorted by one warp
+                             when the bucket's key span is below 2^48) */
   float loss_first;       /* training loss before the first / the last step */
   float loss_last;
 } tqp_learned_stats;

@@ -268,21 +268,6 @@ __global__ void batch_init_acc_kernel(const BatchShape S, long long* acc, long l
   }
 }
 
-__device__ __forceinline__ void batch_fold(long long* slot, const BatchShape& S, const long long* ev) {
-#pragma unroll
-  for (int q = 0; q < TQP_MAX_AGGS; ++q) {
-    if (q < S.naggs) {
-      long long x = S.op[q] == TQP_COUNT ? 1 : ev[S.expr[q]];
-      switch (S.op[q]) {
-        case TQP_MIN: atomicMin(slot + q, x); break;
-        case TQP_MAX: atomicMax(slot + q, x); break;
-        default: atomicAdd(reinterpret_cast<unsigned long long*>(slot + q), (unsigned long long)x); break;
-      }
-    }
-  }
-  atomicAdd(reinterpret_cast<unsigned long long*>(slot + S.naggs), 1ull);
-}
-
 struct BatchProbeArgs {
   const ProbDir* pdir;
   const int* dir;
@@ -373,13 +358,19 @@ __global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, 
           }
           xq = (long long)v;
         }
+        unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dst + q);
         switch (op) {
           case TQP_MIN: atomicMin(dst + q, xq); break;
           case TQP_MAX: atomicMax(dst + q, xq); break;
-          default: atomicAdd(reinterpret_cast<unsigned long long*>(dst + q), (unsigned long long)xq); break;
+          default:
+            if (shared) shared_add_u64(d64, (unsigned long long)xq);
+            else atomicAdd(d64, (unsigned long long)xq);
+            break;
         }
       }
-      atomicAdd(reinterpret_cast<unsigned long long*>(dst + S.naggs), 1ull);
+      unsigned long long* c64 = reinterpret_cast<unsigned long long*>(dst + S.naggs);
+      if (shared) shared_add_u64(c64, 1ull);
+      else atomicAdd(c64, 1ull);
     }
     if (shared) {
       __syncthreads();

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/tqp.h"
 
 namespace tqp {
@@ -63,6 +65,22 @@ __device__ __forceinline__ bool compare(int64_t v, int op, int64_t lit) {
 }
 
 // ---------------------------------------------------------------- memory ops
+// Exact 64-bit add into a word in shared memory through native 32-bit
+// atomics.  The atomic on the low half returns the value it replaced, so each
+// wrap of the low half is seen by exactly one adder, which carries it into
+// the high half.  After a barrier the 8-byte word (little-endian halves)
+// equals the sum of all addends mod 2^64, whatever the order of the adds.
+// Shared-memory 64-bit adds have no single native instruction; this keeps a
+// contended SUM or COUNT to one 32-bit atomic (two when the addend's high
+// half is non-zero or the low half wraps).
+__device__ __forceinline__ void shared_add_u64(unsigned long long* p, unsigned long long x) {
+  unsigned* w = reinterpret_cast<unsigned*>(p);
+  const unsigned lo = (unsigned)x;
+  const unsigned old = atomicAdd(w, lo);
+  const unsigned hi = (unsigned)(x >> 32) + (unsigned)(old + lo < old);
+  if (hi) atomicAdd(w + 1, hi);
+}
+
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

@@ -27,6 +27,7 @@ constexpr int kGradChunk = 1024;  // samples per gradient block
 constexpr int kMaxHeavy = 1024;
 constexpr int kDirBits = 12;      // directory over the top bits of q
 constexpr int kLocalCap = 8192;   // rows a block sorts on-chip
+constexpr int kWarpCap = 1024;    // rows one warp sorts on-chip
 constexpr int kLocalThreads = 512;
 constexpr int kLocalWarps = kLocalThreads / 32;
 constexpr int kLocalItems = kLocalCap / kLocalThreads;  // 16
@@ -447,16 +448,17 @@ __global__ void __launch_bounds__(1024) lp_offsets_kernel(const LearnedPlan* lp,
   __shared__ int s_scan[33];
   __shared__ unsigned s_max[32];
   __shared__ int s_over[32], s_ne[32];
-  __shared__ unsigned long long s_orows[32];
+  __shared__ unsigned long long s_orows[32], s_srows[32];
   const int B = lp->B;
   const int per = (B + 1023) / 1024;
   const int b0 = threadIdx.x * per;
   unsigned sum = 0, mx = 0;
   int over = 0, ne = 0;
-  unsigned long long over_rows = 0;
+  unsigned long long over_rows = 0, small_rows = 0;
   for (int b = b0; b < b0 + per && b < B; ++b) {
     unsigned c = count[b];
     sum += c;
+    small_rows += (c > 1 && c <= (unsigned)kWarpCap) ? c : 0;
     mx = c > mx ? c : mx;
     over += c > (unsigned)kLocalCap;
     over_rows += c > (unsigned)kLocalCap ? c : 0;
@@ -481,24 +483,28 @@ __global__ void __launch_bounds__(1024) lp_offsets_kernel(const LearnedPlan* lp,
     over += __shfl_xor_sync(0xffffffffu, over, o);
     ne += __shfl_xor_sync(0xffffffffu, ne, o);
     over_rows += __shfl_xor_sync(0xffffffffu, over_rows, o);
+    small_rows += __shfl_xor_sync(0xffffffffu, small_rows, o);
   }
   if ((threadIdx.x & 31) == 0) {
     s_max[threadIdx.x >> 5] = mx;
     s_over[threadIdx.x >> 5] = over;
     s_ne[threadIdx.x >> 5] = ne;
     s_orows[threadIdx.x >> 5] = over_rows;
+    s_srows[threadIdx.x >> 5] = small_rows;
   }
   __syncthreads();
   if (threadIdx.x == 0 && stats) {
     unsigned m3 = 0;
-    long long o3 = 0, n3 = 0, r3 = 0;
+    long long o3 = 0, n3 = 0, r3 = 0, q3 = 0;
     for (int w = 0; w < 32; ++w) {
+      q3 += (long long)s_srows[w];
       m3 = s_max[w] > m3 ? s_max[w] : m3;
       o3 += s_over[w];
       n3 += s_ne[w];
       r3 += (long long)s_orows[w];
     }
     stats->over_capacity_rows = r3;
+    stats->small_rows = q3;
     stats->buckets = B;
     stats->heavy_keys = lp->nheavy;
     stats->light_rows = total;
@@ -520,6 +526,16 @@ __device__ __forceinline__ void fold_atomic(long long* slot, int op, long long x
     case TQP_MIN: atomicMin(slot, x); break;
     case TQP_MAX: atomicMax(slot, x); break;
     default: atomicAdd(reinterpret_cast<unsigned long long*>(slot), (unsigned long long)x); break;
+  }
+}
+
+// The same fold into an accumulator in shared memory (SUM and COUNT through
+// the split 32-bit adds).
+__device__ __forceinline__ void fold_shared(long long* slot, int op, long long x) {
+  switch (op) {
+    case TQP_MIN: atomicMin(slot, x); break;
+    case TQP_MAX: atomicMax(slot, x); break;
+    default: shared_add_u64(reinterpret_cast<unsigned long long*>(slot), (unsigned long long)x); break;
   }
 }
 
@@ -561,7 +577,7 @@ __global__ void __launch_bounds__(256) lp_scatter_kernel(PartArgs a, AggProgram 
           long long y = __shfl_sync(peers, x, __ffs(others) - 1);
           acc = agg_fold(op, acc, y);
         }
-        if (lane == leader) fold_atomic(&s_acc[h * P.naggs + q], op, acc);
+        if (lane == leader) fold_shared(&s_acc[h * P.naggs + q], op, acc);
       }
     } else if (h == -1) {
       int b = lp_bucket(p, lp, s_dir, a.thr);
@@ -819,7 +835,6 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
 // words are LSD-sorted on their key bits in the warp's shared memory (the low
 // 16 bits only carry the original index back), and the rows are permuted by
 // the recovered indices.  No block barrier is involved.
-constexpr int kWarpCap = 1024;
 constexpr int kWarpItems = kWarpCap / 32;
 constexpr int kWarpSortWarps = 4;
 

@@ -142,6 +142,7 @@ __global__ void star_slots_kernel(StarPlan* plan, int ndims, const long long* d_
 
 struct StarAcc {
   int naggs;
+  int cnt;               // accumulator that counts rows: a COUNT aggregate, else naggs
   int op[TQP_MAX_AGGS];  // aggregate ops; accumulator naggs holds the row count
   int expr[TQP_MAX_AGGS];
   int nexprs;
@@ -287,30 +288,17 @@ struct ProbeArgs {
   uint32_t num_tiles;
 };
 
-__device__ __forceinline__ void fold_slot(long long* acc, const StarAcc& A, const long long* ev) {
-#pragma unroll
-  for (int q = 0; q < TQP_MAX_AGGS; ++q) {
-    if (q < A.naggs) {
-      long long x = (A.op[q] == TQP_COUNT) ? 1 : ev[A.expr[q]];
-      unsigned long long* p = reinterpret_cast<unsigned long long*>(acc + q);
-      switch (A.op[q]) {
-        case TQP_MIN: atomicMin(reinterpret_cast<long long*>(p), x); break;
-        case TQP_MAX: atomicMax(reinterpret_cast<long long*>(p), x); break;
-        default: atomicAdd(p, (unsigned long long)x); break;
-      }
-    }
-  }
-  atomicAdd(reinterpret_cast<unsigned long long*>(acc + A.naggs), 1ull);
-}
-
 // Each thread carries ITEMS independent fact rows through the stages
 // (predicates, then per dimension: cell bit, directory bounds, key compare;
 // then values and the fold), so that ITEMS memory chains are in flight.
 // SMEM_BM: the first dimension's cell bitmap is copied into dynamic shared
 // memory (when it fits in smem_bm_words) so that a miss costs one shared
 // read; used for small first dimensions, one large block per SM.
-template <int THREADS, int ITEMS, bool SMEM_BM>
+// K32: every dimension key is int32, so the key image, its range test and
+// the cell index are 32-bit arithmetic.
+template <int THREADS, int ITEMS, bool SMEM_BM, bool K32>
 __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(ProbeArgs a, StarAcc Ag, int smem_bm_words) {
+  using UK = typename std::conditional<K32, uint32_t, unsigned long long>::type;
   constexpr int TILE = THREADS * ITEMS;
   __shared__ long long s_acc[kSmemAccWords];
   __shared__ uint32_t s_tile;
@@ -393,19 +381,22 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     for (int d = 0; d < kMaxDims; ++d) {
       if (d >= a.ndims) break;
       const ProbeDim& D = a.dim[d];
-      unsigned long long u[ITEMS];
-      long long c[ITEMS];
+      UK u[ITEMS];
+      UK c[ITEMS];
+      const UK umin = (UK)dd[d].umin, umax = (UK)dd[d].umax;
+      const int bshift = dd[d].bshift;
       // A: key image and cell, cell bit
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
         c[k] = 0;
         if (live[k]) {
           const int64_t r = base + (int64_t)k * THREADS;
-          u[k] = D.key_dt == TQP_I32
-                     ? (unsigned long long)((uint32_t)__ldcs(static_cast<const int32_t*>(D.fk) + r) ^ 0x80000000u)
-                     : ((unsigned long long)__ldcs(static_cast<const long long*>(D.fk) + r) ^ 0x8000000000000000ull);
-          if (u[k] < dd[d].umin || u[k] > dd[d].umax) live[k] = false;
-          else c[k] = (long long)((u[k] - dd[d].umin) >> dd[d].bshift);
+          if (K32 || D.key_dt == TQP_I32)
+            u[k] = (UK)((uint32_t)__ldcs(static_cast<const int32_t*>(D.fk) + r) ^ 0x80000000u);
+          else
+            u[k] = (UK)((unsigned long long)__ldcs(static_cast<const long long*>(D.fk) + r) ^ 0x8000000000000000ull);
+          if (u[k] < umin || u[k] > umax) live[k] = false;
+          else c[k] = (u[k] - umin) >> bshift;
         }
       }
 #pragma unroll
@@ -445,11 +436,11 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
         int l = lo[k], h = hi[k];
         while (h - l > 4) {
           int mid = (l + h) >> 1;
-          if (key_image(D.skeys, D.key_dt, mid) < u[k]) l = mid + 1; else h = mid;
+          if ((UK)key_image(D.skeys, D.key_dt, mid) < u[k]) l = mid + 1; else h = mid;
         }
         int found = -1;
         for (int i = l; i < hi[k]; ++i) {
-          unsigned long long ki = key_image(D.skeys, D.key_dt, i);
+          const UK ki = (UK)key_image(D.skeys, D.key_dt, i);
           if (ki >= u[k]) {
             if (ki == u[k]) found = i;
             break;
@@ -490,13 +481,21 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
           }
           x = (long long)ev;
         }
+        unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dst + q);
         switch (op) {
           case TQP_MIN: atomicMin(dst + q, x); break;
           case TQP_MAX: atomicMax(dst + q, x); break;
-          default: atomicAdd(reinterpret_cast<unsigned long long*>(dst + q), (unsigned long long)x); break;
+          default:
+            if (use_smem) shared_add_u64(d64, (unsigned long long)x);
+            else atomicAdd(d64, (unsigned long long)x);
+            break;
         }
       }
-      atomicAdd(reinterpret_cast<unsigned long long*>(dst + A.naggs), 1ull);
+      if (A.cnt == A.naggs) {  // no COUNT aggregate: the extra accumulator counts the rows
+        unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dst + A.naggs);
+        if (use_smem) shared_add_u64(d64, 1ull);
+        else atomicAdd(d64, 1ull);
+      }
     }
   }
   if (use_smem) {
@@ -521,6 +520,7 @@ struct CompactArgs {
   const StarPlan* plan;
   const long long* acc;
   int naggs;
+  int cnt;  // accumulator that counts rows (non-zero: the slot is a group)
   int ndims;
   const long long* gkey[kMaxDims];  // per dimension group key values by rank (null: no group column)
   int out_key_index[kMaxDims];      // which output key column (or -1)
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(THREADS) star_compact_kernel(CompactArgs a) {
     uint32_t live = 0;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k)
-      if (base + k < S && a.acc[(base + k) * nacc + a.naggs] > 0) live |= 1u << k;
+      if (base + k < S && a.acc[(base + k) * nacc + a.cnt] > 0) live |= 1u << k;
     int total;
     int off = block_exclusive_sum<THREADS>(__popc(live), s_scan, &total);
     if (warp == 0) {

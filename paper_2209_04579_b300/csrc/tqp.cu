@@ -711,6 +711,9 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
     A.op[q] = aggs[q].op;
     A.expr[q] = aggs[q].op == TQP_COUNT ? 0 : aggs[q].expr;
   }
+  A.cnt = naggs;
+  for (int q = naggs - 1; q >= 0; --q)
+    if (aggs[q].op == TQP_COUNT) A.cnt = q;
   // ---- workspace
   Carver c(ws);
   StarDimWs W[kMaxDims];
@@ -945,13 +948,18 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
   TQP_CUDA(cudaMemsetAsync(pcounter, 0, 4, s));
   if (ptiles > 0) {
     prof_mark(1, true, s);
+    bool k32 = true;
+    for (int d = 0; d < ndims; ++d) k32 = k32 && dims[d].key.dtype == TQP_I32;
     if (dims[0].n <= kSmemBitmapDimRows) {
       // small first dimension: its bitmap can live in shared memory
-      auto pk = star_probe_kernel<1024, 4, true>;
+      auto pk = k32 ? star_probe_kernel<1024, 4, true, true> : star_probe_kernel<1024, 4, true, false>;
       const int words = kSmemBitmapBytes / 4;
       static bool attr = false;
       if (!attr) {
-        cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBitmapBytes);
+        cudaFuncSetAttribute(star_probe_kernel<1024, 4, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBitmapBytes);
+        cudaFuncSetAttribute(star_probe_kernel<1024, 4, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBitmapBytes);
         attr = true;
       }
       const int64_t t1024 = (n_fact + 1024 * 4 - 1) / (1024 * 4);
@@ -959,7 +967,7 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
       pk<<<persistent_grid(pk, 1024, kSmemBitmapBytes, t1024), 1024, kSmemBitmapBytes, s>>>(pa, A, words);
       note_launch();
     } else {
-      auto pk = star_probe_kernel<kProbeT, kProbeI, false>;
+      auto pk = k32 ? star_probe_kernel<kProbeT, kProbeI, false, true> : star_probe_kernel<kProbeT, kProbeI, false, false>;
       pk<<<persistent_grid(pk, kProbeT, 0, ptiles), kProbeT, 0, s>>>(pa, A, 0); note_launch();
     }
     prof_mark(1, false, s);
@@ -969,6 +977,7 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
   ca.plan = plan;
   ca.acc = acc;
   ca.naggs = naggs;
+  ca.cnt = A.cnt;
   ca.ndims = ndims;
   int ok = 0;
   for (int d = 0; d < ndims; ++d) {

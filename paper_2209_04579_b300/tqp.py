@@ -87,7 +87,7 @@ class LearnedCfg(ctypes.Structure):
 class LearnedStats(ctypes.Structure):
     _fields_ = [("buckets", ctypes.c_int64), ("heavy_keys", ctypes.c_int64), ("light_rows", ctypes.c_int64),
                 ("max_bucket", ctypes.c_int64), ("over_capacity", ctypes.c_int64), ("nonempty", ctypes.c_int64),
-                ("over_capacity_rows", ctypes.c_int64),
+                ("over_capacity_rows", ctypes.c_int64), ("small_rows", ctypes.c_int64),
                 ("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float)]
 
 
