@@ -8,7 +8,7 @@ $TQP_AUTOTUNE_CACHE, else ~/.cache/tqp/autotune.json.
 
 Tuned parameters:
   batched  -- fact rows per thread of the batched probe tile (4, 8, 16);
-  learned  -- number of learned buckets B (n/1024 .. n/4096, powers of two).
+  learned  -- number of learned buckets B (about n/512 .. n/4096, powers of two).
 """
 from __future__ import annotations
 
@@ -92,10 +92,13 @@ def tune_learned(run, rows, candidates=None, force=False):
     if not force and k in cache:
         return int(cache[k]["best"]), cache[k]
     if candidates is None:
+        # from about 512 rows per bucket (most buckets sorted by one warp)
+        # down to about 4096 (buckets sorted by one block; the steps of the
+        # bucket function fit in shared memory up to 2^15 buckets)
         base = 256
         while base < (1 << 17) and base * 512 < rows:
             base <<= 1
-        candidates = sorted({max(256, base // 2), base, min(1 << 17, base * 2)})
+        candidates = sorted({max(256, base >> s) for s in range(4)})
     times, ref = {}, None
     for b in candidates:
         times[b] = _time(lambda b=b: run(b))

@@ -196,6 +196,7 @@ struct LearnedPlan {
   int B;
   int nheavy;
   int min_count;
+  int slight;           // sample keys that are not heavy
 };
 
 // Identity CDF F(x) = x on [0, 1]: unit j ramps over [j/H, (j+1)/H].
@@ -270,15 +271,52 @@ __device__ __forceinline__ int64_t ub_u64(const unsigned long long* a, int64_t l
   return lo;
 }
 
-// Training pairs from the sorted sample: x = normalised key, y = empirical
-// CDF midpoint (first rank + count / 2) / S of its key.
-__global__ void lp_targets_kernel(const unsigned long long* sorted, int S, const LearnedPlan* lp, float* x, float* y) {
+__device__ __forceinline__ bool in_sorted_list(const unsigned long long* a, int n, unsigned long long x) {
+  int lo = 0, len = n;
+  while (len > 0) {
+    int h = len >> 1;
+    if (a[lo + h] < x) { lo += h + 1; len -= h + 1; } else { len = h; }
+  }
+  return lo < n && a[lo] == x;
+}
+
+// Light prefix of the sorted sample: lpre[i] = sample keys before i that are
+// not heavy, and their total.  One block of 1024 threads, contiguous chunks.
+__global__ void __launch_bounds__(1024) lp_light_prefix_kernel(const unsigned long long* sorted, int S,
+                                                               const unsigned long long* heavy, LearnedPlan* lp,
+                                                               int32_t* lpre) {
+  __shared__ int s_scan[33];
+  const int nh = lp->nheavy;
+  const int per = (S + 1023) / 1024;
+  const int i0 = threadIdx.x * per;
+  const int i1 = i0 + per < S ? i0 + per : S;
+  int cnt = 0;
+  for (int i = i0; i < i1; ++i) cnt += !(nh && in_sorted_list(heavy, nh, sorted[i]));
+  int total;
+  int run = block_exclusive_sum<1024>(cnt, s_scan, &total);
+  for (int i = i0; i < i1; ++i) {
+    lpre[i] = run;
+    run += !(nh && in_sorted_list(heavy, nh, sorted[i]));
+  }
+  if (threadIdx.x == 0) lp->slight = total;
+}
+
+// Training pairs from the sorted sample: x = normalised key, y = the CDF of
+// the light rows (the rows the buckets receive) at the key's midpoint:
+// (light keys before the key + its light count / 2) / light total.  A heavy
+// key has no light count: its pair sits on the light CDF with zero width.
+// Without heavy keys this is (first rank + count / 2) / S.
+__global__ void lp_targets_kernel(const unsigned long long* sorted, int S, const LearnedPlan* lp,
+                                  const unsigned long long* heavy, const int32_t* lpre, float* x, float* y) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S) return;
   unsigned long long k = sorted[i];
   int64_t lo = lb_u64(sorted, S, k);
   int64_t hi = ub_u64(sorted, lo, S, k);
-  y[i] = (float)(((double)lo + 0.5 * (double)(hi - lo)) / (double)S);
+  const int nh = lp->nheavy;
+  const double light = (nh && in_sorted_list(heavy, nh, k)) ? 0.0 : (double)(hi - lo);
+  const double tot = lp->slight > 0 ? (double)lp->slight : 1.0;
+  y[i] = (float)(((double)lpre[lo] + 0.5 * light) / tot);
   x[i] = (float)(k >> lp->shift) * lp->inv;
 }
 
@@ -328,15 +366,25 @@ __global__ void __launch_bounds__(1024) lp_heavy_kernel(const unsigned long long
   if (threadIdx.x == 0) lp->nheavy = s_base;
 }
 
-// Knots at the sample's 1/H quantiles: unit j ramps from x_(jS/H) to
-// x_((j+1)S/H) with weight 1/H, so F is the piecewise-linear empirical CDF
-// (a ramp at least one q step wide stands for a vertical step).
-__global__ void lp_quantile_init_kernel(const float* xs, int S, const LearnedPlan* lp, tqp_cdf_model* md) {
+// Knots at the quantiles of the training targets: unit j ramps from the
+// first x whose target reaches j/H to the first whose target reaches
+// (j+1)/H, with weight 1/H, so F starts as the piecewise-linear empirical CDF
+// of the light rows (a ramp at least one q step wide stands for a step).
+__device__ __forceinline__ int first_at_least(const float* ys, int S, float t) {
+  int lo = 0, len = S;
+  while (len > 0) {
+    int h = len >> 1;
+    if (ys[lo + h] < t) { lo += h + 1; len -= h + 1; } else { len = h; }
+  }
+  return lo < S ? lo : S - 1;
+}
+
+__global__ void lp_quantile_init_kernel(const float* xs, const float* ys, int S, const LearnedPlan* lp,
+                                        tqp_cdf_model* md) {
   const int j = threadIdx.x;
   if (j >= kH) return;
-  int i0 = (int)((long long)j * S / kH);
-  int i1 = (int)((long long)(j + 1) * S / kH);
-  if (i1 > S - 1) i1 = S - 1;
+  int i0 = first_at_least(ys, S, (float)j / (float)kH);
+  int i1 = first_at_least(ys, S, (float)(j + 1) / (float)kH);
   float x0 = xs[i0], x1 = xs[i1];
   float step = lp->inv > 0.0f ? lp->inv : 1.0f;
   float width = x1 - x0 > step ? x1 - x0 : step;
@@ -384,6 +432,10 @@ __global__ void lp_directory_kernel(const LearnedPlan* lp, const unsigned* thr, 
   dir[h] = lo;
 }
 
+// Bucket of packed key p: the directory narrows the steps to those of q's
+// top bits, a binary search finds the first step above q.  thr is in shared
+// memory (THR_SMEM) or global memory.
+template <bool THR_SMEM>
 __device__ __forceinline__ int lp_bucket(unsigned long long p, const LearnedPlan& lp, const int* s_dir,
                                          const unsigned* thr) {
   unsigned long long q = p >> lp.shift;
@@ -391,18 +443,10 @@ __device__ __forceinline__ int lp_bucket(unsigned long long p, const LearnedPlan
   int lo = s_dir[h], hi = s_dir[h + 1];
   while (lo < hi) {  // first step above q
     int mid = (lo + hi) >> 1;
-    if ((unsigned long long)thr[mid] <= q) lo = mid + 1; else hi = mid;
+    const unsigned t = THR_SMEM ? thr[mid] : __ldg(&thr[mid]);
+    if ((unsigned long long)t <= q) lo = mid + 1; else hi = mid;
   }
   return lo;
-}
-
-__device__ __forceinline__ int heavy_index(const unsigned long long* s_heavy, int nh, unsigned long long p) {
-  int lo = 0, len = nh;
-  while (len > 0) {
-    int half = len >> 1;
-    if (s_heavy[lo + half] < p) { lo += half + 1; len -= half + 1; } else { len = half; }
-  }
-  return (lo < nh && s_heavy[lo] == p) ? lo : -1;
 }
 
 struct PartArgs {
@@ -422,21 +466,127 @@ struct PartArgs {
   long long* heavy_acc;     // [nheavy][naggs]
 };
 
-// Light rows per bucket.
-__global__ void __launch_bounds__(256) lp_hist_kernel(PartArgs a) {
-  __shared__ int s_dir[(1 << kDirBits) + 1];
-  __shared__ unsigned long long s_heavy[kMaxHeavy];
-  const LearnedPlan lp = *a.lp;
-  for (int i = threadIdx.x; i <= (1 << kDirBits); i += blockDim.x) s_dir[i] = a.dir[i];
-  for (int i = threadIdx.x; i < lp.nheavy; i += blockDim.x) s_heavy[i] = a.heavy[i];
+// ---- partition kernels: shared-memory layout and setup
+constexpr int kHeavyBits = 11;
+constexpr int kHeavySlots = 1 << kHeavyBits;  // open addressing, load <= 1/2
+constexpr int kPartThreads = 1024;
+constexpr int kPartItems = 4;
+
+// Dynamic shared memory: directory, heavy-key table (key, index; index -1 =
+// empty), the heavy accumulators (scatter) and, when they fit, the steps.
+struct PartSmem {
+  int* dir;
+  unsigned long long* hk;
+  int* hv;
+  long long* acc;
+  unsigned* thr;
+};
+
+inline __host__ __device__ size_t part_smem_bytes(int B, int naggs, bool thr_smem) {
+  size_t o = ((((size_t)1 << kDirBits) + 1) * 4 + 15) & ~(size_t)15;
+  o += (size_t)kHeavySlots * 8 + (size_t)kHeavySlots * 4;
+  o += (size_t)kMaxHeavy * naggs * 8;
+  if (thr_smem) o += (size_t)(B > 1 ? B - 1 : 1) * 4;
+  return o;
+}
+
+__device__ __forceinline__ PartSmem part_carve(unsigned char* base, int naggs) {
+  PartSmem S;
+  size_t o = ((((size_t)1 << kDirBits) + 1) * 4 + 15) & ~(size_t)15;
+  S.dir = reinterpret_cast<int*>(base);
+  S.hk = reinterpret_cast<unsigned long long*>(base + o);
+  o += (size_t)kHeavySlots * 8;
+  S.hv = reinterpret_cast<int*>(base + o);
+  o += (size_t)kHeavySlots * 4;
+  S.acc = reinterpret_cast<long long*>(base + o);
+  o += (size_t)kMaxHeavy * naggs * 8;
+  S.thr = reinterpret_cast<unsigned*>(base + o);
+  return S;
+}
+
+__device__ __forceinline__ int heavy_slot(unsigned long long p) {
+  return (int)((p * 0x9E3779B97F4A7C15ull) >> (64 - kHeavyBits));
+}
+
+// Index of p among the heavy keys, or -1.  The table is at most half full,
+// so a probe sequence ends at an empty slot.
+__device__ __forceinline__ int heavy_lookup(const PartSmem& S, unsigned long long p) {
+  int slot = heavy_slot(p);
+  for (int t = 0; t < kHeavySlots; ++t) {
+    const int v = S.hv[slot];
+    if (v < 0) return -1;
+    if (S.hk[slot] == p) return v;
+    slot = (slot + 1) & (kHeavySlots - 1);
+  }
+  return -1;
+}
+
+// The key columns and their packing, staged in shared memory.
+struct PackPlan {
+  int nkeys;
+  const void* col[TQP_MAX_KEYS];
+  int dt[TQP_MAX_KEYS];
+  long long kmin[TQP_MAX_KEYS];
+  int shift[TQP_MAX_KEYS];
+};
+
+__device__ __forceinline__ unsigned long long pack_row_plan(const PackPlan& K, int64_t row) {
+  unsigned long long u = 0;
+  for (int k = 0; k < K.nkeys; ++k)
+    u |= ((unsigned long long)load_as_i64(K.col[k], K.dt[k], row) - (unsigned long long)K.kmin[k]) << K.shift[k];
+  return u;
+}
+
+// Directory, heavy table, steps (THR_SMEM) and key plan into shared memory.
+template <bool THR_SMEM>
+__device__ __forceinline__ void part_setup(const PartArgs& a, const LearnedPlan& lp, const PartSmem& S, PackPlan& K) {
+  for (int i = threadIdx.x; i <= (1 << kDirBits); i += blockDim.x) S.dir[i] = a.dir[i];
+  for (int i = threadIdx.x; i < kHeavySlots; i += blockDim.x) S.hv[i] = -1;
+  if (THR_SMEM)
+    for (int i = threadIdx.x; i < lp.B - 1; i += blockDim.x) S.thr[i] = a.thr[i];
+  if (threadIdx.x == 0) {
+    K.nkeys = a.ks.nkeys;
+    for (int k = 0; k < TQP_MAX_KEYS; ++k) {
+      K.col[k] = a.ks.col[k];
+      K.dt[k] = a.ks.dt[k];
+      K.kmin[k] = a.gp->kmin[k];
+      K.shift[k] = a.gp->shift[k];
+    }
+  }
   __syncthreads();
+  for (int i = threadIdx.x; i < lp.nheavy; i += blockDim.x) {
+    const unsigned long long p = a.heavy[i];
+    int slot = heavy_slot(p);
+    while (atomicCAS(&S.hv[slot], -1, i) != -1) slot = (slot + 1) & (kHeavySlots - 1);
+    S.hk[slot] = p;
+  }
+  __syncthreads();
+}
+
+// Light rows per bucket.  Each thread carries kPartItems rows at a time.
+template <bool THR_SMEM>
+__global__ void __launch_bounds__(kPartThreads, 1) lp_hist_kernel(PartArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ PackPlan K;
+  const LearnedPlan lp = *a.lp;
+  const PartSmem S = part_carve(smem, 0);
+  part_setup<THR_SMEM>(a, lp, S, K);
+  const unsigned* thr = THR_SMEM ? S.thr : a.thr;
+  const int nh = lp.nheavy;
   const int64_t n = clamp_n(a.n_max, a.d_n);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    int64_t row = a.sel ? a.sel[i] : i;
-    unsigned long long p = pack_row(a.ks, a.gp, row);
-    if (lp.nheavy && heavy_index(s_heavy, lp.nheavy, p) >= 0) continue;
-    atomicAdd(&a.count[lp_bucket(p, lp, s_dir, a.thr)], 1u);
+  constexpr int TILE = kPartThreads * kPartItems;
+  for (int64_t base = (int64_t)blockIdx.x * TILE; base < n; base += (int64_t)gridDim.x * TILE) {
+    unsigned long long p[kPartItems];
+    bool v[kPartItems];
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) {
+      const int64_t i = base + k * kPartThreads + threadIdx.x;
+      v[k] = i < n;
+      p[k] = v[k] ? pack_row_plan(K, a.sel ? (int64_t)a.sel[i] : i) : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k)
+      if (v[k] && (nh == 0 || heavy_lookup(S, p[k]) < 0)) atomicAdd(&a.count[lp_bucket<THR_SMEM>(p[k], lp, S.dir, thr)], 1u);
   }
 }
 
@@ -540,55 +690,72 @@ __device__ __forceinline__ void fold_shared(long long* slot, int op, long long x
 }
 
 // Scatter of the light rows into their buckets; heavy rows folded into
-// per-block shared accumulators, flushed with atomics at the end.
-__global__ void __launch_bounds__(256) lp_scatter_kernel(PartArgs a, AggProgram P) {
-  __shared__ int s_dir[(1 << kDirBits) + 1];
-  __shared__ unsigned long long s_heavy[kMaxHeavy];
-  extern __shared__ long long s_acc[];  // [nheavy][naggs]
+// per-block shared accumulators (rows of one heavy key within a warp
+// combined first), flushed with atomics at the end.  The trip count is
+// uniform over the block, so every lane reaches each warp collective.
+template <bool THR_SMEM>
+__global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a, AggProgram P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ PackPlan K;
   const LearnedPlan lp = *a.lp;
+  const PartSmem S = part_carve(smem, P.naggs);
   const int nh = lp.nheavy;
-  for (int i = threadIdx.x; i <= (1 << kDirBits); i += blockDim.x) s_dir[i] = a.dir[i];
-  for (int i = threadIdx.x; i < nh; i += blockDim.x) s_heavy[i] = a.heavy[i];
-  for (int i = threadIdx.x; i < nh * P.naggs; i += blockDim.x) s_acc[i] = agg_identity(P.op[i % P.naggs]);
-  __syncthreads();
+  for (int i = threadIdx.x; i < nh * P.naggs; i += blockDim.x) S.acc[i] = agg_identity(P.op[i % P.naggs]);
+  part_setup<THR_SMEM>(a, lp, S, K);
+  const unsigned* thr = THR_SMEM ? S.thr : a.thr;
   const int64_t n = clamp_n(a.n_max, a.d_n);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
-  // warp-uniform trip count (lanes past n carry h = -2), so that rows of the
-  // same heavy key within a warp are combined before one shared atomic
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-    const int64_t i = base + threadIdx.x;
-    int64_t row = 0;
-    unsigned long long p = 0;
-    int h = -2;
-    if (i < n) {
-      row = a.sel ? a.sel[i] : i;
-      p = pack_row(a.ks, a.gp, row);
-      h = nh ? heavy_index(s_heavy, nh, p) : -1;
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, h);
-    if (h >= 0) {
-      const int leader = __ffs(peers) - 1;
-      for (int q = 0; q < P.naggs; ++q) {
-        const int op = P.op[q];
-        long long x = op == TQP_COUNT ? 1 : eval_expr(P, P.expr[q], row);
-        long long acc = x;
-        for (unsigned others = peers & ~(1u << leader); others; others &= others - 1) {
-          long long y = __shfl_sync(peers, x, __ffs(others) - 1);
-          acc = agg_fold(op, acc, y);
-        }
-        if (lane == leader) fold_shared(&s_acc[h * P.naggs + q], op, acc);
+  constexpr int TILE = kPartThreads * kPartItems;
+  for (int64_t base = (int64_t)blockIdx.x * TILE; base < n; base += (int64_t)gridDim.x * TILE) {
+    unsigned long long p[kPartItems];
+    int64_t row[kPartItems];
+    int h[kPartItems];
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) {
+      const int64_t i = base + k * kPartThreads + threadIdx.x;
+      row[k] = 0;
+      p[k] = 0;
+      h[k] = -2;  // past the end
+      if (i < n) {
+        row[k] = a.sel ? (int64_t)a.sel[i] : i;
+        p[k] = pack_row_plan(K, row[k]);
+        h[k] = nh ? heavy_lookup(S, p[k]) : -1;
       }
-    } else if (h == -1) {
-      int b = lp_bucket(p, lp, s_dir, a.thr);
-      unsigned pos = atomicAdd(&a.cursor[b], 1u);
-      a.out_p[pos] = p;
-      a.out_row[pos] = (int32_t)row;
+    }
+    // light rows: bucket, cursor, store
+    unsigned pos[kPartItems];
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k)
+      if (h[k] == -1) pos[k] = atomicAdd(&a.cursor[lp_bucket<THR_SMEM>(p[k], lp, S.dir, thr)], 1u);
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k)
+      if (h[k] == -1) {
+        a.out_p[pos[k]] = p[k];
+        a.out_row[pos[k]] = (int32_t)row[k];
+      }
+    // heavy rows: combined within the warp per key, one shared fold each
+    if (nh) {
+#pragma unroll
+      for (int k = 0; k < kPartItems; ++k) {
+        const unsigned peers = __match_any_sync(0xffffffffu, h[k]);
+        if (h[k] < 0) continue;
+        const int leader = __ffs(peers) - 1;
+        for (int q = 0; q < P.naggs; ++q) {
+          const int op = P.op[q];
+          long long x = op == TQP_COUNT ? 1 : eval_expr(P, P.expr[q], row[k]);
+          long long acc = x;
+          for (unsigned others = peers & ~(1u << leader); others; others &= others - 1) {
+            long long y = __shfl_sync(peers, x, __ffs(others) - 1);
+            acc = agg_fold(op, acc, y);
+          }
+          if (lane == leader) fold_shared(&S.acc[h[k] * P.naggs + q], op, acc);
+        }
+      }
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nh * P.naggs; i += blockDim.x) {
-    long long v = s_acc[i];
+    long long v = S.acc[i];
     int op = P.op[i % P.naggs];
     if (v != agg_identity(op)) fold_atomic(&a.heavy_acc[i], op, v);
   }
@@ -597,17 +764,19 @@ __global__ void __launch_bounds__(256) lp_scatter_kernel(PartArgs a, AggProgram 
 // ---------------------------------------------------------------- bucket sort
 // Stable rank within a block whose warp w owns items [w * per, (w + 1) * per)
 // in rounds of 32: returns in pos[] the block-local destination of each item
-// for digit values dig[] (kRadix = invalid).  s_cnt: [WARPS][kRadix + 1],
+// for digit values dig[] (kRadix = invalid).  Only the first `rounds` rounds
+// hold items (the same count in every warp).  s_cnt: [WARPS][kRadix + 1],
 // s_start: [kRadix] (exclusive digit starts), s_scan: 33 ints.
 template <int WARPS, int ITEMS>
-__device__ __forceinline__ void block_rank(const unsigned (&dig)[ITEMS], int (&pos)[ITEMS], unsigned* s_cnt,
-                                           unsigned* s_start, int* s_scan, int* total_out) {
+__device__ __forceinline__ void block_rank(const unsigned (&dig)[ITEMS], int (&pos)[ITEMS], int rounds,
+                                           unsigned* s_cnt, unsigned* s_start, int* s_scan, int* total_out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < WARPS * (kRadix + 1); i += WARPS * 32) s_cnt[i] = 0;
   __syncthreads();
   unsigned rank[ITEMS];
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
+    if (it >= rounds) break;
     unsigned peers = __match_any_sync(0xffffffffu, dig[it]);
     int leader = 31 - __clz(peers);
     unsigned before = __popc(peers & ((1u << lane) - 1));
@@ -635,7 +804,9 @@ __device__ __forceinline__ void block_rank(const unsigned (&dig)[ITEMS], int (&p
   __syncthreads();
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it)
-    pos[it] = dig[it] < kRadix ? (int)(s_start[dig[it]] + s_cnt[warp * (kRadix + 1) + dig[it]] + rank[it]) : -1;
+    pos[it] = (it < rounds && dig[it] < kRadix)
+                  ? (int)(s_start[dig[it]] + s_cnt[warp * (kRadix + 1) + dig[it]] + rank[it])
+                  : -1;
   *total_out = total;
   __syncthreads();
 }
@@ -732,7 +903,7 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
           dig[it] = v ? (unsigned)(((kA[i] - pmin) >> sh) & (kRadix - 1)) : kRadix;
         }
         int total;
-        block_rank<kLocalWarps, kLocalItems>(dig, pos, s_cnt, s_start, s_scan, &total);
+        block_rank<kLocalWarps, kLocalItems>(dig, pos, (per + 31) >> 5, s_cnt, s_start, s_scan, &total);
 #pragma unroll
         for (int it = 0; it < kLocalItems; ++it) {
           if (pos[it] >= 0) {
@@ -795,7 +966,7 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
             dig[it] = v ? (unsigned)(((kk[it] - pmin) >> sh) & (kRadix - 1)) : kRadix;
           }
           int total;
-          block_rank<kLocalWarps, kLocalItems>(dig, pos, s_cnt, s_start, s_scan, &total);
+          block_rank<kLocalWarps, kLocalItems>(dig, pos, (per + 31) >> 5, s_cnt, s_start, s_scan, &total);
 #pragma unroll
           for (int it = 0; it < kLocalItems; ++it) {
             if (pos[it] >= 0) {

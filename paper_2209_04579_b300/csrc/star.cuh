@@ -288,9 +288,73 @@ struct ProbeArgs {
   uint32_t num_tiles;
 };
 
-// Each thread carries ITEMS independent fact rows through the stages
-// (predicates, then per dimension: cell bit, directory bounds, key compare;
-// then values and the fold), so that ITEMS memory chains are in flight.
+// ---- warp-level compaction queues of the probe
+// Position of the k-th (0-based) set bit of m, k < popc(m).
+__device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
+  int p = 0;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    const int c = __popc((m >> p) & ((1u << s) - 1u));
+    if (c <= k) {
+      k -= c;
+      p += s;
+    }
+  }
+  return p;
+}
+
+// Up to 32 pending entries of F ints, entry i in lane i; n is warp-uniform.
+template <int F>
+struct WarpQueue {
+  int v[F];
+  int n;
+};
+
+// Appends, in lane order, the entries of the lanes whose flag is set.  Each
+// time 32 entries are pending, drain(q, 32) runs with every lane holding one
+// and the rest stay queued.  Every lane of the warp must call it.
+template <int F, typename Drain>
+__device__ __forceinline__ void wq_push(WarpQueue<F>& q, bool flag, const int (&val)[F], Drain&& drain) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  const int h = __popc(m);
+  if (h == 0) return;
+  const int take = lane - q.n;
+  const bool recv = take >= 0 && take < h;
+  const int src = recv ? nth_set_bit(m, take) : lane;
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    const int x = __shfl_sync(0xffffffffu, val[f], src);
+    if (recv) q.v[f] = x;
+  }
+  if (q.n + h < 32) {
+    q.n += h;
+    return;
+  }
+  drain(q, 32);
+  const int left = q.n + h - 32;  // new entries 32 - n .. h - 1 move to lanes 0 .. left - 1
+  const bool recv2 = lane < left;
+  const int src2 = recv2 ? nth_set_bit(m, 32 - q.n + lane) : lane;
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    const int x = __shfl_sync(0xffffffffu, val[f], src2);
+    if (recv2) q.v[f] = x;
+  }
+  q.n = left;
+}
+
+// Fused probe + aggregate as a warp pipeline with dense stages.
+//  1. Each thread takes ITEMS fact rows of the tile.  Without fact predicates
+//     they go straight to the dimension probe.  With predicates, the passing
+//     rows are compacted into a 32-entry warp queue that feeds the probe.
+//  2. Dimension probe per row: key image, range, cell bit; a unit-width cell
+//     proves the key, otherwise the directory bounds and the keys of the cell
+//     give its sorted position.
+//  3. Rows that find every dimension are compacted (row and positions) into
+//     a second queue; the fold runs on 32 of them at a time with all lanes
+//     active: group ranks, values and expressions, accumulator updates.
+// Compacting before the expensive stages keeps a warp's instructions on
+// live rows (a fifth of the rows reach the fold in the Q14 shape).
 // SMEM_BM: the first dimension's cell bitmap is copied into dynamic shared
 // memory (when it fits in smem_bm_words) so that a miss costs one shared
 // read; used for small first dimensions, one large block per SM.
@@ -324,6 +388,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   const bool use_smem = plan->use_smem != 0;
   const long long S = plan->S;
   const int nacc = A.naggs + 1;
+  const int lane = threadIdx.x & 31;
   // accumulator copies: as many as fit (up to one per warp); warp w uses copy w % copies
   int copies = 1;
   if (plan->use_smem == 2) {
@@ -337,6 +402,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   }
   DimDir dd[kMaxDims];
   long long stride[kMaxDims];
+  bool unit[kMaxDims];
 #pragma unroll
   for (int d = 0; d < kMaxDims; ++d) {
     if (d < a.ndims) {
@@ -344,8 +410,10 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
       stride[d] = plan->stride[d];
     } else {
       dd[d].ncells = 0;
+      dd[d].bshift = 0;
       stride[d] = 0;
     }
+    unit[d] = dd[d].bshift == 0;
   }
   extern __shared__ uint32_t s_bm[];
   bool sbm = false;
@@ -356,6 +424,125 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
       for (long long i = threadIdx.x; i < words; i += THREADS) s_bm[i] = __ldg(&a.dim[0].bitmap[i]);
   }
   __syncthreads();
+
+  // 2. probe of one fact row through every dimension
+  auto probe = [&](bool live, int64_t row, int (&pos)[kMaxDims]) -> bool {
+#pragma unroll
+    for (int d = 0; d < kMaxDims; ++d) {
+      pos[d] = 0;
+      if (d >= a.ndims) break;
+      const ProbeDim& D = a.dim[d];
+      UK u = 0, c = 0;
+      if (live) {
+        if (K32 || D.key_dt == TQP_I32)
+          u = (UK)((uint32_t)__ldg(static_cast<const int32_t*>(D.fk) + row) ^ 0x80000000u);
+        else
+          u = (UK)((unsigned long long)__ldg(static_cast<const long long*>(D.fk) + row) ^ 0x8000000000000000ull);
+        if (u < (UK)dd[d].umin || u > (UK)dd[d].umax) live = false;
+        else c = (u - (UK)dd[d].umin) >> dd[d].bshift;
+      }
+      if (live) {
+        const uint32_t w = (SMEM_BM && d == 0 && sbm) ? s_bm[c >> 5] : __ldg(&D.bitmap[c >> 5]);
+        live = (w >> (c & 31)) & 1u;
+      }
+      if (unit[d]) {  // unit-width cell: the bit proves the key
+        pos[d] = (int)c;
+        continue;
+      }
+      if (live) {
+        // first key >= u lies in [l, h]; narrow while the interval is long,
+        // then scan forward from l up to the cell's end
+        const int lo = __ldg(&D.dir[c]), hi = __ldg(&D.dir[c + 1]);
+        int l = lo, h = hi;
+        while (h - l > 4) {
+          int mid = (l + h) >> 1;
+          if ((UK)key_image(D.skeys, D.key_dt, mid) < u) l = mid + 1; else h = mid;
+        }
+        int found = -1;
+        for (int i = l; i < hi; ++i) {
+          const UK ki = (UK)key_image(D.skeys, D.key_dt, i);
+          if (ki >= u) {
+            if (ki == u) found = i;
+            break;
+          }
+        }
+        live = found >= 0;
+        pos[d] = found;
+      }
+    }
+    return live;
+  };
+
+  // 3. fold of one surviving row: group slot from the dimensions' ranks,
+  // aggregate expressions, accumulator updates
+  auto fold = [&](bool v, int row, const int (&pos)[kMaxDims]) {
+    if (!v) return;
+    long long slot = 0;
+#pragma unroll
+    for (int d = 0; d < kMaxDims; ++d)
+      if (d < a.ndims)
+        slot += (long long)__ldg(unit[d] ? &a.dim[d].rank_cell[pos[d]] : &a.dim[d].rank_sorted[pos[d]]) * stride[d];
+    long long* dst = use_smem ? my_acc + slot * nacc : a.acc + slot * nacc;
+    for (int q = 0; q < A.naggs; ++q) {
+      long long x = 1;
+      const int op = A.op[q];
+      if (op != TQP_COUNT) {
+        const int e = A.expr[q];
+        unsigned long long ev = 1;
+        for (int t = 0; t < A.nterms[e]; ++t) {
+          const int vi = A.tval[e][t];
+          const int src = s_vsrc[vi];
+          long long val;
+          if (src == 0) {
+            val = load_as_i64(s_vptr[vi], s_vdt[vi], row);
+          } else {
+            const bool cell = src == 1 ? unit[0] : unit[kMaxDims > 1 ? 1 : 0];
+            val = static_cast<const long long*>(cell ? s_vptr_cell[vi] : s_vptr[vi])[src == 1 ? pos[0] : pos[kMaxDims - 1]];
+          }
+          ev *= (unsigned long long)A.tmul[e][t] * (unsigned long long)val + (unsigned long long)A.tadd[e][t];
+        }
+        x = (long long)ev;
+      }
+      unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dst + q);
+      switch (op) {
+        case TQP_MIN: atomicMin(dst + q, x); break;
+        case TQP_MAX: atomicMax(dst + q, x); break;
+        default:
+          if (use_smem) shared_add_u64(d64, (unsigned long long)x);
+          else atomicAdd(d64, (unsigned long long)x);
+          break;
+      }
+    }
+    if (A.cnt == A.naggs) {  // no COUNT aggregate: the extra accumulator counts the rows
+      unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dst + A.naggs);
+      if (use_smem) shared_add_u64(d64, 1ull);
+      else atomicAdd(d64, 1ull);
+    }
+  };
+
+  WarpQueue<1 + kMaxDims> fq;  // rows that found every dimension: row, positions
+  fq.n = 0;
+  WarpQueue<1> pq;  // rows that pass the fact predicates
+  pq.n = 0;
+  auto drain_fold = [&](WarpQueue<1 + kMaxDims>& q, int cnt) {
+    int pos[kMaxDims];
+#pragma unroll
+    for (int d = 0; d < kMaxDims; ++d) pos[d] = q.v[1 + d];
+    fold(lane < cnt, q.v[0], pos);
+  };
+  auto push_survivor = [&](bool alive, int row, const int (&pos)[kMaxDims]) {
+    int val[1 + kMaxDims];
+    val[0] = row;
+#pragma unroll
+    for (int d = 0; d < kMaxDims; ++d) val[1 + d] = pos[d];
+    wq_push(fq, alive, val, drain_fold);
+  };
+  auto drain_probe = [&](WarpQueue<1>& q, int cnt) {
+    int pos[kMaxDims];
+    const bool alive = probe(lane < cnt, q.v[0], pos);
+    push_survivor(alive, q.v[0], pos);
+  };
+
   while (true) {
     if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1u);
     __syncthreads();
@@ -363,141 +550,41 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     __syncthreads();
     if (tile >= a.num_tiles) break;
     const int64_t base = (int64_t)tile * TILE + threadIdx.x;
-    bool live[ITEMS];
-    long long slot[ITEMS];
-    int pos[kMaxDims][ITEMS];
-    bool unit[kMaxDims] = {false, false};
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      live[k] = base + (int64_t)k * THREADS < a.n_fact;
-      slot[k] = 0;
-    }
-    for (int p = 0; p < a.npred; ++p) {
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k)
-        if (live[k]) live[k] = compare(load_as_i64(a.pcol[p], a.pdt[p], base + (int64_t)k * THREADS), a.pop[p], a.plit[p]);
-    }
-#pragma unroll
-    for (int d = 0; d < kMaxDims; ++d) {
-      if (d >= a.ndims) break;
-      const ProbeDim& D = a.dim[d];
-      UK u[ITEMS];
-      UK c[ITEMS];
-      const UK umin = (UK)dd[d].umin, umax = (UK)dd[d].umax;
-      const int bshift = dd[d].bshift;
-      // A: key image and cell, cell bit
+    if (a.npred == 0) {
+      // 1. every row goes to the probe, ITEMS rows in flight per thread
+      int pos[ITEMS][kMaxDims];
+      bool alive[ITEMS];
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
-        c[k] = 0;
-        if (live[k]) {
-          const int64_t r = base + (int64_t)k * THREADS;
-          if (K32 || D.key_dt == TQP_I32)
-            u[k] = (UK)((uint32_t)__ldcs(static_cast<const int32_t*>(D.fk) + r) ^ 0x80000000u);
-          else
-            u[k] = (UK)((unsigned long long)__ldcs(static_cast<const long long*>(D.fk) + r) ^ 0x8000000000000000ull);
-          if (u[k] < umin || u[k] > umax) live[k] = false;
-          else c[k] = (u[k] - umin) >> bshift;
-        }
+        const int64_t r = base + (int64_t)k * THREADS;
+        alive[k] = probe(r < a.n_fact, r, pos[k]);
       }
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k)
-        if (live[k]) {
-          const uint32_t w = (SMEM_BM && d == 0 && sbm) ? s_bm[c[k] >> 5] : __ldg(&D.bitmap[c[k] >> 5]);
-          live[k] = (w >> (c[k] & 31)) & 1u;
-        }
-      if (dd[d].bshift == 0) {
-        // unit-width cells: the bit proves the key; rank and values by cell
+      for (int k = 0; k < ITEMS; ++k) push_survivor(alive[k], (int)(base + (int64_t)k * THREADS), pos[k]);
+    } else {
+      // 1. fact predicates, then the passing rows into the probe queue
+      bool pass[ITEMS];
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-          pos[d][k] = (int)c[k];
-          if (live[k]) slot[k] += (long long)__ldg(&D.rank_cell[c[k]]) * stride[d];
-        }
-        unit[d] = true;
-        continue;
+      for (int k = 0; k < ITEMS; ++k) pass[k] = base + (int64_t)k * THREADS < a.n_fact;
+      for (int p = 0; p < a.npred; ++p) {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k)
+          if (pass[k]) pass[k] = compare(load_as_i64(a.pcol[p], a.pdt[p], base + (int64_t)k * THREADS), a.pop[p], a.plit[p]);
       }
-      unit[d] = false;
-      // B: directory bounds
-      int lo[ITEMS], hi[ITEMS];
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
-        lo[k] = hi[k] = 0;
-        if (live[k]) {
-          lo[k] = __ldg(&D.dir[c[k]]);
-          hi[k] = __ldg(&D.dir[c[k] + 1]);
-        }
-      }
-      // C: the keys of the cell (a bound search when the cell is crowded)
-      {
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k) {
-        if (!live[k]) continue;
-        // first key >= u lies in [l, h]; narrow while the interval is long,
-        // then scan forward from l up to the cell's end
-        int l = lo[k], h = hi[k];
-        while (h - l > 4) {
-          int mid = (l + h) >> 1;
-          if ((UK)key_image(D.skeys, D.key_dt, mid) < u[k]) l = mid + 1; else h = mid;
-        }
-        int found = -1;
-        for (int i = l; i < hi[k]; ++i) {
-          const UK ki = (UK)key_image(D.skeys, D.key_dt, i);
-          if (ki >= u[k]) {
-            if (ki == u[k]) found = i;
-            break;
-          }
-        }
-        live[k] = found >= 0;
-        pos[d][k] = found;
-      }
-      }
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k)
-        if (live[k]) slot[k] += (long long)__ldg(&D.rank_sorted[pos[d][k]]) * stride[d];
-    }
-    // D: values, expressions, fold
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      if (!live[k]) continue;
-      const int64_t row = base + (int64_t)k * THREADS;
-      const int p0 = pos[0][k], p1 = kMaxDims > 1 ? pos[1][k] : 0;
-      long long* dst = use_smem ? my_acc + slot[k] * nacc : a.acc + slot[k] * nacc;
-      for (int q = 0; q < A.naggs; ++q) {
-        long long x = 1;
-        const int op = A.op[q];
-        if (op != TQP_COUNT) {
-          const int e = A.expr[q];
-          unsigned long long ev = 1;
-          for (int t = 0; t < A.nterms[e]; ++t) {
-            const int v = A.tval[e][t];
-            const int src = s_vsrc[v];
-            long long val;
-            if (src == 0) {
-              val = load_as_i64(s_vptr[v], s_vdt[v], row);
-            } else {
-              const bool cell = src == 1 ? unit[0] : unit[1];
-              val = static_cast<const long long*>(cell ? s_vptr_cell[v] : s_vptr[v])[src == 1 ? p0 : p1];
-            }
-            ev *= (unsigned long long)A.tmul[e][t] * (unsigned long long)val + (unsigned long long)A.tadd[e][t];
-          }
-          x = (long long)ev;
-        }
-        unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dst + q);
-        switch (op) {
-          case TQP_MIN: atomicMin(dst + q, x); break;
-          case TQP_MAX: atomicMax(dst + q, x); break;
-          default:
-            if (use_smem) shared_add_u64(d64, (unsigned long long)x);
-            else atomicAdd(d64, (unsigned long long)x);
-            break;
-        }
-      }
-      if (A.cnt == A.naggs) {  // no COUNT aggregate: the extra accumulator counts the rows
-        unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dst + A.naggs);
-        if (use_smem) shared_add_u64(d64, 1ull);
-        else atomicAdd(d64, 1ull);
+        const int val[1] = {(int)(base + (int64_t)k * THREADS)};
+        wq_push(pq, pass[k], val, drain_probe);
       }
     }
   }
+  // the partly filled queues: probe what is pending, then fold the rest
+  if (pq.n > 0) {
+    const int cnt = pq.n;
+    pq.n = 0;
+    drain_probe(pq, cnt);
+  }
+  if (fq.n > 0) drain_fold(fq, fq.n);
   if (use_smem) {
     __syncthreads();
     for (int i = threadIdx.x; i < S * nacc; i += THREADS) {

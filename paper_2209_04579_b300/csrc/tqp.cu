@@ -7,7 +7,9 @@
 #include <climits>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -55,17 +57,18 @@ int num_sms() {
 template <typename Kernel>
 int persistent_grid(Kernel k, int threads, size_t smem, int64_t tiles) {
   static std::mutex mu;
-  static std::unordered_map<const void*, int> cache;
+  static std::map<std::tuple<const void*, int, size_t>, int> cache;
   int per_sm = 1;
   {
     std::lock_guard<std::mutex> g(mu);
-    auto it = cache.find(reinterpret_cast<const void*>(k));
+    const auto key = std::make_tuple(reinterpret_cast<const void*>(k), threads, smem);
+    auto it = cache.find(key);
     if (it != cache.end()) {
       per_sm = it->second;
     } else {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
       if (per_sm < 1) per_sm = 1;
-      cache[reinterpret_cast<const void*>(k)] = per_sm;
+      cache[key] = per_sm;
     }
   }
   int64_t g = (int64_t)per_sm * num_sms();
@@ -399,6 +402,7 @@ constexpr int kFilterT = 256, kFilterI = 16;
 constexpr int kRankT = 256, kRankI = 8;
 constexpr int kProbeT = 256, kProbeI = 8;
 constexpr int kSmemBitmapBytes = 190 * 1024;       // shared bitmap of the first dimension
+constexpr int kMaxSmemOptin = 227 * 1024;          // dynamic shared memory one block may opt in to
 constexpr int64_t kSmemBitmapDimRows = 4'000'000;  // first dimensions up to this size try it
 constexpr int kCompactT = 256, kCompactI = 8;
 
@@ -1166,18 +1170,20 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   lp_sample_kernel<<<(S + 255) / 256, 256, 0, s>>>(ks, d_sel, n, d_n, gp, S, sample); note_launch();
   st = run_sort(ssort, kKeyU64, sample, nullptr, ssorted, srows, S, nullptr, 0, 64, s);
   if (st != TQP_OK) return st;
-  lp_targets_kernel<<<(S + 255) / 256, 256, 0, s>>>(ssorted, S, lp, tx, ty); note_launch();
-  if (cfg->init == 1) {
-    lp_quantile_init_kernel<<<1, kH, 0, s>>>(tx, S, lp, model); note_launch();
-  }
-  // 3. training
-  if (epochs > 0) launch_training(model, tx, ty, S, nullptr, cfg->train_cfg, partial, adam, loss, s);
-  // 4. heavy keys, step positions and their directory
+  // 3. heavy keys; training pairs on the CDF of the light rows (the sort's
+  // row ids are no longer needed: srows holds the light prefix)
   if (cfg->heavy) {
     lp_heavy_kernel<<<1, 1024, 0, s>>>(ssorted, S, lp, heavy); note_launch();
   } else {
     lp_no_heavy_kernel<<<1, 32, 0, s>>>(lp); note_launch();
   }
+  lp_light_prefix_kernel<<<1, 1024, 0, s>>>(ssorted, S, heavy, lp, srows); note_launch();
+  lp_targets_kernel<<<(S + 255) / 256, 256, 0, s>>>(ssorted, S, lp, heavy, srows, tx, ty); note_launch();
+  if (cfg->init == 1) {
+    lp_quantile_init_kernel<<<1, kH, 0, s>>>(tx, ty, S, lp, model); note_launch();
+  }
+  // 4. training, then the step positions of the bucket function and their directory
+  if (epochs > 0) launch_training(model, tx, ty, S, nullptr, cfg->train_cfg, partial, adam, loss, s);
   if (B > 1) {
     lp_thresholds_kernel<<<(B - 1 + 255) / 256, 256, 0, s>>>(model, lp, thr); note_launch();
   }
@@ -1199,19 +1205,20 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   pa.out_row = lrow;
   pa.heavy_acc = heavy_acc;
   TQP_CUDA(cudaMemsetAsync(count, 0, (size_t)B * sizeof(unsigned), s));
-  lp_hist_kernel<<<stride_grid(n, 256, 8), 256, 0, s>>>(pa); note_launch();
-  lp_offsets_kernel<<<1, 1024, 0, s>>>(lp, count, off, cursor, d_stats, loss, epochs, light_n); note_launch();
-  lp_heavy_init_kernel<<<(kMaxHeavy * naggs + 255) / 256, 256, 0, s>>>(lp, P, heavy_acc); note_launch();
   {
-    size_t smem = (size_t)kMaxHeavy * naggs * sizeof(long long);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(lp_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(kMaxHeavy * TQP_MAX_AGGS * sizeof(long long)));
-      attr = true;
-    }
+    // the steps live in shared memory when the scatter's layout still fits
+    const bool thr_smem = part_smem_bytes(B, naggs, true) <= (size_t)kMaxSmemOptin;
+    const size_t hsm = part_smem_bytes(B, 0, thr_smem), ssm = part_smem_bytes(B, naggs, thr_smem);
+    auto hk = thr_smem ? lp_hist_kernel<true> : lp_hist_kernel<false>;
+    auto sk = thr_smem ? lp_scatter_kernel<true> : lp_scatter_kernel<false>;
+    TQP_CUDA(cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+    TQP_CUDA(cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+    const int64_t ptiles = (n + kPartThreads * kPartItems - 1) / (kPartThreads * kPartItems);
+    hk<<<persistent_grid(hk, kPartThreads, hsm, ptiles), kPartThreads, hsm, s>>>(pa); note_launch();
+    lp_offsets_kernel<<<1, 1024, 0, s>>>(lp, count, off, cursor, d_stats, loss, epochs, light_n); note_launch();
+    lp_heavy_init_kernel<<<(kMaxHeavy * naggs + 255) / 256, 256, 0, s>>>(lp, P, heavy_acc); note_launch();
     prof_mark(8, true, s);
-    lp_scatter_kernel<<<stride_grid(n, 256, 2), 256, smem, s>>>(pa, P); note_launch();
+    sk<<<persistent_grid(sk, kPartThreads, ssm, ptiles), kPartThreads, ssm, s>>>(pa, P); note_launch();
     prof_mark(8, false, s);
   }
   // 6. every bucket sorted: on-chip up to the capacity, else by one block in global memory
