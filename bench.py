@@ -357,21 +357,34 @@ class ClockSampler:
         self.thread = None
         self.nv = self.h = None
         self.smi = None
+        self.err = None
         try:
             import pynvml
             pynvml.nvmlInit()
+            self.nv = pynvml
             p = torch.cuda.get_device_properties(device)
-            want = (int(p.pci_domain_id), int(p.pci_bus_id), int(p.pci_device_id))
-            for i in range(pynvml.nvmlDeviceGetCount()):
-                h = pynvml.nvmlDeviceGetHandleByIndex(i)
-                info = pynvml.nvmlDeviceGetPciInfo(h)
-                if (int(info.domain), int(info.bus), int(info.device)) == want:
+            uuid = str(getattr(p, "uuid", "")).lower()
+            pci = (int(p.pci_domain_id), int(p.pci_bus_id), int(p.pci_device_id))
+            handles = [pynvml.nvmlDeviceGetHandleByIndex(i) for i in range(pynvml.nvmlDeviceGetCount())]
+            for h in handles:  # the same GPU by UUID, else by PCI location
+                u = pynvml.nvmlDeviceGetUUID(h)
+                u = (u.decode() if isinstance(u, bytes) else str(u)).lower()
+                if uuid and uuid in u:
                     self.h = h
                     break
-            self.nv = pynvml
+            if self.h is None:
+                for h in handles:
+                    info = pynvml.nvmlDeviceGetPciInfo(h)
+                    if (int(info.domain), int(info.bus), int(info.device)) == pci:
+                        self.h = h
+                        break
+            if self.h is None and len(handles) == 1:
+                self.h = handles[0]
+            if self.h is None:
+                self.err = f"no NVML device matches uuid {uuid} / pci {pci}"
         except Exception as e:
             self.h = None
-            self.err = repr(e)
+            self.err = repr(e)[:200]
 
     def _sample(self):
         nv, h = self.nv, self.h
@@ -426,7 +439,7 @@ class ClockSampler:
 
     def _stop_smi(self):
         if self.smi is None:
-            return None
+            return {"error": self.err} if self.err else None
         self.smi.terminate()
         try:
             self.smi.wait(5)
@@ -450,7 +463,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm), "source": "nvidia-smi, 200 ms"}
+                "samples": len(sm), "source": "nvidia-smi, 200 ms", "nvml_error": self.err}
 
 
 def dist_setup(args):

@@ -59,8 +59,16 @@ def _time(fn, reps=3):
     return best
 
 
+def _flat(o):
+    for t in o:
+        if isinstance(t, (list, tuple)):
+            yield from _flat(t)
+        else:
+            yield t
+
+
 def _fingerprint(outs):
-    return [tuple(t.cpu().numpy().tobytes() for t in o) for o in outs]
+    return [tuple(t.cpu().numpy().tobytes() for t in _flat(o)) for o in outs]
 
 
 def tune_batched(problems, shape, cap=64, candidates=(4, 8, 16), force=False):

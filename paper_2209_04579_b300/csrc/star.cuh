@@ -289,64 +289,60 @@ struct ProbeArgs {
 };
 
 // ---- warp-level compaction queues of the probe
-// Position of the k-th (0-based) set bit of m, k < popc(m).
-__device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
-  int p = 0;
-#pragma unroll
-  for (int s = 16; s > 0; s >>= 1) {
-    const int c = __popc((m >> p) & ((1u << s) - 1u));
-    if (c <= k) {
-      k -= c;
-      p += s;
-    }
-  }
-  return p;
-}
-
-// Up to 32 pending entries of F ints, entry i in lane i; n is warp-uniform.
+// A ring of 64 entries of F ints per warp in shared memory (field-major),
+// with its head and fill count in registers (warp-uniform).
 template <int F>
-struct WarpQueue {
-  int v[F];
+struct WarpRing {
+  int* base;  // this warp's ring: F x 64 ints
+  int head;
   int n;
 };
 
-// Appends, in lane order, the entries of the lanes whose flag is set.  Each
-// time 32 entries are pending, drain(q, 32) runs with every lane holding one
-// and the rest stay queued.  Every lane of the warp must call it.
+// Appends the entries of the lanes whose flag is set.  Each time 32 entries
+// are pending, drain(e, 32) runs with lane i holding entry i (in e[]), and
+// those 32 leave the ring.  Every lane of the warp must call it.
 template <int F, typename Drain>
-__device__ __forceinline__ void wq_push(WarpQueue<F>& q, bool flag, const int (&val)[F], Drain&& drain) {
+__device__ __forceinline__ void ring_push(WarpRing<F>& q, bool flag, const int (&val)[F], Drain&& drain) {
   const int lane = threadIdx.x & 31;
   const unsigned m = __ballot_sync(0xffffffffu, flag);
-  const int h = __popc(m);
-  if (h == 0) return;
-  const int take = lane - q.n;
-  const bool recv = take >= 0 && take < h;
-  const int src = recv ? nth_set_bit(m, take) : lane;
+  if (m == 0) return;
+  if (flag) {
+    const int idx = (q.head + q.n + __popc(m & ((1u << lane) - 1u))) & 63;
 #pragma unroll
-  for (int f = 0; f < F; ++f) {
-    const int x = __shfl_sync(0xffffffffu, val[f], src);
-    if (recv) q.v[f] = x;
+    for (int f = 0; f < F; ++f) q.base[f * 64 + idx] = val[f];
   }
-  if (q.n + h < 32) {
-    q.n += h;
-    return;
-  }
-  drain(q, 32);
-  const int left = q.n + h - 32;  // new entries 32 - n .. h - 1 move to lanes 0 .. left - 1
-  const bool recv2 = lane < left;
-  const int src2 = recv2 ? nth_set_bit(m, 32 - q.n + lane) : lane;
+  q.n += __popc(m);
+  if (q.n < 32) return;
+  __syncwarp();
+  int e[F];
 #pragma unroll
-  for (int f = 0; f < F; ++f) {
-    const int x = __shfl_sync(0xffffffffu, val[f], src2);
-    if (recv2) q.v[f] = x;
-  }
-  q.n = left;
+  for (int f = 0; f < F; ++f) e[f] = q.base[f * 64 + ((q.head + lane) & 63)];
+  __syncwarp();
+  q.head = (q.head + 32) & 63;
+  q.n -= 32;
+  drain(e, 32);
+}
+
+// Drains what is pending (fewer than 32 entries).
+template <int F, typename Drain>
+__device__ __forceinline__ void ring_flush(WarpRing<F>& q, Drain&& drain) {
+  if (q.n == 0) return;
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  int e[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) e[f] = lane < q.n ? q.base[f * 64 + ((q.head + lane) & 63)] : 0;
+  __syncwarp();
+  const int cnt = q.n;
+  q.head = (q.head + cnt) & 63;
+  q.n = 0;
+  drain(e, cnt);
 }
 
 // Fused probe + aggregate as a warp pipeline with dense stages.
 //  1. Each thread takes ITEMS fact rows of the tile.  Without fact predicates
 //     they go straight to the dimension probe.  With predicates, the passing
-//     rows are compacted into a 32-entry warp queue that feeds the probe.
+//     rows are compacted into a warp queue that feeds the probe 32 at a time.
 //  2. Dimension probe per row: key image, range, cell bit; a unit-width cell
 //     proves the key, otherwise the directory bounds and the keys of the cell
 //     give its sorted position.
@@ -364,7 +360,12 @@ template <int THREADS, int ITEMS, bool SMEM_BM, bool K32>
 __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(ProbeArgs a, StarAcc Ag, int smem_bm_words) {
   using UK = typename std::conditional<K32, uint32_t, unsigned long long>::type;
   constexpr int TILE = THREADS * ITEMS;
-  __shared__ long long s_acc[kSmemAccWords];
+  constexpr int WARPS = THREADS / 32;
+  // the shared bitmap variant keeps a smaller accumulator array
+  constexpr int ACC_WORDS = SMEM_BM ? kSmemAccWords / 4 : kSmemAccWords;
+  __shared__ long long s_acc[ACC_WORDS];
+  __shared__ int s_fring[WARPS][(1 + kMaxDims) * 64];  // probe survivors: row, positions
+  __shared__ int s_pring[WARPS][64];                   // rows that pass the fact predicates
   __shared__ uint32_t s_tile;
   // the aggregate program and value references in shared memory: they are
   // indexed by runtime values below (kernel parameters indexed that way are
@@ -385,15 +386,15 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   __syncthreads();
   const StarPlan* plan = a.plan;
   if (plan->unsupported) return;
-  const bool use_smem = plan->use_smem != 0;
   const long long S = plan->S;
   const int nacc = A.naggs + 1;
+  const bool use_smem = plan->use_smem != 0 && S * nacc <= ACC_WORDS;
   const int lane = threadIdx.x & 31;
   // accumulator copies: as many as fit (up to one per warp); warp w uses copy w % copies
   int copies = 1;
-  if (plan->use_smem == 2) {
-    long long fit = kSmemAccWords / (S * nacc);
-    copies = (int)(fit < THREADS / 32 ? fit : THREADS / 32);
+  if (use_smem) {
+    long long fit = ACC_WORDS / (S * nacc);
+    copies = (int)(fit < WARPS ? fit : WARPS);
     if (copies < 1) copies = 1;
   }
   long long* my_acc = s_acc + ((threadIdx.x >> 5) % copies) * S * nacc;
@@ -520,27 +521,29 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     }
   };
 
-  WarpQueue<1 + kMaxDims> fq;  // rows that found every dimension: row, positions
-  fq.n = 0;
-  WarpQueue<1> pq;  // rows that pass the fact predicates
-  pq.n = 0;
-  auto drain_fold = [&](WarpQueue<1 + kMaxDims>& q, int cnt) {
+  WarpRing<1 + kMaxDims> fq;  // rows that found every dimension: row, positions
+  fq.base = s_fring[threadIdx.x >> 5];
+  fq.head = fq.n = 0;
+  WarpRing<1> pq;  // rows that pass the fact predicates
+  pq.base = s_pring[threadIdx.x >> 5];
+  pq.head = pq.n = 0;
+  auto drain_fold = [&](const int (&e)[1 + kMaxDims], int cnt) {
     int pos[kMaxDims];
 #pragma unroll
-    for (int d = 0; d < kMaxDims; ++d) pos[d] = q.v[1 + d];
-    fold(lane < cnt, q.v[0], pos);
+    for (int d = 0; d < kMaxDims; ++d) pos[d] = e[1 + d];
+    fold(lane < cnt, e[0], pos);
   };
   auto push_survivor = [&](bool alive, int row, const int (&pos)[kMaxDims]) {
     int val[1 + kMaxDims];
     val[0] = row;
 #pragma unroll
     for (int d = 0; d < kMaxDims; ++d) val[1 + d] = pos[d];
-    wq_push(fq, alive, val, drain_fold);
+    ring_push(fq, alive, val, drain_fold);
   };
-  auto drain_probe = [&](WarpQueue<1>& q, int cnt) {
+  auto drain_probe = [&](const int (&e)[1], int cnt) {
     int pos[kMaxDims];
-    const bool alive = probe(lane < cnt, q.v[0], pos);
-    push_survivor(alive, q.v[0], pos);
+    const bool alive = probe(lane < cnt, e[0], pos);
+    push_survivor(alive, e[0], pos);
   };
 
   while (true) {
@@ -574,17 +577,13 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
         const int val[1] = {(int)(base + (int64_t)k * THREADS)};
-        wq_push(pq, pass[k], val, drain_probe);
+        ring_push(pq, pass[k], val, drain_probe);
       }
     }
   }
   // the partly filled queues: probe what is pending, then fold the rest
-  if (pq.n > 0) {
-    const int cnt = pq.n;
-    pq.n = 0;
-    drain_probe(pq, cnt);
-  }
-  if (fq.n > 0) drain_fold(fq, fq.n);
+  ring_flush(pq, drain_probe);
+  ring_flush(fq, drain_fold);
   if (use_smem) {
     __syncthreads();
     for (int i = threadIdx.x; i < S * nacc; i += THREADS) {

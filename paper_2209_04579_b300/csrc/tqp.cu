@@ -172,15 +172,29 @@ tqp_status run_sort(const SortWs& w, int key_dt, const void* keys_in, const int3
   sort_hist_kernel<256><<<stride_grid(n, 256), 256, 0, s>>>(a); note_launch();
   sort_plan_kernel<<<1, kRadix, 0, s>>>(a); note_launch();
   prof_mark(2, true, s);
+  // tiles arrive by bulk copies when every source is 16-byte aligned (the
+  // intermediates always are)
+  const bool bulk = (reinterpret_cast<uintptr_t>(keys_in) % 16 == 0) &&
+                    (vals_in == nullptr || reinterpret_cast<uintptr_t>(vals_in) % 16 == 0);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(sort_pass_kernel<uint32_t, kSortThreads, kItems32, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kSortThreads * kItems32 * 8);
+    cudaFuncSetAttribute(sort_pass_kernel<unsigned long long, kSortThreads, kItems64, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kSortThreads * kItems64 * 12);
+    attr = true;
+  }
   for (int p = 0; p < a.npasses; ++p) {
     TQP_CUDA(cudaMemsetAsync(w.status, 0, (size_t)w.tiles * kRadix * sizeof(uint32_t), s));
     if (word_bytes == 4) {
-      auto k = sort_pass_kernel<uint32_t, kSortThreads, kItems32>;
-      size_t smem = (size_t)kSortThreads * kItems32 * 4;
+      auto k = bulk ? sort_pass_kernel<uint32_t, kSortThreads, kItems32, true>
+                    : sort_pass_kernel<uint32_t, kSortThreads, kItems32, false>;
+      size_t smem = (size_t)kSortThreads * kItems32 * (bulk ? 2 * 8 : 4);
       k<<<persistent_grid(k, kSortThreads, smem, w.tiles), kSortThreads, smem, s>>>(a, p, w.tiles); note_launch();
     } else {
-      auto k = sort_pass_kernel<unsigned long long, kSortThreads, kItems64>;
-      size_t smem = (size_t)kSortThreads * kItems64 * 8;
+      auto k = bulk ? sort_pass_kernel<unsigned long long, kSortThreads, kItems64, true>
+                    : sort_pass_kernel<unsigned long long, kSortThreads, kItems64, false>;
+      size_t smem = (size_t)kSortThreads * kItems64 * (bulk ? 2 * 12 : 8);
       k<<<persistent_grid(k, kSortThreads, smem, w.tiles), kSortThreads, smem, s>>>(a, p, w.tiles); note_launch();
     }
   }
@@ -401,7 +415,7 @@ struct StarDimWs {
 constexpr int kFilterT = 256, kFilterI = 16;
 constexpr int kRankT = 256, kRankI = 8;
 constexpr int kProbeT = 256, kProbeI = 8;
-constexpr int kSmemBitmapBytes = 190 * 1024;       // shared bitmap of the first dimension
+constexpr int kSmemBitmapBytes = 184 * 1024;       // shared bitmap of the first dimension
 constexpr int kMaxSmemOptin = 227 * 1024;          // dynamic shared memory one block may opt in to
 constexpr int64_t kSmemBitmapDimRows = 4'000'000;  // first dimensions up to this size try it
 constexpr int kCompactT = 256, kCompactI = 8;
