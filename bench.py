@@ -158,7 +158,7 @@ class Skew:
     @staticmethod
     def cfg(buckets):
         from paper_2209_04579_b300 import tqp
-        return tqp.learned_cfg(sample=65536, buckets=buckets, tcfg=tqp.train_cfg(epochs=100))
+        return tqp.learned_cfg(sample=65536, buckets=buckets, tcfg=tqp.train_cfg(epochs=100, lr=1e-4))
 
     def tune(self):
         """Bucket count from the autotuner (outputs sized to the group count)."""
@@ -291,13 +291,18 @@ class Star:
     name = "star"
     n, n1, n2 = 600_000_000, 20_000_000, 150_000_000
 
-    def __init__(self, master):
+    def __init__(self, master, scale=1):
         from paper_2209_04579_b300 import datagen as dg
         self.dg = dg
+        self.n, self.n1, self.n2 = self.n // scale, self.n1 // scale, self.n2 // scale
+        self.scale = scale
         self.rec = dg.star_tables(self.n1, self.n2, master=master)
         self.master = master
 
     def config(self):
+        if self.scale != 1:
+            return {"workload": f"star join scaled by 1/{self.scale}: fact {self.n}, dim1 {self.n1}, dim2 {self.n2}",
+                    "fact_rows": self.n}
         return {"workload": "star join: fact 600M rows (fk1 int32 into 20M dim1 keys, fk2 int64 into 150M dim2 keys, "
                             "m1..m3 int64 U[0,1e7], date int32 U[0,2556]) WHERE date<767 GROUP BY dim1.cat (int16 "
                             "0..999), dim2.cat (int8 0..49); SUM(m1..m3), COUNT", "fact_rows": self.n}
@@ -342,6 +347,57 @@ WORKLOADS = {"q14": Q14, "q6": Q6, "skew": Skew, "batched": Batched, "star": Sta
 
 # ---------------------------------------------------------------- helpers
 
+class _Nvml:
+    """The few NVML calls the clock sampler reads, through ctypes on the
+    driver's libnvidia-ml (no Python package needed)."""
+    CLOCK_SM = 1
+
+    def __init__(self):
+        import ctypes
+        self.c = ctypes
+        self.l = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.l.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        get = getattr(self.l, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = get if get is not None else self.l.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def handles(self):
+        c = self.c
+        n = c.c_uint(0)
+        self.l.nvmlDeviceGetCount_v2(c.byref(n))
+        out = []
+        for i in range(n.value):
+            h = c.c_void_p()
+            if self.l.nvmlDeviceGetHandleByIndex_v2(c.c_uint(i), c.byref(h)) == 0:
+                out.append(h)
+        return out
+
+    def uuid(self, h):
+        buf = self.c.create_string_buffer(96)
+        self.l.nvmlDeviceGetUUID(h, buf, self.c.c_uint(96))
+        return buf.value.decode().lower()
+
+    def pci(self, h):
+        c = self.c
+
+        class Pci(c.Structure):
+            _fields_ = [("busIdLegacy", c.c_char * 16), ("domain", c.c_uint), ("bus", c.c_uint),
+                        ("device", c.c_uint), ("pciDeviceId", c.c_uint), ("pciSubSystemId", c.c_uint),
+                        ("busId", c.c_char * 32)]
+        info = Pci()
+        self.l.nvmlDeviceGetPciInfo_v3(h, c.byref(info))
+        return (info.domain, info.bus, info.device)
+
+    def sample(self, h):
+        c = self.c
+        sm, mx, r = c.c_uint(0), c.c_uint(0), c.c_ulonglong(0)
+        if self.l.nvmlDeviceGetClockInfo(h, self.CLOCK_SM, c.byref(sm)) != 0:
+            return None
+        self.l.nvmlDeviceGetMaxClockInfo(h, self.CLOCK_SM, c.byref(mx))
+        self.reasons_fn(h, c.byref(r))
+        return sm.value, mx.value, r.value
+
+
 class ClockSampler:
     """SM clock, its maximum and the clock-event (throttle) reasons, sampled
     through NVML every 5 ms by a thread while the timed region runs, plus one
@@ -359,41 +415,34 @@ class ClockSampler:
         self.smi = None
         self.err = None
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            self.nv = pynvml
+            nv = _Nvml()
             p = torch.cuda.get_device_properties(device)
             uuid = str(getattr(p, "uuid", "")).lower()
             pci = (int(p.pci_domain_id), int(p.pci_bus_id), int(p.pci_device_id))
-            handles = [pynvml.nvmlDeviceGetHandleByIndex(i) for i in range(pynvml.nvmlDeviceGetCount())]
+            handles = nv.handles()
             for h in handles:  # the same GPU by UUID, else by PCI location
-                u = pynvml.nvmlDeviceGetUUID(h)
-                u = (u.decode() if isinstance(u, bytes) else str(u)).lower()
-                if uuid and uuid in u:
+                if uuid and uuid in nv.uuid(h):
                     self.h = h
                     break
             if self.h is None:
                 for h in handles:
-                    info = pynvml.nvmlDeviceGetPciInfo(h)
-                    if (int(info.domain), int(info.bus), int(info.device)) == pci:
+                    if nv.pci(h) == pci:
                         self.h = h
                         break
             if self.h is None and len(handles) == 1:
                 self.h = handles[0]
             if self.h is None:
                 self.err = f"no NVML device matches uuid {uuid} / pci {pci}"
+            self.nv = nv
         except Exception as e:
             self.h = None
             self.err = repr(e)[:200]
 
     def _sample(self):
-        nv, h = self.nv, self.h
         try:
-            sm = nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)
-            mx = nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)
-            get = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-                nv.nvmlDeviceGetCurrentClocksThrottleReasons
-            self.samples.append((sm, mx, int(get(h))))
+            r = self.nv.sample(self.h)
+            if r is not None:
+                self.samples.append(r)
         except Exception:
             pass
 
@@ -548,7 +597,7 @@ def run_ours(args, world, rank, local):
     barrier(world)
     from paper_2209_04579_b300 import tqp
     torch.cuda.set_device(local)
-    W = WORKLOADS[args.workload](20220904 + rank)
+    W = WORKLOADS[args.workload](20220904 + rank, **({"scale": args.scale} if args.scale != 1 else {}))
     if args.variant:
         W.variant = args.variant
     inputs = W.make_device()
@@ -716,6 +765,7 @@ def main():
     ap.add_argument("--workload", default="q14", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="", help="skew: 'plain' times the plain radix path as the step")
+    ap.add_argument("--scale", type=int, default=1, help="star: divide the table sizes (small profiling cases)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -318,7 +318,9 @@ tqp_status tqp_cdf_train(const float* d_x, const float* d_y, int64_t n, tqp_cdf_
                          tqp_stream_t stream);
 
 typedef struct {
-  int32_t sample;  /* keys sampled (strided) to train on; power of two in [1024, 2^20] */
+  int32_t sample;  /* keys sampled (strided) to train on; power of two in [1024, 2^20].
+                      Heavy keys are found in a strided sample 4 times larger (at
+                      most 2^20 keys), whose every 4th sorted key is trained on. */
   int32_t buckets; /* learned buckets B (power of two <= 2^17); 0 = from n */
   int32_t train;   /* 1 = train the network; 0 = keep the identity CDF F(x) = x */
   int32_t heavy;   /* 1 = aggregate the sample's frequent keys directly */

@@ -301,16 +301,18 @@ __global__ void __launch_bounds__(1024) lp_light_prefix_kernel(const unsigned lo
   if (threadIdx.x == 0) lp->slight = total;
 }
 
-// Training pairs from the sorted sample: x = normalised key, y = the CDF of
-// the light rows (the rows the buckets receive) at the key's midpoint:
+// Training pairs from every mult-th key of the sorted sample (S keys):
+// x = normalised key, y = the CDF of the light rows (the rows the buckets
+// receive) over the whole sample at the key's midpoint:
 // (light keys before the key + its light count / 2) / light total.  A heavy
 // key has no light count: its pair sits on the light CDF with zero width.
 // Without heavy keys this is (first rank + count / 2) / S.
-__global__ void lp_targets_kernel(const unsigned long long* sorted, int S, const LearnedPlan* lp,
-                                  const unsigned long long* heavy, const int32_t* lpre, float* x, float* y) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= S) return;
-  unsigned long long k = sorted[i];
+__global__ void lp_targets_kernel(const unsigned long long* sorted, int S, int mult, int S_train,
+                                  const LearnedPlan* lp, const unsigned long long* heavy, const int32_t* lpre,
+                                  float* x, float* y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S_train) return;
+  const unsigned long long k = sorted[(int64_t)i * mult];
   int64_t lo = lb_u64(sorted, S, k);
   int64_t hi = ub_u64(sorted, lo, S, k);
   const int nh = lp->nheavy;
@@ -850,19 +852,177 @@ __device__ __forceinline__ unsigned long long block_minmax_span(unsigned long lo
   return hi >= lo ? hi - lo : 0;
 }
 
+// Shared memory of the block bucket sort.
+struct LocalSmem {
+  unsigned long long* kA;
+  unsigned long long* kB;
+  int32_t* rA;
+  int32_t* rB;
+  unsigned* cnt;    // [kLocalWarps][kRadix + 1]
+  unsigned* start;  // [kRadix]
+  int* scan;        // 33
+  unsigned long long* red;  // [2 * kLocalWarps]
+};
+
+// m <= kLocalCap rows from (sp, sr) sorted by key into (dp, dr) (which may
+// be the same arrays): loaded into shared memory, LSD over the bits of the
+// rows' key span, written back.  Called by the whole block.
+__device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, unsigned long long* dp, int32_t* dr,
+                            int m, const LocalSmem& L) {
+  if (m <= 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long* kA = L.kA;
+  unsigned long long* kB = L.kB;
+  int32_t* rA = L.rA;
+  int32_t* rB = L.rB;
+  unsigned long long lo = ~0ull, hi = 0;
+  for (int i = threadIdx.x; i < m; i += kLocalThreads) {
+    unsigned long long k = sp[i];
+    kA[i] = k;
+    rA[i] = sr[i];
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+  unsigned long long pmin;
+  const unsigned long long span = block_minmax_span(lo, hi, L.red, &pmin);
+  if (span != 0) {
+    const int bits = 64 - __clzll((long long)span);
+    const int per = (m + kLocalWarps - 1) / kLocalWarps;
+    const int wbeg = warp * per;
+    for (int sh = 0; sh < bits; sh += kRadixBits) {
+      unsigned dig[kLocalItems];
+      int pos[kLocalItems];
+#pragma unroll
+      for (int it = 0; it < kLocalItems; ++it) {
+        int i = wbeg + it * 32 + lane;
+        bool v = (it * 32 + lane < per) && i < m;
+        dig[it] = v ? (unsigned)(((kA[i] - pmin) >> sh) & (kRadix - 1)) : kRadix;
+      }
+      int total;
+      block_rank<kLocalWarps, kLocalItems>(dig, pos, (per + 31) >> 5, L.cnt, L.start, L.scan, &total);
+#pragma unroll
+      for (int it = 0; it < kLocalItems; ++it) {
+        if (pos[it] >= 0) {
+          int i = wbeg + it * 32 + lane;
+          kB[pos[it]] = kA[i];
+          rB[pos[it]] = rA[i];
+        }
+      }
+      __syncthreads();
+      unsigned long long* tk = kA; kA = kB; kB = tk;
+      int32_t* tr = rA; rA = rB; rB = tr;
+    }
+  } else if (sp == dp) {
+    __syncthreads();
+    return;  // one key, in place: already in order
+  }
+  for (int i = threadIdx.x; i < m; i += kLocalThreads) {
+    dp[i] = kA[i];
+    dr[i] = rA[i];
+  }
+  __syncthreads();
+}
+
+// m rows at (p, row) sorted in place by one block, LSD in global memory
+// tile by tile (tiles in order keep it stable), (alt_p, alt_row) scratch.
+__device__ void global_lsd(unsigned long long* p, int32_t* row, unsigned long long* alt_p, int32_t* alt_row,
+                           int64_t m, const LocalSmem& L) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long lo = ~0ull, hi = 0;
+  for (int64_t i = threadIdx.x; i < m; i += kLocalThreads) {
+    unsigned long long k = p[i];
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+  unsigned long long pmin;
+  const unsigned long long span = block_minmax_span(lo, hi, L.red, &pmin);
+  if (span == 0) return;
+  const int bits = 64 - __clzll((long long)span);
+  unsigned long long* src_p = p;
+  int32_t* src_r = row;
+  unsigned long long* dst_p = alt_p;
+  int32_t* dst_r = alt_row;
+  unsigned* s_base = reinterpret_cast<unsigned*>(L.kA);  // running digit offsets
+  for (int sh = 0; sh < bits; sh += kRadixBits) {
+    unsigned* s_hist = L.start;
+    for (int d = threadIdx.x; d < kRadix; d += kLocalThreads) s_hist[d] = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < m; i += kLocalThreads)
+      atomicAdd(&s_hist[((src_p[i] - pmin) >> sh) & (kRadix - 1)], 1u);
+    __syncthreads();
+    int c = threadIdx.x < kRadix ? (int)s_hist[threadIdx.x] : 0;
+    int tot;
+    int ex = block_exclusive_sum<kLocalThreads>(c, L.scan, &tot);
+    if (threadIdx.x < kRadix) s_base[threadIdx.x] = (unsigned)ex;
+    __syncthreads();
+    for (int64_t t0 = 0; t0 < m; t0 += kLocalCap) {
+      const int tm = (int)(m - t0 < kLocalCap ? m - t0 : kLocalCap);
+      const int per = (tm + kLocalWarps - 1) / kLocalWarps;
+      const int wbeg = warp * per;
+      unsigned dig[kLocalItems];
+      int pos[kLocalItems];
+      unsigned long long kk[kLocalItems];
+#pragma unroll
+      for (int it = 0; it < kLocalItems; ++it) {
+        int i = wbeg + it * 32 + lane;
+        bool v = (it * 32 + lane < per) && i < tm;
+        kk[it] = v ? src_p[t0 + i] : 0ull;
+        dig[it] = v ? (unsigned)(((kk[it] - pmin) >> sh) & (kRadix - 1)) : kRadix;
+      }
+      int total;
+      block_rank<kLocalWarps, kLocalItems>(dig, pos, (per + 31) >> 5, L.cnt, L.start, L.scan, &total);
+#pragma unroll
+      for (int it = 0; it < kLocalItems; ++it) {
+        if (pos[it] >= 0) {
+          int i = wbeg + it * 32 + lane;
+          unsigned d = dig[it];
+          int64_t g = (int64_t)s_base[d] + (pos[it] - (int)L.start[d]);
+          dst_p[g] = kk[it];
+          dst_r[g] = src_r[t0 + i];
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < kRadix) {  // advance by this tile's digit counts
+        unsigned d = threadIdx.x;
+        unsigned next = (d + 1 < kRadix) ? L.start[d + 1] : (unsigned)total;
+        s_base[d] += next - L.start[d];
+      }
+      __syncthreads();
+    }
+    unsigned long long* tp = src_p; src_p = dst_p; dst_p = tp;
+    int32_t* tr = src_r; src_r = dst_r; dst_r = tr;
+  }
+  if (src_p != p) {  // odd number of passes: copy back
+    for (int64_t i = threadIdx.x; i < m; i += kLocalThreads) {
+      p[i] = src_p[i];
+      row[i] = src_r[i];
+    }
+  }
+  __syncthreads();
+}
+
+// Every bucket beyond one warp's share sorted by one block: on-chip up to
+// kLocalCap rows.  A larger bucket is split by one pass on the top 8 bits of
+// its key span into the scratch arrays (a counting scatter: equal keys need
+// no order), then runs of consecutive parts of up to kLocalCap rows are
+// sorted on-chip back into place; a part beyond that is one key (already in
+// order) or is sorted in global memory.
 __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSortArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned long long* const kA0 = reinterpret_cast<unsigned long long*>(smem);
-  unsigned long long* const kB0 = kA0 + kLocalCap;
-  int32_t* const rA0 = reinterpret_cast<int32_t*>(kB0 + kLocalCap);
-  int32_t* const rB0 = rA0 + kLocalCap;
-  unsigned* s_cnt = reinterpret_cast<unsigned*>(rB0 + kLocalCap);
-  unsigned* s_start = s_cnt + kLocalWarps * (kRadix + 1);
   __shared__ int s_scan[33];
   __shared__ unsigned long long s_red[2 * kLocalWarps];
+  __shared__ unsigned s_part[kRadix + 1];
   __shared__ uint32_t s_b;
+  LocalSmem L;
+  L.kA = reinterpret_cast<unsigned long long*>(smem);
+  L.kB = L.kA + kLocalCap;
+  L.rA = reinterpret_cast<int32_t*>(L.kB + kLocalCap);
+  L.rB = L.rA + kLocalCap;
+  L.cnt = reinterpret_cast<unsigned*>(L.rB + kLocalCap);
+  L.start = L.cnt + kLocalWarps * (kRadix + 1);
+  L.scan = s_scan;
+  L.red = s_red;
   const int B = a.lp->B;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   while (true) {
     if (threadIdx.x == 0) s_b = atomicAdd(a.queue, 1u);
     __syncthreads();
@@ -874,127 +1034,63 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
     if (m <= 1) continue;
     if (a.big_flags && m <= kLocalCap && warp_bucket_size(m) && !a.big_flags[b]) continue;  // sorted by a warp
     if (m <= kLocalCap) {
-      // ---- on-chip: load, find the key span, LSD over its bits, store
-      unsigned long long* kA = kA0;
-      unsigned long long* kB = kB0;
-      int32_t* rA = rA0;
-      int32_t* rB = rB0;
-      unsigned long long lo = ~0ull, hi = 0;
-      for (int i = threadIdx.x; i < m; i += kLocalThreads) {
-        unsigned long long k = a.p[o0 + i];
-        kA[i] = k;
-        rA[i] = a.row[o0 + i];
-        lo = k < lo ? k : lo;
-        hi = k > hi ? k : hi;
+      onchip_sort(a.p + o0, a.row + o0, a.p + o0, a.row + o0, (int)m, L);
+      continue;
+    }
+    // ---- split by the top 8 bits of the key span
+    unsigned long long lo = ~0ull, hi = 0;
+    for (int64_t i = threadIdx.x; i < m; i += kLocalThreads) {
+      unsigned long long k = a.p[o0 + i];
+      lo = k < lo ? k : lo;
+      hi = k > hi ? k : hi;
+    }
+    unsigned long long pmin;
+    const unsigned long long span = block_minmax_span(lo, hi, s_red, &pmin);
+    if (span == 0) continue;  // one key
+    const int bits = 64 - __clzll((long long)span);
+    const int sh = bits > kRadixBits ? bits - kRadixBits : 0;
+    unsigned* s_hist = L.start;
+    for (int d = threadIdx.x; d < kRadix; d += kLocalThreads) s_hist[d] = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < m; i += kLocalThreads) atomicAdd(&s_hist[(a.p[o0 + i] - pmin) >> sh], 1u);
+    __syncthreads();
+    {
+      const int c = threadIdx.x < kRadix ? (int)s_hist[threadIdx.x] : 0;
+      int tot;
+      const int ex = block_exclusive_sum<kLocalThreads>(c, s_scan, &tot);
+      if (threadIdx.x < kRadix) {
+        s_part[threadIdx.x] = (unsigned)ex;
+        s_hist[threadIdx.x] = (unsigned)ex;  // becomes the scatter cursor
       }
-      unsigned long long pmin;
-      unsigned long long span = block_minmax_span(lo, hi, s_red, &pmin);
-      if (span == 0) continue;  // one key: already in order
-      const int bits = 64 - __clzll((long long)span);
-      const int per = (int)((m + kLocalWarps - 1) / kLocalWarps);
-      const int wbeg = warp * per;
-      for (int sh = 0; sh < bits; sh += kRadixBits) {
-        unsigned dig[kLocalItems];
-        int pos[kLocalItems];
-#pragma unroll
-        for (int it = 0; it < kLocalItems; ++it) {
-          int i = wbeg + it * 32 + lane;
-          bool v = (it * 32 + lane < per) && i < m;
-          dig[it] = v ? (unsigned)(((kA[i] - pmin) >> sh) & (kRadix - 1)) : kRadix;
-        }
-        int total;
-        block_rank<kLocalWarps, kLocalItems>(dig, pos, (per + 31) >> 5, s_cnt, s_start, s_scan, &total);
-#pragma unroll
-        for (int it = 0; it < kLocalItems; ++it) {
-          if (pos[it] >= 0) {
-            int i = wbeg + it * 32 + lane;
-            kB[pos[it]] = kA[i];
-            rB[pos[it]] = rA[i];
-          }
-        }
-        __syncthreads();
-        unsigned long long* tk = kA; kA = kB; kB = tk;
-        int32_t* tr = rA; rA = rB; rB = tr;
-      }
-      for (int i = threadIdx.x; i < m; i += kLocalThreads) {
-        a.p[o0 + i] = kA[i];
-        a.row[o0 + i] = rA[i];
-      }
+      if (threadIdx.x == 0) s_part[kRadix] = (unsigned)m;
       __syncthreads();
-    } else {
-      // ---- fallback: LSD radix sort of this bucket in global memory by one
-      // block, tile by tile (tiles in order keep it stable)
-      unsigned long long lo = ~0ull, hi = 0;
-      for (int64_t i = threadIdx.x; i < m; i += kLocalThreads) {
-        unsigned long long k = a.p[o0 + i];
-        lo = k < lo ? k : lo;
-        hi = k > hi ? k : hi;
-      }
-      unsigned long long pmin;
-      unsigned long long span = block_minmax_span(lo, hi, s_red, &pmin);
-      if (span == 0) continue;
-      const int bits = 64 - __clzll((long long)span);
-      unsigned long long* src_p = a.p + o0;
-      int32_t* src_r = a.row + o0;
-      unsigned long long* dst_p = a.alt_p + o0;
-      int32_t* dst_r = a.alt_row + o0;
-      unsigned* s_base = reinterpret_cast<unsigned*>(kA0);  // running digit offsets
-      for (int sh = 0; sh < bits; sh += kRadixBits) {
-        unsigned* s_hist = s_start;
-        for (int d = threadIdx.x; d < kRadix; d += kLocalThreads) s_hist[d] = 0;
-        __syncthreads();
-        for (int64_t i = threadIdx.x; i < m; i += kLocalThreads)
-          atomicAdd(&s_hist[((src_p[i] - pmin) >> sh) & (kRadix - 1)], 1u);
-        __syncthreads();
-        int c = threadIdx.x < kRadix ? (int)s_hist[threadIdx.x] : 0;
-        int tot;
-        int ex = block_exclusive_sum<kLocalThreads>(c, s_scan, &tot);
-        if (threadIdx.x < kRadix) s_base[threadIdx.x] = (unsigned)ex;
-        __syncthreads();
-        for (int64_t t0 = 0; t0 < m; t0 += kLocalCap) {
-          const int tm = (int)(m - t0 < kLocalCap ? m - t0 : kLocalCap);
-          const int per = (tm + kLocalWarps - 1) / kLocalWarps;
-          const int wbeg = warp * per;
-          unsigned dig[kLocalItems];
-          int pos[kLocalItems];
-          unsigned long long kk[kLocalItems];
-#pragma unroll
-          for (int it = 0; it < kLocalItems; ++it) {
-            int i = wbeg + it * 32 + lane;
-            bool v = (it * 32 + lane < per) && i < tm;
-            kk[it] = v ? src_p[t0 + i] : 0ull;
-            dig[it] = v ? (unsigned)(((kk[it] - pmin) >> sh) & (kRadix - 1)) : kRadix;
-          }
-          int total;
-          block_rank<kLocalWarps, kLocalItems>(dig, pos, (per + 31) >> 5, s_cnt, s_start, s_scan, &total);
-#pragma unroll
-          for (int it = 0; it < kLocalItems; ++it) {
-            if (pos[it] >= 0) {
-              int i = wbeg + it * 32 + lane;
-              unsigned d = dig[it];
-              int64_t g = (int64_t)s_base[d] + (pos[it] - (int)s_start[d]);
-              dst_p[g] = kk[it];
-              dst_r[g] = src_r[t0 + i];
-            }
-          }
-          __syncthreads();
-          if (threadIdx.x < kRadix) {  // advance by this tile's digit counts
-            unsigned d = threadIdx.x;
-            unsigned next = (d + 1 < kRadix) ? s_start[d + 1] : (unsigned)total;
-            s_base[d] += next - s_start[d];
-          }
-          __syncthreads();
+    }
+    for (int64_t i = threadIdx.x; i < m; i += kLocalThreads) {
+      const unsigned long long k = a.p[o0 + i];
+      const unsigned pos = atomicAdd(&s_hist[(k - pmin) >> sh], 1u);
+      a.alt_p[o0 + pos] = k;
+      a.alt_row[o0 + pos] = a.row[o0 + i];
+    }
+    __syncthreads();
+    // ---- consecutive parts packed into on-chip runs, back into place
+    int d = 0;
+    while (d < kRadix) {
+      const unsigned p0 = s_part[d];
+      if (s_part[d + 1] - p0 > (unsigned)kLocalCap) {
+        const int64_t pm = s_part[d + 1] - p0;
+        for (int64_t i = threadIdx.x; i < pm; i += kLocalThreads) {
+          a.p[o0 + p0 + i] = a.alt_p[o0 + p0 + i];
+          a.row[o0 + p0 + i] = a.alt_row[o0 + p0 + i];
         }
-        unsigned long long* tp = src_p; src_p = dst_p; dst_p = tp;
-        int32_t* tr = src_r; src_r = dst_r; dst_r = tr;
+        __syncthreads();
+        global_lsd(a.p + o0 + p0, a.row + o0 + p0, a.alt_p + o0 + p0, a.alt_row + o0 + p0, pm, L);
+        ++d;
+        continue;
       }
-      if (src_p != a.p + o0) {  // odd number of passes: copy back
-        for (int64_t i = threadIdx.x; i < m; i += kLocalThreads) {
-          a.p[o0 + i] = src_p[i];
-          a.row[o0 + i] = src_r[i];
-        }
-      }
-      __syncthreads();
+      int e = d + 1;
+      while (e < kRadix && s_part[e + 1] - p0 <= (unsigned)kLocalCap) ++e;
+      onchip_sort(a.alt_p + o0 + p0, a.alt_row + o0 + p0, a.p + o0 + p0, a.row + o0 + p0, (int)(s_part[e] - p0), L);
+      d = e;
     }
   }
 }

@@ -158,18 +158,11 @@ __global__ void __launch_bounds__(kRadix) sort_plan_kernel(SortArgs a) {
 constexpr uint32_t kSFlagAgg = 1u << 30, kSFlagPrefix = 2u << 30, kSFlagFailed = 3u << 30;
 constexpr uint32_t kSFlagMask = 3u << 30, kSValMask = ~kSFlagMask;
 
-// BULK: the block takes its next tile before working on the current one and
-// has the copy engine bring that tile's keys and values into the other of
-// two shared buffers (cp.async.bulk on an mbarrier), so every block keeps a
-// tile of loads in flight through its whole compute phase.  The buffer just
-// read is the staging area of the scatter.  Needs 16-byte aligned sources;
-// a ragged last tile is loaded directly.
-template <typename K, int THREADS, int ITEMS, bool BULK>
-__global__ void __launch_bounds__(THREADS, BULK ? 2 : 3) sort_pass_kernel(SortArgs a, int pass, uint32_t num_tiles) {
+template <typename K, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS, 3) sort_pass_kernel(SortArgs a, int pass, uint32_t num_tiles) {
   static_assert(THREADS == kRadix, "one thread per digit");
   constexpr int TILE = THREADS * ITEMS;
   constexpr int WARPS = THREADS / 32;
-  constexpr int BUF = TILE * ((int)sizeof(K) + 4);  // BULK buffer: TILE keys, then TILE values
   const PassDesc pd = a.plan->pass[pass];
   if (!pd.active) return;
 
@@ -180,10 +173,9 @@ __global__ void __launch_bounds__(THREADS, BULK ? 2 : 3) sort_pass_kernel(SortAr
   __shared__ uint32_t s_tile;
   __shared__ int s_failed;
   __shared__ uint8_t s_dig[TILE];  // digit of every staged slot
-  __shared__ __align__(8) unsigned long long s_bar[2];
-  __shared__ int s_bulk[2];  // BULK: buffer holds a copy in flight
-  __shared__ int s_abort;
-  extern __shared__ __align__(16) unsigned char s_raw[];  // staging (TILE keys, reused for values); BULK: 2 buffers
+  extern __shared__ __align__(16) unsigned char s_raw[];  // TILE keys, reused for values
+  K* s_keys = reinterpret_cast<K*>(s_raw);
+  int32_t* s_vals = reinterpret_cast<int32_t*>(s_raw);
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = clamp_n(a.n_max, a.d_n);
@@ -196,100 +188,35 @@ __global__ void __launch_bounds__(THREADS, BULK ? 2 : 3) sort_pass_kernel(SortAr
   const int kout_dt = pd.last ? a.key_dt : (sizeof(K) == 4 ? kKeyU32 : kKeyU64);
   const uint32_t* digit_off = a.hist + pass * kRadix;
   const long long limit = g_spin_limit;
-  const bool has_vals = !(pd.first && vin == nullptr);
-  const int kw = pd.first ? key_bits(a.key_dt) / 8 : (int)sizeof(K);  // bytes per source key
-
-  // BULK: thread 0 starts the copy of tile t into buffer `buf` (full tiles)
-  auto issue = [&](int buf, uint32_t t) {
-    int bulk = 0;
-    if (t < num_tiles) {
-      const int64_t base = (int64_t)t * TILE;
-      if (base + TILE <= n) {
-        unsigned char* dst = s_raw + buf * BUF;
-        const uint32_t kbytes = (uint32_t)(TILE * kw), vbytes = has_vals ? (uint32_t)(TILE * 4) : 0u;
-        mbar_expect_tx(&s_bar[buf], kbytes + vbytes);
-        bulk_g2s(dst, static_cast<const char*>(kin) + base * kw, kbytes, &s_bar[buf]);
-        if (has_vals) bulk_g2s(dst + TILE * sizeof(K), vin + base, vbytes, &s_bar[buf]);
-        bulk = 1;
-      }
-    }
-    s_bulk[buf] = bulk;
-  };
-  uint32_t cur = 0, phase0 = 0, phase1 = 0;
-  int b = 0;
-  if (BULK) {
-    if (threadIdx.x == 0) {
-      mbar_init(&s_bar[0], 1);
-      mbar_init(&s_bar[1], 1);
-      mbar_init_fence();
-      s_abort = 0;
-      s_tile = atomicAdd(&a.tile_counters[pass], 1u);
-      issue(0, s_tile);
-    }
-    __syncthreads();
-    cur = s_tile;
-  }
 
   while (true) {
     if (threadIdx.x == 0) {
+      s_tile = atomicAdd(&a.tile_counters[pass], 1u);
       s_failed = 0;
-      if (!BULK) {
-        s_tile = atomicAdd(&a.tile_counters[pass], 1u);
-      } else if (cur < num_tiles) {
-        s_tile = atomicAdd(&a.tile_counters[pass], 1u);  // the next tile, fetched meanwhile
-        issue(b ^ 1, s_tile);
-      }
     }
     for (int i = threadIdx.x; i < WARPS * (kRadix + 1); i += THREADS) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
-    const uint32_t tile = BULK ? cur : s_tile;
+    const uint32_t tile = s_tile;
     if (tile >= num_tiles) break;
-    const uint32_t next = s_tile;
     const int64_t tile_base = (int64_t)tile * TILE;
-    K* s_keys = reinterpret_cast<K*>(BULK ? s_raw + b * BUF : s_raw);
-    int32_t* s_vals = reinterpret_cast<int32_t*>(BULK ? s_raw + b * BUF : s_raw);
 
     // ---- load (warp-striped) and rank within the warp
     K key[ITEMS];
     int32_t val[ITEMS];
     uint32_t dr[ITEMS];  // (rank within the warp's digit << 9) | digit (kRadix = padding row)
-    if (BULK && s_bulk[b]) {
-      const uint32_t ph = b ? phase1 : phase0;
-      if (!mbar_wait_bounded(&s_bar[b], ph, limit)) atomicExch(&s_abort, 1);
-      if (b) phase1 ^= 1; else phase0 ^= 1;
-      __syncthreads();
-      if (s_abort) {  // a copy that never completed: record it, wait out the other buffer's copy, stop
-        if (threadIdx.x == 0) raise_status(TQP_ERR_TIMEOUT);
-        if (s_bulk[b ^ 1]) mbar_wait_bounded(&s_bar[b ^ 1], b ? phase0 : phase1, limit);
-        return;
-      }
-      const unsigned char* kb = s_raw + b * BUF;
-      const int32_t* vb = reinterpret_cast<const int32_t*>(s_raw + b * BUF + TILE * sizeof(K));
 #pragma unroll
-      for (int it = 0; it < ITEMS; ++it) {
-        const int idx = warp * (32 * ITEMS) + it * 32 + lane;
-        const K u = (K)encode_key(kb, kin_dt, idx);
-        key[it] = u;
-        val[it] = has_vals ? vb[idx] : (int32_t)(tile_base + idx);
-        dr[it] = digit_of(u, a.begin_bit, a.nbits, pass);
+    for (int it = 0; it < ITEMS; ++it) {
+      int64_t row = tile_base + (int64_t)warp * (32 * ITEMS) + it * 32 + lane;
+      bool valid = row < n;
+      K u = 0;
+      int32_t v = 0;
+      if (valid) {
+        u = (K)encode_key(kin, kin_dt, row);
+        v = (pd.first && vin == nullptr) ? (int32_t)row : vin[row];
       }
-      fence_async_smem();
-      __syncthreads();  // the buffer becomes the staging area below
-    } else {
-#pragma unroll
-      for (int it = 0; it < ITEMS; ++it) {
-        int64_t row = tile_base + (int64_t)warp * (32 * ITEMS) + it * 32 + lane;
-        bool valid = row < n;
-        K u = 0;
-        int32_t v = 0;
-        if (valid) {
-          u = (K)encode_key(kin, kin_dt, row);
-          v = has_vals ? vin[row] : (int32_t)row;
-        }
-        key[it] = u;
-        val[it] = v;
-        dr[it] = valid ? digit_of(u, a.begin_bit, a.nbits, pass) : kRadix;
-      }
+      key[it] = u;
+      val[it] = v;
+      dr[it] = valid ? digit_of(u, a.begin_bit, a.nbits, pass) : kRadix;
     }
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
@@ -322,19 +249,20 @@ __global__ void __launch_bounds__(THREADS, BULK ? 2 : 3) sort_pass_kernel(SortAr
       if (!inject) st_volatile_u32(st, kSFlagPrefix | tile_count);
     } else {
       if (!inject) st_volatile_u32(st, kSFlagAgg | tile_count);
-      // walk back four predecessors at a time: their words are loaded
+      // walk back kLookWin predecessors at a time: their words are loaded
       // together, then consumed in order (waiting only on a word not yet set)
+      constexpr int kLookWin = 8;
       bool done = false;
-      for (long long t = (long long)tile - 1; t >= 0 && !done && !failed; t -= 4) {
-        const int cnt = t >= 3 ? 4 : (int)t + 1;
-        uint32_t w4[4];
+      for (long long t = (long long)tile - 1; t >= 0 && !done && !failed; t -= kLookWin) {
+        const int cnt = t >= kLookWin - 1 ? kLookWin : (int)t + 1;
+        uint32_t wv[kLookWin];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          w4[q] = q < cnt ? ld_volatile_u32(a.status + (size_t)(t - q) * kRadix + d) : 0u;
+        for (int q = 0; q < kLookWin; ++q)
+          wv[q] = q < cnt ? ld_volatile_u32(a.status + (size_t)(t - q) * kRadix + d) : 0u;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kLookWin; ++q) {
           if (q >= cnt || done || failed) break;
-          uint32_t sv = w4[q];
+          uint32_t sv = wv[q];
           long long rounds = 0;
           unsigned sleep_ns = 32;
           while (!(sv & kSFlagMask)) {
@@ -362,13 +290,7 @@ __global__ void __launch_bounds__(THREADS, BULK ? 2 : 3) sort_pass_kernel(SortAr
     __syncthreads();
     const int tile_failed = s_failed;
     __syncthreads();
-    if (tile_failed) {  // give up on this tile without writing
-      if (BULK) {
-        cur = next;
-        b ^= 1;
-      }
-      continue;
-    }
+    if (tile_failed) continue;  // give up on this tile without writing
 
     // ---- stage keys in tile order (with each slot's digit)
 #pragma unroll
@@ -404,11 +326,6 @@ __global__ void __launch_bounds__(THREADS, BULK ? 2 : 3) sort_pass_kernel(SortAr
         const unsigned dd = s_dig[j];
         vout[s_gbase[dd] + (j - (int)s_tile_start[dd])] = s_vals[j];
       }
-    }
-    if (BULK) {
-      fence_async_smem();  // this buffer is the target of a later bulk copy
-      cur = next;
-      b ^= 1;
     }
     __syncthreads();
   }

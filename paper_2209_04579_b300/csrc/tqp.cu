@@ -172,29 +172,15 @@ tqp_status run_sort(const SortWs& w, int key_dt, const void* keys_in, const int3
   sort_hist_kernel<256><<<stride_grid(n, 256), 256, 0, s>>>(a); note_launch();
   sort_plan_kernel<<<1, kRadix, 0, s>>>(a); note_launch();
   prof_mark(2, true, s);
-  // tiles arrive by bulk copies when every source is 16-byte aligned (the
-  // intermediates always are)
-  const bool bulk = (reinterpret_cast<uintptr_t>(keys_in) % 16 == 0) &&
-                    (vals_in == nullptr || reinterpret_cast<uintptr_t>(vals_in) % 16 == 0);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(sort_pass_kernel<uint32_t, kSortThreads, kItems32, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kSortThreads * kItems32 * 8);
-    cudaFuncSetAttribute(sort_pass_kernel<unsigned long long, kSortThreads, kItems64, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kSortThreads * kItems64 * 12);
-    attr = true;
-  }
   for (int p = 0; p < a.npasses; ++p) {
     TQP_CUDA(cudaMemsetAsync(w.status, 0, (size_t)w.tiles * kRadix * sizeof(uint32_t), s));
     if (word_bytes == 4) {
-      auto k = bulk ? sort_pass_kernel<uint32_t, kSortThreads, kItems32, true>
-                    : sort_pass_kernel<uint32_t, kSortThreads, kItems32, false>;
-      size_t smem = (size_t)kSortThreads * kItems32 * (bulk ? 2 * 8 : 4);
+      auto k = sort_pass_kernel<uint32_t, kSortThreads, kItems32>;
+      size_t smem = (size_t)kSortThreads * kItems32 * 4;
       k<<<persistent_grid(k, kSortThreads, smem, w.tiles), kSortThreads, smem, s>>>(a, p, w.tiles); note_launch();
     } else {
-      auto k = bulk ? sort_pass_kernel<unsigned long long, kSortThreads, kItems64, true>
-                    : sort_pass_kernel<unsigned long long, kSortThreads, kItems64, false>;
-      size_t smem = (size_t)kSortThreads * kItems64 * (bulk ? 2 * 12 : 8);
+      auto k = sort_pass_kernel<unsigned long long, kSortThreads, kItems64>;
+      size_t smem = (size_t)kSortThreads * kItems64 * 8;
       k<<<persistent_grid(k, kSortThreads, smem, w.tiles), kSortThreads, smem, s>>>(a, p, w.tiles); note_launch();
     }
   }
@@ -417,6 +403,7 @@ constexpr int kRankT = 256, kRankI = 8;
 constexpr int kProbeT = 256, kProbeI = 8;
 constexpr int kSmemBitmapBytes = 184 * 1024;       // shared bitmap of the first dimension
 constexpr int kMaxSmemOptin = 227 * 1024;          // dynamic shared memory one block may opt in to
+constexpr int kHeavyMult = 4;                      // heavy-key sample / training set
 constexpr int64_t kSmemBitmapDimRows = 4'000'000;  // first dimensions up to this size try it
 constexpr int kCompactT = 256, kCompactI = 8;
 
@@ -1114,7 +1101,12 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
     while (B < (1 << 17) && (int64_t)B * 512 < n) B <<= 1;
   }
   const int epochs = cfg->train ? cfg->train_cfg.epochs : 0;
-  long long minc = (long long)((double)S * kLocalCap / (2.0 * (double)(n > 0 ? n : 1))) + 1;
+  // heavy keys are found in a sample kHeavyMult times larger than the
+  // training set (a key far beyond a bucket's capacity must not escape by
+  // sampling noise); the network trains on every kHeavyMult-th sorted key
+  const int SH = S * kHeavyMult <= (1 << 20) ? S * kHeavyMult : (1 << 20);
+  const int mult = SH / S;
+  long long minc = (long long)((double)SH * kLocalCap / (2.0 * (double)(n > 0 ? n : 1))) + 1;
   if (minc < 2) minc = 2;
   if (minc > 4095) minc = 4095;
   const size_t nn = (size_t)(n > 0 ? n : 1);
@@ -1122,10 +1114,10 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   const int64_t rtiles = (n + kReduceThreads * kReduceItems - 1) / (kReduceThreads * kReduceItems);
   Carver c(ws);
   GroupPlan* gp = c.take<GroupPlan>(1);
-  unsigned long long* sample = c.take<unsigned long long>(S);
-  unsigned long long* ssorted = c.take<unsigned long long>(S);
-  int32_t* srows = c.take<int32_t>(S);
-  SortWs ssort = carve_sort(c, S, 8, 8);
+  unsigned long long* sample = c.take<unsigned long long>(SH);
+  unsigned long long* ssorted = c.take<unsigned long long>(SH);
+  int32_t* srows = c.take<int32_t>(SH);
+  SortWs ssort = carve_sort(c, SH, 8, 8);
   float* tx = c.take<float>(S);
   float* ty = c.take<float>(S);
   tqp_cdf_model* model = c.take<tqp_cdf_model>(1);
@@ -1181,18 +1173,18 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   gb_plan_kernel<<<1, 32, 0, s>>>(gp, nkeys, 64); note_launch();
   lp_init_kernel<<<1, 32, 0, s>>>(gp, nkeys, model, lp, adam, B, (int)minc); note_launch();
   // 2. sample, sorted by the radix sort; training pairs
-  lp_sample_kernel<<<(S + 255) / 256, 256, 0, s>>>(ks, d_sel, n, d_n, gp, S, sample); note_launch();
-  st = run_sort(ssort, kKeyU64, sample, nullptr, ssorted, srows, S, nullptr, 0, 64, s);
+  lp_sample_kernel<<<(SH + 255) / 256, 256, 0, s>>>(ks, d_sel, n, d_n, gp, SH, sample); note_launch();
+  st = run_sort(ssort, kKeyU64, sample, nullptr, ssorted, srows, SH, nullptr, 0, 64, s);
   if (st != TQP_OK) return st;
   // 3. heavy keys; training pairs on the CDF of the light rows (the sort's
   // row ids are no longer needed: srows holds the light prefix)
   if (cfg->heavy) {
-    lp_heavy_kernel<<<1, 1024, 0, s>>>(ssorted, S, lp, heavy); note_launch();
+    lp_heavy_kernel<<<1, 1024, 0, s>>>(ssorted, SH, lp, heavy); note_launch();
   } else {
     lp_no_heavy_kernel<<<1, 32, 0, s>>>(lp); note_launch();
   }
-  lp_light_prefix_kernel<<<1, 1024, 0, s>>>(ssorted, S, heavy, lp, srows); note_launch();
-  lp_targets_kernel<<<(S + 255) / 256, 256, 0, s>>>(ssorted, S, lp, heavy, srows, tx, ty); note_launch();
+  lp_light_prefix_kernel<<<1, 1024, 0, s>>>(ssorted, SH, heavy, lp, srows); note_launch();
+  lp_targets_kernel<<<(S + 255) / 256, 256, 0, s>>>(ssorted, SH, mult, S, lp, heavy, srows, tx, ty); note_launch();
   if (cfg->init == 1) {
     lp_quantile_init_kernel<<<1, kH, 0, s>>>(tx, ty, S, lp, model); note_launch();
   }

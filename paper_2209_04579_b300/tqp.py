@@ -404,9 +404,13 @@ def tqp_cdf_train(x, y, model, cfg=None, stream=None):
 
 
 def learned_cfg(sample=65536, buckets=0, train=True, heavy=True, tcfg=None, init=None):
-    """init: 0 = identity CDF, 1 = sample-quantile knots (default: 1 when training)."""
+    """init: 0 = identity CDF, 1 = sample-quantile knots (default: 1 when training).
+    The default training refines the knots with small Adam steps (100 epochs,
+    lr 1e-4): larger steps disturb a fit that starts close."""
     init = (1 if train else 0) if init is None else init
-    return LearnedCfg(sample, buckets, int(train), int(heavy), tcfg or train_cfg(), int(init), 0)
+    if tcfg is None:
+        tcfg = train_cfg(epochs=100, lr=1e-4) if init == 1 else train_cfg()
+    return LearnedCfg(sample, buckets, int(train), int(heavy), tcfg, int(init), 0)
 
 
 def tqp_groupby_agg_learned(keys, vals, exprs, aggs, cap, cfg=None, sel=None, n=None, d_n=None, stream=None):
