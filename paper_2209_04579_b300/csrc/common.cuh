@@ -65,6 +65,21 @@ __device__ __forceinline__ bool compare(int64_t v, int op, int64_t lit) {
 }
 
 // ---------------------------------------------------------------- memory ops
+// Lanes of the warp whose 9-bit value v (a radix digit, or 256 for an
+// empty slot) equals this lane's: one ballot per bit, each kept as is where
+// this lane's bit is set and complemented where it is clear.  Every lane of
+// the warp must call it.
+__device__ __forceinline__ unsigned match_digit9(unsigned v) {
+  unsigned peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const bool bit = (v >> b) & 1u;
+    const unsigned bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
 // Exact 64-bit add into a word in shared memory through native 32-bit
 // atomics.  The atomic on the low half returns the value it replaced, so each
 // wrap of the low half is seen by exactly one adder, which carries it into

@@ -779,7 +779,7 @@ __device__ __forceinline__ void block_rank(const unsigned (&dig)[ITEMS], int (&p
 #pragma unroll
   for (int it = 0; it < ITEMS; ++it) {
     if (it >= rounds) break;
-    unsigned peers = __match_any_sync(0xffffffffu, dig[it]);
+    unsigned peers = match_digit9(dig[it]);
     int leader = 31 - __clz(peers);
     unsigned before = __popc(peers & ((1u << lane) - 1));
     unsigned* c = s_cnt + warp * (kRadix + 1) + dig[it];
@@ -1151,7 +1151,7 @@ __global__ void __launch_bounds__(kWarpSortWarps * 32) lp_bucket_sort_warp_kerne
       for (int it = 0; it < kWarpItems; ++it) {
         int i = it * 32 + lane;
         dig[it] = i < m ? (unsigned)((wA[i] >> sh) & (kRadix - 1)) : kRadix;
-        unsigned peers = __match_any_sync(0xffffffffu, dig[it]);
+        unsigned peers = match_digit9(dig[it]);
         int leader = 31 - __clz(peers);
         unsigned before = __popc(peers & ((1u << lane) - 1));
         unsigned base = cnt[dig[it]];

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(THREADS, 3) sort_pass_kernel(SortArgs a, int p
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
       const unsigned dg = dr[it];
-      unsigned peers = __match_any_sync(0xffffffffu, dg);
+      unsigned peers = match_digit9(dg);
       int leader = 31 - __clz(peers);
       uint32_t before = __popc(peers & ((1u << lane) - 1));
       uint32_t base = s_wcnt[warp][dg];

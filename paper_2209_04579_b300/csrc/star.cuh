@@ -33,6 +33,22 @@ struct StarPlan {
   int unsupported;
 };
 
+__device__ __forceinline__ unsigned long long key_image(const void* p, int dt, int64_t i) {
+  return dt == TQP_I32 ? (unsigned long long)((uint32_t) static_cast<const int32_t*>(p)[i] ^ 0x80000000u)
+                       : ((unsigned long long) static_cast<const long long*>(p)[i] ^ 0x8000000000000000ull);
+}
+
+// Sorted passing keys side by side with their group ranks, so that the
+// probe's key comparison and the rank share one memory access.
+struct KeyRank32 {
+  uint32_t image;  // order-preserving image of the key
+  int32_t rank;
+};
+struct KeyRank64 {
+  unsigned long long image;
+  long long rank;
+};
+
 // ---- group ranks of one dimension: heads of the sorted packed group keys,
 // scanned into dense ranks; rank scattered to the row, key value kept.
 template <typename K, int THREADS, int ITEMS>
@@ -100,6 +116,7 @@ struct PregatherArgs {
   const int64_t* d_n;
   const int32_t* rank_of_row;  // null: no group column
   int32_t* rank_sorted;
+  void* kr;                    // KeyRank32 (int32 keys) or KeyRank64 per sorted position
   int nv;
   const void* vcol[TQP_MAX_VALS];
   int vdt[TQP_MAX_VALS];
@@ -112,7 +129,12 @@ __global__ void star_pregather_kernel(PregatherArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
     int32_t row = a.srows[p];
-    a.rank_sorted[p] = a.rank_of_row ? a.rank_of_row[row] : 0;
+    const int32_t rk = a.rank_of_row ? a.rank_of_row[row] : 0;
+    a.rank_sorted[p] = rk;
+    if (a.key_dt == TQP_I32)
+      static_cast<KeyRank32*>(a.kr)[p] = KeyRank32{(uint32_t)key_image(a.skeys, a.key_dt, p), rk};
+    else
+      static_cast<KeyRank64*>(a.kr)[p] = KeyRank64{key_image(a.skeys, a.key_dt, p), (long long)rk};
     for (int v = 0; v < a.nv; ++v) a.vout[v][p] = load_as_i64(a.vcol[v], a.vdt[v], row);
     if (p > 0 && load_as_i64(a.skeys, a.key_dt, p) == load_as_i64(a.skeys, a.key_dt, p - 1)) {
       if (atomicExch(&a.plan->unsupported, 1) == 0) raise_status(TQP_ERR_UNSUPPORTED);
@@ -174,21 +196,21 @@ __global__ void star_init_acc_kernel(const StarPlan* plan, const StarAcc A, long
 struct DimDir {
   unsigned long long umin, umax;  // order-preserving images of the first and last key
   int bshift;
-  int pad_;
+  int use_bits;                   // probes test the cell bitmap first (unit cells, or a filtered dimension)
   long long ncells;               // 0: no passing rows (every probe misses)
 };
 
-__device__ __forceinline__ unsigned long long key_image(const void* p, int dt, int64_t i) {
-  return dt == TQP_I32 ? (unsigned long long)((uint32_t) static_cast<const int32_t*>(p)[i] ^ 0x80000000u)
-                       : ((unsigned long long) static_cast<const long long*>(p)[i] ^ 0x8000000000000000ull);
-}
 
-__global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, const int64_t* d_n, int log2_cells_max,
-                                DimDir* dd) {
+
+// n_all: the dimension's rows before its predicates.  Wide cells of a
+// dimension that no predicate filtered skip the bitmap: foreign keys find
+// their row, and a miss is still found by the directory and the key.
+__global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, const int64_t* d_n, int64_t n_all,
+                                int log2_cells_max, DimDir* dd) {
   if (threadIdx.x != 0) return;
   const int64_t nd = clamp_n(n_max, d_n);
   DimDir r;
-  r.pad_ = 0;
+  r.use_bits = 1;
   if (nd == 0) {
     r.umin = 1;
     r.umax = 0;
@@ -208,6 +230,7 @@ __global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, co
   if (span < 8ull * (unsigned long long)nd && bits <= log2_cells_max) tb = bits > tb ? bits : tb;
   r.bshift = bits > tb ? bits - tb : 0;
   r.ncells = (long long)(span >> r.bshift) + 1;
+  r.use_bits = (r.bshift == 0 || nd < n_all) ? 1 : 0;
   *dd = r;
 }
 
@@ -257,6 +280,7 @@ __global__ void dir_cells_kernel(CellArgs a) {
 
 struct ProbeDim {
   const void* skeys;   // sorted passing keys (int32 or int64)
+  const void* kr;      // the same keys' images with their group ranks (KeyRank32 / KeyRank64)
   int key_dt;
   int64_t n_max;
   const int64_t* d_n;
@@ -284,8 +308,6 @@ struct ProbeArgs {
   int64_t n_fact;
   const StarPlan* plan;
   long long* acc;
-  uint32_t* tile_counter;
-  uint32_t num_tiles;
 };
 
 // ---- warp-level compaction queues of the probe
@@ -366,7 +388,6 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   __shared__ long long s_acc[ACC_WORDS];
   __shared__ int s_fring[WARPS][(1 + kMaxDims) * 64];  // probe survivors: row, positions
   __shared__ int s_pring[WARPS][64];                   // rows that pass the fact predicates
-  __shared__ uint32_t s_tile;
   // the aggregate program and value references in shared memory: they are
   // indexed by runtime values below (kernel parameters indexed that way are
   // copied to local memory)
@@ -427,7 +448,14 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   __syncthreads();
 
   // 2. probe of one fact row through every dimension
-  auto probe = [&](bool live, int64_t row, int (&pos)[kMaxDims]) -> bool {
+  // image of the fact key of dimension d at row
+  auto fk_image = [&](int d, int64_t row) -> UK {
+    const ProbeDim& D = a.dim[d];
+    if (K32 || D.key_dt == TQP_I32) return (UK)((uint32_t)__ldg(static_cast<const int32_t*>(D.fk) + row) ^ 0x80000000u);
+    return (UK)((unsigned long long)__ldg(static_cast<const long long*>(D.fk) + row) ^ 0x8000000000000000ull);
+  };
+  // pre: the first dimension's key image u0 is already loaded
+  auto probe = [&](bool live, int64_t row, int (&pos)[kMaxDims], bool pre, UK u0) -> bool {
 #pragma unroll
     for (int d = 0; d < kMaxDims; ++d) {
       pos[d] = 0;
@@ -435,14 +463,11 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
       const ProbeDim& D = a.dim[d];
       UK u = 0, c = 0;
       if (live) {
-        if (K32 || D.key_dt == TQP_I32)
-          u = (UK)((uint32_t)__ldg(static_cast<const int32_t*>(D.fk) + row) ^ 0x80000000u);
-        else
-          u = (UK)((unsigned long long)__ldg(static_cast<const long long*>(D.fk) + row) ^ 0x8000000000000000ull);
+        u = (d == 0 && pre) ? u0 : fk_image(d, row);
         if (u < (UK)dd[d].umin || u > (UK)dd[d].umax) live = false;
         else c = (u - (UK)dd[d].umin) >> dd[d].bshift;
       }
-      if (live) {
+      if (live && dd[d].use_bits) {
         const uint32_t w = (SMEM_BM && d == 0 && sbm) ? s_bm[c >> 5] : __ldg(&D.bitmap[c >> 5]);
         live = (w >> (c & 31)) & 1u;
       }
@@ -454,14 +479,19 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
         // first key >= u lies in [l, h]; narrow while the interval is long,
         // then scan forward from l up to the cell's end
         const int lo = __ldg(&D.dir[c]), hi = __ldg(&D.dir[c + 1]);
+        const bool k32d = K32 || D.key_dt == TQP_I32;
+        auto img = [&](int i) -> UK {
+          return k32d ? (UK)__ldg(&static_cast<const KeyRank32*>(D.kr)[i].image)
+                      : (UK)__ldg(&static_cast<const KeyRank64*>(D.kr)[i].image);
+        };
         int l = lo, h = hi;
         while (h - l > 4) {
           int mid = (l + h) >> 1;
-          if ((UK)key_image(D.skeys, D.key_dt, mid) < u) l = mid + 1; else h = mid;
+          if (img(mid) < u) l = mid + 1; else h = mid;
         }
         int found = -1;
         for (int i = l; i < hi; ++i) {
-          const UK ki = (UK)key_image(D.skeys, D.key_dt, i);
+          const UK ki = img(i);
           if (ki >= u) {
             if (ki == u) found = i;
             break;
@@ -480,9 +510,15 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     if (!v) return;
     long long slot = 0;
 #pragma unroll
-    for (int d = 0; d < kMaxDims; ++d)
-      if (d < a.ndims)
-        slot += (long long)__ldg(unit[d] ? &a.dim[d].rank_cell[pos[d]] : &a.dim[d].rank_sorted[pos[d]]) * stride[d];
+    for (int d = 0; d < kMaxDims; ++d) {
+      if (d >= a.ndims) break;
+      const ProbeDim& D = a.dim[d];
+      long long r;
+      if (unit[d]) r = __ldg(&D.rank_cell[pos[d]]);
+      else if (K32 || D.key_dt == TQP_I32) r = __ldg(&static_cast<const KeyRank32*>(D.kr)[pos[d]].rank);
+      else r = __ldg(&static_cast<const KeyRank64*>(D.kr)[pos[d]].rank);
+      slot += r * stride[d];
+    }
     long long* dst = use_smem ? my_acc + slot * nacc : a.acc + slot * nacc;
     for (int q = 0; q < A.naggs; ++q) {
       long long x = 1;
@@ -542,41 +578,59 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   };
   auto drain_probe = [&](const int (&e)[1], int cnt) {
     int pos[kMaxDims];
-    const bool alive = probe(lane < cnt, e[0], pos);
+    const bool alive = probe(lane < cnt, e[0], pos, false, (UK)0);
     push_survivor(alive, e[0], pos);
   };
 
-  while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    __syncthreads();
-    if (tile >= a.num_tiles) break;
-    const int64_t base = (int64_t)tile * TILE + threadIdx.x;
-    if (a.npred == 0) {
-      // 1. every row goes to the probe, ITEMS rows in flight per thread
+  // 1. every warp walks its own tiles of 32 x ITEMS rows (a static
+  // grid-stride order: no block barrier in the loop)
+  constexpr int WT = 32 * ITEMS;
+  const int64_t nwt = (a.n_fact + WT - 1) / WT;
+  const int64_t nwarps = (int64_t)gridDim.x * WARPS;
+  int64_t wt = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+  if (a.npred == 0) {
+    // every row goes to the probe; the next tile's first-dimension keys are
+    // loaded while this tile is probed
+    UK nxt[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const int64_t r = wt * WT + k * 32 + lane;
+      nxt[k] = (wt < nwt && r < a.n_fact) ? fk_image(0, r) : (UK)0;
+    }
+    for (; wt < nwt; wt += nwarps) {
+      UK cur[ITEMS];
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) cur[k] = nxt[k];
+      const int64_t wn = wt + nwarps;
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const int64_t r = wn * WT + k * 32 + lane;
+        nxt[k] = (wn < nwt && r < a.n_fact) ? fk_image(0, r) : (UK)0;
+      }
       int pos[ITEMS][kMaxDims];
       bool alive[ITEMS];
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
-        const int64_t r = base + (int64_t)k * THREADS;
-        alive[k] = probe(r < a.n_fact, r, pos[k]);
+        const int64_t r = wt * WT + k * 32 + lane;
+        alive[k] = probe(r < a.n_fact, r, pos[k], true, cur[k]);
       }
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k) push_survivor(alive[k], (int)(base + (int64_t)k * THREADS), pos[k]);
-    } else {
-      // 1. fact predicates, then the passing rows into the probe queue
+      for (int k = 0; k < ITEMS; ++k) push_survivor(alive[k], (int)(wt * WT + k * 32 + lane), pos[k]);
+    }
+  } else {
+    // fact predicates, then the passing rows into the probe queue
+    for (; wt < nwt; wt += nwarps) {
       bool pass[ITEMS];
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k) pass[k] = base + (int64_t)k * THREADS < a.n_fact;
+      for (int k = 0; k < ITEMS; ++k) pass[k] = wt * WT + k * 32 + lane < a.n_fact;
       for (int p = 0; p < a.npred; ++p) {
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k)
-          if (pass[k]) pass[k] = compare(load_as_i64(a.pcol[p], a.pdt[p], base + (int64_t)k * THREADS), a.pop[p], a.plit[p]);
+          if (pass[k]) pass[k] = compare(load_as_i64(a.pcol[p], a.pdt[p], wt * WT + k * 32 + lane), a.pop[p], a.plit[p]);
       }
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
-        const int val[1] = {(int)(base + (int64_t)k * THREADS)};
+        const int val[1] = {(int)(wt * WT + k * 32 + lane)};
         ring_push(pq, pass[k], val, drain_probe);
       }
     }

@@ -386,6 +386,7 @@ struct StarDimWs {
   long long* gkey;
   long long* G;
   int32_t* rank_sorted;
+  void* kr;
   long long* dval[TQP_MAX_VALS];
   uint32_t ftiles, rtiles;
   int gword;
@@ -755,6 +756,7 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
       w.G = c.take<long long>(1);
     }
     w.rank_sorted = c.take<int32_t>(nn);
+    w.kr = c.take<char>(nn * (eb == 4 ? sizeof(KeyRank32) : sizeof(KeyRank64)));
     for (int v = 0; v < nvals; ++v)
       if (vals[v].src == d + 1) w.dval[v] = c.take<long long>(nn);
     w.log2cells = 1;
@@ -769,7 +771,6 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
   StarPlan* plan = c.take<StarPlan>(1);
   const int nacc = naggs + 1;
   long long* acc = c.take<long long>((size_t)slots_cap * nacc);
-  uint32_t* pcounter = c.take<uint32_t>(1);
   const int64_t ptiles = (n_fact + kProbeT * kProbeI - 1) / (kProbeT * kProbeI);
   const int64_t ctiles = (slots_cap + kCompactT * kCompactI - 1) / (kCompactT * kCompactI);
   unsigned long long* cstatus = c.take<unsigned long long>((size_t)ctiles);
@@ -873,6 +874,7 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
       pg.d_n = dcnt;
       pg.rank_of_row = D.group.data ? w.rank_of_row : nullptr;
       pg.rank_sorted = w.rank_sorted;
+      pg.kr = w.kr;
       pg.plan = plan;
       for (int v = 0; v < nvals; ++v) {
         if (vals[v].src != d + 1) continue;
@@ -883,7 +885,7 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
       }
       star_pregather_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(pg); note_launch();
     }
-    dir_plan_kernel<<<1, 32, 0, s>>>(w.skeys, D.key.dtype, D.n, dcnt, w.log2cells, w.dplan); note_launch();
+    dir_plan_kernel<<<1, 32, 0, s>>>(w.skeys, D.key.dtype, D.n, dcnt, D.n, w.log2cells, w.dplan); note_launch();
     if (D.n > 0) {
       TQP_CUDA(cudaMemsetAsync(w.bitmap, 0, ((size_t)(1ll << w.log2cells) / 32 + 1) * sizeof(uint32_t), s));
       dir_fill_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(w.skeys, D.key.dtype, D.n, dcnt, w.dplan, w.dir,
@@ -916,6 +918,7 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
   pa.ndims = ndims;
   for (int d = 0; d < ndims; ++d) {
     pa.dim[d].skeys = W[d].skeys;
+    pa.dim[d].kr = W[d].kr;
     pa.dim[d].key_dt = dims[d].key.dtype;
     pa.dim[d].n_max = dims[d].n;
     pa.dim[d].d_n = dims[d].npred ? W[d].cnt : nullptr;
@@ -948,9 +951,6 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
   pa.n_fact = n_fact;
   pa.plan = plan;
   pa.acc = acc;
-  pa.tile_counter = pcounter;
-  pa.num_tiles = (uint32_t)ptiles;
-  TQP_CUDA(cudaMemsetAsync(pcounter, 0, 4, s));
   if (ptiles > 0) {
     prof_mark(1, true, s);
     bool k32 = true;
@@ -968,7 +968,6 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
         attr = true;
       }
       const int64_t t1024 = (n_fact + 1024 * 4 - 1) / (1024 * 4);
-      pa.num_tiles = (uint32_t)t1024;
       pk<<<persistent_grid(pk, 1024, kSmemBitmapBytes, t1024), 1024, kSmemBitmapBytes, s>>>(pa, A, words);
       note_launch();
     } else {
