@@ -55,7 +55,7 @@ struct PartialT {
   long long v[N];
   int c;  // segment heads inside the span
 };
-using Partial = PartialT<TQP_MAX_AGGS>;  // storage layout of the look-back payloads
+using Partial = PartialT<TQP_MAX_AGGS>;  // storage layout of the per-tile carries
 
 __device__ __forceinline__ long long agg_identity(int op) {
   return op == TQP_MIN ? LLONG_MAX : (op == TQP_MAX ? LLONG_MIN : 0ll);
@@ -74,18 +74,6 @@ __device__ __forceinline__ void partial_identity(PartialT<N>& p, const AggProgra
 #pragma unroll
   for (int a = 0; a < N; ++a) p.v[a] = (a < P.naggs) ? agg_identity(P.op[a]) : 0;
   p.c = 0;
-}
-
-// left (+) right of the segmented reduction: a head inside `right` cuts off `left`.
-template <int N>
-__device__ __forceinline__ PartialT<N> partial_combine(const PartialT<N>& l, const PartialT<N>& r,
-                                                      const AggProgram& P) {
-  PartialT<N> o;
-#pragma unroll
-  for (int a = 0; a < N; ++a)
-    o.v[a] = (r.c > 0 || a >= P.naggs) ? r.v[a] : agg_fold(P.op[a], l.v[a], r.v[a]);
-  o.c = l.c + r.c;
-  return o;
 }
 
 // Expression e at row: product of (mul * val + add) over its terms, mod 2^64.
@@ -113,24 +101,6 @@ __device__ __forceinline__ void fold_row(PartialT<N>& p, const AggProgram& P, in
       p.v[a] = agg_fold(P.op[a], p.v[a], x);
     }
   }
-}
-
-template <int N>
-__device__ __forceinline__ PartialT<N> shfl_down_partial(const PartialT<N>& p, int d) {
-  PartialT<N> o;
-#pragma unroll
-  for (int a = 0; a < N; ++a) o.v[a] = __shfl_down_sync(0xffffffffu, p.v[a], d);
-  o.c = __shfl_down_sync(0xffffffffu, p.c, d);
-  return o;
-}
-
-template <int N>
-__device__ __forceinline__ PartialT<N> shfl_up_partial(const PartialT<N>& p, int d) {
-  PartialT<N> o;
-#pragma unroll
-  for (int a = 0; a < N; ++a) o.v[a] = __shfl_up_sync(0xffffffffu, p.v[a], d);
-  o.c = __shfl_up_sync(0xffffffffu, p.c, d);
-  return o;
 }
 
 // ---------------------------------------------------------------- key plan
@@ -245,10 +215,8 @@ struct ReduceArgs {
   long long* out_aggs;
   int64_t cap;
   int64_t* d_out_groups;
-  uint32_t* flags;         // [num_tiles] look-back flags
-  Partial* agg_payload;    // [num_tiles]
-  Partial* pre_payload;    // [num_tiles]
-  uint32_t* tile_counter;
+  uint32_t* tile_heads;    // [num_tiles] segment heads per tile, then the heads before each tile
+  Partial* carry;          // [num_tiles] partial of the rows before each tile's first head (c = 1: present)
   uint32_t num_tiles;
   // keys aggregated outside the sorted rows (learned path), merged in key
   // order: sorted packed keys, their count (device) and aggregates [nh][naggs]
@@ -256,15 +224,6 @@ struct ReduceArgs {
   const int* d_nheavy;
   const long long* heavy_acc;
 };
-
-__device__ __forceinline__ int64_t heavy_lower(const unsigned long long* h, int nh, unsigned long long x) {
-  int lo = 0, len = nh;
-  while (len > 0) {
-    int half = len >> 1;
-    if (h[lo + half] < x) { lo += half + 1; len -= half + 1; } else { len = half; }
-  }
-  return lo;
-}
 
 // Writes the key columns of group g, decoded from the packed word.
 __device__ __forceinline__ void write_group_keys(const KeySet& ks, const GroupPlan* plan, long long g,
@@ -305,221 +264,244 @@ __global__ void gb_heavy_only_kernel(ReduceArgs a, int naggs) {
     write_group(a, a.ks, naggs, i, a.heavy[i], a.heavy_acc + (size_t)i * naggs);
 }
 
-template <int N>
-__device__ __forceinline__ void store_partial_relaxed(Partial* dst, const PartialT<N>& p, int naggs) {
-  unsigned long long* d = reinterpret_cast<unsigned long long*>(dst->v);
+// ---------------------------------------------------------------- reduce by key
+// Reduce-by-key over the sorted packed keys in four launches, none of which
+// waits on another block:
+//   gb_heads_kernel      segment heads per tile of TILE rows;
+//   gb_tile_scan_kernel  exclusive scan of the tiles' head counts (the light
+//                        index of each tile's first group) and the total;
+//   gb_reduce_kernel     per tile: every thread folds its ITEMS consecutive
+//                        rows and stores each group whose head it holds; the
+//                        rows before its first head (its lead) belong to an
+//                        earlier group: after a block barrier they are
+//                        combined atomically into that group's output when
+//                        it started in this tile, else into the tile's carry;
+//   gb_carry_kernel      each tile's carry combined atomically into the group
+//                        that reaches into the tile from before.
+// SUM wraps mod 2^64 and MIN / MAX / COUNT commute, so the atomic
+// combinations give exactly the sequential result.  Keys aggregated outside
+// the rows (heavy keys of the learned path) interleave in key order: a light
+// group of light index g and key k goes to g + (heavy keys below k), heavy
+// key i between the light groups g-1 and g to g + i.
+constexpr int kReduceHeavyMax = 1024;  // heavy keys merged by the reduce
+
+template <typename K, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS) gb_heads_kernel(ReduceArgs a) {
+  constexpr int TILE = THREADS * ITEMS;
+  __shared__ int s_red[THREADS / 32];
+  const int64_t n = a.plan->unsupported ? 0 : clamp_n(a.n_max, a.d_n);
+  const K* keys = static_cast<const K*>(a.keys);
+  for (int64_t t = blockIdx.x; t < (int64_t)a.num_tiles; t += gridDim.x) {
+    int h = 0;
 #pragma unroll
-  for (int a = 0; a < N; ++a)
-    if (a < naggs) st_volatile_u64(d + a, (unsigned long long)p.v[a]);
-  st_volatile_u32(reinterpret_cast<uint32_t*>(&dst->c), (uint32_t)p.c);
+    for (int k = 0; k < ITEMS; ++k) {
+      const int64_t p = t * TILE + (int64_t)k * THREADS + threadIdx.x;
+      if (p < n) h += (p == 0 || keys[p] != keys[p - 1]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = h;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < THREADS / 32; ++w) tot += s_red[w];
+      a.tile_heads[t] = (uint32_t)tot;
+    }
+    __syncthreads();
+  }
 }
 
-template <int N>
-__device__ __forceinline__ PartialT<N> load_partial_relaxed(const Partial* src, const AggProgram& P) {
-  PartialT<N> p;
-  const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src->v);
-#pragma unroll
-  for (int a = 0; a < N; ++a) p.v[a] = (a < P.naggs) ? (long long)ld_volatile_u64(s + a) : 0;
-  p.c = (int)ld_volatile_u32(reinterpret_cast<const uint32_t*>(&src->c));
-  return p;
+// One block of 1024 threads: flags[t] becomes the heads before tile t; the
+// group count (light groups + heavy keys) goes to d_out_groups.
+__global__ void __launch_bounds__(1024) gb_tile_scan_kernel(ReduceArgs a) {
+  __shared__ int s_scan[33];
+  const int64_t T = a.num_tiles;
+  const int64_t per = (T + 1023) / 1024;
+  const int64_t t0 = threadIdx.x * per;
+  long long sum = 0;
+  for (int64_t t = t0; t < t0 + per && t < T; ++t) sum += a.tile_heads[t];
+  int total;
+  long long run = block_exclusive_sum<1024>((int)sum, s_scan, &total);
+  for (int64_t t = t0; t < t0 + per && t < T; ++t) {
+    const uint32_t c = a.tile_heads[t];
+    a.tile_heads[t] = (uint32_t)run;
+    run += c;
+  }
+  if (threadIdx.x == 0) {
+    const int nh = (a.heavy && a.d_nheavy) ? *a.d_nheavy : 0;
+    const long long g = (long long)total + nh;
+    *a.d_out_groups = g;
+    if (g > a.cap) raise_status(TQP_ERR_CAPACITY);
+  }
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
+// Heavy keys below x (s_heavy ascending, nh entries).
+template <typename K>
+__device__ __forceinline__ int heavy_below(const unsigned long long* h, int nh, K x) {
+  int lo = 0, len = nh;
+  while (len > 0) {
+    const int half = len >> 1;
+    if (h[lo + half] < (unsigned long long)x) { lo += half + 1; len -= half + 1; } else { len = half; }
+  }
+  return lo;
 }
-__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+
+// Combines the partial p into the output of group g with atomics.
+template <int N>
+__device__ __forceinline__ void combine_group_atomic(const ReduceArgs& a, const AggProgram& P, long long g,
+                                                     const PartialT<N>& p) {
+  if (g < 0 || g >= a.cap) return;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    if (q >= P.naggs) break;
+    long long* d = a.out_aggs + g * P.naggs + q;
+    switch (P.op[q]) {
+      case TQP_MIN: atomicMin(d, p.v[q]); break;
+      case TQP_MAX: atomicMax(d, p.v[q]); break;
+      default: atomicAdd(reinterpret_cast<unsigned long long*>(d), (unsigned long long)p.v[q]); break;
+    }
+  }
 }
 
 template <typename K, int THREADS, int ITEMS, int NAGG>
 __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggProgram Pg) {
   constexpr int TILE = THREADS * ITEMS;
-  constexpr int WARPS = THREADS / 32;
   using PT = PartialT<NAGG>;
-  __shared__ PT s_warp[WARPS];
-  __shared__ PT s_tile_excl;
   __shared__ AggProgram P;  // the program and the key set in shared memory: indexed by runtime values below
   __shared__ KeySet s_ks;
+  __shared__ int s_scan[33];
+  __shared__ long long s_carry[NAGG];
+  __shared__ int s_carry_used;
+  __shared__ unsigned long long s_heavy[kReduceHeavyMax];
   if (threadIdx.x == 0) {
     P = Pg;
     s_ks = a.ks;
   }
+  const int nh = (a.heavy && a.d_nheavy) ? *a.d_nheavy : 0;
+  for (int i = threadIdx.x; i < nh; i += THREADS) s_heavy[i] = a.heavy[i];
   __syncthreads();
-  __shared__ uint32_t s_tile;
-  __shared__ int s_failed;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t n = clamp_n(a.n_max, a.d_n);
+  const int64_t n = a.plan->unsupported ? 0 : clamp_n(a.n_max, a.d_n);
   const K* keys = static_cast<const K*>(a.keys);
   const int32_t* rows = a.rows;  // null: the value columns are already in sorted order
-  const bool unsupported = a.plan->unsupported != 0;
-  const long long limit = g_spin_limit;
-  const int nh = (a.heavy && a.d_nheavy) ? *a.d_nheavy : 0;
 
-  while (true) {
-    if (threadIdx.x == 0) {
-      s_tile = atomicAdd(a.tile_counter, 1u);
-      s_failed = 0;
-    }
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    if (tile >= a.num_tiles) break;
-    const int64_t base = (int64_t)tile * TILE + (int64_t)threadIdx.x * ITEMS;
-    const int64_t nn = unsupported ? 0 : n;
-
-    // ---- pass 1: heads, and the partial of the thread's trailing run
-    K key[ITEMS];
+  for (int64_t t = blockIdx.x; t < (int64_t)a.num_tiles; t += gridDim.x) {
+    if (threadIdx.x == 0) s_carry_used = 0;
+    if (threadIdx.x < NAGG) s_carry[threadIdx.x] = threadIdx.x < P.naggs ? agg_identity(P.op[threadIdx.x]) : 0;
+    const int64_t base = t * TILE + (int64_t)threadIdx.x * ITEMS;
+    // ---- segment heads of the thread's rows
     uint32_t head = 0;
-    K prev = 0;
-    if (base > 0 && base < nn) prev = keys[base - 1];
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      int64_t p = base + k;
-      key[k] = (p < nn) ? keys[p] : (K)0;
-      if (p < nn && (p == 0 || key[k] != (k ? key[k - 1] : prev))) head |= 1u << k;
-    }
-    PT mine;
-    partial_identity(mine, P);
-    mine.c = __popc(head);
+    const K prev = (base > 0 && base < n) ? keys[base - 1] : (K)0;
     {
-      int last_head = head ? (31 - __clz(head)) : 0;
+      K pk = prev;
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k)
-        if (k >= last_head && base + k < nn) fold_row(mine, P, rows ? rows[base + k] : base + k);
-    }
-
-    // ---- block exclusive segmented scan of the thread partials
-    PT incl = mine;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      PT up = shfl_up_partial(incl, d);
-      if (lane >= d) incl = partial_combine(up, incl, P);
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    PT wexcl;
-    partial_identity(wexcl, P);
-    for (int w = 0; w < warp; ++w) wexcl = partial_combine(wexcl, s_warp[w], P);
-    PT texcl = shfl_up_partial(incl, 1);
-    if (lane == 0) partial_identity(texcl, P);
-    PT thread_excl = partial_combine(wexcl, texcl, P);
-
-    // ---- tile look-back (warp 0: 32 predecessors per step, folded in order)
-    if (warp == 0) {
-      PT tile_agg;
-      partial_identity(tile_agg, P);
-      for (int w = 0; w < WARPS; ++w) tile_agg = partial_combine(tile_agg, s_warp[w], P);
-      const bool inject = ((long long)tile == g_unpublished_tile);
-      PT acc;
-      partial_identity(acc, P);
-      bool failed = false;
-      if (tile == 0) {
-        if (lane == 0 && !inject) {
-          store_partial_relaxed(&a.pre_payload[0], tile_agg, P.naggs);
-          st_release_u32(&a.flags[0], 2u);
-        }
-      } else {
-        if (lane == 0 && !inject) {
-          store_partial_relaxed(&a.agg_payload[tile], tile_agg, P.naggs);
-          st_release_u32(&a.flags[tile], 1u);
-        }
-        long long window_end = tile;
-        while (true) {
-          const long long t = window_end - 1 - lane;
-          uint32_t f = 2u;  // before tile 0: an empty inclusive prefix
-          PT v;
-          partial_identity(v, P);
-          if (t >= 0) {
-            long long rounds = 0;
-            unsigned sleep_ns = 32;
-            while (true) {
-              f = ld_acquire_u32(&a.flags[t]);
-              if (f) break;
-              if (++rounds > limit) { f = 3u; break; }
-              __nanosleep(sleep_ns);
-              if (sleep_ns < 1024) sleep_ns <<= 1;
-            }
-            if (f == 1u || f == 2u) v = load_partial_relaxed<NAGG>(f == 2u ? &a.pre_payload[t] : &a.agg_payload[t], P);
-          }
-          if (__ballot_sync(0xffffffffu, f == 3u)) { failed = true; break; }
-          const unsigned pm = __ballot_sync(0xffffffffu, f == 2u);
-          const int first = pm ? __ffs(pm) - 1 : 31;
-          if (lane > first) partial_identity(v, P);
-          // fold lanes first .. 0 (higher lanes are further left)
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            PT other = shfl_down_partial(v, o);
-            if (lane + o < 32) v = partial_combine(other, v, P);
-          }
-          acc = partial_combine(v, acc, P);  // lane 0 holds the window's fold
-          if (pm) break;
-          window_end -= 32;
-        }
-        if (lane == 0 && !inject) {
-          if (failed) {
-            st_release_u32(&a.flags[tile], 3u);
-          } else {
-            store_partial_relaxed(&a.pre_payload[tile], partial_combine(acc, tile_agg, P), P.naggs);
-            st_release_u32(&a.flags[tile], 2u);
-          }
-        }
-      }
-      if (lane == 0) {
-        if (failed) {
-          raise_status(TQP_ERR_TIMEOUT);
-          s_failed = 1;
-        }
-        s_tile_excl = acc;
-        if (!failed && tile == a.num_tiles - 1) {
-          long long g = (long long)acc.c + tile_agg.c + nh;
-          *a.d_out_groups = g;
-          if (g > a.cap) raise_status(TQP_ERR_CAPACITY);
-        }
+      for (int k = 0; k < ITEMS; ++k) {
+        const int64_t p = base + k;
+        const K kk = p < n ? keys[p] : (K)0;
+        if (p < n && (p == 0 || kk != pk)) head |= 1u << k;
+        pk = kk;
       }
     }
-    __syncthreads();
-    const int tile_failed = s_failed;
-    PT in = partial_combine(s_tile_excl, thread_excl, P);
-    __syncthreads();
-    if (tile_failed) continue;
-
-    // ---- pass 2: finish every segment whose last row this thread holds
-    PT run = in;
-    long long seg = (long long)in.c - 1;
-    K next_after = 0;
-    if (base + ITEMS < nn) next_after = keys[base + ITEMS];
+    const K key0 = base < n ? keys[base] : (K)0;
+    int tile_heads;
+    const int before = block_exclusive_sum<THREADS>(__popc(head), s_scan, &tile_heads);
+    const long long g0 = (long long)a.tile_heads[t] + before;  // light index of the thread's first head
+    // ---- fold, storing every group whose head this thread holds
+    PT acc, lead;
+    partial_identity(acc, P);
+    partial_identity(lead, P);
+    bool lead_open = true;  // rows so far belong to a group from before this thread
+    long long g = g0 - 1;
+    int hl = (nh && base < n) ? heavy_below(s_heavy, nh, base > 0 ? prev : key0) : 0;  // heavy keys below the current key
+    K gkey = 0;
 #pragma unroll 1
     for (int k = 0; k < ITEMS; ++k) {
-      int64_t p = base + k;
-      if (p < nn) {
+      const int64_t p = base + k;
+      if (p < n) {
         if (head & (1u << k)) {
-          ++seg;
-#pragma unroll
-          for (int q = 0; q < NAGG; ++q) run.v[q] = (q < P.naggs) ? agg_identity(P.op[q]) : 0;
+          const K kk = keys[p];
+          if (lead_open) {
+            lead = acc;
+            lead_open = false;
+          } else {
+            write_group_regs(a, s_ks, P.naggs, g + hl, (unsigned long long)gkey, acc);
+          }
+          ++g;
+          gkey = kk;
+          partial_identity(acc, P);
           if (nh) {
-            // heavy keys between the previous group's key and this one go just before it
-            int64_t hi_i = heavy_lower(a.heavy, nh, (unsigned long long)key[k]);
-            int64_t lo_i = p == 0 ? 0 : heavy_lower(a.heavy, nh, (unsigned long long)(k ? key[k - 1] : prev));
-            for (int64_t i = lo_i; i < hi_i; ++i)
-              write_group(a, s_ks, P.naggs, seg + i, a.heavy[i], a.heavy_acc + (size_t)i * P.naggs);
+            // heavy keys between the previous row's key and this one go just before this group
+            const int hl_new = heavy_below(s_heavy, nh, kk);
+            for (int i = (p == 0 ? 0 : hl); i < hl_new; ++i)
+              write_group(a, s_ks, P.naggs, g + i, s_heavy[i], a.heavy_acc + (size_t)i * P.naggs);
+            hl = hl_new;
           }
         }
-        fold_row(run, P, rows ? rows[p] : p);
-        K nk = (k + 1 < ITEMS) ? key[k + 1] : next_after;
-        bool last = (p == nn - 1) || (nk != key[k]);
-        if (last && seg >= 0) {
-          long long hr = nh ? heavy_lower(a.heavy, nh, (unsigned long long)key[k]) : 0;
-          write_group_regs(a, s_ks, P.naggs, seg + hr, (unsigned long long)key[k], run);
-          if (nh && p == nn - 1) {
-            // heavy keys above the last group's key
-            for (int64_t i = hr; i < nh; ++i)
-              write_group(a, s_ks, P.naggs, seg + 1 + i, a.heavy[i], a.heavy_acc + (size_t)i * P.naggs);
-          }
+        fold_row(acc, P, rows ? rows[p] : p);
+        if (nh && p == n - 1) {
+          // heavy keys above the last light key
+          for (int i = hl; i < nh; ++i)
+            write_group(a, s_ks, P.naggs, g + 1 + i, s_heavy[i], a.heavy_acc + (size_t)i * P.naggs);
         }
       }
     }
+    const bool has_rows = base < n;
+    if (has_rows && !lead_open) write_group_regs(a, s_ks, P.naggs, g + hl, (unsigned long long)gkey, acc);
+    if (lead_open) lead = acc;
+    const bool has_lead = has_rows && !(head & 1u);
+    __syncthreads();  // every group stored by its head's thread
+    if (has_lead) {
+      if (before > 0) {
+        // the group started earlier in this tile
+        const int hl0 = nh ? heavy_below(s_heavy, nh, key0) : 0;
+        combine_group_atomic(a, P, g0 - 1 + hl0, lead);
+      } else {
+        // the group reaches into this tile from before: the tile's carry
+#pragma unroll
+        for (int q = 0; q < NAGG; ++q) {
+          if (q >= P.naggs) break;
+          long long* d = &s_carry[q];
+          switch (P.op[q]) {
+            case TQP_MIN: atomicMin(d, lead.v[q]); break;
+            case TQP_MAX: atomicMax(d, lead.v[q]); break;
+            default: shared_add_u64(reinterpret_cast<unsigned long long*>(d), (unsigned long long)lead.v[q]); break;
+          }
+        }
+        s_carry_used = 1;
+      }
+    }
     __syncthreads();
+    if (threadIdx.x == 0) {
+      Partial c;
+      for (int q = 0; q < TQP_MAX_AGGS; ++q) c.v[q] = q < NAGG ? s_carry[q < NAGG ? q : 0] : 0;
+      c.c = s_carry_used;
+      a.carry[t] = c;
+    }
+    __syncthreads();  // the carry is read before the next tile resets it
+  }
+}
+
+// Each tile's carry into the group that reaches into it from before (the
+// light group just before the tile's first head).
+template <typename K, int THREADS, int ITEMS>
+__global__ void gb_carry_kernel(ReduceArgs a, AggProgram P) {
+  constexpr int TILE = THREADS * ITEMS;
+  const int nh = (a.heavy && a.d_nheavy) ? *a.d_nheavy : 0;
+  const K* keys = static_cast<const K*>(a.keys);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)a.num_tiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const Partial& c = a.carry[t];
+    if (!c.c) continue;
+    const K k0 = keys[t * TILE];
+    const long long g = (long long)a.tile_heads[t] - 1 + (nh ? heavy_below(a.heavy, nh, k0) : 0);
+    if (g < 0 || g >= a.cap) continue;
+    for (int q = 0; q < P.naggs; ++q) {
+      long long* d = a.out_aggs + g * P.naggs + q;
+      switch (P.op[q]) {
+        case TQP_MIN: atomicMin(d, c.v[q]); break;
+        case TQP_MAX: atomicMax(d, c.v[q]); break;
+        default: atomicAdd(reinterpret_cast<unsigned long long*>(d), (unsigned long long)c.v[q]); break;
+      }
+    }
   }
 }
 

@@ -293,7 +293,9 @@ struct ProbeDim {
 };
 
 struct ProbeArgs {
+  unsigned* wcounter;  // warp tiles taken (predicate path)
   int ndims;
+  int vec0;  // the first dimension's fact keys are int32 at a 16-byte aligned address
   ProbeDim dim[kMaxDims];
   int npred;
   const void* pcol[TQP_MAX_PREDS];
@@ -381,7 +383,6 @@ __device__ __forceinline__ void ring_flush(WarpRing<F>& q, Drain&& drain) {
 template <int THREADS, int ITEMS, bool SMEM_BM, bool K32>
 __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(ProbeArgs a, StarAcc Ag, int smem_bm_words) {
   using UK = typename std::conditional<K32, uint32_t, unsigned long long>::type;
-  constexpr int TILE = THREADS * ITEMS;
   constexpr int WARPS = THREADS / 32;
   // the shared bitmap variant keeps a smaller accumulator array
   constexpr int ACC_WORDS = SMEM_BM ? kSmemAccWords / 4 : kSmemAccWords;
@@ -582,13 +583,50 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     push_survivor(alive, e[0], pos);
   };
 
-  // 1. every warp walks its own tiles of 32 x ITEMS rows (a static
-  // grid-stride order: no block barrier in the loop)
+  // 1. every warp walks its own tiles of 32 x ITEMS rows (no block barrier
+  // in the loop)
   constexpr int WT = 32 * ITEMS;
   const int64_t nwt = (a.n_fact + WT - 1) / WT;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS;
   int64_t wt = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
-  if (a.npred == 0) {
+  if (a.npred == 0 && a.vec0 && ITEMS % 4 == 0) {
+    // every row goes to the probe.  Lane l takes rows l*ITEMS .. l*ITEMS +
+    // ITEMS - 1 of the tile, whose int32 first-dimension keys arrive in
+    // ITEMS/4 16-byte loads; the next tile's keys load while this one is
+    // probed.
+    const int32_t* fk0 = static_cast<const int32_t*>(a.dim[0].fk);
+    auto load4 = [&](int64_t w, int j, UK (&dst)[ITEMS]) {
+      const int64_t r = w * WT + (int64_t)lane * ITEMS + 4 * j;
+      if (w < nwt && r + 3 < a.n_fact) {
+        const int4 q = __ldg(reinterpret_cast<const int4*>(fk0 + r));
+        dst[4 * j] = (UK)((uint32_t)q.x ^ 0x80000000u);
+        dst[4 * j + 1] = (UK)((uint32_t)q.y ^ 0x80000000u);
+        dst[4 * j + 2] = (UK)((uint32_t)q.z ^ 0x80000000u);
+        dst[4 * j + 3] = (UK)((uint32_t)q.w ^ 0x80000000u);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          dst[4 * j + e] = (w < nwt && r + e < a.n_fact) ? (UK)((uint32_t)__ldg(fk0 + r + e) ^ 0x80000000u) : (UK)0;
+      }
+    };
+    UK nxt[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS / 4; ++j) load4(wt, j, nxt);
+    for (; wt < nwt; wt += nwarps) {
+      UK cur[ITEMS];
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) cur[k] = nxt[k];
+#pragma unroll
+      for (int j = 0; j < ITEMS / 4; ++j) load4(wt + nwarps, j, nxt);
+      const int64_t r0 = wt * WT + (int64_t)lane * ITEMS;
+      int pos[ITEMS][kMaxDims];
+      bool alive[ITEMS];
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) alive[k] = probe(r0 + k < a.n_fact, r0 + k, pos[k], true, cur[k]);
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) push_survivor(alive[k], (int)(r0 + k), pos[k]);
+    }
+  } else if (a.npred == 0) {
     // every row goes to the probe; the next tile's first-dimension keys are
     // loaded while this tile is probed
     UK nxt[ITEMS];
@@ -618,8 +656,16 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
       for (int k = 0; k < ITEMS; ++k) push_survivor(alive[k], (int)(wt * WT + k * 32 + lane), pos[k]);
     }
   } else {
-    // fact predicates, then the passing rows into the probe queue
-    for (; wt < nwt; wt += nwarps) {
+    // fact predicates, then the passing rows into the probe queue.  Warp
+    // tiles are taken from a counter: a tile's cost varies with the
+    // dependent reads of its surviving rows.
+    while (true) {
+      {
+        unsigned tk = 0;
+        if (lane == 0) tk = atomicAdd(a.wcounter, 1u);
+        wt = __shfl_sync(0xffffffffu, tk, 0);
+      }
+      if (wt >= nwt) break;
       bool pass[ITEMS];
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) pass[k] = wt * WT + k * 32 + lane < a.n_fact;

@@ -190,7 +190,7 @@ tqp_status run_sort(const SortWs& w, int key_dt, const void* keys_in, const int3
 
 // ---------------------------------------------------------------- group-by (device part)
 constexpr int kReduceThreads = 256;
-constexpr int kReduceItems = 8;
+constexpr int kReduceItems = 16;
 
 struct GroupWs {
   void* gathered[TQP_MAX_VALS];  // value columns in sorted order (large inputs)
@@ -201,8 +201,7 @@ struct GroupWs {
   int32_t* sorted_rows;
   SortWs sort;
   uint32_t* ctrl;  // reduce counter + flags
-  Partial* agg_payload;
-  Partial* pre_payload;
+  Partial* carry;
   uint32_t tiles;
 };
 
@@ -225,9 +224,8 @@ GroupWs carve_group(Carver& c, int64_t n, int word_bytes, const AggProgram* P = 
   w.sort = carve_sort(c, n, word_bytes, word_bytes == 4 ? 4 : 8);
   int64_t t = (n + kReduceThreads * kReduceItems - 1) / (kReduceThreads * kReduceItems);
   w.tiles = (uint32_t)t;
-  w.ctrl = c.take<uint32_t>(1 + (size_t)(t > 0 ? t : 1));
-  w.agg_payload = c.take<Partial>((size_t)(t > 0 ? t : 1));
-  w.pre_payload = c.take<Partial>((size_t)(t > 0 ? t : 1));
+  w.ctrl = c.take<uint32_t>((size_t)(t > 0 ? t : 1));
+  w.carry = c.take<Partial>((size_t)(t > 0 ? t : 1));
   return w;
 }
 
@@ -239,13 +237,22 @@ void launch_reduce_n(const ReduceArgs& r, const AggProgram& P, uint32_t tiles, c
   note_launch();
 }
 
+// Heads per tile, their scan (and the group count), the tiles' groups, the
+// carries between tiles.
 template <typename K>
 void launch_reduce(const ReduceArgs& r, const AggProgram& P, uint32_t tiles, cudaStream_t s) {
+  if (tiles > 0) {
+    auto hk = gb_heads_kernel<K, kReduceThreads, kReduceItems>;
+    hk<<<persistent_grid(hk, kReduceThreads, 0, tiles), kReduceThreads, 0, s>>>(r); note_launch();
+  }
+  gb_tile_scan_kernel<<<1, 1024, 0, s>>>(r); note_launch();
+  if (tiles == 0) return;
   prof_mark(4, true, s);
   if (P.naggs <= 2) launch_reduce_n<K, 2>(r, P, tiles, s);
   else if (P.naggs <= 4) launch_reduce_n<K, 4>(r, P, tiles, s);
   else launch_reduce_n<K, TQP_MAX_AGGS>(r, P, tiles, s);
   prof_mark(4, false, s);
+  gb_carry_kernel<K, kReduceThreads, kReduceItems><<<(tiles + 255) / 256, 256, 0, s>>>(r, P); note_launch();
 }
 
 // Gathers every value column into the order of `rows` (n or *d_n rows);
@@ -330,7 +337,6 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
   tqp_status st = run_sort(w.sort, word_bytes == 4 ? kKeyU32 : kKeyU64, w.packed, w.rows, w.sorted,
                            w.sorted_rows, n, d_n, 0, word_bytes * 8, s);
   if (st != TQP_OK) return st;
-  TQP_CUDA(cudaMemsetAsync(w.ctrl, 0, (1 + (size_t)w.tiles) * sizeof(uint32_t), s));
   ReduceArgs r;
   r.keys = w.sorted;
   r.rows = w.sorted_rows;
@@ -341,10 +347,8 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
   r.out_aggs = out_aggs;
   r.cap = cap;
   r.d_out_groups = d_out_groups;
-  r.tile_counter = w.ctrl;
-  r.flags = w.ctrl + 1;
-  r.agg_payload = w.agg_payload;
-  r.pre_payload = w.pre_payload;
+  r.tile_heads = w.ctrl;
+  r.carry = w.carry;
   r.num_tiles = w.tiles;
   r.heavy = nullptr;
   r.d_nheavy = nullptr;
@@ -771,6 +775,7 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
   StarPlan* plan = c.take<StarPlan>(1);
   const int nacc = naggs + 1;
   long long* acc = c.take<long long>((size_t)slots_cap * nacc);
+  unsigned* wcounter = c.take<unsigned>(1);
   const int64_t ptiles = (n_fact + kProbeT * kProbeI - 1) / (kProbeT * kProbeI);
   const int64_t ctiles = (slots_cap + kCompactT * kCompactI - 1) / (kCompactT * kCompactI);
   unsigned long long* cstatus = c.take<unsigned long long>((size_t)ctiles);
@@ -915,7 +920,10 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
   star_init_acc_kernel<<<stride_grid(slots_cap * nacc, 256, 4), 256, 0, s>>>(plan, A, acc); note_launch();
   ProbeArgs pa;
   std::memset(&pa, 0, sizeof(pa));
+  pa.wcounter = wcounter;
+  TQP_CUDA(cudaMemsetAsync(wcounter, 0, 4, s));
   pa.ndims = ndims;
+  pa.vec0 = dims[0].key.dtype == TQP_I32 && reinterpret_cast<uintptr_t>(fact_cols[fk_col[0]].data) % 16 == 0;
   for (int d = 0; d < ndims; ++d) {
     pa.dim[d].skeys = W[d].skeys;
     pa.dim[d].kr = W[d].kr;
@@ -1138,9 +1146,8 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   int32_t* arow = c.take<int32_t>(nn);
   uint32_t* queue = c.take<uint32_t>(2);
   uint32_t* big_flags = c.take<uint32_t>((size_t)B);
-  uint32_t* rctrl = c.take<uint32_t>(1 + (size_t)(rtiles > 0 ? rtiles : 1));
-  Partial* ragg = c.take<Partial>((size_t)(rtiles > 0 ? rtiles : 1));
-  Partial* rpre = c.take<Partial>((size_t)(rtiles > 0 ? rtiles : 1));
+  uint32_t* rheads = c.take<uint32_t>((size_t)(rtiles > 0 ? rtiles : 1));
+  Partial* rcarry = c.take<Partial>((size_t)(rtiles > 0 ? rtiles : 1));
   void* lgath[TQP_MAX_VALS] = {};
   if (n >= kPregatherRows)
     for (int v = 0; v < P.nvals; ++v) lgath[v] = c.take<char>(nn * dtype_bytes(P.vdt[v]));
@@ -1260,7 +1267,6 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
     prof_mark(7, false, s);
   }
   // 7. reduce-by-key over the sorted light rows, merging the heavy keys
-  TQP_CUDA(cudaMemsetAsync(rctrl, 0, (1 + (size_t)rtiles) * sizeof(uint32_t), s));
   ReduceArgs r;
   r.keys = lpk;
   r.rows = lrow;
@@ -1271,10 +1277,8 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   r.out_aggs = reinterpret_cast<long long*>(d_out_aggs);
   r.cap = cap;
   r.d_out_groups = d_out_groups;
-  r.tile_counter = rctrl;
-  r.flags = rctrl + 1;
-  r.agg_payload = ragg;
-  r.pre_payload = rpre;
+  r.tile_heads = rheads;
+  r.carry = rcarry;
   r.num_tiles = (uint32_t)rtiles;
   r.heavy = heavy;
   r.d_nheavy = &lp->nheavy;
