@@ -463,6 +463,7 @@ struct PartArgs {
   const unsigned long long* heavy;
   unsigned* count;          // [B]
   unsigned* cursor;         // [B]
+  unsigned* bcount;         // kBlockHist: [blocks][B] counts, then each block's start in every bucket
   unsigned long long* out_p;
   int32_t* out_row;
   long long* heavy_acc;     // [nheavy][naggs]
@@ -474,25 +475,35 @@ constexpr int kHeavySlots = 1 << kHeavyBits;  // open addressing, load <= 1/2
 constexpr int kPartThreads = 1024;
 constexpr int kPartItems = 4;
 
+// Partition modes: the bucket function's steps in global memory, in shared
+// memory, or in shared memory with per-block bucket counts and cursors (each
+// block partitions one contiguous chunk of rows into per-block ranges of
+// every bucket, so row positions come from shared-memory cursors).
+constexpr int kThrGlobal = 0, kThrShared = 1, kBlockHist = 2;
+constexpr int kBlockHistMaxB = 1 << 14;
+
 // Dynamic shared memory: directory, heavy-key table (key, index; index -1 =
-// empty), the heavy accumulators (scatter) and, when they fit, the steps.
+// empty), the heavy accumulators (scatter), the steps (kThrShared and up)
+// and the block's bucket counts or cursors (kBlockHist).
 struct PartSmem {
   int* dir;
   unsigned long long* hk;
   int* hv;
   long long* acc;
   unsigned* thr;
+  unsigned* bh;
 };
 
-inline __host__ __device__ size_t part_smem_bytes(int B, int naggs, bool thr_smem) {
+inline __host__ __device__ size_t part_smem_bytes(int B, int naggs, int mode) {
   size_t o = ((((size_t)1 << kDirBits) + 1) * 4 + 15) & ~(size_t)15;
   o += (size_t)kHeavySlots * 8 + (size_t)kHeavySlots * 4;
   o += (size_t)kMaxHeavy * naggs * 8;
-  if (thr_smem) o += (size_t)(B > 1 ? B - 1 : 1) * 4;
+  if (mode >= kThrShared) o += (size_t)(B > 1 ? B - 1 : 1) * 4;
+  if (mode == kBlockHist) o += (size_t)B * 4;
   return o;
 }
 
-__device__ __forceinline__ PartSmem part_carve(unsigned char* base, int naggs) {
+__device__ __forceinline__ PartSmem part_carve(unsigned char* base, int naggs, int B) {
   PartSmem S;
   size_t o = ((((size_t)1 << kDirBits) + 1) * 4 + 15) & ~(size_t)15;
   S.dir = reinterpret_cast<int*>(base);
@@ -503,6 +514,8 @@ __device__ __forceinline__ PartSmem part_carve(unsigned char* base, int naggs) {
   S.acc = reinterpret_cast<long long*>(base + o);
   o += (size_t)kMaxHeavy * naggs * 8;
   S.thr = reinterpret_cast<unsigned*>(base + o);
+  o += (size_t)(B > 1 ? B - 1 : 1) * 4;
+  S.bh = reinterpret_cast<unsigned*>(base + o);
   return S;
 }
 
@@ -539,12 +552,12 @@ __device__ __forceinline__ unsigned long long pack_row_plan(const PackPlan& K, i
   return u;
 }
 
-// Directory, heavy table, steps (THR_SMEM) and key plan into shared memory.
-template <bool THR_SMEM>
+// Directory, heavy table, steps (kThrShared and up) and key plan into shared memory.
+template <int MODE>
 __device__ __forceinline__ void part_setup(const PartArgs& a, const LearnedPlan& lp, const PartSmem& S, PackPlan& K) {
   for (int i = threadIdx.x; i <= (1 << kDirBits); i += blockDim.x) S.dir[i] = a.dir[i];
   for (int i = threadIdx.x; i < kHeavySlots; i += blockDim.x) S.hv[i] = -1;
-  if (THR_SMEM)
+  if (MODE >= kThrShared)
     for (int i = threadIdx.x; i < lp.B - 1; i += blockDim.x) S.thr[i] = a.thr[i];
   if (threadIdx.x == 0) {
     K.nkeys = a.ks.nkeys;
@@ -565,30 +578,77 @@ __device__ __forceinline__ void part_setup(const PartArgs& a, const LearnedPlan&
   __syncthreads();
 }
 
-// Light rows per bucket.  Each thread carries kPartItems rows at a time.
-template <bool THR_SMEM>
+// Rows a block partitions in kBlockHist mode: one contiguous chunk.
+__device__ __forceinline__ void block_chunk(int64_t n, int64_t* c0, int64_t* c1) {
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  *c0 = (int64_t)blockIdx.x * chunk;
+  *c1 = *c0 + chunk < n ? *c0 + chunk : n;
+}
+
+// Light rows per bucket (kBlockHist: per block, into bcount).  Each thread
+// carries kPartItems rows at a time.
+template <int MODE>
 __global__ void __launch_bounds__(kPartThreads, 1) lp_hist_kernel(PartArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PackPlan K;
   const LearnedPlan lp = *a.lp;
-  const PartSmem S = part_carve(smem, 0);
-  part_setup<THR_SMEM>(a, lp, S, K);
-  const unsigned* thr = THR_SMEM ? S.thr : a.thr;
+  const PartSmem S = part_carve(smem, 0, lp.B);
+  if (MODE == kBlockHist)
+    for (int b = threadIdx.x; b < lp.B; b += kPartThreads) S.bh[b] = 0;
+  part_setup<MODE>(a, lp, S, K);
+  const unsigned* thr = MODE >= kThrShared ? S.thr : a.thr;
   const int nh = lp.nheavy;
   const int64_t n = clamp_n(a.n_max, a.d_n);
   constexpr int TILE = kPartThreads * kPartItems;
-  for (int64_t base = (int64_t)blockIdx.x * TILE; base < n; base += (int64_t)gridDim.x * TILE) {
+  int64_t c0 = (int64_t)blockIdx.x * TILE, c1 = n, step = (int64_t)gridDim.x * TILE;
+  if (MODE == kBlockHist) {
+    block_chunk(n, &c0, &c1);
+    step = TILE;
+  }
+  for (int64_t base = c0; base < c1; base += step) {
     unsigned long long p[kPartItems];
     bool v[kPartItems];
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k) {
       const int64_t i = base + k * kPartThreads + threadIdx.x;
-      v[k] = i < n;
+      v[k] = i < c1;
       p[k] = v[k] ? pack_row_plan(K, a.sel ? (int64_t)a.sel[i] : i) : 0ull;
     }
 #pragma unroll
-    for (int k = 0; k < kPartItems; ++k)
-      if (v[k] && (nh == 0 || heavy_lookup(S, p[k]) < 0)) atomicAdd(&a.count[lp_bucket<THR_SMEM>(p[k], lp, S.dir, thr)], 1u);
+    for (int k = 0; k < kPartItems; ++k) {
+      if (!v[k] || (nh && heavy_lookup(S, p[k]) >= 0)) continue;
+      const int b = lp_bucket<MODE >= kThrShared>(p[k], lp, S.dir, thr);
+      if (MODE == kBlockHist) atomicAdd(&S.bh[b], 1u);
+      else atomicAdd(&a.count[b], 1u);
+    }
+  }
+  if (MODE == kBlockHist) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < lp.B; b += kPartThreads) a.bcount[(size_t)blockIdx.x * lp.B + b] = S.bh[b];
+  }
+}
+
+// kBlockHist: bucket totals over the blocks' counts.
+__global__ void lp_bcols_kernel(const unsigned* bcount, int nblk, const LearnedPlan* lp, unsigned* count) {
+  const int B = lp->B;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  unsigned t = 0;
+  for (int k = 0; k < nblk; ++k) t += bcount[(size_t)k * B + b];
+  count[b] = t;
+}
+
+// kBlockHist: each block's start in every bucket (in place), after the
+// bucket offsets.
+__global__ void lp_bstarts_kernel(unsigned* bcount, int nblk, const LearnedPlan* lp, const unsigned* off) {
+  const int B = lp->B;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  unsigned run = off[b];
+  for (int k = 0; k < nblk; ++k) {
+    const unsigned c = bcount[(size_t)k * B + b];
+    bcount[(size_t)k * B + b] = run;
+    run += c;
   }
 }
 
@@ -695,20 +755,27 @@ __device__ __forceinline__ void fold_shared(long long* slot, int op, long long x
 // per-block shared accumulators (rows of one heavy key within a warp
 // combined first), flushed with atomics at the end.  The trip count is
 // uniform over the block, so every lane reaches each warp collective.
-template <bool THR_SMEM>
+template <int MODE>
 __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a, AggProgram P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PackPlan K;
   const LearnedPlan lp = *a.lp;
-  const PartSmem S = part_carve(smem, P.naggs);
+  const PartSmem S = part_carve(smem, P.naggs, lp.B);
   const int nh = lp.nheavy;
   for (int i = threadIdx.x; i < nh * P.naggs; i += blockDim.x) S.acc[i] = agg_identity(P.op[i % P.naggs]);
-  part_setup<THR_SMEM>(a, lp, S, K);
-  const unsigned* thr = THR_SMEM ? S.thr : a.thr;
+  if (MODE == kBlockHist)  // this block's cursor in every bucket
+    for (int b = threadIdx.x; b < lp.B; b += kPartThreads) S.bh[b] = a.bcount[(size_t)blockIdx.x * lp.B + b];
+  part_setup<MODE>(a, lp, S, K);
+  const unsigned* thr = MODE >= kThrShared ? S.thr : a.thr;
   const int64_t n = clamp_n(a.n_max, a.d_n);
   const int lane = threadIdx.x & 31;
   constexpr int TILE = kPartThreads * kPartItems;
-  for (int64_t base = (int64_t)blockIdx.x * TILE; base < n; base += (int64_t)gridDim.x * TILE) {
+  int64_t c0 = (int64_t)blockIdx.x * TILE, c1 = n, step = (int64_t)gridDim.x * TILE;
+  if (MODE == kBlockHist) {
+    block_chunk(n, &c0, &c1);
+    step = TILE;
+  }
+  for (int64_t base = c0; base < c1; base += step) {
     unsigned long long p[kPartItems];
     int64_t row[kPartItems];
     int h[kPartItems];
@@ -718,7 +785,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
       row[k] = 0;
       p[k] = 0;
       h[k] = -2;  // past the end
-      if (i < n) {
+      if (i < c1) {
         row[k] = a.sel ? (int64_t)a.sel[i] : i;
         p[k] = pack_row_plan(K, row[k]);
         h[k] = nh ? heavy_lookup(S, p[k]) : -1;
@@ -727,8 +794,11 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
     // light rows: bucket, cursor, store
     unsigned pos[kPartItems];
 #pragma unroll
-    for (int k = 0; k < kPartItems; ++k)
-      if (h[k] == -1) pos[k] = atomicAdd(&a.cursor[lp_bucket<THR_SMEM>(p[k], lp, S.dir, thr)], 1u);
+    for (int k = 0; k < kPartItems; ++k) {
+      if (h[k] != -1) continue;
+      const int b = lp_bucket<MODE >= kThrShared>(p[k], lp, S.dir, thr);
+      pos[k] = MODE == kBlockHist ? atomicAdd(&S.bh[b], 1u) : atomicAdd(&a.cursor[b], 1u);
+    }
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k)
       if (h[k] == -1) {

@@ -1138,6 +1138,8 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   int* dir = c.take<int>((1 << kDirBits) + 1);
   unsigned* count = c.take<unsigned>((size_t)B);
   unsigned* cursor = c.take<unsigned>((size_t)B);
+  const int nblk = num_sms();
+  unsigned* bcount = c.take<unsigned>(B <= kBlockHistMaxB ? (size_t)nblk * B : 1);
   unsigned* off = c.take<unsigned>((size_t)B + 1);
   int64_t* light_n = c.take<int64_t>(1);
   unsigned long long* lpk = c.take<unsigned long long>(nn);
@@ -1216,21 +1218,37 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   pa.out_p = lpk;
   pa.out_row = lrow;
   pa.heavy_acc = heavy_acc;
+  pa.bcount = bcount;
   TQP_CUDA(cudaMemsetAsync(count, 0, (size_t)B * sizeof(unsigned), s));
   {
-    // the steps live in shared memory when the scatter's layout still fits
-    const bool thr_smem = part_smem_bytes(B, naggs, true) <= (size_t)kMaxSmemOptin;
-    const size_t hsm = part_smem_bytes(B, 0, thr_smem), ssm = part_smem_bytes(B, naggs, thr_smem);
-    auto hk = thr_smem ? lp_hist_kernel<true> : lp_hist_kernel<false>;
-    auto sk = thr_smem ? lp_scatter_kernel<true> : lp_scatter_kernel<false>;
+    // the steps live in shared memory when the scatter's layout still fits;
+    // up to kBlockHistMaxB buckets, each block also keeps its own bucket
+    // counts and cursors there
+    const int mode = (B <= kBlockHistMaxB && part_smem_bytes(B, naggs, kBlockHist) <= (size_t)kMaxSmemOptin)
+                         ? kBlockHist
+                         : (part_smem_bytes(B, naggs, kThrShared) <= (size_t)kMaxSmemOptin ? kThrShared : kThrGlobal);
+    const size_t hsm = part_smem_bytes(B, 0, mode), ssm = part_smem_bytes(B, naggs, mode);
+    auto hk = mode == kBlockHist ? lp_hist_kernel<kBlockHist>
+                                 : (mode == kThrShared ? lp_hist_kernel<kThrShared> : lp_hist_kernel<kThrGlobal>);
+    auto sk = mode == kBlockHist ? lp_scatter_kernel<kBlockHist>
+                                 : (mode == kThrShared ? lp_scatter_kernel<kThrShared> : lp_scatter_kernel<kThrGlobal>);
     TQP_CUDA(cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
     TQP_CUDA(cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
     const int64_t ptiles = (n + kPartThreads * kPartItems - 1) / (kPartThreads * kPartItems);
-    hk<<<persistent_grid(hk, kPartThreads, hsm, ptiles), kPartThreads, hsm, s>>>(pa); note_launch();
+    // kBlockHist: both kernels on the same blocks (one per SM), each owning one chunk of rows
+    const int gh = mode == kBlockHist ? nblk : persistent_grid(hk, kPartThreads, hsm, ptiles);
+    const int gs = mode == kBlockHist ? nblk : persistent_grid(sk, kPartThreads, ssm, ptiles);
+    hk<<<gh, kPartThreads, hsm, s>>>(pa); note_launch();
+    if (mode == kBlockHist) {
+      lp_bcols_kernel<<<(B + 255) / 256, 256, 0, s>>>(bcount, nblk, lp, count); note_launch();
+    }
     lp_offsets_kernel<<<1, 1024, 0, s>>>(lp, count, off, cursor, d_stats, loss, epochs, light_n); note_launch();
+    if (mode == kBlockHist) {
+      lp_bstarts_kernel<<<(B + 255) / 256, 256, 0, s>>>(bcount, nblk, lp, off); note_launch();
+    }
     lp_heavy_init_kernel<<<(kMaxHeavy * naggs + 255) / 256, 256, 0, s>>>(lp, P, heavy_acc); note_launch();
     prof_mark(8, true, s);
-    sk<<<persistent_grid(sk, kPartThreads, ssm, ptiles), kPartThreads, ssm, s>>>(pa, P); note_launch();
+    sk<<<gs, kPartThreads, ssm, s>>>(pa, P); note_launch();
     prof_mark(8, false, s);
   }
   // 6. every bucket sorted: on-chip up to the capacity, else by one block in global memory

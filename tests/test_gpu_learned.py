@@ -115,7 +115,8 @@ def compare(got, want):
 
 
 @pytest.mark.parametrize("n", [1, 1000, 70_001, 3_000_000])
-@pytest.mark.parametrize("train,heavy,buckets", [(1, 1, 0), (0, 1, 0), (1, 0, 0), (1, 1, 2), (0, 0, 16), (1, 1, 1 << 17)])
+@pytest.mark.parametrize("train,heavy,buckets", [(1, 1, 0), (0, 1, 0), (1, 0, 0), (1, 1, 2), (0, 0, 16), (1, 1, 1 << 15),
+                                                (1, 1, 1 << 17)])
 def test_learned_groupby_parity(T, n, train, heavy, buckets):
     from paper_2209_04579_b300 import datagen_device as gd
     from paper_2209_04579_b300 import queries as Q
