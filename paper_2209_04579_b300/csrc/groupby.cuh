@@ -47,6 +47,7 @@ struct AggProgram {
   int nvals;
   const void* val[TQP_MAX_VALS];
   int vdt[TQP_MAX_VALS];
+  int simple;  // every aggregate is COUNT or one column read as is
 };
 
 // ---------------------------------------------------------------- aggregates
@@ -383,6 +384,26 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
   const int64_t n = a.plan->unsupported ? 0 : clamp_n(a.n_max, a.d_n);
   const K* keys = static_cast<const K*>(a.keys);
   const int32_t* rows = a.rows;  // null: the value columns are already in sorted order
+  // a simple program in registers: each aggregate's op and column
+  const bool simple = P.simple != 0;
+  int qop[NAGG], qdt[NAGG];
+  const void* qcol[NAGG];
+#pragma unroll
+  for (int q = 0; q < NAGG; ++q) {
+    qop[q] = q < P.naggs ? P.op[q] : TQP_COUNT;
+    const int c = (q < P.naggs && qop[q] != TQP_COUNT) ? P.tcol[P.expr[q]][0] : 0;
+    qcol[q] = P.nvals ? P.val[c] : nullptr;
+    qdt[q] = P.nvals ? P.vdt[c] : TQP_I64;
+  }
+  auto fold = [&](PT& acc, int64_t r) {
+    if (simple) {
+#pragma unroll
+      for (int q = 0; q < NAGG; ++q)
+        if (q < P.naggs) acc.v[q] = agg_fold(qop[q], acc.v[q], qop[q] == TQP_COUNT ? 1 : load_as_i64(qcol[q], qdt[q], r));
+    } else {
+      fold_row(acc, P, r);
+    }
+  };
 
   for (int64_t t = blockIdx.x; t < (int64_t)a.num_tiles; t += gridDim.x) {
     if (threadIdx.x == 0) s_carry_used = 0;
@@ -436,7 +457,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
             hl = hl_new;
           }
         }
-        fold_row(acc, P, rows ? rows[p] : p);
+        fold(acc, rows ? rows[p] : p);
         if (nh && p == n - 1) {
           // heavy keys above the last light key
           for (int i = hl; i < nh; ++i)

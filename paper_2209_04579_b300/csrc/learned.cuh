@@ -69,11 +69,43 @@ __global__ void cdf_forward_kernel(const tqp_cdf_model* gm, const float* x, int6
   }
 }
 
+struct AdamState {
+  float m[kNP];
+  float v[kNP];
+  unsigned done;  // blocks of the current gradient launch that have written their partials
+};
+
+__device__ __forceinline__ float* param_ptr(tqp_cdf_model* md, int k) {
+  return k < kH ? &md->w[k] : k < 2 * kH ? &md->b[k - kH] : k < 3 * kH ? &md->a[k - 2 * kH] : &md->c;
+}
+
+// One Adam step (parameter k < kNP) from the summed gradient g, then the
+// projection w, a >= 0.
+__device__ __forceinline__ void adam_update(tqp_cdf_model* md, AdamState* st, const tqp_train_cfg& cfg, int step,
+                                            int k, float g) {
+  const float t = (float)(step + 1);
+  float mk = cfg.beta1 * st->m[k] + (1.0f - cfg.beta1) * g;
+  float vk = cfg.beta2 * st->v[k] + (1.0f - cfg.beta2) * g * g;
+  st->m[k] = mk;
+  st->v[k] = vk;
+  float mh = mk / (1.0f - powf(cfg.beta1, t));
+  float vh = vk / (1.0f - powf(cfg.beta2, t));
+  float* p = param_ptr(md, k);
+  float np = *p - cfg.lr * mh / (sqrtf(vh) + cfg.eps);
+  bool nonneg = (k < kH) || (k >= 2 * kH && k < 3 * kH);
+  if (nonneg && np < 0.0f) np = 0.0f;
+  *p = np;
+}
+
 // ---------------------------------------------------------------- gradient
 // One block per chunk of kGradChunk samples writes its partial sums
 // [gw(H), gb(H), ga(H), gc, sum of squared residuals] to partial[block].
-__global__ void __launch_bounds__(256) cdf_grad_kernel(const tqp_cdf_model* gm, const float* x, const float* y,
-                                                       const int64_t* d_n, int64_t n_max, float* partial) {
+// With an Adam state, the block that finishes last sums the partials in block order (the same
+// result whatever the finishing order), takes one Adam step, records the
+// epoch's loss and re-arms the counter for the next launch.
+__global__ void __launch_bounds__(256) cdf_grad_kernel(tqp_cdf_model* gm, const float* x, const float* y,
+                                                       const int64_t* d_n, int64_t n_max, float* partial,
+                                                       AdamState* st, tqp_train_cfg cfg, int step, float* loss_out) {
   __shared__ tqp_cdf_model m;
   __shared__ float sx[kGradChunk], sd[kGradChunk];
   __shared__ float red[4][3 * kH];
@@ -139,6 +171,26 @@ __global__ void __launch_bounds__(256) cdf_grad_kernel(const tqp_cdf_model* gm, 
     for (int w = 0; w < 8; ++w) s += s_loss[w];
     out[kNP] = s;
   }
+  // ---- the last block to finish: the Adam step (st null: gradient only)
+  if (st == nullptr) return;
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&st->done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int k = threadIdx.x;
+  if (k < kGradLen) {
+    float g = 0.0f;
+    for (unsigned b = 0; b < gridDim.x; ++b) g += __ldcg(&partial[(size_t)b * kGradLen + k]);
+    if (k == kNP) {
+      if (loss_out) loss_out[step] = n > 0 ? g / (float)n : 0.0f;
+    } else {
+      adam_update(gm, st, cfg, step, k, g);
+    }
+  }
+  if (k == 0) st->done = 0;
 }
 
 // Sums the block partials in block order: grad[k] (k < kNP), grad[kNP] = loss.
@@ -150,41 +202,6 @@ __global__ void cdf_grad_finish_kernel(const float* partial, int nblocks, const 
   for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * kGradLen + k];
   const int64_t n = clamp_n(n_max, d_n);
   grad[k] = (k == kNP) ? (n > 0 ? s / (float)n : 0.0f) : s;
-}
-
-struct AdamState {
-  float m[kNP];
-  float v[kNP];
-};
-
-__device__ __forceinline__ float* param_ptr(tqp_cdf_model* md, int k) {
-  return k < kH ? &md->w[k] : k < 2 * kH ? &md->b[k - kH] : k < 3 * kH ? &md->a[k - 2 * kH] : &md->c;
-}
-
-// One Adam step from the block partials, then the projection w, a >= 0.
-__global__ void cdf_adam_kernel(tqp_cdf_model* md, const float* partial, int nblocks, const int64_t* d_n,
-                                int64_t n_max, AdamState* st, tqp_train_cfg cfg, int step, float* loss_out) {
-  int k = threadIdx.x;
-  if (k >= kGradLen) return;
-  float s = 0.0f;
-  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * kGradLen + k];
-  if (k == kNP) {
-    const int64_t n = clamp_n(n_max, d_n);
-    if (loss_out) loss_out[step] = n > 0 ? s / (float)n : 0.0f;
-    return;
-  }
-  const float t = (float)(step + 1);
-  float mk = cfg.beta1 * st->m[k] + (1.0f - cfg.beta1) * s;
-  float vk = cfg.beta2 * st->v[k] + (1.0f - cfg.beta2) * s * s;
-  st->m[k] = mk;
-  st->v[k] = vk;
-  float mh = mk / (1.0f - powf(cfg.beta1, t));
-  float vh = vk / (1.0f - powf(cfg.beta2, t));
-  float* p = param_ptr(md, k);
-  float np = *p - cfg.lr * mh / (sqrtf(vh) + cfg.eps);
-  bool nonneg = (k < kH) || (k >= 2 * kH && k < 3 * kH);
-  if (nonneg && np < 0.0f) np = 0.0f;
-  *p = np;
 }
 
 // ---------------------------------------------------------------- learned group-by plan
@@ -234,6 +251,7 @@ __global__ void lp_init_kernel(const GroupPlan* gp, int nkeys, tqp_cdf_model* md
   lp->nheavy = 0;
   lp->min_count = min_count;
   for (int k = 0; k < kNP; ++k) st->m[k] = st->v[k] = 0.0f;
+  st->done = 0;
 }
 
 __device__ __forceinline__ unsigned long long pack_row(const KeySet& ks, const GroupPlan* gp, int64_t row) {
@@ -254,51 +272,105 @@ __global__ void lp_sample_kernel(KeySet ks, const int32_t* sel, int64_t n_max, c
   sample[j] = n > 0 ? pack_row(ks, gp, row) : 0ull;
 }
 
-__device__ __forceinline__ int64_t lb_u64(const unsigned long long* a, int64_t n, unsigned long long x) {
-  int64_t lo = 0, len = n;
-  while (len > 0) {
-    int64_t h = len >> 1;
-    if (a[lo + h] < x) { lo += h + 1; len -= h + 1; } else { len = h; }
+// First index after the run of equal keys that holds i (sorted ascending),
+// by galloping forward from i: a run of length r costs O(log r) loads.
+__device__ __forceinline__ int run_end(const unsigned long long* a, int n, int i) {
+  const unsigned long long k = a[i];
+  int lo = i, step = 1;  // a[lo] == k
+  while (lo + step < n && a[lo + step] == k) {
+    lo += step;
+    step <<= 1;
   }
-  return lo;
-}
-__device__ __forceinline__ int64_t ub_u64(const unsigned long long* a, int64_t lo, int64_t n, unsigned long long x) {
-  int64_t len = n - lo;
-  while (len > 0) {
-    int64_t h = len >> 1;
-    if (!(x < a[lo + h])) { lo += h + 1; len -= h + 1; } else { len = h; }
+  int hi = lo + step < n ? lo + step : n;  // a[hi] != k or hi == n
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] == k) lo = mid; else hi = mid;
   }
-  return lo;
-}
-
-__device__ __forceinline__ bool in_sorted_list(const unsigned long long* a, int n, unsigned long long x) {
-  int lo = 0, len = n;
-  while (len > 0) {
-    int h = len >> 1;
-    if (a[lo + h] < x) { lo += h + 1; len -= h + 1; } else { len = h; }
-  }
-  return lo < n && a[lo] == x;
+  return hi;
 }
 
-// Light prefix of the sorted sample: lpre[i] = sample keys before i that are
-// not heavy, and their total.  One block of 1024 threads, contiguous chunks.
-__global__ void __launch_bounds__(1024) lp_light_prefix_kernel(const unsigned long long* sorted, int S,
-                                                               const unsigned long long* heavy, LearnedPlan* lp,
-                                                               int32_t* lpre) {
+// First index of the run that holds i, by galloping backward.
+__device__ __forceinline__ int run_begin(const unsigned long long* a, int i) {
+  const unsigned long long k = a[i];
+  int hi = i, step = 1;  // a[hi] == k
+  while (hi - step >= 0 && a[hi - step] == k) {
+    hi -= step;
+    step <<= 1;
+  }
+  int lo = hi - step >= 0 ? hi - step : -1;  // a[lo] != k or lo == -1
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] == k) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+// Heavy keys of the sorted sample and the light prefix, one block of 1024
+// threads, each owning a contiguous chunk of the sample.
+//  - heavy: distinct keys whose count reaches min_count; if more than
+//    kMaxHeavy qualify, the count cut is raised until they fit; written in
+//    ascending order (none when want_heavy is 0);
+//  - lpre[i]: sample keys before i that are not heavy; lp->slight the total.
+__global__ void __launch_bounds__(1024) lp_heavy_kernel(const unsigned long long* sorted, int S, int want_heavy,
+                                                         LearnedPlan* lp, unsigned long long* heavy, int32_t* lpre) {
+  __shared__ int hist[4096];
   __shared__ int s_scan[33];
-  const int nh = lp->nheavy;
+  __shared__ int s_cut;
+  for (int i = threadIdx.x; i < 4096; i += 1024) hist[i] = 0;
+  __syncthreads();
+  const int minc = lp->min_count;
   const int per = (S + 1023) / 1024;
-  const int i0 = threadIdx.x * per;
+  const int i0 = threadIdx.x * per < S ? threadIdx.x * per : S;
   const int i1 = i0 + per < S ? i0 + per : S;
-  int cnt = 0;
-  for (int i = i0; i < i1; ++i) cnt += !(nh && in_sorted_list(heavy, nh, sorted[i]));
-  int total;
-  int run = block_exclusive_sum<1024>(cnt, s_scan, &total);
-  for (int i = i0; i < i1; ++i) {
-    lpre[i] = run;
-    run += !(nh && in_sorted_list(heavy, nh, sorted[i]));
+  // 1. counts of the runs that start in the chunk
+  if (want_heavy)
+    for (int i = i0; i < i1;) {
+      const int e = run_end(sorted, S, i);
+      if (i == 0 || sorted[i - 1] != sorted[i]) {
+        const int c = e - i;
+        if (c >= minc) atomicAdd(&hist[c < 4095 ? c : 4095], 1);
+      }
+      i = e;
+    }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0, cut = 1 << 30;
+    if (want_heavy)
+      for (int c = 4095; c >= minc && c >= 1; --c) {
+        if (acc + hist[c] > kMaxHeavy) break;
+        acc += hist[c];
+        cut = c;
+      }
+    s_cut = cut;
   }
-  if (threadIdx.x == 0) lp->slight = total;
+  __syncthreads();
+  const int cut = s_cut;
+  // 2. the chunk's heavy keys and light samples
+  int nheavy = 0, nlight = 0;
+  for (int i = i0; i < i1;) {
+    const int b = run_begin(sorted, i), e = run_end(sorted, S, i);
+    const int ce = e < i1 ? e : i1;
+    if (e - b >= cut) nheavy += (b == i);
+    else nlight += ce - i;
+    i = ce;
+  }
+  int htot, ltot;
+  int hbase = block_exclusive_sum<1024>(nheavy, s_scan, &htot);
+  int lrun = block_exclusive_sum<1024>(nlight, s_scan, &ltot);
+  // 3. write them
+  for (int i = i0; i < i1;) {
+    const int b = run_begin(sorted, i), e = run_end(sorted, S, i);
+    const int ce = e < i1 ? e : i1;
+    const bool hv = e - b >= cut;
+    if (hv && b == i) heavy[hbase++] = sorted[i];
+    for (int j = i; j < ce; ++j) lpre[j] = hv ? lrun : lrun + (j - i);
+    if (!hv) lrun += ce - i;
+    i = ce;
+  }
+  if (threadIdx.x == 0) {
+    lp->nheavy = htot;
+    lp->slight = ltot;
+  }
 }
 
 // Training pairs from every mult-th key of the sorted sample (S keys):
@@ -308,64 +380,16 @@ __global__ void __launch_bounds__(1024) lp_light_prefix_kernel(const unsigned lo
 // key has no light count: its pair sits on the light CDF with zero width.
 // Without heavy keys this is (first rank + count / 2) / S.
 __global__ void lp_targets_kernel(const unsigned long long* sorted, int S, int mult, int S_train,
-                                  const LearnedPlan* lp, const unsigned long long* heavy, const int32_t* lpre,
-                                  float* x, float* y) {
+                                  const LearnedPlan* lp, const int32_t* lpre, float* x, float* y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= S_train) return;
-  const unsigned long long k = sorted[(int64_t)i * mult];
-  int64_t lo = lb_u64(sorted, S, k);
-  int64_t hi = ub_u64(sorted, lo, S, k);
-  const int nh = lp->nheavy;
-  const double light = (nh && in_sorted_list(heavy, nh, k)) ? 0.0 : (double)(hi - lo);
+  const int j = (int)((int64_t)i * mult);
+  const unsigned long long k = sorted[j];
+  const int lo = run_begin(sorted, j), hi = run_end(sorted, S, j);
+  const int light = (hi < S ? lpre[hi] : lp->slight) - lpre[lo];
   const double tot = lp->slight > 0 ? (double)lp->slight : 1.0;
-  y[i] = (float)(((double)lpre[lo] + 0.5 * light) / tot);
+  y[i] = (float)(((double)lpre[lo] + 0.5 * (double)light) / tot);
   x[i] = (float)(k >> lp->shift) * lp->inv;
-}
-
-// Heavy keys: distinct sample keys whose count reaches min_count; if more
-// than kMaxHeavy qualify, the count cut is raised until they fit.  Written
-// in ascending key order.  One block of 1024 threads.
-__global__ void __launch_bounds__(1024) lp_heavy_kernel(const unsigned long long* sorted, int S, LearnedPlan* lp,
-                                                         unsigned long long* heavy) {
-  __shared__ int hist[4096];
-  __shared__ int s_scan[33];
-  __shared__ int s_cut, s_base;
-  for (int i = threadIdx.x; i < 4096; i += 1024) hist[i] = 0;
-  __syncthreads();
-  const int minc = lp->min_count;
-  for (int i = threadIdx.x; i < S; i += 1024) {
-    if (i > 0 && sorted[i] == sorted[i - 1]) continue;
-    int c = (int)(ub_u64(sorted, i, S, sorted[i]) - i);
-    if (c >= minc) atomicAdd(&hist[c < 4095 ? c : 4095], 1);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0, cut = 4096;
-    for (int c = 4095; c >= minc && c >= 1; --c) {
-      if (acc + hist[c] > kMaxHeavy) break;
-      acc += hist[c];
-      cut = c;
-    }
-    s_cut = cut;
-    s_base = 0;
-  }
-  __syncthreads();
-  const int cut = s_cut;
-  for (int base = 0; base < S; base += 1024) {
-    int i = base + threadIdx.x;
-    int flag = 0;
-    if (i < S && (i == 0 || sorted[i] != sorted[i - 1])) {
-      int c = (int)(ub_u64(sorted, i, S, sorted[i]) - i);
-      flag = (c >= cut);
-    }
-    int total;
-    int off = block_exclusive_sum<1024>(flag, s_scan, &total);
-    if (flag) heavy[s_base + off] = sorted[i];
-    __syncthreads();
-    if (threadIdx.x == 0) s_base += total;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) lp->nheavy = s_base;
 }
 
 // Knots at the quantiles of the training targets: unit j ramps from the
@@ -397,9 +421,6 @@ __global__ void lp_quantile_init_kernel(const float* xs, const float* ys, int S,
   if (j == 0) md->c = 0.0f;
 }
 
-__global__ void lp_no_heavy_kernel(LearnedPlan* lp) {
-  if (threadIdx.x == 0) lp->nheavy = 0;
-}
 
 // Step positions of the bucket function: thr[b-1] = min{q : bucket(q) >= b}
 // (qmax + 1 if none), b = 1..B-1.
@@ -463,7 +484,7 @@ struct PartArgs {
   const unsigned long long* heavy;
   unsigned* count;          // [B]
   unsigned* cursor;         // [B]
-  unsigned* bcount;         // kBlockHist: [blocks][B] counts, then each block's start in every bucket
+  unsigned* bcount;         // kBlockHist: [blocks][B] counts
   unsigned long long* out_p;
   int32_t* out_row;
   long long* heavy_acc;     // [nheavy][naggs]
@@ -476,15 +497,14 @@ constexpr int kPartThreads = 1024;
 constexpr int kPartItems = 4;
 
 // Partition modes: the bucket function's steps in global memory, in shared
-// memory, or in shared memory with per-block bucket counts and cursors (each
-// block partitions one contiguous chunk of rows into per-block ranges of
-// every bucket, so row positions come from shared-memory cursors).
+// memory, or (counting only) in shared memory with per-block bucket counts:
+// each block counts one contiguous chunk of rows in shared memory.
 constexpr int kThrGlobal = 0, kThrShared = 1, kBlockHist = 2;
 constexpr int kBlockHistMaxB = 1 << 14;
 
 // Dynamic shared memory: directory, heavy-key table (key, index; index -1 =
 // empty), the heavy accumulators (scatter), the steps (kThrShared and up)
-// and the block's bucket counts or cursors (kBlockHist).
+// and the block's bucket counts (kBlockHist).
 struct PartSmem {
   int* dir;
   unsigned long long* hk;
@@ -638,20 +658,6 @@ __global__ void lp_bcols_kernel(const unsigned* bcount, int nblk, const LearnedP
   count[b] = t;
 }
 
-// kBlockHist: each block's start in every bucket (in place), after the
-// bucket offsets.
-__global__ void lp_bstarts_kernel(unsigned* bcount, int nblk, const LearnedPlan* lp, const unsigned* off) {
-  const int B = lp->B;
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
-  unsigned run = off[b];
-  for (int k = 0; k < nblk; ++k) {
-    const unsigned c = bcount[(size_t)k * B + b];
-    bcount[(size_t)k * B + b] = run;
-    run += c;
-  }
-}
-
 // Exclusive scan of the bucket counts into offsets (and cursors), the
 // light-row total, and statistics.  One block of 1024 threads.
 __global__ void __launch_bounds__(1024) lp_offsets_kernel(const LearnedPlan* lp, const unsigned* count, unsigned* off,
@@ -755,7 +761,7 @@ __device__ __forceinline__ void fold_shared(long long* slot, int op, long long x
 // per-block shared accumulators (rows of one heavy key within a warp
 // combined first), flushed with atomics at the end.  The trip count is
 // uniform over the block, so every lane reaches each warp collective.
-template <int MODE>
+template <int MODE>  // kThrGlobal or kThrShared
 __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a, AggProgram P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PackPlan K;
@@ -763,19 +769,13 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
   const PartSmem S = part_carve(smem, P.naggs, lp.B);
   const int nh = lp.nheavy;
   for (int i = threadIdx.x; i < nh * P.naggs; i += blockDim.x) S.acc[i] = agg_identity(P.op[i % P.naggs]);
-  if (MODE == kBlockHist)  // this block's cursor in every bucket
-    for (int b = threadIdx.x; b < lp.B; b += kPartThreads) S.bh[b] = a.bcount[(size_t)blockIdx.x * lp.B + b];
   part_setup<MODE>(a, lp, S, K);
   const unsigned* thr = MODE >= kThrShared ? S.thr : a.thr;
   const int64_t n = clamp_n(a.n_max, a.d_n);
   const int lane = threadIdx.x & 31;
   constexpr int TILE = kPartThreads * kPartItems;
-  int64_t c0 = (int64_t)blockIdx.x * TILE, c1 = n, step = (int64_t)gridDim.x * TILE;
-  if (MODE == kBlockHist) {
-    block_chunk(n, &c0, &c1);
-    step = TILE;
-  }
-  for (int64_t base = c0; base < c1; base += step) {
+  const int64_t c1 = n;
+  for (int64_t base = (int64_t)blockIdx.x * TILE; base < n; base += (int64_t)gridDim.x * TILE) {
     unsigned long long p[kPartItems];
     int64_t row[kPartItems];
     int h[kPartItems];
@@ -797,7 +797,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
     for (int k = 0; k < kPartItems; ++k) {
       if (h[k] != -1) continue;
       const int b = lp_bucket<MODE >= kThrShared>(p[k], lp, S.dir, thr);
-      pos[k] = MODE == kBlockHist ? atomicAdd(&S.bh[b], 1u) : atomicAdd(&a.cursor[b], 1u);
+      pos[k] = atomicAdd(&a.cursor[b], 1u);
     }
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k)

@@ -314,6 +314,13 @@ tqp_status build_agg_program(const tqp_col* vals, int nvals, const tqp_expr* exp
     P->op[a] = aggs[a].op;
     P->expr[a] = aggs[a].op == TQP_COUNT ? -1 : aggs[a].expr;
   }
+  // every aggregate a plain column (one term, x * 1 + 0) or COUNT
+  P->simple = 1;
+  for (int a = 0; a < naggs; ++a) {
+    if (aggs[a].op == TQP_COUNT) continue;
+    const tqp_expr& e = exprs[aggs[a].expr];
+    if (e.nterms != 1 || e.term[0].mul != 1 || e.term[0].add != 0) P->simple = 0;
+  }
   return TQP_OK;
 }
 
@@ -1042,7 +1049,9 @@ tqp_status tqp_cdf_backward(const tqp_cdf_model* d_model, const float* d_x, cons
   if (!d_model || !d_grad || (n > 0 && (!d_x || !d_y))) return TQP_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (nb > 0) {
-    cdf_grad_kernel<<<nb, 256, 0, s>>>(d_model, d_x, d_y, nullptr, n, partial); note_launch();
+    // gradient only: without an Adam state the model is not written
+    cdf_grad_kernel<<<nb, 256, 0, s>>>(const_cast<tqp_cdf_model*>(d_model), d_x, d_y, nullptr, n, partial, nullptr,
+                                       tqp_train_cfg{}, 0, nullptr); note_launch();
   }
   cdf_grad_finish_kernel<<<1, 256, 0, s>>>(partial, nb, nullptr, n, d_grad); note_launch();
   return last_launch();
@@ -1058,8 +1067,7 @@ void launch_training(tqp_cdf_model* model, const float* x, const float* y, int64
                      const tqp_train_cfg& cfg, float* partial, AdamState* st, float* loss, cudaStream_t s) {
   const int nb = (int)((n + kGradChunk - 1) / kGradChunk);
   for (int e = 0; e < cfg.epochs; ++e) {
-    cdf_grad_kernel<<<nb, 256, 0, s>>>(model, x, y, d_n, n, partial); note_launch();
-    cdf_adam_kernel<<<1, 256, 0, s>>>(model, partial, nb, d_n, n, st, cfg, e, loss); note_launch();
+    cdf_grad_kernel<<<nb, 256, 0, s>>>(model, x, y, d_n, n, partial, st, cfg, e, loss); note_launch();
   }
 }
 }  // namespace
@@ -1186,13 +1194,8 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   if (st != TQP_OK) return st;
   // 3. heavy keys; training pairs on the CDF of the light rows (the sort's
   // row ids are no longer needed: srows holds the light prefix)
-  if (cfg->heavy) {
-    lp_heavy_kernel<<<1, 1024, 0, s>>>(ssorted, SH, lp, heavy); note_launch();
-  } else {
-    lp_no_heavy_kernel<<<1, 32, 0, s>>>(lp); note_launch();
-  }
-  lp_light_prefix_kernel<<<1, 1024, 0, s>>>(ssorted, SH, heavy, lp, srows); note_launch();
-  lp_targets_kernel<<<(S + 255) / 256, 256, 0, s>>>(ssorted, SH, mult, S, lp, heavy, srows, tx, ty); note_launch();
+  lp_heavy_kernel<<<1, 1024, 0, s>>>(ssorted, SH, cfg->heavy ? 1 : 0, lp, heavy, srows); note_launch();
+  lp_targets_kernel<<<(S + 255) / 256, 256, 0, s>>>(ssorted, SH, mult, S, lp, srows, tx, ty); note_launch();
   if (cfg->init == 1) {
     lp_quantile_init_kernel<<<1, kH, 0, s>>>(tx, ty, S, lp, model); note_launch();
   }
@@ -1221,34 +1224,29 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   pa.bcount = bcount;
   TQP_CUDA(cudaMemsetAsync(count, 0, (size_t)B * sizeof(unsigned), s));
   {
-    // the steps live in shared memory when the scatter's layout still fits;
-    // up to kBlockHistMaxB buckets, each block also keeps its own bucket
-    // counts and cursors there
-    const int mode = (B <= kBlockHistMaxB && part_smem_bytes(B, naggs, kBlockHist) <= (size_t)kMaxSmemOptin)
-                         ? kBlockHist
-                         : (part_smem_bytes(B, naggs, kThrShared) <= (size_t)kMaxSmemOptin ? kThrShared : kThrGlobal);
-    const size_t hsm = part_smem_bytes(B, 0, mode), ssm = part_smem_bytes(B, naggs, mode);
-    auto hk = mode == kBlockHist ? lp_hist_kernel<kBlockHist>
-                                 : (mode == kThrShared ? lp_hist_kernel<kThrShared> : lp_hist_kernel<kThrGlobal>);
-    auto sk = mode == kBlockHist ? lp_scatter_kernel<kBlockHist>
-                                 : (mode == kThrShared ? lp_scatter_kernel<kThrShared> : lp_scatter_kernel<kThrGlobal>);
+    // the steps live in shared memory when the scatter's layout still fits.
+    // Counting: up to kBlockHistMaxB buckets each block counts one chunk of
+    // rows in shared memory (then the column sums); placing: one global
+    // cursor per bucket, so each bucket fills as one stream
+    const int smode = part_smem_bytes(B, naggs, kThrShared) <= (size_t)kMaxSmemOptin ? kThrShared : kThrGlobal;
+    const int hmode = (B <= kBlockHistMaxB && part_smem_bytes(B, 0, kBlockHist) <= (size_t)kMaxSmemOptin) ? kBlockHist
+                                                                                                       : smode;
+    const size_t hsm = part_smem_bytes(B, 0, hmode), ssm = part_smem_bytes(B, naggs, smode);
+    auto hk = hmode == kBlockHist ? lp_hist_kernel<kBlockHist>
+                                  : (hmode == kThrShared ? lp_hist_kernel<kThrShared> : lp_hist_kernel<kThrGlobal>);
+    auto sk = smode == kThrShared ? lp_scatter_kernel<kThrShared> : lp_scatter_kernel<kThrGlobal>;
     TQP_CUDA(cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
     TQP_CUDA(cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
     const int64_t ptiles = (n + kPartThreads * kPartItems - 1) / (kPartThreads * kPartItems);
-    // kBlockHist: both kernels on the same blocks (one per SM), each owning one chunk of rows
-    const int gh = mode == kBlockHist ? nblk : persistent_grid(hk, kPartThreads, hsm, ptiles);
-    const int gs = mode == kBlockHist ? nblk : persistent_grid(sk, kPartThreads, ssm, ptiles);
+    const int gh = hmode == kBlockHist ? nblk : persistent_grid(hk, kPartThreads, hsm, ptiles);
     hk<<<gh, kPartThreads, hsm, s>>>(pa); note_launch();
-    if (mode == kBlockHist) {
+    if (hmode == kBlockHist) {
       lp_bcols_kernel<<<(B + 255) / 256, 256, 0, s>>>(bcount, nblk, lp, count); note_launch();
     }
     lp_offsets_kernel<<<1, 1024, 0, s>>>(lp, count, off, cursor, d_stats, loss, epochs, light_n); note_launch();
-    if (mode == kBlockHist) {
-      lp_bstarts_kernel<<<(B + 255) / 256, 256, 0, s>>>(bcount, nblk, lp, off); note_launch();
-    }
     lp_heavy_init_kernel<<<(kMaxHeavy * naggs + 255) / 256, 256, 0, s>>>(lp, P, heavy_acc); note_launch();
     prof_mark(8, true, s);
-    sk<<<gs, kPartThreads, ssm, s>>>(pa, P); note_launch();
+    sk<<<persistent_grid(sk, kPartThreads, ssm, ptiles), kPartThreads, ssm, s>>>(pa, P); note_launch();
     prof_mark(8, false, s);
   }
   // 6. every bucket sorted: on-chip up to the capacity, else by one block in global memory
