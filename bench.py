@@ -158,7 +158,7 @@ class Skew:
     @staticmethod
     def cfg(buckets):
         from paper_2209_04579_b300 import tqp
-        return tqp.learned_cfg(sample=65536, buckets=buckets, tcfg=tqp.train_cfg(epochs=100, lr=1e-4))
+        return tqp.learned_cfg(sample=65536, buckets=buckets, tcfg=tqp.train_cfg(epochs=40, lr=1e-4))
 
     def tune(self):
         """Bucket count from the autotuner (outputs sized to the group count)."""

@@ -214,6 +214,7 @@ struct LearnedPlan {
   int nheavy;
   int min_count;
   int slight;           // sample keys that are not heavy
+  int heavy_cut;        // sample count from which a key is heavy
 };
 
 // Identity CDF F(x) = x on [0, 1]: unit j ramps over [j/H, (j+1)/H].
@@ -305,59 +306,100 @@ __device__ __forceinline__ int run_begin(const unsigned long long* a, int i) {
   return hi;
 }
 
-// Heavy keys of the sorted sample and the light prefix, one block of 1024
-// threads, each owning a contiguous chunk of the sample.
-//  - heavy: distinct keys whose count reaches min_count; if more than
-//    kMaxHeavy qualify, the count cut is raised until they fit; written in
-//    ascending order (none when want_heavy is 0);
-//  - lpre[i]: sample keys before i that are not heavy; lp->slight the total.
-__global__ void __launch_bounds__(1024) lp_heavy_kernel(const unsigned long long* sorted, int S, int want_heavy,
-                                                         LearnedPlan* lp, unsigned long long* heavy, int32_t* lpre) {
-  __shared__ int hist[4096];
-  __shared__ int s_scan[33];
-  __shared__ int s_cut;
-  for (int i = threadIdx.x; i < 4096; i += 1024) hist[i] = 0;
-  __syncthreads();
+// Heavy keys of the sorted sample and the light prefix, over chunks of
+// kHeavyChunk consecutive samples (one thread each), in five launches:
+//  - lp_runhist_kernel: counts of the runs of equal keys that start in each
+//    chunk, as a histogram (counts >= min_count);
+//  - lp_cut_kernel: the count cut: the smallest count >= min_count such
+//    that at most kMaxHeavy keys reach it (none when want_heavy is 0);
+//  - lp_chunk_kernel: per chunk, the heavy runs that start in it and its
+//    light samples;
+//  - lp_chunk_scan_kernel: exclusive scans of both, the totals (nheavy,
+//    slight);
+//  - lp_heavy_write_kernel: heavy keys in ascending order, and lpre[i] =
+//    sample keys before i that are not heavy.
+constexpr int kHeavyChunk = 16;
+constexpr int kCutBins = 4096;
+
+__global__ void lp_runhist_kernel(const unsigned long long* sorted, int S, const LearnedPlan* lp, int* hist) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i0 = t * kHeavyChunk, i1 = i0 + kHeavyChunk < S ? i0 + kHeavyChunk : S;
   const int minc = lp->min_count;
-  const int per = (S + 1023) / 1024;
-  const int i0 = threadIdx.x * per < S ? threadIdx.x * per : S;
-  const int i1 = i0 + per < S ? i0 + per : S;
-  // 1. counts of the runs that start in the chunk
-  if (want_heavy)
-    for (int i = i0; i < i1;) {
-      const int e = run_end(sorted, S, i);
-      if (i == 0 || sorted[i - 1] != sorted[i]) {
-        const int c = e - i;
-        if (c >= minc) atomicAdd(&hist[c < 4095 ? c : 4095], 1);
-      }
-      i = e;
+  for (int i = i0; i < i1;) {
+    const int e = run_end(sorted, S, i);
+    if (i == 0 || sorted[i - 1] != sorted[i]) {
+      const int c = e - i;
+      if (c >= minc) atomicAdd(&hist[c < kCutBins - 1 ? c : kCutBins - 1], 1);
     }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0, cut = 1 << 30;
-    if (want_heavy)
-      for (int c = 4095; c >= minc && c >= 1; --c) {
-        if (acc + hist[c] > kMaxHeavy) break;
-        acc += hist[c];
-        cut = c;
-      }
-    s_cut = cut;
+    i = e;
   }
-  __syncthreads();
-  const int cut = s_cut;
-  // 2. the chunk's heavy keys and light samples
-  int nheavy = 0, nlight = 0;
+}
+
+__global__ void lp_cut_kernel(const int* hist, int want_heavy, LearnedPlan* lp) {
+  if (threadIdx.x != 0) return;
+  const int minc = lp->min_count;
+  int acc = 0, cut = 1 << 30;
+  if (want_heavy)
+    for (int c = kCutBins - 1; c >= minc && c >= 1; --c) {
+      if (acc + hist[c] > kMaxHeavy) break;
+      acc += hist[c];
+      cut = c;
+    }
+  lp->heavy_cut = cut;
+}
+
+__global__ void lp_chunk_kernel(const unsigned long long* sorted, int S, const LearnedPlan* lp, int* ch, int* cl) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i0 = t * kHeavyChunk;
+  if (i0 >= S) return;
+  const int i1 = i0 + kHeavyChunk < S ? i0 + kHeavyChunk : S;
+  const int cut = lp->heavy_cut;
+  int nh = 0, nl = 0;
   for (int i = i0; i < i1;) {
     const int b = run_begin(sorted, i), e = run_end(sorted, S, i);
     const int ce = e < i1 ? e : i1;
-    if (e - b >= cut) nheavy += (b == i);
-    else nlight += ce - i;
+    if (e - b >= cut) nh += (b == i);
+    else nl += ce - i;
     i = ce;
   }
+  ch[t] = nh;
+  cl[t] = nl;
+}
+
+// One block of 1024 threads over the chunk counts.
+__global__ void __launch_bounds__(1024) lp_chunk_scan_kernel(int nchunks, int* ch, int* cl, LearnedPlan* lp) {
+  __shared__ int s_scan[33];
+  const int per = (nchunks + 1023) / 1024;
+  const int c0 = threadIdx.x * per, c1 = c0 + per < nchunks ? c0 + per : nchunks;
+  int sh = 0, sl = 0;
+  for (int c = c0; c < c1; ++c) {
+    sh += ch[c];
+    sl += cl[c];
+  }
   int htot, ltot;
-  int hbase = block_exclusive_sum<1024>(nheavy, s_scan, &htot);
-  int lrun = block_exclusive_sum<1024>(nlight, s_scan, &ltot);
-  // 3. write them
+  int hrun = block_exclusive_sum<1024>(sh, s_scan, &htot);
+  int lrun = block_exclusive_sum<1024>(sl, s_scan, &ltot);
+  for (int c = c0; c < c1; ++c) {
+    const int h = ch[c], l = cl[c];
+    ch[c] = hrun;
+    cl[c] = lrun;
+    hrun += h;
+    lrun += l;
+  }
+  if (threadIdx.x == 0) {
+    lp->nheavy = htot;
+    lp->slight = ltot;
+  }
+}
+
+__global__ void lp_heavy_write_kernel(const unsigned long long* sorted, int S, const LearnedPlan* lp, const int* ch,
+                                      const int* cl, unsigned long long* heavy, int32_t* lpre) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i0 = t * kHeavyChunk;
+  if (i0 >= S) return;
+  const int i1 = i0 + kHeavyChunk < S ? i0 + kHeavyChunk : S;
+  const int cut = lp->heavy_cut;
+  int hbase = ch[t], lrun = cl[t];
   for (int i = i0; i < i1;) {
     const int b = run_begin(sorted, i), e = run_end(sorted, S, i);
     const int ce = e < i1 ? e : i1;
@@ -366,10 +408,6 @@ __global__ void __launch_bounds__(1024) lp_heavy_kernel(const unsigned long long
     for (int j = i; j < ce; ++j) lpre[j] = hv ? lrun : lrun + (j - i);
     if (!hv) lrun += ce - i;
     i = ce;
-  }
-  if (threadIdx.x == 0) {
-    lp->nheavy = htot;
-    lp->slight = ltot;
   }
 }
 

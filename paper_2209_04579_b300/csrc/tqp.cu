@@ -1132,6 +1132,9 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   unsigned long long* sample = c.take<unsigned long long>(SH);
   unsigned long long* ssorted = c.take<unsigned long long>(SH);
   int32_t* srows = c.take<int32_t>(SH);
+  int* cut_hist = c.take<int>(kCutBins);
+  int* chunk_h = c.take<int>((SH + kHeavyChunk - 1) / kHeavyChunk);
+  int* chunk_l = c.take<int>((SH + kHeavyChunk - 1) / kHeavyChunk);
   SortWs ssort = carve_sort(c, SH, 8, 8);
   float* tx = c.take<float>(S);
   float* ty = c.take<float>(S);
@@ -1194,7 +1197,17 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   if (st != TQP_OK) return st;
   // 3. heavy keys; training pairs on the CDF of the light rows (the sort's
   // row ids are no longer needed: srows holds the light prefix)
-  lp_heavy_kernel<<<1, 1024, 0, s>>>(ssorted, SH, cfg->heavy ? 1 : 0, lp, heavy, srows); note_launch();
+  {
+    const int nch = (SH + kHeavyChunk - 1) / kHeavyChunk, g = (nch + 255) / 256;
+    TQP_CUDA(cudaMemsetAsync(cut_hist, 0, kCutBins * sizeof(int), s));
+    if (cfg->heavy) {
+      lp_runhist_kernel<<<g, 256, 0, s>>>(ssorted, SH, lp, cut_hist); note_launch();
+    }
+    lp_cut_kernel<<<1, 32, 0, s>>>(cut_hist, cfg->heavy ? 1 : 0, lp); note_launch();
+    lp_chunk_kernel<<<g, 256, 0, s>>>(ssorted, SH, lp, chunk_h, chunk_l); note_launch();
+    lp_chunk_scan_kernel<<<1, 1024, 0, s>>>(nch, chunk_h, chunk_l, lp); note_launch();
+    lp_heavy_write_kernel<<<g, 256, 0, s>>>(ssorted, SH, lp, chunk_h, chunk_l, heavy, srows); note_launch();
+  }
   lp_targets_kernel<<<(S + 255) / 256, 256, 0, s>>>(ssorted, SH, mult, S, lp, srows, tx, ty); note_launch();
   if (cfg->init == 1) {
     lp_quantile_init_kernel<<<1, kH, 0, s>>>(tx, ty, S, lp, model); note_launch();
