@@ -787,18 +787,23 @@ __device__ __forceinline__ void fold_atomic(long long* slot, int op, long long x
 
 // The same fold into an accumulator in shared memory (SUM and COUNT through
 // the split 32-bit adds).
+// MIN / MAX read the current value first and take the atomic only when x
+// would change it: a hot key's extreme settles early, so most rows skip the
+// compare-and-swap loop (the atomic alone decides; the read only filters).
 __device__ __forceinline__ void fold_shared(long long* slot, int op, long long x) {
   switch (op) {
-    case TQP_MIN: atomicMin(slot, x); break;
-    case TQP_MAX: atomicMax(slot, x); break;
+    case TQP_MIN:
+      if (x < *reinterpret_cast<volatile long long*>(slot)) atomicMin(slot, x);
+      break;
+    case TQP_MAX:
+      if (x > *reinterpret_cast<volatile long long*>(slot)) atomicMax(slot, x);
+      break;
     default: shared_add_u64(reinterpret_cast<unsigned long long*>(slot), (unsigned long long)x); break;
   }
 }
 
 // Scatter of the light rows into their buckets; heavy rows folded into
-// per-block shared accumulators (rows of one heavy key within a warp
-// combined first), flushed with atomics at the end.  The trip count is
-// uniform over the block, so every lane reaches each warp collective.
+// per-block shared accumulators, flushed with atomics at the end.
 template <int MODE>  // kThrGlobal or kThrShared
 __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a, AggProgram P) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -810,7 +815,6 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
   part_setup<MODE>(a, lp, S, K);
   const unsigned* thr = MODE >= kThrShared ? S.thr : a.thr;
   const int64_t n = clamp_n(a.n_max, a.d_n);
-  const int lane = threadIdx.x & 31;
   constexpr int TILE = kPartThreads * kPartItems;
   const int64_t c1 = n;
   for (int64_t base = (int64_t)blockIdx.x * TILE; base < n; base += (int64_t)gridDim.x * TILE) {
@@ -843,22 +847,15 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
         a.out_p[pos[k]] = p[k];
         a.out_row[pos[k]] = (int32_t)row[k];
       }
-    // heavy rows: combined within the warp per key, one shared fold each
+    // heavy rows: folded into the block's accumulators
     if (nh) {
 #pragma unroll
       for (int k = 0; k < kPartItems; ++k) {
-        const unsigned peers = __match_any_sync(0xffffffffu, h[k]);
         if (h[k] < 0) continue;
-        const int leader = __ffs(peers) - 1;
+        long long* acc = &S.acc[h[k] * P.naggs];
         for (int q = 0; q < P.naggs; ++q) {
           const int op = P.op[q];
-          long long x = op == TQP_COUNT ? 1 : eval_expr(P, P.expr[q], row[k]);
-          long long acc = x;
-          for (unsigned others = peers & ~(1u << leader); others; others &= others - 1) {
-            long long y = __shfl_sync(peers, x, __ffs(others) - 1);
-            acc = agg_fold(op, acc, y);
-          }
-          if (lane == leader) fold_shared(&S.acc[h[k] * P.naggs + q], op, acc);
+          fold_shared(&acc[q], op, op == TQP_COUNT ? 1 : eval_expr(P, P.expr[q], row[k]));
         }
       }
     }
