@@ -112,13 +112,29 @@ __global__ void __launch_bounds__(THREADS) filter_kernel(FilterArgs a) {
   }
 }
 
-// out[j] = col[idx[j]]
+// out[j] = col[idx[j]]; eight rows per thread with their reads in flight together
 template <typename T>
 __global__ void gather_kernel(const T* __restrict__ col, const int32_t* __restrict__ idx, int64_t n_max,
                               const int64_t* d_n, T* __restrict__ out) {
+  constexpr int ITEMS = 8;
   const int64_t n = clamp_n(n_max, d_n);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) out[j] = col[idx[j]];
+  const int64_t tile = (int64_t)blockDim.x * ITEMS;
+  for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
+    int32_t ix[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const int64_t j = base + (int64_t)k * blockDim.x + threadIdx.x;
+      ix[k] = j < n ? __ldg(idx + j) : -1;
+    }
+    T v[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) v[k] = ix[k] >= 0 ? __ldg(col + ix[k]) : (T)0;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const int64_t j = base + (int64_t)k * blockDim.x + threadIdx.x;
+      if (j < n) out[j] = v[k];
+    }
+  }
 }
 
 }  // namespace tqp
