@@ -305,7 +305,11 @@ class Star:
                     "fact_rows": self.n}
         return {"workload": "star join: fact 600M rows (fk1 int32 into 20M dim1 keys, fk2 int64 into 150M dim2 keys, "
                             "m1..m3 int64 U[0,1e7], date int32 U[0,2556]) WHERE date<767 GROUP BY dim1.cat (int16 "
-                            "0..999), dim2.cat (int8 0..49); SUM(m1..m3), COUNT", "fact_rows": self.n}
+                            "0..999), dim2.cat (int8 0..49); SUM(m1..m3), COUNT; " +
+                            ("dimension keys sorted by the radix sort" if self.variant == "plain" else
+                             "dimension keys sorted through the learned range partitioner (network trained on the "
+                             "GPU inside every step); the radix-sorted form timed beside it"),
+                "fact_rows": self.n}
 
     def make_device(self):
         from paper_2209_04579_b300 import datagen_device as gd
@@ -314,7 +318,17 @@ class Star:
         self.d2 = gd.make_table(self.rec["dim2"], self.n2)
         return list(self.fact.values()) + list(self.d1.values()) + list(self.d2.values())
 
+    variant = "learned"
+
     def step(self):
+        from paper_2209_04579_b300 import queries as Q
+        from paper_2209_04579_b300 import tqp
+        if self.variant == "plain":
+            return Q.star(self.fact, self.d1, self.d2)
+        return Q.star(self.fact, self.d1, self.d2,
+                      learned=tqp.learned_cfg(sample=65536, tcfg=tqp.train_cfg(epochs=10, lr=1e-4)))
+
+    def plain_step(self):
         from paper_2209_04579_b300 import queries as Q
         return Q.star(self.fact, self.d1, self.d2)
 
@@ -764,7 +778,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="q14", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", default="", help="skew: 'plain' times the plain radix path as the step")
+    ap.add_argument("--variant", default="", help="skew, star: 'plain' times the plain radix path as the step")
     ap.add_argument("--scale", type=int, default=1, help="star: divide the table sizes (small profiling cases)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)

@@ -365,6 +365,24 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
                                    tqp_cdf_model* d_model_out, tqp_learned_stats* d_stats, void* ws,
                                    size_t* ws_bytes, tqp_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * tqp_star_agg_learned -- tqp_star_agg (same inputs, outputs, guarantees
+ * and results) whose dimensions of at least 2^20 passing-row candidates
+ * have their keys sorted through the learned range partitioner instead of
+ * the radix sort: a strided sample of the keys sorted, the network fit to
+ * its CDF (cfg: sample size, bucket count (0: about 4096 keys per bucket),
+ * training, knots; heavy keys do not apply to unique keys), every key
+ * placed in its bucket and every bucket sorted on chip.  The dimension keys
+ * must be unique among the passing rows, as for tqp_star_agg.
+ * ---------------------------------------------------------------------- */
+tqp_status tqp_star_agg_learned(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact,
+                                const tqp_pred* fact_preds, int nfact_preds, const int* fk_col,
+                                const tqp_dim* dims, int ndims, const tqp_valref* vals, int nvals,
+                                const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
+                                void* const* d_out_keys, int64_t* d_out_aggs, int64_t cap,
+                                int64_t* d_out_groups, const tqp_learned_cfg* cfg, void* ws,
+                                size_t* ws_bytes, tqp_stream_t stream);
+
 /* ========================================================================
  * Batched instances: many independent join + filter + group-by problems of
  * uneven size (the Q14 shape of Section 2.3, one query per problem) in one

@@ -512,7 +512,8 @@ __device__ __forceinline__ int lp_bucket(unsigned long long p, const LearnedPlan
 
 struct PartArgs {
   KeySet ks;
-  const int32_t* sel;
+  const int32_t* sel;       // keys at sel[i] (null: at i)
+  const int32_t* payload;   // row id written for key i (null: the key's row)
   int64_t n_max;
   const int64_t* d_n;
   const GroupPlan* gp;
@@ -845,7 +846,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
     for (int k = 0; k < kPartItems; ++k)
       if (h[k] == -1) {
         a.out_p[pos[k]] = p[k];
-        a.out_row[pos[k]] = (int32_t)row[k];
+        a.out_row[pos[k]] = a.payload ? a.payload[base + k * kPartThreads + threadIdx.x] : (int32_t)row[k];
       }
     // heavy rows: folded into the block's accumulators
     if (nh) {
@@ -866,6 +867,17 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
     int op = P.op[i % P.naggs];
     if (v != agg_identity(op)) fold_atomic(&a.heavy_acc[i], op, v);
   }
+}
+
+// Sorted packed keys back to the key column's dtype (one key column,
+// packed as key - kmin).
+__global__ void lp_decode_kernel(const unsigned long long* p, const GroupPlan* gp, int dt, int64_t n_max,
+                                 const int64_t* d_n, void* out) {
+  const int64_t n = clamp_n(n_max, d_n);
+  const unsigned long long kmin = (unsigned long long)gp->kmin[0];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    store_from_i64(out, dt, i, (long long)(p[i] + kmin));
 }
 
 // ---------------------------------------------------------------- bucket sort

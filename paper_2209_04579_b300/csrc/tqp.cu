@@ -375,40 +375,6 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
 
 
 // ---------------------------------------------------------------- star aggregate
-struct StarDimWs {
-  unsigned long long* fstatus;
-  uint32_t* fcounter;
-  int32_t* sel;
-  int64_t* cnt;
-  void* gkeys;
-  void* skeys;
-  int32_t* srows;
-  SortWs ksort;
-  // group ranks
-  GroupPlan* gplan;
-  void* packed;
-  int32_t* prow;
-  void* spacked;
-  int32_t* sprow;
-  SortWs gsort;
-  unsigned long long* rstatus;
-  uint32_t* rcounter;
-  int32_t* rank_of_row;
-  long long* gkey;
-  long long* G;
-  int32_t* rank_sorted;
-  void* kr;
-  long long* dval[TQP_MAX_VALS];
-  uint32_t ftiles, rtiles;
-  int gword;
-  // key directory
-  DimDir* dplan;
-  int* dir;
-  uint32_t* bitmap;
-  int log2cells;
-  int32_t* rank_cell;
-  long long* dval_cell[TQP_MAX_VALS];
-};
 
 constexpr int kFilterT = 256, kFilterI = 16;
 constexpr int kRankT = 256, kRankI = 8;
@@ -416,6 +382,8 @@ constexpr int kProbeT = 256, kProbeI = 8;
 constexpr int kSmemBitmapBytes = 184 * 1024;       // shared bitmap of the first dimension
 constexpr int kMaxSmemOptin = 227 * 1024;          // dynamic shared memory one block may opt in to
 constexpr int kHeavyMult = 4;                      // heavy-key sample / training set
+constexpr int64_t kLearnedSortMinRows = 1 << 20;   // star dimensions sorted by the learned partitioner from here
+constexpr int kLearnedSortRowsPerBucket = 4096;
 constexpr int64_t kSmemBitmapDimRows = 4'000'000;  // first dimensions up to this size try it
 constexpr int kCompactT = 256, kCompactI = 8;
 
@@ -658,11 +626,456 @@ tqp_status tqp_groupby_agg(const tqp_col* keys, int nkeys, const tqp_col* vals, 
                      d_out_groups, reinterpret_cast<cudaStream_t>(stream));
 }
 
-tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact, const tqp_pred* fact_preds,
-                        int nfact_preds, const int* fk_col, const tqp_dim* dims, int ndims, const tqp_valref* vals,
-                        int nvals, const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
-                        void* const* d_out_keys, int64_t* d_out_aggs, int64_t cap, int64_t* d_out_groups, void* ws,
-                        size_t* ws_bytes, tqp_stream_t stream) {
+
+
+// ---------------------------------------------------------------------------
+// Learned CDF model and the learned group-by.
+tqp_status tqp_cdf_forward(const tqp_cdf_model* d_model, const float* d_x, int64_t n, float* d_F, int32_t* d_bucket,
+                           int B, tqp_stream_t stream) {
+  if (n < 0 || n > INT_MAX || (d_bucket && (B < 1 || B > (1 << 24)))) return TQP_ERR_INVALID;
+  if (n == 0) return TQP_OK;
+  if (!d_model || !d_x || !d_F) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cdf_forward_kernel<<<stride_grid(n, 256), 256, 0, s>>>(d_model, d_x, n, d_F, d_bucket, B); note_launch();
+  return last_launch();
+}
+
+tqp_status tqp_cdf_backward(const tqp_cdf_model* d_model, const float* d_x, const float* d_y, int64_t n,
+                            float* d_grad, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || n < 0 || n > (1 << 20)) return TQP_ERR_INVALID;
+  const int nb = (int)((n + kGradChunk - 1) / kGradChunk);
+  Carver c(ws);
+  float* partial = c.take<float>((size_t)(nb > 0 ? nb : 1) * kGradLen);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (!d_model || !d_grad || (n > 0 && (!d_x || !d_y))) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (nb > 0) {
+    // gradient only: without an Adam state the model is not written
+    cdf_grad_kernel<<<nb, 256, 0, s>>>(const_cast<tqp_cdf_model*>(d_model), d_x, d_y, nullptr, n, partial, nullptr,
+                                       tqp_train_cfg{}, 0, nullptr); note_launch();
+  }
+  cdf_grad_finish_kernel<<<1, 256, 0, s>>>(partial, nb, nullptr, n, d_grad); note_launch();
+  return last_launch();
+}
+
+namespace {
+bool valid_train_cfg(const tqp_train_cfg* cfg) {
+  return cfg && cfg->epochs >= 0 && cfg->epochs <= 100000 && cfg->lr > 0 && cfg->beta1 >= 0 && cfg->beta1 < 1 &&
+         cfg->beta2 >= 0 && cfg->beta2 < 1 && cfg->eps > 0;
+}
+
+void launch_training(tqp_cdf_model* model, const float* x, const float* y, int64_t n, const int64_t* d_n,
+                     const tqp_train_cfg& cfg, float* partial, AdamState* st, float* loss, cudaStream_t s) {
+  const int nb = (int)((n + kGradChunk - 1) / kGradChunk);
+  for (int e = 0; e < cfg.epochs; ++e) {
+    cdf_grad_kernel<<<nb, 256, 0, s>>>(model, x, y, d_n, n, partial, st, cfg, e, loss); note_launch();
+  }
+}
+}  // namespace
+
+tqp_status tqp_cdf_train(const float* d_x, const float* d_y, int64_t n, tqp_cdf_model* d_model,
+                         const tqp_train_cfg* cfg, float* d_loss, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || n < 1 || n > (1 << 20) || !valid_train_cfg(cfg)) return TQP_ERR_INVALID;
+  const int nb = (int)((n + kGradChunk - 1) / kGradChunk);
+  Carver c(ws);
+  float* partial = c.take<float>((size_t)nb * kGradLen);
+  AdamState* st = c.take<AdamState>(1);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (!d_x || !d_y || !d_model) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  TQP_CUDA(cudaMemsetAsync(st, 0, sizeof(AdamState), s));
+  launch_training(d_model, d_x, d_y, n, nullptr, *cfg, partial, st, d_loss, s);
+  return last_launch();
+}
+
+namespace {
+// Workspace of the learned range partitioner (the partition and the bucket
+// sorts; the reduce arrays only for the group-by).
+struct LearnedWs {
+  int S, SH, mult, B, nblk, epochs;
+  int64_t rtiles;
+  GroupPlan* gp;
+  unsigned long long* sample;
+  unsigned long long* ssorted;
+  int32_t* srows;
+  int* cut_hist;
+  int* chunk_h;
+  int* chunk_l;
+  SortWs ssort;
+  float* tx;
+  float* ty;
+  tqp_cdf_model* model;
+  LearnedPlan* lp;
+  AdamState* adam;
+  float* partial;
+  float* loss;
+  unsigned long long* heavy;
+  long long* heavy_acc;
+  unsigned* thr;
+  int* dir;
+  unsigned* count;
+  unsigned* cursor;
+  unsigned* bcount;
+  unsigned* off;
+  int64_t* light_n;
+  unsigned long long* lpk;
+  int32_t* lrow;
+  unsigned long long* apk;
+  int32_t* arow;
+  uint32_t* queue;
+  uint32_t* big_flags;
+  uint32_t* rheads;
+  Partial* rcarry;
+  void* lgath[TQP_MAX_VALS];
+};
+
+// B: the bucket count (0 = from n, about rows_per_bucket rows each).
+LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int rows_per_bucket, int naggs,
+                        const AggProgram* P, int32_t* rows_out) {
+  LearnedWs w;
+  std::memset(&w, 0, sizeof(w));
+  w.S = cfg->sample;
+  w.B = cfg->buckets;
+  if (w.B == 0) {
+    w.B = 256;
+    while (w.B < (1 << 17) && (int64_t)w.B * rows_per_bucket < n) w.B <<= 1;
+  }
+  w.epochs = cfg->train ? cfg->train_cfg.epochs : 0;
+  // heavy keys are found in a sample kHeavyMult times larger than the
+  // training set (a key far beyond a bucket's capacity must not escape by
+  // sampling noise); the network trains on every kHeavyMult-th sorted key
+  w.SH = w.S * kHeavyMult <= (1 << 20) ? w.S * kHeavyMult : (1 << 20);
+  w.mult = w.SH / w.S;
+  w.nblk = num_sms();
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const int nb = w.S / kGradChunk;
+  const int B = w.B;
+  w.gp = c.take<GroupPlan>(1);
+  w.sample = c.take<unsigned long long>(w.SH);
+  w.ssorted = c.take<unsigned long long>(w.SH);
+  w.srows = c.take<int32_t>(w.SH);
+  w.cut_hist = c.take<int>(kCutBins);
+  w.chunk_h = c.take<int>((w.SH + kHeavyChunk - 1) / kHeavyChunk);
+  w.chunk_l = c.take<int>((w.SH + kHeavyChunk - 1) / kHeavyChunk);
+  w.ssort = carve_sort(c, w.SH, 8, 8);
+  w.tx = c.take<float>(w.S);
+  w.ty = c.take<float>(w.S);
+  w.model = c.take<tqp_cdf_model>(1);
+  w.lp = c.take<LearnedPlan>(1);
+  w.adam = c.take<AdamState>(1);
+  w.partial = c.take<float>((size_t)nb * kGradLen);
+  w.loss = c.take<float>((size_t)(w.epochs > 0 ? w.epochs : 1));
+  w.heavy = c.take<unsigned long long>(kMaxHeavy);
+  w.heavy_acc = c.take<long long>((size_t)kMaxHeavy * (naggs > 0 ? naggs : 1));
+  w.thr = c.take<unsigned>((size_t)B);
+  w.dir = c.take<int>((1 << kDirBits) + 1);
+  w.count = c.take<unsigned>((size_t)B);
+  w.cursor = c.take<unsigned>((size_t)B);
+  w.bcount = c.take<unsigned>(B <= kBlockHistMaxB ? (size_t)w.nblk * B : 1);
+  w.off = c.take<unsigned>((size_t)B + 1);
+  w.light_n = c.take<int64_t>(1);
+  w.lpk = c.take<unsigned long long>(nn);
+  w.lrow = rows_out ? rows_out : c.take<int32_t>(nn);
+  w.apk = c.take<unsigned long long>(nn);
+  w.arow = c.take<int32_t>(nn);
+  w.queue = c.take<uint32_t>(2);
+  w.big_flags = c.take<uint32_t>((size_t)B);
+  if (P) {  // the group-by's reduce
+    w.rtiles = (n + kReduceThreads * kReduceItems - 1) / (kReduceThreads * kReduceItems);
+    w.rheads = c.take<uint32_t>((size_t)(w.rtiles > 0 ? w.rtiles : 1));
+    w.rcarry = c.take<Partial>((size_t)(w.rtiles > 0 ? w.rtiles : 1));
+    if (n >= kPregatherRows)
+      for (int v = 0; v < P->nvals; ++v) w.lgath[v] = c.take<char>(nn * dtype_bytes(P->vdt[v]));
+  }
+  return w;
+}
+
+// The learned range partition of n packed keys and the sort of every
+// bucket: key range and packing; a strided sample sorted by the radix sort;
+// heavy keys (want_heavy) and the light-CDF training pairs; the network
+// (knots, training); its step positions and their directory; bucket counts,
+// offsets and the scatter (heavy rows folded into heavy_acc by P); every
+// bucket sorted.  Leaves the light rows' packed keys and row ids sorted in
+// (lpk, lrow), their count in light_n.
+tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int32_t* d_sel, const int32_t* payload,
+                                 int64_t n, const int64_t* d_n, const tqp_learned_cfg* cfg, bool want_heavy,
+                                 const AggProgram& P, tqp_learned_stats* d_stats, cudaStream_t s) {
+  const int S = w.S, SH = w.SH, B = w.B, naggs = P.naggs;
+  long long minc = (long long)((double)SH * kLocalCap / (2.0 * (double)(n > 0 ? n : 1))) + 1;
+  if (minc < 2) minc = 2;
+  if (minc > 4095) minc = 4095;
+  // 1. key range and packing (always a 64-bit packed word on this path)
+  gb_init_kernel<<<1, 32, 0, s>>>(w.gp); note_launch();
+  gb_keyrange_kernel<256><<<stride_grid(n, 256, 4), 256, 0, s>>>(ks, d_sel, n, d_n, w.gp); note_launch();
+  gb_plan_kernel<<<1, 32, 0, s>>>(w.gp, ks.nkeys, 64); note_launch();
+  lp_init_kernel<<<1, 32, 0, s>>>(w.gp, ks.nkeys, w.model, w.lp, w.adam, B, (int)minc); note_launch();
+  // 2. sample, sorted by the radix sort
+  lp_sample_kernel<<<(SH + 255) / 256, 256, 0, s>>>(ks, d_sel, n, d_n, w.gp, SH, w.sample); note_launch();
+  tqp_status st = run_sort(w.ssort, kKeyU64, w.sample, nullptr, w.ssorted, w.srows, SH, nullptr, 0, 64, s);
+  if (st != TQP_OK) return st;
+  // 3. heavy keys; training pairs on the CDF of the light rows (the sort's
+  // row ids are no longer needed: srows holds the light prefix)
+  {
+    const int nch = (SH + kHeavyChunk - 1) / kHeavyChunk, g = (nch + 255) / 256;
+    TQP_CUDA(cudaMemsetAsync(w.cut_hist, 0, kCutBins * sizeof(int), s));
+    if (want_heavy) {
+      lp_runhist_kernel<<<g, 256, 0, s>>>(w.ssorted, SH, w.lp, w.cut_hist); note_launch();
+    }
+    lp_cut_kernel<<<1, 32, 0, s>>>(w.cut_hist, want_heavy ? 1 : 0, w.lp); note_launch();
+    lp_chunk_kernel<<<g, 256, 0, s>>>(w.ssorted, SH, w.lp, w.chunk_h, w.chunk_l); note_launch();
+    lp_chunk_scan_kernel<<<1, 1024, 0, s>>>(nch, w.chunk_h, w.chunk_l, w.lp); note_launch();
+    lp_heavy_write_kernel<<<g, 256, 0, s>>>(w.ssorted, SH, w.lp, w.chunk_h, w.chunk_l, w.heavy, w.srows); note_launch();
+  }
+  lp_targets_kernel<<<(S + 255) / 256, 256, 0, s>>>(w.ssorted, SH, w.mult, S, w.lp, w.srows, w.tx, w.ty); note_launch();
+  if (cfg->init == 1) {
+    lp_quantile_init_kernel<<<1, kH, 0, s>>>(w.tx, w.ty, S, w.lp, w.model); note_launch();
+  }
+  // 4. training, then the step positions of the bucket function and their directory
+  if (w.epochs > 0) launch_training(w.model, w.tx, w.ty, S, nullptr, cfg->train_cfg, w.partial, w.adam, w.loss, s);
+  if (B > 1) {
+    lp_thresholds_kernel<<<(B - 1 + 255) / 256, 256, 0, s>>>(w.model, w.lp, w.thr); note_launch();
+  }
+  lp_directory_kernel<<<((1 << kDirBits) + 1 + 255) / 256, 256, 0, s>>>(w.lp, w.thr, w.dir); note_launch();
+  // 5. partition: bucket counts, offsets, scatter (heavy rows folded on the fly)
+  PartArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.ks = ks;
+  pa.sel = d_sel;
+  pa.payload = payload;
+  pa.n_max = n;
+  pa.d_n = d_n;
+  pa.gp = w.gp;
+  pa.lp = w.lp;
+  pa.thr = w.thr;
+  pa.dir = w.dir;
+  pa.heavy = w.heavy;
+  pa.count = w.count;
+  pa.cursor = w.cursor;
+  pa.out_p = w.lpk;
+  pa.out_row = w.lrow;
+  pa.heavy_acc = w.heavy_acc;
+  pa.bcount = w.bcount;
+  TQP_CUDA(cudaMemsetAsync(w.count, 0, (size_t)B * sizeof(unsigned), s));
+  {
+    // the steps live in shared memory when the scatter's layout still fits.
+    // Counting: up to kBlockHistMaxB buckets each block counts one chunk of
+    // rows in shared memory (then the column sums); placing: one global
+    // cursor per bucket, so each bucket fills as one stream
+    const int smode = part_smem_bytes(B, naggs, kThrShared) <= (size_t)kMaxSmemOptin ? kThrShared : kThrGlobal;
+    const int hmode = (B <= kBlockHistMaxB && part_smem_bytes(B, 0, kBlockHist) <= (size_t)kMaxSmemOptin) ? kBlockHist
+                                                                                                       : smode;
+    const size_t hsm = part_smem_bytes(B, 0, hmode), ssm = part_smem_bytes(B, naggs, smode);
+    auto hk = hmode == kBlockHist ? lp_hist_kernel<kBlockHist>
+                                  : (hmode == kThrShared ? lp_hist_kernel<kThrShared> : lp_hist_kernel<kThrGlobal>);
+    auto sk = smode == kThrShared ? lp_scatter_kernel<kThrShared> : lp_scatter_kernel<kThrGlobal>;
+    TQP_CUDA(cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+    TQP_CUDA(cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+    const int64_t ptiles = (n + kPartThreads * kPartItems - 1) / (kPartThreads * kPartItems);
+    const int gh = hmode == kBlockHist ? w.nblk : persistent_grid(hk, kPartThreads, hsm, ptiles);
+    hk<<<gh, kPartThreads, hsm, s>>>(pa); note_launch();
+    if (hmode == kBlockHist) {
+      lp_bcols_kernel<<<(B + 255) / 256, 256, 0, s>>>(w.bcount, w.nblk, w.lp, w.count); note_launch();
+    }
+    lp_offsets_kernel<<<1, 1024, 0, s>>>(w.lp, w.count, w.off, w.cursor, d_stats, w.loss, w.epochs, w.light_n);
+    note_launch();
+    if (naggs > 0) {
+      lp_heavy_init_kernel<<<(kMaxHeavy * naggs + 255) / 256, 256, 0, s>>>(w.lp, P, w.heavy_acc); note_launch();
+    }
+    prof_mark(8, true, s);
+    sk<<<persistent_grid(sk, kPartThreads, ssm, ptiles), kPartThreads, ssm, s>>>(pa, P); note_launch();
+    prof_mark(8, false, s);
+  }
+  // 6. every bucket sorted: on-chip up to the capacity, else by one block in global memory
+  {
+    BucketSortArgs ba;
+    ba.lp = w.lp;
+    ba.off = w.off;
+    ba.p = w.lpk;
+    ba.row = w.lrow;
+    ba.alt_p = w.apk;
+    ba.alt_row = w.arow;
+    ba.queue = w.queue;
+    ba.big_flags = w.big_flags;
+    size_t smem = (size_t)kLocalCap * (8 + 8 + 4 + 4) + (size_t)kLocalWarps * (kRadix + 1) * 4 + kRadix * 4;
+    size_t wsmem = (size_t)kWarpSortWarps * (2 * kWarpCap * 8 + (kRadix + 1) * 4);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(lp_bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(lp_bucket_sort_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+      attr = true;
+    }
+    TQP_CUDA(cudaMemsetAsync(w.queue, 0, 2 * sizeof(uint32_t), s));
+    TQP_CUDA(cudaMemsetAsync(w.big_flags, 0, (size_t)B * sizeof(uint32_t), s));
+    {
+      int gw = persistent_grid(lp_bucket_sort_warp_kernel, kWarpSortWarps * 32, wsmem,
+                               (B + kWarpSortWarps - 1) / kWarpSortWarps);
+      prof_mark(9, true, s);
+      lp_bucket_sort_warp_kernel<<<gw, kWarpSortWarps * 32, wsmem, s>>>(ba, w.queue + 1, w.big_flags); note_launch();
+      prof_mark(9, false, s);
+    }
+    int g = w.nblk;
+    if (g > B) g = B;
+    prof_mark(7, true, s);
+    lp_bucket_sort_kernel<<<g, kLocalThreads, smem, s>>>(ba); note_launch();
+    prof_mark(7, false, s);
+  }
+  return TQP_OK;
+}
+
+bool valid_learned_cfg(const tqp_learned_cfg* cfg) {
+  if (!cfg) return false;
+  const int S = cfg->sample;
+  if (S < 1024 || S > (1 << 20) || (S & (S - 1))) return false;
+  if (cfg->buckets < 0 || cfg->buckets == 1 || cfg->buckets > (1 << 17) || (cfg->buckets & (cfg->buckets - 1)))
+    return false;
+  if (cfg->train && !valid_train_cfg(&cfg->train_cfg)) return false;
+  return cfg->init == 0 || cfg->init == 1;
+}
+
+// Sort of n keys (one int32 / int64 column, distinct keys) with their row
+// ids (vals_in, null: the index) through the learned range partitioner
+// without heavy keys: keys_out in the key's dtype, rows in w.lrow.  Rows of
+// equal keys would come out in no particular order.
+tqp_status run_sort_learned(const LearnedWs& w, int key_dt, const void* keys_in, const int32_t* vals_in,
+                            void* keys_out, int64_t n, const int64_t* d_n, const tqp_learned_cfg* cfg,
+                            cudaStream_t s) {
+  if (n == 0) return TQP_OK;
+  KeySet ks;
+  std::memset(&ks, 0, sizeof(ks));
+  ks.nkeys = 1;
+  ks.col[0] = keys_in;
+  ks.dt[0] = key_dt;
+  AggProgram none;
+  std::memset(&none, 0, sizeof(none));
+  tqp_status st = run_learned_partition(w, ks, nullptr, vals_in, n, d_n, cfg, false, none, nullptr, s);
+  if (st != TQP_OK) return st;
+  lp_decode_kernel<<<stride_grid(n, 256), 256, 0, s>>>(w.lpk, w.gp, key_dt, n, w.light_n, keys_out); note_launch();
+  return TQP_OK;
+}
+}  // namespace
+
+tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col* vals, int nvals,
+                                   const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
+                                   const int32_t* d_sel, int64_t n, const int64_t* d_n, void* const* d_out_keys,
+                                   int64_t* d_out_aggs, int64_t cap, int64_t* d_out_groups,
+                                   const tqp_learned_cfg* cfg, tqp_cdf_model* d_model_out,
+                                   tqp_learned_stats* d_stats, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || !cfg || n < 0 || n >= (1ll << 30) || nkeys < 1 || nkeys > TQP_MAX_KEYS || !keys)
+    return TQP_ERR_INVALID;
+  if (!valid_learned_cfg(cfg)) return TQP_ERR_INVALID;
+  for (int k = 0; k < nkeys; ++k)
+    if (!valid_dtype(keys[k].dtype)) return TQP_ERR_DTYPE;
+  AggProgram P;
+  tqp_status st = build_agg_program(vals, nvals, exprs, nexprs, aggs, naggs, &P, n > 0);
+  if (st != TQP_OK) return st;
+  Carver c(ws);
+  // about 512 rows per bucket by default: most buckets fit one warp's sort
+  const LearnedWs w = carve_learned(c, n, cfg, 512, naggs, &P, nullptr);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (!d_out_groups || cap < 0 || (cap > 0 && (!d_out_aggs || !d_out_keys))) return TQP_ERR_INVALID;
+  KeySet ks;
+  std::memset(&ks, 0, sizeof(ks));
+  ks.nkeys = nkeys;
+  for (int k = 0; k < nkeys; ++k) {
+    if (n > 0 && !keys[k].data) return TQP_ERR_INVALID;
+    if (cap > 0 && !d_out_keys[k]) return TQP_ERR_INVALID;
+    ks.col[k] = keys[k].data;
+    ks.dt[k] = keys[k].dtype;
+    ks.out[k] = cap > 0 ? d_out_keys[k] : nullptr;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    TQP_CUDA(cudaMemsetAsync(d_out_groups, 0, sizeof(int64_t), s));
+    if (d_stats) TQP_CUDA(cudaMemsetAsync(d_stats, 0, sizeof(tqp_learned_stats), s));
+    return TQP_OK;
+  }
+  st = run_learned_partition(w, ks, d_sel, nullptr, n, d_n, cfg, cfg->heavy != 0, P, d_stats, s);
+  if (st != TQP_OK) return st;
+  // 7. reduce-by-key over the sorted light rows, merging the heavy keys
+  ReduceArgs r;
+  r.keys = w.lpk;
+  r.rows = w.lrow;
+  r.n_max = n;
+  r.d_n = w.light_n;
+  r.plan = w.gp;
+  r.ks = ks;
+  r.out_aggs = reinterpret_cast<long long*>(d_out_aggs);
+  r.cap = cap;
+  r.d_out_groups = d_out_groups;
+  r.tile_heads = w.rheads;
+  r.carry = w.rcarry;
+  r.num_tiles = (uint32_t)w.rtiles;
+  r.heavy = w.heavy;
+  r.d_nheavy = &w.lp->nheavy;
+  r.heavy_acc = w.heavy_acc;
+  AggProgram Pr = P;
+  if (w.lgath[0] || P.nvals == 0) {
+    if (P.nvals) Pr = pregather_values(P, const_cast<void* const*>(w.lgath), w.lrow, n, w.light_n, s);
+    r.rows = nullptr;
+  }
+  launch_reduce<unsigned long long>(r, Pr, (uint32_t)w.rtiles, s);
+  gb_heavy_only_kernel<<<(kMaxHeavy + 255) / 256, 256, 0, s>>>(r, naggs); note_launch();
+  if (d_model_out) TQP_CUDA(cudaMemcpyAsync(d_model_out, w.model, sizeof(tqp_cdf_model), cudaMemcpyDeviceToDevice, s));
+  return last_launch();
+}
+
+namespace {
+struct StarDimWs {
+  unsigned long long* fstatus;
+  uint32_t* fcounter;
+  int32_t* sel;
+  int64_t* cnt;
+  void* gkeys;
+  void* skeys;
+  int32_t* srows;
+  SortWs ksort;
+  bool learned;      // keys sorted through the learned range partitioner
+  LearnedWs lws;
+  // group ranks
+  GroupPlan* gplan;
+  void* packed;
+  int32_t* prow;
+  void* spacked;
+  int32_t* sprow;
+  SortWs gsort;
+  unsigned long long* rstatus;
+  uint32_t* rcounter;
+  int32_t* rank_of_row;
+  long long* gkey;
+  long long* G;
+  int32_t* rank_sorted;
+  void* kr;
+  long long* dval[TQP_MAX_VALS];
+  uint32_t ftiles, rtiles;
+  int gword;
+  // key directory
+  DimDir* dplan;
+  int* dir;
+  uint32_t* bitmap;
+  int log2cells;
+  int32_t* rank_cell;
+  long long* dval_cell[TQP_MAX_VALS];
+};
+
+// The fused star aggregate; lcfg (nullable) sorts every large dimension's
+// keys through the learned range partitioner instead of the radix sort.
+tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact, const tqp_pred* fact_preds,
+                         int nfact_preds, const int* fk_col, const tqp_dim* dims, int ndims, const tqp_valref* vals,
+                         int nvals, const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
+                         void* const* d_out_keys, int64_t* d_out_aggs, int64_t cap, int64_t* d_out_groups, void* ws,
+                         size_t* ws_bytes, tqp_stream_t stream, const tqp_learned_cfg* lcfg) {
   if (!ws_bytes || n_fact < 0 || n_fact > INT_MAX || ndims < 1 || ndims > kMaxDims || !dims || !fk_col ||
       !fact_cols || nfact_cols < 1)
     return TQP_ERR_INVALID;
@@ -750,7 +1163,15 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
     }
     w.skeys = c.take<char>(nn * eb);
     w.srows = c.take<int32_t>(nn);
-    w.ksort = carve_sort(c, D.n, eb, eb);
+    // large dimensions' keys through the learned range partitioner when asked
+    w.learned = lcfg && D.n >= kLearnedSortMinRows;
+    if (w.learned) {
+      tqp_learned_cfg lc = *lcfg;
+      lc.heavy = 0;
+      w.lws = carve_learned(c, D.n, &lc, kLearnedSortRowsPerBucket, 0, nullptr, w.srows);
+    } else {
+      w.ksort = carve_sort(c, D.n, eb, eb);
+    }
     if (D.group.data) {
       w.gword = dtype_bytes(D.group.dtype) <= 4 ? 4 : 8;
       w.gplan = c.take<GroupPlan>(1);
@@ -839,7 +1260,8 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
       TQP_CUDA(cudaMemsetAsync(w.cnt, 0, 8, s));
       dcnt = w.cnt;
     }
-    tqp_status st = run_sort(w.ksort, D.key.dtype, kin, vin, w.skeys, w.srows, D.n, dcnt, 0, eb * 8, s);
+    tqp_status st = w.learned ? run_sort_learned(w.lws, D.key.dtype, kin, vin, w.skeys, D.n, dcnt, lcfg, s)
+                              : run_sort(w.ksort, D.key.dtype, kin, vin, w.skeys, w.srows, D.n, dcnt, 0, eb * 8, s);
     if (st != TQP_OK) return st;
     if (D.group.data && D.n > 0) {
       KeySet ks;
@@ -1022,305 +1444,26 @@ tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact
   ck<<<persistent_grid(ck, kCompactT, 0, ctiles), kCompactT, 0, s>>>(ca); note_launch();
   return last_launch();
 }
-
-// ---------------------------------------------------------------------------
-// Learned CDF model and the learned group-by.
-tqp_status tqp_cdf_forward(const tqp_cdf_model* d_model, const float* d_x, int64_t n, float* d_F, int32_t* d_bucket,
-                           int B, tqp_stream_t stream) {
-  if (n < 0 || n > INT_MAX || (d_bucket && (B < 1 || B > (1 << 24)))) return TQP_ERR_INVALID;
-  if (n == 0) return TQP_OK;
-  if (!d_model || !d_x || !d_F) return TQP_ERR_INVALID;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cdf_forward_kernel<<<stride_grid(n, 256), 256, 0, s>>>(d_model, d_x, n, d_F, d_bucket, B); note_launch();
-  return last_launch();
-}
-
-tqp_status tqp_cdf_backward(const tqp_cdf_model* d_model, const float* d_x, const float* d_y, int64_t n,
-                            float* d_grad, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
-  if (!ws_bytes || n < 0 || n > (1 << 20)) return TQP_ERR_INVALID;
-  const int nb = (int)((n + kGradChunk - 1) / kGradChunk);
-  Carver c(ws);
-  float* partial = c.take<float>((size_t)(nb > 0 ? nb : 1) * kGradLen);
-  if (!ws) {
-    *ws_bytes = c.off;
-    return TQP_OK;
-  }
-  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
-  if (!d_model || !d_grad || (n > 0 && (!d_x || !d_y))) return TQP_ERR_INVALID;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (nb > 0) {
-    // gradient only: without an Adam state the model is not written
-    cdf_grad_kernel<<<nb, 256, 0, s>>>(const_cast<tqp_cdf_model*>(d_model), d_x, d_y, nullptr, n, partial, nullptr,
-                                       tqp_train_cfg{}, 0, nullptr); note_launch();
-  }
-  cdf_grad_finish_kernel<<<1, 256, 0, s>>>(partial, nb, nullptr, n, d_grad); note_launch();
-  return last_launch();
-}
-
-namespace {
-bool valid_train_cfg(const tqp_train_cfg* cfg) {
-  return cfg && cfg->epochs >= 0 && cfg->epochs <= 100000 && cfg->lr > 0 && cfg->beta1 >= 0 && cfg->beta1 < 1 &&
-         cfg->beta2 >= 0 && cfg->beta2 < 1 && cfg->eps > 0;
-}
-
-void launch_training(tqp_cdf_model* model, const float* x, const float* y, int64_t n, const int64_t* d_n,
-                     const tqp_train_cfg& cfg, float* partial, AdamState* st, float* loss, cudaStream_t s) {
-  const int nb = (int)((n + kGradChunk - 1) / kGradChunk);
-  for (int e = 0; e < cfg.epochs; ++e) {
-    cdf_grad_kernel<<<nb, 256, 0, s>>>(model, x, y, d_n, n, partial, st, cfg, e, loss); note_launch();
-  }
-}
 }  // namespace
 
-tqp_status tqp_cdf_train(const float* d_x, const float* d_y, int64_t n, tqp_cdf_model* d_model,
-                         const tqp_train_cfg* cfg, float* d_loss, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
-  if (!ws_bytes || n < 1 || n > (1 << 20) || !valid_train_cfg(cfg)) return TQP_ERR_INVALID;
-  const int nb = (int)((n + kGradChunk - 1) / kGradChunk);
-  Carver c(ws);
-  float* partial = c.take<float>((size_t)nb * kGradLen);
-  AdamState* st = c.take<AdamState>(1);
-  if (!ws) {
-    *ws_bytes = c.off;
-    return TQP_OK;
-  }
-  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
-  if (!d_x || !d_y || !d_model) return TQP_ERR_INVALID;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  TQP_CUDA(cudaMemsetAsync(st, 0, sizeof(AdamState), s));
-  launch_training(d_model, d_x, d_y, n, nullptr, *cfg, partial, st, d_loss, s);
-  return last_launch();
+tqp_status tqp_star_agg(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact, const tqp_pred* fact_preds,
+                        int nfact_preds, const int* fk_col, const tqp_dim* dims, int ndims, const tqp_valref* vals,
+                        int nvals, const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
+                        void* const* d_out_keys, int64_t* d_out_aggs, int64_t cap, int64_t* d_out_groups, void* ws,
+                        size_t* ws_bytes, tqp_stream_t stream) {
+  return star_agg_impl(fact_cols, nfact_cols, n_fact, fact_preds, nfact_preds, fk_col, dims, ndims, vals, nvals, exprs,
+                       nexprs, aggs, naggs, d_out_keys, d_out_aggs, cap, d_out_groups, ws, ws_bytes, stream, nullptr);
 }
 
-tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col* vals, int nvals,
-                                   const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
-                                   const int32_t* d_sel, int64_t n, const int64_t* d_n, void* const* d_out_keys,
-                                   int64_t* d_out_aggs, int64_t cap, int64_t* d_out_groups,
-                                   const tqp_learned_cfg* cfg, tqp_cdf_model* d_model_out,
-                                   tqp_learned_stats* d_stats, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
-  if (!ws_bytes || !cfg || n < 0 || n >= (1ll << 30) || nkeys < 1 || nkeys > TQP_MAX_KEYS || !keys)
-    return TQP_ERR_INVALID;
-  const int S = cfg->sample;
-  if (S < 1024 || S > (1 << 20) || (S & (S - 1))) return TQP_ERR_INVALID;
-  if (cfg->buckets < 0 || cfg->buckets == 1 || cfg->buckets > (1 << 17) || (cfg->buckets & (cfg->buckets - 1)))
-    return TQP_ERR_INVALID;
-  if (cfg->train && !valid_train_cfg(&cfg->train_cfg)) return TQP_ERR_INVALID;
-  if (cfg->init != 0 && cfg->init != 1) return TQP_ERR_INVALID;
-  for (int k = 0; k < nkeys; ++k)
-    if (!valid_dtype(keys[k].dtype)) return TQP_ERR_DTYPE;
-  AggProgram P;
-  tqp_status st = build_agg_program(vals, nvals, exprs, nexprs, aggs, naggs, &P, n > 0);
-  if (st != TQP_OK) return st;
-  int B = cfg->buckets;
-  if (B == 0) {  // about 512 rows per bucket: most buckets fit one warp's sort
-    B = 256;
-    while (B < (1 << 17) && (int64_t)B * 512 < n) B <<= 1;
-  }
-  const int epochs = cfg->train ? cfg->train_cfg.epochs : 0;
-  // heavy keys are found in a sample kHeavyMult times larger than the
-  // training set (a key far beyond a bucket's capacity must not escape by
-  // sampling noise); the network trains on every kHeavyMult-th sorted key
-  const int SH = S * kHeavyMult <= (1 << 20) ? S * kHeavyMult : (1 << 20);
-  const int mult = SH / S;
-  long long minc = (long long)((double)SH * kLocalCap / (2.0 * (double)(n > 0 ? n : 1))) + 1;
-  if (minc < 2) minc = 2;
-  if (minc > 4095) minc = 4095;
-  const size_t nn = (size_t)(n > 0 ? n : 1);
-  const int nb = S / kGradChunk;
-  const int64_t rtiles = (n + kReduceThreads * kReduceItems - 1) / (kReduceThreads * kReduceItems);
-  Carver c(ws);
-  GroupPlan* gp = c.take<GroupPlan>(1);
-  unsigned long long* sample = c.take<unsigned long long>(SH);
-  unsigned long long* ssorted = c.take<unsigned long long>(SH);
-  int32_t* srows = c.take<int32_t>(SH);
-  int* cut_hist = c.take<int>(kCutBins);
-  int* chunk_h = c.take<int>((SH + kHeavyChunk - 1) / kHeavyChunk);
-  int* chunk_l = c.take<int>((SH + kHeavyChunk - 1) / kHeavyChunk);
-  SortWs ssort = carve_sort(c, SH, 8, 8);
-  float* tx = c.take<float>(S);
-  float* ty = c.take<float>(S);
-  tqp_cdf_model* model = c.take<tqp_cdf_model>(1);
-  LearnedPlan* lp = c.take<LearnedPlan>(1);
-  AdamState* adam = c.take<AdamState>(1);
-  float* partial = c.take<float>((size_t)nb * kGradLen);
-  float* loss = c.take<float>((size_t)(epochs > 0 ? epochs : 1));
-  unsigned long long* heavy = c.take<unsigned long long>(kMaxHeavy);
-  long long* heavy_acc = c.take<long long>((size_t)kMaxHeavy * naggs);
-  unsigned* thr = c.take<unsigned>((size_t)B);
-  int* dir = c.take<int>((1 << kDirBits) + 1);
-  unsigned* count = c.take<unsigned>((size_t)B);
-  unsigned* cursor = c.take<unsigned>((size_t)B);
-  const int nblk = num_sms();
-  unsigned* bcount = c.take<unsigned>(B <= kBlockHistMaxB ? (size_t)nblk * B : 1);
-  unsigned* off = c.take<unsigned>((size_t)B + 1);
-  int64_t* light_n = c.take<int64_t>(1);
-  unsigned long long* lpk = c.take<unsigned long long>(nn);
-  int32_t* lrow = c.take<int32_t>(nn);
-  unsigned long long* apk = c.take<unsigned long long>(nn);
-  int32_t* arow = c.take<int32_t>(nn);
-  uint32_t* queue = c.take<uint32_t>(2);
-  uint32_t* big_flags = c.take<uint32_t>((size_t)B);
-  uint32_t* rheads = c.take<uint32_t>((size_t)(rtiles > 0 ? rtiles : 1));
-  Partial* rcarry = c.take<Partial>((size_t)(rtiles > 0 ? rtiles : 1));
-  void* lgath[TQP_MAX_VALS] = {};
-  if (n >= kPregatherRows)
-    for (int v = 0; v < P.nvals; ++v) lgath[v] = c.take<char>(nn * dtype_bytes(P.vdt[v]));
-  if (!ws) {
-    *ws_bytes = c.off;
-    return TQP_OK;
-  }
-  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
-  if (!d_out_groups || cap < 0 || (cap > 0 && (!d_out_aggs || !d_out_keys))) return TQP_ERR_INVALID;
-  KeySet ks;
-  std::memset(&ks, 0, sizeof(ks));
-  ks.nkeys = nkeys;
-  for (int k = 0; k < nkeys; ++k) {
-    if (n > 0 && !keys[k].data) return TQP_ERR_INVALID;
-    if (cap > 0 && !d_out_keys[k]) return TQP_ERR_INVALID;
-    ks.col[k] = keys[k].data;
-    ks.dt[k] = keys[k].dtype;
-    ks.out[k] = cap > 0 ? d_out_keys[k] : nullptr;
-  }
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (n == 0) {
-    TQP_CUDA(cudaMemsetAsync(d_out_groups, 0, sizeof(int64_t), s));
-    if (d_stats) TQP_CUDA(cudaMemsetAsync(d_stats, 0, sizeof(tqp_learned_stats), s));
-    return TQP_OK;
-  }
-  // 1. key range and packing (always a 64-bit packed word on this path)
-  gb_init_kernel<<<1, 32, 0, s>>>(gp); note_launch();
-  gb_keyrange_kernel<256><<<stride_grid(n, 256, 4), 256, 0, s>>>(ks, d_sel, n, d_n, gp); note_launch();
-  gb_plan_kernel<<<1, 32, 0, s>>>(gp, nkeys, 64); note_launch();
-  lp_init_kernel<<<1, 32, 0, s>>>(gp, nkeys, model, lp, adam, B, (int)minc); note_launch();
-  // 2. sample, sorted by the radix sort; training pairs
-  lp_sample_kernel<<<(SH + 255) / 256, 256, 0, s>>>(ks, d_sel, n, d_n, gp, SH, sample); note_launch();
-  st = run_sort(ssort, kKeyU64, sample, nullptr, ssorted, srows, SH, nullptr, 0, 64, s);
-  if (st != TQP_OK) return st;
-  // 3. heavy keys; training pairs on the CDF of the light rows (the sort's
-  // row ids are no longer needed: srows holds the light prefix)
-  {
-    const int nch = (SH + kHeavyChunk - 1) / kHeavyChunk, g = (nch + 255) / 256;
-    TQP_CUDA(cudaMemsetAsync(cut_hist, 0, kCutBins * sizeof(int), s));
-    if (cfg->heavy) {
-      lp_runhist_kernel<<<g, 256, 0, s>>>(ssorted, SH, lp, cut_hist); note_launch();
-    }
-    lp_cut_kernel<<<1, 32, 0, s>>>(cut_hist, cfg->heavy ? 1 : 0, lp); note_launch();
-    lp_chunk_kernel<<<g, 256, 0, s>>>(ssorted, SH, lp, chunk_h, chunk_l); note_launch();
-    lp_chunk_scan_kernel<<<1, 1024, 0, s>>>(nch, chunk_h, chunk_l, lp); note_launch();
-    lp_heavy_write_kernel<<<g, 256, 0, s>>>(ssorted, SH, lp, chunk_h, chunk_l, heavy, srows); note_launch();
-  }
-  lp_targets_kernel<<<(S + 255) / 256, 256, 0, s>>>(ssorted, SH, mult, S, lp, srows, tx, ty); note_launch();
-  if (cfg->init == 1) {
-    lp_quantile_init_kernel<<<1, kH, 0, s>>>(tx, ty, S, lp, model); note_launch();
-  }
-  // 4. training, then the step positions of the bucket function and their directory
-  if (epochs > 0) launch_training(model, tx, ty, S, nullptr, cfg->train_cfg, partial, adam, loss, s);
-  if (B > 1) {
-    lp_thresholds_kernel<<<(B - 1 + 255) / 256, 256, 0, s>>>(model, lp, thr); note_launch();
-  }
-  lp_directory_kernel<<<((1 << kDirBits) + 1 + 255) / 256, 256, 0, s>>>(lp, thr, dir); note_launch();
-  // 5. partition: bucket counts, offsets, scatter (heavy rows folded on the fly)
-  PartArgs pa;
-  pa.ks = ks;
-  pa.sel = d_sel;
-  pa.n_max = n;
-  pa.d_n = d_n;
-  pa.gp = gp;
-  pa.lp = lp;
-  pa.thr = thr;
-  pa.dir = dir;
-  pa.heavy = heavy;
-  pa.count = count;
-  pa.cursor = cursor;
-  pa.out_p = lpk;
-  pa.out_row = lrow;
-  pa.heavy_acc = heavy_acc;
-  pa.bcount = bcount;
-  TQP_CUDA(cudaMemsetAsync(count, 0, (size_t)B * sizeof(unsigned), s));
-  {
-    // the steps live in shared memory when the scatter's layout still fits.
-    // Counting: up to kBlockHistMaxB buckets each block counts one chunk of
-    // rows in shared memory (then the column sums); placing: one global
-    // cursor per bucket, so each bucket fills as one stream
-    const int smode = part_smem_bytes(B, naggs, kThrShared) <= (size_t)kMaxSmemOptin ? kThrShared : kThrGlobal;
-    const int hmode = (B <= kBlockHistMaxB && part_smem_bytes(B, 0, kBlockHist) <= (size_t)kMaxSmemOptin) ? kBlockHist
-                                                                                                       : smode;
-    const size_t hsm = part_smem_bytes(B, 0, hmode), ssm = part_smem_bytes(B, naggs, smode);
-    auto hk = hmode == kBlockHist ? lp_hist_kernel<kBlockHist>
-                                  : (hmode == kThrShared ? lp_hist_kernel<kThrShared> : lp_hist_kernel<kThrGlobal>);
-    auto sk = smode == kThrShared ? lp_scatter_kernel<kThrShared> : lp_scatter_kernel<kThrGlobal>;
-    TQP_CUDA(cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
-    TQP_CUDA(cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
-    const int64_t ptiles = (n + kPartThreads * kPartItems - 1) / (kPartThreads * kPartItems);
-    const int gh = hmode == kBlockHist ? nblk : persistent_grid(hk, kPartThreads, hsm, ptiles);
-    hk<<<gh, kPartThreads, hsm, s>>>(pa); note_launch();
-    if (hmode == kBlockHist) {
-      lp_bcols_kernel<<<(B + 255) / 256, 256, 0, s>>>(bcount, nblk, lp, count); note_launch();
-    }
-    lp_offsets_kernel<<<1, 1024, 0, s>>>(lp, count, off, cursor, d_stats, loss, epochs, light_n); note_launch();
-    lp_heavy_init_kernel<<<(kMaxHeavy * naggs + 255) / 256, 256, 0, s>>>(lp, P, heavy_acc); note_launch();
-    prof_mark(8, true, s);
-    sk<<<persistent_grid(sk, kPartThreads, ssm, ptiles), kPartThreads, ssm, s>>>(pa, P); note_launch();
-    prof_mark(8, false, s);
-  }
-  // 6. every bucket sorted: on-chip up to the capacity, else by one block in global memory
-  {
-    BucketSortArgs ba;
-    ba.lp = lp;
-    ba.off = off;
-    ba.p = lpk;
-    ba.row = lrow;
-    ba.alt_p = apk;
-    ba.alt_row = arow;
-    ba.queue = queue;
-    ba.big_flags = big_flags;
-    size_t smem = (size_t)kLocalCap * (8 + 8 + 4 + 4) + (size_t)kLocalWarps * (kRadix + 1) * 4 + kRadix * 4;
-    size_t wsmem = (size_t)kWarpSortWarps * (2 * kWarpCap * 8 + (kRadix + 1) * 4);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(lp_bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(lp_bucket_sort_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
-      attr = true;
-    }
-    TQP_CUDA(cudaMemsetAsync(queue, 0, 2 * sizeof(uint32_t), s));
-    TQP_CUDA(cudaMemsetAsync(big_flags, 0, (size_t)B * sizeof(uint32_t), s));
-    {
-      int gw = persistent_grid(lp_bucket_sort_warp_kernel, kWarpSortWarps * 32, wsmem, (B + kWarpSortWarps - 1) / kWarpSortWarps);
-      prof_mark(9, true, s);
-      lp_bucket_sort_warp_kernel<<<gw, kWarpSortWarps * 32, wsmem, s>>>(ba, queue + 1, big_flags); note_launch();
-      prof_mark(9, false, s);
-    }
-    int g = num_sms();
-    if (g > B) g = B;
-    prof_mark(7, true, s);
-    lp_bucket_sort_kernel<<<g, kLocalThreads, smem, s>>>(ba); note_launch();
-    prof_mark(7, false, s);
-  }
-  // 7. reduce-by-key over the sorted light rows, merging the heavy keys
-  ReduceArgs r;
-  r.keys = lpk;
-  r.rows = lrow;
-  r.n_max = n;
-  r.d_n = light_n;
-  r.plan = gp;
-  r.ks = ks;
-  r.out_aggs = reinterpret_cast<long long*>(d_out_aggs);
-  r.cap = cap;
-  r.d_out_groups = d_out_groups;
-  r.tile_heads = rheads;
-  r.carry = rcarry;
-  r.num_tiles = (uint32_t)rtiles;
-  r.heavy = heavy;
-  r.d_nheavy = &lp->nheavy;
-  r.heavy_acc = heavy_acc;
-  AggProgram Pr = P;
-  if (lgath[0] || P.nvals == 0) {
-    if (P.nvals) Pr = pregather_values(P, lgath, lrow, n, light_n, s);
-    r.rows = nullptr;
-  }
-  launch_reduce<unsigned long long>(r, Pr, (uint32_t)rtiles, s);
-  gb_heavy_only_kernel<<<(kMaxHeavy + 255) / 256, 256, 0, s>>>(r, naggs); note_launch();
-  if (d_model_out) TQP_CUDA(cudaMemcpyAsync(d_model_out, model, sizeof(tqp_cdf_model), cudaMemcpyDeviceToDevice, s));
-  return last_launch();
+tqp_status tqp_star_agg_learned(const tqp_col* fact_cols, int nfact_cols, int64_t n_fact, const tqp_pred* fact_preds,
+                                int nfact_preds, const int* fk_col, const tqp_dim* dims, int ndims,
+                                const tqp_valref* vals, int nvals, const tqp_expr* exprs, int nexprs,
+                                const tqp_agg* aggs, int naggs, void* const* d_out_keys, int64_t* d_out_aggs,
+                                int64_t cap, int64_t* d_out_groups, const tqp_learned_cfg* cfg, void* ws,
+                                size_t* ws_bytes, tqp_stream_t stream) {
+  if (!valid_learned_cfg(cfg)) return TQP_ERR_INVALID;
+  return star_agg_impl(fact_cols, nfact_cols, n_fact, fact_preds, nfact_preds, fk_col, dims, ndims, vals, nvals, exprs,
+                       nexprs, aggs, naggs, d_out_keys, d_out_aggs, cap, d_out_groups, ws, ws_bytes, stream, cfg);
 }
 
 // ---------------------------------------------------------------------------

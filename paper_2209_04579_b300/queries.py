@@ -32,13 +32,15 @@ def q6(t, cap: int = 64):
                                Q6_EXPRS, Q6_AGGS, cap, sel=sel, n=t["ship_day"].numel(), d_n=cnt)
 
 
-def q14(fact, dim, cap: int = 64):
+def q14(fact, dim, cap: int = 64, learned=None):
     """SELECT region, SUM(price), COUNT(*) FROM fact JOIN dim ON fk = key
-    WHERE region < 5 GROUP BY region -- fused star aggregate."""
+    WHERE region < 5 GROUP BY region -- fused star aggregate.  learned: a
+    learned_cfg (the dimension's keys sorted through the learned range
+    partitioner)."""
     D = tqp.DimSpec(dim["key"], cols=[dim["region"], dim["price"]], preds=[(0, tqp.LT, Q14_REGION_LT)],
                     group=dim["region"])
     return tqp.tqp_star_agg([fact["fk"]], [], [0], [D], [(1, 1)], [[(0, 1, 0)]],
-                            [(tqp.SUM, 0), (tqp.COUNT, 0)], cap)
+                            [(tqp.SUM, 0), (tqp.COUNT, 0)], cap, learned=learned)
 
 
 def q14_unfused(fact, dim, cap: int = 64, pair_cap: int | None = None):
@@ -91,13 +93,14 @@ def batched(problems, cap: int = 64, probe_items: int = 8, shape=None):
                                     cap=cap, probe_items=probe_items)
 
 
-def star(fact, dim1, dim2, cap: int = 50_000):
+def star(fact, dim1, dim2, cap: int = 50_000, learned=None):
     """SELECT dim1.cat, dim2.cat, SUM(m1), SUM(m2), SUM(m3), COUNT(*)
     FROM fact JOIN dim1 ON fk1 = dim1.key JOIN dim2 ON fk2 = dim2.key
-    WHERE date < 767 GROUP BY dim1.cat, dim2.cat."""
+    WHERE date < 767 GROUP BY dim1.cat, dim2.cat.  learned: a learned_cfg
+    (the dimensions' keys sorted through the learned range partitioner)."""
     D1 = tqp.DimSpec(dim1["key"], cols=[dim1["cat"]], group=dim1["cat"])
     D2 = tqp.DimSpec(dim2["key"], cols=[dim2["cat"]], group=dim2["cat"])
     cols = [fact["fk1"], fact["fk2"], fact["m1"], fact["m2"], fact["m3"], fact["date"]]
     return tqp.tqp_star_agg(cols, [(5, tqp.LT, STAR_DATE_LT)], [0, 1], [D1, D2], [(0, 2), (0, 3), (0, 4)],
                             [[(0, 1, 0)], [(1, 1, 0)], [(2, 1, 0)]],
-                            [(tqp.SUM, 0), (tqp.SUM, 1), (tqp.SUM, 2), (tqp.COUNT, 0)], cap)
+                            [(tqp.SUM, 0), (tqp.SUM, 1), (tqp.SUM, 2), (tqp.COUNT, 0)], cap, learned=learned)

@@ -123,6 +123,7 @@ _lib.tqp_groupby_agg.argtypes = [_P(Col), _int, _P(Col), _int, _P(Expr), _int, _
                                  _P(_vp), _vp, _i64, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_star_agg.argtypes = [_P(Col), _int, _i64, _P(Pred), _int, _P(_int), _P(Dim), _int, _P(ValRef), _int,
                               _P(Expr), _int, _P(Agg), _int, _P(_vp), _vp, _i64, _vp, _vp, _P(_sz), _vp]
+_lib.tqp_star_agg_learned.argtypes = _lib.tqp_star_agg.argtypes[:-3] + [_P(LearnedCfg), _vp, _P(_sz), _vp]
 _lib.tqp_cdf_forward.argtypes = [_vp, _vp, _i64, _vp, _vp, _int, _vp]
 _lib.tqp_cdf_backward.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_cdf_train.argtypes = [_vp, _vp, _i64, _vp, _P(TrainCfg), _vp, _vp, _P(_sz), _vp]
@@ -139,6 +140,7 @@ _lib.tqp_debug_launch_count.restype = ctypes.c_int64
 _lib.tqp_debug_launch_count.argtypes = []
 _lib.tqp_profile_events.argtypes = [_int, _vp, _vp]
 for _f in ("tqp_filter", "tqp_gather", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
+           "tqp_star_agg_learned",
            "tqp_status_poll", "tqp_profile_events", "tqp_cdf_forward", "tqp_cdf_backward", "tqp_cdf_train",
            "tqp_groupby_agg_learned", "tqp_star_agg_batched", "tqp_debug_set_spin_limit", "tqp_debug_inject_unpublished_tile"):
     getattr(_lib, _f).restype = ctypes.c_int
@@ -322,10 +324,11 @@ class DimSpec:
         self.key, self.cols, self.preds, self.group = key, list(cols), list(preds), group
 
 
-def tqp_star_agg(fact_cols, fact_preds, fk_cols, dims, vals, exprs, aggs, cap, stream=None):
+def tqp_star_agg(fact_cols, fact_preds, fk_cols, dims, vals, exprs, aggs, cap, stream=None, learned=None):
     """Fused star join + filter + group-by.  vals: (src, col) with src 0 =
-    fact column, 1 + d = column of dimension d.  Returns (key columns, aggs,
-    device G)."""
+    fact column, 1 + d = column of dimension d.  learned: a learned_cfg to
+    sort large dimensions' keys through the learned range partitioner
+    (tqp_star_agg_learned).  Returns (key columns, aggs, device G)."""
     dev = fact_cols[0].device
     keep = []
     darr = (Dim * len(dims))()
@@ -348,10 +351,14 @@ def tqp_star_agg(fact_cols, fact_preds, fk_cols, dims, vals, exprs, aggs, cap, s
     kp = (ctypes.c_void_p * max(1, nkeys))(*[k.data_ptr() for k in out_keys])
     fk = (ctypes.c_int * len(fk_cols))(*fk_cols)
     vr = (ValRef * max(1, len(vals)))(*[ValRef(s, c) for s, c in vals])
-    _two_phase(_lib.tqp_star_agg, "tqp_star_agg",
-               [_cols(fact_cols), len(fact_cols), fact_cols[0].numel(), _preds(fact_preds), len(fact_preds), fk, darr,
-                len(dims), vr, len(vals), _exprs(exprs), len(exprs), _aggs(aggs), len(aggs), kp, _ptr(out_aggs), cap,
-                _ptr(G)], dev, stream)
+    args = [_cols(fact_cols), len(fact_cols), fact_cols[0].numel(), _preds(fact_preds), len(fact_preds), fk, darr,
+            len(dims), vr, len(vals), _exprs(exprs), len(exprs), _aggs(aggs), len(aggs), kp, _ptr(out_aggs), cap,
+            _ptr(G)]
+    if learned is None:
+        _two_phase(_lib.tqp_star_agg, "tqp_star_agg", args, dev, stream)
+    else:
+        keep.append(learned)
+        _two_phase(_lib.tqp_star_agg_learned, "tqp_star_agg_learned", args + [learned], dev, stream)
     return out_keys, out_aggs, G
 
 

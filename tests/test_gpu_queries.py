@@ -132,6 +132,51 @@ def test_star_scaled(G):
     assert tqp.tqp_status_poll() == tqp.OK
 
 
+def test_star_scaled_learned_dimension_sort(G):
+    """The scaled star join with the dimensions' keys sorted through the
+    learned range partitioner (tqp_star_agg_learned): dim2 (1.5M keys) takes
+    the learned sort, dim1 (200K) the radix sort; the same groups."""
+    tqp, Q, gd = G
+    rec = dg.star_tables(200_000, 1_500_000)
+    n = 6_000_000
+    want = pl.star(dg.make_table(rec["fact"], n), dg.make_table(rec["dim1"], 200_000),
+                   dg.make_table(rec["dim2"], 1_500_000))
+    got = Q.star(gd.make_table(rec["fact"], n), gd.make_table(rec["dim1"], 200_000),
+                 gd.make_table(rec["dim2"], 1_500_000), learned=tqp.learned_cfg(sample=16384, tcfg=tqp.train_cfg(epochs=10, lr=1e-4)))
+    compare(got, want)
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
+def test_star_learned_both_dimensions(G):
+    """Both dimensions above the learned sort's threshold (1.2M and 2M keys,
+    untrained identity network and a fixed bucket count included)."""
+    tqp, Q, gd = G
+    rec = dg.star_tables(1_200_000, 2_000_000)
+    n = 3_000_000
+    want = pl.star(dg.make_table(rec["fact"], n), dg.make_table(rec["dim1"], 1_200_000),
+                   dg.make_table(rec["dim2"], 2_000_000))
+    for cfg in (tqp.learned_cfg(sample=8192, tcfg=tqp.train_cfg(epochs=5, lr=1e-4)),
+                tqp.learned_cfg(sample=4096, buckets=1024, train=False)):
+        got = Q.star(gd.make_table(rec["fact"], n), gd.make_table(rec["dim1"], 1_200_000),
+                     gd.make_table(rec["dim2"], 2_000_000), learned=cfg)
+        compare(got, want)
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
+def test_q14_learned_filtered_dimension(G):
+    """The Q14 shape at 3M fact rows with a 1.5M-row dimension whose passing
+    rows (region < 5) are sorted through the learned partitioner, their row
+    ids carried as the payload."""
+    tqp, Q, gd = G
+    rec = dg.q14_tables(1_500_000)
+    n = 3_000_000
+    want = pl.q14(dg.make_table(rec["fact"], n), dg.make_table(rec["dim"], 1_500_000))
+    got = Q.q14(gd.make_table(rec["fact"], n), gd.make_table(rec["dim"], 1_500_000),
+                learned=tqp.learned_cfg(sample=16384, tcfg=tqp.train_cfg(epochs=5, lr=1e-4)))
+    compare(got, want)
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
 def test_star_crowded_directory_cells(G):
     """Dimension keys clustered in a tiny part of their range (plus far
     outliers), so one directory cell holds hundreds of keys: the in-cell
@@ -151,9 +196,10 @@ def test_star_crowded_directory_cells(G):
     assert tqp.tqp_status_poll() == tqp.OK
 
 
-def test_star_full_size_invariants(G):
+@pytest.mark.parametrize("learned", [False, True])
+def test_star_full_size_invariants(G, learned):
     """The full star join (fact 600M rows, dims 20M and 150M) in the
-    benchmark's configuration.  At this size the oracle checks properties
+    benchmark's configuration, with the radix or the learned dimension sort.  At this size the oracle checks properties
     that hold at any size: every fact row matches exactly one row of each
     dimension (foreign keys drawn from the dimension keys), so the group
     counts sum to the number of rows with date < 767 and each measure's sums
@@ -165,7 +211,8 @@ def test_star_full_size_invariants(G):
     rec = dg.star_tables(n1, n2)
     fact = gd.make_table(rec["fact"], n)
     d1, d2 = gd.make_table(rec["dim1"], n1), gd.make_table(rec["dim2"], n2)
-    ok, oa, g = Q.star(fact, d1, d2)
+    cfg = tqp.learned_cfg(sample=65536, tcfg=tqp.train_cfg(epochs=10, lr=1e-4)) if learned else None
+    ok, oa, g = Q.star(fact, d1, d2, learned=cfg)
     assert tqp.tqp_status_poll() == tqp.OK
     del fact, d1, d2
     torch.cuda.empty_cache()
