@@ -374,6 +374,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
   __shared__ long long s_carry[NAGG];
   __shared__ int s_carry_used;
   __shared__ unsigned long long s_heavy[kReduceHeavyMax];
+  __shared__ long long s_val[ITEMS][THREADS];  // gathered values, [item][thread]
   if (threadIdx.x == 0) {
     P = Pg;
     s_ks = a.ks;
@@ -395,8 +396,16 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
     qcol[q] = P.nvals ? P.val[c] : nullptr;
     qdt[q] = P.nvals ? P.vdt[c] : TQP_I64;
   }
-  auto fold = [&](PT& acc, int64_t r) {
-    if (simple) {
+  // one value column read through the row ids: the thread's values are
+  // gathered into shared memory first, their reads in flight together
+  const bool gather = simple && rows != nullptr && P.nvals == 1;
+  auto fold = [&](PT& acc, int64_t r, int k) {
+    if (gather) {
+      const long long v = s_val[k][threadIdx.x];
+#pragma unroll
+      for (int q = 0; q < NAGG; ++q)
+        if (q < P.naggs) acc.v[q] = agg_fold(qop[q], acc.v[q], qop[q] == TQP_COUNT ? 1 : v);
+    } else if (simple) {
 #pragma unroll
       for (int q = 0; q < NAGG; ++q)
         if (q < P.naggs) acc.v[q] = agg_fold(qop[q], acc.v[q], qop[q] == TQP_COUNT ? 1 : load_as_i64(qcol[q], qdt[q], r));
@@ -423,6 +432,11 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
       }
     }
     const K key0 = base < n ? keys[base] : (K)0;
+    if (gather) {
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k)
+        s_val[k][threadIdx.x] = base + k < n ? load_as_i64(P.val[0], P.vdt[0], rows[base + k]) : 0;
+    }
     int tile_heads;
     const int before = block_exclusive_sum<THREADS>(__popc(head), s_scan, &tile_heads);
     const long long g0 = (long long)a.tile_heads[t] + before;  // light index of the thread's first head
@@ -457,7 +471,7 @@ __global__ void __launch_bounds__(THREADS) gb_reduce_kernel(ReduceArgs a, AggPro
             hl = hl_new;
           }
         }
-        fold(acc, rows ? rows[p] : p);
+        fold(acc, rows ? rows[p] : p, k);
         if (nh && p == n - 1) {
           // heavy keys above the last light key
           for (int i = hl; i < nh; ++i)

@@ -975,19 +975,83 @@ struct LocalSmem {
   unsigned long long* kB;
   int32_t* rA;
   int32_t* rB;
-  unsigned* cnt;    // [kLocalWarps][kRadix + 1]
+  unsigned* cnt;    // [kLocalWarps][kRadix + 1] (the on-chip sort's cursors: [kMsdBins])
   unsigned* start;  // [kRadix]
   int* scan;        // 33
   unsigned long long* red;  // [2 * kLocalWarps]
+  unsigned* part;   // [kMsdBins + 1] on-chip sort's part starts
+  int* big;         // [kBigParts] its large parts
+  int* nbig;
 };
 
+// LSD sort, by one block, of the m <= kLocalCap keys and rows at (kX, rX) in
+// shared memory over the bits of their span, (kY, rY) as scratch; the
+// result in (kX, rX).
+__device__ void lsd_shared(unsigned long long* kX, int32_t* rX, unsigned long long* kY, int32_t* rY, int m,
+                           const LocalSmem& L) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long lo = ~0ull, hi = 0;
+  for (int i = threadIdx.x; i < m; i += kLocalThreads) {
+    const unsigned long long k = kX[i];
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+  }
+  unsigned long long pmin;
+  const unsigned long long span = block_minmax_span(lo, hi, L.red, &pmin);
+  if (span == 0) return;
+  const int bits = 64 - __clzll((long long)span);
+  const int per = (m + kLocalWarps - 1) / kLocalWarps;
+  const int wbeg = warp * per;
+  unsigned long long* kA = kX;
+  unsigned long long* kB = kY;
+  int32_t* rA = rX;
+  int32_t* rB = rY;
+  for (int sh = 0; sh < bits; sh += kRadixBits) {
+    unsigned dig[kLocalItems];
+    int pos[kLocalItems];
+#pragma unroll
+    for (int it = 0; it < kLocalItems; ++it) {
+      int i = wbeg + it * 32 + lane;
+      bool v = (it * 32 + lane < per) && i < m;
+      dig[it] = v ? (unsigned)(((kA[i] - pmin) >> sh) & (kRadix - 1)) : kRadix;
+    }
+    int total;
+    block_rank<kLocalWarps, kLocalItems>(dig, pos, (per + 31) >> 5, L.cnt, L.start, L.scan, &total);
+#pragma unroll
+    for (int it = 0; it < kLocalItems; ++it) {
+      if (pos[it] >= 0) {
+        int i = wbeg + it * 32 + lane;
+        kB[pos[it]] = kA[i];
+        rB[pos[it]] = rA[i];
+      }
+    }
+    __syncthreads();
+    unsigned long long* tk = kA; kA = kB; kB = tk;
+    int32_t* tr = rA; rA = rB; rB = tr;
+  }
+  if (kA != kX) {  // odd number of passes
+    for (int i = threadIdx.x; i < m; i += kLocalThreads) {
+      kX[i] = kA[i];
+      rX[i] = rA[i];
+    }
+    __syncthreads();
+  }
+}
+
 // m <= kLocalCap rows from (sp, sr) sorted by key into (dp, dr) (which may
-// be the same arrays): loaded into shared memory, LSD over the bits of the
-// rows' key span, written back.  Called by the whole block.
+// be the same arrays), by one block: loaded into shared memory, one counting
+// pass on the top kMsdBits bits of the rows' key span (block-wide counters:
+// equal keys need no order) into kMsdBins parts, every part of at most
+// kSmallPart rows insertion-sorted by one thread, a larger part (typically
+// many rows of one key) sorted by lsd_shared; written back.
+constexpr int kMsdBits = 11;
+constexpr int kMsdBins = 1 << kMsdBits;
+constexpr int kSmallPart = 32;
+constexpr int kBigParts = 64;
+
 __device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, unsigned long long* dp, int32_t* dr,
                             int m, const LocalSmem& L) {
   if (m <= 0) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long* kA = L.kA;
   unsigned long long* kB = L.kB;
   int32_t* rA = L.rA;
@@ -1002,40 +1066,89 @@ __device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, uns
   }
   unsigned long long pmin;
   const unsigned long long span = block_minmax_span(lo, hi, L.red, &pmin);
-  if (span != 0) {
-    const int bits = 64 - __clzll((long long)span);
-    const int per = (m + kLocalWarps - 1) / kLocalWarps;
-    const int wbeg = warp * per;
-    for (int sh = 0; sh < bits; sh += kRadixBits) {
-      unsigned dig[kLocalItems];
-      int pos[kLocalItems];
-#pragma unroll
-      for (int it = 0; it < kLocalItems; ++it) {
-        int i = wbeg + it * 32 + lane;
-        bool v = (it * 32 + lane < per) && i < m;
-        dig[it] = v ? (unsigned)(((kA[i] - pmin) >> sh) & (kRadix - 1)) : kRadix;
+  if (span == 0) {  // one key: already in order
+    if (sp != dp) {
+      for (int i = threadIdx.x; i < m; i += kLocalThreads) {
+        dp[i] = kA[i];
+        dr[i] = rA[i];
       }
-      int total;
-      block_rank<kLocalWarps, kLocalItems>(dig, pos, (per + 31) >> 5, L.cnt, L.start, L.scan, &total);
-#pragma unroll
-      for (int it = 0; it < kLocalItems; ++it) {
-        if (pos[it] >= 0) {
-          int i = wbeg + it * 32 + lane;
-          kB[pos[it]] = kA[i];
-          rB[pos[it]] = rA[i];
-        }
-      }
-      __syncthreads();
-      unsigned long long* tk = kA; kA = kB; kB = tk;
-      int32_t* tr = rA; rA = rB; rB = tr;
     }
-  } else if (sp == dp) {
     __syncthreads();
-    return;  // one key, in place: already in order
+    return;
+  }
+  const int bits = 64 - __clzll((long long)span);
+  const int sh = bits > kMsdBits ? bits - kMsdBits : 0;
+  unsigned* part = L.part;  // [kMsdBins + 1] part starts
+  unsigned* cur = L.cnt;    // [kMsdBins] counts, then cursors
+  for (int d = threadIdx.x; d < kMsdBins; d += kLocalThreads) cur[d] = 0;
+  if (threadIdx.x == 0) *L.nbig = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += kLocalThreads) atomicAdd(&cur[(kA[i] - pmin) >> sh], 1u);
+  __syncthreads();
+  {
+    constexpr int PER = kMsdBins / kLocalThreads;
+    unsigned c[PER], sum = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      c[q] = cur[threadIdx.x * PER + q];
+      sum += c[q];
+    }
+    int tot;
+    unsigned run = (unsigned)block_exclusive_sum<kLocalThreads>((int)sum, L.scan, &tot);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      part[threadIdx.x * PER + q] = run;
+      cur[threadIdx.x * PER + q] = run;
+      run += c[q];
+    }
+    if (threadIdx.x == 0) part[kMsdBins] = (unsigned)m;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += kLocalThreads) {
+    const unsigned long long k = kA[i];
+    const unsigned pos = atomicAdd(&cur[(k - pmin) >> sh], 1u);
+    kB[pos] = k;
+    rB[pos] = rA[i];
+  }
+  __syncthreads();
+  // small parts by one thread each; large ones listed
+  for (int d = threadIdx.x; d < kMsdBins; d += kLocalThreads) {
+    const int p0 = (int)part[d], p1 = (int)part[d + 1];
+    if (p1 - p0 > kSmallPart) {
+      const int at = atomicAdd(L.nbig, 1);
+      if (at < kBigParts) L.big[at] = d;
+      continue;
+    }
+    for (int a = p0 + 1; a < p1; ++a) {
+      const unsigned long long k = kB[a];
+      const int32_t r = rB[a];
+      int b = a - 1;
+      while (b >= p0 && kB[b] > k) {
+        kB[b + 1] = kB[b];
+        rB[b + 1] = rB[b];
+        --b;
+      }
+      kB[b + 1] = k;
+      rB[b + 1] = r;
+    }
+  }
+  __syncthreads();
+  const int nbig = *L.nbig;
+  if (nbig <= kBigParts) {
+    for (int q = 0; q < nbig; ++q) {
+      const int d = L.big[q];
+      const int p0 = (int)part[d];
+      lsd_shared(kB + p0, rB + p0, kA + p0, rA + p0, (int)part[d + 1] - p0, L);
+    }
+  } else {
+    for (int d = 0; d < kMsdBins; ++d) {
+      const int p0 = (int)part[d], pm = (int)part[d + 1] - p0;
+      if (pm > kSmallPart) lsd_shared(kB + p0, rB + p0, kA + p0, rA + p0, pm, L);
+    }
   }
   for (int i = threadIdx.x; i < m; i += kLocalThreads) {
-    dp[i] = kA[i];
-    dr[i] = rA[i];
+    dp[i] = kB[i];
+    dr[i] = rB[i];
   }
   __syncthreads();
 }
@@ -1129,8 +1242,14 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
   __shared__ int s_scan[33];
   __shared__ unsigned long long s_red[2 * kLocalWarps];
   __shared__ unsigned s_part[kRadix + 1];
+  __shared__ unsigned s_msd[kMsdBins + 1];
+  __shared__ int s_big[kBigParts];
+  __shared__ int s_nbig;
   __shared__ uint32_t s_b;
   LocalSmem L;
+  L.part = s_msd;
+  L.big = s_big;
+  L.nbig = &s_nbig;
   L.kA = reinterpret_cast<unsigned long long*>(smem);
   L.kB = L.kA + kLocalCap;
   L.rA = reinterpret_cast<int32_t*>(L.kB + kLocalCap);

@@ -361,7 +361,8 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
   r.d_nheavy = nullptr;
   r.heavy_acc = nullptr;
   AggProgram Pr = P;
-  if (w.gathered[0] || P.nvals == 0) {
+  const bool self_gather = P.simple && P.nvals == 1;  // the reduce reads the values through the row ids
+  if ((w.gathered[0] && !self_gather) || P.nvals == 0) {
     if (P.nvals) Pr = pregather_values(P, w.gathered, w.sorted_rows, n, d_n, s);
     r.rows = nullptr;
   }
@@ -1021,7 +1022,8 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   r.d_nheavy = &w.lp->nheavy;
   r.heavy_acc = w.heavy_acc;
   AggProgram Pr = P;
-  if (w.lgath[0] || P.nvals == 0) {
+  const bool self_gather = P.simple && P.nvals == 1;  // the reduce reads the values through the row ids
+  if ((w.lgath[0] && !self_gather) || P.nvals == 0) {
     if (P.nvals) Pr = pregather_values(P, const_cast<void* const*>(w.lgath), w.lrow, n, w.light_n, s);
     r.rows = nullptr;
   }
