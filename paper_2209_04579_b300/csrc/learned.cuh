@@ -980,8 +980,7 @@ struct LocalSmem {
   int* scan;        // 33
   unsigned long long* red;  // [2 * kLocalWarps]
   unsigned* part;   // [kMsdBins + 1] on-chip sort's part starts
-  int* big;         // [kBigParts] its large parts
-  int* nbig;
+  int* nbig;        // the on-chip sort found a part beyond kSmallPart rows
 };
 
 // LSD sort, by one block, of the m <= kLocalCap keys and rows at (kX, rX) in
@@ -1039,15 +1038,15 @@ __device__ void lsd_shared(unsigned long long* kX, int32_t* rX, unsigned long lo
 }
 
 // m <= kLocalCap rows from (sp, sr) sorted by key into (dp, dr) (which may
-// be the same arrays), by one block: loaded into shared memory, one counting
-// pass on the top kMsdBits bits of the rows' key span (block-wide counters:
-// equal keys need no order) into kMsdBins parts, every part of at most
-// kSmallPart rows insertion-sorted by one thread, a larger part (typically
-// many rows of one key) sorted by lsd_shared; written back.
+// be the same arrays), by one block: loaded into shared memory and counted
+// by the top kMsdBits bits of the rows' key span.  When no part holds more
+// than kSmallPart rows (keys spread over their range), one counting pass
+// places the rows by those bits (block-wide counters: equal keys need no
+// order) and every part is insertion-sorted by one thread; otherwise
+// (repeated or clustered keys) the block's LSD sorts the whole bucket.
 constexpr int kMsdBits = 11;
 constexpr int kMsdBins = 1 << kMsdBits;
 constexpr int kSmallPart = 32;
-constexpr int kBigParts = 64;
 
 __device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, unsigned long long* dp, int32_t* dr,
                             int m, const LocalSmem& L) {
@@ -1088,11 +1087,14 @@ __device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, uns
   {
     constexpr int PER = kMsdBins / kLocalThreads;
     unsigned c[PER], sum = 0;
+    bool big = false;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       c[q] = cur[threadIdx.x * PER + q];
       sum += c[q];
+      big |= c[q] > (unsigned)kSmallPart;
     }
+    if (big) *L.nbig = 1;
     int tot;
     unsigned run = (unsigned)block_exclusive_sum<kLocalThreads>((int)sum, L.scan, &tot);
 #pragma unroll
@@ -1104,6 +1106,16 @@ __device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, uns
     if (threadIdx.x == 0) part[kMsdBins] = (unsigned)m;
   }
   __syncthreads();
+  if (*L.nbig) {
+    // some part is large: the block's LSD over the whole bucket
+    lsd_shared(kA, rA, kB, rB, m, L);
+    for (int i = threadIdx.x; i < m; i += kLocalThreads) {
+      dp[i] = kA[i];
+      dr[i] = rA[i];
+    }
+    __syncthreads();
+    return;
+  }
   for (int i = threadIdx.x; i < m; i += kLocalThreads) {
     const unsigned long long k = kA[i];
     const unsigned pos = atomicAdd(&cur[(k - pmin) >> sh], 1u);
@@ -1111,14 +1123,8 @@ __device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, uns
     rB[pos] = rA[i];
   }
   __syncthreads();
-  // small parts by one thread each; large ones listed
   for (int d = threadIdx.x; d < kMsdBins; d += kLocalThreads) {
     const int p0 = (int)part[d], p1 = (int)part[d + 1];
-    if (p1 - p0 > kSmallPart) {
-      const int at = atomicAdd(L.nbig, 1);
-      if (at < kBigParts) L.big[at] = d;
-      continue;
-    }
     for (int a = p0 + 1; a < p1; ++a) {
       const unsigned long long k = kB[a];
       const int32_t r = rB[a];
@@ -1133,19 +1139,6 @@ __device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, uns
     }
   }
   __syncthreads();
-  const int nbig = *L.nbig;
-  if (nbig <= kBigParts) {
-    for (int q = 0; q < nbig; ++q) {
-      const int d = L.big[q];
-      const int p0 = (int)part[d];
-      lsd_shared(kB + p0, rB + p0, kA + p0, rA + p0, (int)part[d + 1] - p0, L);
-    }
-  } else {
-    for (int d = 0; d < kMsdBins; ++d) {
-      const int p0 = (int)part[d], pm = (int)part[d + 1] - p0;
-      if (pm > kSmallPart) lsd_shared(kB + p0, rB + p0, kA + p0, rA + p0, pm, L);
-    }
-  }
   for (int i = threadIdx.x; i < m; i += kLocalThreads) {
     dp[i] = kB[i];
     dr[i] = rB[i];
@@ -1243,12 +1236,10 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
   __shared__ unsigned long long s_red[2 * kLocalWarps];
   __shared__ unsigned s_part[kRadix + 1];
   __shared__ unsigned s_msd[kMsdBins + 1];
-  __shared__ int s_big[kBigParts];
   __shared__ int s_nbig;
   __shared__ uint32_t s_b;
   LocalSmem L;
   L.part = s_msd;
-  L.big = s_big;
   L.nbig = &s_nbig;
   L.kA = reinterpret_cast<unsigned long long*>(smem);
   L.kB = L.kA + kLocalCap;
