@@ -370,7 +370,7 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
  * and results) whose dimensions of at least 2^20 passing-row candidates
  * have their keys sorted through the learned range partitioner instead of
  * the radix sort: a strided sample of the keys sorted, the network fit to
- * its CDF (cfg: sample size, bucket count (0: about 4096 keys per bucket),
+ * its CDF (cfg: sample size, bucket count (0: 4096 to 8192 keys per bucket),
  * training, knots; heavy keys do not apply to unique keys), every key
  * placed in its bucket and every bucket sorted on chip.  The dimension keys
  * must be unique among the passing rows, as for tqp_star_agg.

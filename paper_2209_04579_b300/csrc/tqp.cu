@@ -384,7 +384,7 @@ constexpr int kSmemBitmapBytes = 184 * 1024;       // shared bitmap of the first
 constexpr int kMaxSmemOptin = 227 * 1024;          // dynamic shared memory one block may opt in to
 constexpr int kHeavyMult = 4;                      // heavy-key sample / training set
 constexpr int64_t kLearnedSortMinRows = 1 << 20;   // star dimensions sorted by the learned partitioner from here
-constexpr int kLearnedSortRowsPerBucket = 4096;
+constexpr int kLearnedSortRowsPerBucket = 8192;  // spread distinct keys: 4096 to 8192 per bucket on average
 constexpr int64_t kSmemBitmapDimRows = 4'000'000;  // first dimensions up to this size try it
 constexpr int kCompactT = 256, kCompactI = 8;
 
