@@ -514,9 +514,6 @@ struct PartArgs {
   KeySet ks;
   const int32_t* sel;       // keys at sel[i] (null: at i)
   const int32_t* payload;   // row id written for key i (null: the key's row)
-  long long* out_val;       // non-null: value column vcol written beside each light row (partition order),
-  const void* vcol;         // and the row's own partition position written as its row id
-  int vdt;
   int64_t n_max;
   const int64_t* d_n;
   const GroupPlan* gp;
@@ -849,12 +846,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
     for (int k = 0; k < kPartItems; ++k)
       if (h[k] == -1) {
         a.out_p[pos[k]] = p[k];
-        if (a.out_val) {
-          a.out_val[pos[k]] = load_as_i64(a.vcol, a.vdt, row[k]);
-          a.out_row[pos[k]] = (int32_t)pos[k];
-        } else {
-          a.out_row[pos[k]] = a.payload ? a.payload[base + k * kPartThreads + threadIdx.x] : (int32_t)row[k];
-        }
+        a.out_row[pos[k]] = a.payload ? a.payload[base + k * kPartThreads + threadIdx.x] : (int32_t)row[k];
       }
     // heavy rows: folded into the block's accumulators
     if (nh) {

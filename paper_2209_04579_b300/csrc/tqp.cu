@@ -736,7 +736,6 @@ struct LearnedWs {
   uint32_t* rheads;
   Partial* rcarry;
   void* lgath[TQP_MAX_VALS];
-  long long* lval;  // the value beside each light row (one simple value column)
 };
 
 // B: the bucket count (0 = from n, about rows_per_bucket rows each).
@@ -794,11 +793,8 @@ LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int ro
     w.rtiles = (n + kReduceThreads * kReduceItems - 1) / (kReduceThreads * kReduceItems);
     w.rheads = c.take<uint32_t>((size_t)(w.rtiles > 0 ? w.rtiles : 1));
     w.rcarry = c.take<Partial>((size_t)(w.rtiles > 0 ? w.rtiles : 1));
-    if (P->simple && P->nvals == 1) {
-      w.lval = c.take<long long>(nn);
-    } else if (n >= kPregatherRows) {
+    if (n >= kPregatherRows)
       for (int v = 0; v < P->nvals; ++v) w.lgath[v] = c.take<char>(nn * dtype_bytes(P->vdt[v]));
-    }
   }
   return w;
 }
@@ -868,11 +864,6 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
   pa.out_row = w.lrow;
   pa.heavy_acc = w.heavy_acc;
   pa.bcount = w.bcount;
-  if (w.lval) {
-    pa.out_val = w.lval;
-    pa.vcol = P.val[0];
-    pa.vdt = P.vdt[0];
-  }
   TQP_CUDA(cudaMemsetAsync(w.count, 0, (size_t)B * sizeof(unsigned), s));
   {
     // the steps live in shared memory when the scatter's layout still fits.
@@ -1031,12 +1022,8 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   r.d_nheavy = &w.lp->nheavy;
   r.heavy_acc = w.heavy_acc;
   AggProgram Pr = P;
-  if (w.lval) {
-    // the values beside the light rows, read through their partition positions
-    // (each bucket's values lie together)
-    Pr.val[0] = w.lval;
-    Pr.vdt[0] = TQP_I64;
-  } else if (w.lgath[0] || P.nvals == 0) {
+  const bool self_gather = P.simple && P.nvals == 1;  // the reduce reads the values through the row ids
+  if ((w.lgath[0] && !self_gather) || P.nvals == 0) {
     if (P.nvals) Pr = pregather_values(P, const_cast<void* const*>(w.lgath), w.lrow, n, w.light_n, s);
     r.rows = nullptr;
   }
