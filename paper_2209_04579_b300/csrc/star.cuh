@@ -380,14 +380,14 @@ __device__ __forceinline__ void ring_flush(WarpRing<F>& q, Drain&& drain) {
 // read; used for small first dimensions, one large block per SM.
 // K32: every dimension key is int32, so the key image, its range test and
 // the cell index are 32-bit arithmetic.
-template <int THREADS, int ITEMS, bool SMEM_BM, bool K32>
+template <int THREADS, int ITEMS, bool SMEM_BM, bool K32, int ND>
 __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(ProbeArgs a, StarAcc Ag, int smem_bm_words) {
   using UK = typename std::conditional<K32, uint32_t, unsigned long long>::type;
   constexpr int WARPS = THREADS / 32;
   // the shared bitmap variant keeps a smaller accumulator array
   constexpr int ACC_WORDS = SMEM_BM ? kSmemAccWords / 4 : kSmemAccWords;
   __shared__ long long s_acc[ACC_WORDS];
-  __shared__ int s_fring[WARPS][(1 + kMaxDims) * 64];  // probe survivors: row, positions
+  __shared__ int s_fring[WARPS][(1 + ND) * 64];  // probe survivors: row, positions
   __shared__ int s_pring[WARPS][64];                   // rows that pass the fact predicates
   // the aggregate program and value references in shared memory: they are
   // indexed by runtime values below (kernel parameters indexed that way are
@@ -423,19 +423,13 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   if (use_smem) {
     for (int i = threadIdx.x; i < S * nacc * copies; i += THREADS) s_acc[i] = acc_identity(A, (i % (S * nacc)) % nacc);
   }
-  DimDir dd[kMaxDims];
-  long long stride[kMaxDims];
-  bool unit[kMaxDims];
+  DimDir dd[ND];
+  long long stride[ND];
+  bool unit[ND];
 #pragma unroll
-  for (int d = 0; d < kMaxDims; ++d) {
-    if (d < a.ndims) {
-      dd[d] = *a.dim[d].dir_plan;
-      stride[d] = plan->stride[d];
-    } else {
-      dd[d].ncells = 0;
-      dd[d].bshift = 0;
-      stride[d] = 0;
-    }
+  for (int d = 0; d < ND; ++d) {
+    dd[d] = *a.dim[d].dir_plan;
+    stride[d] = plan->stride[d];
     unit[d] = dd[d].bshift == 0;
   }
   extern __shared__ uint32_t s_bm[];
@@ -456,11 +450,10 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     return (UK)((unsigned long long)__ldg(static_cast<const long long*>(D.fk) + row) ^ 0x8000000000000000ull);
   };
   // pre: the first dimension's key image u0 is already loaded
-  auto probe = [&](bool live, int64_t row, int (&pos)[kMaxDims], bool pre, UK u0) -> bool {
+  auto probe = [&](bool live, int64_t row, int (&pos)[ND], bool pre, UK u0) -> bool {
 #pragma unroll
-    for (int d = 0; d < kMaxDims; ++d) {
+    for (int d = 0; d < ND; ++d) {
       pos[d] = 0;
-      if (d >= a.ndims) break;
       const ProbeDim& D = a.dim[d];
       UK u = 0, c = 0;
       if (live) {
@@ -507,12 +500,11 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
 
   // 3. fold of one surviving row: group slot from the dimensions' ranks,
   // aggregate expressions, accumulator updates
-  auto fold = [&](bool v, int row, const int (&pos)[kMaxDims]) {
+  auto fold = [&](bool v, int row, const int (&pos)[ND]) {
     if (!v) return;
     long long slot = 0;
 #pragma unroll
-    for (int d = 0; d < kMaxDims; ++d) {
-      if (d >= a.ndims) break;
+    for (int d = 0; d < ND; ++d) {
       const ProbeDim& D = a.dim[d];
       long long r;
       if (unit[d]) r = __ldg(&D.rank_cell[pos[d]]);
@@ -534,8 +526,8 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
           if (src == 0) {
             val = load_as_i64(s_vptr[vi], s_vdt[vi], row);
           } else {
-            const bool cell = src == 1 ? unit[0] : unit[kMaxDims > 1 ? 1 : 0];
-            val = static_cast<const long long*>(cell ? s_vptr_cell[vi] : s_vptr[vi])[src == 1 ? pos[0] : pos[kMaxDims - 1]];
+            const bool cell = src == 1 ? unit[0] : unit[ND - 1];
+            val = static_cast<const long long*>(cell ? s_vptr_cell[vi] : s_vptr[vi])[src == 1 ? pos[0] : pos[ND - 1]];
           }
           ev *= (unsigned long long)A.tmul[e][t] * (unsigned long long)val + (unsigned long long)A.tadd[e][t];
         }
@@ -558,27 +550,27 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     }
   };
 
-  WarpRing<1 + kMaxDims> fq;  // rows that found every dimension: row, positions
+  WarpRing<1 + ND> fq;  // rows that found every dimension: row, positions
   fq.base = s_fring[threadIdx.x >> 5];
   fq.head = fq.n = 0;
   WarpRing<1> pq;  // rows that pass the fact predicates
   pq.base = s_pring[threadIdx.x >> 5];
   pq.head = pq.n = 0;
-  auto drain_fold = [&](const int (&e)[1 + kMaxDims], int cnt) {
-    int pos[kMaxDims];
+  auto drain_fold = [&](const int (&e)[1 + ND], int cnt) {
+    int pos[ND];
 #pragma unroll
-    for (int d = 0; d < kMaxDims; ++d) pos[d] = e[1 + d];
+    for (int d = 0; d < ND; ++d) pos[d] = e[1 + d];
     fold(lane < cnt, e[0], pos);
   };
-  auto push_survivor = [&](bool alive, int row, const int (&pos)[kMaxDims]) {
-    int val[1 + kMaxDims];
+  auto push_survivor = [&](bool alive, int row, const int (&pos)[ND]) {
+    int val[1 + ND];
     val[0] = row;
 #pragma unroll
-    for (int d = 0; d < kMaxDims; ++d) val[1 + d] = pos[d];
+    for (int d = 0; d < ND; ++d) val[1 + d] = pos[d];
     ring_push(fq, alive, val, drain_fold);
   };
   auto drain_probe = [&](const int (&e)[1], int cnt) {
-    int pos[kMaxDims];
+    int pos[ND];
     const bool alive = probe(lane < cnt, e[0], pos, false, (UK)0);
     push_survivor(alive, e[0], pos);
   };
@@ -619,7 +611,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
 #pragma unroll
       for (int j = 0; j < ITEMS / 4; ++j) load4(wt + nwarps, j, nxt);
       const int64_t r0 = wt * WT + (int64_t)lane * ITEMS;
-      int pos[ITEMS][kMaxDims];
+      int pos[ITEMS][ND];
       bool alive[ITEMS];
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) alive[k] = probe(r0 + k < a.n_fact, r0 + k, pos[k], true, cur[k]);
@@ -645,7 +637,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
         const int64_t r = wn * WT + k * 32 + lane;
         nxt[k] = (wn < nwt && r < a.n_fact) ? fk_image(0, r) : (UK)0;
       }
-      int pos[ITEMS][kMaxDims];
+      int pos[ITEMS][ND];
       bool alive[ITEMS];
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {

@@ -1394,23 +1394,28 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     prof_mark(1, true, s);
     bool k32 = true;
     for (int d = 0; d < ndims; ++d) k32 = k32 && dims[d].key.dtype == TQP_I32;
+    using ProbeFn = void (*)(ProbeArgs, StarAcc, int);
     if (dims[0].n <= kSmemBitmapDimRows) {
       // small first dimension: its bitmap can live in shared memory
-      auto pk = k32 ? star_probe_kernel<1024, 4, true, true> : star_probe_kernel<1024, 4, true, false>;
+      const ProbeFn v[2][2] = {{star_probe_kernel<1024, 4, true, false, 1>, star_probe_kernel<1024, 4, true, true, 1>},
+                               {star_probe_kernel<1024, 4, true, false, 2>, star_probe_kernel<1024, 4, true, true, 2>}};
+      const ProbeFn pk = v[ndims - 1][k32 ? 1 : 0];
       const int words = kSmemBitmapBytes / 4;
       static bool attr = false;
       if (!attr) {
-        cudaFuncSetAttribute(star_probe_kernel<1024, 4, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSmemBitmapBytes);
-        cudaFuncSetAttribute(star_probe_kernel<1024, 4, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSmemBitmapBytes);
+        for (int i = 0; i < 2; ++i)
+          for (int j = 0; j < 2; ++j)
+            cudaFuncSetAttribute(v[i][j], cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBitmapBytes);
         attr = true;
       }
       const int64_t t1024 = (n_fact + 1024 * 4 - 1) / (1024 * 4);
       pk<<<persistent_grid(pk, 1024, kSmemBitmapBytes, t1024), 1024, kSmemBitmapBytes, s>>>(pa, A, words);
       note_launch();
     } else {
-      auto pk = k32 ? star_probe_kernel<kProbeT, kProbeI, false, true> : star_probe_kernel<kProbeT, kProbeI, false, false>;
+      const ProbeFn v[2][2] = {
+          {star_probe_kernel<kProbeT, kProbeI, false, false, 1>, star_probe_kernel<kProbeT, kProbeI, false, true, 1>},
+          {star_probe_kernel<kProbeT, kProbeI, false, false, 2>, star_probe_kernel<kProbeT, kProbeI, false, true, 2>}};
+      const ProbeFn pk = v[ndims - 1][k32 ? 1 : 0];
       pk<<<persistent_grid(pk, kProbeT, 0, ptiles), kProbeT, 0, s>>>(pa, A, 0); note_launch();
     }
     prof_mark(1, false, s);
