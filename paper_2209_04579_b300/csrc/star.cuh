@@ -278,17 +278,52 @@ __global__ void dir_cells_kernel(CellArgs a) {
   }
 }
 
+// Wide cells (bshift > 0) get a table of one 32-byte record per cell, so
+// that a probe reads one record instead of the directory entry and then the
+// keys it points to.  The record holds the cell's first keys inline with
+// their group ranks, its first sorted position lo and its key count cnt:
+//   int32 keys: a = {img0, img1, img2, rank0}, b = {rank1, rank2, lo, cnt}
+//   int64 keys: a = {img0 (2 words), img1 (2 words)}, b = {rank0, rank1, lo, cnt}
+// A cell with more keys than fit inline keeps the rest in the sorted
+// key/rank pairs, after position lo + inline count.
+struct __align__(16) DirCell {
+  int4 a, b;
+};
+__host__ __device__ constexpr int cell_inline(bool k32) { return k32 ? 3 : 2; }
+
+__global__ void dir_table_kernel(const void* kr, int key_dt, const DimDir* dd, const int* dir, DirCell* table) {
+  const DimDir r = *dd;
+  if (r.bshift == 0 || r.ncells == 0) return;
+  const bool k32 = key_dt == TQP_I32;
+  const int cap = cell_inline(k32);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < r.ncells; c += stride) {
+    const int lo = dir[c], cnt = dir[c + 1] - lo;
+    uint32_t w[8] = {0, 0, 0, 0, 0, 0, (uint32_t)lo, (uint32_t)cnt};
+    for (int j = 0; j < cap && j < cnt; ++j) {
+      if (k32) {
+        const KeyRank32 e = static_cast<const KeyRank32*>(kr)[lo + j];
+        w[j] = e.image;
+        w[3 + j] = (uint32_t)e.rank;
+      } else {
+        const KeyRank64 e = static_cast<const KeyRank64*>(kr)[lo + j];
+        w[2 * j] = (uint32_t)e.image;
+        w[2 * j + 1] = (uint32_t)(e.image >> 32);
+        w[4 + j] = (uint32_t)e.rank;
+      }
+    }
+    table[c].a = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+    table[c].b = make_int4((int)w[4], (int)w[5], (int)w[6], (int)w[7]);
+  }
+}
+
 struct ProbeDim {
-  const void* skeys;   // sorted passing keys (int32 or int64)
-  const void* kr;      // the same keys' images with their group ranks (KeyRank32 / KeyRank64)
+  const void* kr;      // sorted passing keys' images with their group ranks (KeyRank32 / KeyRank64)
   int key_dt;
-  int64_t n_max;
-  const int64_t* d_n;
-  const int32_t* rank_sorted;
   const int32_t* rank_cell;
   const void* fk;      // fact foreign-key column (same dtype as the key)
   const DimDir* dir_plan;
-  const int* dir;
+  const DirCell* table;
   const uint32_t* bitmap;
 };
 
@@ -387,7 +422,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   // the shared bitmap variant keeps a smaller accumulator array
   constexpr int ACC_WORDS = SMEM_BM ? kSmemAccWords / 4 : kSmemAccWords;
   __shared__ long long s_acc[ACC_WORDS];
-  __shared__ int s_fring[WARPS][(1 + ND) * 64];  // probe survivors: row, positions
+  __shared__ int s_fring[WARPS][(2 + ND) * 64];  // probe survivors: row, slot, positions
   __shared__ int s_pring[WARPS][64];                   // rows that pass the fact predicates
   // the aggregate program and value references in shared memory: they are
   // indexed by runtime values below (kernel parameters indexed that way are
@@ -442,95 +477,132 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   }
   __syncthreads();
 
-  // 2. probe of one fact row through every dimension
-  // image of the fact key of dimension d at row
+  // 2. probe of one fact row through every dimension.  The dimensions'
+  // foreign keys load together, then their wide cells' records (after the
+  // cell bit where a bitmap is tested), so a row waits on two dependent reads
+  // whatever the number of dimensions.  pos: the sorted position (the cell of
+  // a unit-width dimension); slot: the sum of rank * stride over the wide
+  // dimensions (a unit cell's rank is read by the fold, on compacted rows).
+  // pre: the first dimension's key image u0 is already loaded.
   auto fk_image = [&](int d, int64_t row) -> UK {
     const ProbeDim& D = a.dim[d];
     if (K32 || D.key_dt == TQP_I32) return (UK)((uint32_t)__ldg(static_cast<const int32_t*>(D.fk) + row) ^ 0x80000000u);
     return (UK)((unsigned long long)__ldg(static_cast<const long long*>(D.fk) + row) ^ 0x8000000000000000ull);
   };
-  // pre: the first dimension's key image u0 is already loaded
-  auto probe = [&](bool live, int64_t row, int (&pos)[ND], bool pre, UK u0) -> bool {
+  // The keys of a wide cell beyond its inline ones: the first key >= x in
+  // kr[l, h), narrowed while the interval is long, then scanned.
+  auto overflow = [&](int d, UK x, int l, const int hi, int& rk) -> int {
+    const bool k32d = K32 || a.dim[d].key_dt == TQP_I32;
+    auto img = [&](int i) -> UK {
+      return k32d ? (UK)__ldg(&static_cast<const KeyRank32*>(a.dim[d].kr)[i].image)
+                  : (UK)__ldg(&static_cast<const KeyRank64*>(a.dim[d].kr)[i].image);
+    };
+    int h = hi;
+    while (h - l > 4) {
+      const int mid = (l + h) >> 1;
+      if (img(mid) < x) l = mid + 1; else h = mid;
+    }
+    for (int i = l; i < hi; ++i) {
+      const UK ki = img(i);
+      if (ki >= x) {
+        if (ki != x) return -1;
+        rk = k32d ? __ldg(&static_cast<const KeyRank32*>(a.dim[d].kr)[i].rank)
+                  : (int)__ldg(&static_cast<const KeyRank64*>(a.dim[d].kr)[i].rank);
+        return i;
+      }
+    }
+    return -1;
+  };
+  auto probe = [&](bool live, int64_t row, int (&pos)[ND], int& slot, bool pre, UK u0) -> bool {
+    UK u[ND], c[ND];
+    bool lv[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-      pos[d] = 0;
-      const ProbeDim& D = a.dim[d];
-      UK u = 0, c = 0;
-      if (live) {
-        u = (d == 0 && pre) ? u0 : fk_image(d, row);
-        if (u < (UK)dd[d].umin || u > (UK)dd[d].umax) live = false;
-        else c = (u - (UK)dd[d].umin) >> dd[d].bshift;
+      u[d] = 0;
+      if (live) u[d] = (d == 0 && pre) ? u0 : fk_image(d, row);
+    }
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      lv[d] = live && u[d] >= (UK)dd[d].umin && u[d] <= (UK)dd[d].umax;
+      c[d] = lv[d] ? (u[d] - (UK)dd[d].umin) >> dd[d].bshift : (UK)0;
+    }
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      if (lv[d] && dd[d].use_bits) {
+        const uint32_t w = (SMEM_BM && d == 0 && sbm) ? s_bm[c[d] >> 5] : __ldg(&a.dim[d].bitmap[c[d] >> 5]);
+        lv[d] = (w >> (c[d] & 31)) & 1u;
       }
-      if (live && dd[d].use_bits) {
-        const uint32_t w = (SMEM_BM && d == 0 && sbm) ? s_bm[c >> 5] : __ldg(&D.bitmap[c >> 5]);
-        live = (w >> (c & 31)) & 1u;
+    }
+    int4 ra[ND], rb[ND];
+    int rk[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      ra[d] = rb[d] = make_int4(0, 0, 0, 0);
+      rk[d] = 0;
+      if (lv[d] && !unit[d]) {
+        ra[d] = __ldg(&a.dim[d].table[c[d]].a);
+        rb[d] = __ldg(&a.dim[d].table[c[d]].b);
       }
-      if (unit[d]) {  // unit-width cell: the bit proves the key
-        pos[d] = (int)c;
-        continue;
-      }
-      if (live) {
-        // first key >= u lies in [l, h]; narrow while the interval is long,
-        // then scan forward from l up to the cell's end
-        const int lo = __ldg(&D.dir[c]), hi = __ldg(&D.dir[c + 1]);
-        const bool k32d = K32 || D.key_dt == TQP_I32;
-        auto img = [&](int i) -> UK {
-          return k32d ? (UK)__ldg(&static_cast<const KeyRank32*>(D.kr)[i].image)
-                      : (UK)__ldg(&static_cast<const KeyRank64*>(D.kr)[i].image);
-        };
-        int l = lo, h = hi;
-        while (h - l > 4) {
-          int mid = (l + h) >> 1;
-          if (img(mid) < u) l = mid + 1; else h = mid;
-        }
+    }
+    bool all = live;
+    int sl = 0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      pos[d] = (int)c[d];
+      if (!unit[d]) {
+        // match the inline keys; a key above the last inline one of a fuller
+        // cell is searched among the cell's remaining sorted keys
+        const int lo = rb[d].z, cnt = rb[d].w;
         int found = -1;
-        for (int i = l; i < hi; ++i) {
-          const UK ki = img(i);
-          if (ki >= u) {
-            if (ki == u) found = i;
-            break;
-          }
+        if (K32 || a.dim[d].key_dt == TQP_I32) {
+          const uint32_t x = (uint32_t)u[d];
+          if (cnt > 0 && (uint32_t)ra[d].x == x) { found = lo; rk[d] = ra[d].w; }
+          else if (cnt > 1 && (uint32_t)ra[d].y == x) { found = lo + 1; rk[d] = rb[d].x; }
+          else if (cnt > 2 && (uint32_t)ra[d].z == x) { found = lo + 2; rk[d] = rb[d].y; }
+          else if (cnt > 3 && x > (uint32_t)ra[d].z) found = overflow(d, u[d], lo + 3, lo + cnt, rk[d]);
+        } else {
+          const unsigned long long x = (unsigned long long)u[d];
+          const unsigned long long i0 = (unsigned long long)(uint32_t)ra[d].x | ((unsigned long long)(uint32_t)ra[d].y << 32);
+          const unsigned long long i1 = (unsigned long long)(uint32_t)ra[d].z | ((unsigned long long)(uint32_t)ra[d].w << 32);
+          if (cnt > 0 && i0 == x) { found = lo; rk[d] = rb[d].x; }
+          else if (cnt > 1 && i1 == x) { found = lo + 1; rk[d] = rb[d].y; }
+          else if (cnt > 2 && x > i1) found = overflow(d, u[d], lo + 2, lo + cnt, rk[d]);
         }
-        live = found >= 0;
+        lv[d] = lv[d] && found >= 0;
         pos[d] = found;
       }
+      all = all && lv[d];
+      sl += rk[d] * (int)stride[d];
     }
-    return live;
+    slot = sl;
+    return all;
   };
 
-  // 3. fold of one surviving row: group slot from the dimensions' ranks,
-  // aggregate expressions, accumulator updates
-  auto fold = [&](bool v, int row, const int (&pos)[ND]) {
+  // 3. fold of one surviving row: aggregate expressions, accumulator updates
+  // in its group's slot
+  auto term_value = [&](int vi, int row, const int (&pos)[ND]) -> long long {
+    const int src = s_vsrc[vi];
+    if (src == 0) return load_as_i64(s_vptr[vi], s_vdt[vi], row);
+    const bool cell = src == 1 ? unit[0] : unit[ND - 1];
+    return static_cast<const long long*>(cell ? s_vptr_cell[vi] : s_vptr[vi])[src == 1 ? pos[0] : pos[ND - 1]];
+  };
+  auto fold = [&](bool v, int row, int slot, const int (&pos)[ND]) {
     if (!v) return;
-    long long slot = 0;
+    int urk[ND];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      const ProbeDim& D = a.dim[d];
-      long long r;
-      if (unit[d]) r = __ldg(&D.rank_cell[pos[d]]);
-      else if (K32 || D.key_dt == TQP_I32) r = __ldg(&static_cast<const KeyRank32*>(D.kr)[pos[d]].rank);
-      else r = __ldg(&static_cast<const KeyRank64*>(D.kr)[pos[d]].rank);
-      slot += r * stride[d];
-    }
-    long long* dst = use_smem ? my_acc + slot * nacc : a.acc + slot * nacc;
+    for (int d = 0; d < ND; ++d) urk[d] = unit[d] ? __ldg(&a.dim[d].rank_cell[pos[d]]) : 0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) slot += urk[d] * (int)stride[d];
+    long long* dst = use_smem ? my_acc + (long long)slot * nacc : a.acc + (long long)slot * nacc;
     for (int q = 0; q < A.naggs; ++q) {
       long long x = 1;
       const int op = A.op[q];
       if (op != TQP_COUNT) {
         const int e = A.expr[q];
         unsigned long long ev = 1;
-        for (int t = 0; t < A.nterms[e]; ++t) {
-          const int vi = A.tval[e][t];
-          const int src = s_vsrc[vi];
-          long long val;
-          if (src == 0) {
-            val = load_as_i64(s_vptr[vi], s_vdt[vi], row);
-          } else {
-            const bool cell = src == 1 ? unit[0] : unit[ND - 1];
-            val = static_cast<const long long*>(cell ? s_vptr_cell[vi] : s_vptr[vi])[src == 1 ? pos[0] : pos[ND - 1]];
-          }
-          ev *= (unsigned long long)A.tmul[e][t] * (unsigned long long)val + (unsigned long long)A.tadd[e][t];
-        }
+        for (int t = 0; t < A.nterms[e]; ++t)
+          ev *= (unsigned long long)A.tmul[e][t] * (unsigned long long)term_value(A.tval[e][t], row, pos) +
+                (unsigned long long)A.tadd[e][t];
         x = (long long)ev;
       }
       unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dst + q);
@@ -550,29 +622,47 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     }
   };
 
-  WarpRing<1 + ND> fq;  // rows that found every dimension: row, positions
+  WarpRing<2 + ND> fq;  // rows that found every dimension: row, slot, positions
   fq.base = s_fring[threadIdx.x >> 5];
   fq.head = fq.n = 0;
   WarpRing<1> pq;  // rows that pass the fact predicates
   pq.base = s_pring[threadIdx.x >> 5];
   pq.head = pq.n = 0;
-  auto drain_fold = [&](const int (&e)[1 + ND], int cnt) {
+  auto drain_fold = [&](const int (&e)[2 + ND], int cnt) {
     int pos[ND];
 #pragma unroll
-    for (int d = 0; d < ND; ++d) pos[d] = e[1 + d];
-    fold(lane < cnt, e[0], pos);
+    for (int d = 0; d < ND; ++d) pos[d] = e[2 + d];
+    fold(lane < cnt, e[0], e[1], pos);
   };
-  auto push_survivor = [&](bool alive, int row, const int (&pos)[ND]) {
-    int val[1 + ND];
+  auto push_survivor = [&](bool alive, int row, int slot, const int (&pos)[ND]) {
+    int val[2 + ND];
     val[0] = row;
+    val[1] = slot;
 #pragma unroll
-    for (int d = 0; d < ND; ++d) val[1 + d] = pos[d];
+    for (int d = 0; d < ND; ++d) val[2 + d] = pos[d];
     ring_push(fq, alive, val, drain_fold);
   };
   auto drain_probe = [&](const int (&e)[1], int cnt) {
-    int pos[ND];
-    const bool alive = probe(lane < cnt, e[0], pos, false, (UK)0);
-    push_survivor(alive, e[0], pos);
+    int pos[ND], slot;
+    const bool alive = probe(lane < cnt, e[0], pos, slot, false, (UK)0);
+    push_survivor(alive, e[0], slot, pos);
+  };
+  // Pushes a tile's ITEMS probed rows (row0 + k * rstep) in a rolled loop:
+  // the fold behind the queue then exists once in the loop's code (the
+  // instruction cache holds the whole loop).  Each step takes item 0 and
+  // shifts the rest down, so the arrays stay in registers.
+  auto push_items = [&](bool (&alive)[ITEMS], int (&slot)[ITEMS], int (&pos)[ITEMS][ND], int row0, int rstep) {
+#pragma unroll 1
+    for (int k = 0; k < ITEMS; ++k) {
+      push_survivor(alive[0], row0 + k * rstep, slot[0], pos[0]);
+#pragma unroll
+      for (int j = 0; j + 1 < ITEMS; ++j) {
+        alive[j] = alive[j + 1];
+        slot[j] = slot[j + 1];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) pos[j][d] = pos[j + 1][d];
+      }
+    }
   };
 
   // 1. every warp walks its own tiles of 32 x ITEMS rows (no block barrier
@@ -611,12 +701,11 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
 #pragma unroll
       for (int j = 0; j < ITEMS / 4; ++j) load4(wt + nwarps, j, nxt);
       const int64_t r0 = wt * WT + (int64_t)lane * ITEMS;
-      int pos[ITEMS][ND];
+      int pos[ITEMS][ND], slot[ITEMS];
       bool alive[ITEMS];
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k) alive[k] = probe(r0 + k < a.n_fact, r0 + k, pos[k], true, cur[k]);
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k) push_survivor(alive[k], (int)(r0 + k), pos[k]);
+      for (int k = 0; k < ITEMS; ++k) alive[k] = probe(r0 + k < a.n_fact, r0 + k, pos[k], slot[k], true, cur[k]);
+      push_items(alive, slot, pos, (int)r0, 1);
     }
   } else if (a.npred == 0) {
     // every row goes to the probe; the next tile's first-dimension keys are
@@ -637,15 +726,14 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
         const int64_t r = wn * WT + k * 32 + lane;
         nxt[k] = (wn < nwt && r < a.n_fact) ? fk_image(0, r) : (UK)0;
       }
-      int pos[ITEMS][ND];
+      int pos[ITEMS][ND], slot[ITEMS];
       bool alive[ITEMS];
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
         const int64_t r = wt * WT + k * 32 + lane;
-        alive[k] = probe(r < a.n_fact, r, pos[k], true, cur[k]);
+        alive[k] = probe(r < a.n_fact, r, pos[k], slot[k], true, cur[k]);
       }
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k) push_survivor(alive[k], (int)(wt * WT + k * 32 + lane), pos[k]);
+      push_items(alive, slot, pos, (int)(wt * WT + lane), 32);
     }
   } else {
     // fact predicates, then the passing rows into the probe queue.  Warp
@@ -658,18 +746,22 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
         wt = __shfl_sync(0xffffffffu, tk, 0);
       }
       if (wt >= nwt) break;
-      bool pass[ITEMS];
+      unsigned pass = 0;  // bit k: row k * 32 + lane of the tile
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k) pass[k] = wt * WT + k * 32 + lane < a.n_fact;
+      for (int k = 0; k < ITEMS; ++k) pass |= (unsigned)(wt * WT + k * 32 + lane < a.n_fact) << k;
       for (int p = 0; p < a.npred; ++p) {
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k)
-          if (pass[k]) pass[k] = compare(load_as_i64(a.pcol[p], a.pdt[p], wt * WT + k * 32 + lane), a.pop[p], a.plit[p]);
+          if ((pass >> k) & 1u)
+            if (!compare(load_as_i64(a.pcol[p], a.pdt[p], wt * WT + k * 32 + lane), a.pop[p], a.plit[p]))
+              pass &= ~(1u << k);
       }
-#pragma unroll
+      // one rolled loop, so that the probe and the fold behind the queue
+      // exist once in the loop's code
+#pragma unroll 1
       for (int k = 0; k < ITEMS; ++k) {
         const int val[1] = {(int)(wt * WT + k * 32 + lane)};
-        ring_push(pq, pass[k], val, drain_probe);
+        ring_push(pq, (pass >> k) & 1u, val, drain_probe);
       }
     }
   }

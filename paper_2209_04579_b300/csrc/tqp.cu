@@ -380,7 +380,7 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
 constexpr int kFilterT = 256, kFilterI = 16;
 constexpr int kRankT = 256, kRankI = 8;
 constexpr int kProbeT = 256, kProbeI = 8;
-constexpr int kSmemBitmapBytes = 184 * 1024;       // shared bitmap of the first dimension
+constexpr int kSmemBitmapBytes = 184 * 1024;       // shared bitmap of the first dimension (at most)
 constexpr int kMaxSmemOptin = 227 * 1024;          // dynamic shared memory one block may opt in to
 constexpr int kHeavyMult = 4;                      // heavy-key sample / training set
 constexpr int64_t kLearnedSortMinRows = 1 << 20;   // star dimensions sorted by the learned partitioner from here
@@ -1067,6 +1067,7 @@ struct StarDimWs {
   int* dir;
   uint32_t* bitmap;
   int log2cells;
+  DirCell* table;
   int32_t* rank_cell;
   long long* dval_cell[TQP_MAX_VALS];
 };
@@ -1198,6 +1199,12 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     w.dplan = c.take<DimDir>(1);
     w.dir = c.take<int>((size_t)(1ll << w.log2cells) + 2);
     w.bitmap = c.take<uint32_t>((size_t)(1ll << w.log2cells) / 32 + 1);
+    {
+      // wide cells number at most 2^t with 2^t >= 2 x the dimension's rows
+      int t = 1;
+      while (t < w.log2cells && (1ll << t) < 2 * D.n) ++t;
+      w.table = c.take<DirCell>((size_t)(1ll << t) + 1);
+    }
     w.rank_cell = c.take<int32_t>((size_t)(1ll << w.log2cells) + 1);
     for (int v = 0; v < nvals; ++v)
       if (vals[v].src == d + 1) w.dval_cell[v] = c.take<long long>((size_t)(1ll << w.log2cells) + 1);
@@ -1343,6 +1350,12 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
         ++ca.nv;
       }
       dir_cells_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(ca); note_launch();
+      {
+        int t = 1;
+        while (t < w.log2cells && (1ll << t) < 2 * D.n) ++t;
+        dir_table_kernel<<<stride_grid((1ll << t) + 1, 256), 256, 0, s>>>(w.kr, D.key.dtype, w.dplan, w.dir, w.table);
+        note_launch();
+      }
     }
   }
   // ---- slots, accumulators, probe, compaction
@@ -1356,16 +1369,12 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
   pa.ndims = ndims;
   pa.vec0 = dims[0].key.dtype == TQP_I32 && reinterpret_cast<uintptr_t>(fact_cols[fk_col[0]].data) % 16 == 0;
   for (int d = 0; d < ndims; ++d) {
-    pa.dim[d].skeys = W[d].skeys;
     pa.dim[d].kr = W[d].kr;
     pa.dim[d].key_dt = dims[d].key.dtype;
-    pa.dim[d].n_max = dims[d].n;
-    pa.dim[d].d_n = dims[d].npred ? W[d].cnt : nullptr;
-    pa.dim[d].rank_sorted = W[d].rank_sorted;
     pa.dim[d].rank_cell = W[d].rank_cell;
     pa.dim[d].fk = fact_cols[fk_col[d]].data;
     pa.dim[d].dir_plan = W[d].dplan;
-    pa.dim[d].dir = W[d].dir;
+    pa.dim[d].table = W[d].table;
     pa.dim[d].bitmap = W[d].bitmap;
   }
   pa.npred = nfact_preds;
@@ -1400,16 +1409,25 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       const ProbeFn v[2][2] = {{star_probe_kernel<1024, 4, true, false, 1>, star_probe_kernel<1024, 4, true, true, 1>},
                                {star_probe_kernel<1024, 4, true, false, 2>, star_probe_kernel<1024, 4, true, true, 2>}};
       const ProbeFn pk = v[ndims - 1][k32 ? 1 : 0];
-      const int words = kSmemBitmapBytes / 4;
+      // the bitmap takes what the variant's static shared memory leaves of
+      // the opt-in maximum, up to kSmemBitmapBytes
+      static int dyn[2][2];
       static bool attr = false;
       if (!attr) {
         for (int i = 0; i < 2; ++i)
-          for (int j = 0; j < 2; ++j)
-            cudaFuncSetAttribute(v[i][j], cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBitmapBytes);
+          for (int j = 0; j < 2; ++j) {
+            cudaFuncAttributes fa;
+            TQP_CUDA(cudaFuncGetAttributes(&fa, v[i][j]));
+            int b = kMaxSmemOptin - (int)fa.sharedSizeBytes;
+            b = (b < kSmemBitmapBytes ? b : kSmemBitmapBytes) & ~255;
+            TQP_CUDA(cudaFuncSetAttribute(v[i][j], cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+            dyn[i][j] = b;
+          }
         attr = true;
       }
+      const int bytes = dyn[ndims - 1][k32 ? 1 : 0];
       const int64_t t1024 = (n_fact + 1024 * 4 - 1) / (1024 * 4);
-      pk<<<persistent_grid(pk, 1024, kSmemBitmapBytes, t1024), 1024, kSmemBitmapBytes, s>>>(pa, A, words);
+      pk<<<persistent_grid(pk, 1024, bytes, t1024), 1024, bytes, s>>>(pa, A, bytes / 4);
       note_launch();
     } else {
       const ProbeFn v[2][2] = {
