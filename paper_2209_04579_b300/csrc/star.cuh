@@ -106,6 +106,93 @@ __global__ void __launch_bounds__(THREADS) rank_kernel(const K* sorted, const in
   }
 }
 
+// ---- group ranks of one dimension over a small value domain: the group
+// column's passing values span at most 2^kDomBits (kmax - kmin < 2^24, the
+// case of every int8 and int16 column).  A bitmap marks the values present;
+// the dense rank of v is the number of marked values below it, read from a
+// per-word prefix count and one popcount.  No sort and no scatter by row.
+constexpr int kDomBits = 24;
+constexpr int kDomSmemWords = 2048;  // domains up to 2^16 values are marked in shared memory first
+
+struct DomPlan {
+  int on;       // 1: the domain path gives the ranks (the sort path then runs on no rows)
+  int words;    // bitmap words over [kmin, kmax]
+  long long kmin;
+};
+
+__global__ void dom_plan_kernel(const GroupPlan* gp, int64_t n_max, const int64_t* d_n, DomPlan* dp,
+                                int64_t* sort_n) {
+  if (threadIdx.x != 0) return;
+  const int64_t n = clamp_n(n_max, d_n);
+  DomPlan r;
+  r.on = n > 0 && !gp->unsupported && gp->bits[0] <= kDomBits;
+  r.kmin = gp->kmin[0];
+  r.words = r.on ? (int)(((unsigned long long)gp->kmax[0] - (unsigned long long)gp->kmin[0]) >> 5) + 1 : 0;
+  *dp = r;
+  *sort_n = r.on ? 0 : n;
+}
+
+__global__ void __launch_bounds__(256) dom_mark_kernel(const void* gcol, int gdt, const int32_t* sel, int64_t n_max,
+                                                       const int64_t* d_n, const DomPlan* dp, uint32_t* bits) {
+  __shared__ uint32_t s_bits[kDomSmemWords];
+  const DomPlan p = *dp;
+  if (!p.on) return;
+  const int64_t n = clamp_n(n_max, d_n);
+  const bool shared = p.words <= kDomSmemWords;
+  if (shared) {
+    for (int i = threadIdx.x; i < p.words; i += blockDim.x) s_bits[i] = 0;
+    __syncthreads();
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t row = sel ? sel[i] : i;
+    const unsigned long long v = (unsigned long long)load_as_i64(gcol, gdt, row) - (unsigned long long)p.kmin;
+    const uint32_t w = (uint32_t)(v >> 5), b = 1u << (v & 31);
+    if (shared) {
+      if (!(s_bits[w] & b)) atomicOr(&s_bits[w], b);
+    } else if (!(__ldcg(&bits[w]) & b)) {
+      atomicOr(&bits[w], b);
+    }
+  }
+  if (shared) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < p.words; i += blockDim.x)
+      if (s_bits[i]) atomicOr(&bits[i], s_bits[i]);
+  }
+}
+
+// One block: exclusive prefix counts per bitmap word, the group key value of
+// every rank, and the number of groups.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) dom_scan_kernel(const DomPlan* dp, const uint32_t* bits, int* pre,
+                                                           long long* gkey, long long* d_G) {
+  __shared__ int s_scan[33];
+  const DomPlan p = *dp;
+  if (!p.on) return;
+  const int per = (p.words + THREADS - 1) / THREADS;
+  const int w0 = threadIdx.x * per, w1 = min(p.words, w0 + per);
+  int cnt = 0;
+  for (int w = w0; w < w1; ++w) cnt += __popc(bits[w]);
+  int total;
+  int r = block_exclusive_sum<THREADS>(cnt, s_scan, &total);
+  for (int w = w0; w < w1; ++w) {
+    pre[w] = r;
+    uint32_t m = bits[w];
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      gkey[r++] = p.kmin + (long long)w * 32 + b;
+    }
+  }
+  if (threadIdx.x == 0) *d_G = total;
+}
+
+__device__ __forceinline__ int32_t dom_rank(const DomPlan& p, const uint32_t* bits, const int* pre, long long v) {
+  const unsigned long long x = (unsigned long long)v - (unsigned long long)p.kmin;
+  const uint32_t w = (uint32_t)(x >> 5);
+  return pre[w] + __popc(bits[w] & ((1u << (x & 31)) - 1u));
+}
+
 // ---- gather ranks and aggregated dimension columns into key order; check
 // that keys are unique among the passing rows.
 struct PregatherArgs {
@@ -115,6 +202,12 @@ struct PregatherArgs {
   int64_t n_max;
   const int64_t* d_n;
   const int32_t* rank_of_row;  // null: no group column
+  // the domain path (dom->on): rank of the row's group value in the bitmap
+  const DomPlan* dom;
+  const void* gcol;
+  int gdt;
+  const uint32_t* dbits;
+  const int* dpre;
   int32_t* rank_sorted;
   void* kr;                    // KeyRank32 (int32 keys) or KeyRank64 per sorted position
   int nv;
@@ -127,9 +220,14 @@ struct PregatherArgs {
 __global__ void star_pregather_kernel(PregatherArgs a) {
   const int64_t n = clamp_n(a.n_max, a.d_n);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  DomPlan dom;
+  dom.on = 0;
+  if (a.dom) dom = *a.dom;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
     int32_t row = a.srows[p];
-    const int32_t rk = a.rank_of_row ? a.rank_of_row[row] : 0;
+    const int32_t rk = !a.rank_of_row ? 0
+                       : dom.on      ? dom_rank(dom, a.dbits, a.dpre, load_as_i64(a.gcol, a.gdt, row))
+                                     : a.rank_of_row[row];
     a.rank_sorted[p] = rk;
     if (a.key_dt == TQP_I32)
       static_cast<KeyRank32*>(a.kr)[p] = KeyRank32{(uint32_t)key_image(a.skeys, a.key_dt, p), rk};

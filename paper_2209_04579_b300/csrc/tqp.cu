@@ -1057,6 +1057,11 @@ struct StarDimWs {
   int32_t* rank_of_row;
   long long* gkey;
   long long* G;
+  DomPlan* dom;          // group ranks over a small value domain
+  int64_t* sort_n;       // rows the sort path ranks (0 when the domain path does)
+  uint32_t* dbits;
+  int* dpre;
+  int dwords;
   int32_t* rank_sorted;
   void* kr;
   long long* dval[TQP_MAX_VALS];
@@ -1188,6 +1193,14 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       w.rcounter = c.take<uint32_t>(1);
       w.rank_of_row = c.take<int32_t>(nn);
       w.gkey = c.take<long long>(nn);
+      {
+        const int b = 8 * dtype_bytes(D.group.dtype) < kDomBits ? 8 * dtype_bytes(D.group.dtype) : kDomBits;
+        w.dwords = 1 << (b - 5);
+      }
+      w.dom = c.take<DomPlan>(1);
+      w.sort_n = c.take<int64_t>(1);
+      w.dbits = c.take<uint32_t>((size_t)w.dwords);
+      w.dpre = c.take<int>((size_t)w.dwords);
       w.G = c.take<long long>(1);
     }
     w.rank_sorted = c.take<int32_t>(nn);
@@ -1281,14 +1294,18 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       gb_init_kernel<<<1, 32, 0, s>>>(w.gplan); note_launch();
       gb_keyrange_kernel<256><<<stride_grid(D.n, 256, 4), 256, 0, s>>>(ks, w.sel, D.n, dcnt, w.gplan); note_launch();
       gb_plan_kernel<<<1, 32, 0, s>>>(w.gplan, 1, w.gword * 8); note_launch();
+      // a small value domain ranks through a bitmap; otherwise the packed
+      // group keys are sorted and ranked (sort_n: the rows of that path)
+      dom_plan_kernel<<<1, 32, 0, s>>>(w.gplan, D.n, dcnt, w.dom, w.sort_n); note_launch();
+      const int64_t* gn = w.sort_n;
       int g = stride_grid(D.n, 256);
       if (w.gword == 4) {
-        gb_encode_kernel<uint32_t><<<g, 256, 0, s>>>(ks, w.sel, D.n, dcnt, w.gplan, (uint32_t*)w.packed, w.prow); note_launch();
+        gb_encode_kernel<uint32_t><<<g, 256, 0, s>>>(ks, w.sel, D.n, gn, w.gplan, (uint32_t*)w.packed, w.prow); note_launch();
       } else {
-        gb_encode_kernel<unsigned long long><<<g, 256, 0, s>>>(ks, w.sel, D.n, dcnt, w.gplan,
+        gb_encode_kernel<unsigned long long><<<g, 256, 0, s>>>(ks, w.sel, D.n, gn, w.gplan,
                                                                (unsigned long long*)w.packed, w.prow); note_launch();
       }
-      st = run_sort(w.gsort, w.gword == 4 ? kKeyU32 : kKeyU64, w.packed, w.prow, w.spacked, w.sprow, D.n, dcnt, 0,
+      st = run_sort(w.gsort, w.gword == 4 ? kKeyU32 : kKeyU64, w.packed, w.prow, w.spacked, w.sprow, D.n, gn, 0,
                     w.gword * 8, s);
       if (st != TQP_OK) return st;
       TQP_CUDA(cudaMemsetAsync(w.rstatus, 0, (size_t)w.rtiles * 8, s));
@@ -1296,14 +1313,19 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       if (w.gword == 4) {
         auto rk = rank_kernel<uint32_t, kRankT, kRankI>;
         rk<<<persistent_grid(rk, kRankT, 0, w.rtiles), kRankT, 0, s>>>(
-            (const uint32_t*)w.spacked, w.sprow, D.n, dcnt, w.gplan, w.rank_of_row, w.gkey, w.G, w.rstatus,
+            (const uint32_t*)w.spacked, w.sprow, D.n, gn, w.gplan, w.rank_of_row, w.gkey, w.G, w.rstatus,
             w.rcounter, w.rtiles); note_launch();
       } else {
         auto rk = rank_kernel<unsigned long long, kRankT, kRankI>;
         rk<<<persistent_grid(rk, kRankT, 0, w.rtiles), kRankT, 0, s>>>(
-            (const unsigned long long*)w.spacked, w.sprow, D.n, dcnt, w.gplan, w.rank_of_row, w.gkey, w.G,
+            (const unsigned long long*)w.spacked, w.sprow, D.n, gn, w.gplan, w.rank_of_row, w.gkey, w.G,
             w.rstatus, w.rcounter, w.rtiles); note_launch();
       }
+      // after the sort path (which then counted no groups): the bitmap's ranks
+      TQP_CUDA(cudaMemsetAsync(w.dbits, 0, (size_t)w.dwords * sizeof(uint32_t), s));
+      dom_mark_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(D.group.data, D.group.dtype, w.sel, D.n, dcnt, w.dom,
+                                                              w.dbits); note_launch();
+      dom_scan_kernel<1024><<<1, 1024, 0, s>>>(w.dom, w.dbits, w.dpre, w.gkey, w.G); note_launch();
     } else if (D.group.data) {
       TQP_CUDA(cudaMemsetAsync(w.G, 0, 8, s));
     }
@@ -1316,6 +1338,13 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       pg.n_max = D.n;
       pg.d_n = dcnt;
       pg.rank_of_row = D.group.data ? w.rank_of_row : nullptr;
+      if (D.group.data) {
+        pg.dom = w.dom;
+        pg.gcol = D.group.data;
+        pg.gdt = D.group.dtype;
+        pg.dbits = w.dbits;
+        pg.dpre = w.dpre;
+      }
       pg.rank_sorted = w.rank_sorted;
       pg.kr = w.kr;
       pg.plan = plan;

@@ -196,6 +196,50 @@ def test_star_crowded_directory_cells(G):
     assert tqp.tqp_status_poll() == tqp.OK
 
 
+# group columns of the two dimensions: dtype and the span of their values.
+# Spans below 2^24 rank through the value-domain bitmap, wider ones through
+# the sort of the packed group keys; both paths meet at the 2^24 boundary.
+GROUP_DOMAINS = [
+    ((np.int16, -300, 300), (np.int8, -128, 127)),
+    ((np.int8, 7, 7), (np.int16, -32768, 32767)),
+    ((np.int32, 5, 5 + 2**24 - 1), (np.int32, -(2**24), -1)),
+    ((np.int32, -(2**31), 2**31 - 1), (np.int64, -(2**40), 2**40)),
+    ((np.int64, 2**62, 2**62 + 2**23), (np.int32, 0, 2**24)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(GROUP_DOMAINS)))
+def test_star_group_value_domains(G, case):
+    """Star join whose group columns take 40 (or fewer) distinct values
+    spread over spans from one value to the full 64-bit range, including
+    both ends of each span."""
+    tqp, Q, gd = G
+    g1, g2 = GROUP_DOMAINS[case]
+    r = np.random.default_rng(700 + case)
+
+    def column(spec, m):
+        dt, lo, hi = spec
+        vals = np.unique(np.concatenate([[lo, hi], r.integers(lo, hi, 38, endpoint=True)])).astype(dt)
+        col = vals[r.integers(0, len(vals), m)]
+        col[:len(vals)] = vals  # every value present
+        return col[r.permutation(m)]
+
+    n1, n2, n = 2_000, 3_000, 400_000
+    k1 = r.permutation(np.arange(-10**6, 10**6, dtype=np.int32))[:n1]
+    k2 = r.permutation(np.arange(0, 5 * 10**6, dtype=np.int64))[:n2] * 1_000_003 - 2**40
+    dim1 = {"key": k1, "cat": column(g1, n1)}
+    dim2 = {"key": k2, "cat": column(g2, n2)}
+    fk1 = r.choice(np.concatenate([k1, np.arange(2 * 10**6, 2 * 10**6 + 100, dtype=np.int32)]), n).astype(np.int32)
+    fk2 = r.choice(np.concatenate([k2, k2[:50] + 1]), n).astype(np.int64)
+    fact = {"fk1": fk1, "fk2": fk2, "date": r.integers(0, 2557, n).astype(np.int32)}
+    for c in ("m1", "m2", "m3"):
+        fact[c] = r.integers(0, 10**7, n).astype(np.int64)
+    want = pl.star(fact, dim1, dim2)
+    cu = lambda t: {k: torch.from_numpy(v).cuda() for k, v in t.items()}
+    compare(Q.star(cu(fact), cu(dim1), cu(dim2)), want)
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
 @pytest.mark.parametrize("learned", [False, True])
 def test_star_full_size_invariants(G, learned):
     """The full star join (fact 600M rows, dims 20M and 150M) in the
