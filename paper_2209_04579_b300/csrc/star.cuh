@@ -193,6 +193,21 @@ __device__ __forceinline__ int32_t dom_rank(const DomPlan& p, const uint32_t* bi
   return pre[w] + __popc(bits[w] & ((1u << (x & 31)) - 1u));
 }
 
+// Sort payload of the passing rows: the group rank when the bitmap ranks and
+// the caller allows it (rank_payload), else the row.
+__global__ void dom_payload_kernel(const void* gcol, int gdt, const int32_t* sel, int64_t n_max, const int64_t* d_n,
+                                   const DomPlan* dp, const uint32_t* bits, const int* pre, int rank_payload,
+                                   int32_t* out) {
+  const DomPlan p = *dp;
+  const bool rk = rank_payload && p.on;
+  const int64_t n = clamp_n(n_max, d_n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int32_t row = sel ? sel[i] : (int32_t)i;
+    out[i] = rk ? dom_rank(p, bits, pre, load_as_i64(gcol, gdt, row)) : row;
+  }
+}
+
 // ---- gather ranks and aggregated dimension columns into key order; check
 // that keys are unique among the passing rows.
 struct PregatherArgs {
@@ -208,6 +223,7 @@ struct PregatherArgs {
   int gdt;
   const uint32_t* dbits;
   const int* dpre;
+  int rank_payload;            // with dom->on: srows holds each sorted key's group rank
   int32_t* rank_sorted;
   void* kr;                    // KeyRank32 (int32 keys) or KeyRank64 per sorted position
   int nv;
@@ -225,9 +241,10 @@ __global__ void star_pregather_kernel(PregatherArgs a) {
   if (a.dom) dom = *a.dom;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
     int32_t row = a.srows[p];
-    const int32_t rk = !a.rank_of_row ? 0
-                       : dom.on      ? dom_rank(dom, a.dbits, a.dpre, load_as_i64(a.gcol, a.gdt, row))
-                                     : a.rank_of_row[row];
+    const int32_t rk = !a.rank_of_row              ? 0
+                       : dom.on && a.rank_payload ? row
+                       : dom.on                   ? dom_rank(dom, a.dbits, a.dpre, load_as_i64(a.gcol, a.gdt, row))
+                                                  : a.rank_of_row[row];
     a.rank_sorted[p] = rk;
     if (a.key_dt == TQP_I32)
       static_cast<KeyRank32*>(a.kr)[p] = KeyRank32{(uint32_t)key_image(a.skeys, a.key_dt, p), rk};

@@ -1062,6 +1062,8 @@ struct StarDimWs {
   uint32_t* dbits;
   int* dpre;
   int dwords;
+  int rank_payload;      // no value of the dimension is aggregated: the sort may carry ranks
+  int32_t* payload;
   int32_t* rank_sorted;
   void* kr;
   long long* dval[TQP_MAX_VALS];
@@ -1197,6 +1199,10 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
         const int b = 8 * dtype_bytes(D.group.dtype) < kDomBits ? 8 * dtype_bytes(D.group.dtype) : kDomBits;
         w.dwords = 1 << (b - 5);
       }
+      w.rank_payload = 1;
+      for (int v = 0; v < nvals; ++v)
+        if (vals[v].src == d + 1) w.rank_payload = 0;
+      w.payload = c.take<int32_t>(nn);
       w.dom = c.take<DomPlan>(1);
       w.sort_n = c.take<int64_t>(1);
       w.dbits = c.take<uint32_t>((size_t)w.dwords);
@@ -1282,9 +1288,6 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       TQP_CUDA(cudaMemsetAsync(w.cnt, 0, 8, s));
       dcnt = w.cnt;
     }
-    tqp_status st = w.learned ? run_sort_learned(w.lws, D.key.dtype, kin, vin, w.skeys, D.n, dcnt, lcfg, s)
-                              : run_sort(w.ksort, D.key.dtype, kin, vin, w.skeys, w.srows, D.n, dcnt, 0, eb * 8, s);
-    if (st != TQP_OK) return st;
     if (D.group.data && D.n > 0) {
       KeySet ks;
       std::memset(&ks, 0, sizeof(ks));
@@ -1305,7 +1308,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
         gb_encode_kernel<unsigned long long><<<g, 256, 0, s>>>(ks, w.sel, D.n, gn, w.gplan,
                                                                (unsigned long long*)w.packed, w.prow); note_launch();
       }
-      st = run_sort(w.gsort, w.gword == 4 ? kKeyU32 : kKeyU64, w.packed, w.prow, w.spacked, w.sprow, D.n, gn, 0,
+      tqp_status st = run_sort(w.gsort, w.gword == 4 ? kKeyU32 : kKeyU64, w.packed, w.prow, w.spacked, w.sprow, D.n, gn, 0,
                     w.gword * 8, s);
       if (st != TQP_OK) return st;
       TQP_CUDA(cudaMemsetAsync(w.rstatus, 0, (size_t)w.rtiles * 8, s));
@@ -1326,9 +1329,18 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       dom_mark_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(D.group.data, D.group.dtype, w.sel, D.n, dcnt, w.dom,
                                                               w.dbits); note_launch();
       dom_scan_kernel<1024><<<1, 1024, 0, s>>>(w.dom, w.dbits, w.dpre, w.gkey, w.G); note_launch();
+      // the key sort's payload: the group rank itself when the bitmap ranks
+      // and no value of this dimension is aggregated, else the row
+      dom_payload_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(D.group.data, D.group.dtype, w.sel, D.n, dcnt, w.dom,
+                                                                 w.dbits, w.dpre, w.rank_payload, w.payload);
+      note_launch();
+      vin = w.payload;
     } else if (D.group.data) {
       TQP_CUDA(cudaMemsetAsync(w.G, 0, 8, s));
     }
+    const tqp_status st = w.learned ? run_sort_learned(w.lws, D.key.dtype, kin, vin, w.skeys, D.n, dcnt, lcfg, s)
+                              : run_sort(w.ksort, D.key.dtype, kin, vin, w.skeys, w.srows, D.n, dcnt, 0, eb * 8, s);
+    if (st != TQP_OK) return st;
     if (D.n > 0) {
       PregatherArgs pg;
       std::memset(&pg, 0, sizeof(pg));
@@ -1344,6 +1356,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
         pg.gdt = D.group.dtype;
         pg.dbits = w.dbits;
         pg.dpre = w.dpre;
+        pg.rank_payload = w.rank_payload;
       }
       pg.rank_sorted = w.rank_sorted;
       pg.kr = w.kr;
