@@ -313,7 +313,109 @@ struct DimDir {
   int bshift;
   int use_bits;                   // probes test the cell bitmap first (unit cells, or a filtered dimension)
   long long ncells;               // 0: no passing rows (every probe misses)
+  int direct;                     // dense keys: unit cells filled straight from the rows, no key sort
 };
+
+// ---- dense keys without the sort.  When the passing keys are unique and
+// dense in their range (span < 8 x their count, within the cell budget),
+// the directory has one cell per key value: sorting the keys would only
+// place each at key - min, which the cell index already does.  The key
+// range is taken first; dense dimensions then skip the key sort and fill
+// their cells straight from the rows.
+__global__ void dim_range_kernel(const void* keys, int key_dt, int64_t n_max, const int64_t* d_n,
+                                 unsigned long long* range) {
+  const int64_t n = clamp_n(n_max, d_n);
+  unsigned long long lo = ~0ull, hi = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const unsigned long long u = key_image(keys, key_dt, i);
+    lo = u < lo ? u : lo;
+    hi = u > hi ? u : hi;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    lo = l2 < lo ? l2 : lo;
+    hi = h2 > hi ? h2 : hi;
+  }
+  if ((threadIdx.x & 31) == 0 && lo <= hi) {
+    atomicMin(&range[0], lo);
+    atomicMax(&range[1], hi);
+  }
+}
+
+// One thread: the directory plan of a dense dimension (unit cells, direct),
+// or direct = 0; sort_n: the rows the key sort then takes (0 when direct).
+__global__ void dim_direct_plan_kernel(const unsigned long long* range, int64_t n_max, const int64_t* d_n,
+                                       int log2_cells_max, DimDir* dd, int64_t* sort_n) {
+  if (threadIdx.x != 0) return;
+  const int64_t nd = clamp_n(n_max, d_n);
+  DimDir r;
+  r.umin = range[0];
+  r.umax = range[1];
+  r.bshift = 0;
+  r.use_bits = 1;
+  r.direct = 0;
+  r.ncells = 0;
+  if (nd > 0 && r.umin <= r.umax) {
+    const unsigned long long span = r.umax - r.umin;
+    const int bits = span ? 64 - __clzll((long long)span) : 0;
+    r.direct = span < 8ull * (unsigned long long)nd && bits <= log2_cells_max;
+    r.ncells = (long long)span + 1;
+  }
+  if (!r.direct) r.ncells = 0;
+  *dd = r;
+  *sort_n = r.direct ? 0 : nd;
+}
+
+// Cells of a direct dimension: the bit, the group rank and the aggregated
+// values of each passing row at cell key - min.  A bit already set is a
+// repeated key (unsupported, as in the sorted form).
+struct DirectArgs {
+  const void* keys;  // passing keys (compacted when the dimension is filtered)
+  int key_dt;
+  const int32_t* sel;  // row of each passing key (null: the position)
+  int64_t n_max;
+  const int64_t* d_n;
+  const DimDir* dd;
+  uint32_t* bitmap;
+  int32_t* rank_cell;
+  // group rank: the domain bitmap (dom->on), else rank_of_row; none without a group column
+  const int32_t* rank_of_row;
+  const DomPlan* dom;
+  const void* gcol;
+  int gdt;
+  const uint32_t* dbits;
+  const int* dpre;
+  int nv;
+  const void* vcol[TQP_MAX_VALS];
+  int vdt[TQP_MAX_VALS];
+  long long* dval_cell[TQP_MAX_VALS];
+  StarPlan* plan;
+};
+
+__global__ void dir_direct_kernel(DirectArgs a) {
+  const DimDir r = *a.dd;
+  if (!r.direct) return;
+  DomPlan dom;
+  dom.on = 0;
+  if (a.dom) dom = *a.dom;
+  const int64_t n = clamp_n(a.n_max, a.d_n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int32_t row = a.sel ? a.sel[i] : (int32_t)i;
+    const unsigned long long c = key_image(a.keys, a.key_dt, i) - r.umin;
+    const uint32_t bit = 1u << (c & 31);
+    if (atomicOr(&a.bitmap[c >> 5], bit) & bit) {
+      if (atomicExch(&a.plan->unsupported, 1) == 0) raise_status(TQP_ERR_UNSUPPORTED);
+      continue;
+    }
+    a.rank_cell[c] = !a.rank_of_row ? 0
+                     : dom.on      ? dom_rank(dom, a.dbits, a.dpre, load_as_i64(a.gcol, a.gdt, row))
+                                   : a.rank_of_row[row];
+    for (int v = 0; v < a.nv; ++v) a.dval_cell[v][c] = load_as_i64(a.vcol[v], a.vdt[v], row);
+  }
+}
 
 
 
@@ -323,8 +425,10 @@ struct DimDir {
 __global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, const int64_t* d_n, int64_t n_all,
                                 int log2_cells_max, DimDir* dd) {
   if (threadIdx.x != 0) return;
+  if (dd->direct) return;  // planned from the key range, no sorted keys
   const int64_t nd = clamp_n(n_max, d_n);
   DimDir r;
+  r.direct = 0;
   r.use_bits = 1;
   if (nd == 0) {
     r.umin = 1;

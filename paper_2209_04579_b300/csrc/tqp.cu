@@ -1070,6 +1070,8 @@ struct StarDimWs {
   uint32_t ftiles, rtiles;
   int gword;
   // key directory
+  unsigned long long* krange;  // passing key images' min and max (dense-key check)
+  int64_t* ksort_n;            // rows the key sort takes (0 for a dense dimension)
   DimDir* dplan;
   int* dir;
   uint32_t* bitmap;
@@ -1216,6 +1218,8 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     w.log2cells = 1;
     while (w.log2cells < 27 && (1ll << w.log2cells) < 8 * D.n) ++w.log2cells;
     w.dplan = c.take<DimDir>(1);
+    w.krange = c.take<unsigned long long>(2);
+    w.ksort_n = c.take<int64_t>(1);
     w.dir = c.take<int>((size_t)(1ll << w.log2cells) + 2);
     w.bitmap = c.take<uint32_t>((size_t)(1ll << w.log2cells) / 32 + 1);
     {
@@ -1338,8 +1342,19 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     } else if (D.group.data) {
       TQP_CUDA(cudaMemsetAsync(w.G, 0, 8, s));
     }
-    const tqp_status st = w.learned ? run_sort_learned(w.lws, D.key.dtype, kin, vin, w.skeys, D.n, dcnt, lcfg, s)
-                              : run_sort(w.ksort, D.key.dtype, kin, vin, w.skeys, w.srows, D.n, dcnt, 0, eb * 8, s);
+    // dense keys (a possible case up to the cell budget) skip the key sort:
+    // kn counts the rows the sorted form takes
+    const int64_t* kn = dcnt;
+    TQP_CUDA(cudaMemsetAsync(w.dplan, 0, sizeof(DimDir), s));
+    if (D.n > 0 && D.n <= (1ll << w.log2cells)) {
+      TQP_CUDA(cudaMemsetAsync(w.krange, 0xFF, 8, s));
+      TQP_CUDA(cudaMemsetAsync(w.krange + 1, 0, 8, s));
+      dim_range_kernel<<<stride_grid(D.n, 256, 4), 256, 0, s>>>(kin, D.key.dtype, D.n, dcnt, w.krange); note_launch();
+      dim_direct_plan_kernel<<<1, 32, 0, s>>>(w.krange, D.n, dcnt, w.log2cells, w.dplan, w.ksort_n); note_launch();
+      kn = w.ksort_n;
+    }
+    const tqp_status st = w.learned ? run_sort_learned(w.lws, D.key.dtype, kin, vin, w.skeys, D.n, kn, lcfg, s)
+                              : run_sort(w.ksort, D.key.dtype, kin, vin, w.skeys, w.srows, D.n, kn, 0, eb * 8, s);
     if (st != TQP_OK) return st;
     if (D.n > 0) {
       PregatherArgs pg;
@@ -1348,7 +1363,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       pg.key_dt = D.key.dtype;
       pg.srows = w.srows;
       pg.n_max = D.n;
-      pg.d_n = dcnt;
+      pg.d_n = kn;
       pg.rank_of_row = D.group.data ? w.rank_of_row : nullptr;
       if (D.group.data) {
         pg.dom = w.dom;
@@ -1370,10 +1385,10 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       }
       star_pregather_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(pg); note_launch();
     }
-    dir_plan_kernel<<<1, 32, 0, s>>>(w.skeys, D.key.dtype, D.n, dcnt, D.n, w.log2cells, w.dplan); note_launch();
+    dir_plan_kernel<<<1, 32, 0, s>>>(w.skeys, D.key.dtype, D.n, kn, D.n, w.log2cells, w.dplan); note_launch();
     if (D.n > 0) {
       TQP_CUDA(cudaMemsetAsync(w.bitmap, 0, ((size_t)(1ll << w.log2cells) / 32 + 1) * sizeof(uint32_t), s));
-      dir_fill_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(w.skeys, D.key.dtype, D.n, dcnt, w.dplan, w.dir,
+      dir_fill_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(w.skeys, D.key.dtype, D.n, kn, w.dplan, w.dir,
                                                              w.bitmap);
       note_launch();
       CellArgs ca;
@@ -1381,7 +1396,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       ca.skeys = w.skeys;
       ca.key_dt = D.key.dtype;
       ca.n_max = D.n;
-      ca.d_n = dcnt;
+      ca.d_n = kn;
       ca.dd = w.dplan;
       ca.rank_sorted = w.rank_sorted;
       ca.rank_cell = w.rank_cell;
@@ -1398,6 +1413,33 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
         dir_table_kernel<<<stride_grid((1ll << t) + 1, 256), 256, 0, s>>>(w.kr, D.key.dtype, w.dplan, w.dir, w.table);
         note_launch();
       }
+      DirectArgs da;
+      std::memset(&da, 0, sizeof(da));
+      da.keys = kin;
+      da.key_dt = D.key.dtype;
+      da.sel = D.npred ? w.sel : nullptr;
+      da.n_max = D.n;
+      da.d_n = dcnt;
+      da.dd = w.dplan;
+      da.bitmap = w.bitmap;
+      da.rank_cell = w.rank_cell;
+      if (D.group.data) {
+        da.rank_of_row = w.rank_of_row;
+        da.dom = w.dom;
+        da.gcol = D.group.data;
+        da.gdt = D.group.dtype;
+        da.dbits = w.dbits;
+        da.dpre = w.dpre;
+      }
+      for (int v = 0; v < nvals; ++v) {
+        if (vals[v].src != d + 1) continue;
+        da.vcol[da.nv] = D.cols[vals[v].col].data;
+        da.vdt[da.nv] = D.cols[vals[v].col].dtype;
+        da.dval_cell[da.nv] = w.dval_cell[v];
+        ++da.nv;
+      }
+      da.plan = plan;
+      dir_direct_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(da); note_launch();
     }
   }
   // ---- slots, accumulators, probe, compaction

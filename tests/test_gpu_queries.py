@@ -196,6 +196,43 @@ def test_star_crowded_directory_cells(G):
     assert tqp.tqp_status_poll() == tqp.OK
 
 
+@pytest.mark.parametrize("stride", [1, 3, 1000])
+def test_q14_dense_and_spread_dimension_keys(G, stride):
+    """Dimension keys key0 + stride * permutation, five in six passing the
+    region predicate: with stride 1 and 3 the passing keys are dense (span
+    within 8x their count), so the directory cells are filled straight from
+    the rows without a key sort; stride 1000 takes the sorted form.  Foreign
+    keys also fall between and beyond the dimension keys."""
+    tqp, Q, gd = G
+    r = np.random.default_rng(40 + stride)
+    m = 300_000
+    key = (-123_456 + stride * r.permutation(m)).astype(np.int32)
+    dim = {"key": key, "region": r.integers(0, 6, m).astype(np.int8),
+           "price": r.integers(100, 10**6, m).astype(np.int64)}
+    fk = np.concatenate([r.choice(key, 900_000), r.integers(-200_000, 200_000 + stride * m, 100_000)]).astype(np.int32)
+    fact = {"fk": fk[r.permutation(len(fk))]}
+    want = pl.q14(fact, dim)
+    cu = lambda t: {k: torch.from_numpy(v).cuda() for k, v in t.items()}
+    compare(Q.q14(cu(fact), cu(dim)), want)
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
+@pytest.mark.parametrize("stride", [1, 1000])
+def test_q14_repeated_dimension_key_is_unsupported(G, stride):
+    """A repeated key among the passing dimension rows is reported as
+    unsupported, in the dense (direct) and the sorted form alike."""
+    tqp, Q, gd = G
+    r = np.random.default_rng(7)
+    m = 50_000
+    key = (stride * r.permutation(m)).astype(np.int32)
+    key[17] = key[4242]
+    dim = {"key": key, "region": np.zeros(m, np.int8), "price": np.ones(m, np.int64)}
+    fact = {"fk": r.choice(key, 100_000).astype(np.int32)}
+    cu = lambda t: {k: torch.from_numpy(v).cuda() for k, v in t.items()}
+    Q.q14(cu(fact), cu(dim))
+    assert tqp.tqp_status_poll() == tqp.ERR_UNSUPPORTED
+
+
 # group columns of the two dimensions: dtype and the span of their values.
 # Spans below 2^24 rank through the value-domain bitmap, wider ones through
 # the sort of the packed group keys; both paths meet at the 2^24 boundary.
