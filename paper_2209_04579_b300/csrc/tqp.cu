@@ -1305,28 +1305,36 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       // group keys are sorted and ranked (sort_n: the rows of that path)
       dom_plan_kernel<<<1, 32, 0, s>>>(w.gplan, D.n, dcnt, w.dom, w.sort_n); note_launch();
       const int64_t* gn = w.sort_n;
-      int g = stride_grid(D.n, 256);
-      if (w.gword == 4) {
-        gb_encode_kernel<uint32_t><<<g, 256, 0, s>>>(ks, w.sel, D.n, gn, w.gplan, (uint32_t*)w.packed, w.prow); note_launch();
-      } else {
-        gb_encode_kernel<unsigned long long><<<g, 256, 0, s>>>(ks, w.sel, D.n, gn, w.gplan,
-                                                               (unsigned long long*)w.packed, w.prow); note_launch();
-      }
-      tqp_status st = run_sort(w.gsort, w.gword == 4 ? kKeyU32 : kKeyU64, w.packed, w.prow, w.spacked, w.sprow, D.n, gn, 0,
-                    w.gword * 8, s);
-      if (st != TQP_OK) return st;
-      TQP_CUDA(cudaMemsetAsync(w.rstatus, 0, (size_t)w.rtiles * 8, s));
-      TQP_CUDA(cudaMemsetAsync(w.rcounter, 0, 4, s));
-      if (w.gword == 4) {
-        auto rk = rank_kernel<uint32_t, kRankT, kRankI>;
-        rk<<<persistent_grid(rk, kRankT, 0, w.rtiles), kRankT, 0, s>>>(
-            (const uint32_t*)w.spacked, w.sprow, D.n, gn, w.gplan, w.rank_of_row, w.gkey, w.G, w.rstatus,
-            w.rcounter, w.rtiles); note_launch();
-      } else {
-        auto rk = rank_kernel<unsigned long long, kRankT, kRankI>;
-        rk<<<persistent_grid(rk, kRankT, 0, w.rtiles), kRankT, 0, s>>>(
-            (const unsigned long long*)w.spacked, w.sprow, D.n, gn, w.gplan, w.rank_of_row, w.gkey, w.G,
-            w.rstatus, w.rcounter, w.rtiles); note_launch();
+      // int8 and int16 group columns always rank through the bitmap: their
+      // sort path is not launched (G stays 0 unless the bitmap counts groups)
+      const bool small_domain = dtype_bytes(D.group.dtype) <= 2;
+      TQP_CUDA(cudaMemsetAsync(w.G, 0, 8, s));
+      if (!small_domain) {
+        const int g = stride_grid(D.n, 256);
+        if (w.gword == 4) {
+          gb_encode_kernel<uint32_t><<<g, 256, 0, s>>>(ks, w.sel, D.n, gn, w.gplan, (uint32_t*)w.packed, w.prow);
+        } else {
+          gb_encode_kernel<unsigned long long><<<g, 256, 0, s>>>(ks, w.sel, D.n, gn, w.gplan,
+                                                                 (unsigned long long*)w.packed, w.prow);
+        }
+        note_launch();
+        const tqp_status st = run_sort(w.gsort, w.gword == 4 ? kKeyU32 : kKeyU64, w.packed, w.prow, w.spacked,
+                                       w.sprow, D.n, gn, 0, w.gword * 8, s);
+        if (st != TQP_OK) return st;
+        TQP_CUDA(cudaMemsetAsync(w.rstatus, 0, (size_t)w.rtiles * 8, s));
+        TQP_CUDA(cudaMemsetAsync(w.rcounter, 0, 4, s));
+        if (w.gword == 4) {
+          auto rk = rank_kernel<uint32_t, kRankT, kRankI>;
+          rk<<<persistent_grid(rk, kRankT, 0, w.rtiles), kRankT, 0, s>>>(
+              (const uint32_t*)w.spacked, w.sprow, D.n, gn, w.gplan, w.rank_of_row, w.gkey, w.G, w.rstatus,
+              w.rcounter, w.rtiles);
+        } else {
+          auto rk = rank_kernel<unsigned long long, kRankT, kRankI>;
+          rk<<<persistent_grid(rk, kRankT, 0, w.rtiles), kRankT, 0, s>>>(
+              (const unsigned long long*)w.spacked, w.sprow, D.n, gn, w.gplan, w.rank_of_row, w.gkey, w.G,
+              w.rstatus, w.rcounter, w.rtiles);
+        }
+        note_launch();
       }
       // after the sort path (which then counted no groups): the bitmap's ranks
       TQP_CUDA(cudaMemsetAsync(w.dbits, 0, (size_t)w.dwords * sizeof(uint32_t), s));
