@@ -896,6 +896,8 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     // ITEMS/4 16-byte loads; the next tile's keys load while this one is
     // probed.
     const int32_t* fk0 = static_cast<const int32_t*>(a.dim[0].fk);
+    const bool bit_only = SMEM_BM && K32 && ND == 1 && unit[0] && sbm && dd[0].use_bits && dd[0].ncells > 0;
+    const uint32_t umin0 = (uint32_t)dd[0].umin, span0 = (uint32_t)(dd[0].umax - dd[0].umin);
     auto load4 = [&](int64_t w, int j, UK (&dst)[ITEMS]) {
       const int64_t r = w * WT + (int64_t)lane * ITEMS + 4 * j;
       if (w < nwt && r + 3 < a.n_fact) {
@@ -922,8 +924,20 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
       const int64_t r0 = wt * WT + (int64_t)lane * ITEMS;
       int pos[ITEMS][ND], slot[ITEMS];
       bool alive[ITEMS];
+      if (bit_only) {
+        // one dimension of unit cells with its bitmap in shared memory: the
+        // cell bit is the whole probe
 #pragma unroll
-      for (int k = 0; k < ITEMS; ++k) alive[k] = probe(r0 + k < a.n_fact, r0 + k, pos[k], slot[k], true, cur[k]);
+        for (int k = 0; k < ITEMS; ++k) {
+          const uint32_t c = (uint32_t)cur[k] - umin0;
+          alive[k] = r0 + k < a.n_fact && c <= span0 && ((s_bm[c >> 5] >> (c & 31)) & 1u);
+          pos[k][0] = (int)c;
+          slot[k] = 0;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) alive[k] = probe(r0 + k < a.n_fact, r0 + k, pos[k], slot[k], true, cur[k]);
+      }
       push_items(alive, slot, pos, (int)r0, 1);
     }
   } else if (a.npred == 0) {

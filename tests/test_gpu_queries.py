@@ -217,6 +217,27 @@ def test_q14_dense_and_spread_dimension_keys(G, stride):
     assert tqp.tqp_status_poll() == tqp.OK
 
 
+@pytest.mark.parametrize("passing", [0, 1, 2])
+def test_q14_few_passing_dimension_rows(G, passing):
+    """No, one or two dimension rows pass the region predicate (an empty
+    directory, a single cell, two far-apart cells)."""
+    tqp, Q, gd = G
+    r = np.random.default_rng(90 + passing)
+    m = 20_000
+    key = (5 + r.permutation(m)).astype(np.int32)
+    region = np.full(m, 9, np.int8)
+    region[:passing] = [1, 3][:passing]
+    if passing == 2:
+        key[:2] = [-(2**31), 2**31 - 1]
+    dim = {"key": key, "region": region, "price": r.integers(100, 10**6, m).astype(np.int64)}
+    fk = np.concatenate([r.choice(key, 200_000), key[:passing].repeat(7)]).astype(np.int32)
+    fact = {"fk": fk}
+    want = pl.q14(fact, dim)
+    cu = lambda t: {k: torch.from_numpy(v).cuda() for k, v in t.items()}
+    compare(Q.q14(cu(fact), cu(dim)), want)
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
 @pytest.mark.parametrize("stride", [1, 1000])
 def test_q14_repeated_dimension_key_is_unsupported(G, stride):
     """A repeated key among the passing dimension rows is reported as
