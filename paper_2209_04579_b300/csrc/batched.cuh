@@ -321,56 +321,105 @@ __global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, 
     const ProbDir pd = a.pdir[p];
     const int* dir = a.dir + P.cell_off;
     const uint32_t* bm = a.bitmap + P.word_off;
+    // Rows in groups of four per thread, stage by stage (predicates, foreign
+    // keys, cell bits, directory bounds, keys, ranks): each stage issues the
+    // four rows' reads together, so a thread waits on one round trip per
+    // stage instead of one per read of every row.  The fold then takes the
+    // surviving rows one at a time in a rolled loop (one copy in the code).
+    constexpr int Q = 4;
+    static_assert(ITEMS % Q == 0, "rows per thread: a multiple of 4");
 #pragma unroll 1
-    for (int k = 0; k < ITEMS; ++k) {
-      const long long row = r0 + (long long)k * THREADS + threadIdx.x;
-      if (row >= P.n_fact) continue;
-      bool keep = true;
-      for (int q = 0; q < S.npred; ++q)
-        keep = keep && compare(load_as_i64(P.fact[S.pcol[q]], S.fact_dt[S.pcol[q]], row), S.pop[q], S.plit[q]);
-      if (!keep) continue;
-      int32_t x = static_cast<const int32_t*>(P.fact[S.fk_col])[row];
-      const unsigned u = (unsigned)x ^ 0x80000000u;
-      if (u < pd.umin || u > pd.umax) continue;
-      const int c = (int)((u - pd.umin) >> pd.bshift);
-      if (!((__ldg(&bm[c >> 5]) >> (c & 31)) & 1u)) continue;
-      int l = __ldg(&dir[c]);
-      const int hi = __ldg(&dir[c + 1]);
-      int h = hi;
-      while (h - l > 4) {  // first key >= x lies in [l, h]
-        int mid = (l + h) >> 1;
-        if (keys[mid] < x) l = mid + 1; else h = mid;
+    for (int k0 = 0; k0 < ITEMS; k0 += Q) {
+      long long row[Q];
+      bool live[Q];
+      int32_t x[Q];
+      int c[Q], l[Q], hi[Q];
+      long long g[Q];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        row[j] = r0 + (long long)(k0 + j) * THREADS + threadIdx.x;
+        live[j] = row[j] < P.n_fact;
       }
-      while (l < hi && keys[l] < x) ++l;
-      if (l >= hi || keys[l] != x) continue;
-      long long g = ranks[l];
-      long long* dst = shared ? my_acc + g * nacc : gacc + g * nacc;
-      for (int q = 0; q < S.naggs; ++q) {
-        long long xq = 1;
-        const int op = S.op[q];
-        if (op != TQP_COUNT) {
-          const int e = S.expr[q];
-          unsigned long long v = 1;
-          for (int tt = 0; tt < S.nterms[e]; ++tt) {
-            int c = S.tcol[e][tt];
-            long long xv = load_as_i64(P.fact[c], S.fact_dt[c], row);
-            v *= (unsigned long long)S.tmul[e][tt] * (unsigned long long)xv + (unsigned long long)S.tadd[e][tt];
+      for (int q = 0; q < S.npred; ++q) {
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+          if (live[j]) live[j] = compare(load_as_i64(P.fact[S.pcol[q]], S.fact_dt[S.pcol[q]], row[j]), S.pop[q], S.plit[q]);
+      }
+      const int32_t* fk = static_cast<const int32_t*>(P.fact[S.fk_col]);
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        x[j] = live[j] ? __ldg(fk + row[j]) : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        const unsigned u = (unsigned)x[j] ^ 0x80000000u;
+        live[j] = live[j] && u >= pd.umin && u <= pd.umax;
+        c[j] = live[j] ? (int)((u - pd.umin) >> pd.bshift) : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < Q; ++j)
+        if (live[j]) live[j] = (__ldg(&bm[c[j] >> 5]) >> (c[j] & 31)) & 1u;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        l[j] = hi[j] = 0;
+        if (live[j]) {
+          l[j] = __ldg(&dir[c[j]]);
+          hi[j] = __ldg(&dir[c[j] + 1]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        if (!live[j]) continue;
+        int lo = l[j], h = hi[j];
+        while (h - lo > 4) {  // first key >= x lies in [lo, h]
+          const int mid = (lo + h) >> 1;
+          if (keys[mid] < x[j]) lo = mid + 1; else h = mid;
+        }
+        while (lo < hi[j] && keys[lo] < x[j]) ++lo;
+        live[j] = lo < hi[j] && keys[lo] == x[j];
+        l[j] = lo;
+      }
+#pragma unroll
+      for (int j = 0; j < Q; ++j) g[j] = live[j] ? (long long)__ldg(&ranks[l[j]]) : 0;
+#pragma unroll 1
+      for (int j = 0; j < Q; ++j) {
+        if (live[0]) {
+          const long long rw = row[0];
+          long long* dst = shared ? my_acc + g[0] * nacc : gacc + g[0] * nacc;
+          for (int q = 0; q < S.naggs; ++q) {
+            long long xq = 1;
+            const int op = S.op[q];
+            if (op != TQP_COUNT) {
+              const int e = S.expr[q];
+              unsigned long long v = 1;
+              for (int tt = 0; tt < S.nterms[e]; ++tt) {
+                const int cc = S.tcol[e][tt];
+                const long long xv = load_as_i64(P.fact[cc], S.fact_dt[cc], rw);
+                v *= (unsigned long long)S.tmul[e][tt] * (unsigned long long)xv + (unsigned long long)S.tadd[e][tt];
+              }
+              xq = (long long)v;
+            }
+            unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dst + q);
+            switch (op) {
+              case TQP_MIN: atomicMin(dst + q, xq); break;
+              case TQP_MAX: atomicMax(dst + q, xq); break;
+              default:
+                if (shared) shared_add_u64(d64, (unsigned long long)xq);
+                else atomicAdd(d64, (unsigned long long)xq);
+                break;
+            }
           }
-          xq = (long long)v;
+          unsigned long long* c64 = reinterpret_cast<unsigned long long*>(dst + S.naggs);
+          if (shared) shared_add_u64(c64, 1ull);
+          else atomicAdd(c64, 1ull);
         }
-        unsigned long long* d64 = reinterpret_cast<unsigned long long*>(dst + q);
-        switch (op) {
-          case TQP_MIN: atomicMin(dst + q, xq); break;
-          case TQP_MAX: atomicMax(dst + q, xq); break;
-          default:
-            if (shared) shared_add_u64(d64, (unsigned long long)xq);
-            else atomicAdd(d64, (unsigned long long)xq);
-            break;
+#pragma unroll
+        for (int m = 0; m + 1 < Q; ++m) {  // next row into place 0 (registers, no indexing)
+          live[m] = live[m + 1];
+          row[m] = row[m + 1];
+          g[m] = g[m + 1];
         }
       }
-      unsigned long long* c64 = reinterpret_cast<unsigned long long*>(dst + S.naggs);
-      if (shared) shared_add_u64(c64, 1ull);
-      else atomicAdd(c64, 1ull);
     }
     if (shared) {
       __syncthreads();
