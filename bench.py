@@ -36,6 +36,16 @@ def peaks():
 
 # ---------------------------------------------------------------- workloads
 
+def traffic_of(W, kernel):
+    """DRAM bytes (read + write) per launch of the dominant kernel, from the
+    ncu capture its profile summary records (null without one for the
+    kernel as it now is)."""
+    t = W.traffic() if hasattr(W, "traffic") else None
+    if not t or t[0] != kernel:
+        return {"traffic": None}
+    return {"traffic": t[1], "traffic_source": t[2]}
+
+
 class Q14:
     """fact(fk int32) 60M rows JOIN dim(key int32 unique, region int8, price
     int64) 1.5M rows WHERE region < 5 GROUP BY region: SUM(price), COUNT(*)."""
@@ -75,6 +85,10 @@ class Q14:
         # the probe reads every fact key once plus the passing dimension rows'
         # rank and price by cell (4 + 8 B, 20% of the dimension) and their bits
         return [(1, "star_probe_kernel", self.n_fact * 4 + int(self.m_dim * 0.2) * 12 + self.m_dim // 8)]
+
+    def traffic(self):
+        # ncu dram__bytes_read.sum + dram__bytes_write.sum of one probe launch
+        return ("star_probe_kernel", 258_186_752 + 3_123_712, "profiles/star_probe_q14_join_60M_x_1.5M.md")
 
     def oracle_sample(self, rows):
         from oracle import pipelines as pl
@@ -342,6 +356,13 @@ class Star:
         # fk1 (4), fk2 (8), date (4) and m1..m3 (24) of every fact row
         return [(1, "star_probe_kernel", self.n * 40)]
 
+    def traffic(self):
+        # ncu DRAM bytes (read + write) of one probe launch on the quarter-size
+        # case, scaled by the rows processed: fact rows, dimension rows and
+        # survivors all scale together, and so does the traffic
+        return ("star_probe_kernel", int((17_000_192_000 + 3_557_888) * 4 / self.scale),
+                "profiles/star_probe_star_join_150M_quarter_scale.md (x4 rows)")
+
     def oracle_sample(self, rows):
         from oracle import pipelines as pl
         scale = max(1, self.n // max(rows, 1))
@@ -568,10 +589,15 @@ def cpu_baseline(W, target_s=12.0):
     """The oracle as it stands on a bounded sample of the workload (single thread)."""
     import oracle
     oracle.build()
+    # the sample grows until it takes about target_s (a fixed cost such as
+    # the dimension's hash build makes small samples look slow)
     rows = 1_000_000
-    t, _ = W.oracle_sample(rows)
-    rows = int(min(W.rows(), max(rows, rows * target_s / max(t, 1e-3))))
     t, what = W.oracle_sample(rows)
+    for _ in range(3):
+        if t >= target_s / 2 or rows >= W.rows():
+            break
+        rows = int(min(W.rows(), max(rows + 1, rows * target_s / max(t, 1e-3))))
+        t, what = W.oracle_sample(rows)
     rows = getattr(W, "_sample_rows", rows)
     return {"value": rows / t, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": what,
             "seconds": round(t, 3)}
@@ -727,7 +753,8 @@ def run_ours(args, world, rank, local):
                    "launch": "one CUDA graph replay per step"},
         "roofline": {"bound": "hbm", "kernel": dom["kernel"], "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                     "kernel_ms": dom["ms"], "alg_bytes_per_launch": dom["alg_bytes"], "traffic": None},
+                     "kernel_ms": dom["ms"], "alg_bytes_per_launch": dom["alg_bytes"],
+                     **traffic_of(W, dom["kernel"])},
         "kernels": [{**k, "frac": k["gbs"] / peak} for k in kern],
         "step_roofline_frac": W.alg_bytes() / (total_ms / args.steps / 1e3) / 1e9 / peak,
         "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
