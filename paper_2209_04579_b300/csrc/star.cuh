@@ -694,7 +694,42 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     if (sbm)
       for (long long i = threadIdx.x; i < words; i += THREADS) s_bm[i] = __ldg(&a.dim[0].bitmap[i]);
   }
+  // The simple program: every aggregate a COUNT or one term mul * v + add of
+  // an int64 value (a fact column at the row, or a dimension column at the
+  // row's position or cell).  Its fold reads each aggregate's value straight
+  // through one pointer and index kind.
+  __shared__ int s_simple;
+  __shared__ const long long* s_ap[TQP_MAX_AGGS];
+  __shared__ int s_ai[TQP_MAX_AGGS];  // value index: 0 the row, 1 the first dimension's position, 2 the last's
+  __shared__ long long s_am[TQP_MAX_AGGS], s_aa[TQP_MAX_AGGS];
+  if (threadIdx.x == 0) {
+    int simple = 1;
+    for (int q = 0; q < A.naggs; ++q) {
+      s_ap[q] = nullptr;
+      s_ai[q] = 0;
+      s_am[q] = 1;
+      s_aa[q] = 0;
+      if (A.op[q] == TQP_COUNT) continue;
+      const int e = A.expr[q];
+      if (A.nterms[e] != 1) {
+        simple = 0;
+        continue;
+      }
+      const int vi = A.tval[e][0], src = s_vsrc[vi];
+      if (src == 0 && s_vdt[vi] != TQP_I64) {
+        simple = 0;
+        continue;
+      }
+      const bool cell = src == 1 ? unit[0] : (src > 1 && unit[ND - 1]);
+      s_ap[q] = static_cast<const long long*>(cell ? s_vptr_cell[vi] : s_vptr[vi]);
+      s_ai[q] = src == 0 ? 0 : src == 1 ? 1 : 2;
+      s_am[q] = A.tmul[e][0];
+      s_aa[q] = A.tadd[e][0];
+    }
+    s_simple = simple;
+  }
   __syncthreads();
+  const bool simple = s_simple;
 
   // 2. probe of one fact row through every dimension.  The dimensions'
   // foreign keys load together, then their wide cells' records (after the
@@ -816,7 +851,12 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     for (int q = 0; q < A.naggs; ++q) {
       long long x = 1;
       const int op = A.op[q];
-      if (op != TQP_COUNT) {
+      if (op != TQP_COUNT && simple) {
+        const int ai = s_ai[q];
+        const int idx = ai == 0 ? row : ai == 1 ? pos[0] : pos[ND - 1];
+        x = (long long)((unsigned long long)s_am[q] * (unsigned long long)__ldg(s_ap[q] + idx) +
+                        (unsigned long long)s_aa[q]);
+      } else if (op != TQP_COUNT) {
         const int e = A.expr[q];
         unsigned long long ev = 1;
         for (int t = 0; t < A.nterms[e]; ++t)
