@@ -88,7 +88,7 @@ class Q14:
 
     def traffic(self):
         # ncu dram__bytes_read.sum + dram__bytes_write.sum of one probe launch
-        return ("star_probe_kernel", 258_186_752 + 3_123_712, "profiles/star_probe_q14_join_60M_x_1.5M.md")
+        return ("star_probe_kernel", 258_187_008 + 3_142_656, "profiles/star_probe_q14_join_60M_x_1.5M.md")
 
     def oracle_sample(self, rows):
         from oracle import pipelines as pl
@@ -375,7 +375,7 @@ class Star:
         # ncu DRAM bytes (read + write) of one probe launch on the quarter-size
         # case, scaled by the rows processed: fact rows, dimension rows and
         # survivors all scale together, and so does the traffic
-        return ("star_probe_kernel", int((17_000_192_000 + 3_557_888) * 4 / self.scale),
+        return ("star_probe_kernel", int((17_004_073_000 + 3_809_536) * 4 / self.scale),
                 "profiles/star_probe_star_join_150M_quarter_scale.md (x4 rows)")
 
     def oracle_sample(self, rows):

@@ -290,8 +290,32 @@ __global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, 
   __shared__ long long s_acc[kBatchSmemWords];
   __shared__ uint32_t s_tile;
   __shared__ BatchShape S;  // indexed by runtime values: kept in shared memory
-  if (threadIdx.x == 0) S = Sg;
+  // the simple program: every aggregate a COUNT or one term mul * col + add
+  // of an int64 fact column
+  __shared__ int s_simple;
+  __shared__ int s_acol[TQP_MAX_AGGS];
+  __shared__ long long s_am[TQP_MAX_AGGS], s_aa[TQP_MAX_AGGS];
+  if (threadIdx.x == 0) {
+    S = Sg;
+    int simple = 1;
+    for (int q = 0; q < Sg.naggs; ++q) {
+      s_acol[q] = 0;
+      s_am[q] = 1;
+      s_aa[q] = 0;
+      if (Sg.op[q] == TQP_COUNT) continue;
+      const int e = Sg.expr[q];
+      if (Sg.nterms[e] != 1 || Sg.fact_dt[Sg.tcol[e][0]] != TQP_I64) {
+        simple = 0;
+        continue;
+      }
+      s_acol[q] = Sg.tcol[e][0];
+      s_am[q] = Sg.tmul[e][0];
+      s_aa[q] = Sg.tadd[e][0];
+    }
+    s_simple = simple;
+  }
   __syncthreads();
+  const bool simple = s_simple;
   if (*a.flag) return;
   const int nacc = S.naggs + 1;
   while (true) {
@@ -389,7 +413,11 @@ __global__ void __launch_bounds__(THREADS) batch_probe_kernel(BatchProbeArgs a, 
           for (int q = 0; q < S.naggs; ++q) {
             long long xq = 1;
             const int op = S.op[q];
-            if (op != TQP_COUNT) {
+            if (op != TQP_COUNT && simple) {
+              xq = (long long)((unsigned long long)s_am[q] *
+                                   (unsigned long long)__ldg(static_cast<const long long*>(P.fact[s_acol[q]]) + rw) +
+                               (unsigned long long)s_aa[q]);
+            } else if (op != TQP_COUNT) {
               const int e = S.expr[q];
               unsigned long long v = 1;
               for (int tt = 0; tt < S.nterms[e]; ++tt) {
