@@ -3,13 +3,17 @@
 // Section 2.3).
 //
 // Per dimension d (all on the device, no host round trip):
-//   filter the dimension rows (stream compaction), gather their keys, sort
-//   (key, row) stably, give each row the dense rank of its group value among
-//   the passing rows (sort + adjacent difference + look-back scan), and
-//   gather the rank and any aggregated dimension column into key order.
-// Then one pass over the fact table: fact predicates, one bound search per
-// dimension in its sorted keys, and the row's expression values folded into
-// the accumulator slot of its group combination (ranks are in ascending key
+//   filter the dimension rows (stream compaction) and gather their keys;
+//   give each passing row the dense rank of its group value (a presence
+//   bitmap over a small value domain, else sort + adjacent difference +
+//   look-back scan); sort (key, rank or row), gather the rank and any
+//   aggregated dimension column into key order, and build the directory:
+//   cell bitmap, and a 32-byte record per wide cell with its first keys
+//   inline.  Keys dense in their range skip the sort: one cell per key
+//   value, filled straight from the rows.
+// Then one pass over the fact table: fact predicates, one directory probe
+// per dimension, and the row's expression values folded into the
+// accumulator slot of its group combination (ranks are in ascending value
 // order, so slot order is the lexicographic group order).  Few slots live in
 // shared memory per block; many go straight to global 64-bit atomics.
 // A final single-pass scan compacts the non-empty slots into the output.
@@ -622,11 +626,12 @@ __device__ __forceinline__ void ring_flush(WarpRing<F>& q, Drain&& drain) {
 //     they go straight to the dimension probe.  With predicates, the passing
 //     rows are compacted into a warp queue that feeds the probe 32 at a time.
 //  2. Dimension probe per row: key image, range, cell bit; a unit-width cell
-//     proves the key, otherwise the directory bounds and the keys of the cell
-//     give its sorted position.
-//  3. Rows that find every dimension are compacted (row and positions) into
-//     a second queue; the fold runs on 32 of them at a time with all lanes
-//     active: group ranks, values and expressions, accumulator updates.
+//     proves the key, otherwise the cell's record (and, past its inline
+//     keys, the cell's sorted keys) gives its sorted position and rank.
+//  3. Rows that find every dimension are compacted (row, partial group
+//     slot, positions) into a second queue; the fold runs on 32 of them at
+//     a time with all lanes active: unit cells' ranks, values and
+//     expressions, accumulator updates.
 // Compacting before the expensive stages keeps a warp's instructions on
 // live rows (a fifth of the rows reach the fold in the Q14 shape).
 // SMEM_BM: the first dimension's cell bitmap is copied into dynamic shared
