@@ -215,3 +215,13 @@ def partition(bucket, B):
     off = np.empty(B + 1, dtype=np.int64)
     lib().orc_partition(_p(bucket), ctypes.c_int64(len(bucket)), B, _p(rows), _p(off))
     return rows, off
+
+
+def like_prefix(strings, prefix: bytes):
+    """strings: (n, m) uint8, zero-padded rows; 1 where the value starts with prefix."""
+    s = np.ascontiguousarray(strings, dtype=np.uint8)
+    n, m = s.shape
+    p = np.frombuffer(prefix, dtype=np.uint8) if prefix else np.zeros(1, np.uint8)
+    out = np.empty(n, dtype=np.int8)
+    lib().orc_like_prefix(_p(s), ctypes.c_int64(n), m, _p(np.ascontiguousarray(p)), len(prefix), _p(out))
+    return out

@@ -374,4 +374,18 @@ void orc_partition(const int32_t* bucket, int64_t n, int B, int32_t* out_rows, i
   for (int64_t i = 0; i < n; ++i) out_rows[cnt[bucket[i]]++] = static_cast<int32_t>(i);
 }
 
+// String columns (Section 2.1): an (n x m) byte tensor, row i holding the
+// UTF-8 bytes of value i right-padded with zeros to m bytes.  SQL
+// `value LIKE 'p%'` for a prefix p of k bytes (no zero byte in p) holds when
+// the value's first k bytes are p.  A value shorter than k bytes has a zero
+// among them (its padding), which p lacks, so the byte comparison over the
+// row is exact; k > m never matches, and the empty prefix matches every row.
+void orc_like_prefix(const uint8_t* str, int64_t n, int m, const uint8_t* prefix, int k, int8_t* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    bool match = k <= m;
+    for (int j = 0; match && j < k; ++j) match = str[i * m + j] == prefix[j];
+    out[i] = match ? 1 : 0;
+  }
+}
+
 }  // extern "C"

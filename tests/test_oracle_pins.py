@@ -407,3 +407,44 @@ def test_zipf_top_rank_frequency():
     sd = (400_000 * p0 * (1 - p0)) ** 0.5
     assert abs(np.sum(r == 0) - 400_000 * p0) < 6 * sd
     assert r.max() <= 999
+
+
+# ---------------------------------------------------------------- strings
+def _pad(values, m):
+    """Section 2.1's string tensor: each UTF-8 value right-padded with zeros to m bytes."""
+    out = np.zeros((len(values), m), np.uint8)
+    for i, v in enumerate(values):
+        b = v.encode("utf-8")
+        out[i, :len(b)] = np.frombuffer(b, np.uint8)
+    return out
+
+
+def test_like_prefix_worked_example():
+    vals = ["", "a", "ab", "abc", "abd", "b", "abcabc", "abé", "été"]
+    s = _pad(vals, 7)
+    assert orc.like_prefix(s, b"ab").tolist() == [0, 0, 1, 1, 1, 0, 1, 1, 0]
+    assert orc.like_prefix(s, b"").tolist() == [1] * len(vals)            # LIKE '%'
+    assert orc.like_prefix(s, b"abcabc").tolist() == [0, 0, 0, 0, 0, 0, 1, 0, 0]
+    assert orc.like_prefix(s, b"abcabcx").tolist() == [0] * len(vals)     # longer than every value
+    assert orc.like_prefix(s, b"abcabcxy").tolist() == [0] * len(vals)    # longer than the width
+    e = "é".encode("utf-8")                                         # two bytes
+    assert orc.like_prefix(s, e).tolist() == [0, 0, 0, 0, 0, 0, 0, 0, 1]
+    assert orc.like_prefix(s, e[:1]).tolist() == [0, 0, 0, 0, 0, 0, 0, 0, 1]  # a byte prefix
+
+
+@pytest.mark.parametrize("m", [1, 3, 25])
+def test_like_prefix_brute_force(m):
+    r = np.random.default_rng(m)
+    alphabet = "ABCé"
+    vals = []
+    for _ in range(3000):
+        v = "".join(alphabet[j] for j in r.integers(0, len(alphabet), r.integers(0, m + 1)))
+        while len(v.encode("utf-8")) > m:
+            v = v[:-1]
+        vals.append(v)
+    s = _pad(vals, m)
+    for k in range(0, m + 2):
+        for _ in range(3):
+            p = "".join(alphabet[j] for j in r.integers(0, 3, k)).encode("utf-8")[:k]
+            want = [1 if v.encode("utf-8").startswith(p) and len(p) <= m else 0 for v in vals]
+            assert orc.like_prefix(s, p).tolist() == want, (m, p)
