@@ -392,7 +392,67 @@ class Star:
         return time.perf_counter() - t0, f"the workload scaled by 1/{scale} (fact {nf}, dims {self.n1 // scale} and {self.n2 // scale})"
 
 
-WORKLOADS = {"q14": Q14, "q6": Q6, "skew": Skew, "batched": Batched, "star": Star}
+class Q14Promo:
+    """The promotion-revenue shape of Q14: fact(fk int32, ship_ns int64
+    epoch ns, price, disc int64) 60M rows JOIN dim(key int32, type 25-byte
+    zero-padded strings) 1.5M rows WHERE ship_ns in one 30-day month:
+    SUM(CASE WHEN type LIKE 'w%' THEN price*(100-disc) ELSE 0 END),
+    SUM(price*(100-disc))."""
+    name = "q14promo"
+    n_fact, m_dim = 60_000_000, 1_500_000
+
+    def __init__(self, master):
+        from paper_2209_04579_b300 import datagen as dg
+        self.dg = dg
+        self.rec = dg.q14_promo_tables(self.m_dim, master=master)
+        self.table, words = dg.type_strings(master=master)
+        self.prefix = words[0][0]
+        self.d0 = (dg.EPOCH_DAY0 + 1300) * dg.SECONDS_PER_DAY * 10**9
+        self.d1 = self.d0 + 30 * dg.SECONDS_PER_DAY * 10**9
+
+    def config(self):
+        return {"workload": "q14-like promotion revenue: fact 60M rows (fk int32 uniform into dim keys, ship_ns "
+                            "int64 epoch ns over 2557 days, price int64 U[90000,10500000], disc int64 U[0,10]) x dim "
+                            "1.5M rows (unique int32 keys, type: 25-byte zero-padded strings of three synthetic "
+                            "words); WHERE ship_ns in a 30-day month; SUM(CASE WHEN type LIKE '<first word>%' THEN "
+                            "price*(100-disc) ELSE 0 END), SUM(price*(100-disc))",
+                "fact_rows": self.n_fact, "dim_rows": self.m_dim, "string_width": int(self.table.shape[1])}
+
+    def make_device(self):
+        from paper_2209_04579_b300 import datagen_device as gd
+        self.fact = gd.make_table(self.rec["fact"], self.n_fact)
+        self.dim = gd.make_table(self.rec["dim"], self.m_dim)
+        self.dim["type"] = torch.from_numpy(
+            self.dg.type_column(self.m_dim, self.rec["type_seed"], self.table)).cuda()
+        return list(self.fact.values()) + [self.dim["key"], self.dim["type"]]
+
+    def step(self):
+        from paper_2209_04579_b300 import queries as Q
+        return Q.q14_promo(self.fact, self.dim, self.prefix, self.d0, self.d1)
+
+    def rows(self):
+        return self.n_fact
+
+    def alg_bytes(self):
+        # fact columns once (4 + 8 + 8 + 8 B), dim keys and strings once
+        return self.n_fact * 28 + self.m_dim * (4 + int(self.table.shape[1]))
+
+    def prof(self):
+        # the probe reads fk and ship_ns of every row, price and disc of the
+        # rows in the month (30 of 2557 days)
+        return [(1, "star_probe_kernel", self.n_fact * 12 + int(self.n_fact * 30 / 2557) * 16)]
+
+    def oracle_sample(self, rows):
+        from oracle import pipelines as pl
+        fact = self.dg.make_table(self.rec["fact"], rows)
+        dim = self.dg.make_table(self.rec["dim"], self.m_dim)
+        dim["type"] = self.dg.type_column(self.m_dim, self.rec["type_seed"], self.table)
+        t0 = time.perf_counter()
+        pl.q14_promo(fact, dim, self.prefix, self.d0, self.d1)
+        return time.perf_counter() - t0, f"first {rows} of the 60M fact rows joined with the full 1.5M-row dim"
+
+
+WORKLOADS = {"q14": Q14, "q14promo": Q14Promo, "q6": Q6, "skew": Skew, "batched": Batched, "star": Star}
 
 
 # ---------------------------------------------------------------- helpers

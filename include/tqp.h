@@ -171,6 +171,23 @@ tqp_status tqp_gather(tqp_col col, const int32_t* d_idx, int64_t n, const int64_
                       void* d_out, tqp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * tqp_like_prefix -- SQL `value LIKE 'prefix%'` over a string column held,
+ * as Section 2.1 describes, in an (n x width) byte tensor: row i (width
+ * bytes at d_str + i * width, row-major, device memory) holds the UTF-8
+ * bytes of value i right-padded with zeros.  d_out[i] = 1 when the row's
+ * first plen bytes equal prefix, else 0: an empty prefix matches every row;
+ * a prefix longer than width matches none.  The result is an int8 column
+ * that serves as a filter predicate column (d_out != 0) and, as a 0/1 value
+ * term, turns an aggregate into SUM(CASE WHEN ... THEN expr ELSE 0 END).
+ * prefix is host memory, copied at the call: plen <= 64 bytes, no zero byte.
+ * width: 1..256.  Errors: TQP_ERR_INVALID for a bad size, a null pointer or
+ * a zero byte in the prefix.  Rows are staged in shared memory with 16-byte
+ * loads when d_str is 16-byte aligned.
+ * ---------------------------------------------------------------------- */
+tqp_status tqp_like_prefix(const uint8_t* d_str, int64_t n, int32_t width, const uint8_t* prefix, int32_t plen,
+                           int8_t* d_out, tqp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * tqp_sort_pairs -- stable ascending LSD radix sort of (key, value) pairs
  * (the sort under the sort-based join and group-by of Section 2.2).
  * Keys (dtype TQP_I8..TQP_I64) are ordered by bits [begin_bit, end_bit) of

@@ -46,6 +46,22 @@ def q14(fact, dim):
     return orc.groupby_agg([region], [price], [[(0, 1, 0)]], [(orc.SUM, 0), (orc.COUNT, 0)], sel=keep)
 
 
+def q14_promo(fact, dim, prefix: bytes, d0: int, d1: int):
+    """SELECT SUM(CASE WHEN type LIKE 'prefix%' THEN price*(100-disc) ELSE 0 END),
+    SUM(price*(100-disc)) FROM fact JOIN dim ON fk = key
+    WHERE ship_ns >= d0 AND ship_ns < d1 (one group: a constant key)."""
+    pr, br = orc.join_eq(fact["fk"], dim["key"])
+    ship = orc.gather(fact["ship_ns"], pr)
+    keep = orc.filter([ship], [(0, orc.GE, d0), (0, orc.LT, d1)])
+    promo = orc.gather(orc.like_prefix(dim["type"], prefix), br)
+    price = orc.gather(fact["price"], pr)
+    disc = orc.gather(fact["disc"], pr)
+    one = np.zeros(len(pr), np.int8)
+    return orc.groupby_agg([one], [price, disc, promo], [[(0, 1, 0), (1, -1, 100), (2, 1, 0)],
+                                                        [(0, 1, 0), (1, -1, 100)]],
+                           [(orc.SUM, 0), (orc.SUM, 1)], sel=keep)
+
+
 def skew(t):
     """SELECT key, COUNT(*), SUM(value), MIN(value), MAX(value) FROM t
     GROUP BY key ORDER BY key."""

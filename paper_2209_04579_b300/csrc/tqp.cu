@@ -20,6 +20,7 @@
 #include "learned.cuh"
 #include "batched.cuh"
 #include "sort.cuh"
+#include "strings.cuh"
 #include "star.cuh"
 
 namespace tqp {
@@ -506,6 +507,33 @@ tqp_status tqp_gather(tqp_col col, const int32_t* d_idx, int64_t n, const int64_
     case TQP_I32: gather_kernel<int32_t><<<g, 256, 0, s>>>((const int32_t*)col.data, d_idx, n, d_n, (int32_t*)d_out); note_launch(); break;
     default: gather_kernel<long long><<<g, 256, 0, s>>>((const long long*)col.data, d_idx, n, d_n, (long long*)d_out); note_launch(); break;
   }
+  return last_launch();
+}
+
+tqp_status tqp_like_prefix(const uint8_t* d_str, int64_t n, int32_t width, const uint8_t* prefix, int32_t plen,
+                           int8_t* d_out, tqp_stream_t stream) {
+  if (n < 0 || width < 1 || width > kLikeMaxWidth || plen < 0 || plen > kLikeMaxPrefix || (plen && !prefix))
+    return TQP_ERR_INVALID;
+  LikePrefix p;
+  std::memset(&p, 0, sizeof(p));
+  p.k = plen;
+  for (int j = 0; j < plen; ++j) {
+    if (prefix[j] == 0) return TQP_ERR_INVALID;  // zero bytes are padding
+    p.b[j] = prefix[j];
+  }
+  if (n == 0) return TQP_OK;
+  if (!d_str || !d_out) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int smem = kLikeRows * width;
+  static bool attr = false;
+  if (!attr) {
+    TQP_CUDA(cudaFuncSetAttribute(like_prefix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kLikeRows * kLikeMaxWidth));
+    attr = true;
+  }
+  const int64_t ntiles = (n + kLikeRows - 1) / kLikeRows;
+  like_prefix_kernel<<<persistent_grid(like_prefix_kernel, 256, smem, ntiles), 256, smem, s>>>(d_str, n, width, p, d_out);
+  note_launch();
   return last_launch();
 }
 

@@ -34,6 +34,8 @@ from __future__ import annotations
 import dataclasses
 import math
 
+import itertools
+
 import numpy as np
 
 MASTER_SEED = 20220904
@@ -303,6 +305,56 @@ def star_tables(n1: int = 20_000_000, n2: int = 150_000_000, master: int = MASTE
     dim2 = {"key": Recipe(MIX64_KEY, 4, key_seed=k2),
             "cat": Recipe(UNIFORM, 1, _s(510, master), lo=0, hi=49)}
     return {"fact": fact, "dim1": dim1, "dim2": dim2}
+
+
+# ---- string columns (Section 2.1: an (n x m) byte tensor, each UTF-8 value
+# right-padded with zeros to m bytes)
+EPOCH_DAY0 = 8035          # first day of the synthetic date range, in days since the UNIX epoch
+SECONDS_PER_DAY = 86_400
+
+
+def type_strings(width: int = 25, master: int = MASTER_SEED, slots=(6, 8, 5)):
+    """Synthetic type names: one word per slot (4 to 7 uppercase letters,
+    seeded), joined by single spaces; every combination of the slots' words,
+    zero-padded to width bytes.  Returns (table [combinations, width] uint8,
+    the words of each slot)."""
+    words = []
+    for si, count in enumerate(slots):
+        u = draw(_s(600 + si, master), np.arange(count * 8, dtype=np.uint64)).reshape(count, 8)
+        slot = []
+        for w in range(count):
+            length = 4 + int(u[w, 0] % np.uint64(4))
+            slot.append(bytes(65 + int(u[w, 1 + j] % np.uint64(26)) for j in range(length)))
+        words.append(slot)
+    rows = [b" ".join(c) for c in itertools.product(*words)]
+    assert max(len(r) for r in rows) <= width
+    table = np.zeros((len(rows), width), np.uint8)
+    for i, r in enumerate(rows):
+        table[i, :len(r)] = np.frombuffer(r, np.uint8)
+    return table, words
+
+
+def type_column(n: int, seed: int, table: np.ndarray, start: int = 0) -> np.ndarray:
+    """Rows [start, start + n): each row's type drawn uniformly from the table."""
+    i = np.arange(start, start + n, dtype=np.uint64)
+    return table[uniform_from(draw(seed, i), 0, len(table) - 1)]
+
+
+def q14_promo_tables(m: int, master: int = MASTER_SEED):
+    """The promotion-revenue shape of Q14: fact(fk int32 U[1, m], ship_ns
+    int64 epoch nanoseconds at whole seconds over 2557 days, price int64
+    U[90000, 10500000], disc int64 U[0, 10]) into dim(key int32 = seeded
+    permutation of 1..m, type: 25-byte zero-padded strings).  The type column
+    is drawn on the host (type_seed) from type_strings()."""
+    s0 = EPOCH_DAY0 * SECONDS_PER_DAY
+    fact = {
+        "fk": Recipe(UNIFORM, 3, _s(611, master), lo=1, hi=m),
+        "ship_ns": Recipe(UNIFORM, 4, _s(612, master), lo=s0, hi=s0 + 2557 * SECONDS_PER_DAY - 1, mul=10**9),
+        "price": Recipe(UNIFORM, 4, _s(613, master), lo=90000, hi=10500000),
+        "disc": Recipe(UNIFORM, 4, _s(614, master), lo=0, hi=10),
+    }
+    dim = {"key": Recipe(PERM_KEY, 3, key_seed=_s(615, master), m=m, lo=1)}
+    return {"fact": fact, "dim": dim, "type_seed": _s(616, master)}
 
 
 def make_table(recipes: dict, n: int, start: int = 0, zipf: np.ndarray | None = None) -> dict:

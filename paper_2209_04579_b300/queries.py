@@ -43,6 +43,21 @@ def q14(fact, dim, cap: int = 64, learned=None):
                             [(tqp.SUM, 0), (tqp.COUNT, 0)], cap, learned=learned)
 
 
+def q14_promo(fact, dim, prefix: bytes, d0: int, d1: int):
+    """SELECT SUM(CASE WHEN type LIKE 'prefix%' THEN price*(100-disc) ELSE 0
+    END), SUM(price*(100-disc)) FROM fact JOIN dim ON fk = key WHERE ship_ns
+    >= d0 AND ship_ns < d1 -- the promotion-revenue shape of Q14 (its ratio is
+    100 * first / second).  The LIKE runs once over the dimension's string
+    tensor; its 0/1 column is the CASE's factor in the fused aggregate, and
+    the date range is two predicates on the int64 epoch-nanosecond column."""
+    promo = tqp.tqp_like_prefix(dim["type"], prefix)
+    D = tqp.DimSpec(dim["key"], cols=[promo])
+    cols = [fact["fk"], fact["ship_ns"], fact["price"], fact["disc"]]
+    return tqp.tqp_star_agg(cols, [(1, tqp.GE, d0), (1, tqp.LT, d1)], [0], [D], [(0, 2), (0, 3), (1, 0)],
+                            [[(0, 1, 0), (1, -1, 100), (2, 1, 0)], [(0, 1, 0), (1, -1, 100)]],
+                            [(tqp.SUM, 0), (tqp.SUM, 1)], 1)
+
+
 def q14_unfused(fact, dim, cap: int = 64, pair_cap: int | None = None):
     """The same query as a chain of separate operators: join (bound search +
     expand into pairs), gathers, filter on the joined rows, group-by."""

@@ -117,6 +117,7 @@ _P = ctypes.POINTER
 
 _lib.tqp_filter.argtypes = [_P(Col), _int, _P(Pred), _int, _i64, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_gather.argtypes = [Col, _vp, _i64, _vp, _vp, _vp]
+_lib.tqp_like_prefix.argtypes = [_vp, _i64, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32, _vp, _vp]
 _lib.tqp_sort_pairs.argtypes = [ctypes.c_int32, _vp, _vp, _vp, _vp, _i64, _vp, _int, _int, _vp, _P(_sz), _vp]
 _lib.tqp_join_eq.argtypes = [Col, _i64, _vp, Col, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_groupby_agg.argtypes = [_P(Col), _int, _P(Col), _int, _P(Expr), _int, _P(Agg), _int, _vp, _i64, _vp,
@@ -139,7 +140,7 @@ _lib.tqp_status_string.restype = ctypes.c_char_p
 _lib.tqp_debug_launch_count.restype = ctypes.c_int64
 _lib.tqp_debug_launch_count.argtypes = []
 _lib.tqp_profile_events.argtypes = [_int, _vp, _vp]
-for _f in ("tqp_filter", "tqp_gather", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
+for _f in ("tqp_filter", "tqp_gather", "tqp_like_prefix", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
            "tqp_star_agg_learned",
            "tqp_status_poll", "tqp_profile_events", "tqp_cdf_forward", "tqp_cdf_backward", "tqp_cdf_train",
            "tqp_groupby_agg_learned", "tqp_star_agg_batched", "tqp_debug_set_spin_limit", "tqp_debug_inject_unpublished_tile"):
@@ -270,6 +271,18 @@ def tqp_gather(col, idx, n=None, d_n=None, out=None, stream=None):
     out = torch.empty(max(n, 1), dtype=col.dtype, device=col.device) if out is None else out
     _check(_lib.tqp_gather(_col(col), _ptr(idx), n, _ptr(d_n), _ptr(out), _stream(stream)), "tqp_gather")
     return out
+
+
+def tqp_like_prefix(strings, prefix: bytes, out=None, stream=None):
+    """strings: (n, width) uint8 device tensor of zero-padded UTF-8 rows;
+    returns int8 [n], 1 where the value starts with prefix (LIKE 'prefix%')."""
+    n, width = strings.shape
+    if strings.dtype != torch.uint8 or not strings.is_contiguous():
+        raise ValueError("tqp_like_prefix: a contiguous (n, width) uint8 tensor")
+    out = torch.empty(max(n, 1), dtype=torch.int8, device=strings.device) if out is None else out
+    _check(_lib.tqp_like_prefix(_ptr(strings), n, width, bytes(prefix), len(prefix), _ptr(out), _stream(stream)),
+           "tqp_like_prefix")
+    return out[:n]
 
 
 def tqp_sort_pairs(keys, vals=None, begin_bit=0, end_bit=None, n=None, d_n=None, stream=None):

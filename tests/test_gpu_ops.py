@@ -226,3 +226,54 @@ def test_bounded_wait_timeout_keeps_context_usable(T):
     out, cnt = T.tqp_filter([dev(c)], [(0, T.GE, 0)])
     assert int(cnt.item()) == len(c) and np.array_equal(host(out), c)
     assert T.tqp_status_poll() == T.OK
+
+
+# ---------------------------------------------------------------- strings
+def string_tensor(r, n, width, alphabet=b"ABC"):
+    """n zero-padded rows of random lengths 0..width over a small alphabet."""
+    s = np.zeros((n, width), np.uint8)
+    lens = r.integers(0, width + 1, n)
+    letters = np.frombuffer(alphabet, np.uint8)[r.integers(0, len(alphabet), (n, width))]
+    mask = np.arange(width)[None, :] < lens[:, None]
+    s[mask] = letters[mask]
+    return s
+
+
+@pytest.mark.parametrize("width", [1, 7, 25, 256])
+@pytest.mark.parametrize("n", [0, 1, 511, 512, 513, 100_003])
+def test_like_prefix(T, width, n):
+    r = rng(width * 1000 + n)
+    s = string_tensor(r, n, width)
+    d = dev(s)
+    # prefixes: empty, short, the full width, longer than the width (up to
+    # the 64-byte limit of the call)
+    for p in [b"", b"A", b"AB", b"ABCA"[: max(1, min(4, width))], b"C" * min(width, 64), b"B" * min(width + 1, 64)]:
+        got = T.tqp_like_prefix(d, p)
+        assert np.array_equal(host(got), orc.like_prefix(s, p)), p
+
+
+def test_like_prefix_unaligned_rows_and_utf8(T):
+    """A column that starts off a 16-byte boundary (byte loads), and
+    multi-byte UTF-8 values with byte prefixes inside a character."""
+    r = rng(5)
+    vals = ["été", "étage", "ete", "é", "", "abé"] * 5000
+    m = 9
+    s = np.zeros((len(vals), m), np.uint8)
+    for i, v in enumerate(vals):
+        b = v.encode("utf-8")
+        s[i, :len(b)] = np.frombuffer(b, np.uint8)
+    flat = torch.zeros(s.size + 16, dtype=torch.uint8, device="cuda")
+    off = flat[3:3 + s.size].view(len(vals), m)
+    off.copy_(dev(s))
+    assert off.data_ptr() % 16 == 3
+    for p in ["é".encode(), "é".encode()[:1], "ét".encode(), b"a", b"e"]:
+        assert np.array_equal(host(T.tqp_like_prefix(off, p)), orc.like_prefix(s, p)), p
+    del r
+
+
+def test_like_prefix_rejects_zero_byte_and_long_prefix(T):
+    d = dev(np.zeros((4, 8), np.uint8))
+    with pytest.raises(Exception):
+        T.tqp_like_prefix(d, b"A\x00B")
+    with pytest.raises(Exception):
+        T.tqp_like_prefix(d, b"A" * 65)

@@ -254,6 +254,32 @@ def test_q14_repeated_dimension_key_is_unsupported(G, stride):
     assert tqp.tqp_status_poll() == tqp.ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("n,m", [(1, 10), (100_000, 5_000), (6_000_000, 1_500_000)])
+def test_q14_promo(G, n, m):
+    """The promotion-revenue shape of Q14: LIKE over the dimension's
+    zero-padded string tensor, its 0/1 column as the CASE factor of one
+    aggregate, and a one-month range on the epoch-nanosecond ship column."""
+    tqp, Q, gd = G
+    rec = dg.q14_promo_tables(m)
+    table, words = dg.type_strings()
+    d0 = (dg.EPOCH_DAY0 + 1300) * dg.SECONDS_PER_DAY * 10**9
+    d1 = d0 + 30 * dg.SECONDS_PER_DAY * 10**9
+    fact_h = dg.make_table(rec["fact"], n)
+    dim_h = dg.make_table(rec["dim"], m)
+    dim_h["type"] = dg.type_column(m, rec["type_seed"], table)
+    fact = gd.make_table(rec["fact"], n)
+    dim = gd.make_table(rec["dim"], m)
+    dim["type"] = torch.from_numpy(dim_h["type"]).cuda()
+    for prefix, lo, hi in [(words[0][0], d0, d1), (words[0][2][:2], d0, d1), (b"", d0, d1 + 400 * 86_400 * 10**9),
+                           (b"Q" * 26, d0, d1)]:
+        want = pl.q14_promo(fact_h, dim_h, prefix, lo, hi)
+        keys, aggs, g = Q.q14_promo(fact, dim, prefix, lo, hi)
+        G_ = want[1].shape[0]
+        assert int(g.item()) == G_
+        assert np.array_equal(host(aggs)[:G_], want[1])
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
 # group columns of the two dimensions: dtype and the span of their values.
 # Spans below 2^24 rank through the value-domain bitmap, wider ones through
 # the sort of the packed group keys; both paths meet at the 2^24 boundary.
