@@ -452,7 +452,64 @@ class Q14Promo:
         return time.perf_counter() - t0, f"first {rows} of the 60M fact rows joined with the full 1.5M-row dim"
 
 
-WORKLOADS = {"q14": Q14, "q14promo": Q14Promo, "q6": Q6, "skew": Skew, "batched": Batched, "star": Star}
+class Predict:
+    """A prediction query over 100M reviews: rating, the count of rows whose
+    network output over score is at least one half, and COUNT(*), among the
+    rows with votes >= 5 (synthetic weights of the 1 -> 64 -> 1 network)."""
+    name = "predict"
+    n = 100_000_000
+    min_votes = 5
+
+    def __init__(self, master):
+        from paper_2209_04579_b300 import datagen as dg
+        self.dg = dg
+        self.rec = dg.reviews_table(master=master)
+        self.w, self.b, self.a, self.c = dg.predict_model(master=master)
+
+    def config(self):
+        return {"workload": "prediction query: 100M reviews (score float32 U[0,1) on a 2^-24 grid, rating int8 "
+                            "U[1,5], votes int32 U[0,50]); SELECT rating, SUM(CASE WHEN PREDICT(net, score) >= 0.5 "
+                            "THEN 1 ELSE 0 END), COUNT(*) WHERE votes >= 5 GROUP BY rating; net: 1->64->1 monotone "
+                            "MLP with synthetic weights", "rows": self.n}
+
+    def make_device(self):
+        from paper_2209_04579_b300 import datagen_device as gd
+        from paper_2209_04579_b300 import tqp
+        t = gd.make_table(self.rec, self.n)
+        self.t = {"score": t["score_q"].to(torch.float32) / 2**self.dg.SCORE_BITS, "rating": t["rating"],
+                  "votes": t["votes"]}
+        self.model = tqp.model_to_device(self.w, self.b, self.a, self.c)
+        return [self.t["score"], self.t["rating"], self.t["votes"]]
+
+    def step(self):
+        from paper_2209_04579_b300 import queries as Q
+        return Q.predict(self.t, self.model, self.min_votes)
+
+    def rows(self):
+        return self.n
+
+    def alg_bytes(self):
+        # score, rating and votes once; the 0/1 prediction written and read back once
+        return self.n * (4 + 1 + 4) + self.n * 4 * 2
+
+    def prof(self):
+        n = self.n
+        sel = int(n * 46 / 51)
+        # forward: score in, output and its bucket out; filter: votes in, ids
+        # out; reduce: packed key and row id per selected row, the prediction by row
+        return [(10, "cdf_forward_kernel", n * 12), (3, "filter_kernel", n * 4 + sel * 4),
+                (4, "gb_reduce_kernel", sel * 8 + sel * 4)]
+
+    def oracle_sample(self, rows):
+        from oracle import pipelines as pl
+        t = self.dg.make_table(self.rec, rows)
+        t["score"] = (t["score_q"].astype(np.float64) / 2**self.dg.SCORE_BITS).astype(np.float32)
+        t0 = time.perf_counter()
+        pl.predict(t, (self.w, self.b, self.a, self.c), self.min_votes)
+        return time.perf_counter() - t0, f"first {rows} of the 100M reviews"
+
+
+WORKLOADS = {"q14": Q14, "q14promo": Q14Promo, "predict": Predict, "q6": Q6, "skew": Skew, "batched": Batched, "star": Star}
 
 
 # ---------------------------------------------------------------- helpers

@@ -62,6 +62,17 @@ def q14_promo(fact, dim, prefix: bytes, d0: int, d1: int):
                            [(orc.SUM, 0), (orc.SUM, 1)], sel=keep)
 
 
+def predict(t, model, min_votes: int):
+    """SELECT rating, SUM(CASE WHEN PREDICT(model, score) >= 0.5 THEN 1 ELSE
+    0 END), COUNT(*) FROM reviews WHERE votes >= min_votes GROUP BY rating
+    ORDER BY rating.  model: (w, b, a, c); the prediction is the float32
+    network output's bucket of two."""
+    w, b, a, c = model
+    positive = orc.cdf_bucket(orc.cdf_forward_f32(w, b, a, c, t["score"]), 2)
+    keep = orc.filter([t["votes"]], [(0, orc.GE, min_votes)])
+    return orc.groupby_agg([t["rating"]], [positive], [[(0, 1, 0)]], [(orc.SUM, 0), (orc.COUNT, 0)], sel=keep)
+
+
 def skew(t):
     """SELECT key, COUNT(*), SUM(value), MIN(value), MAX(value) FROM t
     GROUP BY key ORDER BY key."""

@@ -357,5 +357,30 @@ def q14_promo_tables(m: int, master: int = MASTER_SEED):
     return {"fact": fact, "dim": dim, "type_seed": _s(616, master)}
 
 
+# ---- prediction query: reviews and a synthetic network
+SCORE_BITS = 24  # score = score_q / 2^24, exact in float32
+
+
+def reviews_table(master: int = MASTER_SEED):
+    """reviews(score_q int32 U[0, 2^24 - 1] (the model input is score_q / 2^24),
+    rating int8 U[1, 5], votes int32 U[0, 50])."""
+    return {"score_q": Recipe(UNIFORM, 3, _s(621, master), lo=0, hi=(1 << SCORE_BITS) - 1),
+            "rating": Recipe(UNIFORM, 1, _s(622, master), lo=1, hi=5),
+            "votes": Recipe(UNIFORM, 3, _s(623, master), lo=0, hi=50)}
+
+
+def predict_model(H: int = 64, master: int = MASTER_SEED):
+    """Synthetic weights of the 1 -> H -> 1 monotone network (no trained
+    model is used): unit j ramps over [k_j, k_j + 1/s_j] with a random knot
+    k_j in [0, 1) and slope s_j in [2, 18); output weights a_j sum to about
+    one.  Returns float32 (w, b, a, c)."""
+    u = draw(_s(624, master), np.arange(3 * H, dtype=np.uint64)).reshape(3, H)
+    f = (u >> np.uint64(40)).astype(np.float64) / float(1 << 24)
+    w = (2.0 + 16.0 * f[0]).astype(np.float32)
+    b = (-w.astype(np.float64) * f[1]).astype(np.float32)
+    a = (2.0 * f[2] / H).astype(np.float32)
+    return w, b, a, np.float32(0.0)
+
+
 def make_table(recipes: dict, n: int, start: int = 0, zipf: np.ndarray | None = None) -> dict:
     return {name: generate(r, n, start, zipf) for name, r in recipes.items()}

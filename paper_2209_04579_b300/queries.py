@@ -119,3 +119,17 @@ def star(fact, dim1, dim2, cap: int = 50_000, learned=None):
     return tqp.tqp_star_agg(cols, [(5, tqp.LT, STAR_DATE_LT)], [0, 1], [D1, D2], [(0, 2), (0, 3), (0, 4)],
                             [[(0, 1, 0)], [(1, 1, 0)], [(2, 1, 0)]],
                             [(tqp.SUM, 0), (tqp.SUM, 1), (tqp.SUM, 2), (tqp.COUNT, 0)], cap, learned=learned)
+
+
+def predict(t, model, min_votes: int, cap: int = 16):
+    """SELECT rating, SUM(CASE WHEN PREDICT(model, score) >= 0.5 THEN 1 ELSE
+    0 END), COUNT(*) FROM reviews WHERE votes >= min_votes GROUP BY rating --
+    a prediction query (Section 3.3): the network's output over the score
+    column, as its bucket of two (0/1: output below or at least one half),
+    is the CASE factor of a filtered group-by.  Every step runs in the
+    library's kernels on one stream, so the whole query captures into one
+    CUDA graph."""
+    _, positive = tqp.tqp_cdf_forward(model, t["score"], B=2)
+    sel, cnt = tqp.tqp_filter([t["votes"]], [(0, tqp.GE, min_votes)])
+    return tqp.tqp_groupby_agg([t["rating"]], [positive], [[(0, 1, 0)]], [(tqp.SUM, 0), (tqp.COUNT, 0)], cap,
+                               sel=sel, n=t["votes"].numel(), d_n=cnt)

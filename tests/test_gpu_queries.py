@@ -280,6 +280,24 @@ def test_q14_promo(G, n, m):
     assert tqp.tqp_status_poll() == tqp.OK
 
 
+@pytest.mark.parametrize("n", [1, 100_003, 10_000_000])
+def test_predict_query(G, n):
+    """The prediction query: the network's output over a float column,
+    thresholded at one half, counted per rating among the filtered rows."""
+    tqp, Q, gd = G
+    rec = dg.reviews_table()
+    host_t = dg.make_table(rec, n)
+    host_t["score"] = (host_t["score_q"].astype(np.float64) / 2**dg.SCORE_BITS).astype(np.float32)
+    t = gd.make_table(rec, n)
+    t["score"] = t["score_q"].to(torch.float32) / 2**dg.SCORE_BITS
+    assert np.array_equal(host(t["score"]), host_t["score"])
+    w, b, a, c = dg.predict_model()
+    model = tqp.model_to_device(w, b, a, c)
+    for votes in (0, 5, 51):
+        compare(Q.predict(t, model, votes), pl.predict(host_t, (w, b, a, c), votes))
+    assert tqp.tqp_status_poll() == tqp.OK
+
+
 # group columns of the two dimensions: dtype and the span of their values.
 # Spans below 2^24 rank through the value-domain bitmap, wider ones through
 # the sort of the packed group keys; both paths meet at the 2^24 boundary.
