@@ -130,9 +130,11 @@ class Q6:
 
     def prof(self):
         sel = int(self.n * 0.939)
-        return [(4, "gb_reduce_kernel", sel * (4 + 32)),          # row ids + the 4 value columns per selected row
-                (3, "filter_kernel", self.n * 4 + sel * 4),        # ship_day in, selected row ids out
-                (2, "sort_pass_kernel (whole sort)", sel * 8 * 2)]  # one pass of (u32 key, row id) in and out
+        # the packed key (flag_a, flag_b) spans 3 bits: the rows fold straight
+        # into slots (no sort); per selected row its id, the 2 key bytes and
+        # the 4 value columns
+        return [(4, "gb_direct_kernel", sel * (4 + 2 + 32)),
+                (3, "filter_kernel", self.n * 4 + sel * 4)]        # ship_day in, selected row ids out
 
     def oracle_sample(self, rows):
         from oracle import pipelines as pl
@@ -496,9 +498,10 @@ class Predict:
         n = self.n
         sel = int(n * 46 / 51)
         # forward: score in, output and its bucket out; filter: votes in, ids
-        # out; reduce: packed key and row id per selected row, the prediction by row
+        # out; the group-by (a 3-bit key: slots, no sort): per selected row
+        # its id, the rating byte and the prediction
         return [(10, "cdf_forward_kernel", n * 12), (3, "filter_kernel", n * 4 + sel * 4),
-                (4, "gb_reduce_kernel", sel * 8 + sel * 4)]
+                (4, "gb_direct_kernel", sel * (4 + 1 + 4))]
 
     def oracle_sample(self, rows):
         from oracle import pipelines as pl

@@ -540,4 +540,142 @@ __global__ void gb_carry_kernel(ReduceArgs a, AggProgram P) {
   }
 }
 
+// ---------------------------------------------------------------- small key domains
+// When the packed group key spans at most 2^kDirectBits values (a handful
+// of flags, a rating, a region), the packed key is itself the group's slot
+// in key order: the rows fold straight into per-warp slot accumulators in
+// shared memory, with no sort.  The decision is the device's (the packed
+// width is known only after the key range pass); the sort path then runs
+// on no rows.
+constexpr int kDirectBits = 10;
+constexpr int kDirectSlots = 1 << kDirectBits;
+constexpr int kDirectSmemBytes = 96 * 1024;  // the accumulator copies of one block
+
+// One thread: direct[0] = 1 when the packed key fits the slots; sort_n:
+// the rows the sort path then takes (0 when direct).
+__global__ void gb_direct_plan_kernel(const GroupPlan* plan, int64_t n_max, const int64_t* d_n, int* direct,
+                                      int64_t* sort_n) {
+  if (threadIdx.x != 0) return;
+  const int64_t n = clamp_n(n_max, d_n);
+  const int on = n > 0 && !plan->unsupported && plan->total_bits <= kDirectBits;
+  *direct = on;
+  *sort_n = on ? 0 : n;
+}
+
+// Identity of every accumulator (naggs aggregates + the row count) of every slot.
+__global__ void gb_direct_init_kernel(const int* direct, AggProgram P, long long* acc) {
+  if (!*direct) return;
+  const int nacc = P.naggs + 1;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kDirectSlots * nacc; i += gridDim.x * blockDim.x) {
+    const int q = i % nacc;
+    acc[i] = q < P.naggs ? agg_identity(P.op[q]) : 0;
+  }
+}
+
+__device__ __forceinline__ void direct_fold(long long* slot, int op, long long x, bool shared) {
+  switch (op) {
+    case TQP_MIN: atomicMin(slot, x); break;
+    case TQP_MAX: atomicMax(slot, x); break;
+    default:
+      if (shared) shared_add_u64(reinterpret_cast<unsigned long long*>(slot), (unsigned long long)x);
+      else atomicAdd(reinterpret_cast<unsigned long long*>(slot), (unsigned long long)x);
+      break;
+  }
+}
+
+// Rows fold into one accumulator copy per warp (as many copies as fit),
+// merged into the global slots at the end.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) gb_direct_kernel(KeySet ks, const int32_t* sel, int64_t n_max,
+                                                            const int64_t* d_n, const GroupPlan* plan,
+                                                            AggProgram Pg, const int* direct, long long* acc) {
+  extern __shared__ long long s_dacc[];
+  __shared__ long long s_kmin[TQP_MAX_KEYS];
+  __shared__ int s_shift[TQP_MAX_KEYS];
+  __shared__ AggProgram P;  // indexed by runtime values: kept in shared memory
+  __shared__ const void* s_col[TQP_MAX_KEYS];
+  __shared__ int s_dt[TQP_MAX_KEYS];
+  if (!*direct) return;
+  if (threadIdx.x == 0) P = Pg;
+  if (threadIdx.x < TQP_MAX_KEYS) {
+    s_col[threadIdx.x] = ks.col[threadIdx.x];
+    s_dt[threadIdx.x] = ks.dt[threadIdx.x];
+    s_kmin[threadIdx.x] = plan->kmin[threadIdx.x];
+    s_shift[threadIdx.x] = plan->shift[threadIdx.x];
+  }
+  __syncthreads();  // the program and the key plan, before any thread reads them
+  constexpr int WARPS = THREADS / 32;
+  const int nacc = P.naggs + 1;
+  const int slots = 1 << plan->total_bits;
+  const int per = slots * nacc;
+  int copies = (kDirectSmemBytes / 8) / per;
+  copies = copies < 1 ? 1 : (copies > WARPS ? WARPS : copies);
+  for (int i = threadIdx.x; i < per * copies; i += THREADS) {
+    const int q = (i % per) % nacc;
+    s_dacc[i] = q < P.naggs ? agg_identity(P.op[q]) : 0;
+  }
+  __syncthreads();
+  long long* my = s_dacc + ((threadIdx.x >> 5) % copies) * per;
+  const int64_t n = clamp_n(n_max, d_n);
+  const int64_t stride = (int64_t)gridDim.x * THREADS;
+  for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < n; i += stride) {
+    const int64_t row = sel ? sel[i] : i;
+    unsigned long long u = 0;
+    for (int k = 0; k < ks.nkeys; ++k)
+      u |= ((unsigned long long)load_as_i64(s_col[k], s_dt[k], row) - (unsigned long long)s_kmin[k]) << s_shift[k];
+    long long* dst = my + (int)u * nacc;
+    for (int q = 0; q < P.naggs; ++q)
+      direct_fold(dst + q, P.op[q], P.op[q] == TQP_COUNT ? 1 : eval_expr(P, P.expr[q], row), true);
+    shared_add_u64(reinterpret_cast<unsigned long long*>(dst + P.naggs), 1ull);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < per; i += THREADS) {
+    const int q = i % nacc;
+    long long v = s_dacc[i];
+    for (int w = 1; w < copies; ++w) {
+      const long long x = s_dacc[w * per + i];
+      v = q < P.naggs ? agg_fold(P.op[q], v, x) : v + x;
+    }
+    if (v == (q < P.naggs ? agg_identity(P.op[q]) : 0)) continue;
+    direct_fold(&acc[i], q < P.naggs ? P.op[q] : TQP_SUM, v, false);
+  }
+}
+
+// One block: the non-empty slots in key order become the groups.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) gb_direct_out_kernel(KeySet ks, const GroupPlan* plan, AggProgram P,
+                                                                const int* direct, const long long* acc,
+                                                                long long* out_aggs, int64_t cap,
+                                                                int64_t* d_out_groups) {
+  __shared__ int s_scan[33];
+  if (!*direct) return;
+  const int nacc = P.naggs + 1;
+  const int slots = 1 << plan->total_bits;
+  constexpr int PER = kDirectSlots / THREADS;
+  int live[PER];
+  int cnt = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int sl = threadIdx.x * PER + j;
+    live[j] = sl < slots && acc[(long long)sl * nacc + P.naggs] > 0;
+    cnt += live[j];
+  }
+  int total;
+  long long g = block_exclusive_sum<THREADS>(cnt, s_scan, &total);
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    if (!live[j]) continue;
+    const int sl = threadIdx.x * PER + j;
+    if (g < cap) {
+      write_group_keys(ks, plan, g, (unsigned long long)sl);
+      for (int q = 0; q < P.naggs; ++q) out_aggs[g * P.naggs + q] = acc[(long long)sl * nacc + q];
+    }
+    ++g;
+  }
+  if (threadIdx.x == 0) {
+    *d_out_groups = total;
+    if (total > cap) raise_status(TQP_ERR_CAPACITY);
+  }
+}
+
 }  // namespace tqp

@@ -204,6 +204,9 @@ struct GroupWs {
   uint32_t* ctrl;  // reduce counter + flags
   Partial* carry;
   uint32_t tiles;
+  int* direct;       // small key domain: slots instead of the sort
+  int64_t* sort_n;   // rows the sort path takes (0 when direct)
+  long long* dacc;   // the slots' accumulators
 };
 
 // From this many rows on, the value columns are gathered into sorted order
@@ -227,6 +230,9 @@ GroupWs carve_group(Carver& c, int64_t n, int word_bytes, const AggProgram* P = 
   w.tiles = (uint32_t)t;
   w.ctrl = c.take<uint32_t>((size_t)(t > 0 ? t : 1));
   w.carry = c.take<Partial>((size_t)(t > 0 ? t : 1));
+  w.direct = c.take<int>(1);
+  w.sort_n = c.take<int64_t>(1);
+  w.dacc = c.take<long long>((size_t)kDirectSlots * (TQP_MAX_AGGS + 1));
   return w;
 }
 
@@ -335,21 +341,25 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
   gb_init_kernel<<<1, 32, 0, s>>>(w.plan); note_launch();
   gb_keyrange_kernel<256><<<stride_grid(n, 256, 4), 256, 0, s>>>(ks, sel, n, d_n, w.plan); note_launch();
   gb_plan_kernel<<<1, 32, 0, s>>>(w.plan, ks.nkeys, word_bytes * 8); note_launch();
+  // a packed key of at most kDirectBits bits folds straight into slots (after
+  // the sort path, which then takes no rows and counts no groups)
+  gb_direct_plan_kernel<<<1, 32, 0, s>>>(w.plan, n, d_n, w.direct, w.sort_n); note_launch();
+  const int64_t* sn = w.sort_n;
   if (word_bytes == 4) {
-    gb_encode_kernel<uint32_t><<<stride_grid(n, 256), 256, 0, s>>>(ks, sel, n, d_n, w.plan,
+    gb_encode_kernel<uint32_t><<<stride_grid(n, 256), 256, 0, s>>>(ks, sel, n, sn, w.plan,
                                                                      static_cast<uint32_t*>(w.packed), w.rows); note_launch();
   } else {
     gb_encode_kernel<unsigned long long><<<stride_grid(n, 256), 256, 0, s>>>(
-        ks, sel, n, d_n, w.plan, static_cast<unsigned long long*>(w.packed), w.rows); note_launch();
+        ks, sel, n, sn, w.plan, static_cast<unsigned long long*>(w.packed), w.rows); note_launch();
   }
   tqp_status st = run_sort(w.sort, word_bytes == 4 ? kKeyU32 : kKeyU64, w.packed, w.rows, w.sorted,
-                           w.sorted_rows, n, d_n, 0, word_bytes * 8, s);
+                           w.sorted_rows, n, sn, 0, word_bytes * 8, s);
   if (st != TQP_OK) return st;
   ReduceArgs r;
   r.keys = w.sorted;
   r.rows = w.sorted_rows;
   r.n_max = n;
-  r.d_n = d_n;
+  r.d_n = sn;
   r.plan = w.plan;
   r.ks = ks;
   r.out_aggs = out_aggs;
@@ -364,7 +374,7 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
   AggProgram Pr = P;
   const bool self_gather = P.simple && P.nvals == 1;  // the reduce reads the values through the row ids
   if ((w.gathered[0] && !self_gather) || P.nvals == 0) {
-    if (P.nvals) Pr = pregather_values(P, w.gathered, w.sorted_rows, n, d_n, s);
+    if (P.nvals) Pr = pregather_values(P, w.gathered, w.sorted_rows, n, sn, s);
     r.rows = nullptr;
   }
   if (word_bytes == 4) {
@@ -372,6 +382,20 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
   } else {
     launch_reduce<unsigned long long>(r, Pr, w.tiles, s);
   }
+  static bool attr = false;
+  if (!attr) {
+    TQP_CUDA(cudaFuncSetAttribute(gb_direct_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kDirectSmemBytes));
+    attr = true;
+  }
+  gb_direct_init_kernel<<<8, 256, 0, s>>>(w.direct, P, w.dacc); note_launch();
+  prof_mark(4, true, s);
+  gb_direct_kernel<256><<<stride_grid(n, 256, 2), 256, kDirectSmemBytes, s>>>(ks, sel, n, d_n, w.plan, P, w.direct,
+                                                                              w.dacc);
+  note_launch();
+  prof_mark(4, false, s);
+  gb_direct_out_kernel<1024><<<1, 1024, 0, s>>>(ks, w.plan, P, w.direct, w.dacc, out_aggs, cap, d_out_groups);
+  note_launch();
   return last_launch();
 }
 

@@ -179,6 +179,39 @@ def test_groupby_shapes(T, n):
                   GB_AGGS)
 
 
+@pytest.mark.parametrize("n", [1, 4097, 300_001])
+def test_groupby_small_key_domains(T, n):
+    """A packed key of at most 10 bits folds straight into slots (no sort);
+    11 bits take the sort.  Both sides of the boundary, two keys packed into
+    one slot index, every aggregate, and a selection."""
+    r = rng(n + 5)
+    vals = [col(r, n, np.int64, -10**9, 10**9), col(r, n, np.int32), col(r, n, np.int16)]
+
+    def with_ends(k, lo, hi):
+        k[:2] = [lo, hi][:len(k[:2])]
+        return k
+
+    check_groupby(T, [with_ends(col(r, n, np.int16, -512, 511), -512, 511)], vals, GB_EXPRS, GB_AGGS)
+    check_groupby(T, [with_ends(col(r, n, np.int16, -512, 512), -512, 512)], vals, GB_EXPRS, GB_AGGS)
+    check_groupby(T, [col(r, n, np.int8, 0, 31), col(r, n, np.int64, -16, 15)], vals, GB_EXPRS, GB_AGGS)
+    sel = np.sort(r.choice(n, max(1, n // 3), replace=False)).astype(np.int32)
+    check_groupby(T, [col(r, n, np.int8, -2, 5)], vals, GB_EXPRS, GB_AGGS, sel=sel)
+
+
+def test_groupby_small_domain_capacity(T):
+    """More groups than the capacity: the count is still the group count,
+    the first groups are written, and the status reports the overflow."""
+    r = rng(8)
+    n = 10_000
+    k = col(r, n, np.int8, 0, 7)
+    v = col(r, n, np.int64, -1000, 1000)
+    wk, wa, _ = orc.groupby_agg([k], [v], [[(0, 1, 0)]], [(orc.SUM, 0), (orc.COUNT, 0)])
+    ok, oa, g = T.tqp_groupby_agg([dev(k)], [dev(v)], [[(0, 1, 0)]], [(orc.SUM, 0), (orc.COUNT, 0)], 3)
+    assert int(g.item()) == wa.shape[0] == 8
+    assert np.array_equal(host(oa)[:3], wa[:3]) and np.array_equal(host(ok[0])[:3].astype(np.int64), wk[0][:3])
+    assert T.tqp_status_poll() == T.ERR_CAPACITY
+
+
 def test_groupby_degenerate(T):
     r = rng(2)
     n = 100_000
