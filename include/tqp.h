@@ -223,7 +223,11 @@ tqp_status tqp_join_eq(tqp_col probe, int64_t n_probe, const int64_t* d_n_probe,
  * lexicographic signed key order; d_out_keys[k] receives key column k (its
  * own dtype, capacity cap); d_out_aggs[g * naggs + a] the aggregates
  * (int64).  G goes to *d_out_groups.  The packed key must fit in 64 bits,
- * else the device status records TQP_ERR_UNSUPPORTED and G = 0.
+ * else the device status records TQP_ERR_UNSUPPORTED and G = 0.  A packed
+ * key of at most 10 bits (decided on the device from the key range) is its
+ * own group slot: the rows are folded into slot accumulators without the
+ * sort, with the same results.  More than cap groups: the first cap are
+ * written, G is the full count, and the status records TQP_ERR_CAPACITY.
  * ---------------------------------------------------------------------- */
 tqp_status tqp_groupby_agg(const tqp_col* keys, int nkeys, const tqp_col* vals, int nvals,
                            const tqp_expr* exprs, int nexprs, const tqp_agg* aggs, int naggs,
