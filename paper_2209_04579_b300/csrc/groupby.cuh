@@ -549,7 +549,7 @@ __global__ void gb_carry_kernel(ReduceArgs a, AggProgram P) {
 // on no rows.
 constexpr int kDirectBits = 10;
 constexpr int kDirectSlots = 1 << kDirectBits;
-constexpr int kDirectSmemBytes = 96 * 1024;  // the accumulator copies of one block
+constexpr int kDirectMaxSmemBytes = kDirectSlots * (TQP_MAX_AGGS + 1) * 8;  // one copy of the widest program
 
 // One thread: direct[0] = 1 when the packed key fits the slots; sort_n:
 // the rows the sort path then takes (0 when direct).
@@ -583,12 +583,14 @@ __device__ __forceinline__ void direct_fold(long long* slot, int op, long long x
   }
 }
 
-// Rows fold into one accumulator copy per warp (as many copies as fit),
+// Rows fold into one accumulator copy per warp (as many copies as fit in
+// smem_bytes, which holds at least one copy of all 2^kDirectBits slots),
 // merged into the global slots at the end.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) gb_direct_kernel(KeySet ks, const int32_t* sel, int64_t n_max,
                                                             const int64_t* d_n, const GroupPlan* plan,
-                                                            AggProgram Pg, const int* direct, long long* acc) {
+                                                            AggProgram Pg, const int* direct, long long* acc,
+                                                            int smem_bytes) {
   extern __shared__ long long s_dacc[];
   __shared__ long long s_kmin[TQP_MAX_KEYS];
   __shared__ int s_shift[TQP_MAX_KEYS];
@@ -608,7 +610,7 @@ __global__ void __launch_bounds__(THREADS) gb_direct_kernel(KeySet ks, const int
   const int nacc = P.naggs + 1;
   const int slots = 1 << plan->total_bits;
   const int per = slots * nacc;
-  int copies = (kDirectSmemBytes / 8) / per;
+  int copies = (smem_bytes / 8) / per;
   copies = copies < 1 ? 1 : (copies > WARPS ? WARPS : copies);
   for (int i = threadIdx.x; i < per * copies; i += THREADS) {
     const int q = (i % per) % nacc;

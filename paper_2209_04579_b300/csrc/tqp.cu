@@ -385,13 +385,15 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
   static bool attr = false;
   if (!attr) {
     TQP_CUDA(cudaFuncSetAttribute(gb_direct_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kDirectSmemBytes));
+                                  kDirectMaxSmemBytes));
     attr = true;
   }
+  // shared memory for one copy of every slot of this program: a narrow
+  // program leaves room for several blocks per SM (the fold waits on reads)
+  const int dsm = kDirectSlots * (P.naggs + 1) * 8;
   gb_direct_init_kernel<<<8, 256, 0, s>>>(w.direct, P, w.dacc); note_launch();
   prof_mark(4, true, s);
-  gb_direct_kernel<256><<<stride_grid(n, 256, 2), 256, kDirectSmemBytes, s>>>(ks, sel, n, d_n, w.plan, P, w.direct,
-                                                                              w.dacc);
+  gb_direct_kernel<256><<<stride_grid(n, 256, 8), 256, dsm, s>>>(ks, sel, n, d_n, w.plan, P, w.direct, w.dacc, dsm);
   note_launch();
   prof_mark(4, false, s);
   gb_direct_out_kernel<1024><<<1, 1024, 0, s>>>(ks, w.plan, P, w.direct, w.dacc, out_aggs, cap, d_out_groups);
