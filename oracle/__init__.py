@@ -49,6 +49,7 @@ def lib():
         _lib.orc_join_eq.restype = ctypes.c_int64
         _lib.orc_groupby_agg.restype = ctypes.c_int64
         _lib.orc_cdf_grad_f64.restype = ctypes.c_double
+        _lib.orc_string_codes.restype = ctypes.c_int64
     return _lib
 
 
@@ -225,3 +226,13 @@ def like_prefix(strings, prefix: bytes):
     out = np.empty(n, dtype=np.int8)
     lib().orc_like_prefix(_p(s), ctypes.c_int64(n), m, _p(np.ascontiguousarray(p)), len(prefix), _p(out))
     return out
+
+
+def string_codes(strings):
+    """(codes int32 [n], number of distinct values): each row's rank among
+    the distinct zero-padded rows in ascending byte order."""
+    s = np.ascontiguousarray(strings, dtype=np.uint8)
+    n, m = s.shape
+    code = np.empty(n, dtype=np.int32)
+    k = lib().orc_string_codes(_p(s), ctypes.c_int64(n), m, _p(code))
+    return code, int(k)

@@ -388,4 +388,17 @@ void orc_like_prefix(const uint8_t* str, int64_t n, int m, const uint8_t* prefix
   }
 }
 
+// Dictionary codes of a string column: code[i] = the rank of row i's value
+// among the column's distinct values in ascending byte order (the zero
+// padding sorts a value before every longer value it prefixes), and the
+// number of distinct values.  Grouping by the code groups by the string.
+int64_t orc_string_codes(const uint8_t* str, int64_t n, int m, int32_t* code) {
+  std::map<std::vector<uint8_t>, int32_t> dict;
+  for (int64_t i = 0; i < n; ++i) dict.emplace(std::vector<uint8_t>(str + i * m, str + (i + 1) * m), 0);
+  int32_t next = 0;
+  for (auto& kv : dict) kv.second = next++;
+  for (int64_t i = 0; i < n; ++i) code[i] = dict[std::vector<uint8_t>(str + i * m, str + (i + 1) * m)];
+  return (int64_t)dict.size();
+}
+
 }  // extern "C"

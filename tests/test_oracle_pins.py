@@ -448,3 +448,22 @@ def test_like_prefix_brute_force(m):
             p = "".join(alphabet[j] for j in r.integers(0, 3, k)).encode("utf-8")[:k]
             want = [1 if v.encode("utf-8").startswith(p) and len(p) <= m else 0 for v in vals]
             assert orc.like_prefix(s, p).tolist() == want, (m, p)
+
+
+@pytest.mark.parametrize("m", [1, 9, 25])
+def test_string_codes_brute_force(m):
+    r = np.random.default_rng(40 + m)
+    vals = ["", "a", "ab", "b", "é", "aé", "ba"] + ["".join("ab"[j] for j in r.integers(0, 2, r.integers(0, 4)))
+                                                  for _ in range(500)]
+    vals = [v for v in vals if len(v.encode("utf-8")) <= m]
+    s = _pad(vals, m)
+    code, k = orc.string_codes(s)
+    distinct = sorted(set(v.encode("utf-8") for v in vals))   # bytes order: a prefix sorts first
+    assert k == len(distinct)
+    assert code.tolist() == [distinct.index(v.encode("utf-8")) for v in vals]
+
+
+def test_string_codes_worked_example():
+    s = _pad(["b", "a", "ab", "a", "", "b"], 3)
+    code, k = orc.string_codes(s)
+    assert k == 4 and code.tolist() == [3, 1, 2, 1, 0, 3]
