@@ -188,6 +188,21 @@ tqp_status tqp_like_prefix(const uint8_t* d_str, int64_t n, int32_t width, const
                            int8_t* d_out, tqp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * tqp_string_codes -- dictionary codes of a string column (the same (n x
+ * width) zero-padded byte tensor as tqp_like_prefix), for grouping or
+ * ordering by a string: d_codes[i] = the rank of row i's value among the
+ * column's distinct values in ascending byte order (the zero padding sorts a
+ * value before every longer value it prefixes); d_rep_rows[c] = a row whose
+ * value has code c, for c < *d_ncodes.  The rows are sorted as multi-word
+ * keys (8-byte big-endian words, least significant first, each round a
+ * stable radix sort), then numbered at each change of value.  Grouping by
+ * d_codes with tqp_groupby_agg groups by the string, in string order.
+ * n < 2^30, width 1..256.  Two-phase workspace sizing as for tqp_sort_pairs.
+ * ---------------------------------------------------------------------- */
+tqp_status tqp_string_codes(const uint8_t* d_str, int64_t n, int32_t width, int32_t* d_codes, int32_t* d_rep_rows,
+                            int64_t* d_ncodes, void* ws, size_t* ws_bytes, tqp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * tqp_sort_pairs -- stable ascending LSD radix sort of (key, value) pairs
  * (the sort under the sort-based join and group-by of Section 2.2).
  * Keys (dtype TQP_I8..TQP_I64) are ordered by bits [begin_bit, end_bit) of

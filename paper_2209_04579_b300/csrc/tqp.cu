@@ -563,6 +563,46 @@ tqp_status tqp_like_prefix(const uint8_t* d_str, int64_t n, int32_t width, const
   return last_launch();
 }
 
+tqp_status tqp_string_codes(const uint8_t* d_str, int64_t n, int32_t width, int32_t* d_codes, int32_t* d_rep_rows,
+                            int64_t* d_ncodes, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || n < 0 || n >= (1ll << 30) || width < 1 || width > kLikeMaxWidth) return TQP_ERR_INVALID;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const int64_t ntiles = (n + kCodeTile - 1) / kCodeTile;
+  Carver c(ws);
+  unsigned long long* keys_a = c.take<unsigned long long>(nn);
+  unsigned long long* keys_b = c.take<unsigned long long>(nn);
+  int32_t* perm_buf[2] = {c.take<int32_t>(nn), c.take<int32_t>(nn)};
+  int32_t* flag = c.take<int32_t>(nn);
+  int32_t* tsum = c.take<int32_t>((size_t)(ntiles > 0 ? ntiles : 1));
+  SortWs sw = carve_sort(c, n, 8, 8);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  if (!d_ncodes) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    TQP_CUDA(cudaMemsetAsync(d_ncodes, 0, sizeof(int64_t), s));
+    return TQP_OK;
+  }
+  if (!d_str || !d_codes || !d_rep_rows) return TQP_ERR_INVALID;
+  // least significant word first; each round sorts the previous round's order
+  const int W = (width + 7) / 8;
+  const int32_t* perm = nullptr;  // identity before the first round
+  for (int w = W - 1, which = 0; w >= 0; --w, which ^= 1) {
+    str_word_kernel<<<stride_grid(n, 256), 256, 0, s>>>(d_str, width, perm, n, w, keys_a); note_launch();
+    const tqp_status st = run_sort(sw, kKeyU64, keys_a, perm, keys_b, perm_buf[which], n, nullptr, 0, 64, s);
+    if (st != TQP_OK) return st;
+    perm = perm_buf[which];
+  }
+  str_heads_kernel<<<stride_grid(n, 256), 256, 0, s>>>(d_str, width, perm, n, flag); note_launch();
+  str_tile_sums_kernel<<<(unsigned)ntiles, kCodeThreads, 0, s>>>(flag, n, tsum); note_launch();
+  str_tile_scan_kernel<<<1, kCodeThreads, 0, s>>>(tsum, ntiles, d_ncodes); note_launch();
+  str_codes_kernel<<<(unsigned)ntiles, kCodeThreads, 0, s>>>(flag, perm, tsum, n, d_codes, d_rep_rows); note_launch();
+  return last_launch();
+}
+
 tqp_status tqp_sort_pairs(int32_t key_dtype, const void* d_keys_in, const int32_t* d_vals_in, void* d_keys_out,
                           int32_t* d_vals_out, int64_t n, const int64_t* d_n, int begin_bit, int end_bit,
                           void* ws, size_t* ws_bytes, tqp_stream_t stream) {

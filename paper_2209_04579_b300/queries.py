@@ -133,3 +133,12 @@ def predict(t, model, min_votes: int, cap: int = 16):
     sel, cnt = tqp.tqp_filter([t["votes"]], [(0, tqp.GE, min_votes)])
     return tqp.tqp_groupby_agg([t["rating"]], [positive], [[(0, 1, 0)]], [(tqp.SUM, 0), (tqp.COUNT, 0)], cap,
                                sel=sel, n=t["votes"].numel(), d_n=cnt)
+
+
+def group_by_string(strings, vals, exprs, aggs, cap: int):
+    """GROUP BY a string column: its dictionary codes (the values' ranks in
+    ascending byte order) are the group key.  Returns (the groups' codes,
+    aggs, device G, a representative row of each code)."""
+    codes, rep, _ = tqp.tqp_string_codes(strings)
+    ok, oa, g = tqp.tqp_groupby_agg([codes], vals, exprs, aggs, cap)
+    return ok[0], oa, g, rep

@@ -118,6 +118,7 @@ _P = ctypes.POINTER
 _lib.tqp_filter.argtypes = [_P(Col), _int, _P(Pred), _int, _i64, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_gather.argtypes = [Col, _vp, _i64, _vp, _vp, _vp]
 _lib.tqp_like_prefix.argtypes = [_vp, _i64, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32, _vp, _vp]
+_lib.tqp_string_codes.argtypes = [_vp, _i64, ctypes.c_int32, _vp, _vp, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_sort_pairs.argtypes = [ctypes.c_int32, _vp, _vp, _vp, _vp, _i64, _vp, _int, _int, _vp, _P(_sz), _vp]
 _lib.tqp_join_eq.argtypes = [Col, _i64, _vp, Col, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_groupby_agg.argtypes = [_P(Col), _int, _P(Col), _int, _P(Expr), _int, _P(Agg), _int, _vp, _i64, _vp,
@@ -140,7 +141,7 @@ _lib.tqp_status_string.restype = ctypes.c_char_p
 _lib.tqp_debug_launch_count.restype = ctypes.c_int64
 _lib.tqp_debug_launch_count.argtypes = []
 _lib.tqp_profile_events.argtypes = [_int, _vp, _vp]
-for _f in ("tqp_filter", "tqp_gather", "tqp_like_prefix", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
+for _f in ("tqp_filter", "tqp_gather", "tqp_like_prefix", "tqp_string_codes", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
            "tqp_star_agg_learned",
            "tqp_status_poll", "tqp_profile_events", "tqp_cdf_forward", "tqp_cdf_backward", "tqp_cdf_train",
            "tqp_groupby_agg_learned", "tqp_star_agg_batched", "tqp_debug_set_spin_limit", "tqp_debug_inject_unpublished_tile"):
@@ -283,6 +284,21 @@ def tqp_like_prefix(strings, prefix: bytes, out=None, stream=None):
     _check(_lib.tqp_like_prefix(_ptr(strings), n, width, bytes(prefix), len(prefix), _ptr(out), _stream(stream)),
            "tqp_like_prefix")
     return out[:n]
+
+
+def tqp_string_codes(strings, stream=None):
+    """Dictionary codes of a (n, width) uint8 string tensor: (codes int32 [n],
+    representative row per code int32 [n], device int64 number of codes)."""
+    n, width = strings.shape
+    if strings.dtype != torch.uint8 or not strings.is_contiguous():
+        raise ValueError("tqp_string_codes: a contiguous (n, width) uint8 tensor")
+    dev = strings.device
+    codes = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    rep = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    k = torch.empty(1, dtype=torch.int64, device=dev)
+    _two_phase(_lib.tqp_string_codes, "tqp_string_codes", [_ptr(strings), n, width, _ptr(codes), _ptr(rep), _ptr(k)],
+               dev, stream)
+    return codes[:n], rep[:n], k
 
 
 def tqp_sort_pairs(keys, vals=None, begin_bit=0, end_bit=None, n=None, d_n=None, stream=None):

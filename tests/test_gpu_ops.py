@@ -310,3 +310,39 @@ def test_like_prefix_rejects_zero_byte_and_long_prefix(T):
         T.tqp_like_prefix(d, b"A\x00B")
     with pytest.raises(Exception):
         T.tqp_like_prefix(d, b"A" * 65)
+
+
+@pytest.mark.parametrize("n,width", [(1, 1), (5000, 3), (100_003, 9), (300_000, 25)])
+def test_string_codes(T, n, width):
+    """Codes are the ranks among distinct values in byte order (unique, so
+    compared exactly); each representative row holds its code's value."""
+    r = rng(n + width)
+    s = string_tensor(r, n, width, alphabet=b"ab\xc3\xa9")
+    codes, rep, k = T.tqp_string_codes(dev(s))
+    want, nk = orc.string_codes(s)
+    assert int(k.item()) == nk
+    assert np.array_equal(host(codes), want)
+    rep = host(rep)[:nk]
+    assert np.array_equal(want[rep], np.arange(nk))
+
+
+def test_group_by_string_column(T):
+    """GROUP BY the synthetic type strings of the promotion-revenue dimension:
+    groups in string order with their aggregates."""
+    from paper_2209_04579_b300 import datagen as dg
+    from paper_2209_04579_b300 import queries as Q
+    m = 400_000
+    rec = dg.q14_promo_tables(m)
+    table, _ = dg.type_strings()
+    types = dg.type_column(m, rec["type_seed"], table)
+    key = dg.make_table(rec["dim"], m)["key"].astype(np.int32)
+    code, nk = orc.string_codes(types)
+    wk, wa, _ = orc.groupby_agg([code], [key], [[(0, 1, 0)]], [(orc.COUNT, 0), (orc.MIN, 0), (orc.MAX, 0)])
+    gk, ga, g, rep = Q.group_by_string(dev(types), [dev(key)], [[(0, 1, 0)]],
+                                       [(T.COUNT, 0), (T.MIN, 0), (T.MAX, 0)], 256)
+    G = wa.shape[0]
+    assert int(g.item()) == G == nk == len(table)
+    assert np.array_equal(host(gk)[:G].astype(np.int64), wk[0]) and np.array_equal(host(ga)[:G], wa)
+    vals = [bytes(types[i]) for i in host(rep)[host(gk)[:G]]]
+    assert vals == sorted(vals) and len(set(vals)) == G
+    assert T.tqp_status_poll() == T.OK
