@@ -512,7 +512,60 @@ class Predict:
         return time.perf_counter() - t0, f"first {rows} of the 100M reviews"
 
 
-WORKLOADS = {"q14": Q14, "q14promo": Q14Promo, "predict": Predict, "q6": Q6, "skew": Skew, "batched": Batched, "star": Star}
+class StrGroup:
+    """GROUP BY a string column: 10M rows of 25-byte zero-padded type
+    strings (240 distinct values): type, COUNT(*), MIN(key), MAX(key)."""
+    name = "strgroup"
+    n = 10_000_000
+
+    def __init__(self, master):
+        from paper_2209_04579_b300 import datagen as dg
+        self.dg = dg
+        self.rec = dg.q14_promo_tables(self.n, master=master)
+        self.table, _ = dg.type_strings(master=master)
+
+    def config(self):
+        return {"workload": "group by a string column: 10M rows, type 25-byte zero-padded strings of three synthetic "
+                            "words (240 distinct), key int32; SELECT type, COUNT(*), MIN(key), MAX(key) GROUP BY type "
+                            "(dictionary codes by a multi-word radix sort, then the group-by on the codes)",
+                "rows": self.n, "string_width": int(self.table.shape[1])}
+
+    def make_device(self):
+        from paper_2209_04579_b300 import datagen_device as gd
+        self.key = gd.make_table(self.rec["dim"], self.n)["key"]
+        self.types = torch.from_numpy(self.dg.type_column(self.n, self.rec["type_seed"], self.table)).cuda()
+        return [self.key, self.types]
+
+    def step(self):
+        from paper_2209_04579_b300 import queries as Q
+        from paper_2209_04579_b300 import tqp
+        gk, ga, g, _ = Q.group_by_string(self.types, [self.key], [[(0, 1, 0)]],
+                                         [(tqp.COUNT, 0), (tqp.MIN, 0), (tqp.MAX, 0)], 256)
+        return ([gk], ga, g)
+
+    def rows(self):
+        return self.n
+
+    def alg_bytes(self):
+        return self.n * (int(self.table.shape[1]) + 4)
+
+    def prof(self):
+        # the string codes, all word rounds (word gathers, radix sorts,
+        # heads, scan, codes): the strings read once, codes and
+        # representative rows written once
+        return [(11, "tqp_string_codes (multi-word radix sort + codes)", self.n * (int(self.table.shape[1]) + 8))]
+
+    def oracle_sample(self, rows):
+        import oracle as orc
+        types = self.dg.type_column(rows, self.rec["type_seed"], self.table)
+        key = self.dg.make_table(self.rec["dim"], rows)["key"]
+        t0 = time.perf_counter()
+        code, _ = orc.string_codes(types)
+        orc.groupby_agg([code], [key], [[(0, 1, 0)]], [(orc.COUNT, 0), (orc.MIN, 0), (orc.MAX, 0)])
+        return time.perf_counter() - t0, f"first {rows} of the 10M rows"
+
+
+WORKLOADS = {"q14": Q14, "q14promo": Q14Promo, "predict": Predict, "strgroup": StrGroup, "q6": Q6, "skew": Skew, "batched": Batched, "star": Star}
 
 
 # ---------------------------------------------------------------- helpers

@@ -504,7 +504,7 @@ const char* tqp_status_string(tqp_status s);
  * sort), 3 = filter, 4 = group-by reduce, 5 = join probe, 6 = batched probe,
  * 7 = learned bucket sort (block kernel), 8 = learned partition scatter,
  * 9 = learned bucket sort (warp kernel), 10 = network forward
- * (tqp_cdf_forward).  Records are
+ * (tqp_cdf_forward), 11 = string codes (all of tqp_string_codes).  Records are
  * external, so under stream capture they become event nodes of the graph. */
 int64_t tqp_debug_launch_count(void);
 tqp_status tqp_profile_events(int kernel_class, void* start_event, void* stop_event);

@@ -588,6 +588,7 @@ tqp_status tqp_string_codes(const uint8_t* d_str, int64_t n, int32_t width, int3
   }
   if (!d_str || !d_codes || !d_rep_rows) return TQP_ERR_INVALID;
   // least significant word first; each round sorts the previous round's order
+  prof_mark(11, true, s);
   const int W = (width + 7) / 8;
   const int32_t* perm = nullptr;  // identity before the first round
   for (int w = W - 1, which = 0; w >= 0; --w, which ^= 1) {
@@ -600,6 +601,7 @@ tqp_status tqp_string_codes(const uint8_t* d_str, int64_t n, int32_t width, int3
   str_tile_sums_kernel<<<(unsigned)ntiles, kCodeThreads, 0, s>>>(flag, n, tsum); note_launch();
   str_tile_scan_kernel<<<1, kCodeThreads, 0, s>>>(tsum, ntiles, d_ncodes); note_launch();
   str_codes_kernel<<<(unsigned)ntiles, kCodeThreads, 0, s>>>(flag, perm, tsum, n, d_codes, d_rep_rows); note_launch();
+  prof_mark(11, false, s);
   return last_launch();
 }
 
