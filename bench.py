@@ -497,10 +497,10 @@ class Predict:
     def prof(self):
         n = self.n
         sel = int(n * 46 / 51)
-        # forward: score in, output and its bucket out; filter: votes in, ids
-        # out; the group-by (a 3-bit key: slots, no sort): per selected row
-        # its id, the rating byte and the prediction
-        return [(10, "cdf_forward_kernel", n * 12), (3, "filter_kernel", n * 4 + sel * 4),
+        # forward: score in, its bucket out; filter: votes in, ids out; the
+        # group-by (a 3-bit key: slots, no sort): per selected row its id,
+        # the rating byte and the prediction
+        return [(10, "cdf_forward_kernel", n * 8), (3, "filter_kernel", n * 4 + sel * 4),
                 (4, "gb_direct_kernel", sel * (4 + 1 + 4))]
 
     def oracle_sample(self, rows):

@@ -333,7 +333,8 @@ typedef struct {
 } tqp_train_cfg;
 
 /* tqp_cdf_forward: F[i] = model(x[i]) (float32, the fixed evaluation order
- * above) for i < n; if d_bucket is not NULL also its bucket of B. */
+ * above) for i < n; if d_bucket is not NULL also its bucket of B.  d_F may
+ * be NULL when d_bucket is given (the buckets alone are written). */
 tqp_status tqp_cdf_forward(const tqp_cdf_model* d_model, const float* d_x, int64_t n, float* d_F,
                            int32_t* d_bucket, int B, tqp_stream_t stream);
 

@@ -64,7 +64,7 @@ __global__ void cdf_forward_kernel(const tqp_cdf_model* gm, const float* x, int6
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     float f = cdf_eval(m, x[i]);
-    F[i] = f;
+    if (F) F[i] = f;
     if (bucket) bucket[i] = cdf_bucket_of(f, B);
   }
 }

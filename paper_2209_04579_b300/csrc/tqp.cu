@@ -731,7 +731,7 @@ tqp_status tqp_cdf_forward(const tqp_cdf_model* d_model, const float* d_x, int64
                            int B, tqp_stream_t stream) {
   if (n < 0 || n > INT_MAX || (d_bucket && (B < 1 || B > (1 << 24)))) return TQP_ERR_INVALID;
   if (n == 0) return TQP_OK;
-  if (!d_model || !d_x || !d_F) return TQP_ERR_INVALID;
+  if (!d_model || !d_x || (!d_F && !d_bucket)) return TQP_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   prof_mark(10, true, s);
   cdf_forward_kernel<<<stride_grid(n, 256), 256, 0, s>>>(d_model, d_x, n, d_F, d_bucket, B); note_launch();

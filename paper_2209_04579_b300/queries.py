@@ -129,7 +129,7 @@ def predict(t, model, min_votes: int, cap: int = 16):
     is the CASE factor of a filtered group-by.  Every step runs in the
     library's kernels on one stream, so the whole query captures into one
     CUDA graph."""
-    _, positive = tqp.tqp_cdf_forward(model, t["score"], B=2)
+    _, positive = tqp.tqp_cdf_forward(model, t["score"], B=2, want_F=False)
     sel, cnt = tqp.tqp_filter([t["votes"]], [(0, tqp.GE, min_votes)])
     return tqp.tqp_groupby_agg([t["rating"]], [positive], [[(0, 1, 0)]], [(tqp.SUM, 0), (tqp.COUNT, 0)], cap,
                                sel=sel, n=t["votes"].numel(), d_n=cnt)

@@ -410,12 +410,13 @@ def empty_model(device="cuda"):
     return torch.zeros(ctypes.sizeof(CdfModel), dtype=torch.uint8, device=device)
 
 
-def tqp_cdf_forward(model, x, B=0, stream=None):
+def tqp_cdf_forward(model, x, B=0, want_F=True, stream=None):
+    """(F, buckets of B or None); want_F=False (with B) writes the buckets alone and returns F None."""
     n = x.numel()
-    F = torch.empty(max(n, 1), dtype=torch.float32, device=x.device)
+    F = torch.empty(max(n, 1), dtype=torch.float32, device=x.device) if want_F or not B else None
     bk = torch.empty(max(n, 1), dtype=torch.int32, device=x.device) if B else None
     _check(_lib.tqp_cdf_forward(_ptr(model), _ptr(x), n, _ptr(F), _ptr(bk), B, _stream(stream)), "tqp_cdf_forward")
-    return F[:n], (bk[:n] if B else None)
+    return (F[:n] if F is not None else None), (bk[:n] if B else None)
 
 
 def tqp_cdf_backward(model, x, y, stream=None):

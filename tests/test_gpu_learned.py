@@ -40,6 +40,8 @@ def test_forward_bit_exact_and_buckets(T):
     want = orc.cdf_forward_f32(w, b, a, float(c), x)
     assert np.array_equal(F.cpu().numpy().view(np.uint32), want.view(np.uint32))
     assert np.array_equal(bk.cpu().numpy(), orc.cdf_bucket(want, 4096))
+    F2, bk2 = T.tqp_cdf_forward(m, torch.from_numpy(x).cuda(), B=2, want_F=False)  # buckets alone
+    assert F2 is None and np.array_equal(bk2.cpu().numpy(), orc.cdf_bucket(want, 2))
 
 
 def test_backward_vs_float64(T):
