@@ -50,6 +50,9 @@ def lib():
         _lib.orc_groupby_agg.restype = ctypes.c_int64
         _lib.orc_cdf_grad_f64.restype = ctypes.c_double
         _lib.orc_string_codes.restype = ctypes.c_int64
+        _lib.orc_light_cdf_targets.restype = ctypes.c_int64
+        _lib.orc_date_parse_iso.restype = ctypes.c_int64
+        _lib.orc_date_from_days.restype = ctypes.c_int64
     return _lib
 
 
@@ -236,3 +239,40 @@ def string_codes(strings):
     code = np.empty(n, dtype=np.int32)
     k = lib().orc_string_codes(_p(s), ctypes.c_int64(n), m, _p(code))
     return code, int(k)
+
+
+def light_cdf_targets(sorted_keys, mult, s_train, min_count, max_heavy):
+    """Training targets over the CDF of the light sample keys (heavy runs:
+    count >= the cut, aggregated directly).  sorted_keys: uint64 ascending.
+    Returns (y float32 [s_train], heavy keys uint64 ascending)."""
+    s = np.ascontiguousarray(sorted_keys, dtype=np.uint64)
+    y = np.empty(max(s_train, 1), dtype=np.float32)
+    heavy = np.empty(max(max_heavy, 1), dtype=np.uint64)
+    k = lib().orc_light_cdf_targets(_p(s), ctypes.c_int64(len(s)), ctypes.c_int64(mult), ctypes.c_int64(s_train),
+                                    ctypes.c_int64(min_count), ctypes.c_int64(max_heavy), _p(heavy), _p(y))
+    return y[:s_train].copy(), heavy[:k].copy()
+
+
+def date_parse_iso(strings):
+    """(n, m) uint8 zero-padded 'YYYY-MM-DD' rows -> (epoch ns int64, ok int8)."""
+    s = np.ascontiguousarray(strings, dtype=np.uint8)
+    n, m = s.shape
+    ns = np.empty(n, dtype=np.int64)
+    ok = np.empty(n, dtype=np.int8)
+    lib().orc_date_parse_iso(_p(s), ctypes.c_int64(n), m, _p(ns), _p(ok))
+    return ns, ok
+
+
+def date_from_days(days):
+    d = np.ascontiguousarray(days, dtype=np.int32)
+    ns = np.empty(len(d), dtype=np.int64)
+    lib().orc_date_from_days(_p(d), ctypes.c_int64(len(d)), _p(ns))
+    return ns
+
+
+def date_parts(ns):
+    """Epoch ns -> (day number, year, month, day of month), all int32."""
+    t = np.ascontiguousarray(ns, dtype=np.int64)
+    out = [np.empty(len(t), dtype=np.int32) for _ in range(4)]
+    lib().orc_date_parts(_p(t), ctypes.c_int64(len(t)), *[_p(o) for o in out])
+    return tuple(out)

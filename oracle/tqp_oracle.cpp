@@ -21,6 +21,8 @@
 // finite differences); none is unpinned.
 
 #include <algorithm>
+#include <climits>
+#include <functional>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -399,6 +401,171 @@ int64_t orc_string_codes(const uint8_t* str, int64_t n, int m, int32_t* code) {
   for (auto& kv : dict) kv.second = next++;
   for (int64_t i = 0; i < n; ++i) code[i] = dict[std::vector<uint8_t>(str + i * m, str + (i + 1) * m)];
   return (int64_t)dict.size();
+}
+
+// Training targets of the learned range partitioner when the sample's
+// frequent ("heavy") keys are aggregated directly instead of routed through
+// the buckets, so that the network is fit to the CDF of the rows the buckets
+// receive (the light rows).  sorted: the sample's SH packed keys ascending.
+//  - A run of c equal keys is heavy when c >= cut, where cut is the smallest
+//    count >= min_count that at most max_heavy runs reach (no heavy key when
+//    max_heavy == 0 or no such count exists).
+//  - light(i) = the number of non-heavy sample keys before position i.
+//  - Training pair t (t < S_train) takes sample position j = t * mult, whose
+//    key k has its run [lo, hi): y[t] = (light(lo) + light count of the run
+//    / 2) / (total light count), computed in double and rounded once to
+//    float.  A heavy run has light count 0: it sits on the light CDF with
+//    zero width.  Without heavy keys this is the plain empirical-CDF
+//    midpoint (first rank + count / 2) / SH of orc_cdf_targets.
+// heavy_out receives the heavy keys ascending; returns their number.
+int64_t orc_light_cdf_targets(const uint64_t* sorted, int64_t SH, int64_t mult, int64_t S_train, int64_t min_count,
+                              int64_t max_heavy, uint64_t* heavy_out, float* y) {
+  // runs of equal keys
+  std::vector<int64_t> run_lo, run_hi;
+  for (int64_t i = 0; i < SH;) {
+    int64_t j = i;
+    while (j < SH && sorted[j] == sorted[i]) ++j;
+    run_lo.push_back(i);
+    run_hi.push_back(j);
+    i = j;
+  }
+  // the count cut: walk the distinct counts from the largest down
+  std::map<int64_t, int64_t, std::greater<int64_t>> by_count;
+  for (size_t r = 0; r < run_lo.size(); ++r) by_count[run_hi[r] - run_lo[r]] += 1;
+  int64_t cut = INT64_MAX, reached = 0;
+  if (max_heavy > 0) {
+    for (const auto& kv : by_count) {
+      if (kv.first < min_count) break;
+      if (reached + kv.second > max_heavy) break;
+      reached += kv.second;
+      cut = kv.first;
+    }
+  }
+  std::vector<int64_t> light_before(static_cast<size_t>(SH) + 1, 0);
+  int64_t nheavy = 0;
+  for (size_t r = 0; r < run_lo.size(); ++r) {
+    const int64_t c = run_hi[r] - run_lo[r];
+    const bool heavy = c >= cut;
+    if (heavy) heavy_out[nheavy++] = sorted[run_lo[r]];
+    for (int64_t i = run_lo[r]; i < run_hi[r]; ++i)
+      light_before[i + 1] = light_before[i] + (heavy ? 0 : 1);
+  }
+  const int64_t light_total = light_before[SH];
+  const double tot = light_total > 0 ? static_cast<double>(light_total) : 1.0;
+  for (int64_t t = 0; t < S_train; ++t) {
+    const int64_t j = t * mult;
+    // the run holding j: the last run starting at or before j
+    const size_t r = static_cast<size_t>(std::upper_bound(run_lo.begin(), run_lo.end(), j) - run_lo.begin()) - 1;
+    const int64_t lo = run_lo[r], hi = run_hi[r];
+    const int64_t light = light_before[hi] - light_before[lo];
+    y[t] = static_cast<float>((static_cast<double>(light_before[lo]) + 0.5 * static_cast<double>(light)) / tot);
+  }
+  return nheavy;
+}
+
+// Date columns (Section 2.1): a date is stored as its UNIX epoch time in
+// nanoseconds, an int64 (n x 1) tensor.  Dates here are days of the
+// proleptic Gregorian calendar; an int64 nanosecond count reaches from
+// 1677-09-22 to 2262-04-11, so only days in [-106751, 106751] relative to
+// 1970-01-01 convert.  The oracle counts days by walking years and months
+// one by one with the leap-year rule (divisible by 4, except centuries not
+// divisible by 400).
+}  // extern "C"
+namespace {
+bool leap_year(int64_t y) { return (y % 4 == 0 && y % 100 != 0) || y % 400 == 0; }
+int days_in_month(int64_t y, int m) {
+  static const int d[12] = {31, 28, 31, 30, 31, 30, 31, 31, 30, 31, 30, 31};
+  return m == 2 && leap_year(y) ? 29 : d[m - 1];
+}
+constexpr int64_t kNsPerDay = 86400LL * 1000000000LL;
+constexpr int64_t kMinDay = -106751, kMaxDay = 106751;  // whole days whose nanoseconds fit in int64
+
+// Days from 1970-01-01 to y-m-d (1 <= m <= 12, 1 <= d <= days in month).
+int64_t days_of(int64_t y, int m, int d) {
+  int64_t days = 0;
+  if (y >= 1970) {
+    for (int64_t k = 1970; k < y; ++k) days += leap_year(k) ? 366 : 365;
+  } else {
+    for (int64_t k = y; k < 1970; ++k) days -= leap_year(k) ? 366 : 365;
+  }
+  for (int k = 1; k < m; ++k) days += days_in_month(y, k);
+  return days + (d - 1);
+}
+}  // namespace
+extern "C" {
+
+// Parses row i of an (n x m) zero-padded string tensor as an ISO date
+// "YYYY-MM-DD" (exactly 10 bytes, then only zero padding): ns[i] = the
+// date's epoch nanoseconds and ok[i] = 1; a malformed or out-of-range row
+// gives ns[i] = INT64_MIN and ok[i] = 0.  Returns the number of bad rows.
+int64_t orc_date_parse_iso(const uint8_t* str, int64_t n, int m, int64_t* ns, int8_t* ok) {
+  int64_t bad = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const uint8_t* r = str + i * m;
+    bool good = m >= 10 && r[4] == '-' && r[7] == '-';
+    int v[8] = {0};
+    const int at[8] = {0, 1, 2, 3, 5, 6, 8, 9};
+    for (int k = 0; good && k < 8; ++k) {
+      const uint8_t c = r[at[k]];
+      good = c >= '0' && c <= '9';
+      v[k] = c - '0';
+    }
+    for (int k = 10; good && k < m; ++k) good = r[k] == 0;
+    int64_t y = 0;
+    int mo = 0, d = 0;
+    if (good) {
+      y = v[0] * 1000 + v[1] * 100 + v[2] * 10 + v[3];
+      mo = v[4] * 10 + v[5];
+      d = v[6] * 10 + v[7];
+      good = mo >= 1 && mo <= 12 && d >= 1 && d <= days_in_month(y, mo);
+    }
+    int64_t days = good ? days_of(y, mo, d) : 0;
+    good = good && days >= kMinDay && days <= kMaxDay;
+    ns[i] = good ? days * kNsPerDay : INT64_MIN;
+    ok[i] = good ? 1 : 0;
+    bad += good ? 0 : 1;
+  }
+  return bad;
+}
+
+// Day numbers (days since 1970-01-01, int32) to epoch nanoseconds; a day
+// outside [-106751, 106751] gives INT64_MIN and counts as bad.
+int64_t orc_date_from_days(const int32_t* days, int64_t n, int64_t* ns) {
+  int64_t bad = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const bool good = days[i] >= kMinDay && days[i] <= kMaxDay;
+    ns[i] = good ? static_cast<int64_t>(days[i]) * kNsPerDay : INT64_MIN;
+    bad += good ? 0 : 1;
+  }
+  return bad;
+}
+
+// Epoch nanoseconds to the calendar: the day number (floor of ns / one
+// day, so an instant before 1970 belongs to the earlier day), and that
+// day's year, month and day of month, found by walking from 1970.
+void orc_date_parts(const int64_t* ns, int64_t n, int32_t* days, int32_t* year, int32_t* month, int32_t* mday) {
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t q = ns[i] / kNsPerDay;
+    if (ns[i] % kNsPerDay != 0 && ns[i] < 0) q -= 1;
+    int64_t y = 1970, rest = q;
+    while (rest < 0) {
+      y -= 1;
+      rest += leap_year(y) ? 366 : 365;
+    }
+    while (rest >= (leap_year(y) ? 366 : 365)) {
+      rest -= leap_year(y) ? 366 : 365;
+      y += 1;
+    }
+    int m = 1;
+    while (rest >= days_in_month(y, m)) {
+      rest -= days_in_month(y, m);
+      ++m;
+    }
+    days[i] = static_cast<int32_t>(q);
+    year[i] = static_cast<int32_t>(y);
+    month[i] = m;
+    mday[i] = static_cast<int32_t>(rest + 1);
+  }
 }
 
 }  // extern "C"

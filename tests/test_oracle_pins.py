@@ -467,3 +467,122 @@ def test_string_codes_worked_example():
     s = _pad(["b", "a", "ab", "a", "", "b"], 3)
     code, k = orc.string_codes(s)
     assert k == 4 and code.tolist() == [3, 1, 2, 1, 0, 3]
+
+
+def test_cdf_normalize_hand_worked_example():
+    """Key normalisation worked by hand (the reading: a 24-bit shifted
+    integer times a float reciprocal).  Keys -2^63, -2^63 + 2^40, 0, 2^63 - 1
+    have order-preserving images 0, 2^40, 2^63, 2^64 - 1; with umin = 0 and
+    shift 40 their q are 0, 1, 2^23, 2^24 - 1.
+    - With inv = 2^-24 (a power of two) every product is exact: 0, 2^-24,
+      1/2 and 1 - 2^-24.
+    - With inv = float(1/3) = 0x3EAAAAAB (= 1/3 + 2^-25/3), q = 3 gives
+      3 * inv = 1 + 2^-25, which rounds to 1.0 (the nearest floats are 1 and
+      1 + 2^-23); q = 1 gives inv itself."""
+    keys = np.array([-2**63, -2**63 + 2**40, 0, 2**63 - 1], np.int64)
+    x = orc.cdf_normalize(keys, 0, 40, 2.0**-24)
+    assert x.tolist() == [0.0, 2.0**-24, 0.5, 1.0 - 2.0**-24]
+    third = np.frombuffer(np.array([0x3EAAAAAB], np.uint32).tobytes(), np.float32)[0]
+    keys = np.array([-2**63, -2**63 + 2**40, -2**63 + 3 * 2**40], np.int64)
+    x = orc.cdf_normalize(keys, 0, 40, float(third))
+    assert x[0] == 0.0 and x[1] == third and x[2] == np.float32(1.0)
+
+
+def test_light_cdf_targets_worked_example():
+    """Sample 1, 2, 2, 2, 2, 3, 4, 4 with runs of 1, 4, 1, 2 keys; counts
+    from 2 on may be heavy, at most 4 heavy keys: keys 2 and 4 are heavy, the
+    light keys are 1 and 3 (total 2).  Key 1 sits at (0 + 1/2) / 2, each
+    heavy key 2 at 1 / 2 (one light key before it, zero width), key 3 at
+    (1 + 1/2) / 2, heavy key 4 at 2 / 2.  With at most one heavy key only
+    the run of 4 qualifies; with none, the plain midpoints (first rank +
+    count / 2) / 8."""
+    s = np.array([1, 2, 2, 2, 2, 3, 4, 4], np.uint64)
+    y, h = orc.light_cdf_targets(s, 1, 8, 2, 4)
+    assert y.tolist() == [0.25, 0.5, 0.5, 0.5, 0.5, 0.75, 1.0, 1.0] and h.tolist() == [2, 4]
+    y, h = orc.light_cdf_targets(s, 1, 8, 2, 1)
+    assert h.tolist() == [2]
+    assert y.tolist() == [0.125, 0.25, 0.25, 0.25, 0.25, 0.375, 0.75, 0.75]
+    y, h = orc.light_cdf_targets(s, 2, 4, 2, 0)
+    assert h.tolist() == [] and y.tolist() == [1 / 16, 3 / 8, 3 / 8, 14 / 16]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_light_cdf_targets_brute_force(seed):
+    """Random samples against a direct statement: heavy keys by counting
+    (the largest counts first, while at most max_heavy keys have reached
+    them), y = (light keys strictly below k + half the light copies of k) /
+    the light total; and without heavy keys the plain targets."""
+    r = np.random.default_rng(seed)
+    SH = int(r.integers(1, 3000))
+    s = np.sort(r.integers(0, int(r.integers(1, 400)), SH).astype(np.uint64))
+    mult = int(r.integers(1, 4))
+    S_train = (SH - 1) // mult + 1
+    min_count, max_heavy = int(r.integers(1, 20)), int(r.integers(0, 12))
+    y, h = orc.light_cdf_targets(s, mult, S_train, min_count, max_heavy)
+    cnt = collections.Counter(s.tolist())
+    cut = None
+    for c in sorted(set(cnt.values()), reverse=True):
+        if c < min_count or max_heavy == 0 or sum(1 for v in cnt.values() if v >= c) > max_heavy:
+            break
+        cut = c
+    heavy = sorted(k for k, v in cnt.items() if cut is not None and v >= cut)
+    assert h.tolist() == heavy
+    light = {k: (0 if k in heavy else v) for k, v in cnt.items()}
+    total = sum(light.values()) or 1
+    for t in range(S_train):
+        k = int(s[t * mult])
+        below = sum(v for kk, v in light.items() if kk < k)
+        assert y[t] == np.float32((below + 0.5 * light[k]) / total)
+    y0, h0 = orc.light_cdf_targets(s, 1, SH, min_count, 0)
+    assert h0.size == 0 and np.array_equal(y0, orc.cdf_targets(s.astype(np.int64)).astype(np.float32))
+
+
+def _iso(dates, m=12):
+    out = np.zeros((len(dates), m), np.uint8)
+    for i, t in enumerate(dates):
+        b = t.encode()
+        out[i, :len(b)] = np.frombuffer(b, np.uint8)
+    return out
+
+
+def test_date_conversions_against_datetime():
+    """ISO strings and day numbers to epoch nanoseconds, and back to the
+    calendar, against Python's datetime (the proleptic Gregorian calendar),
+    over every day of 1600..2300 that an int64 nanosecond count reaches and
+    random instants (negative ones included, not on day boundaries)."""
+    import datetime as dt
+    epoch = dt.date(1970, 1, 1)
+    first, last = dt.date(1677, 9, 22), dt.date(2262, 4, 11)
+    ns_day = 86400 * 10**9
+    assert (first - epoch).days * ns_day >= -2**63 and ((first - epoch).days - 1) * ns_day < -2**63
+    assert (last - epoch).days * ns_day < 2**63 and ((last - epoch).days + 1) * ns_day >= 2**63
+    d = dt.date(1600, 1, 1)
+    dates, want = [], []
+    while d <= dt.date(2300, 12, 31):
+        dates.append(d.isoformat())
+        want.append((d - epoch).days * ns_day if first <= d <= last else -2**63)
+        d += dt.timedelta(days=1)
+    ns, ok = orc.date_parse_iso(_iso(dates))
+    assert ns.tolist() == want and ok.tolist() == [int(w != -2**63) for w in want]
+    days = np.array([(dt.date.fromisoformat(t) - epoch).days for t in dates], np.int64)
+    inr = (days >= -106751) & (days <= 106751)
+    assert orc.date_from_days(days.astype(np.int32)).tolist() == np.where(inr, days * ns_day, -2**63).tolist()
+    r = np.random.default_rng(3)
+    t = np.concatenate([r.integers(-2**63, 2**63 - 1, 20000, dtype=np.int64), [0, -1, 1, ns_day, -ns_day,
+                        -ns_day - 1, -2**63, 2**63 - 1]]).astype(np.int64)
+    dn, y, mo, md = orc.date_parts(t)
+    for i in range(len(t)):
+        q = int(t[i]) // ns_day          # Python floors
+        c = epoch + dt.timedelta(days=q)
+        assert (dn[i], y[i], mo[i], md[i]) == (q, c.year, c.month, c.day)
+
+
+def test_date_parse_rejects_malformed():
+    bad = ["1900-02-29", "2023-13-01", "2023-00-10", "2023-04-31", "2023-04-00", "1970/01/01", "1970-1-01",
+           "19700101", "", "1677-09-21", "2262-04-12", "abcd-ef-gh"]
+    ns, ok = orc.date_parse_iso(_iso(bad))
+    assert ok.tolist() == [0] * len(bad) and ns.tolist() == [-2**63] * len(bad)
+    trailing = _iso(["1970-01-02"])
+    trailing[0, 10] = ord("T")                # a byte after the date that is not padding
+    assert orc.date_parse_iso(trailing)[1].tolist() == [0]
+    assert orc.date_parse_iso(_iso(["2000-02-29"], 10))[0].tolist() == [11016 * 86400 * 10**9]
