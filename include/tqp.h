@@ -203,6 +203,33 @@ tqp_status tqp_string_codes(const uint8_t* d_str, int64_t n, int32_t width, int3
                             int64_t* d_ncodes, void* ws, size_t* ws_bytes, tqp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Date columns (Section 2.1): a date is stored as its UNIX epoch time in
+ * nanoseconds, an int64 column; a range predicate on dates is then two
+ * predicates on that column.  The paper names dates (with strings) as the
+ * columns whose ingestion needs a conversion; these calls do it on the GPU.
+ * Calendar: proleptic Gregorian.  Int64 nanoseconds hold the whole days
+ * -106751..106751 around 1970-01-01 (1677-09-22 to 2262-04-11).
+ *
+ * tqp_date_parse_iso: row i of an (n x width) zero-padded byte tensor (the
+ *   string layout of tqp_like_prefix) holding "YYYY-MM-DD" (exactly ten
+ *   bytes, then only zero bytes) -> d_ns[i] = the date's epoch ns.  A
+ *   malformed row (bad digits or separators, a month or day that does not
+ *   exist, a date outside the range above, other bytes after the date) gets
+ *   INT64_MIN and the device status records TQP_ERR_INVALID.  width 10..256.
+ * tqp_date_from_days: d_days[i] (days since 1970-01-01) -> d_ns[i]; a day
+ *   outside the range gives INT64_MIN and records TQP_ERR_INVALID.
+ * tqp_date_parts: d_ns[i] -> the day number floor(ns / 86400e9) (an instant
+ *   before 1970 belongs to the earlier day), its year, month (1..12) and day
+ *   of month (1..31); each output pointer may be NULL.
+ * All: device pointers, n < 2^31, enqueued on `stream`; TQP_ERR_INVALID for
+ * bad sizes or NULL inputs.
+ * ---------------------------------------------------------------------- */
+tqp_status tqp_date_parse_iso(const uint8_t* d_str, int64_t n, int32_t width, int64_t* d_ns, tqp_stream_t stream);
+tqp_status tqp_date_from_days(const int32_t* d_days, int64_t n, int64_t* d_ns, tqp_stream_t stream);
+tqp_status tqp_date_parts(const int64_t* d_ns, int64_t n, int32_t* d_days, int32_t* d_year, int32_t* d_month,
+                          int32_t* d_mday, tqp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * tqp_sort_pairs -- stable ascending LSD radix sort of (key, value) pairs
  * (the sort under the sort-based join and group-by of Section 2.2).
  * Keys (dtype TQP_I8..TQP_I64) are ordered by bits [begin_bit, end_bit) of

@@ -9,11 +9,13 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <set>
 #include <tuple>
 #include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
+#include "dates.cuh"
 #include "filter.cuh"
 #include "groupby.cuh"
 #include "join.cuh"
@@ -82,6 +84,45 @@ int stride_grid(int64_t n, int threads, int per_sm = 8) {
   int64_t cap = (int64_t)num_sms() * per_sm;
   if (g > cap) g = cap;
   return (int)(g < 1 ? 1 : g);
+}
+
+// Raises a kernel's dynamic shared memory limit to `bytes` on the current
+// device.  The attribute belongs to one device, so it is set once per
+// (device, kernel, size), under a lock shared by every host thread.
+cudaError_t smem_optin(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<int, const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_tuple(dev, fn, bytes);
+  if (done.count(key)) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert(key);
+  return e;
+}
+
+template <typename Kernel>
+cudaError_t smem_optin(Kernel* k, int bytes) {
+  return smem_optin(reinterpret_cast<const void*>(k), bytes);
+}
+
+// Static shared memory of a kernel (the same on every device), cached.
+cudaError_t static_smem(const void* fn, int* bytes) {
+  static std::mutex mu;
+  static std::map<const void*, int> cache;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = cache.find(fn);
+  if (it != cache.end()) {
+    *bytes = it->second;
+    return cudaSuccess;
+  }
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  cache[fn] = *bytes = (int)fa.sharedSizeBytes;
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- launch accounting
@@ -382,12 +423,7 @@ tqp_status run_groupby(const GroupWs& w, const KeySet& ks, const AggProgram& P, 
   } else {
     launch_reduce<unsigned long long>(r, Pr, w.tiles, s);
   }
-  static bool attr = false;
-  if (!attr) {
-    TQP_CUDA(cudaFuncSetAttribute(gb_direct_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kDirectMaxSmemBytes));
-    attr = true;
-  }
+  TQP_CUDA(smem_optin(gb_direct_kernel<256>, kDirectMaxSmemBytes));
   // shared memory for one copy of every slot of this program: a narrow
   // program leaves room for several blocks per SM (the fold waits on reads)
   const int dsm = kDirectSlots * (P.naggs + 1) * 8;
@@ -551,12 +587,7 @@ tqp_status tqp_like_prefix(const uint8_t* d_str, int64_t n, int32_t width, const
   if (!d_str || !d_out) return TQP_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int smem = kLikeRows * width;
-  static bool attr = false;
-  if (!attr) {
-    TQP_CUDA(cudaFuncSetAttribute(like_prefix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  kLikeRows * kLikeMaxWidth));
-    attr = true;
-  }
+  TQP_CUDA(smem_optin(like_prefix_kernel, kLikeRows * kLikeMaxWidth));
   const int64_t ntiles = (n + kLikeRows - 1) / kLikeRows;
   like_prefix_kernel<<<persistent_grid(like_prefix_kernel, 256, smem, ntiles), 256, smem, s>>>(d_str, n, width, p, d_out);
   note_launch();
@@ -602,6 +633,42 @@ tqp_status tqp_string_codes(const uint8_t* d_str, int64_t n, int32_t width, int3
   str_tile_scan_kernel<<<1, kCodeThreads, 0, s>>>(tsum, ntiles, d_ncodes); note_launch();
   str_codes_kernel<<<(unsigned)ntiles, kCodeThreads, 0, s>>>(flag, perm, tsum, n, d_codes, d_rep_rows); note_launch();
   prof_mark(11, false, s);
+  return last_launch();
+}
+
+tqp_status tqp_date_parse_iso(const uint8_t* d_str, int64_t n, int32_t width, int64_t* d_ns, tqp_stream_t stream) {
+  if (n < 0 || n > INT_MAX || width < 10 || width > kLikeMaxWidth) return TQP_ERR_INVALID;
+  if (n == 0) return TQP_OK;
+  if (!d_str || !d_ns) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  TQP_CUDA(smem_optin(date_parse_kernel, kDateRows * kLikeMaxWidth));
+  const int smem = kDateRows * width;
+  const int64_t ntiles = (n + kDateRows - 1) / kDateRows;
+  date_parse_kernel<<<persistent_grid(date_parse_kernel, 256, smem, ntiles), 256, smem, s>>>(
+      d_str, n, width, reinterpret_cast<long long*>(d_ns));
+  note_launch();
+  return last_launch();
+}
+
+tqp_status tqp_date_from_days(const int32_t* d_days, int64_t n, int64_t* d_ns, tqp_stream_t stream) {
+  if (n < 0 || n > INT_MAX) return TQP_ERR_INVALID;
+  if (n == 0) return TQP_OK;
+  if (!d_days || !d_ns) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  date_from_days_kernel<<<stride_grid(n, 256), 256, 0, s>>>(d_days, n, reinterpret_cast<long long*>(d_ns));
+  note_launch();
+  return last_launch();
+}
+
+tqp_status tqp_date_parts(const int64_t* d_ns, int64_t n, int32_t* d_days, int32_t* d_year, int32_t* d_month,
+                          int32_t* d_mday, tqp_stream_t stream) {
+  if (n < 0 || n > INT_MAX) return TQP_ERR_INVALID;
+  if (n == 0) return TQP_OK;
+  if (!d_ns) return TQP_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  date_parts_kernel<<<stride_grid(n, 256), 256, 0, s>>>(reinterpret_cast<const long long*>(d_ns), n, d_days, d_year,
+                                                        d_month, d_mday);
+  note_launch();
   return last_launch();
 }
 
@@ -975,8 +1042,8 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
     auto hk = hmode == kBlockHist ? lp_hist_kernel<kBlockHist>
                                   : (hmode == kThrShared ? lp_hist_kernel<kThrShared> : lp_hist_kernel<kThrGlobal>);
     auto sk = smode == kThrShared ? lp_scatter_kernel<kThrShared> : lp_scatter_kernel<kThrGlobal>;
-    TQP_CUDA(cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
-    TQP_CUDA(cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+    TQP_CUDA(smem_optin(hk, (int)hsm));
+    TQP_CUDA(smem_optin(sk, (int)ssm));
     const int64_t ptiles = (n + kPartThreads * kPartItems - 1) / (kPartThreads * kPartItems);
     const int gh = hmode == kBlockHist ? w.nblk : persistent_grid(hk, kPartThreads, hsm, ptiles);
     hk<<<gh, kPartThreads, hsm, s>>>(pa); note_launch();
@@ -1005,12 +1072,8 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
     ba.big_flags = w.big_flags;
     size_t smem = (size_t)kLocalCap * (8 + 8 + 4 + 4) + (size_t)kLocalWarps * (kRadix + 1) * 4 + kRadix * 4;
     size_t wsmem = (size_t)kWarpSortWarps * (2 * kWarpCap * 8 + (kRadix + 1) * 4);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(lp_bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(lp_bucket_sort_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
-      attr = true;
-    }
+    TQP_CUDA(smem_optin(lp_bucket_sort_kernel, (int)smem));
+    TQP_CUDA(smem_optin(lp_bucket_sort_warp_kernel, (int)wsmem));
     TQP_CUDA(cudaMemsetAsync(w.queue, 0, 2 * sizeof(uint32_t), s));
     TQP_CUDA(cudaMemsetAsync(w.big_flags, 0, (size_t)B * sizeof(uint32_t), s));
     {
@@ -1601,21 +1664,11 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       const ProbeFn pk = v[ndims - 1][k32 ? 1 : 0];
       // the bitmap takes what the variant's static shared memory leaves of
       // the opt-in maximum, up to kSmemBitmapBytes
-      static int dyn[2][2];
-      static bool attr = false;
-      if (!attr) {
-        for (int i = 0; i < 2; ++i)
-          for (int j = 0; j < 2; ++j) {
-            cudaFuncAttributes fa;
-            TQP_CUDA(cudaFuncGetAttributes(&fa, v[i][j]));
-            int b = kMaxSmemOptin - (int)fa.sharedSizeBytes;
-            b = (b < kSmemBitmapBytes ? b : kSmemBitmapBytes) & ~255;
-            TQP_CUDA(cudaFuncSetAttribute(v[i][j], cudaFuncAttributeMaxDynamicSharedMemorySize, b));
-            dyn[i][j] = b;
-          }
-        attr = true;
-      }
-      const int bytes = dyn[ndims - 1][k32 ? 1 : 0];
+      int stat = 0;
+      TQP_CUDA(static_smem(reinterpret_cast<const void*>(pk), &stat));
+      int bytes = kMaxSmemOptin - stat;
+      bytes = (bytes < kSmemBitmapBytes ? bytes : kSmemBitmapBytes) & ~255;
+      TQP_CUDA(smem_optin(pk, bytes));
       const int64_t t1024 = (n_fact + 1024 * 4 - 1) / (1024 * 4);
       pk<<<persistent_grid(pk, 1024, bytes, t1024), 1024, bytes, s>>>(pa, A, bytes / 4);
       note_launch();

@@ -118,6 +118,9 @@ _P = ctypes.POINTER
 _lib.tqp_filter.argtypes = [_P(Col), _int, _P(Pred), _int, _i64, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_gather.argtypes = [Col, _vp, _i64, _vp, _vp, _vp]
 _lib.tqp_like_prefix.argtypes = [_vp, _i64, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32, _vp, _vp]
+_lib.tqp_date_parse_iso.argtypes = [_vp, _i64, ctypes.c_int32, _vp, _vp]
+_lib.tqp_date_from_days.argtypes = [_vp, _i64, _vp, _vp]
+_lib.tqp_date_parts.argtypes = [_vp, _i64, _vp, _vp, _vp, _vp, _vp]
 _lib.tqp_string_codes.argtypes = [_vp, _i64, ctypes.c_int32, _vp, _vp, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_sort_pairs.argtypes = [ctypes.c_int32, _vp, _vp, _vp, _vp, _i64, _vp, _int, _int, _vp, _P(_sz), _vp]
 _lib.tqp_join_eq.argtypes = [Col, _i64, _vp, Col, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
@@ -141,7 +144,8 @@ _lib.tqp_status_string.restype = ctypes.c_char_p
 _lib.tqp_debug_launch_count.restype = ctypes.c_int64
 _lib.tqp_debug_launch_count.argtypes = []
 _lib.tqp_profile_events.argtypes = [_int, _vp, _vp]
-for _f in ("tqp_filter", "tqp_gather", "tqp_like_prefix", "tqp_string_codes", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
+for _f in ("tqp_filter", "tqp_gather", "tqp_like_prefix", "tqp_string_codes", "tqp_date_parse_iso",
+           "tqp_date_from_days", "tqp_date_parts", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
            "tqp_star_agg_learned",
            "tqp_status_poll", "tqp_profile_events", "tqp_cdf_forward", "tqp_cdf_backward", "tqp_cdf_train",
            "tqp_groupby_agg_learned", "tqp_star_agg_batched", "tqp_debug_set_spin_limit", "tqp_debug_inject_unpublished_tile"):
@@ -284,6 +288,33 @@ def tqp_like_prefix(strings, prefix: bytes, out=None, stream=None):
     _check(_lib.tqp_like_prefix(_ptr(strings), n, width, bytes(prefix), len(prefix), _ptr(out), _stream(stream)),
            "tqp_like_prefix")
     return out[:n]
+
+
+def tqp_date_parse_iso(strings, stream=None):
+    """(n, width) uint8 zero-padded 'YYYY-MM-DD' rows -> int64 epoch ns [n]
+    (INT64_MIN, and TQP_ERR_INVALID in the device status, for a bad row)."""
+    n, width = strings.shape
+    if strings.dtype != torch.uint8 or not strings.is_contiguous():
+        raise ValueError("tqp_date_parse_iso: a contiguous (n, width) uint8 tensor")
+    out = torch.empty(max(n, 1), dtype=torch.int64, device=strings.device)
+    _check(_lib.tqp_date_parse_iso(_ptr(strings), n, width, _ptr(out), _stream(stream)), "tqp_date_parse_iso")
+    return out[:n]
+
+
+def tqp_date_from_days(days, stream=None):
+    """int32 days since 1970-01-01 -> int64 epoch ns."""
+    n = days.numel()
+    out = torch.empty(max(n, 1), dtype=torch.int64, device=days.device)
+    _check(_lib.tqp_date_from_days(_ptr(days), n, _ptr(out), _stream(stream)), "tqp_date_from_days")
+    return out[:n]
+
+
+def tqp_date_parts(ns, stream=None):
+    """int64 epoch ns -> (day number, year, month, day of month), int32 each."""
+    n = ns.numel()
+    out = [torch.empty(max(n, 1), dtype=torch.int32, device=ns.device) for _ in range(4)]
+    _check(_lib.tqp_date_parts(_ptr(ns), n, *[_ptr(o) for o in out], _stream(stream)), "tqp_date_parts")
+    return tuple(o[:n] for o in out)
 
 
 def tqp_string_codes(strings, stream=None):

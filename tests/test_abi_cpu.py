@@ -129,3 +129,47 @@ def test_struct_layouts_match_header(tmp_path):
         assert want[(cname, "size")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert want[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def _header_text():
+    text = open(os.path.join(ROOT, "include", "tqp.h")).read()
+    return re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+
+
+def _enum_values(text, name):
+    """Values of the members of `typedef enum { ... } name;` (explicit or
+    counted from the previous member)."""
+    body = re.search(r"typedef enum\s*\{([^}]*)\}\s*" + name + r"\s*;", text, flags=re.S).group(1)
+    out, nxt = {}, 0
+    for item in body.split(","):
+        item = item.strip()
+        if not item:
+            continue
+        m = re.match(r"([A-Z_0-9]+)\s*(?:=\s*(-?\d+))?$", item)
+        assert m, item
+        nxt = int(m.group(2)) if m.group(2) is not None else nxt
+        out[m.group(1)] = nxt
+        nxt += 1
+    return out
+
+
+def test_binding_constants_match_header():
+    """The Python binding restates the header's status codes, enums and
+    limits; they must stay in step with include/tqp.h."""
+    from paper_2209_04579_b300 import tqp
+    text = _header_text()
+    status = _enum_values(text, "tqp_status")
+    assert status == {"TQP_OK": tqp.OK, "TQP_ERR_INVALID": tqp.ERR_INVALID, "TQP_ERR_DTYPE": tqp.ERR_DTYPE,
+                      "TQP_ERR_CAPACITY": tqp.ERR_CAPACITY, "TQP_ERR_CUDA": tqp.ERR_CUDA,
+                      "TQP_ERR_TIMEOUT": tqp.ERR_TIMEOUT, "TQP_ERR_WORKSPACE": tqp.ERR_WORKSPACE,
+                      "TQP_ERR_UNSUPPORTED": tqp.ERR_UNSUPPORTED, "TQP_ERR_TOO_LARGE": tqp.ERR_TOO_LARGE}
+    assert _enum_values(text, "tqp_dtype") == {"TQP_I8": tqp.I8, "TQP_I16": tqp.I16, "TQP_I32": tqp.I32,
+                                               "TQP_I64": tqp.I64}
+    assert _enum_values(text, "tqp_cmp") == {"TQP_LT": tqp.LT, "TQP_LE": tqp.LE, "TQP_GT": tqp.GT,
+                                             "TQP_GE": tqp.GE, "TQP_EQ": tqp.EQ, "TQP_NE": tqp.NE}
+    assert _enum_values(text, "tqp_aggop") == {"TQP_COUNT": tqp.COUNT, "TQP_SUM": tqp.SUM, "TQP_MIN": tqp.MIN,
+                                               "TQP_MAX": tqp.MAX}
+    m = re.search(r"#define\s+TQP_NOALLOC_MAX_ROWS\s+\(1LL\s*<<\s*(\d+)\)", text)
+    assert m and (1 << int(m.group(1))) == tqp.NOALLOC_MAX_ROWS
+    m = re.search(r"#define\s+TQP_CDF_HIDDEN\s+(\d+)", text)
+    assert m and int(m.group(1)) == tqp.H

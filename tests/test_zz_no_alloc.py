@@ -44,3 +44,24 @@ def test_filter_noalloc_matches_filter_on_two_calls():
     st = lib.tqp_filter_noalloc(tqp._cols(cols), 1, tqp._preds([(0, tqp.LT, 1)]), 1, tqp.NOALLOC_MAX_ROWS + 1,
                                 None, None, 0, ctypes.c_void_p(cnt.data_ptr()), None)
     assert st == tqp.ERR_TOO_LARGE
+
+
+def test_filter_noalloc_device_count_through_binding():
+    """The Python wrapper with a device-resident row count d_n below n: only
+    the first *d_n rows are filtered, exactly as by tqp_filter given the same
+    d_n, again on two calls in a row."""
+    from paper_2209_04579_b300 import build
+    build.build()
+    from paper_2209_04579_b300 import tqp
+    rng = np.random.default_rng(77)
+    n = 1_000_003
+    col = torch.from_numpy(rng.integers(0, 1000, n).astype(np.int32)).cuda()
+    for used in (654_321, 4_097):
+        d_n = torch.tensor([used], dtype=torch.int64, device="cuda")
+        want, want_n = tqp.tqp_filter([col], [(0, tqp.LT, 500)], d_n=d_n)
+        got, got_n = tqp.tqp_filter_noalloc([col], [(0, tqp.LT, 500)], d_n=d_n)
+        k = int(want_n.item())
+        assert int(got_n.item()) == k
+        assert k == int((col[:used] < 500).sum().item())
+        assert torch.equal(got[:k], want[:k])
+    assert tqp.tqp_status_poll() == tqp.OK
