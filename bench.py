@@ -1,11 +1,18 @@
-"""Benchmark: input rows/s of the join + filter + group-by query on one B300
-(default workload: fact 60M rows x dim 1.5M rows, SELECT region, SUM(price),
-COUNT(*) ... WHERE region < 5 GROUP BY region), plus the HBM roofline of the
-dominant kernel, end-to-end throughput from pinned host buffers, and the CPU
-oracle as a baseline.
+"""Benchmark: input rows/s of filter + join + group-by queries on one B300,
+learned/batched forms against the plain radix path, with the HBM roofline of
+each workload's dominant kernel, an end-to-end figure from pinned host
+buffers, and the CPU oracle as a baseline.
+
+Default workload: the star join -- fact 600M rows JOIN dim1 (20M int32 keys)
+JOIN dim2 (150M int64 keys) WHERE date < 767 GROUP BY (dim1.cat, dim2.cat):
+SUM(m1..m3), COUNT(*) -- with the dimension keys sorted through the learned
+range partitioner (network trained inside every step); the serving form
+(no training) and the plain radix form are timed beside it.  The skewed
+100M-row learned group-by and the 512-problem batched call are measured in
+the same run and attached under "extra" (--extra '' skips them).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload q14|q6|skew|star]
+                       [--workload star|skew|batched|q14|q14promo|q6|predict|strgroup]
 Under torchrun each rank runs its own independent instance (weak scaling, no
 collective on the data path); rank 0 prints one JSON line.
 """
@@ -24,6 +31,7 @@ import torch
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 L2_FLUSH_BYTES = 256 << 20
+METRIC = "input rows/s (filter+join+group-by), learned/batched vs plain; % HBM roofline"
 
 
 def peaks():
@@ -279,6 +287,8 @@ class Batched:
         from paper_2209_04579_b300 import queries as Q
         return Q.batched(self.probs, probe_items=self.items)
 
+    plain_what = "the same 512 problems as 512 separate fused calls"
+
     def plain_step(self):
         from paper_2209_04579_b300 import queries as Q
         return [Q.batched_one(f, d) for f, d in self.probs]
@@ -370,8 +380,16 @@ class Star:
         return self.n * 40 + self.n1 * 6 + self.n2 * 9
 
     def prof(self):
-        # fk1 (4), fk2 (8), date (4) and m1..m3 (24) of every fact row
-        return [(1, "star_probe_kernel", self.n * 40)]
+        # probe: fk1 (4), fk2 (8), date (4) and m1..m3 (24) of every fact row.
+        # Key sorts: (key, rank payload) pairs read and written once.
+        # Directories: the sorted keys with their ranks read once, and a
+        # compact (key, rank) table written once.
+        n, n1, n2 = self.n, self.n1, self.n2
+        return [(1, "star_probe_kernel", n * 40),
+                (12, "dim1 key sort (20M int32 keys with their group ranks)", n1 * 8 * 2),
+                (13, "dim2 key sort (150M int64 keys with their group ranks)", n2 * 12 * 2),
+                (14, "dim1 directory and cell records", n1 * 8 * 2),
+                (15, "dim2 directory and cell records", n2 * 12 * 2)]
 
     def traffic(self):
         # ncu DRAM bytes (read + write) of one probe launch on the quarter-size
@@ -810,7 +828,7 @@ def run_reference(args, world, rank):
         total_rows += rows
     v = total_rows / total_t
     print(json.dumps({
-        "impl": "reference", "metric": "input rows/s (join+filter+group-by)", "value": v, "unit": "rows/s",
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "rows/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": W.config(),
@@ -818,22 +836,44 @@ def run_reference(args, world, rank):
         "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 
-def run_ours(args, world, rank, local):
-    from paper_2209_04579_b300 import build as b
-    if rank == 0:
-        b.build()
-    barrier(world)
-    from paper_2209_04579_b300 import tqp
-    torch.cuda.set_device(local)
-    W = WORKLOADS[args.workload](20220904 + rank, **({"scale": args.scale} if args.scale != 1 else {}))
-    if args.variant:
-        W.variant = args.variant
-    inputs = W.make_device()
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+def capture(fn):
+    """One call of fn captured into a CUDA graph (after an eager call and a
+    call on a side stream, which size the workspace of the capture stream)."""
+    fn()
     torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    with torch.cuda.graph(g):
+        out = fn()
+    torch.cuda.synchronize()
+    return g, out
 
-    # eager warm-up (allocates the workspace of the capture stream's twin)
-    out = W.step()
+
+def time_graph(g, steps, flush, e0, e1):
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0.record()
+        g.replay()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def measure(W, args, world, local, flush, main):
+    """Builds the workload's inputs, captures its step into a CUDA graph with
+    each profiled kernel class bracketed by its own events, and times K
+    replays (L2 flushed before each).  main: the printed line's workload
+    (clocks, end-to-end run); otherwise an attached extra workload."""
+    from paper_2209_04579_b300 import tqp
+    inputs = W.make_device()
+    torch.cuda.synchronize()
+    out = W.step()                       # eager warm-up
     torch.cuda.synchronize()
     assert tqp.tqp_status_poll() == tqp.OK
     if hasattr(W, "tune") and getattr(W, "variant", "") != "plain":
@@ -842,8 +882,6 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         assert tqp.tqp_status_poll() == tqp.OK
 
-    # capture one step into a CUDA graph, with each profiled kernel class
-    # bracketed by its own pair of events
     classes = [c for c, _, _ in W.prof()]
     kev = {}
     for c in classes:
@@ -853,6 +891,8 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     for c in classes:
         tqp.tqp_profile_events(c, *kev[c])
+    W.step()
+    torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
@@ -873,13 +913,15 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     assert tqp.tqp_status_poll() == tqp.OK
 
-    clocks = ClockSampler(local)
-    clocks.start()
+    steps = args.steps if main else max(3, min(args.steps, 10))
+    clocks = ClockSampler(local) if main else None
+    if clocks:
+        clocks.start()
     barrier(world)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_ms, kern_ms = [], {c: [] for c in classes}
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         e0.record()
         g.replay()
@@ -890,12 +932,12 @@ def run_ours(args, world, rank, local):
             kern_ms[c].append(kev[c][0].elapsed_time(kev[c][1]))
     torch.cuda.synchronize()
     barrier(world)
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     status = tqp.tqp_status_poll()
     assert status == tqp.OK, status
 
     total_ms = max_over_ranks(sum(step_ms), world)
-    rows_all = sum_over_ranks(W.rows() * args.steps, world)
+    rows_all = sum_over_ranks(W.rows() * steps, world)
     value = rows_all / (total_ms / 1e3)
     peak, peak_kind = peaks()
     kern = []
@@ -904,38 +946,8 @@ def run_ours(args, world, rank, local):
         kern.append({"kernel": name, "ms": ms, "alg_bytes": nbytes, "gbs": nbytes / (ms / 1e3) / 1e9})
     dom = max(kern, key=lambda k: k["ms"])
     achieved = dom["gbs"]
-
-    # ---- end to end through the public API from pinned host buffers (eager calls)
-    host_in = [t.cpu().pin_memory() for t in inputs]
-    h2d = sum(t.numel() * t.element_size() for t in host_in)
-    e2e_ms = []
-    d2h = 0
-    for i in range(args.steps + 1):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0.record()
-        for hsrc, ddst in zip(host_in, inputs):
-            ddst.copy_(hsrc, non_blocking=True)
-        outs = W.step()
-        outs = outs if isinstance(outs, list) else [outs]
-        res = []
-        for ok, oa, G in outs:
-            res += [G.to("cpu", non_blocking=True), oa.to("cpu", non_blocking=True)] + \
-                   [k.to("cpu", non_blocking=True) for k in ok]
-        e1.record()
-        e1.synchronize()
-        if i > 0:
-            e2e_ms.append(e0.elapsed_time(e1))
-        d2h = sum(r.numel() * r.element_size() for r in res)
-    e2e_total = max_over_ranks(sum(e2e_ms), world)
-    e2e_value = rows_all / (e2e_total / 1e3)
-
-    if rank != 0:
-        return
-    line = {
-        "metric": "input rows/s (join+filter+group-by)", "value": value, "unit": "rows/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded, generated on device)",
+    res = {
+        "value": value, "unit": "rows/s", "steps": steps, "ms_per_step": total_ms / steps,
         "config": {**W.config(), "parallelism": f"replicas x{world} (independent instances, no collective)",
                    "l2": "flushed before every step (256 MB write, outside the step's events)",
                    "launch": "one CUDA graph replay per step"},
@@ -944,53 +956,97 @@ def run_ours(args, world, rank, local):
                      "kernel_ms": dom["ms"], "alg_bytes_per_launch": dom["alg_bytes"],
                      **traffic_of(W, dom["kernel"])},
         "kernels": [{**k, "frac": k["gbs"] / peak} for k in kern],
-        "step_roofline_frac": W.alg_bytes() / (total_ms / args.steps / 1e3) / 1e9 / peak,
-        "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": launches_per_step * args.steps,
-        "clocks": clk,
+        "step_roofline_frac": W.alg_bytes() / (total_ms / steps / 1e3) / 1e9 / peak,
+        "gpu_launches": launches_per_step * steps,
     }
-    def side_arm(fn):
-        # another form of the same workload, captured and replayed the same way
-        fn()
-        torch.cuda.synchronize()
-        g2 = torch.cuda.CUDAGraph()
-        side2 = torch.cuda.Stream()
-        side2.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side2):
-            fn()
-        torch.cuda.current_stream().wait_stream(side2)
-        with torch.cuda.graph(g2):
-            fn()
-        g2.replay()
-        torch.cuda.synchronize()
-        pm = []
-        for _ in range(max(1, min(args.steps, 5))):
+    if clk is not None:
+        res["clocks"] = clk
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    if main:
+        # ---- end to end through the public API from pinned host buffers (eager calls)
+        host_in = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t) for t in inputs]
+        h2d = sum(t.numel() * t.element_size() for t in host_in)
+        e2e_ms = []
+        d2h = 0
+        for i in range(steps + 1):
             flush.zero_()
+            torch.cuda.synchronize()
             e0.record()
-            g2.replay()
+            for hsrc, ddst in zip(host_in, inputs):
+                ddst.copy_(hsrc, non_blocking=True)
+            outs = W.step()
+            outs = outs if isinstance(outs, list) else [outs]
+            res_t = []
+            for ok, oa, G in outs:
+                res_t += [G.to("cpu", non_blocking=True), oa.to("cpu", non_blocking=True)] + \
+                    [k.to("cpu", non_blocking=True) for k in ok]
             e1.record()
             e1.synchronize()
-            pm.append(e0.elapsed_time(e1))
+            if i > 0:
+                e2e_ms.append(e0.elapsed_time(e1))
+            d2h = sum(r.numel() * r.element_size() for r in res_t)
+        del host_in
+        e2e_total = max_over_ranks(sum(e2e_ms), world)
+        res["e2e"] = {"value": rows_all / (e2e_total / 1e3), "unit": "rows/s", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h}
+    del g
+
+    def side_arm(fn):
+        # another form of the same workload, captured and replayed the same way
+        g2, _ = capture(fn)
+        g2.replay()
+        torch.cuda.synchronize()
+        pm = time_graph(g2, max(1, min(steps, 5)), flush, e0, e1)
         assert tqp.tqp_status_poll() == tqp.OK
         del g2
         return {"value": W.rows() / (sum(pm) / len(pm) / 1e3), "unit": "rows/s",
                 "ms_per_step": sum(pm) / len(pm), "launch": "one CUDA graph replay per step"}
 
     if hasattr(W, "serving_step") and getattr(W, "variant", "") != "plain":
-        line["serving"] = {**side_arm(W.serving_step),
-                           "what": "the learned step without training (quantile-knot network, no Adam epochs)"}
+        res["serving"] = {**side_arm(W.serving_step),
+                          "what": "the learned step without training (quantile-knot network, no Adam epochs)"}
     if hasattr(W, "plain_step"):
         # the same workload through the plain path (no learned partition /
         # one call per problem)
-        line["plain_path"] = side_arm(W.plain_step)
+        res["plain_path"] = side_arm(W.plain_step)
+        res["plain_path"]["what"] = getattr(W, "plain_what", "the same workload through the plain radix path")
         if hasattr(W, "stats"):
-            from paper_2209_04579_b300 import tqp as _t
-            line["learned_stats"] = _t.stats_from_device(W.stats)
+            res["learned_stats"] = tqp.stats_from_device(W.stats)
         if hasattr(W, "tune_info"):
-            line["autotune"] = W.tune_info
+            res["autotune"] = W.tune_info
+    del inputs
+    return res
+
+
+def run_ours(args, world, rank, local):
+    from paper_2209_04579_b300 import build as b
+    if rank == 0:
+        b.build()
+    barrier(world)
+    torch.cuda.set_device(local)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    W = WORKLOADS[args.workload](20220904 + rank, **({"scale": args.scale} if args.scale != 1 else {}))
+    if args.variant:
+        W.variant = args.variant
+    res = measure(W, args, world, local, flush, main=True)
+    line = {"metric": METRIC, "value": res.pop("value"), "unit": "rows/s", "n_gpus": world,
+            "steps": res.pop("steps"), "warmup": args.warmup, "ms_per_step": res.pop("ms_per_step"),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded, generated on device)", **res}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)
-    print(json.dumps(line), flush=True)
+    # the other headline workloads, each measured the same way in this run
+    extras = [x for x in args.extra.split(",") if x and x != args.workload]
+    if extras:
+        line["extra"] = {}
+        for name in extras:
+            del W
+            torch.cuda.empty_cache()
+            W = WORKLOADS[name](20220904 + rank)
+            line["extra"][name] = measure(W, args, world, local, flush, main=False)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def main():
@@ -999,7 +1055,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="q14", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="star", choices=sorted(WORKLOADS))
+    ap.add_argument("--extra", default="skew,batched",
+                    help="other workloads measured in the same run and attached under 'extra' ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="", help="skew, star: 'plain' times the plain radix path as the step")
     ap.add_argument("--scale", type=int, default=1, help="star: divide the table sizes (small profiling cases)")

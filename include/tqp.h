@@ -430,6 +430,36 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
                                    size_t* ws_bytes, tqp_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * tqp_partition_learned -- the learned range partitioner on its own: the
+ * rows (d_sel[0..n) or 0..n-1; n or *d_n) split into B ordered key-range
+ * buckets by the network of this header's model, fit on the GPU to the
+ * key distribution (the same fit as tqp_groupby_agg_learned: key range and
+ * packing; a strided sample of SH = min(4 * cfg->sample, 2^20) packed keys,
+ * sorted; with cfg->heavy, the sample's heavy keys -- counts of at least
+ * max(2, floor(SH * 8192 / (2 n)) + 1), the most frequent ones, at most
+ * 1024 -- set apart; training pairs on the CDF of the other (light) sample
+ * keys from every (SH / sample)-th sorted key: x = the normalised key, y =
+ * (light keys before it + half its light count) / light total; knots and
+ * Adam training).  Outputs (each pointer may be NULL):
+ *   d_bucket[i]   bucket id of the i-th row: a light row's bucket 0..B-1
+ *                 (non-decreasing in the key), a row of heavy key h
+ *                 (heavy keys ascending) the id B + h;
+ *   d_rows[k]     the rows' ids grouped by bucket id, in input order within
+ *                 a bucket (a stable counting sort by bucket id);
+ *   d_offsets[b]  the first position of bucket id b in d_rows,
+ *                 b = 0..B + 1024 (B + 1025 entries; the last ones n);
+ *   d_train_x, d_train_y  the cfg->sample training pairs (float32);
+ *   d_model_out   the trained network;  d_stats  the statistics below.
+ * B = cfg->buckets, or (0) the power of two giving about 512 rows a bucket.
+ * Two-phase workspace sizing; limits and errors as tqp_groupby_agg_learned.
+ * ---------------------------------------------------------------------- */
+#define TQP_MAX_HEAVY 1024
+tqp_status tqp_partition_learned(const tqp_col* keys, int nkeys, const int32_t* d_sel, int64_t n, const int64_t* d_n,
+                                 const tqp_learned_cfg* cfg, int32_t* d_bucket, int32_t* d_rows, int64_t* d_offsets,
+                                 float* d_train_x, float* d_train_y, tqp_cdf_model* d_model_out,
+                                 tqp_learned_stats* d_stats, void* ws, size_t* ws_bytes, tqp_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * tqp_star_agg_learned -- tqp_star_agg (same inputs, outputs, guarantees
  * and results) whose dimensions of at least 2^20 passing-row candidates
  * have their keys sorted through the learned range partitioner instead of
@@ -532,7 +562,10 @@ const char* tqp_status_string(tqp_status s);
  * sort), 3 = filter, 4 = group-by reduce, 5 = join probe, 6 = batched probe,
  * 7 = learned bucket sort (block kernel), 8 = learned partition scatter,
  * 9 = learned bucket sort (warp kernel), 10 = network forward
- * (tqp_cdf_forward), 11 = string codes (all of tqp_string_codes).  Records are
+ * (tqp_cdf_forward), 11 = string codes (all of tqp_string_codes), 12 / 13 =
+ * the key sort (radix or learned, with its dense-key check) of star dimension
+ * 0 / 1, 14 / 15 = the directory and cell records of star dimension 0 / 1.
+ * Records are
  * external, so under stream capture they become event nodes of the graph. */
 int64_t tqp_debug_launch_count(void);
 tqp_status tqp_profile_events(int kernel_class, void* start_event, void* stop_event);

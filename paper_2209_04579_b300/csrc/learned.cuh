@@ -24,7 +24,7 @@ constexpr int kH = TQP_CDF_HIDDEN;
 constexpr int kNP = 3 * kH + 1;   // parameters: w, b, a, c
 constexpr int kGradLen = kNP + 1; // + loss
 constexpr int kGradChunk = 1024;  // samples per gradient block
-constexpr int kMaxHeavy = 1024;
+constexpr int kMaxHeavy = TQP_MAX_HEAVY;
 constexpr int kDirBits = 12;      // directory over the top bits of q
 constexpr int kLocalCap = 8192;   // rows a block sorts on-chip
 constexpr int kWarpCap = 1024;    // rows one warp sorts on-chip
@@ -685,6 +685,94 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_hist_kernel(PartArgs a) {
     __syncthreads();
     for (int b = threadIdx.x; b < lp.B; b += kPartThreads) a.bcount[(size_t)blockIdx.x * lp.B + b] = S.bh[b];
   }
+}
+
+// Bucket id of every (selected) row for the standalone partition: a light
+// row its learned bucket 0..B-1, a row of heavy key h (ascending heavy keys)
+// the id B + h.
+template <int MODE>  // kThrGlobal or kThrShared
+__global__ void __launch_bounds__(kPartThreads, 1) lp_bucket_ids_kernel(PartArgs a, int32_t* ids) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ PackPlan K;
+  const LearnedPlan lp = *a.lp;
+  const PartSmem S = part_carve(smem, 0, lp.B);
+  part_setup<MODE>(a, lp, S, K);
+  const unsigned* thr = MODE >= kThrShared ? S.thr : a.thr;
+  const int nh = lp.nheavy;
+  const int64_t n = clamp_n(a.n_max, a.d_n);
+  const int64_t stride = (int64_t)gridDim.x * kPartThreads;
+  for (int64_t i = (int64_t)blockIdx.x * kPartThreads + threadIdx.x; i < n; i += stride) {
+    const unsigned long long p = pack_row_plan(K, a.sel ? (int64_t)a.sel[i] : i);
+    const int h = nh ? heavy_lookup(S, p) : -1;
+    ids[i] = h >= 0 ? lp.B + h : lp_bucket<MODE >= kThrShared>(p, lp, S.dir, thr);
+  }
+}
+
+// off[b] = the first position of bucket id b among the n sorted ids
+// (n where no id >= b follows), b = 0..nb.
+__global__ void lp_offsets_sorted_kernel(const uint32_t* sorted, int64_t n_max, const int64_t* d_n, int nb,
+                                         long long* off) {
+  const int64_t n = clamp_n(n_max, d_n);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n == 0) {
+    for (int64_t b = t0; b <= nb; b += stride) off[b] = 0;
+    return;
+  }
+  for (int64_t p = t0; p < n; p += stride) {
+    const long long cur = sorted[p];
+    const long long prev = p ? (long long)sorted[p - 1] : -1;
+    for (long long b = prev + 1; b <= cur; ++b) off[b] = p;
+    if (p == n - 1)
+      for (long long b = cur + 1; b <= nb; ++b) off[b] = n;
+  }
+}
+
+// Statistics of a standalone partition from its offsets (one block).
+__global__ void __launch_bounds__(1024) lp_partition_stats_kernel(const LearnedPlan* lp, const long long* off,
+                                                                  const float* loss, int epochs,
+                                                                  tqp_learned_stats* st) {
+  __shared__ long long s_mx[32], s_ov[32], s_ne[32], s_or[32], s_sm[32];
+  const int B = lp->B;
+  long long mx = 0, ov = 0, ne = 0, orows = 0, small = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const long long c = off[b + 1] - off[b];
+    mx = c > mx ? c : mx;
+    ov += c > kLocalCap;
+    orows += c > kLocalCap ? c : 0;
+    ne += c > 0;
+    small += (c > 1 && c <= kWarpCap) ? c : 0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = m2 > mx ? m2 : mx;
+    ov += __shfl_xor_sync(0xffffffffu, ov, o);
+    ne += __shfl_xor_sync(0xffffffffu, ne, o);
+    orows += __shfl_xor_sync(0xffffffffu, orows, o);
+    small += __shfl_xor_sync(0xffffffffu, small, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    const int w = threadIdx.x >> 5;
+    s_mx[w] = mx; s_ov[w] = ov; s_ne[w] = ne; s_or[w] = orows; s_sm[w] = small;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  tqp_learned_stats r;
+  r.buckets = B;
+  r.heavy_keys = lp->nheavy;
+  r.light_rows = off[B];
+  r.max_bucket = r.over_capacity = r.nonempty = r.over_capacity_rows = r.small_rows = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    r.max_bucket = s_mx[w] > r.max_bucket ? s_mx[w] : r.max_bucket;
+    r.over_capacity += s_ov[w];
+    r.nonempty += s_ne[w];
+    r.over_capacity_rows += s_or[w];
+    r.small_rows += s_sm[w];
+  }
+  r.loss_first = (loss && epochs > 0) ? loss[0] : 0.0f;
+  r.loss_last = (loss && epochs > 0) ? loss[epochs - 1] : 0.0f;
+  *st = r;
 }
 
 // kBlockHist: bucket totals over the blocks' counts.

@@ -905,7 +905,7 @@ struct LearnedWs {
 
 // B: the bucket count (0 = from n, about rows_per_bucket rows each).
 LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int rows_per_bucket, int naggs,
-                        const AggProgram* P, int32_t* rows_out) {
+                        const AggProgram* P, int32_t* rows_out, bool scatter = true) {
   LearnedWs w;
   std::memset(&w, 0, sizeof(w));
   w.S = cfg->sample;
@@ -948,10 +948,12 @@ LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int ro
   w.bcount = c.take<unsigned>(B <= kBlockHistMaxB ? (size_t)w.nblk * B : 1);
   w.off = c.take<unsigned>((size_t)B + 1);
   w.light_n = c.take<int64_t>(1);
-  w.lpk = c.take<unsigned long long>(nn);
-  w.lrow = rows_out ? rows_out : c.take<int32_t>(nn);
-  w.apk = c.take<unsigned long long>(nn);
-  w.arow = c.take<int32_t>(nn);
+  if (scatter) {
+    w.lpk = c.take<unsigned long long>(nn);
+    w.lrow = rows_out ? rows_out : c.take<int32_t>(nn);
+    w.apk = c.take<unsigned long long>(nn);
+    w.arow = c.take<int32_t>(nn);
+  }
   w.queue = c.take<uint32_t>(2);
   w.big_flags = c.take<uint32_t>((size_t)B);
   if (P) {  // the group-by's reduce
@@ -964,20 +966,22 @@ LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int ro
   return w;
 }
 
-// The learned range partition of n packed keys and the sort of every
-// bucket: key range and packing; a strided sample sorted by the radix sort;
-// heavy keys (want_heavy) and the light-CDF training pairs; the network
-// (knots, training); its step positions and their directory; bucket counts,
-// offsets and the scatter (heavy rows folded into heavy_acc by P); every
-// bucket sorted.  Leaves the light rows' packed keys and row ids sorted in
-// (lpk, lrow), their count in light_n.
-tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int32_t* d_sel, const int32_t* payload,
-                                 int64_t n, const int64_t* d_n, const tqp_learned_cfg* cfg, bool want_heavy,
-                                 const AggProgram& P, tqp_learned_stats* d_stats, cudaStream_t s) {
-  const int S = w.S, SH = w.SH, B = w.B, naggs = P.naggs;
+// Heavy-key threshold: a key whose sample count reaches it would fill half a
+// bucket's on-chip capacity on its own.
+long long heavy_min_count(int SH, int64_t n) {
   long long minc = (long long)((double)SH * kLocalCap / (2.0 * (double)(n > 0 ? n : 1))) + 1;
   if (minc < 2) minc = 2;
   if (minc > 4095) minc = 4095;
+  return minc;
+}
+
+// Steps 1-4 of the learned range partition: key range and packing, the
+// sorted sample, heavy keys (want_heavy) and the light-CDF training pairs,
+// the network (knots, training), its step positions and their directory.
+tqp_status run_learned_fit(const LearnedWs& w, const KeySet& ks, const int32_t* d_sel, int64_t n, const int64_t* d_n,
+                           const tqp_learned_cfg* cfg, bool want_heavy, cudaStream_t s) {
+  const int S = w.S, SH = w.SH, B = w.B;
+  const long long minc = heavy_min_count(SH, n);
   // 1. key range and packing (always a 64-bit packed word on this path)
   gb_init_kernel<<<1, 32, 0, s>>>(w.gp); note_launch();
   gb_keyrange_kernel<256><<<stride_grid(n, 256, 4), 256, 0, s>>>(ks, d_sel, n, d_n, w.gp); note_launch();
@@ -1010,6 +1014,20 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
     lp_thresholds_kernel<<<(B - 1 + 255) / 256, 256, 0, s>>>(w.model, w.lp, w.thr); note_launch();
   }
   lp_directory_kernel<<<((1 << kDirBits) + 1 + 255) / 256, 256, 0, s>>>(w.lp, w.thr, w.dir); note_launch();
+  return TQP_OK;
+}
+
+// The learned range partition of n packed keys and the sort of every
+// bucket (see run_learned_fit for steps 1-4), then bucket counts, offsets
+// and the scatter (heavy rows folded into heavy_acc by P), and every bucket
+// sorted.  Leaves the light rows' packed keys and row ids sorted in
+// (lpk, lrow), their count in light_n.
+tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int32_t* d_sel, const int32_t* payload,
+                                 int64_t n, const int64_t* d_n, const tqp_learned_cfg* cfg, bool want_heavy,
+                                 const AggProgram& P, tqp_learned_stats* d_stats, cudaStream_t s) {
+  const int B = w.B, naggs = P.naggs;
+  tqp_status st = run_learned_fit(w, ks, d_sel, n, d_n, cfg, want_heavy, s);
+  if (st != TQP_OK) return st;
   // 5. partition: bucket counts, offsets, scatter (heavy rows folded on the fly)
   PartArgs pa;
   std::memset(&pa, 0, sizeof(pa));
@@ -1190,6 +1208,86 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
   }
   launch_reduce<unsigned long long>(r, Pr, (uint32_t)w.rtiles, s);
   gb_heavy_only_kernel<<<(kMaxHeavy + 255) / 256, 256, 0, s>>>(r, naggs); note_launch();
+  if (d_model_out) TQP_CUDA(cudaMemcpyAsync(d_model_out, w.model, sizeof(tqp_cdf_model), cudaMemcpyDeviceToDevice, s));
+  return last_launch();
+}
+
+tqp_status tqp_partition_learned(const tqp_col* keys, int nkeys, const int32_t* d_sel, int64_t n, const int64_t* d_n,
+                                 const tqp_learned_cfg* cfg, int32_t* d_bucket, int32_t* d_rows, int64_t* d_offsets,
+                                 float* d_train_x, float* d_train_y, tqp_cdf_model* d_model_out,
+                                 tqp_learned_stats* d_stats, void* ws, size_t* ws_bytes, tqp_stream_t stream) {
+  if (!ws_bytes || !cfg || n < 0 || n >= (1ll << 30) || nkeys < 1 || nkeys > TQP_MAX_KEYS || !keys)
+    return TQP_ERR_INVALID;
+  if (!valid_learned_cfg(cfg)) return TQP_ERR_INVALID;
+  for (int k = 0; k < nkeys; ++k)
+    if (!valid_dtype(keys[k].dtype)) return TQP_ERR_DTYPE;
+  Carver c(ws);
+  const LearnedWs w = carve_learned(c, n, cfg, 512, 0, nullptr, nullptr, false);
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const int nb = w.B + kMaxHeavy;  // bucket ids: B light buckets, then one per heavy key
+  int nbits = 1;
+  while ((1 << nbits) < nb) ++nbits;
+  int32_t* ids = c.take<int32_t>(nn);
+  uint32_t* sids = c.take<uint32_t>(nn);
+  int32_t* rows = c.take<int32_t>(nn);
+  long long* off = c.take<long long>((size_t)nb + 1);
+  SortWs sw = carve_sort(c, n, 4, (nbits + kRadixBits - 1) / kRadixBits);
+  if (!ws) {
+    *ws_bytes = c.off;
+    return TQP_OK;
+  }
+  if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
+  KeySet ks;
+  std::memset(&ks, 0, sizeof(ks));
+  ks.nkeys = nkeys;
+  for (int k = 0; k < nkeys; ++k) {
+    if (n > 0 && !keys[k].data) return TQP_ERR_INVALID;
+    ks.col[k] = keys[k].data;
+    ks.dt[k] = keys[k].dtype;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    if (d_offsets) TQP_CUDA(cudaMemsetAsync(d_offsets, 0, ((size_t)nb + 1) * sizeof(int64_t), s));
+    if (d_stats) TQP_CUDA(cudaMemsetAsync(d_stats, 0, sizeof(tqp_learned_stats), s));
+    return TQP_OK;
+  }
+  tqp_status st = run_learned_fit(w, ks, d_sel, n, d_n, cfg, cfg->heavy != 0, s);
+  if (st != TQP_OK) return st;
+  // every row's bucket id
+  PartArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.ks = ks;
+  pa.sel = d_sel;
+  pa.n_max = n;
+  pa.d_n = d_n;
+  pa.gp = w.gp;
+  pa.lp = w.lp;
+  pa.thr = w.thr;
+  pa.dir = w.dir;
+  pa.heavy = w.heavy;
+  int32_t* id_out = d_bucket ? d_bucket : ids;
+  {
+    const int mode = part_smem_bytes(w.B, 0, kThrShared) <= (size_t)kMaxSmemOptin ? kThrShared : kThrGlobal;
+    const size_t sm = part_smem_bytes(w.B, 0, mode);
+    auto k = mode == kThrShared ? lp_bucket_ids_kernel<kThrShared> : lp_bucket_ids_kernel<kThrGlobal>;
+    TQP_CUDA(smem_optin(k, (int)sm));
+    const int64_t tiles = (n + kPartThreads - 1) / kPartThreads;
+    k<<<persistent_grid(k, kPartThreads, sm, tiles), kPartThreads, sm, s>>>(pa, id_out); note_launch();
+  }
+  // rows grouped by bucket id, in input order within a bucket (a stable
+  // radix sort of the ids, the row ids as payload), and the offsets
+  if (d_rows || d_offsets || d_stats) {
+    int32_t* rows_out = d_rows ? d_rows : rows;
+    st = run_sort(sw, kKeyU32, id_out, d_sel, sids, rows_out, n, d_n, 0, nbits, s);
+    if (st != TQP_OK) return st;
+    long long* off_out = d_offsets ? reinterpret_cast<long long*>(d_offsets) : off;
+    lp_offsets_sorted_kernel<<<stride_grid(n, 256), 256, 0, s>>>(sids, n, d_n, nb, off_out); note_launch();
+    if (d_stats) {
+      lp_partition_stats_kernel<<<1, 1024, 0, s>>>(w.lp, off_out, w.loss, w.epochs, d_stats); note_launch();
+    }
+  }
+  if (d_train_x) TQP_CUDA(cudaMemcpyAsync(d_train_x, w.tx, (size_t)w.S * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (d_train_y) TQP_CUDA(cudaMemcpyAsync(d_train_y, w.ty, (size_t)w.S * sizeof(float), cudaMemcpyDeviceToDevice, s));
   if (d_model_out) TQP_CUDA(cudaMemcpyAsync(d_model_out, w.model, sizeof(tqp_cdf_model), cudaMemcpyDeviceToDevice, s));
   return last_launch();
 }
@@ -1514,6 +1612,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     // dense keys (a possible case up to the cell budget) skip the key sort:
     // kn counts the rows the sorted form takes
     const int64_t* kn = dcnt;
+    prof_mark(12 + d, true, s);
     TQP_CUDA(cudaMemsetAsync(w.dplan, 0, sizeof(DimDir), s));
     if (D.n > 0 && D.n <= (1ll << w.log2cells)) {
       TQP_CUDA(cudaMemsetAsync(w.krange, 0xFF, 8, s));
@@ -1525,6 +1624,8 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     const tqp_status st = w.learned ? run_sort_learned(w.lws, D.key.dtype, kin, vin, w.skeys, D.n, kn, lcfg, s)
                               : run_sort(w.ksort, D.key.dtype, kin, vin, w.skeys, w.srows, D.n, kn, 0, eb * 8, s);
     if (st != TQP_OK) return st;
+    prof_mark(12 + d, false, s);
+    prof_mark(14 + d, true, s);
     if (D.n > 0) {
       PregatherArgs pg;
       std::memset(&pg, 0, sizeof(pg));
@@ -1610,6 +1711,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       da.plan = plan;
       dir_direct_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(da); note_launch();
     }
+    prof_mark(14 + d, false, s);
   }
   // ---- slots, accumulators, probe, compaction
   star_slots_kernel<<<1, 32, 0, s>>>(plan, ndims, dims[0].group.data ? W[0].G : nullptr,

@@ -134,6 +134,8 @@ _lib.tqp_cdf_backward.argtypes = [_vp, _vp, _vp, _i64, _vp, _vp, _P(_sz), _vp]
 _lib.tqp_cdf_train.argtypes = [_vp, _vp, _i64, _vp, _P(TrainCfg), _vp, _vp, _P(_sz), _vp]
 _lib.tqp_groupby_agg_learned.argtypes = [_P(Col), _int, _P(Col), _int, _P(Expr), _int, _P(Agg), _int, _vp, _i64,
                                          _vp, _P(_vp), _vp, _i64, _vp, _P(LearnedCfg), _vp, _vp, _vp, _P(_sz), _vp]
+_lib.tqp_partition_learned.argtypes = [_P(Col), _int, _vp, _i64, _vp, _P(LearnedCfg), _vp, _vp, _vp, _vp, _vp, _vp,
+                                       _vp, _vp, _P(_sz), _vp]
 _lib.tqp_star_agg_batched.argtypes = [_P(BatchShape), _P(Problem), _int, _P(BatchCfg), _vp, _P(_sz), _vp]
 _lib.tqp_filter_noalloc.argtypes = [_P(Col), _int, _P(Pred), _int, _i64, _vp, _vp, _i64, _vp, _vp]
 _lib.tqp_filter_noalloc.restype = ctypes.c_int
@@ -148,7 +150,7 @@ for _f in ("tqp_filter", "tqp_gather", "tqp_like_prefix", "tqp_string_codes", "t
            "tqp_date_from_days", "tqp_date_parts", "tqp_sort_pairs", "tqp_join_eq", "tqp_groupby_agg", "tqp_star_agg",
            "tqp_star_agg_learned",
            "tqp_status_poll", "tqp_profile_events", "tqp_cdf_forward", "tqp_cdf_backward", "tqp_cdf_train",
-           "tqp_groupby_agg_learned", "tqp_star_agg_batched", "tqp_debug_set_spin_limit", "tqp_debug_inject_unpublished_tile"):
+           "tqp_groupby_agg_learned", "tqp_partition_learned", "tqp_star_agg_batched", "tqp_debug_set_spin_limit", "tqp_debug_inject_unpublished_tile"):
     getattr(_lib, _f).restype = ctypes.c_int
 
 
@@ -499,6 +501,38 @@ def tqp_groupby_agg_learned(keys, vals, exprs, aggs, cap, cfg=None, sel=None, n=
                 _ptr(sel), n, _ptr(d_n), kp, _ptr(out_aggs), cap, _ptr(G), ctypes.byref(cfg), _ptr(model),
                 _ptr(stats)], dev, stream)
     return out_keys, out_aggs, G, model, stats
+
+
+MAX_HEAVY = 1024  # TQP_MAX_HEAVY
+
+
+def tqp_partition_learned(keys, cfg=None, sel=None, n=None, d_n=None, stream=None):
+    """The learned range partition alone.  Returns a dict: bucket (int32 [n],
+    light buckets 0..B-1, heavy key h -> B + h), rows (int32 [n], grouped by
+    bucket id, input order within a bucket), offsets (int64 [B + MAX_HEAVY +
+    1]), train_x / train_y (float32 [sample]), model (device bytes), stats
+    (device bytes)."""
+    dev = keys[0].device
+    cfg = cfg or learned_cfg()
+    if n is None:
+        n = sel.numel() if sel is not None else keys[0].numel()
+    B = cfg.buckets
+    if B == 0:
+        B = 256
+        while B < (1 << 17) and B * 512 < n:
+            B <<= 1
+    out = {"bucket": torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+           "rows": torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+           "offsets": torch.empty(B + MAX_HEAVY + 1, dtype=torch.int64, device=dev),
+           "train_x": torch.empty(cfg.sample, dtype=torch.float32, device=dev),
+           "train_y": torch.empty(cfg.sample, dtype=torch.float32, device=dev),
+           "model": empty_model(dev),
+           "stats": torch.zeros(ctypes.sizeof(LearnedStats), dtype=torch.uint8, device=dev), "B": B}
+    _two_phase(_lib.tqp_partition_learned, "tqp_partition_learned",
+               [_cols(keys), len(keys), _ptr(sel), n, _ptr(d_n), ctypes.byref(cfg), _ptr(out["bucket"]),
+                _ptr(out["rows"]), _ptr(out["offsets"]), _ptr(out["train_x"]), _ptr(out["train_y"]),
+                _ptr(out["model"]), _ptr(out["stats"])], dev, stream)
+    return out
 
 
 def stats_from_device(t):

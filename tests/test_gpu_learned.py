@@ -173,3 +173,75 @@ def test_trained_network_gains_over_identity(T):
     assert res[True]["max_bucket"] * 4 < res[False]["max_bucket"]
     assert res[True]["over_capacity_rows"] * 4 < res[False]["over_capacity_rows"]
     assert res[True]["loss_last"] <= res[True]["loss_first"]
+
+
+def _partition_case(case):
+    r = np.random.default_rng(len(case) * 7 + 3)
+    sel = None
+    if case == "skew_heavy" or case == "skew_light":
+        z = dg.zipf_table(dg.ZIPF_S, dg.ZIPF_N)
+        keys = dg.make_table(dg.skew_groupby(), 600_000, zipf=z)["key"]
+    elif case == "lognormal_sel":
+        keys = np.exp(r.normal(12, 1.5, 800_000)).astype(np.int64) - 2**40
+        sel = np.sort(r.choice(len(keys), 500_000, replace=False)).astype(np.int32)
+    else:  # int32 keys over the full range with repeats
+        keys = r.integers(-2**31, 2**31, 400_000, dtype=np.int64).astype(np.int32)
+        keys[::3] = keys[5]
+    return keys, sel
+
+
+@pytest.mark.parametrize("case", ["skew_heavy", "skew_light", "lognormal_sel", "int32"])
+def test_partition_learned_against_oracle(T, case):
+    """The standalone learned partition, bit for bit: its training pairs
+    against the oracle's light-CDF targets (heavy keys set apart) and key
+    normalisation on the same sorted sample; every row's bucket against the
+    oracle's float32 evaluation of the returned network (the GPU finds the
+    bucket from the network's step positions, never by evaluating it per
+    row); heavy rows' ids against the oracle's heavy keys; the grouped rows
+    and offsets against the oracle's stable partition by bucket id."""
+    keys, sel = _partition_case(case)
+    heavy = case != "skew_light"
+    S = 16384
+    cfg = T.learned_cfg(sample=S, heavy=heavy, tcfg=T.train_cfg(epochs=20, lr=1e-4))
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = T.tqp_partition_learned([cu(keys)], cfg=cfg, sel=None if sel is None else cu(sel))
+    B = out["B"]
+    rows = np.arange(len(keys), dtype=np.int64) if sel is None else sel.astype(np.int64)
+    n = len(rows)
+    kr = keys[rows].astype(np.int64)
+    kmin = int(kr.min())
+    packed = (kr - kmin).astype(np.uint64)          # key - min: exact in 64-bit two's complement
+    SH = min(4 * S, 1 << 20)
+    mult = SH // S
+    samp = (np.arange(SH, dtype=np.int64) * n) // SH
+    order = np.argsort(packed[samp], kind="stable")
+    sorted_packed = packed[samp][order]
+    sorted_keys = kr[samp][order]
+    minc = max(2, min(4095, int(SH * 8192 / (2.0 * n)) + 1))
+    y_want, heavy_keys = orc.light_cdf_targets(sorted_packed, mult, S, minc, 1024 if heavy else 0)
+    m = T.model_from_device(out["model"])
+    umin = (kmin ^ (1 << 63)) if kmin >= 0 else (kmin + 2**64) ^ (1 << 63)
+    x_want = orc.cdf_normalize(sorted_keys[::mult][:S], umin, m["shift"], m["inv"])
+    assert np.array_equal(out["train_y"].cpu().numpy(), y_want)
+    assert np.array_equal(out["train_x"].cpu().numpy(), x_want)
+    st = T.stats_from_device(out["stats"])
+    assert st["heavy_keys"] == len(heavy_keys)
+    assert (len(heavy_keys) > 0) == (case in ("skew_heavy", "int32"))
+    # bucket ids: the network evaluated per row by the oracle, heavy keys apart
+    x = orc.cdf_normalize(kr, umin, m["shift"], m["inv"])
+    F = orc.cdf_forward_f32(np.array(m["w"], np.float32), np.array(m["b"], np.float32),
+                            np.array(m["a"], np.float32), m["c"], x)
+    want = orc.cdf_bucket(F, B)
+    hidx = np.searchsorted(heavy_keys, packed)
+    is_heavy = (hidx < len(heavy_keys)) & (heavy_keys[np.minimum(hidx, max(len(heavy_keys) - 1, 0))] == packed) \
+        if len(heavy_keys) else np.zeros(n, bool)
+    want = np.where(is_heavy, B + hidx, want).astype(np.int32)
+    got = out["bucket"].cpu().numpy()[:n]
+    assert np.array_equal(got, want)
+    light = ~is_heavy
+    assert np.all(np.diff(want[light][np.argsort(kr[light], kind="stable")]) >= 0)   # monotone in the key
+    prow, poff = orc.partition(want, B + T.MAX_HEAVY)
+    assert np.array_equal(out["offsets"].cpu().numpy(), poff)
+    assert np.array_equal(out["rows"].cpu().numpy()[:n], rows[prow].astype(np.int32))
+    assert st["light_rows"] == int(light.sum()) and st["buckets"] == B
+    assert T.tqp_status_poll() == T.OK
