@@ -76,11 +76,20 @@ class Q14:
         from paper_2209_04579_b300 import datagen_device as gd
         self.fact = gd.make_table(self.rec["fact"], self.n_fact)
         self.dim = gd.make_table(self.rec["dim"], self.m_dim)
+        # the sparse-key variant: dimension keys fmix32(i ^ seed) (unique,
+        # spread over the int32 range), foreign keys drawn among them
+        rs = self.dg.q14_tables(self.m_dim, True, master=self.master)
+        self.fact_s = gd.make_table(rs["fact"], self.n_fact)
+        self.dim_s = gd.make_table(rs["dim"], self.m_dim)
         return [self.fact["fk"], self.dim["key"], self.dim["region"], self.dim["price"]]
 
     def step(self):
         from paper_2209_04579_b300 import queries as Q
         return Q.q14(self.fact, self.dim)
+
+    def sparse_step(self):
+        from paper_2209_04579_b300 import queries as Q
+        return Q.q14(self.fact_s, self.dim_s)
 
     def rows(self):
         return self.n_fact
@@ -182,7 +191,7 @@ class Skew:
     @staticmethod
     def cfg(buckets):
         from paper_2209_04579_b300 import tqp
-        return tqp.learned_cfg(sample=65536, buckets=buckets, tcfg=tqp.train_cfg(epochs=40, lr=1e-4))
+        return tqp.learned_cfg(sample=65536, buckets=buckets, tcfg=tqp.train_cfg(epochs=40, lr=1e-5))
 
     def tune(self):
         """Bucket count from the autotuner (outputs sized to the group count)."""
@@ -216,7 +225,19 @@ class Skew:
         from paper_2209_04579_b300 import queries as Q
         from paper_2209_04579_b300 import tqp
         cfg = tqp.learned_cfg(sample=65536, buckets=self.buckets, train=False, init=1)
-        return Q.skew_learned(self.t, cap=self.cap, cfg=cfg)[:3]
+        r = Q.skew_learned(self.t, cap=self.cap, cfg=cfg)
+        self.serving_stats = r[4]
+        return r[:3]
+
+    def identity_step(self):
+        """The partitioned step with the identity CDF F(x) = x in place of a
+        fitted network (the method without its network)."""
+        from paper_2209_04579_b300 import queries as Q
+        from paper_2209_04579_b300 import tqp
+        cfg = tqp.learned_cfg(sample=65536, buckets=self.buckets, train=False, init=0)
+        r = Q.skew_learned(self.t, cap=self.cap, cfg=cfg)
+        self.identity_stats = r[4]
+        return r[:3]
 
     def rows(self):
         return self.n
@@ -361,7 +382,7 @@ class Star:
         if self.variant == "plain":
             return Q.star(self.fact, self.d1, self.d2)
         return Q.star(self.fact, self.d1, self.d2,
-                      learned=tqp.learned_cfg(sample=65536, tcfg=tqp.train_cfg(epochs=10, lr=1e-4)))
+                      learned=tqp.learned_cfg(sample=65536, tcfg=tqp.train_cfg(epochs=10, lr=1e-5)))
 
     def plain_step(self):
         from paper_2209_04579_b300 import queries as Q
@@ -1006,6 +1027,16 @@ def measure(W, args, world, local, flush, main):
     if hasattr(W, "serving_step") and getattr(W, "variant", "") != "plain":
         res["serving"] = {**side_arm(W.serving_step),
                           "what": "the learned step without training (quantile-knot network, no Adam epochs)"}
+        if hasattr(W, "serving_stats"):
+            res["serving"]["learned_stats"] = tqp.stats_from_device(W.serving_stats)
+    if hasattr(W, "identity_step") and getattr(W, "variant", "") != "plain":
+        res["identity"] = {**side_arm(W.identity_step),
+                           "what": "the partitioned step with the identity CDF in place of a fitted network"}
+        res["identity"]["learned_stats"] = tqp.stats_from_device(W.identity_stats)
+    if hasattr(W, "sparse_step"):
+        res["sparse_keys"] = {**side_arm(W.sparse_step),
+                              "what": "the same query with sparse dimension keys (fmix32 of the row, spread over the "
+                                      "int32 range; foreign keys drawn among them): no dense-key shortcut"}
     if hasattr(W, "plain_step"):
         # the same workload through the plain path (no learned partition /
         # one call per problem)

@@ -404,8 +404,10 @@ typedef struct {          /* written to device memory by the learned group-by */
   int64_t over_capacity_rows; /* rows in buckets sorted by the fallback */
   int64_t small_rows;     /* rows in buckets of 2..1024 rows (sorted by one warp
                              when the bucket's key span is below 2^48) */
-  float loss_first;       /* training loss before the first / the last step */
-  float loss_last;
+  float loss_first;       /* training loss of the network before training */
+  float loss_last;        /* training loss of the returned network: training keeps the
+                             parameters of the lowest loss it evaluated, so
+                             loss_last <= loss_first */
 } tqp_learned_stats;
 
 /* ------------------------------------------------------------------------

@@ -73,7 +73,17 @@ struct AdamState {
   float m[kNP];
   float v[kNP];
   unsigned done;  // blocks of the current gradient launch that have written their partials
+  int has_best;   // best[] holds the parameters of the lowest loss evaluated so far
+  float best_loss;
+  float best[kNP];
 };
+
+// Training modes of one gradient launch: a plain Adam step; an Adam step
+// that first records the parameters it evaluated when their loss is the
+// lowest so far; and the closing evaluation, which records likewise, takes
+// no step, and restores the best parameters (so training never returns a
+// network worse on its training pairs than the one it started from).
+constexpr int kTrainStep = 0, kTrainStepKeepBest = 1, kTrainRestoreBest = 2;
 
 __device__ __forceinline__ float* param_ptr(tqp_cdf_model* md, int k) {
   return k < kH ? &md->w[k] : k < 2 * kH ? &md->b[k - kH] : k < 3 * kH ? &md->a[k - 2 * kH] : &md->c;
@@ -105,7 +115,8 @@ __device__ __forceinline__ void adam_update(tqp_cdf_model* md, AdamState* st, co
 // epoch's loss and re-arms the counter for the next launch.
 __global__ void __launch_bounds__(256) cdf_grad_kernel(tqp_cdf_model* gm, const float* x, const float* y,
                                                        const int64_t* d_n, int64_t n_max, float* partial,
-                                                       AdamState* st, tqp_train_cfg cfg, int step, float* loss_out) {
+                                                       AdamState* st, tqp_train_cfg cfg, int step, float* loss_out,
+                                                       int mode = kTrainStep) {
   __shared__ tqp_cdf_model m;
   __shared__ float sx[kGradChunk], sd[kGradChunk];
   __shared__ float red[4][3 * kH];
@@ -180,15 +191,32 @@ __global__ void __launch_bounds__(256) cdf_grad_kernel(tqp_cdf_model* gm, const 
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  __shared__ float s_L;
   const int k = threadIdx.x;
-  if (k < kGradLen) {
-    float g = 0.0f;
+  float g = 0.0f;
+  if (k < kGradLen)
     for (unsigned b = 0; b < gridDim.x; ++b) g += __ldcg(&partial[(size_t)b * kGradLen + k]);
-    if (k == kNP) {
-      if (loss_out) loss_out[step] = n > 0 ? g / (float)n : 0.0f;
-    } else {
-      adam_update(gm, st, cfg, step, k, g);
+  if (k == kNP) {
+    s_L = n > 0 ? g / (float)n : 0.0f;
+    if (loss_out && mode != kTrainRestoreBest) loss_out[step] = s_L;
+  }
+  __syncthreads();
+  if (mode != kTrainStep) {
+    // the parameters this launch evaluated, if their loss is the lowest yet
+    const bool better = !st->has_best || s_L < st->best_loss;
+    if (better && k < kNP) st->best[k] = *param_ptr(gm, k);
+    __syncthreads();
+    if (better && k == 0) {
+      st->best_loss = s_L;
+      st->has_best = 1;
     }
+  }
+  if (mode != kTrainRestoreBest) {
+    if (k < kNP) adam_update(gm, st, cfg, step, k, g);
+  } else {
+    if (k < kNP) *param_ptr(gm, k) = st->best[k];
+    __syncthreads();
+    if (k == 0 && loss_out) loss_out[step] = st->best_loss;  // the returned parameters' loss
   }
   if (k == 0) st->done = 0;
 }
@@ -253,6 +281,7 @@ __global__ void lp_init_kernel(const GroupPlan* gp, int nkeys, tqp_cdf_model* md
   lp->min_count = min_count;
   for (int k = 0; k < kNP; ++k) st->m[k] = st->v[k] = 0.0f;
   st->done = 0;
+  st->has_best = 0;
 }
 
 __device__ __forceinline__ unsigned long long pack_row(const KeySet& ks, const GroupPlan* gp, int64_t row) {
@@ -771,7 +800,7 @@ __global__ void __launch_bounds__(1024) lp_partition_stats_kernel(const LearnedP
     r.small_rows += s_sm[w];
   }
   r.loss_first = (loss && epochs > 0) ? loss[0] : 0.0f;
-  r.loss_last = (loss && epochs > 0) ? loss[epochs - 1] : 0.0f;
+  r.loss_last = (loss && epochs > 0) ? loss[epochs] : 0.0f;
   *st = r;
 }
 
@@ -857,7 +886,7 @@ __global__ void __launch_bounds__(1024) lp_offsets_kernel(const LearnedPlan* lp,
     stats->over_capacity = o3;
     stats->nonempty = n3;
     stats->loss_first = (loss && epochs > 0) ? loss[0] : 0.0f;
-    stats->loss_last = (loss && epochs > 0) ? loss[epochs - 1] : 0.0f;
+    stats->loss_last = (loss && epochs > 0) ? loss[epochs] : 0.0f;  // the returned (best) network's
   }
 }
 

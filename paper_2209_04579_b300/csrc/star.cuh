@@ -318,7 +318,21 @@ struct DimDir {
   int use_bits;                   // probes test the cell bitmap first (unit cells, or a filtered dimension)
   long long ncells;               // 0: no passing rows (every probe misses)
   int direct;                     // dense keys: unit cells filled straight from the rows, no key sort
+  int compact;                    // compact form: dir[] plus one 32-bit entry per sorted key
 };
+
+// The compact form of a wide-cell directory, for a dimension whose 32-byte
+// records would not stay in L2 but whose compact form does: about five to
+// ten keys a cell, the cell's first sorted position in dir[c], and one
+// 32-bit entry per sorted key holding the key's offset within its cell (the
+// low bshift bits of key image - umin) and, above them, its group rank.  A
+// probe reads dir[c], dir[c + 1] and the cell's entries, all L2 hits, in
+// place of one random DRAM read of a record.
+#ifndef TQP_COMPACT_DIR_MAX_BYTES
+#define TQP_COMPACT_DIR_MAX_BYTES (100ll << 20)
+#endif
+constexpr long long kCompactDirMaxBytes = TQP_COMPACT_DIR_MAX_BYTES;  // dir + entries kept within L2 (126 MB)
+constexpr int kCompactKeysPerCell = 8;                   // cells: the power of two >= keys / this
 
 // ---- dense keys without the sort.  When the passing keys are unique and
 // dense in their range (span < 8 x their count, within the cell budget),
@@ -360,6 +374,7 @@ __global__ void dim_direct_plan_kernel(const unsigned long long* range, int64_t 
   r.bshift = 0;
   r.use_bits = 1;
   r.direct = 0;
+  r.compact = 0;
   r.ncells = 0;
   if (nd > 0 && r.umin <= r.umax) {
     const unsigned long long span = r.umax - r.umin;
@@ -427,12 +442,13 @@ __global__ void dir_direct_kernel(DirectArgs a) {
 // dimension that no predicate filtered skip the bitmap: foreign keys find
 // their row, and a miss is still found by the directory and the key.
 __global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, const int64_t* d_n, int64_t n_all,
-                                int log2_cells_max, DimDir* dd) {
+                                int log2_cells_max, const long long* d_G, DimDir* dd) {
   if (threadIdx.x != 0) return;
   if (dd->direct) return;  // planned from the key range, no sorted keys
   const int64_t nd = clamp_n(n_max, d_n);
   DimDir r;
   r.direct = 0;
+  r.compact = 0;
   r.use_bits = 1;
   if (nd == 0) {
     r.umin = 1;
@@ -453,8 +469,50 @@ __global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, co
   if (span < 8ull * (unsigned long long)nd && bits <= log2_cells_max) tb = bits > tb ? bits : tb;
   r.bshift = bits > tb ? bits - tb : 0;
   r.ncells = (long long)(span >> r.bshift) + 1;
+  if (r.bshift > 0) {
+    // the compact form when the records would leave L2 and it would not,
+    // and a key's cell offset and group rank share 32 bits
+    int tc = 1;
+    while (tc < log2_cells_max && (1ll << tc) * kCompactKeysPerCell < nd) ++tc;
+    const int cshift = bits > tc ? bits - tc : 0;
+    const long long G = d_G ? *d_G : 1;
+    const int rbits = G > 1 ? 64 - __clzll(G - 1) : 0;
+    const long long ccells = (long long)(span >> cshift) + 1;
+    const long long cbytes = (ccells + 1) * 4 + (long long)nd * 4;
+    if (cshift >= 1 && cshift + rbits <= 32 && cbytes <= kCompactDirMaxBytes &&
+        r.ncells * 32 > kCompactDirMaxBytes) {
+      r.compact = 1;
+      r.bshift = cshift;
+      r.ncells = ccells;
+    }
+  }
   r.use_bits = (r.bshift == 0 || nd < n_all) ? 1 : 0;
   *dd = r;
+}
+
+// Entries of the compact form: the key's offset within its cell and its
+// group rank above it.
+__global__ void dir_compact_kernel(const void* kr, int key_dt, int64_t n_max, const int64_t* d_n, const DimDir* dd,
+                                   uint32_t* entries) {
+  const DimDir r = *dd;
+  if (!r.compact) return;
+  const int64_t nd = clamp_n(n_max, d_n);
+  const unsigned long long mask = (1ull << r.bshift) - 1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nd; p += stride) {
+    unsigned long long img;
+    long long rank;
+    if (key_dt == TQP_I32) {
+      const KeyRank32 e = static_cast<const KeyRank32*>(kr)[p];
+      img = e.image;
+      rank = e.rank;
+    } else {
+      const KeyRank64 e = static_cast<const KeyRank64*>(kr)[p];
+      img = e.image;
+      rank = e.rank;
+    }
+    entries[p] = (uint32_t)(((img - r.umin) & mask) | ((unsigned long long)rank << r.bshift));
+  }
 }
 
 __global__ void dir_fill_kernel(const void* skeys, int key_dt, int64_t n_max, const int64_t* d_n, const DimDir* dd,
@@ -516,7 +574,7 @@ __host__ __device__ constexpr int cell_inline(bool k32) { return k32 ? 3 : 2; }
 
 __global__ void dir_table_kernel(const void* kr, int key_dt, const DimDir* dd, const int* dir, DirCell* table) {
   const DimDir r = *dd;
-  if (r.bshift == 0 || r.ncells == 0) return;
+  if (r.bshift == 0 || r.ncells == 0 || r.compact) return;
   const bool k32 = key_dt == TQP_I32;
   const int cap = cell_inline(k32);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -548,6 +606,8 @@ struct ProbeDim {
   const DimDir* dir_plan;
   const DirCell* table;
   const uint32_t* bitmap;
+  const int* dir;            // compact form: first sorted position of each cell
+  const uint32_t* entries;   // compact form: (cell offset, rank) per sorted key
 };
 
 struct ProbeArgs {
@@ -621,6 +681,20 @@ __device__ __forceinline__ void ring_flush(WarpRing<F>& q, Drain&& drain) {
   drain(e, cnt);
 }
 
+// Loads of data the probe reads once (fact columns, random records):
+// streaming (evict first) so that they do not displace re-read tables.
+#ifndef TQP_PROBE_STREAM_LOADS
+#define TQP_PROBE_STREAM_LOADS 1
+#endif
+template <typename T>
+__device__ __forceinline__ T ld_once(const T* p) {
+#if TQP_PROBE_STREAM_LOADS
+  return __ldcs(p);
+#else
+  return __ldg(p);
+#endif
+}
+
 // Fused probe + aggregate as a warp pipeline with dense stages.
 //  1. Each thread takes ITEMS fact rows of the tile.  Without fact predicates
 //     they go straight to the dimension probe.  With predicates, the passing
@@ -684,12 +758,15 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   }
   DimDir dd[ND];
   long long stride[ND];
-  bool unit[ND];
+  bool unit[ND], cpt[ND];
+  uint32_t cmask[ND];  // compact form: a key's offset bits within its cell
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     dd[d] = *a.dim[d].dir_plan;
     stride[d] = plan->stride[d];
     unit[d] = dd[d].bshift == 0;
+    cpt[d] = dd[d].compact != 0;
+    cmask[d] = dd[d].bshift >= 32 ? 0xFFFFFFFFu : (1u << dd[d].bshift) - 1u;
   }
   extern __shared__ uint32_t s_bm[];
   bool sbm = false;
@@ -743,10 +820,12 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   // a unit-width dimension); slot: the sum of rank * stride over the wide
   // dimensions (a unit cell's rank is read by the fold, on compacted rows).
   // pre: the first dimension's key image u0 is already loaded.
+  // fact columns are read once: streaming loads, so that they do not evict
+  // the dimension tables that stay in L2
   auto fk_image = [&](int d, int64_t row) -> UK {
     const ProbeDim& D = a.dim[d];
-    if (K32 || D.key_dt == TQP_I32) return (UK)((uint32_t)__ldg(static_cast<const int32_t*>(D.fk) + row) ^ 0x80000000u);
-    return (UK)((unsigned long long)__ldg(static_cast<const long long*>(D.fk) + row) ^ 0x8000000000000000ull);
+    if (K32 || D.key_dt == TQP_I32) return (UK)((uint32_t)ld_once(static_cast<const int32_t*>(D.fk) + row) ^ 0x80000000u);
+    return (UK)((unsigned long long)ld_once(static_cast<const long long*>(D.fk) + row) ^ 0x8000000000000000ull);
   };
   // The keys of a wide cell beyond its inline ones: the first key >= x in
   // kr[l, h), narrowed while the interval is long, then scanned.
@@ -799,8 +878,15 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
       ra[d] = rb[d] = make_int4(0, 0, 0, 0);
       rk[d] = 0;
       if (lv[d] && !unit[d]) {
-        ra[d] = __ldg(&a.dim[d].table[c[d]].a);
-        rb[d] = __ldg(&a.dim[d].table[c[d]].b);
+        if (cpt[d]) {
+          // compact form: the cell's range of sorted positions (L2 hits)
+          ra[d].x = __ldg(&a.dim[d].dir[c[d]]);
+          ra[d].y = __ldg(&a.dim[d].dir[c[d] + 1]);
+        } else {
+          // a random record, read once: streaming, like the fact columns
+          ra[d] = ld_once(&a.dim[d].table[c[d]].a);
+          rb[d] = ld_once(&a.dim[d].table[c[d]].b);
+        }
       }
     }
     bool all = live;
@@ -808,7 +894,25 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
       pos[d] = (int)c[d];
-      if (!unit[d]) {
+      if (!unit[d] && cpt[d]) {
+        // compact form: the cell's entries ascend by key; the first whose
+        // offset reaches the key's decides
+        const uint32_t off = (uint32_t)(u[d] - (UK)dd[d].umin) & cmask[d];
+        int found = -1;
+        if (lv[d])
+          for (int i = ra[d].x; i < ra[d].y; ++i) {
+            const uint32_t e = __ldg(&a.dim[d].entries[i]);
+            const uint32_t eo = e & cmask[d];
+            if (eo < off) continue;
+            if (eo == off) {
+              found = i;
+              rk[d] = dd[d].bshift >= 32 ? 0 : (int)(e >> dd[d].bshift);
+            }
+            break;
+          }
+        lv[d] = lv[d] && found >= 0;
+        pos[d] = found;
+      } else if (!unit[d]) {
         // match the inline keys; a key above the last inline one of a fuller
         // cell is searched among the cell's remaining sorted keys
         const int lo = rb[d].z, cnt = rb[d].w;
@@ -841,7 +945,8 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   // in its group's slot
   auto term_value = [&](int vi, int row, const int (&pos)[ND]) -> long long {
     const int src = s_vsrc[vi];
-    if (src == 0) return load_as_i64(s_vptr[vi], s_vdt[vi], row);
+    if (src == 0) return TQP_PROBE_STREAM_LOADS ? load_as_i64_stream(s_vptr[vi], s_vdt[vi], row)
+                                                : load_as_i64(s_vptr[vi], s_vdt[vi], row);
     const bool cell = src == 1 ? unit[0] : unit[ND - 1];
     return static_cast<const long long*>(cell ? s_vptr_cell[vi] : s_vptr[vi])[src == 1 ? pos[0] : pos[ND - 1]];
   };
@@ -859,8 +964,8 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
       if (op != TQP_COUNT && simple) {
         const int ai = s_ai[q];
         const int idx = ai == 0 ? row : ai == 1 ? pos[0] : pos[ND - 1];
-        x = (long long)((unsigned long long)s_am[q] * (unsigned long long)__ldg(s_ap[q] + idx) +
-                        (unsigned long long)s_aa[q]);
+        const long long v = ai == 0 ? ld_once(s_ap[q] + idx) : __ldg(s_ap[q] + idx);
+        x = (long long)((unsigned long long)s_am[q] * (unsigned long long)v + (unsigned long long)s_aa[q]);
       } else if (op != TQP_COUNT) {
         const int e = A.expr[q];
         unsigned long long ev = 1;
@@ -946,7 +1051,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     auto load4 = [&](int64_t w, int j, UK (&dst)[ITEMS]) {
       const int64_t r = w * WT + (int64_t)lane * ITEMS + 4 * j;
       if (w < nwt && r + 3 < a.n_fact) {
-        const int4 q = __ldg(reinterpret_cast<const int4*>(fk0 + r));
+        const int4 q = ld_once(reinterpret_cast<const int4*>(fk0 + r));
         dst[4 * j] = (UK)((uint32_t)q.x ^ 0x80000000u);
         dst[4 * j + 1] = (UK)((uint32_t)q.y ^ 0x80000000u);
         dst[4 * j + 2] = (UK)((uint32_t)q.z ^ 0x80000000u);
@@ -954,7 +1059,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
       } else {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          dst[4 * j + e] = (w < nwt && r + e < a.n_fact) ? (UK)((uint32_t)__ldg(fk0 + r + e) ^ 0x80000000u) : (UK)0;
+          dst[4 * j + e] = (w < nwt && r + e < a.n_fact) ? (UK)((uint32_t)ld_once(fk0 + r + e) ^ 0x80000000u) : (UK)0;
       }
     };
     UK nxt[ITEMS];
@@ -1031,7 +1136,9 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k)
           if ((pass >> k) & 1u)
-            if (!compare(load_as_i64(a.pcol[p], a.pdt[p], wt * WT + k * 32 + lane), a.pop[p], a.plit[p]))
+            if (!compare(TQP_PROBE_STREAM_LOADS ? load_as_i64_stream(a.pcol[p], a.pdt[p], wt * WT + k * 32 + lane)
+                                                : load_as_i64(a.pcol[p], a.pdt[p], wt * WT + k * 32 + lane),
+                         a.pop[p], a.plit[p]))
               pass &= ~(1u << k);
       }
       // one rolled loop, so that the probe and the fold behind the queue

@@ -9,7 +9,6 @@
 #include <atomic>
 #include <map>
 #include <mutex>
-#include <set>
 #include <tuple>
 #include <unordered_map>
 #include <vector>
@@ -86,20 +85,23 @@ int stride_grid(int64_t n, int threads, int per_sm = 8) {
   return (int)(g < 1 ? 1 : g);
 }
 
-// Raises a kernel's dynamic shared memory limit to `bytes` on the current
-// device.  The attribute belongs to one device, so it is set once per
-// (device, kernel, size), under a lock shared by every host thread.
+// Makes a kernel accept `bytes` of dynamic shared memory on the current
+// device.  The attribute belongs to one device and is a ceiling, so it is
+// only ever raised: per (device, kernel) the largest value set so far is
+// kept, under a lock shared by every host thread.  (Lowering it for a
+// smaller launch would make a later, larger launch fail.)
 cudaError_t smem_optin(const void* fn, int bytes) {
   static std::mutex mu;
-  static std::set<std::tuple<int, const void*, int>> done;
+  static std::map<std::pair<int, const void*>, int> ceiling;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> g(mu);
-  const auto key = std::make_tuple(dev, fn, bytes);
-  if (done.count(key)) return cudaSuccess;
+  const auto key = std::make_pair(dev, fn);
+  auto it = ceiling.find(key);
+  if (it != ceiling.end() && it->second >= bytes) return cudaSuccess;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done.insert(key);
+  if (e == cudaSuccess) ceiling[key] = bytes;
   return e;
 }
 
@@ -151,6 +153,13 @@ tqp_status last_launch() { return cudaGetLastError() == cudaSuccess ? TQP_OK : T
 #define TQP_CUDA(call)                               \
   do {                                               \
     if ((call) != cudaSuccess) return TQP_ERR_CUDA;  \
+  } while (0)
+
+// After a launch whose later kernels depend on it (and which can fail to
+// launch, e.g. for its shared memory): stop before enqueueing them.
+#define TQP_LAUNCHED()                                                  \
+  do {                                                                  \
+    if (cudaPeekAtLastError() != cudaSuccess) return last_launch();     \
   } while (0)
 
 // ---------------------------------------------------------------- sort
@@ -834,11 +843,20 @@ bool valid_train_cfg(const tqp_train_cfg* cfg) {
          cfg->beta2 >= 0 && cfg->beta2 < 1 && cfg->eps > 0;
 }
 
+// cfg.epochs Adam steps.  keep_best: each step first records the parameters
+// it evaluated when their loss is the lowest so far, and a closing
+// evaluation restores the best (loss[epochs] then holds its loss).
 void launch_training(tqp_cdf_model* model, const float* x, const float* y, int64_t n, const int64_t* d_n,
-                     const tqp_train_cfg& cfg, float* partial, AdamState* st, float* loss, cudaStream_t s) {
+                     const tqp_train_cfg& cfg, float* partial, AdamState* st, float* loss, cudaStream_t s,
+                     bool keep_best = false) {
   const int nb = (int)((n + kGradChunk - 1) / kGradChunk);
   for (int e = 0; e < cfg.epochs; ++e) {
-    cdf_grad_kernel<<<nb, 256, 0, s>>>(model, x, y, d_n, n, partial, st, cfg, e, loss); note_launch();
+    cdf_grad_kernel<<<nb, 256, 0, s>>>(model, x, y, d_n, n, partial, st, cfg, e, loss,
+                                       keep_best ? kTrainStepKeepBest : kTrainStep); note_launch();
+  }
+  if (keep_best && cfg.epochs > 0) {
+    cdf_grad_kernel<<<nb, 256, 0, s>>>(model, x, y, d_n, n, partial, st, cfg, cfg.epochs, loss, kTrainRestoreBest);
+    note_launch();
   }
 }
 }  // namespace
@@ -938,7 +956,7 @@ LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int ro
   w.lp = c.take<LearnedPlan>(1);
   w.adam = c.take<AdamState>(1);
   w.partial = c.take<float>((size_t)nb * kGradLen);
-  w.loss = c.take<float>((size_t)(w.epochs > 0 ? w.epochs : 1));
+  w.loss = c.take<float>((size_t)w.epochs + 1);  // per epoch, then the returned network's
   w.heavy = c.take<unsigned long long>(kMaxHeavy);
   w.heavy_acc = c.take<long long>((size_t)kMaxHeavy * (naggs > 0 ? naggs : 1));
   w.thr = c.take<unsigned>((size_t)B);
@@ -1009,7 +1027,8 @@ tqp_status run_learned_fit(const LearnedWs& w, const KeySet& ks, const int32_t* 
     lp_quantile_init_kernel<<<1, kH, 0, s>>>(w.tx, w.ty, S, w.lp, w.model); note_launch();
   }
   // 4. training, then the step positions of the bucket function and their directory
-  if (w.epochs > 0) launch_training(w.model, w.tx, w.ty, S, nullptr, cfg->train_cfg, w.partial, w.adam, w.loss, s);
+  if (w.epochs > 0)
+    launch_training(w.model, w.tx, w.ty, S, nullptr, cfg->train_cfg, w.partial, w.adam, w.loss, s, true);
   if (B > 1) {
     lp_thresholds_kernel<<<(B - 1 + 255) / 256, 256, 0, s>>>(w.model, w.lp, w.thr); note_launch();
   }
@@ -1065,6 +1084,7 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
     const int64_t ptiles = (n + kPartThreads * kPartItems - 1) / (kPartThreads * kPartItems);
     const int gh = hmode == kBlockHist ? w.nblk : persistent_grid(hk, kPartThreads, hsm, ptiles);
     hk<<<gh, kPartThreads, hsm, s>>>(pa); note_launch();
+    TQP_LAUNCHED();
     if (hmode == kBlockHist) {
       lp_bcols_kernel<<<(B + 255) / 256, 256, 0, s>>>(w.bcount, w.nblk, w.lp, w.count); note_launch();
     }
@@ -1075,6 +1095,7 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
     }
     prof_mark(8, true, s);
     sk<<<persistent_grid(sk, kPartThreads, ssm, ptiles), kPartThreads, ssm, s>>>(pa, P); note_launch();
+    TQP_LAUNCHED();
     prof_mark(8, false, s);
   }
   // 6. every bucket sorted: on-chip up to the capacity, else by one block in global memory
@@ -1099,12 +1120,14 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
                                (B + kWarpSortWarps - 1) / kWarpSortWarps);
       prof_mark(9, true, s);
       lp_bucket_sort_warp_kernel<<<gw, kWarpSortWarps * 32, wsmem, s>>>(ba, w.queue + 1, w.big_flags); note_launch();
+      TQP_LAUNCHED();
       prof_mark(9, false, s);
     }
     int g = w.nblk;
     if (g > B) g = B;
     prof_mark(7, true, s);
     lp_bucket_sort_kernel<<<g, kLocalThreads, smem, s>>>(ba); note_launch();
+    TQP_LAUNCHED();
     prof_mark(7, false, s);
   }
   return TQP_OK;
@@ -1273,6 +1296,7 @@ tqp_status tqp_partition_learned(const tqp_col* keys, int nkeys, const int32_t* 
     TQP_CUDA(smem_optin(k, (int)sm));
     const int64_t tiles = (n + kPartThreads - 1) / kPartThreads;
     k<<<persistent_grid(k, kPartThreads, sm, tiles), kPartThreads, sm, s>>>(pa, id_out); note_launch();
+    TQP_LAUNCHED();
   }
   // rows grouped by bucket id, in input order within a bucket (a stable
   // radix sort of the ids, the row ids as payload), and the offsets
@@ -1336,6 +1360,7 @@ struct StarDimWs {
   uint32_t* bitmap;
   int log2cells;
   DirCell* table;
+  uint32_t* entries;           // compact form: one 32-bit entry per sorted key
   int32_t* rank_cell;
   long long* dval_cell[TQP_MAX_VALS];
 };
@@ -1487,6 +1512,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       while (t < w.log2cells && (1ll << t) < 2 * D.n) ++t;
       w.table = c.take<DirCell>((size_t)(1ll << t) + 1);
     }
+    w.entries = c.take<uint32_t>(nn);
     w.rank_cell = c.take<int32_t>((size_t)(1ll << w.log2cells) + 1);
     for (int v = 0; v < nvals; ++v)
       if (vals[v].src == d + 1) w.dval_cell[v] = c.take<long long>((size_t)(1ll << w.log2cells) + 1);
@@ -1655,7 +1681,8 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       }
       star_pregather_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(pg); note_launch();
     }
-    dir_plan_kernel<<<1, 32, 0, s>>>(w.skeys, D.key.dtype, D.n, kn, D.n, w.log2cells, w.dplan); note_launch();
+    dir_plan_kernel<<<1, 32, 0, s>>>(w.skeys, D.key.dtype, D.n, kn, D.n, w.log2cells,
+                                     D.group.data ? w.G : nullptr, w.dplan); note_launch();
     if (D.n > 0) {
       TQP_CUDA(cudaMemsetAsync(w.bitmap, 0, ((size_t)(1ll << w.log2cells) / 32 + 1) * sizeof(uint32_t), s));
       dir_fill_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(w.skeys, D.key.dtype, D.n, kn, w.dplan, w.dir,
@@ -1683,6 +1710,8 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
         dir_table_kernel<<<stride_grid((1ll << t) + 1, 256), 256, 0, s>>>(w.kr, D.key.dtype, w.dplan, w.dir, w.table);
         note_launch();
       }
+      dir_compact_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(w.kr, D.key.dtype, D.n, kn, w.dplan, w.entries);
+      note_launch();
       DirectArgs da;
       std::memset(&da, 0, sizeof(da));
       da.keys = kin;
@@ -1731,6 +1760,8 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     pa.dim[d].dir_plan = W[d].dplan;
     pa.dim[d].table = W[d].table;
     pa.dim[d].bitmap = W[d].bitmap;
+    pa.dim[d].dir = W[d].dir;
+    pa.dim[d].entries = W[d].entries;
   }
   pa.npred = nfact_preds;
   for (int p = 0; p < nfact_preds; ++p) {
