@@ -410,7 +410,11 @@ class Star:
                 (12, "dim1 key sort (20M int32 keys with their group ranks)", n1 * 8 * 2),
                 (13, "dim2 key sort (150M int64 keys with their group ranks)", n2 * 12 * 2),
                 (14, "dim1 directory and cell records", n1 * 8 * 2),
-                (15, "dim2 directory and cell records", n2 * 12 * 2)]
+                (15, "dim2 directory and cell records", n2 * 12 * 2),
+                # the learned partition's kernels of the last dimension sorted (dim2):
+                # the scatter reads key and rank and writes them bucketed
+                (8, "lp_scatter_kernel (dim2)", n2 * 12 * 2),
+                (7, "lp_bucket_sort_kernel (dim2)", n2 * 12 * 2)]
 
     def traffic(self):
         # ncu DRAM bytes (read + write) of one probe launch on the quarter-size

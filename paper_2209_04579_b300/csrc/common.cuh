@@ -40,18 +40,6 @@ __device__ __forceinline__ int64_t load_as_i64(const void* p, int dt, int64_t i)
   }
 }
 
-// The same load marked as streaming (ld.global.cs: evict first from L1 and
-// L2), for data read once per pass, so that it does not push out of L2 the
-// tables a kernel re-reads at random.
-__device__ __forceinline__ int64_t load_as_i64_stream(const void* p, int dt, int64_t i) {
-  switch (dt) {
-    case TQP_I8: return __ldcs(static_cast<const signed char*>(p) + i);
-    case TQP_I16: return __ldcs(static_cast<const short*>(p) + i);
-    case TQP_I32: return __ldcs(static_cast<const int*>(p) + i);
-    default: return __ldcs(static_cast<const long long*>(p) + i);
-  }
-}
-
 __device__ __forceinline__ void store_from_i64(void* p, int dt, int64_t i, int64_t v) {
   switch (dt) {
     case TQP_I8: static_cast<int8_t*>(p)[i] = static_cast<int8_t>(v); break;

@@ -31,6 +31,13 @@ constexpr int kWarpCap = 1024;    // rows one warp sorts on-chip
 constexpr int kLocalThreads = 512;
 constexpr int kLocalWarps = kLocalThreads / 32;
 constexpr int kLocalItems = kLocalCap / kLocalThreads;  // 16
+// Bucket cursors of the scatter sit this many words apart (32: one per
+// 128-byte L2 line), so that the per-row atomics on different cursors do
+// not queue behind each other at one L2 line.
+#ifndef TQP_CURSOR_STRIDE
+#define TQP_CURSOR_STRIDE 32
+#endif
+constexpr int kCursorStride = TQP_CURSOR_STRIDE;
 
 __device__ __forceinline__ float cdf_eval(const tqp_cdf_model& m, float x) {
   float f = m.c;
@@ -551,7 +558,7 @@ struct PartArgs {
   const int* dir;
   const unsigned long long* heavy;
   unsigned* count;          // [B]
-  unsigned* cursor;         // [B]
+  unsigned* cursor;         // [B * kCursorStride]: bucket b's cursor at b * kCursorStride
   unsigned* bcount;         // kBlockHist: [blocks][B] counts
   unsigned long long* out_p;
   int32_t* out_row;
@@ -843,7 +850,7 @@ __global__ void __launch_bounds__(1024) lp_offsets_kernel(const LearnedPlan* lp,
   unsigned run = (unsigned)excl;
   for (int b = b0; b < b0 + per && b < B; ++b) {
     off[b] = run;
-    cursor[b] = run;
+    cursor[(size_t)b * kCursorStride] = run;
     run += count[b];
   }
   if (threadIdx.x == 1023) {
@@ -957,7 +964,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
     for (int k = 0; k < kPartItems; ++k) {
       if (h[k] != -1) continue;
       const int b = lp_bucket<MODE >= kThrShared>(p[k], lp, S.dir, thr);
-      pos[k] = atomicAdd(&a.cursor[b], 1u);
+      pos[k] = atomicAdd(&a.cursor[(size_t)b * kCursorStride], 1u);
     }
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k)
@@ -987,9 +994,11 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
 }
 
 // Sorted packed keys back to the key column's dtype (one key column,
-// packed as key - kmin).
+// packed as key - kmin).  skip: a device flag that, when set, says the
+// decoded keys are not needed.
 __global__ void lp_decode_kernel(const unsigned long long* p, const GroupPlan* gp, int dt, int64_t n_max,
-                                 const int64_t* d_n, void* out) {
+                                 const int64_t* d_n, void* out, const int* skip = nullptr) {
+  if (skip && *skip) return;
   const int64_t n = clamp_n(n_max, d_n);
   const unsigned long long kmin = (unsigned long long)gp->kmin[0];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;

@@ -212,6 +212,21 @@ __global__ void dom_payload_kernel(const void* gcol, int gdt, const int32_t* sel
   }
 }
 
+// ---- key directory of one dimension: the range of its sorted passing keys
+// is cut into at most 2^log2_cells cells of 2^bshift key values; dir[c] is
+// the first sorted position whose key falls in cell c or later, and a bitmap
+// marks the non-empty cells.  A probe tests the cell's bit (an L1-resident
+// word) and then compares the few keys of dir[c] .. dir[c+1]: a bound search
+// whose first levels are the directory.  Exact for any key distribution.
+struct DimDir {
+  unsigned long long umin, umax;  // order-preserving images of the first and last key
+  int bshift;
+  int use_bits;                   // probes test the cell bitmap first (unit cells, or a filtered dimension)
+  long long ncells;               // 0: no passing rows (every probe misses)
+  int direct;                     // dense keys: unit cells filled straight from the rows, no key sort
+  int fused;                      // the whole directory comes from one pass over the sorted packed keys
+};
+
 // ---- gather ranks and aggregated dimension columns into key order; check
 // that keys are unique among the passing rows.
 struct PregatherArgs {
@@ -228,6 +243,7 @@ struct PregatherArgs {
   const uint32_t* dbits;
   const int* dpre;
   int rank_payload;            // with dom->on: srows holds each sorted key's group rank
+  const DimDir* dd;            // nothing to do when the fused pass built the directory
   int32_t* rank_sorted;
   void* kr;                    // KeyRank32 (int32 keys) or KeyRank64 per sorted position
   int nv;
@@ -238,6 +254,7 @@ struct PregatherArgs {
 };
 
 __global__ void star_pregather_kernel(PregatherArgs a) {
+  if (a.dd && a.dd->fused) return;
   const int64_t n = clamp_n(a.n_max, a.d_n);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   DomPlan dom;
@@ -306,33 +323,6 @@ __global__ void star_init_acc_kernel(const StarPlan* plan, const StarAcc A, long
     acc[i] = acc_identity(A, (int)(i % nacc));
 }
 
-// ---- key directory of one dimension: the range of its sorted passing keys
-// is cut into at most 2^log2_cells cells of 2^bshift key values; dir[c] is
-// the first sorted position whose key falls in cell c or later, and a bitmap
-// marks the non-empty cells.  A probe tests the cell's bit (an L1-resident
-// word) and then compares the few keys of dir[c] .. dir[c+1]: a bound search
-// whose first levels are the directory.  Exact for any key distribution.
-struct DimDir {
-  unsigned long long umin, umax;  // order-preserving images of the first and last key
-  int bshift;
-  int use_bits;                   // probes test the cell bitmap first (unit cells, or a filtered dimension)
-  long long ncells;               // 0: no passing rows (every probe misses)
-  int direct;                     // dense keys: unit cells filled straight from the rows, no key sort
-  int compact;                    // compact form: dir[] plus one 32-bit entry per sorted key
-};
-
-// The compact form of a wide-cell directory, for a dimension whose 32-byte
-// records would not stay in L2 but whose compact form does: about five to
-// ten keys a cell, the cell's first sorted position in dir[c], and one
-// 32-bit entry per sorted key holding the key's offset within its cell (the
-// low bshift bits of key image - umin) and, above them, its group rank.  A
-// probe reads dir[c], dir[c + 1] and the cell's entries, all L2 hits, in
-// place of one random DRAM read of a record.
-#ifndef TQP_COMPACT_DIR_MAX_BYTES
-#define TQP_COMPACT_DIR_MAX_BYTES (100ll << 20)
-#endif
-constexpr long long kCompactDirMaxBytes = TQP_COMPACT_DIR_MAX_BYTES;  // dir + entries kept within L2 (126 MB)
-constexpr int kCompactKeysPerCell = 8;                   // cells: the power of two >= keys / this
 
 // ---- dense keys without the sort.  When the passing keys are unique and
 // dense in their range (span < 8 x their count, within the cell budget),
@@ -374,7 +364,7 @@ __global__ void dim_direct_plan_kernel(const unsigned long long* range, int64_t 
   r.bshift = 0;
   r.use_bits = 1;
   r.direct = 0;
-  r.compact = 0;
+  r.fused = 0;
   r.ncells = 0;
   if (nd > 0 && r.umin <= r.umax) {
     const unsigned long long span = r.umax - r.umin;
@@ -438,28 +428,38 @@ __global__ void dir_direct_kernel(DirectArgs a) {
 
 
 
-// n_all: the dimension's rows before its predicates.  Wide cells of a
+// Wide cells (bshift > 0) get a table of one 32-byte record per cell, so
+// that a probe reads one record instead of the directory entry and then the
+// keys it points to.  The record holds the cell's first keys inline with
+// their group ranks, its first sorted position lo and its key count cnt:
+//   int32 keys: a = {img0, img1, img2, rank0}, b = {rank1, rank2, lo, cnt}
+//   int64 keys: a = {img0 (2 words), img1 (2 words)}, b = {rank0, rank1, lo, cnt}
+// A cell with more keys than fit inline keeps the rest in the sorted
+// key/rank pairs, after position lo + inline count.
+struct __align__(16) DirCell {
+  int4 a, b;
+};
+__host__ __device__ constexpr int cell_inline(bool k32) { return k32 ? 3 : 2; }
+
+// The cell plan of nd sorted passing keys whose images run from umin to
+// umax.  n_all: the dimension's rows before its predicates.  Wide cells of a
 // dimension that no predicate filtered skip the bitmap: foreign keys find
 // their row, and a miss is still found by the directory and the key.
-__global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, const int64_t* d_n, int64_t n_all,
-                                int log2_cells_max, const long long* d_G, DimDir* dd) {
-  if (threadIdx.x != 0) return;
-  if (dd->direct) return;  // planned from the key range, no sorted keys
-  const int64_t nd = clamp_n(n_max, d_n);
+__device__ DimDir plan_cells(unsigned long long umin, unsigned long long umax, int64_t nd, int64_t n_all,
+                             int log2_cells_max, const long long* d_G) {
   DimDir r;
   r.direct = 0;
-  r.compact = 0;
+  r.fused = 0;
   r.use_bits = 1;
   if (nd == 0) {
     r.umin = 1;
     r.umax = 0;
     r.bshift = 0;
     r.ncells = 0;
-    *dd = r;
-    return;
+    return r;
   }
-  r.umin = key_image(skeys, key_dt, 0);
-  r.umax = key_image(skeys, key_dt, nd - 1);
+  r.umin = umin;
+  r.umax = umax;
   unsigned long long span = r.umax - r.umin;
   int tb = 1;
   while (tb < log2_cells_max && (1ll << tb) < 2 * nd) ++tb;
@@ -469,56 +469,127 @@ __global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, co
   if (span < 8ull * (unsigned long long)nd && bits <= log2_cells_max) tb = bits > tb ? bits : tb;
   r.bshift = bits > tb ? bits - tb : 0;
   r.ncells = (long long)(span >> r.bshift) + 1;
-  if (r.bshift > 0) {
-    // the compact form when the records would leave L2 and it would not,
-    // and a key's cell offset and group rank share 32 bits
-    int tc = 1;
-    while (tc < log2_cells_max && (1ll << tc) * kCompactKeysPerCell < nd) ++tc;
-    const int cshift = bits > tc ? bits - tc : 0;
-    const long long G = d_G ? *d_G : 1;
-    const int rbits = G > 1 ? 64 - __clzll(G - 1) : 0;
-    const long long ccells = (long long)(span >> cshift) + 1;
-    const long long cbytes = (ccells + 1) * 4 + (long long)nd * 4;
-    if (cshift >= 1 && cshift + rbits <= 32 && cbytes <= kCompactDirMaxBytes &&
-        r.ncells * 32 > kCompactDirMaxBytes) {
-      r.compact = 1;
-      r.bshift = cshift;
-      r.ncells = ccells;
-    }
-  }
   r.use_bits = (r.bshift == 0 || nd < n_all) ? 1 : 0;
+  return r;
+}
+
+__global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, const int64_t* d_n, int64_t n_all,
+                                int log2_cells_max, const long long* d_G, DimDir* dd) {
+  if (threadIdx.x != 0) return;
+  if (dd->direct || dd->fused) return;  // planned from the key range, or by the fused pass
+  const int64_t nd = clamp_n(n_max, d_n);
+  *dd = plan_cells(nd ? key_image(skeys, key_dt, 0) : 1, nd ? key_image(skeys, key_dt, nd - 1) : 0, nd, n_all,
+                   log2_cells_max, d_G);
+}
+
+// ---- the directory in one pass, for a dimension sorted by the learned
+// partitioner: its keys sorted as packed words (key - kmin), and each
+// sorted key's group rank as the sort's payload (or no group column).
+// The plan is taken from the first and last packed keys; when the cells
+// are wide and no dimension value is aggregated (eligible), dir_emit_kernel
+// writes every structure the probe reads -- the key/rank pairs, the cell
+// starts, the bitmap, and the 32-byte records -- and
+// the decode, gather and directory passes of the sorted form skip their
+// work (fused = 1).
+__device__ __forceinline__ unsigned long long packed_image(unsigned long long packed, long long kmin, int key_dt) {
+  const unsigned long long key = packed + (unsigned long long)kmin;  // the key, 64-bit two's complement
+  return key_dt == TQP_I32 ? (unsigned long long)((uint32_t)key ^ 0x80000000u) : key ^ 0x8000000000000000ull;
+}
+
+__global__ void dir_plan_packed_kernel(const unsigned long long* packed, const GroupPlan* gp, int key_dt,
+                                       int64_t n_max, const int64_t* d_n, int64_t n_all, int log2_cells_max,
+                                       const long long* d_G, const DomPlan* dom, int eligible, DimDir* dd) {
+  if (threadIdx.x != 0) return;
+  if (dd->direct) return;
+  const int64_t nd = clamp_n(n_max, d_n);
+  const long long kmin = gp->kmin[0];
+  DimDir r = plan_cells(nd ? packed_image(packed[0], kmin, key_dt) : 1,
+                        nd ? packed_image(packed[nd - 1], kmin, key_dt) : 0, nd, n_all, log2_cells_max, d_G);
+  // the payload is each key's group rank (a bitmap-ranked group column) or
+  // there is no group column
+  const bool ranks_in_payload = dom == nullptr || dom->on;
+  r.fused = eligible && ranks_in_payload && nd > 0 && r.bshift > 0;
   *dd = r;
 }
 
-// Entries of the compact form: the key's offset within its cell and its
-// group rank above it.
-__global__ void dir_compact_kernel(const void* kr, int key_dt, int64_t n_max, const int64_t* d_n, const DimDir* dd,
-                                   uint32_t* entries) {
-  const DimDir r = *dd;
-  if (!r.compact) return;
-  const int64_t nd = clamp_n(n_max, d_n);
-  const unsigned long long mask = (1ull << r.bshift) - 1;
+struct EmitArgs {
+  const unsigned long long* packed;  // sorted packed keys
+  const int32_t* payload;            // their group ranks (when the dimension has a group column)
+  int has_group;
+  const GroupPlan* gp;               // kmin of the key column
+  int key_dt;
+  int64_t n_max;
+  const int64_t* d_n;
+  const DimDir* dd;
+  void* kr;                          // KeyRank32 / KeyRank64 per sorted position
+  int* dir;
+  uint32_t* bitmap;
+  DirCell* table;
+  StarPlan* plan;
+};
+
+__global__ void dir_emit_kernel(EmitArgs a) {
+  const DimDir r = *a.dd;
+  if (!r.fused) return;
+  const int64_t nd = clamp_n(a.n_max, a.d_n);
+  const long long kmin = a.gp->kmin[0];
+  const bool k32 = a.key_dt == TQP_I32;
+  const int cap = cell_inline(k32);
+  auto cell_at = [&](int64_t q) -> long long {
+    return (long long)((packed_image(__ldg(&a.packed[q]), kmin, a.key_dt) - r.umin) >> r.bshift);
+  };
+  auto rank_at = [&](int64_t q) -> int32_t { return a.has_group ? __ldg(&a.payload[q]) : 0; };
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nd; p += stride) {
-    unsigned long long img;
-    long long rank;
-    if (key_dt == TQP_I32) {
-      const KeyRank32 e = static_cast<const KeyRank32*>(kr)[p];
-      img = e.image;
-      rank = e.rank;
-    } else {
-      const KeyRank64 e = static_cast<const KeyRank64*>(kr)[p];
-      img = e.image;
-      rank = e.rank;
+    const unsigned long long pk = __ldg(&a.packed[p]);
+    const unsigned long long u = packed_image(pk, kmin, a.key_dt);
+    const int32_t rk = rank_at(p);
+    if (k32)
+      static_cast<KeyRank32*>(a.kr)[p] = KeyRank32{(uint32_t)u, rk};
+    else
+      static_cast<KeyRank64*>(a.kr)[p] = KeyRank64{u, (long long)rk};
+    if (p > 0 && __ldg(&a.packed[p - 1]) == pk) {
+      if (atomicExch(&a.plan->unsupported, 1) == 0) raise_status(TQP_ERR_UNSUPPORTED);
     }
-    entries[p] = (uint32_t)(((img - r.umin) & mask) | ((unsigned long long)rank << r.bshift));
+    const long long c = (long long)((u - r.umin) >> r.bshift);
+    const long long prev = p ? cell_at(p - 1) : -1;
+    if (p == nd - 1) a.dir[c + 1] = (int)nd;
+    if (c == prev) continue;
+    // the first key of cell c: the starts of the empty cells before it and
+    // of its own, its bit, and (records form) the records of those cells
+    for (long long h = prev + 1; h <= c; ++h) a.dir[h] = (int)p;
+    if (r.use_bits) atomicOr(&a.bitmap[c >> 5], 1u << (c & 31));
+    for (long long h = prev + 1; h < c; ++h) {
+      a.table[h].a = make_int4(0, 0, 0, 0);
+      a.table[h].b = make_int4(0, 0, (int)p, 0);
+    }
+    int64_t e = p + 1;
+    while (e < nd && cell_at(e) == c) ++e;
+    const int cnt = (int)(e - p);
+    uint32_t w[8] = {0, 0, 0, 0, 0, 0, (uint32_t)p, (uint32_t)cnt};
+    for (int j = 0; j < cap && j < cnt; ++j) {
+      const unsigned long long uj = j ? packed_image(__ldg(&a.packed[p + j]), kmin, a.key_dt) : u;
+      const int32_t rj = j ? rank_at(p + j) : rk;
+      if (k32) {
+        w[j] = (uint32_t)uj;
+        w[3 + j] = (uint32_t)rj;
+      } else {
+        w[2 * j] = (uint32_t)uj;
+        w[2 * j + 1] = (uint32_t)(uj >> 32);
+        w[4 + j] = (uint32_t)rj;
+      }
+    }
+    a.table[c].a = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+    a.table[c].b = make_int4((int)w[4], (int)w[5], (int)w[6], (int)w[7]);
   }
 }
+
 
 __global__ void dir_fill_kernel(const void* skeys, int key_dt, int64_t n_max, const int64_t* d_n, const DimDir* dd,
                                 int* dir, uint32_t* bitmap) {
   const int64_t nd = clamp_n(n_max, d_n);
   const DimDir r = *dd;
+  if (r.fused) return;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nd; p += stride) {
     long long c = (long long)((key_image(skeys, key_dt, p) - r.umin) >> r.bshift);
@@ -559,22 +630,9 @@ __global__ void dir_cells_kernel(CellArgs a) {
   }
 }
 
-// Wide cells (bshift > 0) get a table of one 32-byte record per cell, so
-// that a probe reads one record instead of the directory entry and then the
-// keys it points to.  The record holds the cell's first keys inline with
-// their group ranks, its first sorted position lo and its key count cnt:
-//   int32 keys: a = {img0, img1, img2, rank0}, b = {rank1, rank2, lo, cnt}
-//   int64 keys: a = {img0 (2 words), img1 (2 words)}, b = {rank0, rank1, lo, cnt}
-// A cell with more keys than fit inline keeps the rest in the sorted
-// key/rank pairs, after position lo + inline count.
-struct __align__(16) DirCell {
-  int4 a, b;
-};
-__host__ __device__ constexpr int cell_inline(bool k32) { return k32 ? 3 : 2; }
-
 __global__ void dir_table_kernel(const void* kr, int key_dt, const DimDir* dd, const int* dir, DirCell* table) {
   const DimDir r = *dd;
-  if (r.bshift == 0 || r.ncells == 0 || r.compact) return;
+  if (r.bshift == 0 || r.ncells == 0 || r.fused) return;
   const bool k32 = key_dt == TQP_I32;
   const int cap = cell_inline(k32);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -606,8 +664,6 @@ struct ProbeDim {
   const DimDir* dir_plan;
   const DirCell* table;
   const uint32_t* bitmap;
-  const int* dir;            // compact form: first sorted position of each cell
-  const uint32_t* entries;   // compact form: (cell offset, rank) per sorted key
 };
 
 struct ProbeArgs {
@@ -681,20 +737,6 @@ __device__ __forceinline__ void ring_flush(WarpRing<F>& q, Drain&& drain) {
   drain(e, cnt);
 }
 
-// Loads of data the probe reads once (fact columns, random records):
-// streaming (evict first) so that they do not displace re-read tables.
-#ifndef TQP_PROBE_STREAM_LOADS
-#define TQP_PROBE_STREAM_LOADS 1
-#endif
-template <typename T>
-__device__ __forceinline__ T ld_once(const T* p) {
-#if TQP_PROBE_STREAM_LOADS
-  return __ldcs(p);
-#else
-  return __ldg(p);
-#endif
-}
-
 // Fused probe + aggregate as a warp pipeline with dense stages.
 //  1. Each thread takes ITEMS fact rows of the tile.  Without fact predicates
 //     they go straight to the dimension probe.  With predicates, the passing
@@ -758,15 +800,12 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   }
   DimDir dd[ND];
   long long stride[ND];
-  bool unit[ND], cpt[ND];
-  uint32_t cmask[ND];  // compact form: a key's offset bits within its cell
+  bool unit[ND];
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     dd[d] = *a.dim[d].dir_plan;
     stride[d] = plan->stride[d];
     unit[d] = dd[d].bshift == 0;
-    cpt[d] = dd[d].compact != 0;
-    cmask[d] = dd[d].bshift >= 32 ? 0xFFFFFFFFu : (1u << dd[d].bshift) - 1u;
   }
   extern __shared__ uint32_t s_bm[];
   bool sbm = false;
@@ -820,12 +859,10 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   // a unit-width dimension); slot: the sum of rank * stride over the wide
   // dimensions (a unit cell's rank is read by the fold, on compacted rows).
   // pre: the first dimension's key image u0 is already loaded.
-  // fact columns are read once: streaming loads, so that they do not evict
-  // the dimension tables that stay in L2
   auto fk_image = [&](int d, int64_t row) -> UK {
     const ProbeDim& D = a.dim[d];
-    if (K32 || D.key_dt == TQP_I32) return (UK)((uint32_t)ld_once(static_cast<const int32_t*>(D.fk) + row) ^ 0x80000000u);
-    return (UK)((unsigned long long)ld_once(static_cast<const long long*>(D.fk) + row) ^ 0x8000000000000000ull);
+    if (K32 || D.key_dt == TQP_I32) return (UK)((uint32_t)__ldg(static_cast<const int32_t*>(D.fk) + row) ^ 0x80000000u);
+    return (UK)((unsigned long long)__ldg(static_cast<const long long*>(D.fk) + row) ^ 0x8000000000000000ull);
   };
   // The keys of a wide cell beyond its inline ones: the first key >= x in
   // kr[l, h), narrowed while the interval is long, then scanned.
@@ -878,15 +915,8 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
       ra[d] = rb[d] = make_int4(0, 0, 0, 0);
       rk[d] = 0;
       if (lv[d] && !unit[d]) {
-        if (cpt[d]) {
-          // compact form: the cell's range of sorted positions (L2 hits)
-          ra[d].x = __ldg(&a.dim[d].dir[c[d]]);
-          ra[d].y = __ldg(&a.dim[d].dir[c[d] + 1]);
-        } else {
-          // a random record, read once: streaming, like the fact columns
-          ra[d] = ld_once(&a.dim[d].table[c[d]].a);
-          rb[d] = ld_once(&a.dim[d].table[c[d]].b);
-        }
+        ra[d] = __ldg(&a.dim[d].table[c[d]].a);
+        rb[d] = __ldg(&a.dim[d].table[c[d]].b);
       }
     }
     bool all = live;
@@ -894,25 +924,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
       pos[d] = (int)c[d];
-      if (!unit[d] && cpt[d]) {
-        // compact form: the cell's entries ascend by key; the first whose
-        // offset reaches the key's decides
-        const uint32_t off = (uint32_t)(u[d] - (UK)dd[d].umin) & cmask[d];
-        int found = -1;
-        if (lv[d])
-          for (int i = ra[d].x; i < ra[d].y; ++i) {
-            const uint32_t e = __ldg(&a.dim[d].entries[i]);
-            const uint32_t eo = e & cmask[d];
-            if (eo < off) continue;
-            if (eo == off) {
-              found = i;
-              rk[d] = dd[d].bshift >= 32 ? 0 : (int)(e >> dd[d].bshift);
-            }
-            break;
-          }
-        lv[d] = lv[d] && found >= 0;
-        pos[d] = found;
-      } else if (!unit[d]) {
+      if (!unit[d]) {
         // match the inline keys; a key above the last inline one of a fuller
         // cell is searched among the cell's remaining sorted keys
         const int lo = rb[d].z, cnt = rb[d].w;
@@ -945,8 +957,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
   // in its group's slot
   auto term_value = [&](int vi, int row, const int (&pos)[ND]) -> long long {
     const int src = s_vsrc[vi];
-    if (src == 0) return TQP_PROBE_STREAM_LOADS ? load_as_i64_stream(s_vptr[vi], s_vdt[vi], row)
-                                                : load_as_i64(s_vptr[vi], s_vdt[vi], row);
+    if (src == 0) return load_as_i64(s_vptr[vi], s_vdt[vi], row);
     const bool cell = src == 1 ? unit[0] : unit[ND - 1];
     return static_cast<const long long*>(cell ? s_vptr_cell[vi] : s_vptr[vi])[src == 1 ? pos[0] : pos[ND - 1]];
   };
@@ -964,8 +975,8 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
       if (op != TQP_COUNT && simple) {
         const int ai = s_ai[q];
         const int idx = ai == 0 ? row : ai == 1 ? pos[0] : pos[ND - 1];
-        const long long v = ai == 0 ? ld_once(s_ap[q] + idx) : __ldg(s_ap[q] + idx);
-        x = (long long)((unsigned long long)s_am[q] * (unsigned long long)v + (unsigned long long)s_aa[q]);
+        x = (long long)((unsigned long long)s_am[q] * (unsigned long long)__ldg(s_ap[q] + idx) +
+                        (unsigned long long)s_aa[q]);
       } else if (op != TQP_COUNT) {
         const int e = A.expr[q];
         unsigned long long ev = 1;
@@ -1051,7 +1062,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
     auto load4 = [&](int64_t w, int j, UK (&dst)[ITEMS]) {
       const int64_t r = w * WT + (int64_t)lane * ITEMS + 4 * j;
       if (w < nwt && r + 3 < a.n_fact) {
-        const int4 q = ld_once(reinterpret_cast<const int4*>(fk0 + r));
+        const int4 q = __ldg(reinterpret_cast<const int4*>(fk0 + r));
         dst[4 * j] = (UK)((uint32_t)q.x ^ 0x80000000u);
         dst[4 * j + 1] = (UK)((uint32_t)q.y ^ 0x80000000u);
         dst[4 * j + 2] = (UK)((uint32_t)q.z ^ 0x80000000u);
@@ -1059,7 +1070,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
       } else {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          dst[4 * j + e] = (w < nwt && r + e < a.n_fact) ? (UK)((uint32_t)ld_once(fk0 + r + e) ^ 0x80000000u) : (UK)0;
+          dst[4 * j + e] = (w < nwt && r + e < a.n_fact) ? (UK)((uint32_t)__ldg(fk0 + r + e) ^ 0x80000000u) : (UK)0;
       }
     };
     UK nxt[ITEMS];
@@ -1136,9 +1147,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(Pr
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k)
           if ((pass >> k) & 1u)
-            if (!compare(TQP_PROBE_STREAM_LOADS ? load_as_i64_stream(a.pcol[p], a.pdt[p], wt * WT + k * 32 + lane)
-                                                : load_as_i64(a.pcol[p], a.pdt[p], wt * WT + k * 32 + lane),
-                         a.pop[p], a.plit[p]))
+            if (!compare(load_as_i64(a.pcol[p], a.pdt[p], wt * WT + k * 32 + lane), a.pop[p], a.plit[p]))
               pass &= ~(1u << k);
       }
       // one rolled loop, so that the probe and the fold behind the queue

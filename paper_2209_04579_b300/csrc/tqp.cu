@@ -962,7 +962,7 @@ LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int ro
   w.thr = c.take<unsigned>((size_t)B);
   w.dir = c.take<int>((1 << kDirBits) + 1);
   w.count = c.take<unsigned>((size_t)B);
-  w.cursor = c.take<unsigned>((size_t)B);
+  w.cursor = c.take<unsigned>((size_t)B * kCursorStride);
   w.bcount = c.take<unsigned>(B <= kBlockHistMaxB ? (size_t)w.nblk * B : 1);
   w.off = c.take<unsigned>((size_t)B + 1);
   w.light_n = c.take<int64_t>(1);
@@ -1160,7 +1160,9 @@ tqp_status run_sort_learned(const LearnedWs& w, int key_dt, const void* keys_in,
   std::memset(&none, 0, sizeof(none));
   tqp_status st = run_learned_partition(w, ks, nullptr, vals_in, n, d_n, cfg, false, none, nullptr, s);
   if (st != TQP_OK) return st;
-  lp_decode_kernel<<<stride_grid(n, 256), 256, 0, s>>>(w.lpk, w.gp, key_dt, n, w.light_n, keys_out); note_launch();
+  if (keys_out) {
+    lp_decode_kernel<<<stride_grid(n, 256), 256, 0, s>>>(w.lpk, w.gp, key_dt, n, w.light_n, keys_out); note_launch();
+  }
   return TQP_OK;
 }
 }  // namespace
@@ -1360,7 +1362,6 @@ struct StarDimWs {
   uint32_t* bitmap;
   int log2cells;
   DirCell* table;
-  uint32_t* entries;           // compact form: one 32-bit entry per sorted key
   int32_t* rank_cell;
   long long* dval_cell[TQP_MAX_VALS];
 };
@@ -1512,7 +1513,6 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       while (t < w.log2cells && (1ll << t) < 2 * D.n) ++t;
       w.table = c.take<DirCell>((size_t)(1ll << t) + 1);
     }
-    w.entries = c.take<uint32_t>(nn);
     w.rank_cell = c.take<int32_t>((size_t)(1ll << w.log2cells) + 1);
     for (int v = 0; v < nvals; ++v)
       if (vals[v].src == d + 1) w.dval_cell[v] = c.take<long long>((size_t)(1ll << w.log2cells) + 1);
@@ -1647,9 +1647,24 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       dim_direct_plan_kernel<<<1, 32, 0, s>>>(w.krange, D.n, dcnt, w.log2cells, w.dplan, w.ksort_n); note_launch();
       kn = w.ksort_n;
     }
-    const tqp_status st = w.learned ? run_sort_learned(w.lws, D.key.dtype, kin, vin, w.skeys, D.n, kn, lcfg, s)
-                              : run_sort(w.ksort, D.key.dtype, kin, vin, w.skeys, w.srows, D.n, kn, 0, eb * 8, s);
-    if (st != TQP_OK) return st;
+    // no value of this dimension aggregated: the fused directory pass may
+    // build it straight from the learned sort's packed keys and ranks
+    bool dim_vals = false;
+    for (int v = 0; v < nvals; ++v) dim_vals = dim_vals || vals[v].src == d + 1;
+    tqp_status st;
+    if (w.learned) {
+      // the packed keys sorted (skeys only decoded when the fused pass does not run)
+      st = run_sort_learned(w.lws, D.key.dtype, kin, vin, nullptr, D.n, kn, lcfg, s);
+      if (st != TQP_OK) return st;
+      dir_plan_packed_kernel<<<1, 32, 0, s>>>(w.lws.lpk, w.lws.gp, D.key.dtype, D.n, kn, D.n, w.log2cells,
+                                              D.group.data ? w.G : nullptr, D.group.data ? w.dom : nullptr,
+                                              dim_vals ? 0 : 1, w.dplan); note_launch();
+      lp_decode_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(w.lws.lpk, w.lws.gp, D.key.dtype, D.n, kn, w.skeys,
+                                                               &w.dplan->fused); note_launch();
+    } else {
+      st = run_sort(w.ksort, D.key.dtype, kin, vin, w.skeys, w.srows, D.n, kn, 0, eb * 8, s);
+      if (st != TQP_OK) return st;
+    }
     prof_mark(12 + d, false, s);
     prof_mark(14 + d, true, s);
     if (D.n > 0) {
@@ -1672,6 +1687,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       pg.rank_sorted = w.rank_sorted;
       pg.kr = w.kr;
       pg.plan = plan;
+      pg.dd = w.dplan;
       for (int v = 0; v < nvals; ++v) {
         if (vals[v].src != d + 1) continue;
         pg.vcol[pg.nv] = D.cols[vals[v].col].data;
@@ -1685,6 +1701,23 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
                                      D.group.data ? w.G : nullptr, w.dplan); note_launch();
     if (D.n > 0) {
       TQP_CUDA(cudaMemsetAsync(w.bitmap, 0, ((size_t)(1ll << w.log2cells) / 32 + 1) * sizeof(uint32_t), s));
+      if (w.learned) {
+        EmitArgs ea;
+        ea.packed = w.lws.lpk;
+        ea.payload = w.srows;
+        ea.has_group = D.group.data ? 1 : 0;
+        ea.gp = w.lws.gp;
+        ea.key_dt = D.key.dtype;
+        ea.n_max = D.n;
+        ea.d_n = kn;
+        ea.dd = w.dplan;
+        ea.kr = w.kr;
+        ea.dir = w.dir;
+        ea.bitmap = w.bitmap;
+        ea.table = w.table;
+        ea.plan = plan;
+        dir_emit_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(ea); note_launch();
+      }
       dir_fill_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(w.skeys, D.key.dtype, D.n, kn, w.dplan, w.dir,
                                                              w.bitmap);
       note_launch();
@@ -1710,8 +1743,6 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
         dir_table_kernel<<<stride_grid((1ll << t) + 1, 256), 256, 0, s>>>(w.kr, D.key.dtype, w.dplan, w.dir, w.table);
         note_launch();
       }
-      dir_compact_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(w.kr, D.key.dtype, D.n, kn, w.dplan, w.entries);
-      note_launch();
       DirectArgs da;
       std::memset(&da, 0, sizeof(da));
       da.keys = kin;
@@ -1760,8 +1791,6 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     pa.dim[d].dir_plan = W[d].dplan;
     pa.dim[d].table = W[d].table;
     pa.dim[d].bitmap = W[d].bitmap;
-    pa.dim[d].dir = W[d].dir;
-    pa.dim[d].entries = W[d].entries;
   }
   pa.npred = nfact_preds;
   for (int p = 0; p < nfact_preds; ++p) {
