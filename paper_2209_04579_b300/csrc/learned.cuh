@@ -993,6 +993,238 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
   }
 }
 
+// ---- two-level scatter (no heavy keys): the rows reach their buckets in
+// two splits, each a block-level multisplit of tiles of kSplitTile rows.
+// Split 1 bins a tile by the coarse bucket (the bucket's top bits: at most
+// 256 coarse buckets), split 2 bins a tile of one coarse bucket by the
+// bucket itself.  A tile's rows are ranked per bin in shared memory, each
+// non-empty bin reserves its run with one global atomic, and the tile is
+// written out bin by bin from shared memory, so the rows leave in runs.
+// One atomic per (tile, bin) replaces the returning per-row atomic of
+// lp_scatter_kernel, whose latency bounded it.
+constexpr int kSplitThreads = 512, kSplitItems = 8, kSplitTile = kSplitThreads * kSplitItems;
+constexpr int kSplitMaxBins = 512;
+constexpr int kSplitCoarseBits = 8;
+// The bucket function's steps in shared memory when they fit (one block per
+// SM), else read from global memory (several blocks per SM).
+#ifndef TQP_SPLIT_THR_SHARED
+#define TQP_SPLIT_THR_SHARED 1
+#endif
+constexpr bool kSplitThrShared = TQP_SPLIT_THR_SHARED != 0;
+
+__host__ __device__ inline int split_fine_bits(int B) {  // log2(fine buckets per coarse bucket)
+  int lb = 0;
+  while ((1 << lb) < B) ++lb;
+  return lb > kSplitCoarseBits ? lb - kSplitCoarseBits : 0;
+}
+
+inline __host__ __device__ size_t split_smem_bytes(int B, bool thr_smem) {
+  size_t o = ((((size_t)1 << kDirBits) + 1) * 4 + 15) & ~(size_t)15;
+  if (thr_smem) o += (((size_t)(B > 1 ? B - 1 : 1) * 4) + 15) & ~(size_t)15;
+  return o + (size_t)kSplitTile * (8 + 4 + 2);
+}
+
+struct SplitSmem {
+  int* dir;
+  unsigned* thr;
+  unsigned long long* key;
+  int32_t* row;
+  unsigned short* bin;
+};
+
+__device__ __forceinline__ SplitSmem split_carve(unsigned char* base, int B, bool thr_smem) {
+  SplitSmem S;
+  size_t o = ((((size_t)1 << kDirBits) + 1) * 4 + 15) & ~(size_t)15;
+  S.dir = reinterpret_cast<int*>(base);
+  S.thr = reinterpret_cast<unsigned*>(base + o);
+  if (thr_smem) o += (((size_t)(B > 1 ? B - 1 : 1) * 4) + 15) & ~(size_t)15;
+  S.key = reinterpret_cast<unsigned long long*>(base + o);
+  o += (size_t)kSplitTile * 8;
+  S.row = reinterpret_cast<int32_t*>(base + o);
+  o += (size_t)kSplitTile * 4;
+  S.bin = reinterpret_cast<unsigned short*>(base + o);
+  return S;
+}
+
+template <bool THR_SMEM>
+__device__ __forceinline__ void split_setup(const PartArgs& a, const LearnedPlan& lp, const SplitSmem& S) {
+  for (int i = threadIdx.x; i <= (1 << kDirBits); i += blockDim.x) S.dir[i] = a.dir[i];
+  if (THR_SMEM)
+    for (int i = threadIdx.x; i < lp.B - 1; i += blockDim.x) S.thr[i] = a.thr[i];
+}
+
+struct SplitBins {
+  unsigned hist[kSplitMaxBins];   // counts, ranked into by atomics
+  unsigned start[kSplitMaxBins];  // the tile's bin starts
+  unsigned base[kSplitMaxBins];   // the bins' global run starts
+  int scan[33];
+};
+
+// The tile's rows (per thread: packed key, payload, bin or -1, rank in its
+// bin) are counted in B.hist: reserve each bin's run at cur[(first + bin) *
+// kCursorStride], stage the rows in bin order, write them out.
+__device__ __forceinline__ void split_place(const unsigned long long (&p)[kSplitItems], const int32_t (&r)[kSplitItems],
+                                            const int (&bin)[kSplitItems], const unsigned (&rk)[kSplitItems],
+                                            int nbins, int first, unsigned* cur, SplitBins& B, const SplitSmem& S,
+                                            unsigned long long* out_p, int32_t* out_row) {
+  __syncthreads();
+  const unsigned cnt = threadIdx.x < nbins ? B.hist[threadIdx.x] : 0u;
+  int total;
+  const int st = block_exclusive_sum<kSplitThreads>((int)cnt, B.scan, &total);
+  if (threadIdx.x < nbins) {
+    B.start[threadIdx.x] = (unsigned)st;
+    if (cnt) B.base[threadIdx.x] = atomicAdd(&cur[(size_t)(first + threadIdx.x) * kCursorStride], cnt);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kSplitItems; ++k)
+    if (bin[k] >= 0) {
+      const unsigned slot = B.start[bin[k]] + rk[k];
+      S.key[slot] = p[k];
+      S.row[slot] = r[k];
+      S.bin[slot] = (unsigned short)bin[k];
+    }
+  __syncthreads();
+  for (int j = threadIdx.x; j < total; j += kSplitThreads) {
+    const int b = S.bin[j];
+    const unsigned dst = B.base[b] + ((unsigned)j - B.start[b]);
+    out_p[dst] = S.key[j];
+    out_row[dst] = S.row[j];
+  }
+  __syncthreads();
+}
+
+// Split 1: the (selected) rows by coarse bucket (bucket >> F) into
+// (out_p, out_row), coarse cursors in cur.
+template <bool THR_SMEM>
+__global__ void __launch_bounds__(kSplitThreads, 1) lp_split1_kernel(PartArgs a, int F, unsigned* cur,
+                                                                     unsigned long long* out_p, int32_t* out_row) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ PackPlan K;
+  __shared__ SplitBins SB;
+  const LearnedPlan lp = *a.lp;
+  const SplitSmem S = split_carve(smem, lp.B, THR_SMEM);
+  split_setup<THR_SMEM>(a, lp, S);
+  if (threadIdx.x == 0) {
+    K.nkeys = a.ks.nkeys;
+    for (int k = 0; k < TQP_MAX_KEYS; ++k) {
+      K.col[k] = a.ks.col[k];
+      K.dt[k] = a.ks.dt[k];
+      K.kmin[k] = a.gp->kmin[k];
+      K.shift[k] = a.gp->shift[k];
+    }
+  }
+  __syncthreads();
+  const unsigned* thr = THR_SMEM ? S.thr : a.thr;
+  const int nbins = lp.B >> F;
+  const int64_t n = clamp_n(a.n_max, a.d_n);
+  for (int64_t base = (int64_t)blockIdx.x * kSplitTile; base < n; base += (int64_t)gridDim.x * kSplitTile) {
+    for (int i = threadIdx.x; i < nbins; i += kSplitThreads) SB.hist[i] = 0;
+    __syncthreads();
+    unsigned long long p[kSplitItems];
+    int32_t r[kSplitItems];
+    int bin[kSplitItems];
+    unsigned rk[kSplitItems];
+#pragma unroll
+    for (int k = 0; k < kSplitItems; ++k) {
+      const int64_t i = base + k * kSplitThreads + threadIdx.x;
+      bin[k] = -1;
+      p[k] = 0;
+      r[k] = 0;
+      rk[k] = 0;
+      if (i < n) {
+        const int64_t row = a.sel ? (int64_t)a.sel[i] : i;
+        p[k] = pack_row_plan(K, row);
+        r[k] = a.payload ? a.payload[i] : (int32_t)row;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kSplitItems; ++k)
+      if (base + k * kSplitThreads + threadIdx.x < n) {
+        bin[k] = lp_bucket<THR_SMEM>(p[k], lp, S.dir, thr) >> F;
+        rk[k] = atomicAdd(&SB.hist[bin[k]], 1u);
+      }
+    split_place(p, r, bin, rk, nbins, 0, cur, SB, S, out_p, out_row);
+  }
+}
+
+// Tile starts of split 2 (one block of 256 threads): coarse bucket c has
+// ceil(rows / kSplitTile) tiles, starting at tstart[c]; tstart[C] = all.
+// Also the coarse cursors of split 1, at the coarse buckets' first rows.
+__global__ void __launch_bounds__(256) lp_split_tiles_kernel(const unsigned* off, const LearnedPlan* lp, int F,
+                                                             unsigned* tstart, unsigned* cur1) {
+  __shared__ int s_scan[33];
+  const int C = lp->B >> F;
+  const int c = threadIdx.x;
+  unsigned nt = 0;
+  if (c < C) {
+    nt = (off[(c + 1) << F] - off[c << F] + kSplitTile - 1) / kSplitTile;
+    cur1[(size_t)c * kCursorStride] = off[c << F];
+  }
+  int total;
+  const int ex = block_exclusive_sum<256>((int)nt, s_scan, &total);
+  if (c < C) tstart[c] = (unsigned)ex;
+  if (c == 0) tstart[C] = (unsigned)total;
+}
+
+// Split 2: each tile holds rows of one coarse bucket c; they go to their
+// buckets (c << F) + bin, through the buckets' cursors.
+template <bool THR_SMEM>
+__global__ void __launch_bounds__(kSplitThreads, 1) lp_split2_kernel(PartArgs a, int F, const unsigned* off,
+                                                                     const unsigned* tstart,
+                                                                     const unsigned long long* in_p,
+                                                                     const int32_t* in_row, unsigned* cursor,
+                                                                     unsigned long long* out_p, int32_t* out_row) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ SplitBins SB;
+  __shared__ unsigned s_tstart[(1 << kSplitCoarseBits) + 1];
+  const LearnedPlan lp = *a.lp;
+  const SplitSmem S = split_carve(smem, lp.B, THR_SMEM);
+  split_setup<THR_SMEM>(a, lp, S);
+  const int C = lp.B >> F;
+  for (int i = threadIdx.x; i <= C; i += kSplitThreads) s_tstart[i] = tstart[i];
+  __syncthreads();
+  const unsigned* thr = THR_SMEM ? S.thr : a.thr;
+  const int nbins = 1 << F;
+  const unsigned ntiles = s_tstart[C];
+  for (unsigned t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // the coarse bucket of tile t: the last c with tstart[c] <= t
+    int lo = 0, hi = C;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_tstart[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int c = lo;
+    const int64_t row0 = (int64_t)off[c << F] + (int64_t)(t - s_tstart[c]) * kSplitTile;
+    const int64_t row1 = off[(c + 1) << F];
+    for (int i = threadIdx.x; i < nbins; i += kSplitThreads) SB.hist[i] = 0;
+    __syncthreads();
+    unsigned long long p[kSplitItems];
+    int32_t r[kSplitItems];
+    int bin[kSplitItems];
+    unsigned rk[kSplitItems];
+#pragma unroll
+    for (int k = 0; k < kSplitItems; ++k) {
+      const int64_t i = row0 + k * kSplitThreads + threadIdx.x;
+      bin[k] = -1;
+      p[k] = 0;
+      r[k] = 0;
+      rk[k] = 0;
+      if (i < row1) {
+        p[k] = in_p[i];
+        r[k] = in_row[i];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kSplitItems; ++k)
+      if (row0 + k * kSplitThreads + threadIdx.x < row1) {
+        bin[k] = lp_bucket<THR_SMEM>(p[k], lp, S.dir, thr) - (c << F);
+        rk[k] = atomicAdd(&SB.hist[bin[k]], 1u);
+      }
+    split_place(p, r, bin, rk, nbins, c << F, cursor, SB, S, out_p, out_row);
+  }
+}
+
 // Sorted packed keys back to the key column's dtype (one key column,
 // packed as key - kmin).  skip: a device flag that, when set, says the
 // decoded keys are not needed.

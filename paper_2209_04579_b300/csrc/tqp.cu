@@ -916,6 +916,8 @@ struct LearnedWs {
   int32_t* arow;
   uint32_t* queue;
   uint32_t* big_flags;
+  unsigned* tstart;  // two-level scatter: split 2's tile starts per coarse bucket
+  unsigned* cur1;    // two-level scatter: coarse cursors
   uint32_t* rheads;
   Partial* rcarry;
   void* lgath[TQP_MAX_VALS];
@@ -974,6 +976,8 @@ LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int ro
   }
   w.queue = c.take<uint32_t>(2);
   w.big_flags = c.take<uint32_t>((size_t)B);
+  w.tstart = c.take<unsigned>((1 << kSplitCoarseBits) + 1);
+  w.cur1 = c.take<unsigned>((size_t)(1 << kSplitCoarseBits) * kCursorStride);
   if (P) {  // the group-by's reduce
     w.rtiles = (n + kReduceThreads * kReduceItems - 1) / (kReduceThreads * kReduceItems);
     w.rheads = c.take<uint32_t>((size_t)(w.rtiles > 0 ? w.rtiles : 1));
@@ -1094,8 +1098,35 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
       lp_heavy_init_kernel<<<(kMaxHeavy * naggs + 255) / 256, 256, 0, s>>>(w.lp, P, w.heavy_acc); note_launch();
     }
     prof_mark(8, true, s);
-    sk<<<persistent_grid(sk, kPartThreads, ssm, ptiles), kPartThreads, ssm, s>>>(pa, P); note_launch();
-    TQP_LAUNCHED();
+    if (want_heavy) {
+      sk<<<persistent_grid(sk, kPartThreads, ssm, ptiles), kPartThreads, ssm, s>>>(pa, P); note_launch();
+      TQP_LAUNCHED();
+    } else {
+      // no heavy keys: the two-level scatter (block-level multisplits)
+      const int F = split_fine_bits(B);
+      const bool tsm = kSplitThrShared && split_smem_bytes(B, true) + 8192 <= (size_t)kMaxSmemOptin;
+      const size_t xsm = split_smem_bytes(B, tsm);
+      auto k1 = tsm ? lp_split1_kernel<true> : lp_split1_kernel<false>;
+      auto k2 = tsm ? lp_split2_kernel<true> : lp_split2_kernel<false>;
+      TQP_CUDA(smem_optin(k1, (int)xsm));
+      TQP_CUDA(smem_optin(k2, (int)xsm));
+      lp_split_tiles_kernel<<<1, 256, 0, s>>>(w.off, w.lp, F, w.tstart, w.cur1); note_launch();
+      const int64_t tiles1 = (n + kSplitTile - 1) / kSplitTile;
+      if (F == 0) {  // at most 256 buckets: one split, straight into the buckets
+        k1<<<persistent_grid(k1, kSplitThreads, xsm, tiles1), kSplitThreads, xsm, s>>>(pa, 0, w.cursor, w.lpk, w.lrow);
+        note_launch();
+        TQP_LAUNCHED();
+      } else {
+        k1<<<persistent_grid(k1, kSplitThreads, xsm, tiles1), kSplitThreads, xsm, s>>>(pa, F, w.cur1, w.apk, w.arow);
+        note_launch();
+        TQP_LAUNCHED();
+        const int64_t tiles2 = tiles1 + (B >> F) + 1;
+        k2<<<persistent_grid(k2, kSplitThreads, xsm, tiles2), kSplitThreads, xsm, s>>>(pa, F, w.off, w.tstart, w.apk,
+                                                                                          w.arow, w.cursor, w.lpk, w.lrow);
+        note_launch();
+        TQP_LAUNCHED();
+      }
+    }
     prof_mark(8, false, s);
   }
   // 6. every bucket sorted: on-chip up to the capacity, else by one block in global memory
@@ -1793,6 +1824,9 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     pa.dim[d].bitmap = W[d].bitmap;
   }
   pa.npred = nfact_preds;
+  // the first predicate column can be bulk-copied tile by tile (16-byte aligned, at most 4 bytes a row)
+  pa.pf0 = nfact_preds > 0 && dtype_bytes(fact_cols[fact_preds[0].col].dtype) <= 4 &&
+           reinterpret_cast<uintptr_t>(fact_cols[fact_preds[0].col].data) % 16 == 0;
   for (int p = 0; p < nfact_preds; ++p) {
     pa.pcol[p] = fact_cols[fact_preds[p].col].data;
     pa.pdt[p] = fact_cols[fact_preds[p].col].dtype;
