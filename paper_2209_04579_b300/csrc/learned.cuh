@@ -1018,10 +1018,12 @@ __host__ __device__ inline int split_fine_bits(int B) {  // log2(fine buckets pe
   return lb > kSplitCoarseBits ? lb - kSplitCoarseBits : 0;
 }
 
-inline __host__ __device__ size_t split_smem_bytes(int B, bool thr_smem) {
-  size_t o = ((((size_t)1 << kDirBits) + 1) * 4 + 15) & ~(size_t)15;
-  if (thr_smem) o += (((size_t)(B > 1 ? B - 1 : 1) * 4) + 15) & ~(size_t)15;
-  return o + (size_t)kSplitTile * (8 + 4 + 2);
+// Split 1: directory, steps (thr_smem), staged keys, rows, bins and fine
+// ids.  Split 2 needs only the staging (dir_thr = false).
+inline __host__ __device__ size_t split_smem_bytes(int B, bool thr_smem, bool dir_thr = true) {
+  size_t o = dir_thr ? ((((size_t)1 << kDirBits) + 1) * 4 + 15) & ~(size_t)15 : 0;
+  if (dir_thr && thr_smem) o += (((size_t)(B > 1 ? B - 1 : 1) * 4) + 15) & ~(size_t)15;
+  return o + (size_t)kSplitTile * (8 + 4 + 2 + 2);
 }
 
 struct SplitSmem {
@@ -1030,19 +1032,22 @@ struct SplitSmem {
   unsigned long long* key;
   int32_t* row;
   unsigned short* bin;
+  unsigned short* fine;  // split 1: each row's bucket within its coarse bucket
 };
 
-__device__ __forceinline__ SplitSmem split_carve(unsigned char* base, int B, bool thr_smem) {
+__device__ __forceinline__ SplitSmem split_carve(unsigned char* base, int B, bool thr_smem, bool dir_thr = true) {
   SplitSmem S;
-  size_t o = ((((size_t)1 << kDirBits) + 1) * 4 + 15) & ~(size_t)15;
+  size_t o = dir_thr ? ((((size_t)1 << kDirBits) + 1) * 4 + 15) & ~(size_t)15 : 0;
   S.dir = reinterpret_cast<int*>(base);
   S.thr = reinterpret_cast<unsigned*>(base + o);
-  if (thr_smem) o += (((size_t)(B > 1 ? B - 1 : 1) * 4) + 15) & ~(size_t)15;
+  if (dir_thr && thr_smem) o += (((size_t)(B > 1 ? B - 1 : 1) * 4) + 15) & ~(size_t)15;
   S.key = reinterpret_cast<unsigned long long*>(base + o);
   o += (size_t)kSplitTile * 8;
   S.row = reinterpret_cast<int32_t*>(base + o);
   o += (size_t)kSplitTile * 4;
   S.bin = reinterpret_cast<unsigned short*>(base + o);
+  o += (size_t)kSplitTile * 2;
+  S.fine = reinterpret_cast<unsigned short*>(base + o);
   return S;
 }
 
@@ -1066,7 +1071,8 @@ struct SplitBins {
 __device__ __forceinline__ void split_place(const unsigned long long (&p)[kSplitItems], const int32_t (&r)[kSplitItems],
                                             const int (&bin)[kSplitItems], const unsigned (&rk)[kSplitItems],
                                             int nbins, int first, unsigned* cur, SplitBins& B, const SplitSmem& S,
-                                            unsigned long long* out_p, int32_t* out_row) {
+                                            unsigned long long* out_p, int32_t* out_row,
+                                            const int* fine = nullptr, unsigned short* out_fine = nullptr) {
   __syncthreads();
   const unsigned cnt = threadIdx.x < nbins ? B.hist[threadIdx.x] : 0u;
   int total;
@@ -1083,6 +1089,7 @@ __device__ __forceinline__ void split_place(const unsigned long long (&p)[kSplit
       S.key[slot] = p[k];
       S.row[slot] = r[k];
       S.bin[slot] = (unsigned short)bin[k];
+      if (out_fine) S.fine[slot] = (unsigned short)fine[k];
     }
   __syncthreads();
   for (int j = threadIdx.x; j < total; j += kSplitThreads) {
@@ -1090,6 +1097,7 @@ __device__ __forceinline__ void split_place(const unsigned long long (&p)[kSplit
     const unsigned dst = B.base[b] + ((unsigned)j - B.start[b]);
     out_p[dst] = S.key[j];
     out_row[dst] = S.row[j];
+    if (out_fine) out_fine[dst] = S.fine[j];
   }
   __syncthreads();
 }
@@ -1098,7 +1106,8 @@ __device__ __forceinline__ void split_place(const unsigned long long (&p)[kSplit
 // (out_p, out_row), coarse cursors in cur.
 template <bool THR_SMEM>
 __global__ void __launch_bounds__(kSplitThreads, 1) lp_split1_kernel(PartArgs a, int F, unsigned* cur,
-                                                                     unsigned long long* out_p, int32_t* out_row) {
+                                                                     unsigned long long* out_p, int32_t* out_row,
+                                                                     unsigned short* out_fine) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PackPlan K;
   __shared__ SplitBins SB;
@@ -1123,12 +1132,13 @@ __global__ void __launch_bounds__(kSplitThreads, 1) lp_split1_kernel(PartArgs a,
     __syncthreads();
     unsigned long long p[kSplitItems];
     int32_t r[kSplitItems];
-    int bin[kSplitItems];
+    int bin[kSplitItems], fine[kSplitItems];
     unsigned rk[kSplitItems];
 #pragma unroll
     for (int k = 0; k < kSplitItems; ++k) {
       const int64_t i = base + k * kSplitThreads + threadIdx.x;
       bin[k] = -1;
+      fine[k] = 0;
       p[k] = 0;
       r[k] = 0;
       rk[k] = 0;
@@ -1141,10 +1151,12 @@ __global__ void __launch_bounds__(kSplitThreads, 1) lp_split1_kernel(PartArgs a,
 #pragma unroll
     for (int k = 0; k < kSplitItems; ++k)
       if (base + k * kSplitThreads + threadIdx.x < n) {
-        bin[k] = lp_bucket<THR_SMEM>(p[k], lp, S.dir, thr) >> F;
+        const int b = lp_bucket<THR_SMEM>(p[k], lp, S.dir, thr);
+        bin[k] = b >> F;
+        fine[k] = b & ((1 << F) - 1);
         rk[k] = atomicAdd(&SB.hist[bin[k]], 1u);
       }
-    split_place(p, r, bin, rk, nbins, 0, cur, SB, S, out_p, out_row);
+    split_place(p, r, bin, rk, nbins, 0, cur, SB, S, out_p, out_row, fine, out_fine);
   }
 }
 
@@ -1168,23 +1180,23 @@ __global__ void __launch_bounds__(256) lp_split_tiles_kernel(const unsigned* off
 }
 
 // Split 2: each tile holds rows of one coarse bucket c; they go to their
-// buckets (c << F) + bin, through the buckets' cursors.
-template <bool THR_SMEM>
-__global__ void __launch_bounds__(kSplitThreads, 1) lp_split2_kernel(PartArgs a, int F, const unsigned* off,
+// buckets (c << F) + fine id (the id split 1 computed), through the
+// buckets' cursors.  No bucket function here: shared memory holds only the
+// staging, so several blocks share an SM.
+__global__ void __launch_bounds__(kSplitThreads, 2) lp_split2_kernel(const LearnedPlan* lpp, int F, const unsigned* off,
                                                                      const unsigned* tstart,
                                                                      const unsigned long long* in_p,
-                                                                     const int32_t* in_row, unsigned* cursor,
+                                                                     const int32_t* in_row,
+                                                                     const unsigned short* in_fine, unsigned* cursor,
                                                                      unsigned long long* out_p, int32_t* out_row) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SplitBins SB;
   __shared__ unsigned s_tstart[(1 << kSplitCoarseBits) + 1];
-  const LearnedPlan lp = *a.lp;
-  const SplitSmem S = split_carve(smem, lp.B, THR_SMEM);
-  split_setup<THR_SMEM>(a, lp, S);
-  const int C = lp.B >> F;
+  const int Bk = lpp->B;
+  const SplitSmem S = split_carve(smem, Bk, false, false);
+  const int C = Bk >> F;
   for (int i = threadIdx.x; i <= C; i += kSplitThreads) s_tstart[i] = tstart[i];
   __syncthreads();
-  const unsigned* thr = THR_SMEM ? S.thr : a.thr;
   const int nbins = 1 << F;
   const unsigned ntiles = s_tstart[C];
   for (unsigned t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -1213,14 +1225,12 @@ __global__ void __launch_bounds__(kSplitThreads, 1) lp_split2_kernel(PartArgs a,
       if (i < row1) {
         p[k] = in_p[i];
         r[k] = in_row[i];
+        bin[k] = in_fine[i];
       }
     }
 #pragma unroll
     for (int k = 0; k < kSplitItems; ++k)
-      if (row0 + k * kSplitThreads + threadIdx.x < row1) {
-        bin[k] = lp_bucket<THR_SMEM>(p[k], lp, S.dir, thr) - (c << F);
-        rk[k] = atomicAdd(&SB.hist[bin[k]], 1u);
-      }
+      if (bin[k] >= 0) rk[k] = atomicAdd(&SB.hist[bin[k]], 1u);
     split_place(p, r, bin, rk, nbins, c << F, cursor, SB, S, out_p, out_row);
   }
 }

@@ -668,7 +668,6 @@ struct ProbeDim {
 
 struct ProbeArgs {
   unsigned* wcounter;  // warp tiles taken (predicate path)
-  int pf0;             // the first predicate column is 1, 2 or 4 bytes a row and 16-byte aligned
   int ndims;
   int vec0;  // the first dimension's fact keys are int32 at a 16-byte aligned address
   ProbeDim dim[kMaxDims];
@@ -756,35 +755,15 @@ __device__ __forceinline__ void ring_flush(WarpRing<F>& q, Drain&& drain) {
 // read; used for small first dimensions, one large block per SM.
 // K32: every dimension key is int32, so the key image, its range test and
 // the cell index are 32-bit arithmetic.
-#ifndef TQP_PROBE_PRELOAD
-#define TQP_PROBE_PRELOAD 3
-#endif
-#ifndef TQP_PROBE_MIN_BLOCKS
-#define TQP_PROBE_MIN_BLOCKS 3
-#endif
-constexpr int kProbePreload = TQP_PROBE_PRELOAD;  // fact values preloaded per probed row (at most)
 template <int THREADS, int ITEMS, bool SMEM_BM, bool K32, int ND>
-__global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : TQP_PROBE_MIN_BLOCKS)
-    star_probe_kernel(ProbeArgs a, StarAcc Ag, int smem_bm_words) {
+__global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : 3) star_probe_kernel(ProbeArgs a, StarAcc Ag, int smem_bm_words) {
   using UK = typename std::conditional<K32, uint32_t, unsigned long long>::type;
   constexpr int WARPS = THREADS / 32;
   // the shared bitmap variant keeps a smaller accumulator array
   constexpr int ACC_WORDS = SMEM_BM ? kSmemAccWords / 4 : kSmemAccWords;
   __shared__ long long s_acc[ACC_WORDS];
-  // PRE: fact values of the simple program loaded when a batch of rows
-  // enters the probe, with the foreign keys, and carried through the queue,
-  // so that the fold issues no load of its own (the variant with a shared
-  // bitmap keeps its shared memory for the bitmap)
-  constexpr int PRE = SMEM_BM ? 0 : kProbePreload;
-  constexpr int FQ = 2 + ND + 2 * PRE;
-  __shared__ int s_fring[WARPS][FQ * 64];  // probe survivors: row, slot, positions, preloaded values
+  __shared__ int s_fring[WARPS][(2 + ND) * 64];  // probe survivors: row, slot, positions
   __shared__ int s_pring[WARPS][64];                   // rows that pass the fact predicates
-  // predicate path: each warp's next tile of the first predicate column (up
-  // to 4 bytes a row), brought in by a TMA bulk copy; two buffers per warp
-  constexpr bool PF = !SMEM_BM;
-  constexpr int WTR = 32 * ITEMS;
-  __shared__ __align__(16) uint32_t s_pbuf[PF ? WARPS : 1][2][PF ? WTR : 4];
-  __shared__ __align__(8) unsigned long long s_pbar[PF ? WARPS : 1][2];
   // the aggregate program and value references in shared memory: they are
   // indexed by runtime values below (kernel parameters indexed that way are
   // copied to local memory)
@@ -844,9 +823,6 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : TQP_PROBE_MIN_BLOCKS)
   __shared__ const long long* s_ap[TQP_MAX_AGGS];
   __shared__ int s_ai[TQP_MAX_AGGS];  // value index: 0 the row, 1 the first dimension's position, 2 the last's
   __shared__ long long s_am[TQP_MAX_AGGS], s_aa[TQP_MAX_AGGS];
-  __shared__ int s_pre[TQP_MAX_AGGS];       // preloaded value slot of each aggregate, or -1
-  __shared__ const long long* s_prep[PRE > 0 ? PRE : 1];
-  __shared__ int s_npre;
   if (threadIdx.x == 0) {
     int simple = 1;
     for (int q = 0; q < A.naggs; ++q) {
@@ -872,21 +848,9 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : TQP_PROBE_MIN_BLOCKS)
       s_aa[q] = A.tadd[e][0];
     }
     s_simple = simple;
-    // fact-valued aggregates of the simple program, preloaded on the
-    // predicate path (up to PRE of them)
-    int np = 0;
-    for (int q = 0; q < A.naggs; ++q) {
-      s_pre[q] = -1;
-      if (simple && A.op[q] != TQP_COUNT && s_ai[q] == 0 && np < PRE && a.npred > 0) {
-        s_pre[q] = np;
-        s_prep[np++] = s_ap[q];
-      }
-    }
-    s_npre = np;
   }
   __syncthreads();
   const bool simple = s_simple;
-  const int npre = s_npre;
 
   // 2. probe of one fact row through every dimension.  The dimensions'
   // foreign keys load together, then their wide cells' records (after the
@@ -997,7 +961,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : TQP_PROBE_MIN_BLOCKS)
     const bool cell = src == 1 ? unit[0] : unit[ND - 1];
     return static_cast<const long long*>(cell ? s_vptr_cell[vi] : s_vptr[vi])[src == 1 ? pos[0] : pos[ND - 1]];
   };
-  auto fold = [&](bool v, int row, int slot, const int (&pos)[ND], const long long (&pv)[PRE > 0 ? PRE : 1]) {
+  auto fold = [&](bool v, int row, int slot, const int (&pos)[ND]) {
     if (!v) return;
     int urk[ND];
 #pragma unroll
@@ -1011,16 +975,8 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : TQP_PROBE_MIN_BLOCKS)
       if (op != TQP_COUNT && simple) {
         const int ai = s_ai[q];
         const int idx = ai == 0 ? row : ai == 1 ? pos[0] : pos[ND - 1];
-        long long val = 0;
-        const int j = PRE > 0 ? s_pre[q] : -1;
-        if (PRE > 0 && j >= 0) {
-#pragma unroll
-          for (int t = 0; t < (PRE > 0 ? PRE : 1); ++t)
-            if (t == j) val = pv[t];
-        } else {
-          val = __ldg(s_ap[q] + idx);
-        }
-        x = (long long)((unsigned long long)s_am[q] * (unsigned long long)val + (unsigned long long)s_aa[q]);
+        x = (long long)((unsigned long long)s_am[q] * (unsigned long long)__ldg(s_ap[q] + idx) +
+                        (unsigned long long)s_aa[q]);
       } else if (op != TQP_COUNT) {
         const int e = A.expr[q];
         unsigned long long ev = 1;
@@ -1046,56 +1002,39 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : TQP_PROBE_MIN_BLOCKS)
     }
   };
 
-  WarpRing<FQ> fq;  // rows that found every dimension: row, slot, positions, preloaded values
+  WarpRing<2 + ND> fq;  // rows that found every dimension: row, slot, positions
   fq.base = s_fring[threadIdx.x >> 5];
   fq.head = fq.n = 0;
   WarpRing<1> pq;  // rows that pass the fact predicates
   pq.base = s_pring[threadIdx.x >> 5];
   pq.head = pq.n = 0;
-  using PreVals = long long[PRE > 0 ? PRE : 1];
-  auto drain_fold = [&](const int (&e)[FQ], int cnt) {
+  auto drain_fold = [&](const int (&e)[2 + ND], int cnt) {
     int pos[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) pos[d] = e[2 + d];
-    PreVals pv;
-#pragma unroll
-    for (int t = 0; t < (PRE > 0 ? PRE : 1); ++t)
-      pv[t] = PRE > 0 ? (long long)(((unsigned long long)(uint32_t)e[2 + ND + 2 * t + 1] << 32) |
-                                    (unsigned long long)(uint32_t)e[2 + ND + 2 * t])
-                      : 0;
-    fold(lane < cnt, e[0], e[1], pos, pv);
+    fold(lane < cnt, e[0], e[1], pos);
   };
-  auto push_survivor = [&](bool alive, int row, int slot, const int (&pos)[ND], const PreVals& pv) {
-    int val[FQ];
+  auto push_survivor = [&](bool alive, int row, int slot, const int (&pos)[ND]) {
+    int val[2 + ND];
     val[0] = row;
     val[1] = slot;
 #pragma unroll
     for (int d = 0; d < ND; ++d) val[2 + d] = pos[d];
-#pragma unroll
-    for (int t = 0; t < PRE; ++t) {
-      val[2 + ND + 2 * t] = (int)(uint32_t)(unsigned long long)pv[t];
-      val[2 + ND + 2 * t + 1] = (int)(uint32_t)((unsigned long long)pv[t] >> 32);
-    }
     ring_push(fq, alive, val, drain_fold);
   };
   auto drain_probe = [&](const int (&e)[1], int cnt) {
-    // the batch's fact values load with its foreign keys (one round trip)
-    PreVals pv;
-#pragma unroll
-    for (int t = 0; t < (PRE > 0 ? PRE : 1); ++t) pv[t] = (t < npre && lane < cnt) ? __ldg(s_prep[t] + e[0]) : 0;
     int pos[ND], slot;
     const bool alive = probe(lane < cnt, e[0], pos, slot, false, (UK)0);
-    push_survivor(alive, e[0], slot, pos, pv);
+    push_survivor(alive, e[0], slot, pos);
   };
   // Pushes a tile's ITEMS probed rows (row0 + k * rstep) in a rolled loop:
   // the fold behind the queue then exists once in the loop's code (the
   // instruction cache holds the whole loop).  Each step takes item 0 and
   // shifts the rest down, so the arrays stay in registers.
   auto push_items = [&](bool (&alive)[ITEMS], int (&slot)[ITEMS], int (&pos)[ITEMS][ND], int row0, int rstep) {
-    const PreVals none = {};
 #pragma unroll 1
     for (int k = 0; k < ITEMS; ++k) {
-      push_survivor(alive[0], row0 + k * rstep, slot[0], pos[0], none);
+      push_survivor(alive[0], row0 + k * rstep, slot[0], pos[0]);
 #pragma unroll
       for (int j = 0; j + 1 < ITEMS; ++j) {
         alive[j] = alive[j + 1];
@@ -1192,70 +1131,19 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : TQP_PROBE_MIN_BLOCKS)
     }
   } else {
     // fact predicates, then the passing rows into the probe queue.  Warp
-    // tiles are taken from a counter (a tile's cost varies with the
-    // dependent reads of its surviving rows), claimed one tile ahead.  With
-    // pf0, the next tile's first predicate column is copied into this
-    // warp's shared buffer by a TMA bulk copy (one lane issues it,
-    // completion on an mbarrier) while the current tile is probed, so the
-    // predicate's loads leave the tile's critical path.
-    const int wid = PF ? (threadIdx.x >> 5) : 0;
-    unsigned long long* bar = s_pbar[wid];
-    const bool pf = PF && a.pf0;
-    const unsigned cbytes = pf ? (unsigned)(WTR * dtype_bytes(a.pdt[0])) : 0u;
-    if (pf) {
-      if (lane == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init_fence();
+    // tiles are taken from a counter: a tile's cost varies with the
+    // dependent reads of its surviving rows.
+    while (true) {
+      {
+        unsigned tk = 0;
+        if (lane == 0) tk = atomicAdd(a.wcounter, 1u);
+        wt = __shfl_sync(0xffffffffu, tk, 0);
       }
-      __syncwarp();
-    }
-    unsigned parity = 0;  // bit b: the phase to wait for on buffer b
-    bool pf_ok = pf;
-    int stuck = -1;       // a buffer whose copy did not complete in the bounded wait
-    auto claim = [&]() -> int64_t {
-      unsigned tk = 0;
-      if (lane == 0) tk = atomicAdd(a.wcounter, 1u);
-      return (int64_t)__shfl_sync(0xffffffffu, tk, 0);
-    };
-    auto whole = [&](int64_t t) { return t < nwt && (t + 1) * WT <= a.n_fact; };
-    auto issue = [&](int64_t t, int b) {
-      if (lane == 0) {
-        fence_proxy_async_smem();  // this buffer's earlier reads before the copy refills it
-        mbar_arrive_expect_tx(&bar[b], cbytes);
-        bulk_copy_g2s(s_pbuf[wid][b], static_cast<const char*>(a.pcol[0]) + (size_t)t * cbytes, cbytes, &bar[b]);
-      }
-    };
-    int64_t t = claim();
-    int cb = 0;
-    bool cur_pf = pf_ok && whole(t);
-    if (cur_pf) issue(t, 0);
-    while (t < nwt) {
-      const int64_t tn = claim();
-      const bool nxt_pf = pf_ok && whole(tn);
-      if (nxt_pf) issue(tn, cb ^ 1);
-      wt = t;
+      if (wt >= nwt) break;
       unsigned pass = 0;  // bit k: row k * 32 + lane of the tile
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) pass |= (unsigned)(wt * WT + k * 32 + lane < a.n_fact) << k;
-      int p0 = 0;
-      if (cur_pf) {
-        const bool ok = mbar_wait_bounded(&bar[cb], (parity >> cb) & 1u);
-        parity ^= 1u << cb;
-        if (ok) {
-#pragma unroll
-          for (int k = 0; k < ITEMS; ++k)
-            if ((pass >> k) & 1u)
-              if (!compare(load_as_i64(s_pbuf[wid][cb], a.pdt[0], k * 32 + lane), a.pop[0], a.plit[0]))
-                pass &= ~(1u << k);
-          p0 = 1;
-        } else {  // the copy did not arrive: record it, read the column directly from now on
-          if (lane == 0) raise_status(TQP_ERR_TIMEOUT);
-          pf_ok = false;
-          stuck = cb;
-        }
-      }
-      for (int p = p0; p < a.npred; ++p) {
+      for (int p = 0; p < a.npred; ++p) {
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k)
           if ((pass >> k) & 1u)
@@ -1269,14 +1157,7 @@ __global__ void __launch_bounds__(THREADS, SMEM_BM ? 1 : TQP_PROBE_MIN_BLOCKS)
         const int val[1] = {(int)(wt * WT + k * 32 + lane)};
         ring_push(pq, (pass >> k) & 1u, val, drain_probe);
       }
-      __syncwarp();  // every lane is done with buffer cb before a copy refills it
-      t = tn;
-      cb ^= 1;
-      cur_pf = nxt_pf;
     }
-    // a copy that missed its wait must land before the block's shared memory
-    // goes away (bounded as well)
-    if (stuck >= 0) mbar_wait_bounded(&bar[stuck], (parity >> stuck) & 1u ^ 1u);
   }
   // the partly filled queues: probe what is pending, then fold the rest
   ring_flush(pq, drain_probe);

@@ -918,6 +918,7 @@ struct LearnedWs {
   uint32_t* big_flags;
   unsigned* tstart;  // two-level scatter: split 2's tile starts per coarse bucket
   unsigned* cur1;    // two-level scatter: coarse cursors
+  unsigned short* fine;  // two-level scatter: each row's bucket within its coarse bucket
   uint32_t* rheads;
   Partial* rcarry;
   void* lgath[TQP_MAX_VALS];
@@ -977,6 +978,7 @@ LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int ro
   w.queue = c.take<uint32_t>(2);
   w.big_flags = c.take<uint32_t>((size_t)B);
   w.tstart = c.take<unsigned>((1 << kSplitCoarseBits) + 1);
+  if (scatter) w.fine = c.take<unsigned short>(nn);
   w.cur1 = c.take<unsigned>((size_t)(1 << kSplitCoarseBits) * kCursorStride);
   if (P) {  // the group-by's reduce
     w.rtiles = (n + kReduceThreads * kReduceItems - 1) / (kReduceThreads * kReduceItems);
@@ -1106,23 +1108,27 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
       const int F = split_fine_bits(B);
       const bool tsm = kSplitThrShared && split_smem_bytes(B, true) + 8192 <= (size_t)kMaxSmemOptin;
       const size_t xsm = split_smem_bytes(B, tsm);
+      const size_t xsm2 = split_smem_bytes(B, false, false);
       auto k1 = tsm ? lp_split1_kernel<true> : lp_split1_kernel<false>;
-      auto k2 = tsm ? lp_split2_kernel<true> : lp_split2_kernel<false>;
+      auto k2 = lp_split2_kernel;
       TQP_CUDA(smem_optin(k1, (int)xsm));
-      TQP_CUDA(smem_optin(k2, (int)xsm));
+      TQP_CUDA(smem_optin(k2, (int)xsm2));
       lp_split_tiles_kernel<<<1, 256, 0, s>>>(w.off, w.lp, F, w.tstart, w.cur1); note_launch();
       const int64_t tiles1 = (n + kSplitTile - 1) / kSplitTile;
       if (F == 0) {  // at most 256 buckets: one split, straight into the buckets
-        k1<<<persistent_grid(k1, kSplitThreads, xsm, tiles1), kSplitThreads, xsm, s>>>(pa, 0, w.cursor, w.lpk, w.lrow);
+        k1<<<persistent_grid(k1, kSplitThreads, xsm, tiles1), kSplitThreads, xsm, s>>>(pa, 0, w.cursor, w.lpk, w.lrow,
+                                                                                       nullptr);
         note_launch();
         TQP_LAUNCHED();
       } else {
-        k1<<<persistent_grid(k1, kSplitThreads, xsm, tiles1), kSplitThreads, xsm, s>>>(pa, F, w.cur1, w.apk, w.arow);
+        k1<<<persistent_grid(k1, kSplitThreads, xsm, tiles1), kSplitThreads, xsm, s>>>(pa, F, w.cur1, w.apk, w.arow,
+                                                                                       w.fine);
         note_launch();
         TQP_LAUNCHED();
         const int64_t tiles2 = tiles1 + (B >> F) + 1;
-        k2<<<persistent_grid(k2, kSplitThreads, xsm, tiles2), kSplitThreads, xsm, s>>>(pa, F, w.off, w.tstart, w.apk,
-                                                                                          w.arow, w.cursor, w.lpk, w.lrow);
+        k2<<<persistent_grid(k2, kSplitThreads, xsm2, tiles2), kSplitThreads, xsm2, s>>>(w.lp, F, w.off, w.tstart, w.apk,
+                                                                                            w.arow, w.fine, w.cursor, w.lpk,
+                                                                                            w.lrow);
         note_launch();
         TQP_LAUNCHED();
       }
@@ -1824,9 +1830,6 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     pa.dim[d].bitmap = W[d].bitmap;
   }
   pa.npred = nfact_preds;
-  // the first predicate column can be bulk-copied tile by tile (16-byte aligned, at most 4 bytes a row)
-  pa.pf0 = nfact_preds > 0 && dtype_bytes(fact_cols[fact_preds[0].col].dtype) <= 4 &&
-           reinterpret_cast<uintptr_t>(fact_cols[fact_preds[0].col].data) % 16 == 0;
   for (int p = 0; p < nfact_preds; ++p) {
     pa.pcol[p] = fact_cols[fact_preds[p].col].data;
     pa.pdt[p] = fact_cols[fact_preds[p].col].dtype;
