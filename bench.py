@@ -194,11 +194,14 @@ class Skew:
         return tqp.learned_cfg(sample=65536, buckets=buckets, tcfg=tqp.train_cfg(epochs=40, lr=1e-5))
 
     def tune(self):
-        """Bucket count from the autotuner (outputs sized to the group count)."""
+        """Bucket count from the autotuner (outputs sized to the group count),
+        and the radix sort's tile for 64-bit keys (the plain path's sort)."""
         from paper_2209_04579_b300 import autotune
         from paper_2209_04579_b300 import queries as Q
         self.buckets, self.tune_info = autotune.tune_learned(
             lambda b: Q.skew_learned(self.t, cap=self.cap, cfg=self.cfg(b)), self.n)
+        items, info = autotune.tune_sort(self.t["key"][: 1 << 24])
+        self.tune_info = {"learned_buckets": self.tune_info, "sort_tile_64bit": info}
 
     def step(self):
         from paper_2209_04579_b300 import queries as Q
@@ -375,14 +378,31 @@ class Star:
         return list(self.fact.values()) + list(self.d1.values()) + list(self.d2.values())
 
     variant = "learned"
+    buckets = 0  # learned bucket count of the dimension sorts (0: from each dimension's size)
+
+    def lcfg(self, buckets, train=True):
+        from paper_2209_04579_b300 import tqp
+        if not train:
+            return tqp.learned_cfg(sample=65536, buckets=buckets, train=False, init=1)
+        return tqp.learned_cfg(sample=65536, buckets=buckets, tcfg=tqp.train_cfg(epochs=10, lr=1e-5))
+
+    def tune(self):
+        """The learned bucket count (candidates give identical groups), and
+        the radix sort's tiles for the plain path's 32- and 64-bit keys."""
+        from paper_2209_04579_b300 import autotune
+        from paper_2209_04579_b300 import queries as Q
+        self.buckets, info = autotune.tune_learned(
+            lambda b: Q.star(self.fact, self.d1, self.d2, learned=self.lcfg(b)), self.n2,
+            candidates=[0, 16384, 32768, 65536], op="star_learned")
+        _, s64 = autotune.tune_sort(self.d2["key"][: 1 << 24])
+        _, s32 = autotune.tune_sort(self.d1["key"][: 1 << 24])
+        self.tune_info = {"learned_buckets": info, "sort_tile_64bit": s64, "sort_tile_32bit": s32}
 
     def step(self):
         from paper_2209_04579_b300 import queries as Q
-        from paper_2209_04579_b300 import tqp
         if self.variant == "plain":
             return Q.star(self.fact, self.d1, self.d2)
-        return Q.star(self.fact, self.d1, self.d2,
-                      learned=tqp.learned_cfg(sample=65536, tcfg=tqp.train_cfg(epochs=10, lr=1e-5)))
+        return Q.star(self.fact, self.d1, self.d2, learned=self.lcfg(self.buckets))
 
     def plain_step(self):
         from paper_2209_04579_b300 import queries as Q
@@ -391,8 +411,7 @@ class Star:
     def serving_step(self):
         """The learned form without training: quantile-knot networks, no Adam epochs."""
         from paper_2209_04579_b300 import queries as Q
-        from paper_2209_04579_b300 import tqp
-        return Q.star(self.fact, self.d1, self.d2, learned=tqp.learned_cfg(sample=65536, train=False, init=1))
+        return Q.star(self.fact, self.d1, self.d2, learned=self.lcfg(self.buckets, train=False))
 
     def rows(self):
         return self.n
@@ -417,11 +436,10 @@ class Star:
                 (7, "lp_bucket_sort_kernel (dim2)", n2 * 12 * 2)]
 
     def traffic(self):
-        # ncu DRAM bytes (read + write) of one probe launch on the quarter-size
-        # case, scaled by the rows processed: fact rows, dimension rows and
-        # survivors all scale together, and so does the traffic
-        return ("star_probe_kernel", int((17_004_073_000 + 3_809_536) * 4 / self.scale),
-                "profiles/star_probe_star_join_150M_quarter_scale.md (x4 rows)")
+        # ncu DRAM bytes (read + write) of one full-size probe launch; a scaled
+        # case scales its fact rows, dimension rows and survivors together
+        return ("star_probe_kernel", int((72_420_000_000 + 3_610_000) / self.scale),
+                "profiles/star_probe_star_join_600M_traffic.md" + ("" if self.scale == 1 else f" (/{self.scale})"))
 
     def oracle_sample(self, rows):
         from oracle import pipelines as pl

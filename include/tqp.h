@@ -549,6 +549,13 @@ tqp_status tqp_star_agg_batched(const tqp_batch_shape* shape, const tqp_problem*
  * bounded waits run out; -1 disables it.
  * ---------------------------------------------------------------------- */
 tqp_status tqp_status_poll(tqp_stream_t stream);
+/* tqp_sort_tiles: rows per thread of the radix sort's tiles (of 256
+ * threads), process-wide, for 32-bit keys (8, 12 or 16; default 16) and
+ * 64-bit keys (6, 8 or 12; default 12); 0 leaves a width unchanged.  Any
+ * choice sorts identically; it only changes speed (the autotuner's knob).
+ * A call's workspace is sized with the setting at its size query, so change
+ * it between calls, not between a call's size query and the call. */
+tqp_status tqp_sort_tiles(int items32, int items64);
 tqp_status tqp_debug_set_spin_limit(int64_t rounds);
 tqp_status tqp_debug_inject_unpublished_tile(int64_t tile);
 const char* tqp_status_string(tqp_status s);

@@ -8,7 +8,14 @@ $TQP_AUTOTUNE_CACHE, else ~/.cache/tqp/autotune.json.
 
 Tuned parameters:
   batched  -- fact rows per thread of the batched probe tile (4, 8, 16);
-  learned  -- number of learned buckets B (about n/512 .. n/4096, powers of two).
+  learned  -- number of learned buckets B (about n/512 .. n/4096, powers of two),
+              for the learned group-by and, through the same search with its
+              own candidates, for the star join's learned dimension sorts;
+  sort     -- rows per thread of the radix sort's tiles, per key width
+              (8, 12, 16 for 32-bit keys; 6, 8, 12 for 64-bit keys), set
+              process-wide with tqp_sort_tiles.
+The radix digit is 8 bits by construction (one thread per digit value in
+each pass), so the digit width is not a tuned parameter.
 """
 from __future__ import annotations
 
@@ -92,11 +99,12 @@ def tune_batched(problems, shape, cap=64, candidates=(4, 8, 16), force=False):
     return best, cache[k]
 
 
-def tune_learned(run, rows, candidates=None, force=False):
-    """Best bucket count for the learned group-by.  run(B) performs one call
-    and returns its outputs (for the identity check)."""
+def tune_learned(run, rows, candidates=None, force=False, op="learned"):
+    """Best bucket count for the learned group-by (op names the call for
+    the cache).  run(B) performs one call and returns its outputs (for the
+    identity check)."""
     cache = _load()
-    k = _key("learned", rows)
+    k = _key(op, rows)
     if not force and k in cache:
         return int(cache[k]["best"]), cache[k]
     if candidates is None:
@@ -118,4 +126,31 @@ def tune_learned(run, rows, candidates=None, force=False):
     best = min(times, key=times.get)
     cache[k] = {"best": best, "ms": {str(b): t for b, t in times.items()}}
     _store(cache)
+    return best, cache[k]
+
+
+def tune_sort(keys, vals=None, force=False):
+    """Best sort tile for keys of this width (a representative input of the
+    sorts to come), set with tqp_sort_tiles; every candidate must sort
+    identically."""
+    wide = keys.element_size() > 4
+    cands = (6, 8, 12) if wide else (8, 12, 16)
+    cache = _load()
+    k = _key("sort64" if wide else "sort32", keys.numel())
+    if not force and k in cache:
+        best = int(cache[k]["best"])
+    else:
+        times, ref = {}, None
+        for c in cands:
+            tqp.tqp_sort_tiles(0, c) if wide else tqp.tqp_sort_tiles(c, 0)
+            times[c] = _time(lambda: tqp.tqp_sort_pairs(keys, vals))
+            fp = _fingerprint([tqp.tqp_sort_pairs(keys, vals)])
+            if ref is None:
+                ref = fp
+            elif fp != ref:
+                raise RuntimeError(f"sort results differ between tile choices ({c})")
+        best = min(times, key=times.get)
+        cache[k] = {"best": best, "ms": {str(c): t for c, t in times.items()}}
+        _store(cache)
+    tqp.tqp_sort_tiles(0, best) if wide else tqp.tqp_sort_tiles(best, 0)
     return best, cache[k]

@@ -117,6 +117,28 @@ __global__ void gb_init_kernel(GroupPlan* plan) {
   }
 }
 
+// Minimum and maximum of one column of T over rows i = first + j * stride,
+// eight rows a thread in flight (independent loads issued together).
+template <typename T>
+__device__ __forceinline__ void column_range(const T* col, int64_t n, int64_t first, int64_t stride, long long* mn,
+                                             long long* mx) {
+  constexpr int U = 8;
+  for (int64_t base = first; base < n; base += stride * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * stride;
+      v[u] = i < n ? __ldg(col + i) : __ldg(col + base);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long x = (long long)v[u];
+      *mn = x < *mn ? x : *mn;
+      *mx = x > *mx ? x : *mx;
+    }
+  }
+}
+
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS) gb_keyrange_kernel(KeySet ks, const int32_t* sel, int64_t n_max,
                                                               const int64_t* d_n, GroupPlan* plan) {
@@ -126,7 +148,17 @@ __global__ void __launch_bounds__(THREADS) gb_keyrange_kernel(KeySet ks, const i
 #pragma unroll
   for (int k = 0; k < TQP_MAX_KEYS; ++k) { mn[k] = LLONG_MAX; mx[k] = LLONG_MIN; }
   const int64_t stride = (int64_t)gridDim.x * THREADS;
-  for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < n; i += stride) {
+  const int64_t first = (int64_t)blockIdx.x * THREADS + threadIdx.x;
+  if (ks.nkeys == 1 && sel == nullptr) {
+    // one column over every row: typed loads, several in flight
+    switch (ks.dt[0]) {
+      case TQP_I8: column_range(static_cast<const signed char*>(ks.col[0]), n, first, stride, &mn[0], &mx[0]); break;
+      case TQP_I16: column_range(static_cast<const short*>(ks.col[0]), n, first, stride, &mn[0], &mx[0]); break;
+      case TQP_I32: column_range(static_cast<const int*>(ks.col[0]), n, first, stride, &mn[0], &mx[0]); break;
+      default: column_range(static_cast<const long long*>(ks.col[0]), n, first, stride, &mn[0], &mx[0]); break;
+    }
+  }
+  for (int64_t i = first; i < n && !(ks.nkeys == 1 && sel == nullptr); i += stride) {
     int64_t row = sel ? sel[i] : i;
 #pragma unroll
     for (int k = 0; k < TQP_MAX_KEYS; ++k) {

@@ -28,7 +28,10 @@ constexpr int kMaxHeavy = TQP_MAX_HEAVY;
 constexpr int kDirBits = 12;      // directory over the top bits of q
 constexpr int kLocalCap = 8192;   // rows a block sorts on-chip
 constexpr int kWarpCap = 1024;    // rows one warp sorts on-chip
-constexpr int kLocalThreads = 512;
+#ifndef TQP_LOCAL_THREADS
+#define TQP_LOCAL_THREADS 512
+#endif
+constexpr int kLocalThreads = TQP_LOCAL_THREADS;
 constexpr int kLocalWarps = kLocalThreads / 32;
 constexpr int kLocalItems = kLocalCap / kLocalThreads;  // 16
 // Bucket cursors of the scatter sit this many words apart (32: one per
@@ -563,6 +566,7 @@ struct PartArgs {
   unsigned long long* out_p;
   int32_t* out_row;
   long long* heavy_acc;     // [nheavy][naggs]
+  unsigned short* ids;      // the counting pass's bucket of every row (no heavy keys, B <= 65536), or null
 };
 
 // ---- partition kernels: shared-memory layout and setup
@@ -715,6 +719,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_hist_kernel(PartArgs a) {
       const int b = lp_bucket<MODE >= kThrShared>(p[k], lp, S.dir, thr);
       if (MODE == kBlockHist) atomicAdd(&S.bh[b], 1u);
       else atomicAdd(&a.count[b], 1u);
+      if (a.ids) a.ids[base + k * kPartThreads + threadIdx.x] = (unsigned short)b;
     }
   }
   if (MODE == kBlockHist) {
@@ -1104,16 +1109,18 @@ __device__ __forceinline__ void split_place(const unsigned long long (&p)[kSplit
 
 // Split 1: the (selected) rows by coarse bucket (bucket >> F) into
 // (out_p, out_row), coarse cursors in cur.
-template <bool THR_SMEM>
-__global__ void __launch_bounds__(kSplitThreads, 1) lp_split1_kernel(PartArgs a, int F, unsigned* cur,
+// IDS: the bucket comes from the counting pass (a.ids), so no bucket
+// function is evaluated and shared memory holds only the staging.
+template <bool THR_SMEM, bool IDS>
+__global__ void __launch_bounds__(kSplitThreads, IDS ? 2 : 1) lp_split1_kernel(PartArgs a, int F, unsigned* cur,
                                                                      unsigned long long* out_p, int32_t* out_row,
                                                                      unsigned short* out_fine) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PackPlan K;
   __shared__ SplitBins SB;
   const LearnedPlan lp = *a.lp;
-  const SplitSmem S = split_carve(smem, lp.B, THR_SMEM);
-  split_setup<THR_SMEM>(a, lp, S);
+  const SplitSmem S = split_carve(smem, lp.B, THR_SMEM, !IDS);
+  if (!IDS) split_setup<THR_SMEM>(a, lp, S);
   if (threadIdx.x == 0) {
     K.nkeys = a.ks.nkeys;
     for (int k = 0; k < TQP_MAX_KEYS; ++k) {
@@ -1151,7 +1158,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) lp_split1_kernel(PartArgs a,
 #pragma unroll
     for (int k = 0; k < kSplitItems; ++k)
       if (base + k * kSplitThreads + threadIdx.x < n) {
-        const int b = lp_bucket<THR_SMEM>(p[k], lp, S.dir, thr);
+        const int b = IDS ? (int)a.ids[base + k * kSplitThreads + threadIdx.x] : lp_bucket<THR_SMEM>(p[k], lp, S.dir, thr);
         bin[k] = b >> F;
         fine[k] = b & ((1 << F) - 1);
         rk[k] = atomicAdd(&SB.hist[bin[k]], 1u);
@@ -1412,7 +1419,10 @@ __device__ void lsd_shared(unsigned long long* kX, int32_t* rX, unsigned long lo
 // places the rows by those bits (block-wide counters: equal keys need no
 // order) and every part is insertion-sorted by one thread; otherwise
 // (repeated or clustered keys) the block's LSD sorts the whole bucket.
-constexpr int kMsdBits = 11;
+#ifndef TQP_MSD_BITS
+#define TQP_MSD_BITS 12
+#endif
+constexpr int kMsdBits = TQP_MSD_BITS;
 constexpr int kMsdBins = 1 << kMsdBits;
 constexpr int kSmallPart = 32;
 

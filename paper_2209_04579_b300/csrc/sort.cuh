@@ -158,6 +158,33 @@ __global__ void __launch_bounds__(kRadix) sort_plan_kernel(SortArgs a) {
 constexpr uint32_t kSFlagAgg = 1u << 30, kSFlagPrefix = 2u << 30, kSFlagFailed = 3u << 30;
 constexpr uint32_t kSFlagMask = 3u << 30, kSValMask = ~kSFlagMask;
 
+// The ranks of a warp's keys by digit (stable: ordered by item, then lane).
+// match_digit9 separates the padding rows of a partial tile (digit kRadix);
+// a full tile needs only the 8 digit bits.
+__device__ __forceinline__ unsigned match_digit8(unsigned v) {
+  unsigned peers = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (v >> b) & 1u;
+    const unsigned bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
+// Order-preserving image of a word of K's own width: keys of a signed dtype
+// of that width flip their sign bit, unsigned words stay as they are.
+template <typename K>
+__device__ __forceinline__ K sign_flip_of(int dt) {
+  if (sizeof(K) == 4) return dt == TQP_I32 ? (K)0x80000000u : (K)0;
+  return dt == TQP_I64 ? (K)0x8000000000000000ull : (K)0;
+}
+
+template <typename K>
+__host__ __device__ __forceinline__ bool word_dtype(int dt) {
+  return sizeof(K) == 4 ? (dt == TQP_I32 || dt == kKeyU32) : (dt == TQP_I64 || dt == kKeyU64);
+}
+
 template <typename K, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS, 3) sort_pass_kernel(SortArgs a, int pass, uint32_t num_tiles) {
   static_assert(THREADS == kRadix, "one thread per digit");
@@ -168,14 +195,14 @@ __global__ void __launch_bounds__(THREADS, 3) sort_pass_kernel(SortArgs a, int p
 
   __shared__ uint32_t s_wcnt[WARPS][kRadix + 1];  // per-warp digit counters (+1 bin for padding rows)
   __shared__ uint32_t s_tile_start[kRadix];
-  __shared__ int64_t s_gbase[kRadix];
+  __shared__ long long s_gofs[kRadix];  // global position of the digit's first staged slot, minus that slot
   __shared__ int s_scan[33];
   __shared__ uint32_t s_tile;
   __shared__ int s_failed;
   __shared__ uint8_t s_dig[TILE];  // digit of every staged slot
-  extern __shared__ __align__(16) unsigned char s_raw[];  // TILE keys, reused for values
+  extern __shared__ __align__(16) unsigned char s_raw[];  // TILE keys, then TILE values
   K* s_keys = reinterpret_cast<K*>(s_raw);
-  int32_t* s_vals = reinterpret_cast<int32_t*>(s_raw);
+  int32_t* s_vals = reinterpret_cast<int32_t*>(s_raw + (size_t)TILE * sizeof(K));
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = clamp_n(a.n_max, a.d_n);
@@ -186,6 +213,14 @@ __global__ void __launch_bounds__(THREADS, 3) sort_pass_kernel(SortArgs a, int p
   void* kout = pd.dst == 0 ? a.keys_out : (pd.dst == 1 ? a.alt_keys[0] : a.alt_keys[1]);
   int32_t* vout = pd.dst == 0 ? a.vals_out : (pd.dst == 1 ? a.alt_vals[0] : a.alt_vals[1]);
   const int kout_dt = pd.last ? a.key_dt : (sizeof(K) == 4 ? kKeyU32 : kKeyU64);
+  // words of K's width load and store as K (an image that is a sign flip);
+  // narrower dtypes (first or last pass only) go through encode/decode
+  const bool word_in = word_dtype<K>(kin_dt), word_out = word_dtype<K>(kout_dt);
+  const K flip_in = sign_flip_of<K>(kin_dt), flip_out = sign_flip_of<K>(kout_dt);
+  const bool row_vals = pd.first && vin == nullptr;
+  const int shift = a.begin_bit + pass * kRadixBits;
+  const unsigned dmask = (a.nbits - pass * kRadixBits >= kRadixBits) ? (kRadix - 1u)
+                                                                      : ((1u << (a.nbits - pass * kRadixBits)) - 1u);
   const uint32_t* digit_off = a.hist + pass * kRadix;
   const long long limit = g_spin_limit;
 
@@ -199,32 +234,51 @@ __global__ void __launch_bounds__(THREADS, 3) sort_pass_kernel(SortArgs a, int p
     const uint32_t tile = s_tile;
     if (tile >= num_tiles) break;
     const int64_t tile_base = (int64_t)tile * TILE;
+    const bool full = tile_base + TILE <= n;
 
     // ---- load (warp-striped) and rank within the warp
     K key[ITEMS];
     int32_t val[ITEMS];
     uint32_t dr[ITEMS];  // (rank within the warp's digit << 9) | digit (kRadix = padding row)
+    const int64_t r0 = tile_base + (int64_t)warp * (32 * ITEMS) + lane;
+    if (full && word_in) {
+      const K* kp = static_cast<const K*>(kin) + r0;
 #pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-      int64_t row = tile_base + (int64_t)warp * (32 * ITEMS) + it * 32 + lane;
-      bool valid = row < n;
-      K u = 0;
-      int32_t v = 0;
-      if (valid) {
-        u = (K)encode_key(kin, kin_dt, row);
-        v = (pd.first && vin == nullptr) ? (int32_t)row : vin[row];
+      for (int it = 0; it < ITEMS; ++it) key[it] = kp[it * 32] ^ flip_in;
+      if (row_vals) {
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) val[it] = (int32_t)(r0 + it * 32);
+      } else {
+        const int32_t* vp = vin + r0;
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) val[it] = vp[it * 32];
       }
-      key[it] = u;
-      val[it] = v;
-      dr[it] = valid ? digit_of(u, a.begin_bit, a.nbits, pass) : kRadix;
+    } else {
+#pragma unroll
+      for (int it = 0; it < ITEMS; ++it) {
+        const int64_t row = r0 + it * 32;
+        key[it] = 0;
+        val[it] = 0;
+        if (row < n) {
+          key[it] = (K)encode_key(kin, kin_dt, row);
+          val[it] = row_vals ? (int32_t)row : vin[row];
+        }
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) dr[it] = (unsigned)(key[it] >> shift) & dmask;
+    if (!full) {
+#pragma unroll
+      for (int it = 0; it < ITEMS; ++it)
+        if (r0 + it * 32 >= n) dr[it] = kRadix;
     }
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
       const unsigned dg = dr[it];
-      unsigned peers = match_digit9(dg);
-      int leader = 31 - __clz(peers);
-      uint32_t before = __popc(peers & ((1u << lane) - 1));
-      uint32_t base = s_wcnt[warp][dg];
+      const unsigned peers = full ? match_digit8(dg) : match_digit9(dg);
+      const int leader = 31 - __clz(peers);
+      const uint32_t before = __popc(peers & ((1u << lane) - 1));
+      const uint32_t base = s_wcnt[warp][dg];
       __syncwarp();
       if (lane == leader) s_wcnt[warp][dg] = base + __popc(peers);
       __syncwarp();
@@ -232,7 +286,8 @@ __global__ void __launch_bounds__(THREADS, 3) sort_pass_kernel(SortArgs a, int p
     }
     __syncthreads();
 
-    // ---- per digit (thread d): warp prefix, tile count, look-back
+    // ---- per digit (thread d): warp prefix and tile count, published at
+    // once; the tile is staged before the look-back waits on predecessors
     const int d = threadIdx.x;
     uint32_t tile_count = 0;
 #pragma unroll
@@ -243,12 +298,28 @@ __global__ void __launch_bounds__(THREADS, 3) sort_pass_kernel(SortArgs a, int p
     }
     uint32_t* st = a.status + (size_t)tile * kRadix + d;
     const bool inject = ((long long)tile == g_unpublished_tile);
+    if (!inject) st_volatile_u32(st, (tile == 0 ? kSFlagPrefix : kSFlagAgg) | tile_count);
+    int total;
+    const int start = block_exclusive_sum<THREADS>((int)tile_count, s_scan, &total);  // (ends on a barrier)
+    s_tile_start[d] = (uint32_t)start;
+    __syncthreads();
+
+    // ---- stage keys and values in tile order (with each slot's digit)
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const unsigned dg = dr[it] & 511u;
+      if (dg < kRadix) {
+        const unsigned slot = s_tile_start[dg] + s_wcnt[warp][dg] + (dr[it] >> 9);
+        s_keys[slot] = key[it];
+        s_vals[slot] = val[it];
+        s_dig[slot] = (uint8_t)dg;
+      }
+    }
+
+    // ---- look-back (thread d): the count of digit d in all earlier tiles
     long long excl = 0;
     bool failed = false;
-    if (tile == 0) {
-      if (!inject) st_volatile_u32(st, kSFlagPrefix | tile_count);
-    } else {
-      if (!inject) st_volatile_u32(st, kSFlagAgg | tile_count);
+    if (tile > 0) {
       // walk back kLookWin predecessors at a time: their words are loaded
       // together, then consumed in order (waiting only on a word not yet set)
       constexpr int kLookWin = 8;
@@ -283,48 +354,34 @@ __global__ void __launch_bounds__(THREADS, 3) sort_pass_kernel(SortArgs a, int p
       raise_status(TQP_ERR_TIMEOUT);
       s_failed = 1;
     }
-    s_gbase[d] = (int64_t)digit_off[d] + excl;
-    int total;
-    int start = block_exclusive_sum<THREADS>((int)tile_count, s_scan, &total);
-    s_tile_start[d] = (uint32_t)start;
+    s_gofs[d] = (long long)digit_off[d] + excl - start;
     __syncthreads();
-    const int tile_failed = s_failed;
-    __syncthreads();
-    if (tile_failed) continue;  // give up on this tile without writing
+    if (s_failed) {  // give up on this tile without writing
+      __syncthreads();
+      continue;
+    }
 
-    // ---- stage keys in tile order (with each slot's digit)
+    // ---- write each staged slot to its digit's run in the output
+    if (word_out) {
+      K* ko = static_cast<K*>(kout);
 #pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-      const unsigned dg = dr[it] & 511u;
-      if (dg < kRadix) {
-        const unsigned slot = s_tile_start[dg] + s_wcnt[warp][dg] + (dr[it] >> 9);
-        s_keys[slot] = key[it];
-        s_dig[slot] = (uint8_t)dg;
+      for (int it = 0; it < ITEMS; ++it) {
+        const int j = it * THREADS + threadIdx.x;
+        if (j < total) {
+          const long long g = s_gofs[s_dig[j]] + j;
+          ko[g] = s_keys[j] ^ flip_out;
+          vout[g] = s_vals[j];
+        }
       }
-    }
-    __syncthreads();
+    } else {
 #pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-      int j = it * THREADS + threadIdx.x;
-      if (j < total) {
-        const unsigned dd = s_dig[j];
-        store_decoded(kout, kout_dt, s_gbase[dd] + (j - (int)s_tile_start[dd]), (unsigned long long)s_keys[j]);
-      }
-    }
-    __syncthreads();
-    // ---- stage values in tile order
-#pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-      const unsigned dg = dr[it] & 511u;
-      if (dg < kRadix) s_vals[s_tile_start[dg] + s_wcnt[warp][dg] + (dr[it] >> 9)] = val[it];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-      int j = it * THREADS + threadIdx.x;
-      if (j < total) {
-        const unsigned dd = s_dig[j];
-        vout[s_gbase[dd] + (j - (int)s_tile_start[dd])] = s_vals[j];
+      for (int it = 0; it < ITEMS; ++it) {
+        const int j = it * THREADS + threadIdx.x;
+        if (j < total) {
+          const long long g = s_gofs[s_dig[j]] + j;
+          store_decoded(kout, kout_dt, g, (unsigned long long)s_keys[j]);
+          vout[g] = s_vals[j];
+        }
       }
     }
     __syncthreads();

@@ -487,10 +487,11 @@ __global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, co
 // sorted key's group rank as the sort's payload (or no group column).
 // The plan is taken from the first and last packed keys; when the cells
 // are wide and no dimension value is aggregated (eligible), dir_emit_kernel
-// writes every structure the probe reads -- the key/rank pairs, the cell
-// starts, the bitmap, and the 32-byte records -- and
+// writes every structure the probe reads -- the bitmap, the 32-byte
+// records, and the key/rank pairs of keys past a record's inline ones -- and
 // the decode, gather and directory passes of the sorted form skip their
-// work (fused = 1).
+// work (fused = 1).  The cell starts (dir) are not written: the records
+// carry each cell's first position and count.
 __device__ __forceinline__ unsigned long long packed_image(unsigned long long packed, long long kmin, int key_dt) {
   const unsigned long long key = packed + (unsigned long long)kmin;  // the key, 64-bit two's complement
   return key_dt == TQP_I32 ? (unsigned long long)((uint32_t)key ^ 0x80000000u) : key ^ 0x8000000000000000ull;
@@ -521,8 +522,7 @@ struct EmitArgs {
   int64_t n_max;
   const int64_t* d_n;
   const DimDir* dd;
-  void* kr;                          // KeyRank32 / KeyRank64 per sorted position
-  int* dir;
+  void* kr;                          // KeyRank32 / KeyRank64 per sorted position (overflow keys only)
   uint32_t* bitmap;
   DirCell* table;
   StarPlan* plan;
@@ -543,21 +543,15 @@ __global__ void dir_emit_kernel(EmitArgs a) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nd; p += stride) {
     const unsigned long long pk = __ldg(&a.packed[p]);
     const unsigned long long u = packed_image(pk, kmin, a.key_dt);
-    const int32_t rk = rank_at(p);
-    if (k32)
-      static_cast<KeyRank32*>(a.kr)[p] = KeyRank32{(uint32_t)u, rk};
-    else
-      static_cast<KeyRank64*>(a.kr)[p] = KeyRank64{u, (long long)rk};
     if (p > 0 && __ldg(&a.packed[p - 1]) == pk) {
       if (atomicExch(&a.plan->unsupported, 1) == 0) raise_status(TQP_ERR_UNSUPPORTED);
     }
     const long long c = (long long)((u - r.umin) >> r.bshift);
     const long long prev = p ? cell_at(p - 1) : -1;
-    if (p == nd - 1) a.dir[c + 1] = (int)nd;
     if (c == prev) continue;
-    // the first key of cell c: the starts of the empty cells before it and
-    // of its own, its bit, and (records form) the records of those cells
-    for (long long h = prev + 1; h <= c; ++h) a.dir[h] = (int)p;
+    // the first key of cell c writes the cell's bit, the records of the
+    // empty cells before it and its own, and the key/rank pairs of the keys
+    // beyond the record's inline ones (the only pairs a probe reads)
     if (r.use_bits) atomicOr(&a.bitmap[c >> 5], 1u << (c & 31));
     for (long long h = prev + 1; h < c; ++h) {
       a.table[h].a = make_int4(0, 0, 0, 0);
@@ -567,10 +561,15 @@ __global__ void dir_emit_kernel(EmitArgs a) {
     while (e < nd && cell_at(e) == c) ++e;
     const int cnt = (int)(e - p);
     uint32_t w[8] = {0, 0, 0, 0, 0, 0, (uint32_t)p, (uint32_t)cnt};
-    for (int j = 0; j < cap && j < cnt; ++j) {
+    for (int j = 0; j < cnt; ++j) {
       const unsigned long long uj = j ? packed_image(__ldg(&a.packed[p + j]), kmin, a.key_dt) : u;
-      const int32_t rj = j ? rank_at(p + j) : rk;
-      if (k32) {
+      const int32_t rj = rank_at(p + j);
+      if (j >= cap) {
+        if (k32)
+          static_cast<KeyRank32*>(a.kr)[p + j] = KeyRank32{(uint32_t)uj, rj};
+        else
+          static_cast<KeyRank64*>(a.kr)[p + j] = KeyRank64{uj, (long long)rj};
+      } else if (k32) {
         w[j] = (uint32_t)uj;
         w[3 + j] = (uint32_t)rj;
       } else {

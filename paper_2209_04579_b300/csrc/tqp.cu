@@ -164,8 +164,12 @@ tqp_status last_launch() { return cudaGetLastError() == cudaSuccess ? TQP_OK : T
 
 // ---------------------------------------------------------------- sort
 constexpr int kSortThreads = 256;
-constexpr int kItems32 = 16;
-constexpr int kItems64 = 12;
+// Rows per thread of a sort tile, per key width: a process-wide setting
+// (tqp_sort_tiles, the autotuner's knob) among the compiled choices.
+std::atomic<int> g_items32{16};
+std::atomic<int> g_items64{12};
+bool valid_items32(int v) { return v == 8 || v == 12 || v == 16; }
+bool valid_items64(int v) { return v == 6 || v == 8 || v == 12; }
 
 struct SortWs {
   uint32_t* ctrl;  // hist [P*256] + counters [P]
@@ -175,16 +179,17 @@ struct SortWs {
   int32_t* alt_vals[2];
   size_t ctrl_words;
   uint32_t tiles;
+  int items;  // rows per thread of a tile, fixed when the workspace is carved
 };
-
-int64_t sort_tile(int word_bytes) { return (int64_t)kSortThreads * (word_bytes == 4 ? kItems32 : kItems64); }
 
 SortWs carve_sort(Carver& c, int64_t n, int word_bytes, int npasses) {
   SortWs w;
   w.ctrl_words = (size_t)npasses * kRadix + npasses;
   w.ctrl = c.take<uint32_t>(w.ctrl_words);
   w.plan = c.take<SortPlan>(1);
-  int64_t t = (n + sort_tile(word_bytes) - 1) / sort_tile(word_bytes);
+  w.items = word_bytes == 4 ? g_items32.load() : g_items64.load();
+  const int64_t tile = (int64_t)kSortThreads * w.items;
+  int64_t t = (n + tile - 1) / tile;
   w.tiles = (uint32_t)t;
   w.status = c.take<uint32_t>((size_t)(t > 0 ? t : 1) * kRadix);
   for (int i = 0; i < 2; ++i) {
@@ -226,12 +231,18 @@ tqp_status run_sort(const SortWs& w, int key_dt, const void* keys_in, const int3
   for (int p = 0; p < a.npasses; ++p) {
     TQP_CUDA(cudaMemsetAsync(w.status, 0, (size_t)w.tiles * kRadix * sizeof(uint32_t), s));
     if (word_bytes == 4) {
-      auto k = sort_pass_kernel<uint32_t, kSortThreads, kItems32>;
-      size_t smem = (size_t)kSortThreads * kItems32 * 4;
+      auto k = w.items == 8    ? sort_pass_kernel<uint32_t, kSortThreads, 8>
+               : w.items == 12 ? sort_pass_kernel<uint32_t, kSortThreads, 12>
+                               : sort_pass_kernel<uint32_t, kSortThreads, 16>;
+      size_t smem = (size_t)kSortThreads * w.items * (4 + 4);  // staged keys and values
+      TQP_CUDA(smem_optin(k, (int)smem));
       k<<<persistent_grid(k, kSortThreads, smem, w.tiles), kSortThreads, smem, s>>>(a, p, w.tiles); note_launch();
     } else {
-      auto k = sort_pass_kernel<unsigned long long, kSortThreads, kItems64>;
-      size_t smem = (size_t)kSortThreads * kItems64 * 8;
+      auto k = w.items == 6   ? sort_pass_kernel<unsigned long long, kSortThreads, 6>
+               : w.items == 8 ? sort_pass_kernel<unsigned long long, kSortThreads, 8>
+                              : sort_pass_kernel<unsigned long long, kSortThreads, 12>;
+      size_t smem = (size_t)kSortThreads * w.items * (8 + 4);  // staged keys and values
+      TQP_CUDA(smem_optin(k, (int)smem));
       k<<<persistent_grid(k, kSortThreads, smem, w.tiles), kSortThreads, smem, s>>>(a, p, w.tiles); note_launch();
     }
   }
@@ -499,6 +510,13 @@ tqp_status tqp_profile_events(int kernel_class, void* start_event, void* stop_ev
   if (kernel_class < 1 || kernel_class > 15) return TQP_ERR_INVALID;
   g_prof_start[kernel_class] = static_cast<cudaEvent_t>(start_event);
   g_prof_stop[kernel_class] = static_cast<cudaEvent_t>(stop_event);
+  return TQP_OK;
+}
+
+tqp_status tqp_sort_tiles(int items32, int items64) {
+  if ((items32 && !valid_items32(items32)) || (items64 && !valid_items64(items64))) return TQP_ERR_INVALID;
+  if (items32) g_items32.store(items32);
+  if (items64) g_items64.store(items64);
   return TQP_OK;
 }
 
@@ -919,6 +937,7 @@ struct LearnedWs {
   unsigned* tstart;  // two-level scatter: split 2's tile starts per coarse bucket
   unsigned* cur1;    // two-level scatter: coarse cursors
   unsigned short* fine;  // two-level scatter: each row's bucket within its coarse bucket
+  unsigned short* ids;   // two-level scatter: each row's bucket from the counting pass (B <= 65536)
   uint32_t* rheads;
   Partial* rcarry;
   void* lgath[TQP_MAX_VALS];
@@ -979,6 +998,7 @@ LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int ro
   w.big_flags = c.take<uint32_t>((size_t)B);
   w.tstart = c.take<unsigned>((1 << kSplitCoarseBits) + 1);
   if (scatter) w.fine = c.take<unsigned short>(nn);
+  if (scatter && B <= 65536) w.ids = c.take<unsigned short>(nn);
   w.cur1 = c.take<unsigned>((size_t)(1 << kSplitCoarseBits) * kCursorStride);
   if (P) {  // the group-by's reduce
     w.rtiles = (n + kReduceThreads * kReduceItems - 1) / (kReduceThreads * kReduceItems);
@@ -1072,6 +1092,7 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
   pa.out_row = w.lrow;
   pa.heavy_acc = w.heavy_acc;
   pa.bcount = w.bcount;
+  pa.ids = want_heavy ? nullptr : w.ids;  // the two-level scatter reads the counting pass's buckets
   TQP_CUDA(cudaMemsetAsync(w.count, 0, (size_t)B * sizeof(unsigned), s));
   {
     // the steps live in shared memory when the scatter's layout still fits.
@@ -1106,10 +1127,12 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
     } else {
       // no heavy keys: the two-level scatter (block-level multisplits)
       const int F = split_fine_bits(B);
-      const bool tsm = kSplitThrShared && split_smem_bytes(B, true) + 8192 <= (size_t)kMaxSmemOptin;
-      const size_t xsm = split_smem_bytes(B, tsm);
+      const bool ids = pa.ids != nullptr;
+      const bool tsm = !ids && kSplitThrShared && split_smem_bytes(B, true) + 8192 <= (size_t)kMaxSmemOptin;
+      const size_t xsm = split_smem_bytes(B, tsm, !ids);
       const size_t xsm2 = split_smem_bytes(B, false, false);
-      auto k1 = tsm ? lp_split1_kernel<true> : lp_split1_kernel<false>;
+      auto k1 = ids ? lp_split1_kernel<false, true>
+                    : (tsm ? lp_split1_kernel<true, false> : lp_split1_kernel<false, false>);
       auto k2 = lp_split2_kernel;
       TQP_CUDA(smem_optin(k1, (int)xsm));
       TQP_CUDA(smem_optin(k2, (int)xsm2));
@@ -1749,7 +1772,6 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
         ea.d_n = kn;
         ea.dd = w.dplan;
         ea.kr = w.kr;
-        ea.dir = w.dir;
         ea.bitmap = w.bitmap;
         ea.table = w.table;
         ea.plan = plan;

@@ -140,6 +140,8 @@ _lib.tqp_star_agg_batched.argtypes = [_P(BatchShape), _P(Problem), _int, _P(Batc
 _lib.tqp_filter_noalloc.argtypes = [_P(Col), _int, _P(Pred), _int, _i64, _vp, _vp, _i64, _vp, _vp]
 _lib.tqp_filter_noalloc.restype = ctypes.c_int
 _lib.tqp_status_poll.argtypes = [_vp]
+_lib.tqp_sort_tiles.argtypes = [_int, _int]
+_lib.tqp_sort_tiles.restype = ctypes.c_int
 _lib.tqp_debug_set_spin_limit.argtypes = [_i64]
 _lib.tqp_debug_inject_unpublished_tile.argtypes = [_i64]
 _lib.tqp_status_string.restype = ctypes.c_char_p
@@ -533,6 +535,11 @@ def tqp_partition_learned(keys, cfg=None, sel=None, n=None, d_n=None, stream=Non
                 _ptr(out["rows"]), _ptr(out["offsets"]), _ptr(out["train_x"]), _ptr(out["train_y"]),
                 _ptr(out["model"]), _ptr(out["stats"])], dev, stream)
     return out
+
+
+def tqp_sort_tiles(items32=0, items64=0):
+    """Rows per thread of the radix sort's tiles (0: unchanged)."""
+    _check(_lib.tqp_sort_tiles(items32, items64), "tqp_sort_tiles")
 
 
 def stats_from_device(t):

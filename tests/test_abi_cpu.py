@@ -173,3 +173,13 @@ def test_binding_constants_match_header():
     assert m and (1 << int(m.group(1))) == tqp.NOALLOC_MAX_ROWS
     m = re.search(r"#define\s+TQP_CDF_HIDDEN\s+(\d+)", text)
     assert m and int(m.group(1)) == tqp.H
+
+
+def test_sort_tiles_setting_checks():
+    """The sort tile setting accepts only its compiled choices (no device work)."""
+    from paper_2209_04579_b300 import tqp
+    lib = tqp._lib
+    assert lib.tqp_sort_tiles(7, 0) == tqp.ERR_INVALID
+    assert lib.tqp_sort_tiles(0, 16) == tqp.ERR_INVALID
+    assert lib.tqp_sort_tiles(0, 0) == tqp.OK
+    assert lib.tqp_sort_tiles(16, 12) == tqp.OK      # the defaults

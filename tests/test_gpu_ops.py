@@ -346,3 +346,27 @@ def test_group_by_string_column(T):
     vals = [bytes(types[i]) for i in host(rep)[host(gk)[:G]]]
     assert vals == sorted(vals) and len(set(vals)) == G
     assert T.tqp_status_poll() == T.OK
+
+
+@pytest.mark.parametrize("items32,items64", [(8, 6), (12, 8), (16, 12)])
+def test_sort_every_tile_choice(T, items32, items64):
+    """Every tile size the autotuner may pick sorts exactly as the oracle:
+    stable, several tiles and a ragged tail, 32- and 64-bit keys, full and
+    partial bit ranges."""
+    r = rng(items32 * 7 + items64)
+    try:
+        T.tqp_sort_tiles(items32, items64)
+        for dt, n in ((np.int32, 250_003), (np.int64, 180_001), (np.int16, 70_001)):
+            k = col(r, n, dt)
+            k[::5] = k[3]                        # ties: the payload shows stability
+            v = r.integers(-2**31, 2**31, n).astype(np.int32)
+            want = orc.sort_pairs(k, v)
+            ko, vo = T.tqp_sort_pairs(dev(k), dev(v))
+            assert np.array_equal(host(ko), want[0]) and np.array_equal(host(vo), want[1])
+            bits = np.dtype(dt).itemsize * 8
+            want = orc.sort_pairs(k, v, 3, bits - 5)
+            ko, vo = T.tqp_sort_pairs(dev(k), dev(v), 3, bits - 5)
+            assert np.array_equal(host(vo), want[1])
+    finally:
+        T.tqp_sort_tiles(16, 12)
+    assert T.tqp_status_poll() == T.OK
