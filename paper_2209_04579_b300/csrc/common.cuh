@@ -40,6 +40,31 @@ __device__ __forceinline__ int64_t load_as_i64(const void* p, int dt, int64_t i)
   }
 }
 
+// N elements of a column (idx[k] where ok[k]; 0 elsewhere) widened to
+// int64: one switch on the dtype, then the N loads issued together.
+template <int N>
+__device__ __forceinline__ void load_many_as_i64(const void* p, int dt, const int64_t (&idx)[N], const bool (&ok)[N],
+                                                 long long (&out)[N]) {
+  switch (dt) {
+    case TQP_I8:
+#pragma unroll
+      for (int k = 0; k < N; ++k) out[k] = ok[k] ? static_cast<const int8_t*>(p)[idx[k]] : 0;
+      break;
+    case TQP_I16:
+#pragma unroll
+      for (int k = 0; k < N; ++k) out[k] = ok[k] ? static_cast<const int16_t*>(p)[idx[k]] : 0;
+      break;
+    case TQP_I32:
+#pragma unroll
+      for (int k = 0; k < N; ++k) out[k] = ok[k] ? static_cast<const int32_t*>(p)[idx[k]] : 0;
+      break;
+    default:
+#pragma unroll
+      for (int k = 0; k < N; ++k) out[k] = ok[k] ? static_cast<const long long*>(p)[idx[k]] : 0;
+      break;
+  }
+}
+
 __device__ __forceinline__ void store_from_i64(void* p, int dt, int64_t i, int64_t v) {
   switch (dt) {
     case TQP_I8: static_cast<int8_t*>(p)[i] = static_cast<int8_t>(v); break;

@@ -567,6 +567,8 @@ struct PartArgs {
   int32_t* out_row;
   long long* heavy_acc;     // [nheavy][naggs]
   unsigned short* ids;      // the counting pass's bucket of every row (no heavy keys, B <= 65536), or null
+  int coarse_F;             // > 0: the counting pass counts coarse buckets b >> coarse_F only (into
+                            // count[c << coarse_F]); the fine counts come after split 1
 };
 
 // ---- partition kernels: shared-memory layout and setup
@@ -574,11 +576,13 @@ constexpr int kHeavyBits = 11;
 constexpr int kHeavySlots = 1 << kHeavyBits;  // open addressing, load <= 1/2
 constexpr int kPartThreads = 1024;
 constexpr int kPartItems = 4;
+constexpr int kHistItems = 8;  // rows per thread per round of the counting pass (loads in flight)
 
 // Partition modes: the bucket function's steps in global memory, in shared
 // memory, or (counting only) in shared memory with per-block bucket counts:
 // each block counts one contiguous chunk of rows in shared memory.
 constexpr int kThrGlobal = 0, kThrShared = 1, kBlockHist = 2;
+constexpr int kPartCoarseBins = 512;  // coarse buckets a counting pass may count in shared memory
 constexpr int kBlockHistMaxB = 1 << 14;
 
 // Dynamic shared memory: directory, heavy-key table (key, index; index -1 =
@@ -651,6 +655,50 @@ __device__ __forceinline__ unsigned long long pack_row_plan(const PackPlan& K, i
   return u;
 }
 
+// The packed keys of N rows (rows[k], where valid[k]; 0 elsewhere).  With
+// one key column the N loads are issued together under one switch on its
+// dtype, instead of one round trip per row through pack_row_plan.
+template <int N>
+__device__ __forceinline__ void pack_rows(const PackPlan& K, const int64_t (&rows)[N], const bool (&valid)[N],
+                                          unsigned long long (&out)[N]) {
+  if (K.nkeys == 1) {
+    const unsigned long long kmin = (unsigned long long)K.kmin[0];
+    const int sh = K.shift[0];
+    long long v[N];
+    switch (K.dt[0]) {
+      case TQP_I8: {
+        const int8_t* c = static_cast<const int8_t*>(K.col[0]);
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] = valid[k] ? c[rows[k]] : 0;
+        break;
+      }
+      case TQP_I16: {
+        const int16_t* c = static_cast<const int16_t*>(K.col[0]);
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] = valid[k] ? c[rows[k]] : 0;
+        break;
+      }
+      case TQP_I32: {
+        const int32_t* c = static_cast<const int32_t*>(K.col[0]);
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] = valid[k] ? c[rows[k]] : 0;
+        break;
+      }
+      default: {
+        const long long* c = static_cast<const long long*>(K.col[0]);
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] = valid[k] ? c[rows[k]] : 0;
+        break;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = valid[k] ? ((unsigned long long)v[k] - kmin) << sh : 0ull;
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) out[k] = valid[k] ? pack_row_plan(K, rows[k]) : 0ull;
+}
+
 // Directory, heavy table, steps (kThrShared and up) and key plan into shared memory.
 template <int MODE>
 __device__ __forceinline__ void part_setup(const PartArgs& a, const LearnedPlan& lp, const PartSmem& S, PackPlan& K) {
@@ -685,39 +733,46 @@ __device__ __forceinline__ void block_chunk(int64_t n, int64_t* c0, int64_t* c1)
 }
 
 // Light rows per bucket (kBlockHist: per block, into bcount).  Each thread
-// carries kPartItems rows at a time.
+// carries kHistItems rows at a time.
 template <int MODE>
 __global__ void __launch_bounds__(kPartThreads, 1) lp_hist_kernel(PartArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ PackPlan K;
+  __shared__ unsigned s_coarse[kPartCoarseBins];  // coarse_F > 0: the block's coarse counts
   const LearnedPlan lp = *a.lp;
   const PartSmem S = part_carve(smem, 0, lp.B);
+  const int cF = MODE == kBlockHist ? 0 : a.coarse_F;
   if (MODE == kBlockHist)
     for (int b = threadIdx.x; b < lp.B; b += kPartThreads) S.bh[b] = 0;
+  if (cF)
+    for (int c = threadIdx.x; c < kPartCoarseBins; c += kPartThreads) s_coarse[c] = 0;
   part_setup<MODE>(a, lp, S, K);
   const unsigned* thr = MODE >= kThrShared ? S.thr : a.thr;
   const int nh = lp.nheavy;
   const int64_t n = clamp_n(a.n_max, a.d_n);
-  constexpr int TILE = kPartThreads * kPartItems;
+  constexpr int TILE = kPartThreads * kHistItems;
   int64_t c0 = (int64_t)blockIdx.x * TILE, c1 = n, step = (int64_t)gridDim.x * TILE;
   if (MODE == kBlockHist) {
     block_chunk(n, &c0, &c1);
     step = TILE;
   }
   for (int64_t base = c0; base < c1; base += step) {
-    unsigned long long p[kPartItems];
-    bool v[kPartItems];
+    unsigned long long p[kHistItems];
+    bool v[kHistItems];
+    int64_t rw[kHistItems];
 #pragma unroll
-    for (int k = 0; k < kPartItems; ++k) {
+    for (int k = 0; k < kHistItems; ++k) {
       const int64_t i = base + k * kPartThreads + threadIdx.x;
       v[k] = i < c1;
-      p[k] = v[k] ? pack_row_plan(K, a.sel ? (int64_t)a.sel[i] : i) : 0ull;
+      rw[k] = v[k] ? (a.sel ? (int64_t)a.sel[i] : i) : 0;
     }
+    pack_rows(K, rw, v, p);
 #pragma unroll
-    for (int k = 0; k < kPartItems; ++k) {
+    for (int k = 0; k < kHistItems; ++k) {
       if (!v[k] || (nh && heavy_lookup(S, p[k]) >= 0)) continue;
       const int b = lp_bucket<MODE >= kThrShared>(p[k], lp, S.dir, thr);
       if (MODE == kBlockHist) atomicAdd(&S.bh[b], 1u);
+      else if (cF) atomicAdd(&s_coarse[b >> cF], 1u);
       else atomicAdd(&a.count[b], 1u);
       if (a.ids) a.ids[base + k * kPartThreads + threadIdx.x] = (unsigned short)b;
     }
@@ -725,6 +780,11 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_hist_kernel(PartArgs a) {
   if (MODE == kBlockHist) {
     __syncthreads();
     for (int b = threadIdx.x; b < lp.B; b += kPartThreads) a.bcount[(size_t)blockIdx.x * lp.B + b] = S.bh[b];
+  }
+  if (cF) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < (lp.B >> cF); c += kPartThreads)
+      if (s_coarse[c]) atomicAdd(&a.count[c << cF], s_coarse[c]);
   }
 }
 
@@ -950,19 +1010,17 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
   for (int64_t base = (int64_t)blockIdx.x * TILE; base < n; base += (int64_t)gridDim.x * TILE) {
     unsigned long long p[kPartItems];
     int64_t row[kPartItems];
+    bool v[kPartItems];
     int h[kPartItems];
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k) {
       const int64_t i = base + k * kPartThreads + threadIdx.x;
-      row[k] = 0;
-      p[k] = 0;
-      h[k] = -2;  // past the end
-      if (i < c1) {
-        row[k] = a.sel ? (int64_t)a.sel[i] : i;
-        p[k] = pack_row_plan(K, row[k]);
-        h[k] = nh ? heavy_lookup(S, p[k]) : -1;
-      }
+      v[k] = i < c1;
+      row[k] = v[k] ? (a.sel ? (int64_t)a.sel[i] : i) : 0;
     }
+    pack_rows(K, row, v, p);
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) h[k] = v[k] ? (nh ? heavy_lookup(S, p[k]) : -1) : -2;  // -2: past the end
     // light rows: bucket, cursor, store
     unsigned pos[kPartItems];
 #pragma unroll
@@ -1141,20 +1199,19 @@ __global__ void __launch_bounds__(kSplitThreads, IDS ? 2 : 1) lp_split1_kernel(P
     int32_t r[kSplitItems];
     int bin[kSplitItems], fine[kSplitItems];
     unsigned rk[kSplitItems];
+    int64_t rw[kSplitItems];
+    bool v[kSplitItems];
 #pragma unroll
     for (int k = 0; k < kSplitItems; ++k) {
       const int64_t i = base + k * kSplitThreads + threadIdx.x;
       bin[k] = -1;
       fine[k] = 0;
-      p[k] = 0;
-      r[k] = 0;
       rk[k] = 0;
-      if (i < n) {
-        const int64_t row = a.sel ? (int64_t)a.sel[i] : i;
-        p[k] = pack_row_plan(K, row);
-        r[k] = a.payload ? a.payload[i] : (int32_t)row;
-      }
+      v[k] = i < n;
+      rw[k] = v[k] ? (a.sel ? (int64_t)a.sel[i] : i) : 0;
+      r[k] = v[k] ? (a.payload ? a.payload[i] : (int32_t)rw[k]) : 0;
     }
+    pack_rows(K, rw, v, p);
 #pragma unroll
     for (int k = 0; k < kSplitItems; ++k)
       if (base + k * kSplitThreads + threadIdx.x < n) {
@@ -1242,6 +1299,46 @@ __global__ void __launch_bounds__(kSplitThreads, 2) lp_split2_kernel(const Learn
   }
 }
 
+// Fine counts after split 1: each tile of split 2's tiling (rows of one
+// coarse bucket c) counts its rows' fine ids in shared memory and adds them
+// into count[(c << F) + fine], one atomic per (tile, fine bucket).
+__global__ void __launch_bounds__(kSplitThreads) lp_fine_count_kernel(const LearnedPlan* lpp, int F, const unsigned* off,
+                                                                     const unsigned* tstart,
+                                                                     const unsigned short* in_fine, unsigned* count) {
+  __shared__ unsigned s_cnt[kSplitMaxBins];
+  __shared__ unsigned s_tstart[(1 << kSplitCoarseBits) + 1];
+  const int C = lpp->B >> F;
+  for (int i = threadIdx.x; i <= C; i += kSplitThreads) s_tstart[i] = tstart[i];
+  __syncthreads();
+  const int nbins = 1 << F;
+  const unsigned ntiles = s_tstart[C];
+  for (unsigned t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int lo = 0, hi = C;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_tstart[mid] <= t) lo = mid; else hi = mid;
+    }
+    const int c = lo;
+    const int64_t row0 = (int64_t)off[c << F] + (int64_t)(t - s_tstart[c]) * kSplitTile;
+    const int64_t row1 = off[(c + 1) << F];
+    for (int i = threadIdx.x; i < nbins; i += kSplitThreads) s_cnt[i] = 0;
+    __syncthreads();
+    unsigned short f[kSplitItems];
+#pragma unroll
+    for (int k = 0; k < kSplitItems; ++k) {
+      const int64_t i = row0 + k * kSplitThreads + threadIdx.x;
+      f[k] = i < row1 ? in_fine[i] : (unsigned short)0xffff;
+    }
+#pragma unroll
+    for (int k = 0; k < kSplitItems; ++k)
+      if (f[k] != 0xffff) atomicAdd(&s_cnt[f[k]], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbins; i += kSplitThreads)
+      if (s_cnt[i]) atomicAdd(&count[(c << F) + i], s_cnt[i]);
+    __syncthreads();
+  }
+}
+
 // Sorted packed keys back to the key column's dtype (one key column,
 // packed as key - kmin).  skip: a device flag that, when set, says the
 // decoded keys are not needed.
@@ -1313,7 +1410,8 @@ struct BucketSortArgs {
   unsigned long long* alt_p;    // scratch of the same size (global fallback)
   int32_t* alt_row;
   uint32_t* queue;
-  const uint32_t* big_flags;  // null, or: small buckets handled by the warp kernel unless flagged
+  const uint32_t* big_flags;  // null, or: small buckets handled by the warp kernel unless flagged (bit 0)
+  int only_flagged;           // the MSD kernel ran first: sort only the buckets it flagged (bit 1)
 };
 
 __device__ __forceinline__ bool warp_bucket_size(long long m) { return m > 1 && m <= 1024; }
@@ -1433,21 +1531,38 @@ __device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, uns
   unsigned long long* kB = L.kB;
   int32_t* rA = L.rA;
   int32_t* rB = L.rB;
-  unsigned long long lo = ~0ull, hi = 0;
-  for (int i = threadIdx.x; i < m; i += kLocalThreads) {
-    unsigned long long k = sp[i];
-    kA[i] = k;
-    rA[i] = sr[i];
-    lo = k < lo ? k : lo;
-    hi = k > hi ? k : hi;
+  // every row's loads are issued before any is used: the bucket comes in
+  // one memory round trip, and stays in registers until it is placed
+  unsigned long long kr[kLocalItems];
+  int32_t rr[kLocalItems];
+#pragma unroll
+  for (int q = 0; q < kLocalItems; ++q) {
+    const int i = q * kLocalThreads + threadIdx.x;
+    kr[q] = 0;
+    rr[q] = 0;
+    if (i < m) {
+      kr[q] = sp[i];
+      rr[q] = sr[i];
+    }
   }
+  unsigned long long lo = ~0ull, hi = 0;
+#pragma unroll
+  for (int q = 0; q < kLocalItems; ++q)
+    if (q * kLocalThreads + threadIdx.x < m) {
+      lo = kr[q] < lo ? kr[q] : lo;
+      hi = kr[q] > hi ? kr[q] : hi;
+    }
   unsigned long long pmin;
   const unsigned long long span = block_minmax_span(lo, hi, L.red, &pmin);
   if (span == 0) {  // one key: already in order
     if (sp != dp) {
-      for (int i = threadIdx.x; i < m; i += kLocalThreads) {
-        dp[i] = kA[i];
-        dr[i] = rA[i];
+#pragma unroll
+      for (int q = 0; q < kLocalItems; ++q) {
+        const int i = q * kLocalThreads + threadIdx.x;
+        if (i < m) {
+          dp[i] = kr[q];
+          dr[i] = rr[q];
+        }
       }
     }
     __syncthreads();
@@ -1460,7 +1575,9 @@ __device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, uns
   for (int d = threadIdx.x; d < kMsdBins; d += kLocalThreads) cur[d] = 0;
   if (threadIdx.x == 0) *L.nbig = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < m; i += kLocalThreads) atomicAdd(&cur[(kA[i] - pmin) >> sh], 1u);
+#pragma unroll
+  for (int q = 0; q < kLocalItems; ++q)
+    if (q * kLocalThreads + threadIdx.x < m) atomicAdd(&cur[(kr[q] - pmin) >> sh], 1u);
   __syncthreads();
   {
     constexpr int PER = kMsdBins / kLocalThreads;
@@ -1485,7 +1602,17 @@ __device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, uns
   }
   __syncthreads();
   if (*L.nbig) {
-    // some part is large: the block's LSD over the whole bucket
+    // some part is large: the block's LSD over the whole bucket (rows in
+    // their input order, which keeps it stable)
+#pragma unroll
+    for (int q = 0; q < kLocalItems; ++q) {
+      const int i = q * kLocalThreads + threadIdx.x;
+      if (i < m) {
+        kA[i] = kr[q];
+        rA[i] = rr[q];
+      }
+    }
+    __syncthreads();
     lsd_shared(kA, rA, kB, rB, m, L);
     for (int i = threadIdx.x; i < m; i += kLocalThreads) {
       dp[i] = kA[i];
@@ -1494,12 +1621,13 @@ __device__ void onchip_sort(const unsigned long long* sp, const int32_t* sr, uns
     __syncthreads();
     return;
   }
-  for (int i = threadIdx.x; i < m; i += kLocalThreads) {
-    const unsigned long long k = kA[i];
-    const unsigned pos = atomicAdd(&cur[(k - pmin) >> sh], 1u);
-    kB[pos] = k;
-    rB[pos] = rA[i];
-  }
+#pragma unroll
+  for (int q = 0; q < kLocalItems; ++q)
+    if (q * kLocalThreads + threadIdx.x < m) {
+      const unsigned pos = atomicAdd(&cur[(kr[q] - pmin) >> sh], 1u);
+      kB[pos] = kr[q];
+      rB[pos] = rr[q];
+    }
   __syncthreads();
   for (int d = threadIdx.x; d < kMsdBins; d += kLocalThreads) {
     const int p0 = (int)part[d], p1 = (int)part[d + 1];
@@ -1637,7 +1765,11 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
     const int64_t o0 = a.off[b], o1 = a.off[b + 1];
     const int64_t m = o1 - o0;
     if (m <= 1) continue;
-    if (a.big_flags && m <= kLocalCap && warp_bucket_size(m) && !a.big_flags[b]) continue;  // sorted by a warp
+    if (a.only_flagged) {
+      if (!(a.big_flags[b] & 2u)) continue;  // sorted by the warp or the MSD kernel
+    } else if (a.big_flags && m <= kLocalCap && warp_bucket_size(m) && !(a.big_flags[b] & 1u)) {
+      continue;  // sorted by a warp
+    }
     if (m <= kLocalCap) {
       onchip_sort(a.p + o0, a.row + o0, a.p + o0, a.row + o0, (int)m, L);
       continue;
@@ -1700,6 +1832,130 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
   }
 }
 
+
+// Buckets of up to kLocalCap rows whose keys spread over their range, two
+// blocks per SM: the rows stay in registers from their load to their place,
+// shared memory holds only the placed rows and the kMsdBins part cursors.
+// The rows are counted by the top kMsdBits bits of the bucket's key span,
+// placed by part, and each part (at most kSmallPart rows) is insertion-
+// sorted by one thread; a bucket with a larger part, or beyond kLocalCap
+// rows, is flagged (bit 1) for lp_bucket_sort_kernel.  Buckets of the warp
+// kernel's size are skipped unless it flagged them (bit 0).
+constexpr size_t kMsdSortSmem = (size_t)kLocalCap * (8 + 4) + (size_t)kMsdBins * 4;
+
+__global__ void __launch_bounds__(kLocalThreads, 2) lp_bucket_msd_kernel(BucketSortArgs a, uint32_t* queue,
+                                                                        uint32_t* flags) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_scan[33];
+  __shared__ unsigned long long s_red[2 * kLocalWarps];
+  __shared__ int s_nbig;
+  __shared__ uint32_t s_b;
+  unsigned long long* kB = reinterpret_cast<unsigned long long*>(smem);
+  int32_t* rB = reinterpret_cast<int32_t*>(kB + kLocalCap);
+  unsigned* cur = reinterpret_cast<unsigned*>(rB + kLocalCap);  // [kMsdBins] counts, then part cursors
+  const int B = a.lp->B;
+  while (true) {
+    if (threadIdx.x == 0) s_b = atomicAdd(queue, 1u);
+    __syncthreads();
+    const uint32_t b = s_b;
+    __syncthreads();
+    if (b >= (uint32_t)B) break;
+    const int64_t o0 = a.off[b];
+    const int m = (int)((int64_t)a.off[b + 1] - o0);
+    if (m <= 1) continue;
+    const uint32_t fl = flags[b];
+    if (warp_bucket_size(m) && !(fl & 1u)) continue;  // sorted by a warp
+    if (m > kLocalCap) {
+      if (threadIdx.x == 0) flags[b] = fl | 2u;
+      continue;
+    }
+    unsigned long long kr[kLocalItems];
+    int32_t rr[kLocalItems];
+#pragma unroll
+    for (int q = 0; q < kLocalItems; ++q) {
+      const int i = q * kLocalThreads + threadIdx.x;
+      kr[q] = 0;
+      rr[q] = 0;
+      if (i < m) {
+        kr[q] = a.p[o0 + i];
+        rr[q] = a.row[o0 + i];
+      }
+    }
+    unsigned long long lo = ~0ull, hi = 0;
+#pragma unroll
+    for (int q = 0; q < kLocalItems; ++q)
+      if (q * kLocalThreads + threadIdx.x < m) {
+        lo = kr[q] < lo ? kr[q] : lo;
+        hi = kr[q] > hi ? kr[q] : hi;
+      }
+    unsigned long long pmin;
+    const unsigned long long span = block_minmax_span(lo, hi, s_red, &pmin);
+    if (span == 0) continue;  // one key: already in order
+    const int bits = 64 - __clzll((long long)span);
+    const int sh = bits > kMsdBits ? bits - kMsdBits : 0;
+    for (int d = threadIdx.x; d < kMsdBins; d += kLocalThreads) cur[d] = 0;
+    if (threadIdx.x == 0) s_nbig = 0;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kLocalItems; ++q)
+      if (q * kLocalThreads + threadIdx.x < m) atomicAdd(&cur[(kr[q] - pmin) >> sh], 1u);
+    __syncthreads();
+    {
+      constexpr int PER = kMsdBins / kLocalThreads;
+      unsigned c[PER], sum = 0;
+      bool big = false;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        c[q] = cur[threadIdx.x * PER + q];
+        sum += c[q];
+        big |= c[q] > (unsigned)kSmallPart;
+      }
+      if (big) s_nbig = 1;
+      int tot;
+      unsigned run = (unsigned)block_exclusive_sum<kLocalThreads>((int)sum, s_scan, &tot);
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        cur[threadIdx.x * PER + q] = run;
+        run += c[q];
+      }
+    }
+    __syncthreads();
+    if (s_nbig) {  // a large part: the LSD of lp_bucket_sort_kernel
+      if (threadIdx.x == 0) flags[b] = fl | 2u;
+      continue;
+    }
+#pragma unroll
+    for (int q = 0; q < kLocalItems; ++q)
+      if (q * kLocalThreads + threadIdx.x < m) {
+        const unsigned pos = atomicAdd(&cur[(kr[q] - pmin) >> sh], 1u);
+        kB[pos] = kr[q];
+        rB[pos] = rr[q];
+      }
+    __syncthreads();
+    // part d now ends at cur[d] and starts where part d - 1 ends
+    for (int d = threadIdx.x; d < kMsdBins; d += kLocalThreads) {
+      const int p0 = d ? (int)cur[d - 1] : 0, p1 = (int)cur[d];
+      for (int x = p0 + 1; x < p1; ++x) {
+        const unsigned long long k = kB[x];
+        const int32_t r = rB[x];
+        int y = x - 1;
+        while (y >= p0 && kB[y] > k) {
+          kB[y + 1] = kB[y];
+          rB[y + 1] = rB[y];
+          --y;
+        }
+        kB[y + 1] = k;
+        rB[y + 1] = r;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += kLocalThreads) {
+      a.p[o0 + i] = kB[i];
+      a.row[o0 + i] = rB[i];
+    }
+    __syncthreads();
+  }
+}
 
 // ---------------------------------------------------------------- warp bucket sort
 // Small buckets (at most kWarpCap rows, key span below 2^48) are sorted by

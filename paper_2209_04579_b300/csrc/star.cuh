@@ -136,6 +136,8 @@ __global__ void dom_plan_kernel(const GroupPlan* gp, int64_t n_max, const int64_
   *sort_n = r.on ? 0 : n;
 }
 
+constexpr int kDomItems = 8;  // rows per thread per round of the value-domain passes
+
 __global__ void __launch_bounds__(256) dom_mark_kernel(const void* gcol, int gdt, const int32_t* sel, int64_t n_max,
                                                        const int64_t* d_n, const DomPlan* dp, uint32_t* bits) {
   __shared__ uint32_t s_bits[kDomSmemWords];
@@ -147,15 +149,29 @@ __global__ void __launch_bounds__(256) dom_mark_kernel(const void* gcol, int gdt
     for (int i = threadIdx.x; i < p.words; i += blockDim.x) s_bits[i] = 0;
     __syncthreads();
   }
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int64_t row = sel ? sel[i] : i;
-    const unsigned long long v = (unsigned long long)load_as_i64(gcol, gdt, row) - (unsigned long long)p.kmin;
-    const uint32_t w = (uint32_t)(v >> 5), b = 1u << (v & 31);
-    if (shared) {
-      if (!(s_bits[w] & b)) atomicOr(&s_bits[w], b);
-    } else if (!(__ldcg(&bits[w]) & b)) {
-      atomicOr(&bits[w], b);
+  // kDomItems rows per thread at a time, their loads issued together
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kDomItems;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kDomItems + threadIdx.x; base < n; base += stride) {
+    int64_t row[kDomItems];
+    bool ok[kDomItems];
+    long long val[kDomItems];
+#pragma unroll
+    for (int k = 0; k < kDomItems; ++k) {
+      const int64_t i = base + (int64_t)k * blockDim.x;
+      ok[k] = i < n;
+      row[k] = ok[k] ? (sel ? sel[i] : i) : 0;
+    }
+    load_many_as_i64(gcol, gdt, row, ok, val);
+#pragma unroll
+    for (int k = 0; k < kDomItems; ++k) {
+      if (!ok[k]) continue;
+      const unsigned long long v = (unsigned long long)val[k] - (unsigned long long)p.kmin;
+      const uint32_t w = (uint32_t)(v >> 5), b = 1u << (v & 31);
+      if (shared) {
+        if (!(s_bits[w] & b)) atomicOr(&s_bits[w], b);
+      } else if (!(__ldcg(&bits[w]) & b)) {
+        atomicOr(&bits[w], b);
+      }
     }
   }
   if (shared) {
@@ -205,10 +221,27 @@ __global__ void dom_payload_kernel(const void* gcol, int gdt, const int32_t* sel
   const DomPlan p = *dp;
   const bool rk = rank_payload && p.on;
   const int64_t n = clamp_n(n_max, d_n);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int32_t row = sel ? sel[i] : (int32_t)i;
-    out[i] = rk ? dom_rank(p, bits, pre, load_as_i64(gcol, gdt, row)) : row;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kDomItems;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kDomItems + threadIdx.x; base < n; base += stride) {
+    int64_t row[kDomItems];
+    bool ok[kDomItems];
+    long long val[kDomItems];
+#pragma unroll
+    for (int k = 0; k < kDomItems; ++k) {
+      const int64_t i = base + (int64_t)k * blockDim.x;
+      ok[k] = i < n;
+      row[k] = ok[k] ? (sel ? sel[i] : i) : 0;
+    }
+    if (rk) {
+      load_many_as_i64(gcol, gdt, row, ok, val);
+#pragma unroll
+      for (int k = 0; k < kDomItems; ++k)
+        if (ok[k]) out[base + (int64_t)k * blockDim.x] = dom_rank(p, bits, pre, val[k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kDomItems; ++k)
+        if (ok[k]) out[base + (int64_t)k * blockDim.x] = (int32_t)row[k];
+    }
   }
 }
 
@@ -440,13 +473,19 @@ struct __align__(16) DirCell {
   int4 a, b;
 };
 __host__ __device__ constexpr int cell_inline(bool k32) { return k32 ? 3 : 2; }
+// Wide cells wanted for nd keys: one per key for 32-bit keys (three inline
+// in a record), two per key for 64-bit keys (two inline), so that few cells
+// hold more keys than their record.
+__host__ __device__ inline long long wide_cells_wanted(int64_t nd, int key_dt) {
+  return key_dt == TQP_I32 ? (long long)nd : 2ll * nd;
+}
 
 // The cell plan of nd sorted passing keys whose images run from umin to
 // umax.  n_all: the dimension's rows before its predicates.  Wide cells of a
 // dimension that no predicate filtered skip the bitmap: foreign keys find
 // their row, and a miss is still found by the directory and the key.
 __device__ DimDir plan_cells(unsigned long long umin, unsigned long long umax, int64_t nd, int64_t n_all,
-                             int log2_cells_max, const long long* d_G) {
+                             int log2_cells_max, const long long* d_G, int key_dt) {
   DimDir r;
   r.direct = 0;
   r.fused = 0;
@@ -462,7 +501,7 @@ __device__ DimDir plan_cells(unsigned long long umin, unsigned long long umax, i
   r.umax = umax;
   unsigned long long span = r.umax - r.umin;
   int tb = 1;
-  while (tb < log2_cells_max && (1ll << tb) < 2 * nd) ++tb;
+  while (tb < log2_cells_max && (1ll << tb) < wide_cells_wanted(nd, key_dt)) ++tb;
   int bits = span ? 64 - __clzll((long long)span) : 0;
   // keys dense in their range (span within 8x their count): one cell per key
   // value, so the bit alone decides membership
@@ -479,7 +518,7 @@ __global__ void dir_plan_kernel(const void* skeys, int key_dt, int64_t n_max, co
   if (dd->direct || dd->fused) return;  // planned from the key range, or by the fused pass
   const int64_t nd = clamp_n(n_max, d_n);
   *dd = plan_cells(nd ? key_image(skeys, key_dt, 0) : 1, nd ? key_image(skeys, key_dt, nd - 1) : 0, nd, n_all,
-                   log2_cells_max, d_G);
+                   log2_cells_max, d_G, key_dt);
 }
 
 // ---- the directory in one pass, for a dimension sorted by the learned
@@ -505,7 +544,7 @@ __global__ void dir_plan_packed_kernel(const unsigned long long* packed, const G
   const int64_t nd = clamp_n(n_max, d_n);
   const long long kmin = gp->kmin[0];
   DimDir r = plan_cells(nd ? packed_image(packed[0], kmin, key_dt) : 1,
-                        nd ? packed_image(packed[nd - 1], kmin, key_dt) : 0, nd, n_all, log2_cells_max, d_G);
+                        nd ? packed_image(packed[nd - 1], kmin, key_dt) : 0, nd, n_all, log2_cells_max, d_G, key_dt);
   // the payload is each key's group rank (a bitmap-ranked group column) or
   // there is no group column
   const bool ranks_in_payload = dom == nullptr || dom->on;
@@ -528,58 +567,114 @@ struct EmitArgs {
   StarPlan* plan;
 };
 
-__global__ void dir_emit_kernel(EmitArgs a) {
+// Each warp takes 32 consecutive sorted positions: one coalesced load of
+// the keys and ranks, cell heads found by ballot, a head's count from the
+// next head in the warp (or, for a cell that runs past the warp, from the
+// keys after it), its inline keys and ranks from the following lanes.  Each
+// head writes its record and the (zero) records of the empty cells before
+// it.
+constexpr int kEmitThreads = 256;
+
+__global__ void __launch_bounds__(kEmitThreads) dir_emit_kernel(EmitArgs a) {
   const DimDir r = *a.dd;
   if (!r.fused) return;
   const int64_t nd = clamp_n(a.n_max, a.d_n);
   const long long kmin = a.gp->kmin[0];
   const bool k32 = a.key_dt == TQP_I32;
   const int cap = cell_inline(k32);
-  auto cell_at = [&](int64_t q) -> long long {
-    return (long long)((packed_image(__ldg(&a.packed[q]), kmin, a.key_dt) - r.umin) >> r.bshift);
-  };
+  const int lane = threadIdx.x & 31;
+  auto image_at = [&](int64_t q) -> unsigned long long { return packed_image(__ldg(&a.packed[q]), kmin, a.key_dt); };
+  auto cell_of = [&](unsigned long long u) -> long long { return (long long)((u - r.umin) >> r.bshift); };
   auto rank_at = [&](int64_t q) -> int32_t { return a.has_group ? __ldg(&a.payload[q]) : 0; };
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nd; p += stride) {
-    const unsigned long long pk = __ldg(&a.packed[p]);
-    const unsigned long long u = packed_image(pk, kmin, a.key_dt);
-    if (p > 0 && __ldg(&a.packed[p - 1]) == pk) {
+  const int64_t step = (((int64_t)gridDim.x * blockDim.x) >> 5) * 32;
+  // the next chunk's key, rank (and, in lane 0, the key before it) are
+  // loaded while the current chunk is processed
+  auto fetch = [&](int64_t q, unsigned long long& pk, int32_t& rk, unsigned long long& before) {
+    pk = 0;
+    rk = 0;
+    before = 0;
+    if (q < nd) {
+      pk = __ldg(&a.packed[q]);
+      rk = rank_at(q);
+      if (lane == 0 && q > 0) before = __ldg(&a.packed[q - 1]);
+    }
+  };
+  int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+  unsigned long long pk_n, before_n;
+  int32_t rk_n;
+  fetch(base + lane, pk_n, rk_n, before_n);
+  for (; base < nd; base += step) {
+    const int64_t p = base + lane;
+    const bool valid = p < nd;
+    const unsigned long long pk = pk_n, before = before_n;
+    const int32_t rk = rk_n;
+    fetch(base + step + lane, pk_n, rk_n, before_n);
+    const unsigned long long u = valid ? packed_image(pk, kmin, a.key_dt) : 0ull;
+    const long long c = valid ? cell_of(u) : -2;
+    unsigned long long prev_pk = __shfl_up_sync(0xffffffffu, pk, 1);
+    long long prev_c = __shfl_up_sync(0xffffffffu, c, 1);
+    if (lane == 0) {
+      prev_pk = p > 0 ? before : ~pk;
+      prev_c = p > 0 ? cell_of(packed_image(prev_pk, kmin, a.key_dt)) : -1;
+    }
+    if (valid && p > 0 && prev_pk == pk) {
       if (atomicExch(&a.plan->unsupported, 1) == 0) raise_status(TQP_ERR_UNSUPPORTED);
     }
-    const long long c = (long long)((u - r.umin) >> r.bshift);
-    const long long prev = p ? cell_at(p - 1) : -1;
-    if (c == prev) continue;
-    // the first key of cell c writes the cell's bit, the records of the
-    // empty cells before it and its own, and the key/rank pairs of the keys
-    // beyond the record's inline ones (the only pairs a probe reads)
-    if (r.use_bits) atomicOr(&a.bitmap[c >> 5], 1u << (c & 31));
-    for (long long h = prev + 1; h < c; ++h) {
-      a.table[h].a = make_int4(0, 0, 0, 0);
-      a.table[h].b = make_int4(0, 0, (int)p, 0);
+    const bool head = valid && c != prev_c;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    // the following lanes' keys and ranks (inline keys of a head)
+    unsigned long long un[3];
+    int32_t rn[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      un[j] = __shfl_down_sync(0xffffffffu, u, j);
+      rn[j] = __shfl_down_sync(0xffffffffu, rk, j);
     }
-    int64_t e = p + 1;
-    while (e < nd && cell_at(e) == c) ++e;
-    const int cnt = (int)(e - p);
-    uint32_t w[8] = {0, 0, 0, 0, 0, 0, (uint32_t)p, (uint32_t)cnt};
-    for (int j = 0; j < cnt; ++j) {
-      const unsigned long long uj = j ? packed_image(__ldg(&a.packed[p + j]), kmin, a.key_dt) : u;
-      const int32_t rj = rank_at(p + j);
-      if (j >= cap) {
+    if (head) {
+      // the first key of cell c writes the cell's bit, its record, the
+      // records of the empty cells before it, and the key/rank pairs of the
+      // keys beyond the record's inline ones (the only pairs a probe reads)
+      if (r.use_bits) atomicOr(&a.bitmap[c >> 5], 1u << (c & 31));
+      for (long long h = prev_c + 1; h < c; ++h) {
+        a.table[h].a = make_int4(0, 0, 0, 0);
+        a.table[h].b = make_int4(0, 0, 0, 0);
+      }
+      const unsigned later = lane < 31 ? heads & (0xfffffffeu << lane) : 0u;
+      int64_t e;
+      if (later) {
+        e = base + (__ffs(later) - 1);
+      } else {
+        e = base + 32;
+        while (e < nd && cell_of(image_at(e)) == c) ++e;
+        if (e > nd) e = nd;
+      }
+      const int cnt = (int)(e - p);
+      uint32_t w[8] = {0, 0, 0, 0, 0, 0, (uint32_t)p, (uint32_t)cnt};
+      const int ninl = cnt < cap ? cnt : cap;
+      for (int j = 0; j < ninl; ++j) {
+        const bool in_warp = lane + j < 32;
+        const unsigned long long uj = in_warp ? (j == 0 ? un[0] : j == 1 ? un[1] : un[2]) : image_at(p + j);
+        const int32_t rj = in_warp ? (j == 0 ? rn[0] : j == 1 ? rn[1] : rn[2]) : rank_at(p + j);
+        if (k32) {
+          w[j] = (uint32_t)uj;
+          w[3 + j] = (uint32_t)rj;
+        } else {
+          w[2 * j] = (uint32_t)uj;
+          w[2 * j + 1] = (uint32_t)(uj >> 32);
+          w[4 + j] = (uint32_t)rj;
+        }
+      }
+      for (int j = cap; j < cnt; ++j) {
+        const unsigned long long uj = image_at(p + j);
+        const int32_t rj = rank_at(p + j);
         if (k32)
           static_cast<KeyRank32*>(a.kr)[p + j] = KeyRank32{(uint32_t)uj, rj};
         else
           static_cast<KeyRank64*>(a.kr)[p + j] = KeyRank64{uj, (long long)rj};
-      } else if (k32) {
-        w[j] = (uint32_t)uj;
-        w[3 + j] = (uint32_t)rj;
-      } else {
-        w[2 * j] = (uint32_t)uj;
-        w[2 * j + 1] = (uint32_t)(uj >> 32);
-        w[4 + j] = (uint32_t)rj;
       }
+      a.table[c].a = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+      a.table[c].b = make_int4((int)w[4], (int)w[5], (int)w[6], (int)w[7]);
     }
-    a.table[c].a = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
-    a.table[c].b = make_int4((int)w[4], (int)w[5], (int)w[6], (int)w[7]);
   }
 }
 

@@ -994,7 +994,7 @@ LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int ro
     w.apk = c.take<unsigned long long>(nn);
     w.arow = c.take<int32_t>(nn);
   }
-  w.queue = c.take<uint32_t>(2);
+  w.queue = c.take<uint32_t>(3);
   w.big_flags = c.take<uint32_t>((size_t)B);
   w.tstart = c.take<unsigned>((1 << kSplitCoarseBits) + 1);
   if (scatter) w.fine = c.take<unsigned short>(nn);
@@ -1110,6 +1110,13 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
     TQP_CUDA(smem_optin(sk, (int)ssm));
     const int64_t ptiles = (n + kPartThreads * kPartItems - 1) / (kPartThreads * kPartItems);
     const int gh = hmode == kBlockHist ? w.nblk : persistent_grid(hk, kPartThreads, hsm, ptiles);
+    // two-level scatter with the counting pass's ids and global counters:
+    // the pass counts coarse buckets in shared memory, and the fine counts
+    // are taken after split 1 from its fine ids (one atomic per tile and
+    // fine bucket instead of one per row)
+    const int Fsplit = split_fine_bits(B);
+    const bool late_fine = !want_heavy && pa.ids != nullptr && Fsplit > 0 && hmode != kBlockHist;
+    pa.coarse_F = late_fine ? Fsplit : 0;
     hk<<<gh, kPartThreads, hsm, s>>>(pa); note_launch();
     TQP_LAUNCHED();
     if (hmode == kBlockHist) {
@@ -1149,6 +1156,14 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
         note_launch();
         TQP_LAUNCHED();
         const int64_t tiles2 = tiles1 + (B >> F) + 1;
+        if (late_fine) {
+          TQP_CUDA(cudaMemsetAsync(w.count, 0, (size_t)B * sizeof(unsigned), s));
+          lp_fine_count_kernel<<<persistent_grid(lp_fine_count_kernel, kSplitThreads, 0, tiles2), kSplitThreads, 0, s>>>(
+              w.lp, F, w.off, w.tstart, w.fine, w.count);
+          note_launch();
+          lp_offsets_kernel<<<1, 1024, 0, s>>>(w.lp, w.count, w.off, w.cursor, d_stats, w.loss, w.epochs, w.light_n);
+          note_launch();
+        }
         k2<<<persistent_grid(k2, kSplitThreads, xsm2, tiles2), kSplitThreads, xsm2, s>>>(w.lp, F, w.off, w.tstart, w.apk,
                                                                                             w.arow, w.fine, w.cursor, w.lpk,
                                                                                             w.lrow);
@@ -1169,11 +1184,12 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
     ba.alt_row = w.arow;
     ba.queue = w.queue;
     ba.big_flags = w.big_flags;
+    ba.only_flagged = 0;
     size_t smem = (size_t)kLocalCap * (8 + 8 + 4 + 4) + (size_t)kLocalWarps * (kRadix + 1) * 4 + kRadix * 4;
     size_t wsmem = (size_t)kWarpSortWarps * (2 * kWarpCap * 8 + (kRadix + 1) * 4);
     TQP_CUDA(smem_optin(lp_bucket_sort_kernel, (int)smem));
     TQP_CUDA(smem_optin(lp_bucket_sort_warp_kernel, (int)wsmem));
-    TQP_CUDA(cudaMemsetAsync(w.queue, 0, 2 * sizeof(uint32_t), s));
+    TQP_CUDA(cudaMemsetAsync(w.queue, 0, 3 * sizeof(uint32_t), s));
     TQP_CUDA(cudaMemsetAsync(w.big_flags, 0, (size_t)B * sizeof(uint32_t), s));
     {
       int gw = persistent_grid(lp_bucket_sort_warp_kernel, kWarpSortWarps * 32, wsmem,
@@ -1186,6 +1202,15 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
     int g = w.nblk;
     if (g > B) g = B;
     prof_mark(7, true, s);
+    if (!want_heavy) {
+      // distinct, spread keys (no heavy keys): the MSD kernel at two blocks
+      // per SM takes the buckets it can; the block kernel the rest
+      TQP_CUDA(smem_optin(lp_bucket_msd_kernel, (int)kMsdSortSmem));
+      const int gm = persistent_grid(lp_bucket_msd_kernel, kLocalThreads, kMsdSortSmem, B);
+      lp_bucket_msd_kernel<<<gm, kLocalThreads, kMsdSortSmem, s>>>(ba, w.queue + 2, w.big_flags); note_launch();
+      TQP_LAUNCHED();
+      ba.only_flagged = 1;
+    }
     lp_bucket_sort_kernel<<<g, kLocalThreads, smem, s>>>(ba); note_launch();
     TQP_LAUNCHED();
     prof_mark(7, false, s);
@@ -1570,7 +1595,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     {
       // wide cells number at most 2^t with 2^t >= 2 x the dimension's rows
       int t = 1;
-      while (t < w.log2cells && (1ll << t) < 2 * D.n) ++t;
+      while (t < w.log2cells && (1ll << t) < wide_cells_wanted(D.n, D.key.dtype)) ++t;
       w.table = c.take<DirCell>((size_t)(1ll << t) + 1);
     }
     w.rank_cell = c.take<int32_t>((size_t)(1ll << w.log2cells) + 1);
@@ -1683,13 +1708,13 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       }
       // after the sort path (which then counted no groups): the bitmap's ranks
       TQP_CUDA(cudaMemsetAsync(w.dbits, 0, (size_t)w.dwords * sizeof(uint32_t), s));
-      dom_mark_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(D.group.data, D.group.dtype, w.sel, D.n, dcnt, w.dom,
-                                                              w.dbits); note_launch();
+      const int gd = stride_grid((D.n + kDomItems - 1) / kDomItems, 256);
+      dom_mark_kernel<<<gd, 256, 0, s>>>(D.group.data, D.group.dtype, w.sel, D.n, dcnt, w.dom, w.dbits); note_launch();
       dom_scan_kernel<1024><<<1, 1024, 0, s>>>(w.dom, w.dbits, w.dpre, w.gkey, w.G); note_launch();
       // the key sort's payload: the group rank itself when the bitmap ranks
       // and no value of this dimension is aggregated, else the row
-      dom_payload_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(D.group.data, D.group.dtype, w.sel, D.n, dcnt, w.dom,
-                                                                 w.dbits, w.dpre, w.rank_payload, w.payload);
+      dom_payload_kernel<<<gd, 256, 0, s>>>(D.group.data, D.group.dtype, w.sel, D.n, dcnt, w.dom, w.dbits, w.dpre,
+                                            w.rank_payload, w.payload);
       note_launch();
       vin = w.payload;
     } else if (D.group.data) {
@@ -1775,7 +1800,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
         ea.bitmap = w.bitmap;
         ea.table = w.table;
         ea.plan = plan;
-        dir_emit_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(ea); note_launch();
+        dir_emit_kernel<<<stride_grid(D.n, kEmitThreads), kEmitThreads, 0, s>>>(ea); note_launch();
       }
       dir_fill_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(w.skeys, D.key.dtype, D.n, kn, w.dplan, w.dir,
                                                              w.bitmap);
@@ -1798,7 +1823,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
       dir_cells_kernel<<<stride_grid(D.n, 256), 256, 0, s>>>(ca); note_launch();
       {
         int t = 1;
-        while (t < w.log2cells && (1ll << t) < 2 * D.n) ++t;
+        while (t < w.log2cells && (1ll << t) < wide_cells_wanted(D.n, D.key.dtype)) ++t;
         dir_table_kernel<<<stride_grid((1ll << t) + 1, 256), 256, 0, s>>>(w.kr, D.key.dtype, w.dplan, w.dir, w.table);
         note_launch();
       }
