@@ -1109,7 +1109,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="star", choices=sorted(WORKLOADS))
-    ap.add_argument("--extra", default="skew,batched",
+    ap.add_argument("--extra", default="skew,batched,q14",
                     help="other workloads measured in the same run and attached under 'extra' ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="", help="skew, star: 'plain' times the plain radix path as the step")

@@ -65,6 +65,22 @@ __device__ __forceinline__ void load_many_as_i64(const void* p, int dt, const in
   }
 }
 
+// Group ranks over a small value domain (see the star join's dimension
+// group columns): a bitmap marks the values present, and the dense rank of
+// v is the number of marked values below it, from a per-word prefix count
+// and one popcount.
+struct DomPlan {
+  int on;       // 1: the domain path gives the ranks (the sort path then runs on no rows)
+  int words;    // bitmap words over [kmin, kmax]
+  long long kmin;
+};
+
+__device__ __forceinline__ int32_t dom_rank(const DomPlan& p, const uint32_t* bits, const int* pre, long long v) {
+  const unsigned long long x = (unsigned long long)v - (unsigned long long)p.kmin;
+  const uint32_t w = (uint32_t)(x >> 5);
+  return pre[w] + __popc(bits[w] & ((1u << (x & 31)) - 1u));
+}
+
 __device__ __forceinline__ void store_from_i64(void* p, int dt, int64_t i, int64_t v) {
   switch (dt) {
     case TQP_I8: static_cast<int8_t*>(p)[i] = static_cast<int8_t>(v); break;

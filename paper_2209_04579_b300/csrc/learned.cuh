@@ -901,6 +901,7 @@ __global__ void __launch_bounds__(1024) lp_offsets_kernel(const LearnedPlan* lp,
   unsigned sum = 0, mx = 0;
   int over = 0, ne = 0;
   unsigned long long over_rows = 0, small_rows = 0;
+#pragma unroll 8
   for (int b = b0; b < b0 + per && b < B; ++b) {
     unsigned c = count[b];
     sum += c;
@@ -913,6 +914,7 @@ __global__ void __launch_bounds__(1024) lp_offsets_kernel(const LearnedPlan* lp,
   int total;
   int excl = block_exclusive_sum<1024>((int)sum, s_scan, &total);
   unsigned run = (unsigned)excl;
+#pragma unroll 8
   for (int b = b0; b < b0 + per && b < B; ++b) {
     off[b] = run;
     cursor[(size_t)b * kCursorStride] = run;
@@ -1066,8 +1068,15 @@ __global__ void __launch_bounds__(kPartThreads, 1) lp_scatter_kernel(PartArgs a,
 // One atomic per (tile, bin) replaces the returning per-row atomic of
 // lp_scatter_kernel, whose latency bounded it.
 constexpr int kSplitThreads = 512, kSplitItems = 8, kSplitTile = kSplitThreads * kSplitItems;
-constexpr int kSplitMaxBins = 512;
-constexpr int kSplitCoarseBits = 8;
+#ifndef TQP_SPLIT_COARSE_BITS
+#define TQP_SPLIT_COARSE_BITS 8
+#endif
+constexpr int kSplitCoarseBits = TQP_SPLIT_COARSE_BITS;  // at most 256 coarse buckets (split 1's bins)
+// bins of one split: the coarse buckets, or the buckets of one coarse bucket
+// (B <= 2^17)
+constexpr int kSplitMaxBins = (1 << kSplitCoarseBits) > (1 << (17 - kSplitCoarseBits)) ? (1 << kSplitCoarseBits)
+                                                                                       : (1 << (17 - kSplitCoarseBits));
+static_assert(kSplitCoarseBits <= 8, "split tiles are planned by one block of 256 threads");
 // The bucket function's steps in shared memory when they fit (one block per
 // SM), else read from global memory (several blocks per SM).
 #ifndef TQP_SPLIT_THR_SHARED

@@ -118,11 +118,6 @@ __global__ void __launch_bounds__(THREADS) rank_kernel(const K* sorted, const in
 constexpr int kDomBits = 24;
 constexpr int kDomSmemWords = 2048;  // domains up to 2^16 values are marked in shared memory first
 
-struct DomPlan {
-  int on;       // 1: the domain path gives the ranks (the sort path then runs on no rows)
-  int words;    // bitmap words over [kmin, kmax]
-  long long kmin;
-};
 
 __global__ void dom_plan_kernel(const GroupPlan* gp, int64_t n_max, const int64_t* d_n, DomPlan* dp,
                                 int64_t* sort_n) {
@@ -149,29 +144,60 @@ __global__ void __launch_bounds__(256) dom_mark_kernel(const void* gcol, int gdt
     for (int i = threadIdx.x; i < p.words; i += blockDim.x) s_bits[i] = 0;
     __syncthreads();
   }
-  // kDomItems rows per thread at a time, their loads issued together
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kDomItems;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kDomItems + threadIdx.x; base < n; base += stride) {
-    int64_t row[kDomItems];
-    bool ok[kDomItems];
-    long long val[kDomItems];
-#pragma unroll
-    for (int k = 0; k < kDomItems; ++k) {
-      const int64_t i = base + (int64_t)k * blockDim.x;
-      ok[k] = i < n;
-      row[k] = ok[k] ? (sel ? sel[i] : i) : 0;
+  auto mark = [&](long long x) {
+    const unsigned long long v = (unsigned long long)x - (unsigned long long)p.kmin;
+    const uint32_t w = (uint32_t)(v >> 5), b = 1u << (v & 31);
+    if (shared) {
+      if (!(s_bits[w] & b)) atomicOr(&s_bits[w], b);
+    } else if (!(__ldcg(&bits[w]) & b)) {
+      atomicOr(&bits[w], b);
     }
-    load_many_as_i64(gcol, gdt, row, ok, val);
+  };
+  const int esz = gdt == TQP_I8 ? 1 : gdt == TQP_I16 ? 2 : 0;
+  if (sel == nullptr && esz && ((uintptr_t)gcol & 15) == 0) {
+    // a 1- or 2-byte column read as 16-byte words, four in flight per
+    // thread, then the scalar tail
+    const int per = 16 / esz;
+    const int64_t nw = n / per;
+    const int4* wp = static_cast<const int4*>(gcol);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < nw; base += stride * 4) {
+      int4 v[4];
 #pragma unroll
-    for (int k = 0; k < kDomItems; ++k) {
-      if (!ok[k]) continue;
-      const unsigned long long v = (unsigned long long)val[k] - (unsigned long long)p.kmin;
-      const uint32_t w = (uint32_t)(v >> 5), b = 1u << (v & 31);
-      if (shared) {
-        if (!(s_bits[w] & b)) atomicOr(&s_bits[w], b);
-      } else if (!(__ldcg(&bits[w]) & b)) {
-        atomicOr(&bits[w], b);
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(wp + (base + u * stride < nw ? base + u * stride : base));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (base + u * stride >= nw) continue;
+        if (esz == 1) {
+          const signed char* e = reinterpret_cast<const signed char*>(&v[u]);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) mark(e[j]);
+        } else {
+          const short* e = reinterpret_cast<const short*>(&v[u]);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) mark(e[j]);
+        }
       }
+    }
+    for (int64_t i = nw * per + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+      mark(load_as_i64(gcol, gdt, i));
+  } else {
+    // kDomItems rows per thread at a time, their loads issued together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kDomItems;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kDomItems + threadIdx.x; base < n; base += stride) {
+      int64_t row[kDomItems];
+      bool ok[kDomItems];
+      long long val[kDomItems];
+#pragma unroll
+      for (int k = 0; k < kDomItems; ++k) {
+        const int64_t i = base + (int64_t)k * blockDim.x;
+        ok[k] = i < n;
+        row[k] = ok[k] ? (sel ? sel[i] : i) : 0;
+      }
+      load_many_as_i64(gcol, gdt, row, ok, val);
+#pragma unroll
+      for (int k = 0; k < kDomItems; ++k)
+        if (ok[k]) mark(val[k]);
     }
   }
   if (shared) {
@@ -207,11 +233,6 @@ __global__ void __launch_bounds__(THREADS) dom_scan_kernel(const DomPlan* dp, co
   if (threadIdx.x == 0) *d_G = total;
 }
 
-__device__ __forceinline__ int32_t dom_rank(const DomPlan& p, const uint32_t* bits, const int* pre, long long v) {
-  const unsigned long long x = (unsigned long long)v - (unsigned long long)p.kmin;
-  const uint32_t w = (uint32_t)(x >> 5);
-  return pre[w] + __popc(bits[w] & ((1u << (x & 31)) - 1u));
-}
 
 // Sort payload of the passing rows: the group rank when the bitmap ranks and
 // the caller allows it (rank_payload), else the row.
