@@ -438,7 +438,7 @@ class Star:
     def traffic(self):
         # ncu DRAM bytes (read + write) of one full-size probe launch; a scaled
         # case scales its fact rows, dimension rows and survivors together
-        return ("star_probe_kernel", int((72_420_000_000 + 3_610_000) / self.scale),
+        return ("star_probe_kernel", int((72_241_741_824 + 3_328_512) / self.scale),
                 "profiles/star_probe_star_join_600M_traffic.md" + ("" if self.scale == 1 else f" (/{self.scale})"))
 
     def oracle_sample(self, rows):

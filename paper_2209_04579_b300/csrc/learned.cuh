@@ -1420,7 +1420,9 @@ struct BucketSortArgs {
   int32_t* alt_row;
   uint32_t* queue;
   const uint32_t* big_flags;  // null, or: small buckets handled by the warp kernel unless flagged (bit 0)
-  int only_flagged;           // the MSD kernel ran first: sort only the buckets it flagged (bit 1)
+  int only_flagged;           // the MSD kernel ran first: sort only the buckets it flagged (bit 1),
+  uint32_t* flagged;          // listed here by the MSD kernel
+  uint32_t* nflagged;         // (their count)
 };
 
 __device__ __forceinline__ bool warp_bucket_size(long long m) { return m > 1 && m <= 1024; }
@@ -1765,12 +1767,14 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
   L.scan = s_scan;
   L.red = s_red;
   const int B = a.lp->B;
+  const uint32_t nlist = a.only_flagged ? *a.nflagged : 0u;
   while (true) {
     if (threadIdx.x == 0) s_b = atomicAdd(a.queue, 1u);
     __syncthreads();
-    const uint32_t b = s_b;
+    const uint32_t i = s_b;
     __syncthreads();
-    if (b >= (uint32_t)B) break;
+    if (a.only_flagged ? i >= nlist : i >= (uint32_t)B) break;
+    const uint32_t b = a.only_flagged ? a.flagged[i] : i;
     const int64_t o0 = a.off[b], o1 = a.off[b + 1];
     const int64_t m = o1 - o0;
     if (m <= 1) continue;
@@ -1848,7 +1852,7 @@ __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSor
 // The rows are counted by the top kMsdBits bits of the bucket's key span,
 // placed by part, and each part (at most kSmallPart rows) is insertion-
 // sorted by one thread; a bucket with a larger part, or beyond kLocalCap
-// rows, is flagged (bit 1) for lp_bucket_sort_kernel.  Buckets of the warp
+// rows, is flagged (bit 1) and listed for lp_bucket_sort_kernel.  Buckets of the warp
 // kernel's size are skipped unless it flagged them (bit 0).
 constexpr size_t kMsdSortSmem = (size_t)kLocalCap * (8 + 4) + (size_t)kMsdBins * 4;
 
@@ -1875,7 +1879,10 @@ __global__ void __launch_bounds__(kLocalThreads, 2) lp_bucket_msd_kernel(BucketS
     const uint32_t fl = flags[b];
     if (warp_bucket_size(m) && !(fl & 1u)) continue;  // sorted by a warp
     if (m > kLocalCap) {
-      if (threadIdx.x == 0) flags[b] = fl | 2u;
+      if (threadIdx.x == 0) {
+        flags[b] = fl | 2u;
+        a.flagged[atomicAdd(a.nflagged, 1u)] = b;
+      }
       continue;
     }
     unsigned long long kr[kLocalItems];
@@ -1930,7 +1937,10 @@ __global__ void __launch_bounds__(kLocalThreads, 2) lp_bucket_msd_kernel(BucketS
     }
     __syncthreads();
     if (s_nbig) {  // a large part: the LSD of lp_bucket_sort_kernel
-      if (threadIdx.x == 0) flags[b] = fl | 2u;
+      if (threadIdx.x == 0) {
+        flags[b] = fl | 2u;
+        a.flagged[atomicAdd(a.nflagged, 1u)] = b;
+      }
       continue;
     }
 #pragma unroll

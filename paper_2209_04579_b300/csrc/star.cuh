@@ -239,9 +239,51 @@ __global__ void __launch_bounds__(THREADS) dom_scan_kernel(const DomPlan* dp, co
 __global__ void dom_payload_kernel(const void* gcol, int gdt, const int32_t* sel, int64_t n_max, const int64_t* d_n,
                                    const DomPlan* dp, const uint32_t* bits, const int* pre, int rank_payload,
                                    int32_t* out) {
+  __shared__ uint32_t s_bits[kDomSmemWords];
+  __shared__ int s_pre[kDomSmemWords];
   const DomPlan p = *dp;
   const bool rk = rank_payload && p.on;
   const int64_t n = clamp_n(n_max, d_n);
+  const int esz = gdt == TQP_I8 ? 1 : gdt == TQP_I16 ? 2 : 0;
+  if (rk && sel == nullptr && esz && p.words <= kDomSmemWords && ((uintptr_t)gcol & 15) == 0 &&
+      ((uintptr_t)out & 15) == 0) {
+    // a 1- or 2-byte group column read as 16-byte words, its bitmap and
+    // prefix counts in shared memory, the ranks written as 16-byte words;
+    // then the scalar tail
+    for (int i = threadIdx.x; i < p.words; i += blockDim.x) {
+      s_bits[i] = bits[i];
+      s_pre[i] = pre[i];
+    }
+    __syncthreads();
+    auto rank_of = [&](int v) -> int {
+      const unsigned x = (unsigned)((long long)v - p.kmin);
+      return s_pre[x >> 5] + __popc(s_bits[x >> 5] & ((1u << (x & 31)) - 1u));
+    };
+    const int per = 16 / esz;
+    const int64_t nw = n / per;
+    const int4* wp = static_cast<const int4*>(gcol);
+    int4* op = reinterpret_cast<int4*>(out);
+    const int64_t tstride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += tstride) {
+      const int4 v = __ldg(wp + w);
+      int r[16];
+      if (esz == 1) {
+        const signed char* e = reinterpret_cast<const signed char*>(&v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) r[j] = rank_of(e[j]);
+      } else {
+        const short* e = reinterpret_cast<const short*>(&v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) r[j] = rank_of(e[j]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q * 4 < per) op[w * (per / 4) + q] = make_int4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    }
+    for (int64_t i = nw * per + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += tstride)
+      out[i] = rank_of((int)load_as_i64(gcol, gdt, i));
+    return;
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x * kDomItems;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kDomItems + threadIdx.x; base < n; base += stride) {
     int64_t row[kDomItems];

@@ -934,6 +934,7 @@ struct LearnedWs {
   int32_t* arow;
   uint32_t* queue;
   uint32_t* big_flags;
+  uint32_t* flagged;  // buckets the MSD kernel left to the block kernel
   unsigned* tstart;  // two-level scatter: split 2's tile starts per coarse bucket
   unsigned* cur1;    // two-level scatter: coarse cursors
   unsigned short* fine;  // two-level scatter: each row's bucket within its coarse bucket
@@ -994,8 +995,9 @@ LearnedWs carve_learned(Carver& c, int64_t n, const tqp_learned_cfg* cfg, int ro
     w.apk = c.take<unsigned long long>(nn);
     w.arow = c.take<int32_t>(nn);
   }
-  w.queue = c.take<uint32_t>(3);
+  w.queue = c.take<uint32_t>(4);  // block, warp and MSD kernel queues; the flagged buckets' count
   w.big_flags = c.take<uint32_t>((size_t)B);
+  w.flagged = c.take<uint32_t>((size_t)B);
   w.tstart = c.take<unsigned>((1 << kSplitCoarseBits) + 1);
   if (scatter) w.fine = c.take<unsigned short>(nn);
   if (scatter && B <= 65536) w.ids = c.take<unsigned short>(nn);
@@ -1185,11 +1187,13 @@ tqp_status run_learned_partition(const LearnedWs& w, const KeySet& ks, const int
     ba.queue = w.queue;
     ba.big_flags = w.big_flags;
     ba.only_flagged = 0;
+    ba.flagged = w.flagged;
+    ba.nflagged = w.queue + 3;
     size_t smem = (size_t)kLocalCap * (8 + 8 + 4 + 4) + (size_t)kLocalWarps * (kRadix + 1) * 4 + kRadix * 4;
     size_t wsmem = (size_t)kWarpSortWarps * (2 * kWarpCap * 8 + (kRadix + 1) * 4);
     TQP_CUDA(smem_optin(lp_bucket_sort_kernel, (int)smem));
     TQP_CUDA(smem_optin(lp_bucket_sort_warp_kernel, (int)wsmem));
-    TQP_CUDA(cudaMemsetAsync(w.queue, 0, 3 * sizeof(uint32_t), s));
+    TQP_CUDA(cudaMemsetAsync(w.queue, 0, 4 * sizeof(uint32_t), s));
     TQP_CUDA(cudaMemsetAsync(w.big_flags, 0, (size_t)B * sizeof(uint32_t), s));
     {
       int gw = persistent_grid(lp_bucket_sort_warp_kernel, kWarpSortWarps * 32, wsmem,
