@@ -431,9 +431,10 @@ class Star:
                 (14, "dim1 directory and cell records", n1 * 8 * 2),
                 (15, "dim2 directory and cell records", n2 * 12 * 2),
                 # the learned partition's kernels of the last dimension sorted (dim2):
-                # the scatter reads key and rank and writes them bucketed
-                (8, "lp_scatter_kernel (dim2)", n2 * 12 * 2),
-                (7, "lp_bucket_sort_kernel (dim2)", n2 * 12 * 2)]
+                # the two-level scatter (split 1, fine counts, split 2) reads key and
+                # rank and writes them bucketed; the bucket sorts read and write them
+                (8, "learned scatter: lp_split1/2_kernel (dim2)", n2 * 12 * 2),
+                (7, "bucket sort: lp_bucket_msd_kernel + lp_bucket_sort_kernel (dim2)", n2 * 12 * 2)]
 
     def traffic(self):
         # ncu DRAM bytes (read + write) of one full-size probe launch; a scaled
