@@ -26,7 +26,8 @@
  *  - Workspace: every call that needs scratch takes (ws, ws_bytes).  Call it
  *    first with ws == NULL: it writes the bytes it needs to *ws_bytes, does
  *    nothing else and returns TQP_OK.  Then call again with a device buffer
- *    of at least that size (256-byte aligned).  The size depends only on the
+ *    of at least that size, 256-byte aligned (a misaligned workspace is
+ *    refused with TQP_ERR_INVALID before any work).  The size depends only on the
  *    host arguments (sizes, counts, dtypes), not on the data.
  *  - Row counts: n is the (maximum) row count known on the host.  Where an
  *    argument d_n is accepted, a non-NULL d_n points to a device int64 that

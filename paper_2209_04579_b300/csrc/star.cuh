@@ -638,6 +638,14 @@ struct EmitArgs {
 // it.
 constexpr int kEmitThreads = 256;
 
+// One 32-byte record in a single 256-bit store (records are 32-byte aligned:
+// the table starts on a 256-byte boundary).
+__device__ __forceinline__ void store_cell(DirCell* dst, const uint32_t (&w)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "r"(w[0]), "r"(w[1]),
+               "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+               : "memory");
+}
+
 __global__ void __launch_bounds__(kEmitThreads) dir_emit_kernel(EmitArgs a) {
   const DimDir r = *a.dd;
   if (!r.fused) return;
@@ -698,10 +706,8 @@ __global__ void __launch_bounds__(kEmitThreads) dir_emit_kernel(EmitArgs a) {
       // records of the empty cells before it, and the key/rank pairs of the
       // keys beyond the record's inline ones (the only pairs a probe reads)
       if (r.use_bits) atomicOr(&a.bitmap[c >> 5], 1u << (c & 31));
-      for (long long h = prev_c + 1; h < c; ++h) {
-        a.table[h].a = make_int4(0, 0, 0, 0);
-        a.table[h].b = make_int4(0, 0, 0, 0);
-      }
+      const uint32_t zero[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (long long h = prev_c + 1; h < c; ++h) store_cell(&a.table[h], zero);
       const unsigned later = lane < 31 ? heads & (0xfffffffeu << lane) : 0u;
       int64_t e;
       if (later) {
@@ -735,8 +741,7 @@ __global__ void __launch_bounds__(kEmitThreads) dir_emit_kernel(EmitArgs a) {
         else
           static_cast<KeyRank64*>(a.kr)[p + j] = KeyRank64{uj, (long long)rj};
       }
-      a.table[c].a = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
-      a.table[c].b = make_int4((int)w[4], (int)w[5], (int)w[6], (int)w[7]);
+      store_cell(&a.table[c], w);
     }
   }
 }

@@ -546,6 +546,7 @@ tqp_status tqp_filter(const tqp_col* cols, int ncols, const tqp_pred* preds, int
     *ws_bytes = c.off;
     return TQP_OK;
   }
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return TQP_ERR_INVALID;  // the carved arrays need it
   if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
   if (!d_out_n || (cap > 0 && !d_out_idx) || cap < 0) return TQP_ERR_INVALID;
   FilterArgs a;
@@ -637,6 +638,7 @@ tqp_status tqp_string_codes(const uint8_t* d_str, int64_t n, int32_t width, int3
     *ws_bytes = c.off;
     return TQP_OK;
   }
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return TQP_ERR_INVALID;  // the carved arrays need it
   if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
   if (!d_ncodes) return TQP_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -714,6 +716,7 @@ tqp_status tqp_sort_pairs(int32_t key_dtype, const void* d_keys_in, const int32_
     *ws_bytes = c.off;
     return TQP_OK;
   }
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return TQP_ERR_INVALID;  // the carved arrays need it
   if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
   if (n > 0 && (!d_keys_in || !d_keys_out || !d_vals_out)) return TQP_ERR_INVALID;
   return run_sort(sw, key_dtype, d_keys_in, d_vals_in, d_keys_out, d_vals_out, n, d_n, begin_bit, end_bit,
@@ -739,6 +742,7 @@ tqp_status tqp_join_eq(tqp_col probe, int64_t n_probe, const int64_t* d_n_probe,
     *ws_bytes = c.off;
     return TQP_OK;
   }
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return TQP_ERR_INVALID;  // the carved arrays need it
   if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
   if (!d_out_n || cap < 0 || (cap > 0 && (!d_out_probe || !d_out_build))) return TQP_ERR_INVALID;
   if ((n_probe > 0 && !probe.data) || (n_build > 0 && !build.data)) return TQP_ERR_INVALID;
@@ -801,6 +805,7 @@ tqp_status tqp_groupby_agg(const tqp_col* keys, int nkeys, const tqp_col* vals, 
     *ws_bytes = c.off;
     return TQP_OK;
   }
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return TQP_ERR_INVALID;  // the carved arrays need it
   if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
   if (!d_out_groups || cap < 0 || (cap > 0 && (!d_out_aggs || !d_out_keys))) return TQP_ERR_INVALID;
   KeySet ks;
@@ -843,6 +848,7 @@ tqp_status tqp_cdf_backward(const tqp_cdf_model* d_model, const float* d_x, cons
     *ws_bytes = c.off;
     return TQP_OK;
   }
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return TQP_ERR_INVALID;  // the carved arrays need it
   if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
   if (!d_model || !d_grad || (n > 0 && (!d_x || !d_y))) return TQP_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -890,6 +896,7 @@ tqp_status tqp_cdf_train(const float* d_x, const float* d_y, int64_t n, tqp_cdf_
     *ws_bytes = c.off;
     return TQP_OK;
   }
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return TQP_ERR_INVALID;  // the carved arrays need it
   if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
   if (!d_x || !d_y || !d_model) return TQP_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -1277,6 +1284,7 @@ tqp_status tqp_groupby_agg_learned(const tqp_col* keys, int nkeys, const tqp_col
     *ws_bytes = c.off;
     return TQP_OK;
   }
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return TQP_ERR_INVALID;  // the carved arrays need it
   if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
   if (!d_out_groups || cap < 0 || (cap > 0 && (!d_out_aggs || !d_out_keys))) return TQP_ERR_INVALID;
   KeySet ks;
@@ -1350,6 +1358,7 @@ tqp_status tqp_partition_learned(const tqp_col* keys, int nkeys, const int32_t* 
     *ws_bytes = c.off;
     return TQP_OK;
   }
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return TQP_ERR_INVALID;  // the carved arrays need it
   if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
   KeySet ks;
   std::memset(&ks, 0, sizeof(ks));
@@ -1618,6 +1627,7 @@ tqp_status star_agg_impl(const tqp_col* fact_cols, int nfact_cols, int64_t n_fac
     *ws_bytes = c.off;
     return TQP_OK;
   }
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return TQP_ERR_INVALID;  // the carved arrays need it
   if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
   if (!d_out_groups || cap < 0 || (cap > 0 && (!d_out_aggs || (nout_keys && !d_out_keys)))) return TQP_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -2092,6 +2102,7 @@ tqp_status tqp_star_agg_batched(const tqp_batch_shape* shape, const tqp_problem*
     *ws_bytes = c.off;
     return TQP_OK;
   }
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return TQP_ERR_INVALID;  // the carved arrays need it
   if (*ws_bytes < c.off) return TQP_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // ---- descriptors through kernel parameters (capturable, no host buffer kept)

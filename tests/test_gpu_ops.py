@@ -370,3 +370,23 @@ def test_sort_every_tile_choice(T, items32, items64):
     finally:
         T.tqp_sort_tiles(16, 12)
     assert T.tqp_status_poll() == T.OK
+
+
+def test_misaligned_workspace_is_rejected(T):
+    """A workspace off the 256-byte boundary the header asks for is refused
+    before any launch; the same call on the aligned buffer sorts."""
+    import ctypes
+    keys = torch.arange(1000, 0, -1, dtype=torch.int64, device="cuda")
+    ko = torch.empty_like(keys)
+    vo = torch.empty(1000, dtype=torch.int32, device="cuda")
+    args = [T._DTYPE[keys.dtype], T._ptr(keys), None, T._ptr(ko), T._ptr(vo), 1000, None, 0, 64]
+    need = ctypes.c_size_t(0)
+    assert T._lib.tqp_sort_pairs(*args, None, ctypes.byref(need), None) == T.OK
+    ws = torch.empty(need.value + 512, dtype=torch.uint8, device="cuda")
+    have = ctypes.c_size_t(need.value)
+    base = ws.data_ptr()
+    aligned = (base + 255) & ~255
+    assert T._lib.tqp_sort_pairs(*args, ctypes.c_void_p(aligned + 32), ctypes.byref(have), None) == T.ERR_INVALID
+    assert T._lib.tqp_sort_pairs(*args, ctypes.c_void_p(aligned), ctypes.byref(have), None) == T.OK
+    torch.cuda.synchronize()
+    assert torch.equal(ko, torch.arange(1, 1001, dtype=torch.int64, device="cuda"))
