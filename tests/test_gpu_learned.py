@@ -118,7 +118,12 @@ def compare(got, want):
 
 @pytest.mark.parametrize("n", [1, 1000, 70_001, 3_000_000])
 @pytest.mark.parametrize("train,heavy,buckets", [(1, 1, 0), (0, 1, 0), (1, 0, 0), (1, 1, 2), (0, 0, 16), (1, 1, 1 << 15),
-                                                (1, 1, 1 << 17)])
+                                                (1, 1, 1 << 17),
+                                                # no heavy keys, repeated keys: buckets of thousands of rows
+                                                # (the MSD kernel, which flags parts holding several keys),
+                                                # and more buckets than one block counts (coarse counts,
+                                                # fine counts after split 1)
+                                                (1, 0, 1 << 10), (0, 0, 1 << 15)])
 def test_learned_groupby_parity(T, n, train, heavy, buckets):
     from paper_2209_04579_b300 import datagen_device as gd
     from paper_2209_04579_b300 import queries as Q
