@@ -630,12 +630,12 @@ struct EmitArgs {
   StarPlan* plan;
 };
 
-// Each warp takes 32 consecutive sorted positions: one coalesced load of
-// the keys and ranks, cell heads found by ballot, a head's count from the
-// next head in the warp (or, for a cell that runs past the warp, from the
-// keys after it), its inline keys and ranks from the following lanes.  Each
-// head writes its record and the (zero) records of the empty cells before
-// it.
+// A warp takes 32 consecutive sorted positions at a time: one coalesced load
+// of the keys and ranks, cell heads found by ballot, a head's count from the
+// next head in the chunk (or, for the chunk's last cell, in the next chunk,
+// which is already loaded), its inline keys and ranks from the following
+// lanes.  Each head writes its record and the (zero) records of the empty
+// cells before it.
 constexpr int kEmitThreads = 256;
 
 // One 32-byte record in a single 256-bit store (records are 32-byte aligned:
@@ -657,29 +657,35 @@ __global__ void __launch_bounds__(kEmitThreads) dir_emit_kernel(EmitArgs a) {
   auto image_at = [&](int64_t q) -> unsigned long long { return packed_image(__ldg(&a.packed[q]), kmin, a.key_dt); };
   auto cell_of = [&](unsigned long long u) -> long long { return (long long)((u - r.umin) >> r.bshift); };
   auto rank_at = [&](int64_t q) -> int32_t { return a.has_group ? __ldg(&a.payload[q]) : 0; };
-  const int64_t step = (((int64_t)gridDim.x * blockDim.x) >> 5) * 32;
-  // the next chunk's key, rank (and, in lane 0, the key before it) are
-  // loaded while the current chunk is processed
-  auto fetch = [&](int64_t q, unsigned long long& pk, int32_t& rk, unsigned long long& before) {
+  // each warp takes a contiguous run of 32-position chunks; the next chunk's
+  // keys and ranks are loaded while the current chunk is processed, and give
+  // the last cell of a chunk its count and its inline keys past the chunk
+  auto fetch = [&](int64_t q, unsigned long long& pk, int32_t& rk) {
     pk = 0;
     rk = 0;
-    before = 0;
     if (q < nd) {
       pk = __ldg(&a.packed[q]);
       rk = rank_at(q);
-      if (lane == 0 && q > 0) before = __ldg(&a.packed[q - 1]);
     }
   };
-  int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
-  unsigned long long pk_n, before_n;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nchunks = (nd + 31) / 32;
+  const int64_t per = (nchunks + nwarps - 1) / nwarps;
+  const int64_t cbeg = wid * per;
+  const int64_t cend = cbeg + per < nchunks ? cbeg + per : nchunks;
+  if (cbeg >= cend) return;
+  int64_t base = cbeg * 32;
+  unsigned long long pk_n;
   int32_t rk_n;
-  fetch(base + lane, pk_n, rk_n, before_n);
-  for (; base < nd; base += step) {
+  fetch(base + lane, pk_n, rk_n);
+  unsigned long long before = base > 0 ? __ldg(&a.packed[base - 1]) : 0ull;  // the key before the run
+  for (int64_t ch = cbeg; ch < cend; ++ch, base += 32) {
     const int64_t p = base + lane;
     const bool valid = p < nd;
-    const unsigned long long pk = pk_n, before = before_n;
+    const unsigned long long pk = pk_n;
     const int32_t rk = rk_n;
-    fetch(base + step + lane, pk_n, rk_n, before_n);
+    fetch(base + 32 + lane, pk_n, rk_n);
     const unsigned long long u = valid ? packed_image(pk, kmin, a.key_dt) : 0ull;
     const long long c = valid ? cell_of(u) : -2;
     unsigned long long prev_pk = __shfl_up_sync(0xffffffffu, pk, 1);
@@ -688,19 +694,29 @@ __global__ void __launch_bounds__(kEmitThreads) dir_emit_kernel(EmitArgs a) {
       prev_pk = p > 0 ? before : ~pk;
       prev_c = p > 0 ? cell_of(packed_image(prev_pk, kmin, a.key_dt)) : -1;
     }
+    before = __shfl_sync(0xffffffffu, pk, 31);  // the next chunk's predecessor
     if (valid && p > 0 && prev_pk == pk) {
       if (atomicExch(&a.plan->unsupported, 1) == 0) raise_status(TQP_ERR_UNSUPPORTED);
     }
     const bool head = valid && c != prev_c;
     const unsigned heads = __ballot_sync(0xffffffffu, head);
-    // the following lanes' keys and ranks (inline keys of a head)
-    unsigned long long un[3];
-    int32_t rn[3];
+    // the following lanes' keys and ranks (inline keys of a head), in this
+    // chunk or, past lane 31, in the next
+    const bool valid_n = base + 32 + lane < nd;
+    const unsigned long long u_n = valid_n ? packed_image(pk_n, kmin, a.key_dt) : 0ull;
+    unsigned long long un[3], wn[3];
+    int32_t rn[3], wr[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       un[j] = __shfl_down_sync(0xffffffffu, u, j);
       rn[j] = __shfl_down_sync(0xffffffffu, rk, j);
+      wn[j] = __shfl_sync(0xffffffffu, u_n, (lane + j) & 31);
+      wr[j] = __shfl_sync(0xffffffffu, rk_n, (lane + j) & 31);
     }
+    // where the chunk's last cell ends in the next chunk
+    const int last = nd - base < 32 ? (int)(nd - base) - 1 : 31;
+    const long long c_last = __shfl_sync(0xffffffffu, c, last);
+    const unsigned ends = __ballot_sync(0xffffffffu, valid_n && cell_of(u_n) != c_last);
     if (head) {
       // the first key of cell c writes the cell's bit, its record, the
       // records of the empty cells before it, and the key/rank pairs of the
@@ -712,8 +728,10 @@ __global__ void __launch_bounds__(kEmitThreads) dir_emit_kernel(EmitArgs a) {
       int64_t e;
       if (later) {
         e = base + (__ffs(later) - 1);
-      } else {
-        e = base + 32;
+      } else if (ends) {  // the chunk's last cell ends in the next chunk
+        e = base + 32 + (__ffs(ends) - 1);
+      } else {  // it covers the next chunk's keys (or the keys end)
+        e = base + 64;
         while (e < nd && cell_of(image_at(e)) == c) ++e;
         if (e > nd) e = nd;
       }
@@ -722,8 +740,8 @@ __global__ void __launch_bounds__(kEmitThreads) dir_emit_kernel(EmitArgs a) {
       const int ninl = cnt < cap ? cnt : cap;
       for (int j = 0; j < ninl; ++j) {
         const bool in_warp = lane + j < 32;
-        const unsigned long long uj = in_warp ? (j == 0 ? un[0] : j == 1 ? un[1] : un[2]) : image_at(p + j);
-        const int32_t rj = in_warp ? (j == 0 ? rn[0] : j == 1 ? rn[1] : rn[2]) : rank_at(p + j);
+        const unsigned long long uj = in_warp ? (j == 0 ? un[0] : j == 1 ? un[1] : un[2]) : (j == 1 ? wn[1] : wn[2]);
+        const int32_t rj = in_warp ? (j == 0 ? rn[0] : j == 1 ? rn[1] : rn[2]) : (j == 1 ? wr[1] : wr[2]);
         if (k32) {
           w[j] = (uint32_t)uj;
           w[3 + j] = (uint32_t)rj;
