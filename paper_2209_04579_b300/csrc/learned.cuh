@@ -1746,7 +1746,8 @@ __device__ void global_lsd(unsigned long long* p, int32_t* row, unsigned long lo
 // its key span into the scratch arrays (a counting scatter: equal keys need
 // no order), then runs of consecutive parts of up to kLocalCap rows are
 // sorted on-chip back into place; a part beyond that is one key (already in
-// order) or is sorted in global memory.
+// order) or is sorted in global memory.  After lp_bucket_msd_kernel
+// (only_flagged), the block takes just the buckets that kernel listed.
 __global__ void __launch_bounds__(kLocalThreads) lp_bucket_sort_kernel(BucketSortArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_scan[33];
